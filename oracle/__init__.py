@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for the sub-domain strongly coupled immersed-boundary FSI method
+(Nair & Goza, "A strongly coupled immersed boundary method for fluid-structure
+interaction that mimics the efficiency of stationary body methods").
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it.  It shares no code with the CUDA library.
+
+Everything is plain numpy in float64.  The one library primitive used for a
+transform is a dense matrix product with the sine matrix (a naive O(N^2)
+DST-I per axis).  Small dense systems are solved with ``numpy.linalg.solve``.
+
+Module map
+  grid.py  -- staggered streamfunction/vorticity operators, DST-diagonalised
+              solves, nested multidomain levels (Sec. 2.2, Sec. 3.2.1, App. A)
+  ib.py    -- discrete delta, sub-domain interpolation E0, hat interpolation P,
+              sub-domain matrix B0 by columns (Sec. 3.1, Eqs. ibsdinterp,
+              weights, action; Algorithm 1)
+  fsi.py   -- torsional / rigid bodies, FSI iteration, one time step and runs
+              (Eqs. predictor2-corrector2, Algorithm 2, App. A)
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+except the multidomain level coupling, which is only pinned loosely (Lamb-Oseen
+convergence); see the header of ``grid.py``.
+"""
+
+from . import grid, ib, fsi  # noqa: F401

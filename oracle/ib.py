@@ -1,0 +1,150 @@
+"""Oracle: immersed-boundary coupling operators (FP64, numpy).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+* ``delta3``     -- the 3-point regularised discrete delta (reading R1: Roma,
+                    Peskin & Berger); the paper names no specific kernel (Sec. 3.1).
+* ``hat``        -- the two-point hat ``d_p`` of Sec. 3.1.2 used to build ``P``
+                    (``d_p = 0`` at ``|r| = dr``, reading R9).
+* ``Subdomain``  -- the fixed sub-domain Omega_0: a box of flow-grid vertices at
+                    spacing h (Sec. 3.1.1), and the operators
+                    ``E0`` (Eq. ibsdinterp), ``E0^T`` and ``P`` (Eq. weights).
+* ``b0_column``  -- column j of ``B0 = E0 C (C^T A C)^{-1} C^T E0^T`` computed as the
+                    action on the canonical vector e_j (Eq. action, Algorithm 1).
+
+Unknown ordering of sub-domain vectors: the ``n_sd`` x-components first, then
+the ``n_sd`` y-components; points are numbered row by row (j-major) inside the box.
+"""
+
+import numpy as np
+
+from . import grid
+
+
+def delta3(r):
+    """3-point discrete delta in grid units (reading R1)."""
+    r = np.abs(np.asarray(r, dtype=np.float64))
+    out = np.zeros_like(r)
+    m1 = r <= 0.5
+    out[m1] = (1.0 + np.sqrt(1.0 - 3.0 * r[m1] ** 2)) / 3.0
+    m2 = (r > 0.5) & (r <= 1.5)
+    out[m2] = (5.0 - 3.0 * r[m2] - np.sqrt(np.maximum(0.0, 1.0 - 3.0 * (1.0 - r[m2]) ** 2))) / 6.0
+    return out
+
+
+def hat(r, dr):
+    """Two-point hat of Sec. 3.1.2: ``1 - |r|/dr`` for ``|r| < dr``, else 0."""
+    r = np.abs(np.asarray(r, dtype=np.float64))
+    return np.where(r < dr, 1.0 - r / dr, 0.0)
+
+
+class Subdomain:
+    """Omega_0: the vertices ``i_lo..i_hi`` x ``j_lo..j_hi`` of the finest level (Sec. 3.1.1)."""
+
+    def __init__(self, lev, i_lo, i_hi, j_lo, j_hi):
+        if i_lo < 2 or j_lo < 2 or i_hi > lev.nx - 2 or j_hi > lev.ny - 2 or i_hi <= i_lo or j_hi <= j_lo:
+            raise ValueError("sub-domain must lie at least 2 cells inside the grid")
+        self.lev = lev
+        self.i_lo, self.i_hi, self.j_lo, self.j_hi = int(i_lo), int(i_hi), int(j_lo), int(j_hi)
+        self.ni = self.i_hi - self.i_lo + 1
+        self.nj = self.j_hi - self.j_lo + 1
+        self.n_sd = self.ni * self.nj
+        jj, ii = np.meshgrid(np.arange(self.j_lo, self.j_hi + 1), np.arange(self.i_lo, self.i_hi + 1), indexing="ij")
+        self.pi = ii.ravel()
+        self.pj = jj.ravel()
+
+    @classmethod
+    def from_box(cls, lev, x_lo, x_hi, y_lo, y_hi):
+        """Snap a physical box to vertices, clipped to >= 2 cells from the boundary (reading R10)."""
+        i_lo = max(int(np.ceil((x_lo - lev.x0) / lev.h - 1e-9)), 2)
+        i_hi = min(int(np.floor((x_hi - lev.x0) / lev.h + 1e-9)), lev.nx - 2)
+        j_lo = max(int(np.ceil((y_lo - lev.y0) / lev.h - 1e-9)), 2)
+        j_hi = min(int(np.floor((y_hi - lev.y0) / lev.h + 1e-9)), lev.ny - 2)
+        return cls(lev, i_lo, i_hi, j_lo, j_hi)
+
+    # -- E0 (Eq. ibsdinterp): weights d(x_face - x_k) d(y_face - y_k) --------------------
+
+    def _u_window(self):
+        """u-face indices and delta weights around every Omega_0 point (support window, zeros kept)."""
+        di = np.arange(-2, 3)
+        dj = np.arange(-2, 2)             # u[j', i'] sits at y_{j'+1/2}
+        I = self.pi[:, None, None] + di[None, None, :]
+        J = self.pj[:, None, None] + dj[None, :, None]
+        w = delta3(I - self.pi[:, None, None]) * delta3(J + 0.5 - self.pj[:, None, None])
+        return I, J, w
+
+    def _v_window(self):
+        di = np.arange(-2, 2)             # v[j', i'] sits at x_{i'+1/2}
+        dj = np.arange(-2, 3)
+        I = self.pi[:, None, None] + di[None, None, :]
+        J = self.pj[:, None, None] + dj[None, :, None]
+        w = delta3(I + 0.5 - self.pi[:, None, None]) * delta3(J - self.pj[:, None, None])
+        return I, J, w
+
+    def e0(self, u, v):
+        """``E0 q``: interpolate face fluxes to all Omega_0 points -> vector of length ``2 n_sd``."""
+        I, J, w = self._u_window()
+        u0 = np.sum(w * u[J, I], axis=(1, 2))
+        I, J, w = self._v_window()
+        v0 = np.sum(w * v[J, I], axis=(1, 2))
+        return np.concatenate([u0, v0])
+
+    def e0t(self, g):
+        """``E0^T g``: spread a sub-domain vector onto the faces (same weights, transposed)."""
+        lev = self.lev
+        u = np.zeros((lev.ny, lev.nx + 1))
+        v = np.zeros((lev.ny + 1, lev.nx))
+        I, J, w = self._u_window()
+        np.add.at(u, (J, I), w * g[: self.n_sd, None, None])
+        I, J, w = self._v_window()
+        np.add.at(v, (J, I), w * g[self.n_sd:, None, None])
+        return u, v
+
+    # -- P (Eqs. sdapprox3, weights): 4 tensor-cell neighbours, hat weights --------------
+
+    def p_rows(self, pts):
+        """For each body point: the 4 Omega_0 point indices and hat weights (reading R9)."""
+        lev = self.lev
+        x_lo = lev.x0 + self.i_lo * lev.h
+        y_lo = lev.y0 + self.j_lo * lev.h
+        x_hi = lev.x0 + self.i_hi * lev.h
+        y_hi = lev.y0 + self.j_hi * lev.h
+        idx = np.zeros((len(pts), 4), dtype=np.int64)
+        wts = np.zeros((len(pts), 4))
+        for p, (x, y) in enumerate(pts):
+            if not (x_lo <= x <= x_hi and y_lo <= y <= y_hi):
+                raise ValueError("body point outside the sub-domain")
+            ci = min(max(int(np.floor((x - x_lo) / lev.h)), 0), self.ni - 2)
+            cj = min(max(int(np.floor((y - y_lo) / lev.h)), 0), self.nj - 2)
+            k = 0
+            for b in (0, 1):
+                for a in (0, 1):
+                    xs = x_lo + (ci + a) * lev.h
+                    ys = y_lo + (cj + b) * lev.h
+                    idx[p, k] = (cj + b) * self.ni + (ci + a)
+                    wts[p, k] = hat(x - xs, lev.h) * hat(y - ys, lev.h)
+                    k += 1
+        return idx, wts
+
+
+def b0_column(sd, col, re, dt):
+    """Column ``col`` of ``B0``: ``E0 C Lap^{-1} A_w^{-1} C^T E0^T e_col`` (Eq. action).
+
+    The solves use the finest level with homogeneous boundary values (reading R6).
+    """
+    lev = sd.lev
+    e = np.zeros(2 * sd.n_sd)
+    e[col] = 1.0
+    u, v = sd.e0t(e)
+    src = grid.curl_faces(u, v, lev)
+    zero = np.zeros(lev.shape)
+    w = grid.solve_aw(src, zero, lev, re, dt)
+    s = np.zeros(lev.shape)
+    s[1:-1, 1:-1] = grid.solve_lap(w, zero, lev)
+    qu, qv = grid.faces_from_s(s, lev)
+    return sd.e0(qu, qv)
+
+
+def b0_dense(sd, re, dt):
+    """All columns of ``B0`` (Algorithm 1 with zero drop tolerance); small grids only."""
+    return np.stack([b0_column(sd, c, re, dt) for c in range(2 * sd.n_sd)], axis=1)
