@@ -1,0 +1,282 @@
+#!/usr/bin/env python3
+"""Benchmark of the online stage (Algorithm 2) on the 3-level 512x256 flag workload.
+
+One step = one full time step of the hot path: advection/right-hand side on every level, multidomain
+coupling, the DST predictor solves on all levels, the FSI iteration (P B0 P^T assembly + solve + body
+update) and the corrector solve.  B0 (Algorithm 1) is built once before timing and reported separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--precision fp32|fp64]
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the context stream, with
+an L2 flush (a 512 MiB buffer write) between timed steps outside the events.  value = cell-steps/s
+summed over ranks (cells = sum over levels of nx*ny).  The reference arm times the FP64 CPU oracle.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+METRIC = "FSI cell-steps/s, mixed vs FP64 on GPU at <=1e-5 force err; p50/p99 step ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2103_06415_gb300 import workloads as wl
+    return wl.flag_512x256_3lvl()
+
+
+def cells_per_step(w):
+    return w["n_levels"] * w["nx"] * w["ny"]
+
+
+def oracle_sample(w, budget_s):
+    """Time the FP64 oracle as it stands on a bounded prefix of the workload (after one untimed step)."""
+    import numpy as np  # noqa: F401
+    from runners import oracle_sim
+    sim = oracle_sim(w)
+    t0 = time.perf_counter()
+    sim.step()                                 # first step also builds the B0 columns it touches
+    t_first = time.perf_counter() - t0
+    n, t0 = 0, time.perf_counter()
+    while True:
+        sim.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "0") or 0) or os.cpu_count()
+    return dict(value=cells_per_step(w) * n / el, unit="cell-steps/s", cores=cores, kind="oracle",
+                sample="%d steps of %s after 1 untimed step (%.1f s incl. its B0 columns); numpy FP64, "
+                       "naive dense-DST transforms" % (n, w["name"], t_first),
+                ms_per_step=1e3 * el / n)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    budget = max(10.0, 2.0 * args.steps)
+    base = oracle_sample(w, budget_s=min(budget, 30.0))
+    line = {"metric": METRIC, "value": base["value"], "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "cells_per_step": cells_per_step(w)},
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": base["value"], "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = workload()
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # CPU baseline first, before any GPU call (rank 0, N = 1 only)
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = oracle_sample(w, budget_s=15.0)
+
+    import numpy as np
+    import torch
+    from paper_2103_06415_gb300 import build as _b
+    _b.build()
+    import paper_2103_06415_gb300 as lib
+    from runners import gpu_context
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    prec = lib.FSI_PREC_FP32 if args.precision == "fp32" else lib.FSI_PREC_FP64
+
+    def make(p):
+        st = torch.cuda.Stream()
+        t0 = time.perf_counter()
+        c = gpu_context(w, precision=p, precompute=False, stream=st.cuda_stream)
+        c.precompute()
+        return c, st, time.perf_counter() - t0
+
+    ctx, stream, b0_s = make(prec)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctx.advance(args.warmup)
+    ctx.sync()
+
+    def timed_steps(c, stream, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        for e0, e1 in evs:
+            flush.zero_()
+            torch.cuda.current_stream().synchronize()
+            e0.record(stream)
+            c.advance(1)
+            e1.record(stream)
+        c.sync()
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    clk = Clocks(local)
+    times = timed_steps(ctx, stream, args.steps)
+    clocks = clk.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells = cells_per_step(w)
+    value = cells * args.steps * world / (total_ms * 1e-3)
+    stats = ctx.stats()
+    hist_mixed = ctx.history(0)
+
+    # FP64 path on the same workload (same steps) and the force error of the mixed path against it
+    extra = {}
+    if prec == lib.FSI_PREC_FP32 and rank == 0:
+        ctx64, stream64, b0_64 = make(lib.FSI_PREC_FP64)
+        ctx64.advance(args.warmup)
+        t64 = timed_steps(ctx64, stream64, args.steps)
+        h64 = ctx64.history(0)
+        n = min(len(h64), len(hist_mixed))
+        errs = {}
+        for k, nm in enumerate(("fx", "fy", "moment", "theta")):
+            ref = h64[:n, k]
+            errs[nm] = float(np.linalg.norm(hist_mixed[:n, k] - ref) / max(np.linalg.norm(ref), 1e-300))
+        extra["fp64_path"] = {"value": cells * args.steps / (sum(t64) * 1e-3), "unit": "cell-steps/s",
+                              "ms_per_step": statistics.mean(t64), "p50_ms": statistics.median(t64),
+                              "p99_ms": float(np.percentile(t64, 99))}
+        extra["mixed_vs_fp64_rel_l2"] = errs
+        extra["mixed_within_1e-5"] = bool(max(errs.values()) <= 1e-5)
+        ctx64.close()
+
+    # dominant-kernel roofline: live CUDA-event timing of each launch of the class on the context stream
+    roof = None
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        shares = {}
+        for name in ("ysolve", "xf", "xi", "fsi", "rhs", "src"):
+            ms, nl = ctx.profile_kernel(name, 8)
+            shares[name] = (ms, nl / 8.0)
+        esz = 4 if prec == lib.FSI_PREC_FP32 else 8
+        nxi, nyi = w["nx"] - 1, w["ny"] - 1
+        ys_ms = shares["ysolve"][0]
+        bytes_ys = 3 * nxi * nyi * esz     # read the x-transformed level, write w and s half-transforms
+        achieved = bytes_ys / (ys_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_ysolve (DST y-pass: forward, diagonal solve, inverse)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+                "traffic": None, "algorithmic_bytes_per_launch": bytes_ys, "avg_launch_ms": ys_ms,
+                "per_step_kernel_ms": {k: v[0] * v[1] for k, v in shares.items()}}
+
+    # end to end through the public API: build the run from host descriptors, precompute, then each step
+    # advance + read the forces back to the host (synchronising), destroy
+    e2e = None
+    if rank == 0:
+        ke = max(10, args.steps // 4)
+        t0 = time.perf_counter()
+        c2 = gpu_context(w, precision=prec, precompute=False)
+        c2.precompute()
+        for _ in range(ke):
+            c2.advance(1)
+            c2.forces(0)
+        c2.close()
+        el = time.perf_counter() - t0
+        e2e = {"value": cells * ke / el, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": 96 + 4, "steps": ke,
+               "note": "wall clock incl. context creation, B0 precompute and a forces read-back per step"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "p50_ms": statistics.median(times), "p99_ms": float(np.percentile(times, 99)),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == lib.FSI_PREC_FP32 else "f64", "data": "synthetic",
+                "config": {"workload": w["name"] + " (torsional-plate stand-in for the flag)",
+                           "levels": w["n_levels"], "nx": w["nx"], "ny": w["ny"], "cells_per_step": cells,
+                           "body_points": sum(b["n_pts"] for b in w["bodies"]), "n_sd": stats["n_sd"],
+                           "b0_seconds": b0_s, "l2": "flushed between timed steps (512 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "gpu_launches": stats["launches_per_step"] * args.steps,
+                "clocks": clocks, "roofline": roof, "e2e": e2e}
+        line.update(extra)
+        if base is not None:
+            line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

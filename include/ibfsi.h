@@ -1,0 +1,183 @@
+/*
+ * ibfsi.h -- C ABI of the GB300 library for the sub-domain strongly coupled
+ * immersed-boundary fluid-structure interaction method of Nair & Goza
+ * ("A strongly coupled immersed boundary method for fluid-structure interaction
+ * that mimics the efficiency of stationary body methods").
+ *
+ * The calls follow the paper's statement of the problem: a fluid grid of nested
+ * levels (Sec. 5, multidomain far field), bodies (Sec. 2.1, Eqs. newtons-bct),
+ * a fixed sub-domain Omega_0 (Sec. 3.1.1), the offline stage that precomputes
+ * B0 = E0 C (C^T A C)^{-1} C^T E0^T (Algorithm 1, Eq. action) and the online
+ * stage that advances the coupled system (Algorithm 2, Eqs. predictor2-corrector2).
+ *
+ * Conventions
+ *  - Every call returns an fsi_status; no call aborts the process and device
+ *    code never traps.  Errors detected on the device are latched in a status
+ *    word and returned by the next synchronising call.
+ *  - All pointers in this header are HOST pointers unless stated otherwise.
+ *    Inputs are copied during the call; the caller keeps ownership of every
+ *    buffer it passes and of every output buffer it provides.
+ *  - The library owns its device memory (cudaMalloc); fsi_destroy frees it.
+ *  - Work is issued on the stream given at creation (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  fsi_advance is asynchronous; the
+ *    fsi_get_* calls synchronise that stream.
+ *  - Floating-point inputs are double precision whatever the compute precision.
+ */
+#ifndef IBFSI_H
+#define IBFSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FSI_OK = 0,
+  FSI_ERR_INVALID_ARG = 1,
+  FSI_ERR_OOM = 2,
+  FSI_ERR_UNSUPPORTED = 3,
+  FSI_ERR_BODY_OUTSIDE_SUBDOMAIN = 4, /* a body point left Omega_0 (Sec. 3.1.1 requires it to stay inside) */
+  FSI_ERR_NOT_CONVERGED = 5,          /* FSI iteration exceeded max_iters (Algorithm 2 while-loop) */
+  FSI_ERR_NONFINITE = 6,              /* NaN/Inf in the small system or in the forces */
+  FSI_ERR_TIMEOUT = 7,
+  FSI_ERR_CUDA = 8,                   /* a CUDA runtime call failed; see fsi_last_error_message */
+  FSI_ERR_STATE = 9                   /* call made in the wrong stage (e.g. advance before precompute) */
+} fsi_status;
+
+typedef enum {
+  FSI_PREC_FP64 = 0, /* every fluid transform and stencil in double */
+  FSI_PREC_FP32 = 1  /* fluid transforms and stencils in float; B0, the small system, Newton update and
+                        force reductions stay in double */
+} fsi_precision;
+
+typedef enum { FSI_BODY_RIGID = 0, FSI_BODY_TORSIONAL = 1, FSI_BODY_DEFORMABLE = 2 } fsi_body_type;
+
+/* Fluid grid (Sec. 2.2; multidomain of Sec. 5).  Level 0 is the finest: nx x ny cells of spacing h with
+ * lower-left corner (x0, y0).  Level g has the same cell counts, spacing 2^g h and the same centre.
+ * nx and ny must be powers of two in [16, 2048] (the DST length N+1 = nx, ny); n_levels >= 1.
+ * re = Reynolds number, dt = time step, uinf = free-stream velocity. */
+typedef struct {
+  int nx, ny, n_levels;
+  double x0, y0, h;
+  double re, dt;
+  double uinf[2];
+} fsi_grid_desc;
+
+/* Execution options.  stream: cudaStream_t (NULL = default stream).  max_iters (<= 0 -> 50) and tol
+ * (<= 0 -> 1e-7) control the FSI iteration of Algorithm 2 (convergence on max |dtheta|, Sec. 5).
+ * history_cap: number of steps kept in the per-step output ring (<= 0 -> 1<<16).
+ * use_graph: nonzero captures one time step into a CUDA graph and replays it. */
+typedef struct {
+  int precision;
+  void* stream;
+  int max_iters;
+  double tol;
+  int history_cap;
+  int use_graph;
+} fsi_exec_desc;
+
+/* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at
+ * hinge + j*ds*(cos(theta0+theta), sin(theta0+theta)), rotating about the hinge on a spring
+ * (inertia, damping, stiffness; Eq. newtons with g_t = 0); theta_init, phi_init = initial deflection and
+ * angular velocity.  RIGID: n_pts fixed points pts[2*j], pts[2*j+1] with prescribed velocity ur (same
+ * layout; NULL = stationary).  DEFORMABLE returns FSI_ERR_UNSUPPORTED.
+ * All bodies of one context must use the same ds (the surface-stress regularisation weight). */
+typedef struct {
+  int type;
+  int n_pts;
+  double ds;
+  double hinge[2];
+  double theta0, theta_init, phi_init;
+  double inertia, damping, stiffness;
+  const double* pts;
+  const double* ur;
+} fsi_body_desc;
+
+typedef struct {
+  double x_lo, x_hi, y_lo, y_hi;
+} fsi_box;
+
+typedef struct {
+  int64_t steps_done;
+  int last_iters;      /* FSI iterations of the last step */
+  int max_iters_seen;  /* largest FSI iteration count so far */
+  int n_sd;            /* number of Omega_0 points (2*n_sd unknowns) */
+  int nf;              /* number of surface-stress unknowns (2 x body points) */
+  double b0_seconds;   /* wall time of the last fsi_precompute */
+  size_t device_bytes; /* device memory held by the context */
+  int launches_per_step; /* kernels this library launches per time step */
+} fsi_stats;
+
+typedef struct fsi_ctx fsi_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char* fsi_status_string(int status);
+/* Text of the last CUDA error recorded by this thread (static buffer). */
+const char* fsi_last_error_message(void);
+
+/* Create a context: allocates the per-level vorticity/streamfunction fields and transform buffers on the
+ * current device.  Fields start at zero (impulsive start).  *out receives the handle. */
+fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc* exec, fsi_ctx** out);
+
+/* Add a body (Sec. 2.1, App. A).  Host arrays are copied.  Must precede fsi_precompute. */
+fsi_status fsi_add_body(fsi_ctx* ctx, const fsi_body_desc* body, int* body_id);
+
+/* Fix the sub-domain Omega_0 (Sec. 3.1.1): the box is snapped to level-0 vertices at spacing h and clipped
+ * to vertices at least 2 cells from the boundary.  Exactly one box and no extra points are supported
+ * (n_boxes == 1, n_extra == 0; otherwise FSI_ERR_UNSUPPORTED). */
+fsi_status fsi_set_subdomain(fsi_ctx* ctx, const fsi_box* boxes, int n_boxes, const double* extra_pts,
+                             int n_extra);
+
+/* Offline stage (Algorithm 1): build the dense B0 (2 n_sd x 2 n_sd, double) on the device.
+ * drop_tol must be 0 (the dense operator); sparse filtering (Eq. filtereq) returns FSI_ERR_UNSUPPORTED. */
+fsi_status fsi_precompute(fsi_ctx* ctx, double drop_tol);
+
+/* Online stage (Algorithm 2): enqueue n_steps time steps on the context stream.  Asynchronous. */
+fsi_status fsi_advance(fsi_ctx* ctx, int n_steps);
+
+/* Wait for the context stream and return the latched device status. */
+fsi_status fsi_sync(fsi_ctx* ctx);
+
+/* Outputs of the last completed step for one body (synchronising).  fx, fy = ds * sum of the surface
+ * stress (force by the fluid on the body; c_d = 2 fx, c_l = 2 fy at unit density, speed and chord);
+ * moment = ds * S f about the hinge (0 for rigid bodies).  Any output pointer may be NULL. */
+fsi_status fsi_get_forces(fsi_ctx* ctx, int body, double* fx, double* fy, double* moment);
+fsi_status fsi_get_deflection(fsi_ctx* ctx, int body, double* theta, double* phi);
+
+/* Per-step history of one body: field 0 fx, 1 fy, 2 moment, 3 theta, 4 phi, 5 FSI iterations.
+ * Copies the last min(cap, kept) steps, oldest first; *n receives the count (synchronising). */
+fsi_status fsi_get_history(fsi_ctx* ctx, int body, int field, double* out, int cap, int* n);
+
+/* Copy a vertex field of one level to the host as double, row-major [(ny+1) x (nx+1)], boundary ring
+ * included.  which: 0 = vorticity, 1 = streamfunction. */
+fsi_status fsi_get_field(fsi_ctx* ctx, int level, int which, double* out);
+/* Overwrite a vertex field (same layout) from the host, e.g. to start from a given state. */
+fsi_status fsi_set_field(fsi_ctx* ctx, int level, int which, const double* in);
+
+/* Sampled entries of B0: out[k] = B0[rows[k], cols[k]] for k < n (synchronising).  Unknown ordering:
+ * the n_sd x-components (points row by row inside the box), then the n_sd y-components. */
+fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n,
+                                    double* out);
+
+/* Interpolation map P of the last step's final FSI iterate (Eq. weights): for each body point p the four
+ * Omega_0 point indices idx[4p..4p+3] and hat weights w[4p..4p+3] (synchronising). */
+fsi_status fsi_get_interp(fsi_ctx* ctx, int64_t* idx, double* w, int cap_points);
+
+fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);
+
+/* Live timing of one kernel class: runs n_steps (1..1024) ordinary time steps without a graph, records a
+ * CUDA event pair on the context stream around every launch of that class and returns the mean launch
+ * duration in ms and the number of timed launches.  The steps advance the simulation like fsi_advance.
+ * Classes: 1 forward-x DST pass, 2 y-solve DST pass, 3 inverse-x DST pass, 4 FSI iteration kernel,
+ * 5 advection/right-hand side, 6 corrector source, 7 level boundary, 8 boundary-side DSTs, 9 injection. */
+fsi_status fsi_profile_kernel(fsi_ctx* ctx, int kernel_class, int n_steps, double* avg_ms, int* launches);
+
+/* Free all device memory and the handle (synchronises the stream first). */
+void fsi_destroy(fsi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBFSI_H */

@@ -1,0 +1,31 @@
+/*
+ * ibfsi_ops.h -- operator-level entry points of the GB300 sub-domain IB-FSI library, for testing and
+ * measuring single stages of the hot path in isolation.  Same conventions as ibfsi.h: host pointers,
+ * inputs copied, caller owns every buffer, status codes instead of aborts.
+ */
+#ifndef IBFSI_OPS_H
+#define IBFSI_OPS_H
+
+#include "ibfsi.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One DST-diagonalised solve on a single level with zero boundary values (Sec. 3.2.1, Eq. predictor2):
+ * w = A_w^{-1} rhs with A_w = 1/dt - lap_h/(2 re), then s = (-lap_h)^{-1} w.
+ * rhs: interior values, row-major [(ny-1) x (nx-1)] (rows = y).  w_out, s_out: same layout.
+ * precision: FSI_PREC_FP64 or FSI_PREC_FP32 (inputs/outputs are double either way).
+ * nx, ny: powers of two in [16, 2048]; h, re, dt > 0.  Runs on the current device, synchronously. */
+fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt, const double* rhs,
+                              double* w_out, double* s_out);
+
+/* Throughput of a project-written fused multiply-add loop on the current device (independent chains, all
+ * SMs busy), used as the arithmetic roofline of the FP64 and FP32 paths.  *flops_per_s receives the
+ * measured rate (2 flops per FMA).  precision: FSI_PREC_FP64 or FSI_PREC_FP32. */
+fsi_status fsi_op_fma_rate(int precision, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBFSI_OPS_H */

@@ -1,0 +1,178 @@
+"""GB300 implementation of the sub-domain strongly coupled immersed-boundary FSI method
+(Nair & Goza): Python binding of the C ABI in ``include/ibfsi.h``.
+
+``Context`` wraps one run: grid levels, bodies, the sub-domain Omega_0, the offline stage
+(``precompute``, Algorithm 1) and the online stage (``advance``, Algorithm 2).  Arrays cross the
+boundary as float64 numpy arrays; all computation happens in ``libibfsi.so``.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
+
+__all__ = ["Context", "level_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """One FSI run on the current CUDA device.
+
+    grid: nx, ny (powers of two), n_levels, x0, y0, h, re, dt, uinf=(U, V)
+    precision: FSI_PREC_FP64 or FSI_PREC_FP32; stream: a cudaStream_t handle (int) or None.
+    """
+
+    def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
+                 stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True):
+        self._lib = _lib.load()
+        g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
+        x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
+                          1 if use_graph else 0)
+        h_ = ctypes.c_void_p()
+        check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
+        self._h = h_
+        self.nx, self.ny, self.n_levels = nx, ny, n_levels
+        self.n_bodies = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fsi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- setup -------------------------------------------------------------------------------
+
+    def add_torsional(self, hinge, theta0, n_pts, ds, inertia, damping, stiffness, theta_init, phi_init=0.0):
+        b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, n_pts, ds, (ctypes.c_double * 2)(*hinge), theta0, theta_init,
+                          phi_init, inertia, damping, stiffness, None, None)
+        bid = ctypes.c_int()
+        check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
+        self.n_bodies += 1
+        return bid.value
+
+    def add_rigid(self, pts, ds, ur=None):
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+        urp = None
+        if ur is not None:
+            ur = np.ascontiguousarray(ur, dtype=np.float64).reshape(-1, 2)
+            urp = _dp(ur)
+        b = _lib.BodyDesc(_lib.FSI_BODY_RIGID, len(pts), ds, (ctypes.c_double * 2)(0, 0), 0, 0, 0, 0, 0, 0,
+                          _dp(pts), urp)
+        bid = ctypes.c_int()
+        check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
+        self.n_bodies += 1
+        return bid.value
+
+    def set_subdomain(self, x_lo, x_hi, y_lo, y_hi):
+        box = _lib.Box(x_lo, x_hi, y_lo, y_hi)
+        check(self._lib.fsi_set_subdomain(self._h, ctypes.byref(box), 1, None, 0), "fsi_set_subdomain")
+
+    def precompute(self, drop_tol=0.0):
+        check(self._lib.fsi_precompute(self._h, drop_tol), "fsi_precompute")
+
+    # -- online ------------------------------------------------------------------------------
+
+    def advance(self, n_steps):
+        check(self._lib.fsi_advance(self._h, n_steps), "fsi_advance")
+
+    def sync(self):
+        check(self._lib.fsi_sync(self._h), "fsi_sync")
+
+    # -- outputs -----------------------------------------------------------------------------
+
+    def forces(self, body=0):
+        fx, fy, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(self._lib.fsi_get_forces(self._h, body, ctypes.byref(fx), ctypes.byref(fy), ctypes.byref(m)),
+              "fsi_get_forces")
+        return fx.value, fy.value, m.value
+
+    def deflection(self, body=0):
+        th, ph = ctypes.c_double(), ctypes.c_double()
+        check(self._lib.fsi_get_deflection(self._h, body, ctypes.byref(th), ctypes.byref(ph)), "fsi_get_deflection")
+        return th.value, ph.value
+
+    def history(self, body=0, cap=1 << 16):
+        """Per-step array [n, 6]: fx, fy, moment, theta, phi, FSI iterations (oldest first)."""
+        cols = []
+        for field in range(6):
+            out = np.zeros(cap)
+            n = ctypes.c_int()
+            check(self._lib.fsi_get_history(self._h, body, field, _dp(out), cap, ctypes.byref(n)), "fsi_get_history")
+            cols.append(out[: n.value])
+        return np.stack(cols, axis=1)
+
+    def field(self, level, which):
+        out = np.zeros((self.ny + 1, self.nx + 1))
+        check(self._lib.fsi_get_field(self._h, level, which, _dp(out)), "fsi_get_field")
+        return out
+
+    def set_field(self, level, which, arr):
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+        assert arr.shape == (self.ny + 1, self.nx + 1)
+        check(self._lib.fsi_set_field(self._h, level, which, _dp(arr)), "fsi_set_field")
+
+    def operator_entries(self, rows, cols):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        out = np.zeros(len(rows))
+        check(self._lib.fsi_get_operator_entries(self._h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                 cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(rows),
+                                                 _dp(out)), "fsi_get_operator_entries")
+        return out
+
+    def interp(self, n_points):
+        idx = np.zeros(4 * n_points, dtype=np.int64)
+        w = np.zeros(4 * n_points)
+        check(self._lib.fsi_get_interp(self._h, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(w),
+                                       n_points), "fsi_get_interp")
+        return idx.reshape(-1, 4), w.reshape(-1, 4)
+
+    KERNEL_CLASSES = {"xf": 1, "ysolve": 2, "xi": 3, "fsi": 4, "rhs": 5, "src": 6, "ring": 7, "vecdst": 8,
+                      "inject": 9}
+
+    def profile_kernel(self, name, n_steps):
+        """Run n_steps eager steps timing every launch of one kernel class; returns (mean ms, launches)."""
+        ms, n = ctypes.c_double(), ctypes.c_int()
+        check(self._lib.fsi_profile_kernel(self._h, self.KERNEL_CLASSES[name], n_steps, ctypes.byref(ms),
+                                           ctypes.byref(n)), "fsi_profile_kernel")
+        return ms.value, n.value
+
+    def stats(self):
+        s = _lib.Stats()
+        check(self._lib.fsi_get_stats(self._h, ctypes.byref(s)), "fsi_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64):
+    """``w = A_w^{-1} rhs``, ``s = (-lap_h)^{-1} w`` on one level with zero boundary values (interior arrays)."""
+    lib = _lib.load()
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    ny1, nx1 = rhs.shape
+    w = np.zeros_like(rhs)
+    s = np.zeros_like(rhs)
+    check(lib.fsi_op_level_solve(precision, nx1 + 1, ny1 + 1, h, re, dt, _dp(rhs), _dp(w), _dp(s)),
+          "fsi_op_level_solve")
+    return w, s
+
+
+def fma_rate(precision):
+    lib = _lib.load()
+    r = ctypes.c_double()
+    check(lib.fsi_op_fma_rate(precision, ctypes.byref(r)), "fsi_op_fma_rate")
+    return r.value

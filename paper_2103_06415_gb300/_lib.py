@@ -1,0 +1,115 @@
+"""ctypes binding of ``libibfsi.so`` (argument marshalling only; every step runs in the CUDA library).
+
+The structures mirror ``include/ibfsi.h``.  Loading fails loudly if the library has not been built:
+there is no fallback implementation.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libibfsi.so")
+
+FSI_PREC_FP64 = 0
+FSI_PREC_FP32 = 1
+FSI_BODY_RIGID = 0
+FSI_BODY_TORSIONAL = 1
+FSI_BODY_DEFORMABLE = 2
+
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "UNSUPPORTED", 4: "BODY_OUTSIDE_SUBDOMAIN",
+    5: "NOT_CONVERGED", 6: "NONFINITE", 7: "TIMEOUT", 8: "CUDA", 9: "STATE",
+}
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double),
+                ("re", ctypes.c_double), ("dt", ctypes.c_double), ("uinf", ctypes.c_double * 2)]
+
+
+class ExecDesc(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
+                ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("n_pts", ctypes.c_int), ("ds", ctypes.c_double),
+                ("hinge", ctypes.c_double * 2), ("theta0", ctypes.c_double), ("theta_init", ctypes.c_double),
+                ("phi_init", ctypes.c_double), ("inertia", ctypes.c_double), ("damping", ctypes.c_double),
+                ("stiffness", ctypes.c_double), ("pts", ctypes.POINTER(ctypes.c_double)),
+                ("ur", ctypes.POINTER(ctypes.c_double))]
+
+
+class Box(ctypes.Structure):
+    _fields_ = [("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double), ("y_lo", ctypes.c_double),
+                ("y_hi", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps_done", ctypes.c_int64), ("last_iters", ctypes.c_int), ("max_iters_seen", ctypes.c_int),
+                ("n_sd", ctypes.c_int), ("nf", ctypes.c_int), ("b0_seconds", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_INT = ctypes.c_int
+
+SIGNATURES = {
+    "fsi_status_string": (ctypes.c_char_p, [_INT]),
+    "fsi_last_error_message": (ctypes.c_char_p, []),
+    "fsi_create": (_INT, [ctypes.POINTER(GridDesc), ctypes.POINTER(ExecDesc), ctypes.POINTER(_P)]),
+    "fsi_add_body": (_INT, [_P, ctypes.POINTER(BodyDesc), ctypes.POINTER(_INT)]),
+    "fsi_set_subdomain": (_INT, [_P, ctypes.POINTER(Box), _INT, _D, _INT]),
+    "fsi_precompute": (_INT, [_P, ctypes.c_double]),
+    "fsi_advance": (_INT, [_P, _INT]),
+    "fsi_sync": (_INT, [_P]),
+    "fsi_get_forces": (_INT, [_P, _INT, _D, _D, _D]),
+    "fsi_get_deflection": (_INT, [_P, _INT, _D, _D]),
+    "fsi_get_history": (_INT, [_P, _INT, _INT, _D, _INT, ctypes.POINTER(_INT)]),
+    "fsi_get_field": (_INT, [_P, _INT, _INT, _D]),
+    "fsi_set_field": (_INT, [_P, _INT, _INT, _D]),
+    "fsi_get_operator_entries": (_INT, [_P, _I64, _I64, _INT, _D]),
+    "fsi_get_interp": (_INT, [_P, _I64, _D, _INT]),
+    "fsi_get_stats": (_INT, [_P, ctypes.POINTER(Stats)]),
+    "fsi_profile_kernel": (_INT, [_P, _INT, _INT, _D, ctypes.POINTER(_INT)]),
+    "fsi_destroy": (None, [_P]),
+    "fsi_op_level_solve": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D]),
+    "fsi_op_fma_rate": (_INT, [_INT, _D]),
+}
+
+_lib = None
+
+
+def load():
+    """Load ``libibfsi.so`` (raises if it is missing: build it with ``paper_2103_06415_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libibfsi.so is not built; run `python -m paper_2103_06415_gb300.build` "
+                          "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FsiError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s: %s" % (where, STATUS.get(code, code))
+        if code == 8 and _lib is not None:
+            msg += " (%s)" % _lib.fsi_last_error_message().decode()
+        super().__init__(msg)
+
+
+def check(code, where):
+    if code != 0:
+        raise FsiError(code, where)
+    return code

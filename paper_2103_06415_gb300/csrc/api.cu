@@ -1,0 +1,608 @@
+// C ABI: context life cycle, offline/online stages and read-back (see include/ibfsi.h).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "internal.h"
+
+int fsi_kernel_max_ctas_per_sm(int nf);
+size_t fsi_smem_bytes(int nf);
+
+static thread_local char g_errmsg[512] = "";
+
+void fsi_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+extern "C" const char* fsi_last_error_message(void) { return g_errmsg; }
+
+extern "C" const char* fsi_status_string(int s) {
+  switch (s) {
+    case FSI_OK: return "ok";
+    case FSI_ERR_INVALID_ARG: return "invalid argument";
+    case FSI_ERR_OOM: return "out of device memory";
+    case FSI_ERR_UNSUPPORTED: return "unsupported";
+    case FSI_ERR_BODY_OUTSIDE_SUBDOMAIN: return "body point outside the sub-domain";
+    case FSI_ERR_NOT_CONVERGED: return "FSI iteration did not converge";
+    case FSI_ERR_NONFINITE: return "non-finite value";
+    case FSI_ERR_TIMEOUT: return "timeout";
+    case FSI_ERR_CUDA: return "CUDA error";
+    case FSI_ERR_STATE: return "call made in the wrong stage";
+    default: return "unknown status";
+  }
+}
+
+void* ctx_alloc(fsi_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaMemsetAsync(p, 0, bytes, c->stream);
+  c->allocs.push_back(p);
+  c->dev_bytes += bytes;
+  return p;
+}
+
+static void ctx_free_all(fsi_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->dev_bytes = 0;
+}
+
+static bool pow2_ok(int n) { return n >= 16 && (n & (n - 1)) == 0 && n <= 2048; }
+
+template <typename T>
+static fsi_status upload_twiddles(fsi_ctx* c, int L, void** out) {
+  std::vector<T> tw(2 * (size_t)L);
+  for (int m = 0; m < L; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)L;
+    tw[2 * m] = (T)std::cos(a);
+    tw[2 * m + 1] = (T)std::sin(a);
+  }
+  *out = ctx_alloc(c, tw.size() * sizeof(T));
+  if (!*out) return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaMemcpyAsync(*out, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return FSI_OK;
+}
+
+static fsi_status upload_d(fsi_ctx* c, const std::vector<double>& v, double** out) {
+  *out = (double*)ctx_alloc(c, v.size() * 8);
+  if (!*out) return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaMemcpyAsync(*out, v.data(), v.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  return FSI_OK;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    fsi_status _s = (x);             \
+    if (_s != FSI_OK) return _s;     \
+  } while (0)
+
+static fsi_status create_impl(fsi_ctx* c) {
+  const fsi_grid_desc& g = c->g;
+  c->G = g.n_levels;
+  c->nx = g.nx;
+  c->ny = g.ny;
+  c->Nx = g.nx - 1;
+  c->Ny = g.ny - 1;
+  c->Mx = g.nx;
+  c->My = g.ny;
+  c->logLx = ilog2_exact(2 * g.nx);
+  c->logLy = ilog2_exact(2 * g.ny);
+  c->ps = padded_stride(g.nx + 1);
+  c->lvl_elems = (long)(g.ny + 1) * c->ps;
+  c->ldT = padded_stride(c->Ny);
+  c->ldX = padded_stride(c->Nx);
+  c->ring_ld = padded_stride(c->Nx > c->Ny ? c->Nx : c->Ny);
+  const size_t E = c->esz;
+  const size_t lvl = (size_t)c->G * c->lvl_elems * E;
+  if (!(c->w_all = ctx_alloc(c, lvl)) || !(c->s_all = ctx_alloc(c, lvl)) || !(c->nprev_all = ctx_alloc(c, lvl)) ||
+      !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)c->Nx * c->ldT * E)) ||
+      !(c->T2w = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) || !(c->T2s = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) ||
+      !(c->src = ctx_alloc(c, (size_t)c->lvl_elems * E)) || !(c->ring = ctx_alloc(c, (size_t)8 * c->ring_ld * E)))
+    return FSI_ERR_OOM;
+  std::vector<double> lx(c->Mx + 1), ly(c->My + 1), sx1(c->Mx + 1), sxN(c->Mx + 1), sy1(c->My + 1), syN(c->My + 1);
+  for (int k = 0; k <= c->Mx; ++k) {
+    const double s = std::sin(M_PI * k / (2.0 * c->Mx));
+    lx[k] = 4.0 * s * s;
+    sx1[k] = std::sin(M_PI * k / (double)c->Mx);
+    sxN[k] = std::sin(M_PI * (double)k * c->Nx / (double)c->Mx);
+  }
+  for (int l = 0; l <= c->My; ++l) {
+    const double s = std::sin(M_PI * l / (2.0 * c->My));
+    ly[l] = 4.0 * s * s;
+    sy1[l] = std::sin(M_PI * l / (double)c->My);
+    syN[l] = std::sin(M_PI * (double)l * c->Ny / (double)c->My);
+  }
+  TRY(upload_d(c, lx, &c->lx));
+  TRY(upload_d(c, ly, &c->ly));
+  TRY(upload_d(c, sx1, &c->sx1));
+  TRY(upload_d(c, sxN, &c->sxN));
+  TRY(upload_d(c, sy1, &c->sy1));
+  TRY(upload_d(c, syN, &c->syN));
+  if (c->prec == FSI_PREC_FP64) {
+    TRY(upload_twiddles<double>(c, 2 * c->Mx, &c->twx));
+    TRY(upload_twiddles<double>(c, 2 * c->My, &c->twy));
+  } else {
+    TRY(upload_twiddles<float>(c, 2 * c->Mx, &c->twx));
+    TRY(upload_twiddles<float>(c, 2 * c->My, &c->twy));
+  }
+  // ring-side pointer tables: per level [side0: wL wR sL sR | side1: wB wT sB sT]
+  std::vector<void*> srcs(8 * (size_t)c->G), dsts(8 * (size_t)c->G);
+  std::vector<long> es(8 * (size_t)c->G);
+  for (int l = 0; l < c->G; ++l) {
+    char* w = (char*)c->w_all + (size_t)l * c->lvl_elems * E;
+    char* s = (char*)c->s_all + (size_t)l * c->lvl_elems * E;
+    char* r = (char*)c->ring;
+    const long ps = c->ps;
+    void* side0[4] = {w + ps * E, w + (ps + c->nx) * E, s + ps * E, s + (ps + c->nx) * E};
+    void* side1[4] = {w + E, w + ((long)c->ny * ps + 1) * E, s + E, s + ((long)c->ny * ps + 1) * E};
+    const int d0[4] = {0, 1, 4, 5}, d1[4] = {2, 3, 6, 7};
+    for (int v = 0; v < 4; ++v) {
+      srcs[8 * l + v] = side0[v];
+      es[8 * l + v] = ps;
+      dsts[8 * l + v] = r + (size_t)d0[v] * c->ring_ld * E;
+      srcs[8 * l + 4 + v] = side1[v];
+      es[8 * l + 4 + v] = 1;
+      dsts[8 * l + 4 + v] = r + (size_t)d1[v] * c->ring_ld * E;
+    }
+  }
+  if (!(c->ring_src = (void**)ctx_alloc(c, srcs.size() * sizeof(void*))) ||
+      !(c->ring_dst = (void**)ctx_alloc(c, dsts.size() * sizeof(void*))) ||
+      !(c->ring_es = (long*)ctx_alloc(c, es.size() * sizeof(long))))
+    return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_src, srcs.data(), srcs.size() * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
+  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_dst, dsts.data(), dsts.size() * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
+  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_es, es.data(), es.size() * sizeof(long), cudaMemcpyHostToDevice, c->stream));
+  if (!(c->d_status = (int*)ctx_alloc(c, 64)) || !(c->d_ctrl = (int*)ctx_alloc(c, 64))) return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc* exec, fsi_ctx** out) {
+  if (!grid || !out) return FSI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!pow2_ok(grid->nx) || !pow2_ok(grid->ny) || grid->n_levels < 1 || grid->n_levels > 12 || !(grid->h > 0) ||
+      !(grid->re > 0) || !(grid->dt > 0) || !std::isfinite(grid->x0) || !std::isfinite(grid->y0))
+    return FSI_ERR_INVALID_ARG;
+  fsi_ctx* c = new (std::nothrow) fsi_ctx();
+  if (!c) return FSI_ERR_OOM;
+  c->g = *grid;
+  memset(&c->x, 0, sizeof(c->x));
+  if (exec) c->x = *exec;
+  if (c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32) {
+    delete c;
+    return FSI_ERR_INVALID_ARG;
+  }
+  if (c->x.max_iters <= 0) c->x.max_iters = 50;
+  if (!(c->x.tol > 0)) c->x.tol = 1e-7;
+  if (c->x.history_cap <= 0) c->x.history_cap = 1 << 16;
+  c->prec = c->x.precision;
+  c->esz = c->prec == FSI_PREC_FP64 ? 8 : 4;
+  c->own_stream = 0;
+  if (c->x.stream) {
+    c->stream = (cudaStream_t)c->x.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return FSI_ERR_CUDA;
+    }
+    c->own_stream = 1;
+  }
+  c->first_pending = 1;
+  fsi_status st = create_impl(c);
+  if (st != FSI_OK) {
+    ctx_free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body_id) {
+  if (!c || !b) return FSI_ERR_INVALID_ARG;
+  if (c->stage >= 1) return FSI_ERR_STATE;
+  if (b->type == FSI_BODY_DEFORMABLE) return FSI_ERR_UNSUPPORTED;
+  if (b->type != FSI_BODY_RIGID && b->type != FSI_BODY_TORSIONAL) return FSI_ERR_INVALID_ARG;
+  if (b->n_pts < 1 || !(b->ds > 0)) return FSI_ERR_INVALID_ARG;
+  if (!c->bodies.empty() && std::fabs(b->ds - c->ds) > 1e-15 * c->ds) return FSI_ERR_UNSUPPORTED;
+  BodyHost h = {};
+  h.type = b->type;
+  h.n = b->n_pts;
+  h.off = c->nb;
+  if (b->type == FSI_BODY_TORSIONAL) {
+    if (!(b->inertia > 0) || b->stiffness < 0 || b->damping < 0) return FSI_ERR_INVALID_ARG;
+    h.hx = b->hinge[0];
+    h.hy = b->hinge[1];
+    h.theta0 = b->theta0;
+    h.inertia = b->inertia;
+    h.damping = b->damping;
+    h.stiffness = b->stiffness;
+    h.theta = b->theta_init;
+    h.phi = b->phi_init;
+    h.phidot = (-b->stiffness * b->theta_init - b->damping * b->phi_init) / b->inertia;
+    for (int j = 0; j < b->n_pts; ++j) {
+      c->rigid_pts.push_back(0.0);
+      c->rigid_pts.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+    }
+  } else {
+    if (!b->pts) return FSI_ERR_INVALID_ARG;
+    for (int j = 0; j < 2 * b->n_pts; ++j) {
+      c->rigid_pts.push_back(b->pts[j]);
+      c->rigid_ur.push_back(b->ur ? b->ur[j] : 0.0);
+    }
+  }
+  c->ds = b->ds;
+  c->bodies.push_back(h);
+  c->nb += b->n_pts;
+  if (body_id) *body_id = (int)c->bodies.size() - 1;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_boxes, const double* extra,
+                                        int n_extra) {
+  (void)extra;
+  if (!c || !boxes) return FSI_ERR_INVALID_ARG;
+  if (c->stage >= 1) return FSI_ERR_STATE;
+  if (n_boxes != 1 || n_extra != 0) return FSI_ERR_UNSUPPORTED;
+  const fsi_box& b = boxes[0];
+  const double h = c->g.h;
+  int i_lo = (int)std::ceil((b.x_lo - c->g.x0) / h - 1e-9), i_hi = (int)std::floor((b.x_hi - c->g.x0) / h + 1e-9);
+  int j_lo = (int)std::ceil((b.y_lo - c->g.y0) / h - 1e-9), j_hi = (int)std::floor((b.y_hi - c->g.y0) / h + 1e-9);
+  if (i_lo < 2) i_lo = 2;
+  if (j_lo < 2) j_lo = 2;
+  if (i_hi > c->nx - 2) i_hi = c->nx - 2;
+  if (j_hi > c->ny - 2) j_hi = c->ny - 2;
+  if (i_hi <= i_lo || j_hi <= j_lo) return FSI_ERR_INVALID_ARG;
+  c->i_lo = i_lo;
+  c->i_hi = i_hi;
+  c->j_lo = j_lo;
+  c->j_hi = j_hi;
+  c->ni = i_hi - i_lo + 1;
+  c->nj = j_hi - j_lo + 1;
+  c->n_sd = c->ni * c->nj;
+  c->have_sd = 1;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
+  if (!c) return FSI_ERR_INVALID_ARG;
+  if (drop_tol != 0.0) return FSI_ERR_UNSUPPORTED;
+  if (c->stage >= 1) return FSI_ERR_STATE;
+  if (!c->have_sd) return FSI_ERR_STATE;
+  c->n_bodies = (int)c->bodies.size();
+  c->nf = 2 * c->nb;
+  if (c->n_bodies > 256) return FSI_ERR_UNSUPPORTED;
+  if (c->nb > 0 && fsi_smem_bytes(c->nf) > 220 * 1024) return FSI_ERR_UNSUPPORTED;
+  const size_t n2 = 2 * (size_t)c->n_sd;
+  if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
+  fsi_status st = build_b0(c);
+  if (st != FSI_OK) return st;
+  c->have_b0 = 1;
+  if (c->nb > 0) {
+    std::vector<BodyDev> bd;
+    std::vector<BodyState> bs;
+    std::vector<int> pb;
+    for (size_t i = 0; i < c->bodies.size(); ++i) {
+      const BodyHost& h = c->bodies[i];
+      BodyDev d = {};
+      d.type = h.type;
+      d.off = h.off;
+      d.n = h.n;
+      d.hx = h.hx;
+      d.hy = h.hy;
+      d.theta0 = h.theta0;
+      d.inertia = h.inertia;
+      d.damping = h.damping;
+      d.stiffness = h.stiffness;
+      bd.push_back(d);
+      BodyState s = {};
+      s.theta = h.theta;
+      s.phi = h.phi;
+      s.phidot = h.phidot;
+      bs.push_back(s);
+      for (int j = 0; j < h.n; ++j) pb.push_back((int)i);
+    }
+    c->hist_cap = c->x.history_cap;
+    if (!(c->d_bodies = (BodyDev*)ctx_alloc(c, bd.size() * sizeof(BodyDev))) ||
+        !(c->d_state = (BodyState*)ctx_alloc(c, bs.size() * sizeof(BodyState))) ||
+        !(c->d_point_body = (int*)ctx_alloc(c, pb.size() * sizeof(int))) ||
+        !(c->d_rpts = (double*)ctx_alloc(c, c->rigid_pts.size() * 8)) ||
+        !(c->d_rur = (double*)ctx_alloc(c, c->rigid_ur.size() * 8)) ||
+        !(c->d_pidx = (int*)ctx_alloc(c, (size_t)c->nb * 4 * sizeof(int))) ||
+        !(c->d_pw = (double*)ctx_alloc(c, (size_t)c->nb * 4 * 8)) ||
+        !(c->d_sv = (double*)ctx_alloc(c, (size_t)c->nb * 2 * 8)) ||
+        !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+        !(c->d_K = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)) ||
+        !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+        !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
+      return FSI_ERR_OOM;
+    FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bodies, bd.data(), bd.size() * sizeof(BodyDev), cudaMemcpyHostToDevice, c->stream));
+    FSI_CUDA_TRY(cudaMemcpyAsync(c->d_state, bs.data(), bs.size() * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
+    FSI_CUDA_TRY(cudaMemcpyAsync(c->d_point_body, pb.data(), pb.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rpts, c->rigid_pts.data(), c->rigid_pts.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rur, c->rigid_ur.data(), c->rigid_ur.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf);
+    if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
+    c->fsi_grid = nsm;
+  }
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->stage = 1;
+  return FSI_OK;
+}
+
+void prof_mark(fsi_ctx* c, int cls) {
+  if (c->prof_class != cls || c->prof_used >= (int)c->prof_ev.size()) return;
+  cudaEventRecord(c->prof_ev[c->prof_used++], c->stream);
+}
+
+static fsi_status enqueue_step(fsi_ctx* c, int first) {
+  c->launches_per_step = 0;
+  TRY(launch_predictor(c, first));
+  if (c->nb > 0) {
+    TRY(launch_fsi(c));
+    TRY(launch_corrector(c));
+  }
+  return FSI_OK;
+}
+
+static fsi_status build_graph(fsi_ctx* c) {
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return FSI_ERR_CUDA;
+  }
+  fsi_status st = enqueue_step(c, 0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (st != FSI_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return FSI_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return FSI_ERR_CUDA;
+  }
+  c->graph = g;
+  c->graph_ok = 1;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_advance(fsi_ctx* c, int n_steps) {
+  if (!c || n_steps < 0) return FSI_ERR_INVALID_ARG;
+  if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
+  if (c->nb > 0 && !c->have_b0) return FSI_ERR_STATE;
+  for (int n = 0; n < n_steps; ++n) {
+    if (c->first_pending) {
+      TRY(enqueue_step(c, 1));
+      c->first_pending = 0;
+    } else if (c->x.use_graph) {
+      if (!c->graph_ok && !c->graph_failed) {
+        if (build_graph(c) != FSI_OK) c->graph_failed = 1;
+      }
+      if (c->graph_ok) {
+        FSI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
+      } else {
+        TRY(enqueue_step(c, 0));
+      }
+    } else {
+      TRY(enqueue_step(c, 0));
+    }
+    c->steps_done++;
+  }
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_profile_kernel(fsi_ctx* c, int kernel_class, int n_steps, double* avg_ms,
+                                         int* launches) {
+  if (!c || kernel_class < KC_XF || kernel_class > KC_INJECT || n_steps < 1 || n_steps > 1024 || !avg_ms ||
+      !launches)
+    return FSI_ERR_INVALID_ARG;
+  if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
+  const int cap = 2 * 32 * n_steps;
+  c->prof_ev.assign(cap, nullptr);
+  fsi_status st = FSI_OK;
+  for (int k = 0; k < cap; ++k)
+    if (cudaEventCreate(&c->prof_ev[k]) != cudaSuccess) st = FSI_ERR_CUDA;
+  c->prof_class = kernel_class;
+  c->prof_used = 0;
+  for (int n = 0; st == FSI_OK && n < n_steps; ++n) {
+    st = enqueue_step(c, c->first_pending);
+    c->first_pending = 0;
+    c->steps_done++;
+  }
+  c->prof_class = KC_NONE;
+  double sum = 0.0;
+  int pairs = 0;
+  if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+  for (int k = 0; st == FSI_OK && k + 1 < c->prof_used; k += 2) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[k], c->prof_ev[k + 1]) != cudaSuccess) st = FSI_ERR_CUDA;
+    sum += ms;
+    ++pairs;
+  }
+  for (cudaEvent_t e : c->prof_ev)
+    if (e) cudaEventDestroy(e);
+  c->prof_ev.clear();
+  c->prof_used = 0;
+  *launches = pairs;
+  *avg_ms = pairs ? sum / pairs : 0.0;
+  return st;
+}
+
+extern "C" fsi_status fsi_sync(fsi_ctx* c) {
+  if (!c) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  int st = 0;
+  FSI_CUDA_TRY(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  return (fsi_status)st;
+}
+
+static fsi_status read_state(fsi_ctx* c, int body, BodyState* s) {
+  if (!c || body < 0 || body >= (int)c->bodies.size() || !c->d_state) return FSI_ERR_INVALID_ARG;
+  fsi_status st = fsi_sync(c);
+  if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
+  FSI_CUDA_TRY(cudaMemcpy(s, c->d_state + body, sizeof(BodyState), cudaMemcpyDeviceToHost));
+  return st;
+}
+
+extern "C" fsi_status fsi_get_forces(fsi_ctx* c, int body, double* fx, double* fy, double* moment) {
+  BodyState s;
+  fsi_status st = read_state(c, body, &s);
+  if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
+  if (fx) *fx = s.fx;
+  if (fy) *fy = s.fy;
+  if (moment) *moment = s.moment;
+  return st;
+}
+
+extern "C" fsi_status fsi_get_deflection(fsi_ctx* c, int body, double* theta, double* phi) {
+  BodyState s;
+  fsi_status st = read_state(c, body, &s);
+  if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
+  if (theta) *theta = s.theta;
+  if (phi) *phi = s.phi;
+  return st;
+}
+
+extern "C" fsi_status fsi_get_history(fsi_ctx* c, int body, int field, double* out, int cap, int* n) {
+  if (!c || !out || !n || field < 0 || field > 5 || body < 0 || body >= (int)c->bodies.size() || !c->d_hist)
+    return FSI_ERR_INVALID_ARG;
+  fsi_status st = fsi_sync(c);
+  if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
+  const long long done = c->steps_done;
+  long long kept = done < c->hist_cap ? done : c->hist_cap;
+  if (kept > cap) kept = cap;
+  std::vector<double> buf((size_t)c->hist_cap * c->n_bodies * 6);
+  FSI_CUDA_TRY(cudaMemcpy(buf.data(), c->d_hist, buf.size() * 8, cudaMemcpyDeviceToHost));
+  for (long long k = 0; k < kept; ++k) {
+    const long long step = done - kept + k;
+    const long slot = (long)(step % c->hist_cap);
+    out[k] = buf[((size_t)slot * c->n_bodies + body) * 6 + field];
+  }
+  *n = (int)kept;
+  return st;
+}
+
+template <typename T>
+static void to_double(const void* src, double* dst, long rows, long cols, long ld) {
+  const T* s = (const T*)src;
+  for (long j = 0; j < rows; ++j)
+    for (long i = 0; i < cols; ++i) dst[j * cols + i] = (double)s[j * ld + i];
+}
+
+extern "C" fsi_status fsi_get_field(fsi_ctx* c, int level, int which, double* out) {
+  if (!c || !out || level < 0 || level >= c->G || which < 0 || which > 1) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::vector<char> buf((size_t)c->lvl_elems * c->esz);
+  const char* base = (const char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->esz;
+  FSI_CUDA_TRY(cudaMemcpy(buf.data(), base, buf.size(), cudaMemcpyDeviceToHost));
+  if (c->prec == FSI_PREC_FP64)
+    to_double<double>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
+  else
+    to_double<float>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_set_field(fsi_ctx* c, int level, int which, const double* in) {
+  if (!c || !in || level < 0 || level >= c->G || which < 0 || which > 1) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::vector<char> buf((size_t)c->lvl_elems * c->esz, 0);
+  for (long j = 0; j <= c->ny; ++j)
+    for (long i = 0; i <= c->nx; ++i) {
+      const double v = in[j * (c->nx + 1) + i];
+      if (c->prec == FSI_PREC_FP64)
+        ((double*)buf.data())[j * c->ps + i] = v;
+      else
+        ((float*)buf.data())[j * c->ps + i] = (float)v;
+    }
+  char* base = (char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->esz;
+  FSI_CUDA_TRY(cudaMemcpy(base, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  c->first_pending = 1;
+  return FSI_OK;
+}
+
+__global__ static void k_gather_b0(const double* B0, long n2, const int64_t* rows, const int64_t* cols, int n,
+                                   double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = B0[rows[k] * n2 + cols[k]];
+}
+
+extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, const int64_t* cols, int n,
+                                               double* out) {
+  if (!c || n < 0 || (n > 0 && (!rows || !cols || !out))) return FSI_ERR_INVALID_ARG;
+  if (!c->have_b0) return FSI_ERR_STATE;
+  const long n2 = 2L * c->n_sd;
+  for (int k = 0; k < n; ++k)
+    if (rows[k] < 0 || rows[k] >= n2 || cols[k] < 0 || cols[k] >= n2) return FSI_ERR_INVALID_ARG;
+  if (n == 0) return FSI_OK;
+  int64_t *dr = nullptr, *dc = nullptr;
+  double* dout = nullptr;
+  fsi_status st = FSI_OK;
+  if (cudaMalloc(&dr, n * 8) != cudaSuccess || cudaMalloc(&dc, n * 8) != cudaSuccess ||
+      cudaMalloc(&dout, n * 8) != cudaSuccess) {
+    st = FSI_ERR_OOM;
+  } else if (cudaMemcpyAsync(dr, rows, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+             cudaMemcpyAsync(dc, cols, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    st = FSI_ERR_CUDA;
+  } else {
+    k_gather_b0<<<(n + 255) / 256, 256, 0, c->stream>>>(c->B0, n2, dr, dc, n, dout);
+    if (cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      st = FSI_ERR_CUDA;
+  }
+  cudaFree(dr);
+  cudaFree(dc);
+  cudaFree(dout);
+  return st;
+}
+
+extern "C" fsi_status fsi_get_interp(fsi_ctx* c, int64_t* idx, double* w, int cap_points) {
+  if (!c || !idx || !w || cap_points < c->nb || !c->d_pidx) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::vector<int> pi((size_t)c->nb * 4);
+  FSI_CUDA_TRY(cudaMemcpy(pi.data(), c->d_pidx, pi.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  FSI_CUDA_TRY(cudaMemcpy(w, c->d_pw, pi.size() * 8, cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < pi.size(); ++k) idx[k] = pi[k];
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
+  if (!c || !out) return FSI_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  out->steps_done = c->steps_done;
+  out->n_sd = c->n_sd;
+  out->nf = c->nf;
+  out->b0_seconds = c->b0_seconds;
+  out->device_bytes = c->dev_bytes;
+  out->launches_per_step = c->launches_per_step;
+  if (c->d_ctrl) {
+    FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int ctrl[4];
+    FSI_CUDA_TRY(cudaMemcpy(ctrl, c->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    out->last_iters = ctrl[1];
+  }
+  return FSI_OK;
+}
+
+extern "C" void fsi_destroy(fsi_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  ctx_free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}

@@ -1,0 +1,325 @@
+// Batched DST-I passes built on a shared-memory Stockham FFT (radix 4, one radix-2 stage when log2 L is
+// odd).  The DST-I of two real rows x1, x2 of length N = M-1 is read off one complex FFT of length
+// L = 2M of the packed odd extension z = (x1 + i x2) extended oddly about 0 and M:
+//   X1_k = -Im(Z_k)/2,  X2_k = Re(Z_k)/2,  k = 1..N,
+// with X_k = sum_j x_j sin(pi j k / M) (unnormalised; the inverse is (2/M) times the same transform).
+// The 2-D DST diagonalises C^T C and A (Sec. 3.2.1), so a Poisson-type solve is
+//   forward x (pass XF) -> forward y, diagonal scaling, inverse y (pass Y) -> inverse x (pass XI),
+// with the x <-> y transposition folded into the stores of passes XF and Y.
+#pragma once
+#include "common.cuh"
+
+namespace dst {
+
+// Twiddle table tw[m] = exp(-2 pi i m / L), m < L (host-computed in double).
+template <typename T, int PER>
+__device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int logL,
+                                          const typename C2<T>::t* __restrict__ tw) {
+  using c2 = typename C2<T>::t;
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  int logNs = 0;
+  int rem = logL;
+  while (rem > 0) {
+    c2 v[4 * PER];
+    if (rem >= 2) {
+      const int logLr = logL - 2, Lr = 1 << logLr;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int b = tid + q * nthr;
+        const int f = b >> logLr, j = b & (Lr - 1);
+        const c2* x = buf + ((long)f << logL);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[4 * q + r] = x[j + r * Lr];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int b = tid + q * nthr;
+        const int f = b >> logLr, j = b & (Lr - 1);
+        const int k = j & ((1 << logNs) - 1);
+        const int tstep = k << (logL - logNs - 2);
+        c2* a = &v[4 * q];
+        if (logNs > 0) {
+#pragma unroll
+          for (int r = 1; r < 4; ++r) {
+            const c2 w = tw[r * tstep];
+            const T re = a[r].x * w.x - a[r].y * w.y;
+            const T im = a[r].x * w.y + a[r].y * w.x;
+            a[r].x = re;
+            a[r].y = im;
+          }
+        }
+        const T a0x = a[0].x + a[2].x, a0y = a[0].y + a[2].y;
+        const T a1x = a[0].x - a[2].x, a1y = a[0].y - a[2].y;
+        const T a2x = a[1].x + a[3].x, a2y = a[1].y + a[3].y;
+        const T dx = a[1].x - a[3].x, dy = a[1].y - a[3].y;  // (d)(-i) = (dy, -dx)
+        c2* x = buf + ((long)f << logL);
+        const int o = ((j >> logNs) << (logNs + 2)) + k;
+        const int ns = 1 << logNs;
+        x[o].x = a0x + a2x;
+        x[o].y = a0y + a2y;
+        x[o + ns].x = a1x + dy;
+        x[o + ns].y = a1y - dx;
+        x[o + 2 * ns].x = a0x - a2x;
+        x[o + 2 * ns].y = a0y - a2y;
+        x[o + 3 * ns].x = a1x - dy;
+        x[o + 3 * ns].y = a1y + dx;
+      }
+      __syncthreads();
+      logNs += 2;
+      rem -= 2;
+    } else {
+      const int logLr = logL - 1, Lr = 1 << logLr;
+#pragma unroll
+      for (int q = 0; q < 2 * PER; ++q) {
+        const int b = tid + q * nthr;
+        const int f = b >> logLr, j = b & (Lr - 1);
+        const c2* x = buf + ((long)f << logL);
+        v[2 * q] = x[j];
+        v[2 * q + 1] = x[j + Lr];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 2 * PER; ++q) {
+        const int b = tid + q * nthr;
+        const int f = b >> logLr, j = b & (Lr - 1);
+        const int k = j & ((1 << logNs) - 1);
+        c2 a0 = v[2 * q], a1 = v[2 * q + 1];
+        if (logNs > 0) {
+          const c2 w = tw[k << (logL - logNs - 1)];
+          const T re = a1.x * w.x - a1.y * w.y;
+          const T im = a1.x * w.y + a1.y * w.x;
+          a1.x = re;
+          a1.y = im;
+        }
+        c2* x = buf + ((long)f << logL);
+        const int o = ((j >> logNs) << (logNs + 1)) + k;
+        x[o].x = a0.x + a1.x;
+        x[o].y = a0.y + a1.y;
+        x[o + (1 << logNs)].x = a0.x - a1.x;
+        x[o + (1 << logNs)].y = a0.y - a1.y;
+      }
+      __syncthreads();
+      logNs += 1;
+      rem -= 1;
+    }
+  }
+}
+
+// Pack rows r0 (real part) and r1 (imag part) of length N into the odd extension in buffer f.
+// Rows beyond nrows read as zero.  Caller syncs afterwards.
+template <typename T>
+__device__ __forceinline__ void zero_ends(typename C2<T>::t* buf, int nf, int L) {
+  const int M = L >> 1;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    buf[(long)f * L].x = 0;
+    buf[(long)f * L].y = 0;
+    buf[(long)f * L + M].x = 0;
+    buf[(long)f * L + M].y = 0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void put_pair(typename C2<T>::t* z, int L, int n, T a, T b) {
+  z[n + 1].x = a;
+  z[n + 1].y = b;
+  z[L - 1 - n].x = -a;
+  z[L - 1 - n].y = -b;
+}
+
+// Diagonal scaling data for pass Y (Sec. 3.2.1): A_w = 1/dt + lambda/(2 Re), lambda = (lx_k + ly_l)/h^2
+// with lx_k = 4 sin^2(pi k/(2 Mx)).  Boundary-ring terms of a nested level enter as a rank-4 sum over the
+// sine transforms of the four ring sides (left/right along y, bottom/top along x).
+template <typename T>
+struct SpecParams {
+  const double* lx;   // [Mx] (index k = 1..Nx used)
+  const double* ly;   // [My]
+  const double* sx1;  // sin(pi k/Mx)
+  const double* sxN;  // sin(pi k Nx/Mx)
+  const double* sy1;
+  const double* syN;
+  const T* ring;      // 8 spectra: wL wR (len Ny) wB wT (len Nx) sL sR sB sT, each stride ring_ld; NULL = no ring
+  long ring_ld;
+  double inv_h2, inv_dt, inv_2re, norm;  // norm = 4/(Mx My)
+  int Mx, My;
+};
+
+// Pass XF: rows j of `in` (row stride in_ld, nrows rows of length N) -> unnormalised DST along the row ->
+// transposed store out[k*out_ld + j] (k = 0..N-1).  blockIdx.y indexes a batch with element strides.
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
+                                            T* __restrict__ out, long out_ld, long out_bs,
+                                            const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
+  using c2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2* buf = reinterpret_cast<c2*>(smem_raw);
+  const int L = 1 << logL;
+  const int row0 = blockIdx.x * 2 * nf;
+  in += (long)blockIdx.y * in_bs;
+  out += (long)blockIdx.y * out_bs;
+  zero_ends<T>(buf, nf, L);
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, n = idx - f * N;
+    const int r0 = row0 + 2 * f;
+    const T a = (r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
+    const T b = (r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
+    put_pair<T>(buf + (long)f * L, L, n, a, b);
+  }
+  __syncthreads();
+  block_fft<T, PER>(buf, L, logL, tw);
+  const int nr = 2 * nf;
+  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
+    const int r = idx % nr, k = idx / nr;
+    const int row = row0 + r;
+    if (row < nrows) {
+      const c2 z = buf[(long)(r >> 1) * L + k + 1];
+      out[(long)k * out_ld + row] = (r & 1) ? T(0.5) * z.x : T(-0.5) * z.y;
+    }
+  }
+}
+
+// Pass Y: rows k of `in` (x-frequency k+1; nrows = Nx rows of length N = Ny) -> DST along y -> diagonal
+// solve for w~ = (r^ + bc_w)/A_w and s~ = (w~ + bc_s)/lambda, both times norm -> DST along y (inverse) ->
+// transposed stores outw[j*out_ld + k], outs[j*out_ld + k].
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
+                                                T* __restrict__ outw, T* __restrict__ outs, long out_ld,
+                                                long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
+                                                int nf, SpecParams<T> sp) {
+  using c2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2* buf = reinterpret_cast<c2*>(smem_raw);
+  c2* buf2 = buf + (long)nf * (1 << logL);
+  const int L = 1 << logL;
+  const int row0 = blockIdx.x * 2 * nf;
+  in += (long)blockIdx.y * in_bs;
+  outw += (long)blockIdx.y * out_bs;
+  outs += (long)blockIdx.y * out_bs;
+  zero_ends<T>(buf, nf, L);
+  zero_ends<T>(buf2, 2 * nf, L);
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, n = idx - f * N;
+    const int r0 = row0 + 2 * f;
+    const T a = (r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
+    const T b = (r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
+    put_pair<T>(buf + (long)f * L, L, n, a, b);
+  }
+  __syncthreads();
+  block_fft<T, PER>(buf, L, logL, tw);
+  const int nr = 2 * nf;
+  const T* ring = sp.ring;
+  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
+    const int r = idx / N, l0 = idx - r * N;  // l0 = l-1
+    const int k = row0 + r + 1;              // x-frequency
+    const int l = l0 + 1;
+    const c2 z = buf[(long)(r >> 1) * L + l];
+    T rh = (r & 1) ? T(0.5) * z.x : T(-0.5) * z.y;
+    T wt, st;
+    if (k <= nrows) {
+      const T lam = T((sp.lx[k] + sp.ly[l]) * sp.inv_h2);
+      const T aw = T(sp.inv_dt) + lam * T(sp.inv_2re);
+      T bcs = T(0);
+      if (ring) {
+        const int Nx = nrows;
+        const T bw = T(sp.sx1[k]) * ring[0 * sp.ring_ld + l0] + T(sp.sxN[k]) * ring[1 * sp.ring_ld + l0] +
+                     ring[2 * sp.ring_ld + (k - 1)] * T(sp.sy1[l]) + ring[3 * sp.ring_ld + (k - 1)] * T(sp.syN[l]);
+        bcs = T(sp.sx1[k]) * ring[4 * sp.ring_ld + l0] + T(sp.sxN[k]) * ring[5 * sp.ring_ld + l0] +
+              ring[6 * sp.ring_ld + (k - 1)] * T(sp.sy1[l]) + ring[7 * sp.ring_ld + (k - 1)] * T(sp.syN[l]);
+        rh += bw * T(sp.inv_2re * sp.inv_h2);
+        bcs *= T(sp.inv_h2);
+        (void)Nx;
+      }
+      wt = rh / aw;
+      st = (wt + bcs) / lam;
+      wt *= T(sp.norm);
+      st *= T(sp.norm);
+    } else {
+      wt = T(0);
+      st = T(0);
+    }
+    put_pair<T>(buf2 + (long)r * L, L, l0, wt, st);
+  }
+  __syncthreads();
+  block_fft<T, 2 * PER>(buf2, L, logL, tw);
+  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
+    const int r = idx % nr, j = idx / nr;
+    const int k = row0 + r;
+    if (k < nrows) {
+      const c2 z = buf2[(long)r * L + j + 1];
+      outw[(long)j * out_ld + k] = T(-0.5) * z.y;
+      outs[(long)j * out_ld + k] = T(0.5) * z.x;
+    }
+  }
+}
+
+// Pass XI: row j of inw and ins (length N = Nx) -> DST along x -> w, s rows written to the level fields
+// (row j+1, columns 1..N of a vertex array with row stride f_ld).  mode 0: store, 1: subtract.
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* __restrict__ ins, long in_ld,
+                                            long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
+                                            long f_ld, long f_bs, int mode,
+                                            const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
+  using c2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2* buf = reinterpret_cast<c2*>(smem_raw);
+  const int L = 1 << logL;
+  const int row0 = blockIdx.x * nf;
+  inw += (long)blockIdx.y * in_bs;
+  ins += (long)blockIdx.y * in_bs;
+  fw += (long)blockIdx.y * f_bs;
+  fs += (long)blockIdx.y * f_bs;
+  zero_ends<T>(buf, nf, L);
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, n = idx - f * N;
+    const int r = row0 + f;
+    const T a = (r < nrows) ? inw[(long)r * in_ld + n] : T(0);
+    const T b = (r < nrows) ? ins[(long)r * in_ld + n] : T(0);
+    put_pair<T>(buf + (long)f * L, L, n, a, b);
+  }
+  __syncthreads();
+  block_fft<T, PER>(buf, L, logL, tw);
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, i = idx - f * N;
+    const int r = row0 + f;
+    if (r < nrows) {
+      const c2 z = buf[(long)f * L + i + 1];
+      const long o = (long)(r + 1) * f_ld + 1 + i;
+      const T w = T(-0.5) * z.y, s = T(0.5) * z.x;
+      if (mode == 0) {
+        fw[o] = w;
+        fs[o] = s;
+      } else {
+        fw[o] -= w;
+        fs[o] -= s;
+      }
+    }
+  }
+}
+
+// Plain DST of strided vectors (used for the four ring sides): vectors v = 2*blockIdx.x + {0, 1} are read
+// from srcs[v] with element stride es[v] and written contiguously to dsts[v].
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_vec_dst(const T* const* __restrict__ srcs, const long* __restrict__ es,
+                                                 int nvec, int N, T* const* __restrict__ dsts,
+                                                 const typename C2<T>::t* __restrict__ tw, int logL) {
+  using c2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2* buf = reinterpret_cast<c2*>(smem_raw);
+  const int L = 1 << logL;
+  const int v0 = blockIdx.x * 2;
+  zero_ends<T>(buf, 1, L);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const T a = (v0 < nvec) ? srcs[v0][(long)n * es[v0]] : T(0);
+    const T b = (v0 + 1 < nvec) ? srcs[v0 + 1][(long)n * es[v0 + 1]] : T(0);
+    put_pair<T>(buf, L, n, a, b);
+  }
+  __syncthreads();
+  block_fft<T, PER>(buf, L, logL, tw);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const c2 z = buf[n + 1];
+    if (v0 < nvec) dsts[v0][n] = T(-0.5) * z.y;
+    if (v0 + 1 < nvec) dsts[v0 + 1][n] = T(0.5) * z.x;
+  }
+}
+
+}  // namespace dst

@@ -1,0 +1,112 @@
+// Internal context layout and launcher declarations (not part of the C ABI).
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+struct LevelBufs {
+  void* w;      // vertex vorticity [(ny+1) x ps]
+  void* s;      // vertex streamfunction
+  void* nprev;  // advection term of the previous step (interior entries used)
+  void* rhs;    // right-hand side, interior rows stored at [j-1][i-1] with stride ps
+};
+
+struct BodyHost {
+  int type, off, n;
+  double hx, hy, theta0, inertia, damping, stiffness;
+  double theta, phi, phidot;
+};
+
+// Device-side body record (double).
+struct BodyDev {
+  int type, off, n, pad;
+  double hx, hy, theta0, inertia, damping, stiffness;
+};
+
+// Mutable per-body state on the device.
+struct BodyState {
+  double theta, phi, phidot;
+  double theta_k, phi_k, r_phi, r_theta, jac;
+  double fx, fy, moment;
+};
+
+struct fsi_ctx {
+  fsi_grid_desc g;
+  fsi_exec_desc x;
+  int prec;  // FSI_PREC_*
+  size_t esz;
+  cudaStream_t stream;
+  int G, nx, ny, Nx, Ny, Mx, My, logLx, logLy;
+  long ps;        // vertex row stride (elements)
+  long lvl_elems; // (ny+1)*ps
+  long ldT;       // row stride of the x->y transposed buffer (>= Ny)
+  long ldX;       // row stride of the y->x buffers (>= Nx)
+  // fluid buffers (precision prec)
+  void *w_all, *s_all, *nprev_all, *rhs_all;
+  void *T1, *T2w, *T2s, *src, *ring;  // ring: 8 x ring_ld spectra
+  long ring_ld;
+  // tables (double)
+  double *lx, *ly, *sx1, *sxN, *sy1, *syN;
+  void *twx, *twy;  // complex twiddles in precision prec (length Lx, Ly)
+  // ring DST pointer tables, per level: [G][8] src pointers, strides, dst pointers
+  void **ring_src, **ring_dst;
+  long* ring_es;
+  // sub-domain
+  int have_sd;
+  int i_lo, i_hi, j_lo, j_hi, ni, nj, n_sd;
+  double* B0;  // (2 n_sd)^2 row-major, double
+  int have_b0;
+  double b0_seconds;
+  // bodies
+  std::vector<BodyHost> bodies;
+  std::vector<double> rigid_pts, rigid_ur;  // [nb*2] (zeros for torsional points)
+  int nb, nf, n_bodies;
+  double ds;
+  BodyDev* d_bodies;
+  BodyState* d_state;
+  int* d_point_body;  // body index per point
+  double *d_rpts, *d_rur;
+  // FSI workspace
+  int* d_pidx;     // [nb*4] Omega_0 point index
+  double* d_pw;    // [nb*4]
+  double* d_sv;    // [nb*2] torsional S entries (Q_j R)
+  double* d_rhs;   // [nf]
+  double* d_K;     // [nf*nf]
+  double* d_f;     // [nf]
+  int* d_ctrl;     // [0] converged flag, [1] iteration count, [2] step index, [3..6] bbox
+  int* d_status;
+  double* d_hist;  // [cap][n_bodies][6]
+  int hist_cap;
+  long long steps_done;
+  int max_iters_seen;
+  int fsi_grid;  // CTAs of the cooperative FSI kernel
+  // graph
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  int graph_ok, graph_failed;
+  int own_stream;     // stream created by the library (caller passed NULL)
+  int first_pending;  // next step uses N^{n-1} := N^n (first step, or fields were overwritten)
+  int stage;          // 0 = setup, 1 = precomputed
+  // live kernel timing: events around every launch of one kernel class (eager steps only)
+  int prof_class;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used;
+  int launches_per_step;
+  size_t dev_bytes;
+  std::vector<void*> allocs;
+};
+
+// fluid.cu
+fsi_status launch_predictor(fsi_ctx* c, int first);
+fsi_status launch_corrector(fsi_ctx* c);
+fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void* s, int use_ring, int mode);
+// fsi.cu
+fsi_status launch_fsi(fsi_ctx* c);
+// b0.cu
+fsi_status build_b0(fsi_ctx* c);
+
+void* ctx_alloc(fsi_ctx* c, size_t bytes);
+
+// kernel classes for fsi_profile_kernel
+enum { KC_NONE = 0, KC_XF = 1, KC_YSOLVE = 2, KC_XI = 3, KC_FSI = 4, KC_RHS = 5, KC_SRC = 6, KC_RING = 7,
+       KC_VECDST = 8, KC_INJECT = 9 };
+void prof_mark(fsi_ctx* c, int cls);  // records one event if cls is being profiled

@@ -1,0 +1,93 @@
+// Operator-level entry points (include/ibfsi_ops.h): a stand-alone level solve and an FMA-rate probe.
+#include <vector>
+#include "internal.h"
+#include "../../include/ibfsi_ops.h"
+
+extern "C" fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt,
+                                         const double* rhs, double* w_out, double* s_out) {
+  if (!rhs || !w_out || !s_out) return FSI_ERR_INVALID_ARG;
+  fsi_grid_desc g = {};
+  g.nx = nx;
+  g.ny = ny;
+  g.n_levels = 1;
+  g.h = h;
+  g.re = re;
+  g.dt = dt;
+  fsi_exec_desc x = {};
+  x.precision = precision;
+  fsi_ctx* c = nullptr;
+  fsi_status st = fsi_create(&g, &x, &c);
+  if (st != FSI_OK) return st;
+  const long Nx = nx - 1, Ny = ny - 1;
+  std::vector<char> buf((size_t)c->lvl_elems * c->esz, 0);
+  for (long j = 0; j < Ny; ++j)
+    for (long i = 0; i < Nx; ++i) {
+      const double v = rhs[j * Nx + i];
+      if (c->prec == FSI_PREC_FP64)
+        ((double*)buf.data())[j * c->ps + i] = v;
+      else
+        ((float*)buf.data())[j * c->ps + i] = (float)v;
+    }
+  if (cudaMemcpy(c->rhs_all, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) st = FSI_ERR_CUDA;
+  if (st == FSI_OK) st = launch_level_solve(c, 0, c->rhs_all, c->w_all, c->s_all, 0, 0);
+  if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+  std::vector<double> full((size_t)(nx + 1) * (ny + 1));
+  if (st == FSI_OK) st = fsi_get_field(c, 0, 0, full.data());
+  for (long j = 0; st == FSI_OK && j < Ny; ++j)
+    for (long i = 0; i < Nx; ++i) w_out[j * Nx + i] = full[(j + 1) * (nx + 1) + i + 1];
+  if (st == FSI_OK) st = fsi_get_field(c, 0, 1, full.data());
+  for (long j = 0; st == FSI_OK && j < Ny; ++j)
+    for (long i = 0; i < Nx; ++i) s_out[j * Nx + i] = full[(j + 1) * (nx + 1) + i + 1];
+  fsi_destroy(c);
+  return st;
+}
+
+template <typename T>
+__global__ void k_fma(T* out, int iters, T a, T b) {
+  T x0 = (T)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b);
+    x1 = fma(x1, a, b);
+    x2 = fma(x2, a, b);
+    x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b);
+    x5 = fma(x5, a, b);
+    x6 = fma(x6, a, b);
+    x7 = fma(x7, a, b);
+  }
+  const T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == (T)-1.2345) out[0] = s;  // keeps the loop alive
+}
+
+template <typename T>
+static fsi_status fma_rate(double* r) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  T* out = nullptr;
+  FSI_CUDA_TRY(cudaMalloc(&out, sizeof(T)));
+  const int blocks = nsm * 8, threads = 256, iters = sizeof(T) == 8 ? 4096 : 65536;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma<T><<<blocks, threads>>>(out, 16, (T)0.999, (T)0.001);
+  cudaEventRecord(e0);
+  k_fma<T><<<blocks, threads>>>(out, iters, (T)0.999, (T)0.001);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  FSI_CUDA_TRY(e);
+  *r = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_op_fma_rate(int precision, double* flops_per_s) {
+  if (!flops_per_s) return FSI_ERR_INVALID_ARG;
+  if (precision == FSI_PREC_FP64) return fma_rate<double>(flops_per_s);
+  if (precision == FSI_PREC_FP32) return fma_rate<float>(flops_per_s);
+  return FSI_ERR_INVALID_ARG;
+}

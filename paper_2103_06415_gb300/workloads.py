@@ -1,0 +1,67 @@
+"""Synthetic workloads shaped like the paper's experiments, and seeded input generators.
+
+This module holds parameters and random inputs only (no arithmetic of the method), so both the CUDA
+path and the CPU oracle can be driven from the same inputs.
+
+Configurations (their readings are listed in the design doc):
+
+* ``plate_128``  -- single level 128x128 cells on [-1,3]x[-2,2] (h = 1/32), Re 100, dt 0.002, one rigid
+  flat plate of chord 1 hinged at its leading edge (0,0) on a torsional spring (inertia 1, stiffness 0.5,
+  no damping), initial angle 20 deg, 33 points at ds = h; Omega_0 = [-1.2,1.2]^2.
+* ``flag_512x256_3lvl`` -- 3 nested levels of 512x256 cells, finest h = 1/100 on [-1,4.12]x[-1.28,1.28],
+  Re 200, dt 5e-4; body: a torsional plate of 101 points (length 1) hinged at (0,0) standing in for the
+  clamped flag (inertia 0.1/3 = mass ratio 0.1 plate about its end, spring 1e-3 = bending stiffness / L),
+  initial deflection 0.1 rad; Omega_0 = [-0.2,1.2]x[-0.7,0.7] (141 x 141 points).
+"""
+
+import numpy as np
+
+SEED = 20261203
+
+
+def plate_128():
+    return dict(
+        name="plate_128", nx=128, ny=128, n_levels=1, x0=-1.0, y0=-2.0, h=1.0 / 32, re=100.0, dt=0.002,
+        uinf=(1.0, 0.0), steps=100, sd_box=(-1.2, 1.2, -1.2, 1.2),
+        bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=33, inertia=1.0, damping=0.0,
+                     stiffness=0.5, theta=np.deg2rad(20.0))],
+        ds=1.0 / 32)
+
+
+def flag_512x256_3lvl():
+    return dict(
+        name="flag_512x256_3lvl", nx=512, ny=256, n_levels=3, x0=-1.0, y0=-1.28, h=0.01, re=200.0, dt=5e-4,
+        uinf=(1.0, 0.0), steps=2000, sd_box=(-0.2, 1.2, -0.7, 0.7),
+        bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=101, inertia=0.1 / 3.0, damping=0.0,
+                     stiffness=1e-3, theta=0.1)],
+        ds=0.01)
+
+
+def small_plate(nx=48, ny=40, n_levels=1):
+    """A small torsional-plate case the oracle runs in seconds (several FFT tiles, ragged Omega_0 box)."""
+    h = 1.0 / 16
+    return dict(
+        name="small_plate_%dx%d_%dlvl" % (nx, ny, n_levels), nx=nx, ny=ny, n_levels=n_levels, x0=-1.0,
+        y0=-1.25, h=h, re=100.0, dt=0.004, uinf=(1.0, 0.0), steps=20, sd_box=(-0.6, 0.8, -0.7, 0.8),
+        bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=9, inertia=0.05, damping=0.0,
+                     stiffness=0.5, theta=np.deg2rad(20.0))],
+        ds=h)
+
+
+def random_field(shape, seed, smooth=True):
+    """Seeded vertex field: a few low sine modes plus small noise (ring included)."""
+    rng = np.random.default_rng(seed)
+    ny1, nx1 = shape
+    y = np.linspace(0, 1, ny1)[:, None]
+    x = np.linspace(0, 1, nx1)[None, :]
+    f = np.zeros(shape)
+    if smooth:
+        for _ in range(4):
+            k, l = rng.integers(1, 5, size=2)
+            f += rng.standard_normal() * np.sin(np.pi * k * x) * np.sin(np.pi * l * y)
+    f += 0.05 * rng.standard_normal(shape)
+    return f
+
+
+def random_rhs(ny_int, nx_int, seed):
+    return np.random.default_rng(seed).standard_normal((ny_int, nx_int))

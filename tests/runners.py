@@ -1,0 +1,44 @@
+"""Build an oracle run and a CUDA-library run from the same workload description."""
+
+import numpy as np
+
+from oracle import fsi as ofsi
+
+
+def oracle_sim(w):
+    bodies = []
+    for b in w["bodies"]:
+        if b["kind"] == "torsional":
+            bodies.append(ofsi.TorsionalBody(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"],
+                                             b["stiffness"], b["theta"]))
+        else:
+            bodies.append(ofsi.RigidBody(b["pts"], b.get("ur")))
+    return ofsi.Sim(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["n_levels"], w["re"], w["dt"], w["uinf"],
+                    w["sd_box"], bodies, w["ds"])
+
+
+def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None):
+    import paper_2103_06415_gb300 as lib
+    c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
+                    precision=precision, use_graph=use_graph, stream=stream)
+    for b in w["bodies"]:
+        if b["kind"] == "torsional":
+            c.add_torsional(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"], b["stiffness"],
+                            b["theta"])
+        else:
+            c.add_rigid(b["pts"], w["ds"], b.get("ur"))
+    if w.get("sd_box") is not None:
+        c.set_subdomain(*w["sd_box"])
+        if precompute:
+            c.precompute()
+    return c
+
+
+def oracle_history(sim, body=0):
+    return np.array([[r["bodies"][body][k] for k in ("fx", "fy", "moment", "theta", "phi")] + [r["iters"]]
+                     for r in sim.history])
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

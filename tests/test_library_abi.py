@@ -1,0 +1,45 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every symbol the headers declare."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(fsi_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_builds_and_exports_all_declared_symbols():
+    from paper_2103_06415_gb300 import build as b
+    lib = b.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (fsi_[a-z0-9_]+)", out))
+    declared = _declared()
+    assert declared, "no declarations found"
+    assert declared <= exported, sorted(declared - exported)
+
+
+def test_binding_signatures_cover_headers_and_load():
+    from paper_2103_06415_gb300 import _lib
+    lib = _lib.load()
+    assert set(_lib.SIGNATURES) == _declared()
+    assert lib.fsi_status_string(4) == b"body point outside the sub-domain"
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    from paper_2103_06415_gb300 import _lib
+    import ctypes
+    lib = _lib.load()
+    g = _lib.GridDesc(100, 64, 1, 0, 0, 0.1, 100, 0.01, (ctypes.c_double * 2)(1, 0))   # nx not a power of two
+    h = ctypes.c_void_p()
+    assert lib.fsi_create(ctypes.byref(g), None, ctypes.byref(h)) == 1
+    assert lib.fsi_advance(None, 1) == 1
