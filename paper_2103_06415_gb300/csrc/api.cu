@@ -320,7 +320,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_pidx = (int*)ctx_alloc(c, (size_t)c->nb * 4 * sizeof(int))) ||
         !(c->d_pw = (double*)ctx_alloc(c, (size_t)c->nb * 4 * 8)) ||
         !(c->d_sv = (double*)ctx_alloc(c, (size_t)c->nb * 2 * 8)) ||
-        !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+        !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 2 * 8)) ||
         !(c->d_K = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)) ||
         !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))

@@ -86,7 +86,8 @@ __device__ void make_stencil(int comp, double h, Stencil* s) {
     }
 }
 
-// tables[((ca*2+cb)*4 + term)][ix][iy], term bit0: x uses the sum index, bit1: y uses the sum index
+// tables[((ca*2+cb)*4 + term)][iy][ix] (x index contiguous), term bit0: x uses the sum index, bit1: y uses
+// the sum index
 __global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g, int Mx, int My, int ni, int nj,
                          int i_lo, int j_lo, double h) {
   const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
@@ -95,7 +96,7 @@ __global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g,
   if (e >= 16 * per) return;
   const int tb = (int)(e / per);
   const long r = e - (long)tb * per;
-  const int ix = (int)(r / ny2), iy = (int)(r - (long)ix * ny2);
+  const int iy = (int)(r / nx2), ix = (int)(r - (long)iy * nx2);
   const int term = tb & 3, cab = tb >> 2, ca = cab >> 1, cb = cab & 1;
   Stencil sa, sb;
   make_stencil(ca, h, &sa);
@@ -113,20 +114,32 @@ __global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g,
   tab[e] = acc;
 }
 
-__global__ void k_fill(double* __restrict__ B0, const double* __restrict__ tab, int ni, int nj, int n_sd) {
+// One CTA per row a of B0: B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb) - T-+(ia-ib, ja+jb)
+// + T++(ia+ib, ja+jb); threads run along ib so stores and table reads are contiguous.
+__global__ void __launch_bounds__(256) k_fill(double* __restrict__ B0, const double* __restrict__ tab, int ni,
+                                              int nj, int n_sd) {
   const long n2 = 2L * n_sd;
   const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
   const long per = (long)nx2 * ny2;
-  const long total = n2 * n2;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    const long a = e / n2, b = e - a * n2;
-    const int ca = (int)(a / n_sd), cb = (int)(b / n_sd);
-    const int pa = (int)(a - (long)ca * n_sd), pb = (int)(b - (long)cb * n_sd);
-    const int ja = pa / ni, ia = pa - ja * ni, jb = pb / ni, ib = pb - jb * ni;
-    const int D = ia - ib + ni - 1, S = ia + ib, Dy = ja - jb + nj - 1, Sy = ja + jb;
-    const double* t = tab + (long)((ca * 2 + cb) * 4) * per;
-    B0[e] = t[(long)D * ny2 + Dy] - t[per + (long)S * ny2 + Dy] - t[2 * per + (long)D * ny2 + Sy] +
-            t[3 * per + (long)S * ny2 + Sy];
+  for (long a = blockIdx.x; a < n2; a += gridDim.x) {
+    const int ca = (int)(a / n_sd);
+    const int pa = (int)(a - (long)ca * n_sd);
+    const int ja = pa / ni, ia = pa - ja * ni;
+    double* row = B0 + a * n2;
+    for (int cb = 0; cb < 2; ++cb) {
+      const double* t = tab + (long)((ca * 2 + cb) * 4) * per;
+      for (int jb = 0; jb < nj; ++jb) {
+        const double* tmm = t + (long)(ja - jb + nj - 1) * nx2;
+        const double* tpm = t + per + (long)(ja - jb + nj - 1) * nx2;
+        const double* tmp = t + 2 * per + (long)(ja + jb) * nx2;
+        const double* tpp = t + 3 * per + (long)(ja + jb) * nx2;
+        double* out = row + (long)cb * n_sd + (long)jb * ni;
+        for (int ib = threadIdx.x; ib < ni; ib += blockDim.x) {
+          const int D = ia - ib + ni - 1, S = ia + ib;
+          out[ib] = tmm[D] - tpm[S] - tmp[D] + tpp[S];
+        }
+      }
+    }
   }
 }
 
@@ -164,7 +177,7 @@ fsi_status build_b0(fsi_ctx* c) {
                                                                      c->j_lo, h);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
-    k_fill<<<nsm * 8, 256, 0, c->stream>>>(c->B0, d_tab, c->ni, c->nj, c->n_sd);
+    k_fill<<<nsm * 16, 256, 0, c->stream>>>(c->B0, d_tab, c->ni, c->nj, c->n_sd);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
   cudaFree(d_cx);

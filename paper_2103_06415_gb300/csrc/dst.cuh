@@ -127,6 +127,18 @@ __device__ __forceinline__ void put_pair(typename C2<T>::t* z, int L, int n, T a
   z[L - 1 - n].y = -b;
 }
 
+// One real row into the real (part 0) or imaginary (part 1) lane of an odd extension.
+template <typename T>
+__device__ __forceinline__ void put_one(typename C2<T>::t* z, int L, int n, T a, int part) {
+  if (part) {
+    z[n + 1].y = a;
+    z[L - 1 - n].y = -a;
+  } else {
+    z[n + 1].x = a;
+    z[L - 1 - n].x = -a;
+  }
+}
+
 // Diagonal scaling data for pass Y (Sec. 3.2.1): A_w = 1/dt + lambda/(2 Re), lambda = (lx_k + ly_l)/h^2
 // with lx_k = 4 sin^2(pi k/(2 Mx)).  Boundary-ring terms of a nested level enter as a rank-4 sum over the
 // sine transforms of the four ring sides (left/right along y, bottom/top along x).
@@ -237,7 +249,10 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
       wt = T(0);
       st = T(0);
     }
-    put_pair<T>(buf2 + (long)r * L, L, l0, wt, st);
+    // neighbouring rows of the same field share one complex FFT (w~ rows in buffers 0..nf-1, s~ rows in
+    // nf..2nf-1): s~ is smaller than w~ by ~1/lambda, so packing w~ with s~ would bury s~ in rounding.
+    put_one<T>(buf2 + (long)(r >> 1) * L, L, l0, wt, r & 1);
+    put_one<T>(buf2 + (long)(nf + (r >> 1)) * L, L, l0, st, r & 1);
   }
   __syncthreads();
   block_fft<T, 2 * PER>(buf2, L, logL, tw);
@@ -245,15 +260,17 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     const int r = idx % nr, j = idx / nr;
     const int k = row0 + r;
     if (k < nrows) {
-      const c2 z = buf2[(long)r * L + j + 1];
-      outw[(long)j * out_ld + k] = T(-0.5) * z.y;
-      outs[(long)j * out_ld + k] = T(0.5) * z.x;
+      const c2 zw = buf2[(long)(r >> 1) * L + j + 1];
+      const c2 zs = buf2[(long)(nf + (r >> 1)) * L + j + 1];
+      outw[(long)j * out_ld + k] = (r & 1) ? T(0.5) * zw.x : T(-0.5) * zw.y;
+      outs[(long)j * out_ld + k] = (r & 1) ? T(0.5) * zs.x : T(-0.5) * zs.y;
     }
   }
 }
 
-// Pass XI: row j of inw and ins (length N = Nx) -> DST along x -> w, s rows written to the level fields
+// Pass XI: rows j of inw and ins (length N = Nx) -> DST along x -> w, s rows written to the level fields
 // (row j+1, columns 1..N of a vertex array with row stride f_ld).  mode 0: store, 1: subtract.
+// A CTA takes 2*nf rows; rows j, j+1 of w share one FFT (buffer f), rows j, j+1 of s another (nf + f).
 template <typename T, int PER>
 __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* __restrict__ ins, long in_ld,
                                             long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
@@ -263,28 +280,32 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = 1 << logL;
-  const int row0 = blockIdx.x * nf;
+  const int row0 = blockIdx.x * 2 * nf;
   inw += (long)blockIdx.y * in_bs;
   ins += (long)blockIdx.y * in_bs;
   fw += (long)blockIdx.y * f_bs;
   fs += (long)blockIdx.y * f_bs;
-  zero_ends<T>(buf, nf, L);
+  zero_ends<T>(buf, 2 * nf, L);
   for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
     const int f = idx / N, n = idx - f * N;
-    const int r = row0 + f;
-    const T a = (r < nrows) ? inw[(long)r * in_ld + n] : T(0);
-    const T b = (r < nrows) ? ins[(long)r * in_ld + n] : T(0);
-    put_pair<T>(buf + (long)f * L, L, n, a, b);
+    const int r0 = row0 + 2 * f;
+    const bool v0 = r0 < nrows, v1 = r0 + 1 < nrows;
+    put_pair<T>(buf + (long)f * L, L, n, v0 ? inw[(long)r0 * in_ld + n] : T(0),
+                v1 ? inw[(long)(r0 + 1) * in_ld + n] : T(0));
+    put_pair<T>(buf + (long)(nf + f) * L, L, n, v0 ? ins[(long)r0 * in_ld + n] : T(0),
+                v1 ? ins[(long)(r0 + 1) * in_ld + n] : T(0));
   }
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tw);
-  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
-    const int f = idx / N, i = idx - f * N;
-    const int r = row0 + f;
+  block_fft<T, 2 * PER>(buf, L, logL, tw);
+  for (int idx = threadIdx.x; idx < 2 * nf * N; idx += blockDim.x) {
+    const int f2 = idx / N, i = idx - f2 * N;  // f2 = local row
+    const int r = row0 + f2;
     if (r < nrows) {
-      const c2 z = buf[(long)f * L + i + 1];
+      const c2 zw = buf[(long)(f2 >> 1) * L + i + 1];
+      const c2 zs = buf[(long)(nf + (f2 >> 1)) * L + i + 1];
       const long o = (long)(r + 1) * f_ld + 1 + i;
-      const T w = T(-0.5) * z.y, s = T(0.5) * z.x;
+      const T w = (f2 & 1) ? T(0.5) * zw.x : T(-0.5) * zw.y;
+      const T s = (f2 & 1) ? T(0.5) * zs.x : T(-0.5) * zs.y;
       if (mode == 0) {
         fw[o] = w;
         fs[o] = s;

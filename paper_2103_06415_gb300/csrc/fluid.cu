@@ -224,11 +224,11 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     }
   }
   prof_mark(c, KC_YSOLVE);
-  // XI: nf rows per CTA, one FFT per row pair (w, s)
+  // XI: 2*nf rows per CTA; rows j, j+1 of w share one FFT, rows j, j+1 of s another
   prof_mark(c, KC_XI);
   {
-    dim3 grid((c->Ny + cx.nf - 1) / cx.nf, 1);
-    const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
+    dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
+    const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
     switch (cx.per) {
       case 1: dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
       case 2: dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;

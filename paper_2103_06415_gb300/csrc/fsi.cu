@@ -1,13 +1,13 @@
 // FSI iteration of one time step (Algorithm 2; Eqs. stress2 and dtheta2) in double precision, as one
-// cooperative kernel over the whole GPU:
+// cooperative kernel over a fixed set of CTAs:
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
 //   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
-//   C  f = K^{-1} rhs to double accuracy: Cholesky of K rounded to float in shared memory, then
-//      iterative refinement with double residuals r = rhs - K f (K read in double);
-//      dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta|                  [CTA 0]
+//   C  f = K^{-1} rhs to double accuracy: blocked Cholesky of K rounded to float in the shared memory of
+//      CTA 0, three solves with that factor separated by double residuals r = rhs - K f   [CTA 0 + all]
+//   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta|                 [CTA 0]
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs.
-// Data written by other CTAs inside this kernel is read with __ldcg (L2) so no stale L1 line is used.
+// Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
 #include "internal.h"
@@ -15,6 +15,10 @@
 namespace cg = cooperative_groups;
 
 namespace {
+
+constexpr int kSolves = 3;  // factor solves; kSolves-1 double residuals in between
+constexpr int BS = 32;      // Cholesky block (one warp)
+constexpr unsigned FULL = 0xffffffffu;
 
 struct FsiArgs {
   const void* s0;
@@ -33,7 +37,7 @@ struct FsiArgs {
   int* pidx;
   double* pw;
   double* sv;
-  double* rhs;
+  double* rhs;  // [nf] right-hand side, then [nf] residual
   double* K;
   double* f;
   int* ctrl;
@@ -73,18 +77,128 @@ __device__ double block_sum(double x, double* red) {
   return r;
 }
 
-constexpr int kRefine = 4;
+// Blocked right-looking Cholesky of the lower triangle of L (row stride ld) in shared memory.
+// Returns false (in every thread) if a pivot is not positive.
+__device__ bool chol_blocked(float* L, int n, int ld, int* bad) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int jb = 0; jb < n; jb += BS) {
+    const int bs = min(BS, n - jb);
+    if (wid == 0) {  // diagonal block in registers: lane r holds row jb + r
+      float a[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) a[c] = (lane < bs && c < bs) ? L[(long)(jb + lane) * ld + jb + c] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < BS; ++c)
+        if (lane >= bs && c == lane) a[c] = 1.0f;  // identity padding keeps the padded factor defined
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        float d = __shfl_sync(FULL, a[c], c);
+        if (!(d > 0.0f)) {
+          if (lane == 0 && c < bs) *bad = 1;
+          d = 1.0f;
+        }
+        d = sqrtf(d);
+        if (lane == c) a[c] = d;
+        if (lane > c) a[c] /= d;
+#pragma unroll
+        for (int cc = c + 1; cc < BS; ++cc) {
+          const float lcc = __shfl_sync(FULL, a[c], cc);
+          if (lane > c && cc <= lane) a[cc] -= a[c] * lcc;
+        }
+      }
+      if (lane < bs) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+          if (c <= lane && c < bs) L[(long)(jb + lane) * ld + jb + c] = a[c];
+      }
+    }
+    __syncthreads();
+    // panel: rows below solve X Ldiag^T = A (row-wise forward substitution)
+    for (int i = jb + bs + tid; i < n; i += blockDim.x) {
+      float* row = L + (long)i * ld + jb;
+      for (int c = 0; c < bs; ++c) {
+        float v = row[c];
+        const float* dr = L + (long)(jb + c) * ld + jb;
+        for (int cc = 0; cc < c; ++cc) v -= row[cc] * dr[cc];
+        row[c] = v / dr[c];
+      }
+    }
+    __syncthreads();
+    // trailing update A22 -= L21 L21^T (lower part), one warp per row
+    const int t0 = jb + bs;
+    for (int i = t0 + wid; i < n; i += nw) {
+      const float* ri = L + (long)i * ld + jb;
+      for (int k = t0 + lane; k <= i; k += 32) {
+        const float* rk = L + (long)k * ld + jb;
+        float acc = 0.0f;
+        for (int c = 0; c < bs; ++c) acc += ri[c] * rk[c];
+        L[(long)i * ld + k] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  return *bad == 0;
+}
+
+// y <- (L L^T)^{-1} y with the blocked factor (float, in shared memory).
+__device__ void chol_solve(const float* L, int n, int ld, float* y) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nblk = (n + BS - 1) / BS;
+  for (int b = 0; b < nblk; ++b) {  // forward
+    const int jb = b * BS, bs = min(BS, n - jb);
+    if (wid == 0) {
+      float v = lane < bs ? y[jb + lane] : 0.0f;
+      for (int c = 0; c < bs; ++c) {
+        const float yc = __shfl_sync(FULL, v, c) / L[(long)(jb + c) * ld + jb + c];
+        if (lane == c) v = yc;
+        if (lane > c && lane < bs) v -= L[(long)(jb + lane) * ld + jb + c] * yc;
+      }
+      if (lane < bs) y[jb + lane] = v;
+    }
+    __syncthreads();
+    for (int i = jb + bs + tid; i < n; i += blockDim.x) {
+      const float* ri = L + (long)i * ld + jb;
+      float acc = 0.0f;
+      for (int c = 0; c < bs; ++c) acc += ri[c] * y[jb + c];
+      y[i] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward with L^T
+    const int jb = b * BS, bs = min(BS, n - jb);
+    if (wid == 0) {
+      float v = lane < bs ? y[jb + lane] : 0.0f;
+      for (int c = bs - 1; c >= 0; --c) {
+        const float xc = __shfl_sync(FULL, v, c) / L[(long)(jb + c) * ld + jb + c];
+        if (lane == c) v = xc;
+        if (lane < c) v -= L[(long)(jb + c) * ld + jb + lane] * xc;
+      }
+      if (lane < bs) y[jb + lane] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < jb; i += blockDim.x) {
+      float acc = 0.0f;
+      for (int c = 0; c < bs; ++c) acc += L[(long)(jb + c) * ld + i] * y[jb + c];
+      y[i] -= acc;
+    }
+    __syncthreads();
+  }
+}
 
 __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
-  __shared__ int sh_flag;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  __shared__ int sh_flag, sh_bad;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   const long gtid = (long)blockIdx.x * nthr + tid;
   const long gsize = (long)gridDim.x * nthr;
   const int nb = a.nb, nf = a.nf;
+  const int ld = nf | 1;
   const double dt = a.dt;
+  double* res = a.rhs + nf;
 
   if (blockIdx.x == 0 && tid < a.n_bodies) {
     const BodyDev b = a.bodies[tid];
@@ -99,6 +213,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     }
   }
   if (gtid == 0) a.ctrl[0] = 0;
+  if (tid == 0) sh_flag = 0;
   grid.sync();
 
   int it = 0;
@@ -159,7 +274,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.rhs[nb + p] = uby - ucy + svy * coef;
     }
     grid.sync();
-    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (lower triangle)
+    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles written)
     const double kscale = a.ds / (a.h * a.h);
     const long n2 = 2L * a.n_sd;
     for (long e = gtid; e < (long)nf * nf; e += gsize) {
@@ -188,76 +303,49 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL)
         kv += (2.0 * a.ds / dt) / __ldcg(&a.st[ba].jac) * __ldcg(&a.sv[2 * pa + ca]) * __ldcg(&a.sv[2 * pb + cb]);
       a.K[(long)r * nf + cidx] = kv;
+      a.K[(long)cidx * nf + r] = kv;
     }
     grid.sync();
-    // ---- C: solve K f = rhs (CTA 0): float Cholesky in shared memory + double iterative refinement
+    // ---- C: float factor in CTA 0, kSolves solves with double residuals computed by all CTAs
+    float* Lf = reinterpret_cast<float*>(dyn_smem);  // [nf][ld]
+    double* xs = reinterpret_cast<double*>(dyn_smem + (((size_t)nf * ld * 4 + 15) / 16) * 16);  // [nf]
+    float* yv = reinterpret_cast<float*>(xs + nf);   // [nf]
     if (blockIdx.x == 0) {
-      float* Lf = reinterpret_cast<float*>(dyn_smem);             // [nf][nf] lower factor
-      double* xs = reinterpret_cast<double*>(Lf + (long)nf * nf);  // [nf] solution (double)
-      double* rs = xs + nf;                                        // [nf] residual (double)
-      float* ds_ = reinterpret_cast<float*>(rs + nf);              // [nf] correction (float)
-      for (long e = tid; e < (long)nf * nf; e += nthr) {
-        const int i = (int)(e / nf), k = (int)(e % nf);
-        Lf[e] = k <= i ? (float)__ldcg(&a.K[e]) : 0.0f;
-      }
-      for (int i = tid; i < nf; i += nthr) {
-        xs[i] = 0.0;
-        rs[i] = __ldcg(&a.rhs[i]);
-      }
+      for (int i = tid >> 5; i < nf; i += nthr >> 5)
+        for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
       __syncthreads();
-      for (int j = 0; j < nf; ++j) {
-        if (tid == 0) {
-          const float d = Lf[(long)j * nf + j];
-          if (!(d > 0.0f) || !isfinite(d)) {
-            dev_set_status(a.status, FSI_ERR_NONFINITE);
-            Lf[(long)j * nf + j] = 1.0f;
-          } else {
-            Lf[(long)j * nf + j] = sqrtf(d);
-          }
-        }
+      if (!chol_blocked(Lf, nf, ld, &sh_bad) && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
+      for (int i = tid; i < nf; i += nthr) xs[i] = 0.0;
+    }
+    for (int sidx = 0; sidx < kSolves; ++sidx) {
+      if (blockIdx.x == 0) {
+        const double* r = sidx == 0 ? a.rhs : res;
+        for (int i = tid; i < nf; i += nthr) yv[i] = (float)__ldcg(&r[i]);
         __syncthreads();
-        const float dj = Lf[(long)j * nf + j];
-        for (int i = j + 1 + tid; i < nf; i += nthr) Lf[(long)i * nf + j] /= dj;
-        __syncthreads();
-        const int m = nf - j - 1;
-        for (long idx = tid; idx < (long)m * m; idx += nthr) {
-          const int i = j + 1 + (int)(idx / m), k = j + 1 + (int)(idx % m);
-          if (k <= i) Lf[(long)i * nf + k] -= Lf[(long)i * nf + j] * Lf[(long)k * nf + j];
-        }
-        __syncthreads();
-      }
-      for (int ref = 0; ref < kRefine; ++ref) {
-        // d = (L L^T)^{-1} r in float
-        for (int i = tid; i < nf; i += nthr) ds_[i] = (float)rs[i];
-        __syncthreads();
-        for (int j = 0; j < nf; ++j) {
-          if (tid == 0) ds_[j] /= Lf[(long)j * nf + j];
-          __syncthreads();
-          const float yj = ds_[j];
-          for (int i = j + 1 + tid; i < nf; i += nthr) ds_[i] -= Lf[(long)i * nf + j] * yj;
-          __syncthreads();
-        }
-        for (int j = nf - 1; j >= 0; --j) {
-          if (tid == 0) ds_[j] /= Lf[(long)j * nf + j];
-          __syncthreads();
-          const float xj = ds_[j];
-          for (int i = tid; i < j; i += nthr) ds_[i] -= Lf[(long)j * nf + i] * xj;
-          __syncthreads();
-        }
-        for (int i = tid; i < nf; i += nthr) xs[i] += (double)ds_[i];
-        __syncthreads();
-        // r = rhs - K x in double (K symmetric, lower triangle stored)
+        chol_solve(Lf, nf, ld, yv);
         for (int i = tid; i < nf; i += nthr) {
-          double acc = __ldcg(&a.rhs[i]);
-          for (int k = 0; k <= i; ++k) acc -= __ldcg(&a.K[(long)i * nf + k]) * xs[k];
-          for (int k = i + 1; k < nf; ++k) acc -= __ldcg(&a.K[(long)k * nf + i]) * xs[k];
-          rs[i] = acc;
+          xs[i] += (double)yv[i];
+          a.f[i] = xs[i];
         }
         __syncthreads();
       }
-      for (int i = tid; i < nf; i += nthr) a.f[i] = xs[i];
-      __syncthreads();
-      // dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta|
+      if (sidx == kSolves - 1) break;
+      grid.sync();
+      // residual r = rhs - K x in double, one warp per row
+      {
+        const long wg = gtid >> 5, nwg = gsize >> 5;
+        for (long i = wg; i < nf; i += nwg) {
+          double acc = 0.0;
+          for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.K[i * nf + k]) * __ldcg(&a.f[k]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+          if (lane == 0) res[i] = __ldcg(&a.rhs[i]) - acc;
+        }
+      }
+      grid.sync();
+    }
+    // ---- D: dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta| (CTA 0)
+    if (blockIdx.x == 0) {
       double dmax = 0.0;
       bool finite = true;
       for (int bi = 0; bi < a.n_bodies; ++bi) {
@@ -332,14 +420,19 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
 
 }  // namespace
 
-size_t fsi_smem_bytes(int nf) { return (size_t)nf * nf * 4 + (size_t)nf * 20 + 64; }
+size_t fsi_smem_bytes(int nf) {
+  const size_t ld = (size_t)(nf | 1);
+  return (((size_t)nf * ld * 4 + 15) / 16) * 16 + (size_t)nf * 12 + 64;
+}
+
+int fsi_kernel_max_ctas_per_sm(int nf) {
+  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, fsi_smem_bytes(nf));
+  return n;
+}
 
 fsi_status launch_fsi(fsi_ctx* c) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
   FsiArgs a;
   a.s0 = c->s_all;
   a.fp64 = c->prec == FSI_PREC_FP64;
@@ -392,11 +485,4 @@ fsi_status launch_fsi(fsi_ctx* c) {
   prof_mark(c, KC_FSI);
   c->launches_per_step += 1;
   return FSI_OK;
-}
-
-int fsi_kernel_max_ctas_per_sm(int nf) {
-  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, fsi_smem_bytes(nf));
-  return n;
 }

@@ -37,12 +37,12 @@ def flag_512x256_3lvl():
         ds=0.01)
 
 
-def small_plate(nx=48, ny=40, n_levels=1):
+def small_plate(nx=64, ny=32, n_levels=1):
     """A small torsional-plate case the oracle runs in seconds (several FFT tiles, ragged Omega_0 box)."""
     h = 1.0 / 16
     return dict(
         name="small_plate_%dx%d_%dlvl" % (nx, ny, n_levels), nx=nx, ny=ny, n_levels=n_levels, x0=-1.0,
-        y0=-1.25, h=h, re=100.0, dt=0.004, uinf=(1.0, 0.0), steps=20, sd_box=(-0.6, 0.8, -0.7, 0.8),
+        y0=-1.0, h=h, re=100.0, dt=0.004, uinf=(1.0, 0.0), steps=20, sd_box=(-0.6, 0.8, -0.7, 0.8),
         bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=9, inertia=0.05, damping=0.0,
                      stiffness=0.5, theta=np.deg2rad(20.0))],
         ds=h)
