@@ -281,7 +281,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   c->n_bodies = (int)c->bodies.size();
   c->nf = 2 * c->nb;
   if (c->n_bodies > 256) return FSI_ERR_UNSUPPORTED;
-  if (c->nb > 0 && fsi_smem_bytes(c->nf) > 220 * 1024) return FSI_ERR_UNSUPPORTED;
+  if (c->nb > 0 && fsi_smem_bytes(c->nf) > 200 * 1024) return FSI_ERR_UNSUPPORTED;
   const size_t n2 = 2 * (size_t)c->n_sd;
   if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
   fsi_status st = build_b0(c);
@@ -323,6 +323,9 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 2 * 8)) ||
         !(c->d_K = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)) ||
         !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+        !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bodies, bd.data(), bd.size() * sizeof(BodyDev), cudaMemcpyHostToDevice, c->stream));
@@ -335,7 +338,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf);
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
-    c->fsi_grid = nsm;
+    c->fsi_grid = nsm / 2 > 0 ? nsm / 2 : 1;  // fewer CTAs -> cheaper grid-wide barriers
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;

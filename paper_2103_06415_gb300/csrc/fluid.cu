@@ -126,25 +126,30 @@ __global__ void k_ring(T* __restrict__ wf, T* __restrict__ sf, const T* __restri
 }
 
 // O5 source: src = (ds/h^2) curl_h(E0^T P^T f) on the level-0 vertices of the Omega_0 box grown by 3
-// cells.  Deterministic gather: each face sums over all body points (no atomics), so results do not depend
-// on scheduling.  Face weights: P row (hat, 4 nodes) times the E0 stencil (1/6, 2/3, 1/6) x (1/2, 1/2).
+// cells.  Deterministic gather: each face sums over all body points in a fixed order (no atomics), so a run
+// gives the same bits every time.  Face weights: P row (hat, 4 nodes) times the E0 stencil
+// (1/6, 2/3, 1/6) x (1/2, 1/2).  Body-point data is staged in shared memory in chunks.
 __device__ __forceinline__ double wx3(int d) { return d == 0 ? 2.0 / 3.0 : ((d == 1 || d == -1) ? 1.0 / 6.0 : 0.0); }
 
-__device__ double face_force(int comp, int fi, int fj, const int* __restrict__ pidx, const double* __restrict__ pw,
-                             const double* __restrict__ f, int nb, int ni, int i_lo, int j_lo) {
-  // comp 0: u-face (fi, fj+1/2); comp 1: v-face (fi+1/2, fj)
+constexpr int kSrcChunk = 256;
+
+struct SrcPt {
+  int ci, cj;        // absolute level-0 vertex of the cell's lower-left node
+  double w[4], fx, fy;
+};
+
+// comp 0: u-face (fi, fj+1/2); comp 1: v-face (fi+1/2, fj)
+__device__ __forceinline__ double face_force(int comp, int fi, int fj, const SrcPt* pts, int n) {
   double acc = 0.0;
-  for (int p = 0; p < nb; ++p) {
-    const int n0 = pidx[4 * p];
-    const int ci = n0 % ni + i_lo, cj = n0 / ni + j_lo;  // absolute vertex of the cell corner
-    if (fi < ci - 2 || fi > ci + 3 || fj < cj - 2 || fj > cj + 3) continue;
+  for (int p = 0; p < n; ++p) {
+    const SrcPt& q = pts[p];
+    if (fi < q.ci - 2 || fi > q.ci + 3 || fj < q.cj - 2 || fj > q.cj + 3) continue;
     double wsum = 0.0;
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        const double wp = pw[4 * p + 2 * b + a];
-        const int vi = ci + a, vj = cj + b;
+        const int vi = q.ci + a, vj = q.cj + b;
         double e;
         if (comp == 0) {
           const int dj = fj - vj;  // face y = fj+1/2 ; offsets -1/2 (dj=-1) or +1/2 (dj=0)
@@ -153,26 +158,48 @@ __device__ double face_force(int comp, int fi, int fj, const int* __restrict__ p
           const int di = fi - vi;
           e = ((di == 0 || di == -1) ? 0.5 : 0.0) * wx3(fj - vj);
         }
-        wsum += wp * e;
+        wsum += q.w[2 * b + a] * e;
       }
-    acc += wsum * f[comp * nb + p];
+    acc += wsum * (comp == 0 ? q.fx : q.fy);
   }
   return acc;
 }
 
 template <typename T>
-__global__ void k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
-                      const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni, int i_lo,
-                      int i_hi, int j_lo, int j_hi, double scale, double h) {
+__global__ void __launch_bounds__(256) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
+                                             const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
+                                             int i_lo, int i_hi, int j_lo, int j_hi, double scale, double h) {
+  __shared__ SrcPt pts[kSrcChunk];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int i = i_lo - 3 + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = j_lo - 3 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > i_hi + 3 || j > j_hi + 3 || i < 1 || j < 1 || i > nx - 1 || j > ny - 1) return;
-  // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
-  const double fve = face_force(1, i, j, pidx, pw, f, nb, ni, i_lo, j_lo);
-  const double fvw = face_force(1, i - 1, j, pidx, pw, f, nb, ni, i_lo, j_lo);
-  const double fun = face_force(0, i, j, pidx, pw, f, nb, ni, i_lo, j_lo);
-  const double fus = face_force(0, i, j - 1, pidx, pw, f, nb, ni, i_lo, j_lo);
-  src[(long)(j - 1) * ps + (i - 1)] = T(scale * ((fve - fvw) - (fun - fus)) / h);
+  const bool active = !(i > i_hi + 3 || j > j_hi + 3 || i < 1 || j < 1 || i > nx - 1 || j > ny - 1);
+  double fve = 0.0, fvw = 0.0, fun = 0.0, fus = 0.0;
+  for (int p0 = 0; p0 < nb; p0 += kSrcChunk) {
+    const int n = min(kSrcChunk, nb - p0);
+    if (tid < n) {
+      const int p = p0 + tid;
+      const int n0 = pidx[4 * p];
+      SrcPt q;
+      q.ci = n0 % ni + i_lo;
+      q.cj = n0 / ni + j_lo;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q.w[k] = pw[4 * p + k];
+      q.fx = f[p];
+      q.fy = f[nb + p];
+      pts[tid] = q;
+    }
+    __syncthreads();
+    if (active) {
+      // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
+      fve += face_force(1, i, j, pts, n);
+      fvw += face_force(1, i - 1, j, pts, n);
+      fun += face_force(0, i, j, pts, n);
+      fus += face_force(0, i, j - 1, pts, n);
+    }
+    __syncthreads();
+  }
+  if (active) src[(long)(j - 1) * ps + (i - 1)] = T(scale * ((fve - fvw) - (fun - fus)) / h);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -3,10 +3,13 @@
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
 //   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
-//   C  f = K^{-1} rhs to double accuracy: blocked Cholesky of K rounded to float in the shared memory of
-//      CTA 0, three solves with that factor separated by double residuals r = rhs - K f   [CTA 0 + all]
-//   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta|                 [CTA 0]
-// repeated until max |dtheta| <= tol, then the Newmark update and force outputs.
+//   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = Kinv r with a float inverse Kinv,
+//      f += d, r = rhs - K f in double, until |d| <= 1e-12 |f|                            [all CTAs]
+//      Kinv (from a blocked float Cholesky and triangular inverse of K, CTA 0 + all CTAs) is kept
+//      across iterations and steps and rebuilt only when the refinement needs more than 4 solves.
+//   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta| (every CTA computes the same
+//      value in the same order, so all CTAs take the same branch without another barrier)
+// repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
@@ -16,8 +19,11 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kSolves = 3;  // factor solves; kSolves-1 double residuals in between
-constexpr int BS = 32;      // Cholesky block (one warp)
+constexpr int kMaxSolves = 5;     // refinement solves per attempt
+constexpr int kRefactorAfter = 4;  // more solves than this -> rebuild Kinv for the next iteration
+constexpr double kRefineTol = 1e-12;
+constexpr int BS = 32;  // Cholesky / inverse block (one warp)
+constexpr int kMaxBodies = 256;
 constexpr unsigned FULL = 0xffffffffu;
 
 struct FsiArgs {
@@ -36,11 +42,13 @@ struct FsiArgs {
   const double* rur;
   int* pidx;
   double* pw;
-  double* sv;
-  double* rhs;  // [nf] right-hand side, then [nf] residual
-  double* K;
-  double* f;
-  int* ctrl;
+  double* rhs;   // [nf] right-hand side, then [nf] residual
+  double* K;     // [nf][nf] double, both triangles
+  double* f;     // [nf]
+  float* Kinv;   // [nf][nf]
+  float* W;      // [nf][nf] inverse Cholesky factor (lower)
+  double* part;  // [2 * gridDim] per-CTA maxima
+  int* ctrl;     // [0] unused, [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves
   int* status;
   double* hist;
   int hist_cap;
@@ -63,7 +71,7 @@ __device__ void e0cs(const FsiArgs& a, int I, int J, double* u, double* v) {
   *v = -sv / (2.0 * a.h) + a.V;
 }
 
-// Deterministic block sum (fixed tree); all threads must call; result valid in every thread.
+// Deterministic block reductions (fixed tree); all threads must call; result valid in every thread.
 __device__ double block_sum(double x, double* red) {
   const int tid = threadIdx.x;
   red[tid] = x;
@@ -77,8 +85,20 @@ __device__ double block_sum(double x, double* red) {
   return r;
 }
 
+__device__ double block_max(double x, double* red) {
+  const int tid = threadIdx.x;
+  red[tid] = x;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
 // Blocked right-looking Cholesky of the lower triangle of L (row stride ld) in shared memory.
-// Returns false (in every thread) if a pivot is not positive.
 __device__ bool chol_blocked(float* L, int n, int ld, int* bad) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) *bad = 0;
@@ -115,8 +135,7 @@ __device__ bool chol_blocked(float* L, int n, int ld, int* bad) {
       }
     }
     __syncthreads();
-    // panel: rows below solve X Ldiag^T = A (row-wise forward substitution)
-    for (int i = jb + bs + tid; i < n; i += blockDim.x) {
+    for (int i = jb + bs + tid; i < n; i += blockDim.x) {  // panel: X Ldiag^T = A
       float* row = L + (long)i * ld + jb;
       for (int c = 0; c < bs; ++c) {
         float v = row[c];
@@ -126,8 +145,7 @@ __device__ bool chol_blocked(float* L, int n, int ld, int* bad) {
       }
     }
     __syncthreads();
-    // trailing update A22 -= L21 L21^T (lower part), one warp per row
-    const int t0 = jb + bs;
+    const int t0 = jb + bs;  // trailing update, one warp per row
     for (int i = t0 + wid; i < n; i += nw) {
       const float* ri = L + (long)i * ld + jb;
       for (int k = t0 + lane; k <= i; k += 32) {
@@ -142,104 +160,142 @@ __device__ bool chol_blocked(float* L, int n, int ld, int* bad) {
   return *bad == 0;
 }
 
-// y <- (L L^T)^{-1} y with the blocked factor (float, in shared memory).
-__device__ void chol_solve(const float* L, int n, int ld, float* y) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// W = L^{-1} (lower triangular, float, row-major [n][n] in global memory) from the shared-memory factor.
+// Diagonal blocks: one warp each, lane r holds row r (forward substitution with shuffles).  Off-diagonal
+// blocks W_ij = -W_ii sum_{k=j}^{i-1} L_ik W_kj: one warp per block column j, rows i in order.
+__device__ void tri_inverse(const float* L, int n, int ld, float* W) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int nblk = (n + BS - 1) / BS;
-  for (int b = 0; b < nblk; ++b) {  // forward
+  for (long e = tid; e < (long)n * n; e += blockDim.x) W[e] = 0.0f;
+  __syncthreads();
+  for (int b = wid; b < nblk; b += nw) {
     const int jb = b * BS, bs = min(BS, n - jb);
-    if (wid == 0) {
-      float v = lane < bs ? y[jb + lane] : 0.0f;
-      for (int c = 0; c < bs; ++c) {
-        const float yc = __shfl_sync(FULL, v, c) / L[(long)(jb + c) * ld + jb + c];
-        if (lane == c) v = yc;
-        if (lane > c && lane < bs) v -= L[(long)(jb + lane) * ld + jb + c] * yc;
+    float a[BS], x[BS];
+#pragma unroll
+    for (int c = 0; c < BS; ++c) {
+      a[c] = (lane < bs && c <= lane && c < bs) ? L[(long)(jb + lane) * ld + jb + c] : 0.0f;
+      x[c] = (c == lane) ? 1.0f : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < BS; ++c)
+      if (lane >= bs && c == lane) a[c] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < BS; ++k) {
+      if (lane == k) {
+        const float inv = 1.0f / a[k];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) x[c] *= inv;
       }
-      if (lane < bs) y[jb + lane] = v;
-    }
-    __syncthreads();
-    for (int i = jb + bs + tid; i < n; i += blockDim.x) {
-      const float* ri = L + (long)i * ld + jb;
-      float acc = 0.0f;
-      for (int c = 0; c < bs; ++c) acc += ri[c] * y[jb + c];
-      y[i] -= acc;
-    }
-    __syncthreads();
-  }
-  for (int b = nblk - 1; b >= 0; --b) {  // backward with L^T
-    const int jb = b * BS, bs = min(BS, n - jb);
-    if (wid == 0) {
-      float v = lane < bs ? y[jb + lane] : 0.0f;
-      for (int c = bs - 1; c >= 0; --c) {
-        const float xc = __shfl_sync(FULL, v, c) / L[(long)(jb + c) * ld + jb + c];
-        if (lane == c) v = xc;
-        if (lane < c) v -= L[(long)(jb + c) * ld + jb + lane] * xc;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        const float xk = __shfl_sync(FULL, x[c], k);
+        if (lane > k) x[c] -= a[k] * xk;
       }
-      if (lane < bs) y[jb + lane] = v;
     }
-    __syncthreads();
-    for (int i = tid; i < jb; i += blockDim.x) {
-      float acc = 0.0f;
-      for (int c = 0; c < bs; ++c) acc += L[(long)(jb + c) * ld + i] * y[jb + c];
-      y[i] -= acc;
+    if (lane < bs) {
+#pragma unroll
+      for (int c = 0; c < BS; ++c)
+        if (c <= lane && c < bs) W[(long)(jb + lane) * n + jb + c] = x[c];
     }
-    __syncthreads();
   }
+  __syncthreads();
+  for (int bj = wid; bj < nblk; bj += nw) {
+    const int jb = bj * BS, bsj = min(BS, n - jb);
+    for (int bi = bj + 1; bi < nblk; ++bi) {
+      const int ib = bi * BS, bsi = min(BS, n - ib);
+      float t[BS];  // lane r: row ib + r of T = sum_k L_ik W_kj
+#pragma unroll
+      for (int c = 0; c < BS; ++c) t[c] = 0.0f;
+      for (int bk = bj; bk < bi; ++bk) {
+        const int kb = bk * BS, bsk = min(BS, n - kb);
+        float wrow[BS];  // lane m: row kb + m of W_kj
+#pragma unroll
+        for (int c = 0; c < BS; ++c) wrow[c] = (lane < bsk && c < bsj) ? W[(long)(kb + lane) * n + jb + c] : 0.0f;
+        for (int m = 0; m < bsk; ++m) {
+          const float lim = lane < bsi ? L[(long)(ib + lane) * ld + kb + m] : 0.0f;
+#pragma unroll
+          for (int c = 0; c < BS; ++c) t[c] += lim * __shfl_sync(FULL, wrow[c], m);
+        }
+      }
+      float wii[BS];  // lane r: row ib + r of W_ii
+#pragma unroll
+      for (int c = 0; c < BS; ++c) wii[c] = (lane < bsi && c < bsi) ? W[(long)(ib + lane) * n + ib + c] : 0.0f;
+      float out[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) out[c] = 0.0f;
+      for (int m = 0; m < bsi; ++m) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c) out[c] -= wii[m] * __shfl_sync(FULL, t[c], m);
+      }
+      if (lane < bsi) {
+#pragma unroll
+        for (int c = 0; c < BS; ++c)
+          if (c < bsj) W[(long)(ib + lane) * n + jb + c] = out[c];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
-  __shared__ int sh_flag, sh_bad;
+  __shared__ double b_th[kMaxBodies], b_ph[kMaxBodies], b_rphi[kMaxBodies], b_rth[kMaxBodies], b_jac[kMaxBodies];
+  __shared__ double b_tp[kMaxBodies];  // angle of the iterate that produced the current f (S, P of the solve)
+  __shared__ int sh_bad;
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   const long gtid = (long)blockIdx.x * nthr + tid;
   const long gsize = (long)gridDim.x * nthr;
+  const long wg = gtid >> 5, nwg = gsize >> 5;
   const int nb = a.nb, nf = a.nf;
   const int ld = nf | 1;
   const double dt = a.dt;
   double* res = a.rhs + nf;
 
-  if (blockIdx.x == 0 && tid < a.n_bodies) {
-    const BodyDev b = a.bodies[tid];
-    BodyState& s = a.st[tid];
+  // per-CTA copy of the structural state (identical in every CTA)
+  for (int bi = tid; bi < a.n_bodies; bi += nthr) {
+    const BodyDev b = a.bodies[bi];
+    const BodyState s = a.st[bi];
     if (b.type == FSI_BODY_TORSIONAL) {
-      s.jac = 4.0 * b.inertia / (dt * dt) + 2.0 * b.damping / dt + b.stiffness;
-      s.r_phi = b.inertia * (4.0 * s.theta / (dt * dt) + 4.0 * s.phi / dt + s.phidot) +
-                b.damping * (2.0 * s.theta / dt + s.phi);
-      s.r_theta = s.phi + 2.0 / dt * s.theta;
-      s.theta_k = s.theta;
-      s.phi_k = s.phi;
+      b_jac[bi] = 4.0 * b.inertia / (dt * dt) + 2.0 * b.damping / dt + b.stiffness;
+      b_rphi[bi] = b.inertia * (4.0 * s.theta / (dt * dt) + 4.0 * s.phi / dt + s.phidot) +
+                   b.damping * (2.0 * s.theta / dt + s.phi);
+      b_rth[bi] = s.phi + 2.0 / dt * s.theta;
+      b_th[bi] = s.theta;
+      b_ph[bi] = s.phi;
+      b_tp[bi] = s.theta;
+    } else {
+      b_jac[bi] = 1.0;
+      b_rphi[bi] = b_rth[bi] = b_th[bi] = b_ph[bi] = b_tp[bi] = 0.0;
     }
   }
-  if (gtid == 0) a.ctrl[0] = 0;
-  if (tid == 0) sh_flag = 0;
-  grid.sync();
+  int kinv_valid = *(volatile int*)&a.ctrl[4];
+  __syncthreads();
 
-  int it = 0;
+  bool converged = false;
+  int it = 0, solves_total = 0;
   for (; it < a.max_iters; ++it) {
     // ---- A: body points, P, right-hand side
     for (long p = gtid; p < nb; p += gsize) {
       const int bi = a.point_body[p];
       const BodyDev b = a.bodies[bi];
-      const double th_k = __ldcg(&a.st[bi].theta_k), ph_k = __ldcg(&a.st[bi].phi_k);
-      const double s_rphi = __ldcg(&a.st[bi].r_phi), s_rth = __ldcg(&a.st[bi].r_theta);
-      const double s_jac = __ldcg(&a.st[bi].jac);
       double x, y, svx = 0.0, svy = 0.0, ucx, ucy, coef = 0.0;
       if (b.type == FSI_BODY_TORSIONAL) {
+        const double th_k = b_th[bi], ph_k = b_ph[bi];
         const int j = (int)p - b.off;
-        const double ang = b.theta0 + th_k;
         double sn, cs;
-        sincos(ang, &sn, &cs);
+        sincos(b.theta0 + th_k, &sn, &cs);
         x = b.hx + (double)j * a.ds * cs;
         y = b.hy + (double)j * a.ds * sn;
         svx = (double)j * a.ds * (-sn);
         svy = (double)j * a.ds * cs;
         ucx = svx * ph_k;
         ucy = svy * ph_k;
-        const double rphik = s_rphi - s_jac * th_k;
-        const double rthk = s_rth - 2.0 / dt * th_k + ph_k;
-        coef = rthk - 2.0 / dt * rphik / s_jac;
+        const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
+        const double rthk = b_rth[bi] - 2.0 / dt * th_k + ph_k;
+        coef = rthk - 2.0 / dt * rphik / b_jac[bi];
       } else {
         x = a.rpts[2 * p];
         y = a.rpts[2 * p + 1];
@@ -268,128 +324,180 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         ubx += wts[q] * u;
         uby += wts[q] * v;
       }
-      a.sv[2 * p] = svx;
-      a.sv[2 * p + 1] = svy;
       a.rhs[p] = ubx - ucx + svx * coef;
       a.rhs[nb + p] = uby - ucy + svy * coef;
     }
     grid.sync();
     // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles written)
-    const double kscale = a.ds / (a.h * a.h);
-    const long n2 = 2L * a.n_sd;
-    for (long e = gtid; e < (long)nf * nf; e += gsize) {
-      const int r = (int)(e / nf), cidx = (int)(e % nf);
-      if (cidx > r) continue;
-      const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
-      double acc = 0.0;
-      int ib[4];
-      double wb[4];
+    {
+      const double kscale = a.ds / (a.h * a.h);
+      const long n2 = 2L * a.n_sd;
+      for (long e = gtid; e < (long)nf * nf; e += gsize) {
+        const int r = (int)(e / nf), cidx = (int)(e % nf);
+        if (cidx > r) continue;
+        const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
+        double acc = 0.0;
+        int ib[4];
+        double wb[4];
 #pragma unroll
-      for (int be = 0; be < 4; ++be) {
-        ib[be] = __ldcg(&a.pidx[4 * pb + be]);
-        wb[be] = __ldcg(&a.pw[4 * pb + be]);
-      }
-      for (int al = 0; al < 4; ++al) {
-        const long row = (long)ca * a.n_sd + __ldcg(&a.pidx[4 * pa + al]);
-        const double wa = __ldcg(&a.pw[4 * pa + al]);
-        const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
-        double t = 0.0;
+        for (int be = 0; be < 4; ++be) {
+          ib[be] = __ldcg(&a.pidx[4 * pb + be]);
+          wb[be] = __ldcg(&a.pw[4 * pb + be]);
+        }
+        for (int al = 0; al < 4; ++al) {
+          const long row = (long)ca * a.n_sd + __ldcg(&a.pidx[4 * pa + al]);
+          const double wa = __ldcg(&a.pw[4 * pa + al]);
+          const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
+          double t = 0.0;
 #pragma unroll
-        for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
-        acc += wa * t;
+          for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
+          acc += wa * t;
+        }
+        double kv = kscale * acc;
+        const int ba = a.point_body[pa], bbd = a.point_body[pb];
+        if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
+          const BodyDev b = a.bodies[ba];
+          double sn, cs;
+          sincos(b.theta0 + b_th[ba], &sn, &cs);
+          const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
+          const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
+          kv += (2.0 * a.ds / dt) / b_jac[ba] * sa * sb;
+        }
+        a.K[(long)r * nf + cidx] = kv;
+        a.K[(long)cidx * nf + r] = kv;
       }
-      double kv = kscale * acc;
-      const int ba = a.point_body[pa], bbd = a.point_body[pb];
-      if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL)
-        kv += (2.0 * a.ds / dt) / __ldcg(&a.st[ba].jac) * __ldcg(&a.sv[2 * pa + ca]) * __ldcg(&a.sv[2 * pb + cb]);
-      a.K[(long)r * nf + cidx] = kv;
-      a.K[(long)cidx * nf + r] = kv;
     }
     grid.sync();
-    // ---- C: float factor in CTA 0, kSolves solves with double residuals computed by all CTAs
-    float* Lf = reinterpret_cast<float*>(dyn_smem);  // [nf][ld]
-    double* xs = reinterpret_cast<double*>(dyn_smem + (((size_t)nf * ld * 4 + 15) / 16) * 16);  // [nf]
-    float* yv = reinterpret_cast<float*>(xs + nf);   // [nf]
-    if (blockIdx.x == 0) {
-      for (int i = tid >> 5; i < nf; i += nthr >> 5)
-        for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
-      __syncthreads();
-      if (!chol_blocked(Lf, nf, ld, &sh_bad) && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
-      for (int i = tid; i < nf; i += nthr) xs[i] = 0.0;
-    }
-    for (int sidx = 0; sidx < kSolves; ++sidx) {
-      if (blockIdx.x == 0) {
-        const double* r = sidx == 0 ? a.rhs : res;
-        for (int i = tid; i < nf; i += nthr) yv[i] = (float)__ldcg(&r[i]);
-        __syncthreads();
-        chol_solve(Lf, nf, ld, yv);
-        for (int i = tid; i < nf; i += nthr) {
-          xs[i] += (double)yv[i];
-          a.f[i] = xs[i];
+    // ---- C: iterative refinement with the float inverse (rebuilt when missing or slow)
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (!kinv_valid) {
+        float* Lf = reinterpret_cast<float*>(dyn_smem);
+        if (blockIdx.x == 0) {
+          for (int i = tid >> 5; i < nf; i += nthr >> 5)
+            for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
+          __syncthreads();
+          if (!chol_blocked(Lf, nf, ld, &sh_bad) && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
+          tri_inverse(Lf, nf, ld, a.W);
         }
-        __syncthreads();
+        grid.sync();
+        for (long i = wg; i < nf; i += nwg) {  // Kinv = W^T W, warp per row i, lanes over k <= i
+          for (int k0 = 0; k0 <= i; k0 += 32) {
+            const int k = k0 + lane;
+            float acc = 0.0f;
+            if (k <= i)
+              for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.W[(long)m * nf + i]) * __ldcg(&a.W[(long)m * nf + k]);
+            if (k <= i) {
+              a.Kinv[i * nf + k] = acc;
+              a.Kinv[(long)k * nf + i] = acc;
+            }
+          }
+        }
+        grid.sync();
+        kinv_valid = 1;
       }
-      if (sidx == kSolves - 1) break;
-      grid.sync();
-      // residual r = rhs - K x in double, one warp per row
-      {
-        const long wg = gtid >> 5, nwg = gsize >> 5;
-        for (long i = wg; i < nf; i += nwg) {
+      bool done = false;
+      int s = 0;
+      for (; s < kMaxSolves; ++s) {
+        double dmax = 0.0, xmax = 0.0;
+        for (long i = wg; i < nf; i += nwg) {  // d = Kinv r, f += d
+          const double* r = s == 0 ? a.rhs : res;
+          float acc = 0.0f;
+          for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.Kinv[i * nf + k]) * (float)__ldcg(&r[k]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+          if (lane == 0) {
+            const double xi = (s == 0 ? 0.0 : a.f[i]) + (double)acc;
+            a.f[i] = xi;
+            dmax = fmax(dmax, fabs((double)acc));
+            xmax = fmax(xmax, fabs(xi));
+            if (!isfinite(xi)) dmax = INFINITY;
+          }
+        }
+        dmax = block_max(dmax, red);
+        xmax = block_max(xmax, red);
+        if (tid == 0) {
+          a.part[2 * blockIdx.x] = dmax;
+          a.part[2 * blockIdx.x + 1] = xmax;
+        }
+        grid.sync();
+        double gd = 0.0, gx = 0.0;
+        for (int c = 0; c < (int)gridDim.x; ++c) {
+          gd = fmax(gd, __ldcg(&a.part[2 * c]));
+          gx = fmax(gx, __ldcg(&a.part[2 * c + 1]));
+        }
+        if (!isfinite(gd)) {
+          if (tid == 0 && blockIdx.x == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
+          done = true;
+          break;
+        }
+        if (gd <= kRefineTol * gx) {
+          done = true;
+          break;
+        }
+        if (s == kMaxSolves - 1) break;
+        for (long i = wg; i < nf; i += nwg) {  // r = rhs - K f in double
           double acc = 0.0;
           for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.K[i * nf + k]) * __ldcg(&a.f[k]);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
           if (lane == 0) res[i] = __ldcg(&a.rhs[i]) - acc;
         }
+        grid.sync();
       }
-      grid.sync();
+      solves_total += s + 1;
+      if (s + 1 > kRefactorAfter) kinv_valid = 0;
+      if (done) break;
+      kinv_valid = 0;  // not converged with this inverse: rebuild it and solve again
+      if (attempt == 1 && blockIdx.x == 0 && tid == 0) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
     }
-    // ---- D: dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta| (CTA 0)
-    if (blockIdx.x == 0) {
-      double dmax = 0.0;
-      bool finite = true;
-      for (int bi = 0; bi < a.n_bodies; ++bi) {
-        const BodyDev b = a.bodies[bi];
-        double part = 0.0;
-        for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
-          part += __ldcg(&a.sv[2 * p]) * xs[p] + __ldcg(&a.sv[2 * p + 1]) * xs[nb + p];
-          if (!isfinite(xs[p]) || !isfinite(xs[nb + p])) finite = false;
-        }
-        const double sf = block_sum(part, red);
-        if (b.type == FSI_BODY_TORSIONAL && tid == 0) {
-          BodyState& s = a.st[bi];
-          const double dth = (s.r_phi - s.jac * s.theta_k + a.ds * sf) / s.jac;
-          s.theta_k += dth;
-          s.phi_k = 2.0 / dt * s.theta_k - s.r_theta;
-          dmax = fmax(dmax, fabs(dth));
-        }
+    // ---- D: dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta| (same in every CTA)
+    double dmax = 0.0;
+    bool finite = true;
+    for (int bi = 0; bi < a.n_bodies; ++bi) {
+      const BodyDev b = a.bodies[bi];
+      if (b.type != FSI_BODY_TORSIONAL) continue;
+      double sn, cs;
+      sincos(b.theta0 + b_th[bi], &sn, &cs);
+      double part = 0.0;
+      for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
+        const double q = (double)(p - b.off) * a.ds;
+        const double fxp = __ldcg(&a.f[p]), fyp = __ldcg(&a.f[nb + p]);
+        part += q * (-sn) * fxp + q * cs * fyp;
       }
-      if (!finite) dev_set_status(a.status, FSI_ERR_NONFINITE);
+      const double sf = block_sum(part, red);
+      const double dth = (b_rphi[bi] - b_jac[bi] * b_th[bi] + a.ds * sf) / b_jac[bi];
+      __syncthreads();
       if (tid == 0) {
-        const int conv = (dmax <= a.tol) || !isfinite(dmax) || (*(volatile int*)a.status != 0);
-        a.ctrl[0] = conv;
-        a.ctrl[1] = it + 1;
+        b_tp[bi] = b_th[bi];
+        b_th[bi] += dth;
+        b_ph[bi] = 2.0 / dt * b_th[bi] - b_rth[bi];
       }
+      if (!isfinite(dth)) finite = false;
+      dmax = fmax(dmax, fabs(dth));
       __syncthreads();
     }
-    grid.sync();
-    if (tid == 0) sh_flag = *(volatile int*)&a.ctrl[0];
-    __syncthreads();
-    if (sh_flag) break;
-    grid.sync();  // nobody may overwrite ctrl[0] before all CTAs have read it
+    if (!finite && blockIdx.x == 0 && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
+    converged = (dmax <= a.tol) || !finite;
+    if (converged) break;
+    // No barrier here: after the last barrier of phase C only f is read (phase D), and the next write of
+    // f comes after the phase-A and phase-B barriers of the next iteration.
   }
 
   // ---- Newmark update, forces, history (CTA 0)
   if (blockIdx.x == 0) {
-    if (tid == 0 && !sh_flag) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
+    if (tid == 0 && !converged) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
     const int slot = a.ctrl[2] % a.hist_cap;
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
+      double sn = 0.0, cs = 0.0;
+      if (b.type == FSI_BODY_TORSIONAL) sincos(b.theta0 + b_tp[bi], &sn, &cs);  // S of the final solve
       double px = 0.0, py = 0.0, pm = 0.0;
       for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
-        px += a.f[p];
-        py += a.f[nb + p];
-        pm += __ldcg(&a.sv[2 * p]) * a.f[p] + __ldcg(&a.sv[2 * p + 1]) * a.f[nb + p];
+        const double fxp = __ldcg(&a.f[p]), fyp = __ldcg(&a.f[nb + p]);
+        const double q = (double)(p - b.off) * a.ds;
+        px += fxp;
+        py += fyp;
+        pm += q * (-sn) * fxp + q * cs * fyp;
       }
       const double sx = block_sum(px, red), sy = block_sum(py, red), sm = block_sum(pm, red);
       if (tid == 0) {
@@ -398,11 +506,13 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         s.fy = a.ds * sy;
         s.moment = b.type == FSI_BODY_TORSIONAL ? a.ds * sm : 0.0;
         if (b.type == FSI_BODY_TORSIONAL) {
-          const double th_new = s.theta_k;
-          const double ph_new = 2.0 / dt * th_new - s.r_theta;
+          const double th_new = b_th[bi];
+          const double ph_new = 2.0 / dt * th_new - b_rth[bi];
           s.phidot = 4.0 / (dt * dt) * (th_new - s.theta) - 4.0 / dt * s.phi - s.phidot;
           s.theta = th_new;
           s.phi = ph_new;
+          s.theta_k = th_new;
+          s.phi_k = ph_new;
         }
         double* hrow = a.hist + ((long)slot * a.n_bodies + bi) * 6;
         hrow[0] = s.fx;
@@ -410,11 +520,16 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         hrow[2] = s.moment;
         hrow[3] = b.type == FSI_BODY_TORSIONAL ? s.theta : 0.0;
         hrow[4] = b.type == FSI_BODY_TORSIONAL ? s.phi : 0.0;
-        hrow[5] = (double)a.ctrl[1];
+        hrow[5] = (double)(it + 1);
         if (!isfinite(s.fx) || !isfinite(s.fy)) dev_set_status(a.status, FSI_ERR_NONFINITE);
       }
     }
-    if (tid == 0) a.ctrl[2] += 1;
+    if (tid == 0) {
+      a.ctrl[1] = it + 1;
+      a.ctrl[2] += 1;
+      a.ctrl[4] = kinv_valid;
+      a.ctrl[5] = solves_total;
+    }
   }
 }
 
@@ -422,11 +537,11 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
 
 size_t fsi_smem_bytes(int nf) {
   const size_t ld = (size_t)(nf | 1);
-  return (((size_t)nf * ld * 4 + 15) / 16) * 16 + (size_t)nf * 12 + 64;
+  return (((size_t)nf * ld * 4 + 15) / 16) * 16 + 64;
 }
 
 int fsi_kernel_max_ctas_per_sm(int nf) {
-  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, fsi_smem_bytes(nf));
   return n;
@@ -462,10 +577,12 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.rur = c->d_rur;
   a.pidx = c->d_pidx;
   a.pw = c->d_pw;
-  a.sv = c->d_sv;
   a.rhs = c->d_rhs;
   a.K = c->d_K;
   a.f = c->d_f;
+  a.Kinv = c->d_Kinv;
+  a.W = c->d_W;
+  a.part = c->d_part;
   a.ctrl = c->d_ctrl;
   a.status = c->d_status;
   a.hist = c->d_hist;

@@ -72,6 +72,9 @@ struct fsi_ctx {
   double* d_rhs;   // [nf]
   double* d_K;     // [nf*nf]
   double* d_f;     // [nf]
+  float* d_Kinv;   // [nf*nf] float inverse of K used for iterative refinement
+  float* d_W;      // [nf*nf] inverse Cholesky factor
+  double* d_part;  // [2*fsi_grid] per-CTA maxima
   int* d_ctrl;     // [0] converged flag, [1] iteration count, [2] step index, [3..6] bbox
   int* d_status;
   double* d_hist;  // [cap][n_bodies][6]
