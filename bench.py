@@ -268,6 +268,8 @@ def main():
                            "b0_seconds": b0_s, "l2": "flushed between timed steps (512 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": stats["launches_per_step"] * args.steps,
+                "fsi_solver": {"iterations_last_step": stats["last_iters"], "solves_last_step": stats["last_solves"],
+                               "inverse_rebuilds": stats["inverse_rebuilds"], "steps_run": stats["steps_done"]},
                 "clocks": clocks, "roofline": roof, "e2e": e2e}
         line.update(extra)
         if base is not None:

@@ -108,6 +108,8 @@ typedef struct {
   double b0_seconds;   /* wall time of the last fsi_precompute */
   size_t device_bytes; /* device memory held by the context */
   int launches_per_step; /* kernels this library launches per time step */
+  int last_solves;       /* refinement solves of the small system in the last step (all FSI iterations) */
+  int inverse_rebuilds;  /* times the float inverse of the small system was rebuilt so far */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;

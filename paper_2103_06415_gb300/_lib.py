@@ -49,7 +49,8 @@ class Box(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int64), ("last_iters", ctypes.c_int), ("max_iters_seen", ctypes.c_int),
                 ("n_sd", ctypes.c_int), ("nf", ctypes.c_int), ("b0_seconds", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int)]
+                ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int),
+                ("last_solves", ctypes.c_int), ("inverse_rebuilds", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

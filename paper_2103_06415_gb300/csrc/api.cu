@@ -593,9 +593,11 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   out->launches_per_step = c->launches_per_step;
   if (c->d_ctrl) {
     FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    int ctrl[4];
+    int ctrl[12];
     FSI_CUDA_TRY(cudaMemcpy(ctrl, c->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
     out->last_iters = ctrl[1];
+    out->last_solves = ctrl[5];
+    out->inverse_rebuilds = ctrl[6];
   }
   return FSI_OK;
 }

@@ -125,81 +125,76 @@ __global__ void k_ring(T* __restrict__ wf, T* __restrict__ sf, const T* __restri
   sf[(long)j * ps + i] = s;
 }
 
-// O5 source: src = (ds/h^2) curl_h(E0^T P^T f) on the level-0 vertices of the Omega_0 box grown by 3
-// cells.  Deterministic gather: each face sums over all body points in a fixed order (no atomics), so a run
-// gives the same bits every time.  Face weights: P row (hat, 4 nodes) times the E0 stencil
-// (1/6, 2/3, 1/6) x (1/2, 1/2).  Body-point data is staged in shared memory in chunks.
+// O5 source: src = (ds/h^2) curl_h(E0^T P^T f) on the level-0 vertices near the body.  Deterministic
+// gather: every vertex sums over all body points with a fixed order and reduction tree (no atomics), so a
+// run gives the same bits every time.  Face weights: P row (hat, 4 nodes) times the E0 stencil
+// (1/6, 2/3, 1/6) x (1/2, 1/2).
 __device__ __forceinline__ double wx3(int d) { return d == 0 ? 2.0 / 3.0 : ((d == 1 || d == -1) ? 1.0 / 6.0 : 0.0); }
 
-constexpr int kSrcChunk = 256;
-
-struct SrcPt {
-  int ci, cj;        // absolute level-0 vertex of the cell's lower-left node
-  double w[4], fx, fy;
-};
-
-// comp 0: u-face (fi, fj+1/2); comp 1: v-face (fi+1/2, fj)
-__device__ __forceinline__ double face_force(int comp, int fi, int fj, const SrcPt* pts, int n) {
-  double acc = 0.0;
-  for (int p = 0; p < n; ++p) {
-    const SrcPt& q = pts[p];
-    if (fi < q.ci - 2 || fi > q.ci + 3 || fj < q.cj - 2 || fj > q.cj + 3) continue;
-    double wsum = 0.0;
+// Contribution of body point p to the four faces around vertex (i, j) that enter the curl.
+__device__ __forceinline__ void point_faces(int i, int j, int ci, int cj, const double* w, double fxp, double fyp,
+                                            double* fve, double* fvw, double* fun, double* fus) {
+  if (i < ci - 2 || i > ci + 4 || j < cj - 2 || j > cj + 4) return;
+  double ve = 0.0, vw = 0.0, un = 0.0, us = 0.0;
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int vi = q.ci + a, vj = q.cj + b;
-        double e;
-        if (comp == 0) {
-          const int dj = fj - vj;  // face y = fj+1/2 ; offsets -1/2 (dj=-1) or +1/2 (dj=0)
-          e = wx3(fi - vi) * ((dj == 0 || dj == -1) ? 0.5 : 0.0);
-        } else {
-          const int di = fi - vi;
-          e = ((di == 0 || di == -1) ? 0.5 : 0.0) * wx3(fj - vj);
-        }
-        wsum += q.w[2 * b + a] * e;
-      }
-    acc += wsum * (comp == 0 ? q.fx : q.fy);
-  }
-  return acc;
+    for (int a = 0; a < 2; ++a) {
+      const int vi = ci + a, vj = cj + b;
+      const double wp = w[2 * b + a];
+      // u-face (fi, fj+1/2): wx3(fi - vi) * 1/2 if fj - vj in {-1, 0}; v-face (fi+1/2, fj) likewise
+      const int dn = j - vj, ds_ = j - 1 - vj;
+      un += wp * wx3(i - vi) * ((dn == 0 || dn == -1) ? 0.5 : 0.0);
+      us += wp * wx3(i - vi) * ((ds_ == 0 || ds_ == -1) ? 0.5 : 0.0);
+      const int de = i - vi, dw = i - 1 - vi;
+      ve += wp * ((de == 0 || de == -1) ? 0.5 : 0.0) * wx3(j - vj);
+      vw += wp * ((dw == 0 || dw == -1) ? 0.5 : 0.0) * wx3(j - vj);
+    }
+  *fve += ve * fyp;
+  *fvw += vw * fyp;
+  *fun += un * fxp;
+  *fus += us * fxp;
 }
 
+// One warp per vertex: lanes take body points p = lane, lane + 32, ... and the four face sums are reduced
+// with a fixed shuffle tree.  Vertices outside the box written by the FSI kernel (ctrl[8..11]) are set to
+// zero.  Grid: x covers the Omega_0 box grown by 3 cells in tiles of 32 vertices, y its rows.
 template <typename T>
 __global__ void __launch_bounds__(256) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
-                                             int i_lo, int i_hi, int j_lo, int j_hi, double scale, double h) {
-  __shared__ SrcPt pts[kSrcChunk];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int i = i_lo - 3 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = j_lo - 3 + blockIdx.y * blockDim.y + threadIdx.y;
-  const bool active = !(i > i_hi + 3 || j > j_hi + 3 || i < 1 || j < 1 || i > nx - 1 || j > ny - 1);
-  double fve = 0.0, fvw = 0.0, fun = 0.0, fus = 0.0;
-  for (int p0 = 0; p0 < nb; p0 += kSrcChunk) {
-    const int n = min(kSrcChunk, nb - p0);
-    if (tid < n) {
-      const int p = p0 + tid;
-      const int n0 = pidx[4 * p];
-      SrcPt q;
-      q.ci = n0 % ni + i_lo;
-      q.cj = n0 / ni + j_lo;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) q.w[k] = pw[4 * p + k];
-      q.fx = f[p];
-      q.fy = f[nb + p];
-      pts[tid] = q;
-    }
-    __syncthreads();
-    if (active) {
-      // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
-      fve += face_force(1, i, j, pts, n);
-      fvw += face_force(1, i - 1, j, pts, n);
-      fun += face_force(0, i, j, pts, n);
-      fus += face_force(0, i, j - 1, pts, n);
-    }
-    __syncthreads();
+                                             int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
+                                             double scale, double h) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int j = j_lo - 3 + blockIdx.y;
+  const int i0 = i_lo - 3 + blockIdx.x * 32;
+  if (j < 1 || j > ny - 1 || j > j_hi + 3) return;
+  const int bi0 = box[0], bi1 = box[1], bj0 = box[2], bj1 = box[3];
+  const bool row_in = j >= bj0 && j <= bj1;
+  if (tid < 32) {
+    const int i = i0 + tid;
+    if (i >= 1 && i <= nx - 1 && i <= i_hi + 3 && !(row_in && i >= bi0 && i <= bi1))
+      src[(long)(j - 1) * ps + (i - 1)] = T(0);
   }
-  if (active) src[(long)(j - 1) * ps + (i - 1)] = T(scale * ((fve - fvw) - (fun - fus)) / h);
+  if (!row_in) return;
+  for (int v = wid; v < 32; v += blockDim.x >> 5) {
+    const int i = i0 + v;
+    if (i < 1 || i > nx - 1 || i > i_hi + 3 || i < bi0 || i > bi1) continue;  // warp-uniform
+    double fve = 0.0, fvw = 0.0, fun = 0.0, fus = 0.0;
+    for (int p = lane; p < nb; p += 32) {
+      const int n0 = pidx[4 * p];
+      const double w[4] = {pw[4 * p], pw[4 * p + 1], pw[4 * p + 2], pw[4 * p + 3]};
+      point_faces(i, j, n0 % ni + i_lo, n0 / ni + j_lo, w, f[p], f[nb + p], &fve, &fvw, &fun, &fus);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fve += __shfl_xor_sync(0xffffffffu, fve, o);
+      fvw += __shfl_xor_sync(0xffffffffu, fvw, o);
+      fun += __shfl_xor_sync(0xffffffffu, fun, o);
+      fus += __shfl_xor_sync(0xffffffffu, fus, o);
+    }
+    // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
+    if (lane == 0) src[(long)(j - 1) * ps + (i - 1)] = T(scale * ((fve - fvw) - (fun - fus)) / h);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -341,11 +336,11 @@ template <typename T>
 fsi_status corrector_t(fsi_ctx* c) {
   dim3 b(32, 8);
   const int wi = c->ni + 6, wj = c->nj + 6;
-  dim3 gr((wi + 31) / 32, (wj + 7) / 8);
+  dim3 gr((wi + 31) / 32, wj);
   const double scale = c->ds / (c->g.h * c->g.h);
   prof_mark(c, KC_SRC);
-  k_src<T><<<gr, b, 0, c->stream>>>((T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
-                                    c->i_lo, c->i_hi, c->j_lo, c->j_hi, scale, c->g.h);
+  k_src<T><<<gr, 256, 0, c->stream>>>((T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
+                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, scale, c->g.h);
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());

@@ -4,9 +4,10 @@
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
 //   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
 //   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = Kinv r with a float inverse Kinv,
-//      f += d, r = rhs - K f in double, until |d| <= 1e-12 |f|                            [all CTAs]
+//      f += d, r = rhs - K f in double, until |d| <= 1e-10 |f|                            [all CTAs]
 //      Kinv (from a blocked float Cholesky and triangular inverse of K, CTA 0 + all CTAs) is kept
-//      across iterations and steps and rebuilt only when the refinement needs more than 4 solves.
+//      across iterations and steps and rebuilt only when a solve reduces the correction by less than
+//      a factor 50 (the inverse has gone stale as the body moved).
 //   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta| (every CTA computes the same
 //      value in the same order, so all CTAs take the same branch without another barrier)
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
@@ -19,9 +20,9 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kMaxSolves = 5;     // refinement solves per attempt
-constexpr int kRefactorAfter = 4;  // more solves than this -> rebuild Kinv for the next iteration
-constexpr double kRefineTol = 1e-12;
+constexpr int kMaxSolves = 8;         // refinement solves per attempt
+constexpr double kStaleRatio = 0.02;  // |d_s| / |d_{s-1}| above this -> rebuild Kinv for the next iteration
+constexpr double kRefineTol = 1e-10;  // stop at |d| <= 1e-10 |f|; the next correction would be ~ratio times that
 constexpr int BS = 32;  // Cholesky / inverse block (one warp)
 constexpr int kMaxBodies = 256;
 constexpr unsigned FULL = 0xffffffffu;
@@ -48,7 +49,8 @@ struct FsiArgs {
   float* Kinv;   // [nf][nf]
   float* W;      // [nf][nf] inverse Cholesky factor (lower)
   double* part;  // [2 * gridDim] per-CTA maxima
-  int* ctrl;     // [0] unused, [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves
+  int* ctrl;     // [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves of the last
+                 // step, [6] Kinv rebuilds so far, [8..11] vertex box touched by the corrector source
   int* status;
   double* hist;
   int hist_cap;
@@ -394,9 +396,11 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         }
         grid.sync();
         kinv_valid = 1;
+        if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
       }
       bool done = false;
       int s = 0;
+      double gd_prev = 0.0, worst_ratio = 0.0;
       for (; s < kMaxSolves; ++s) {
         double dmax = 0.0, xmax = 0.0;
         for (long i = wg; i < nf; i += nwg) {  // d = Kinv r, f += d
@@ -430,6 +434,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           done = true;
           break;
         }
+        if (s > 0 && gd_prev > 0.0) worst_ratio = fmax(worst_ratio, gd / gd_prev);
+        gd_prev = gd;
         if (gd <= kRefineTol * gx) {
           done = true;
           break;
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         grid.sync();
       }
       solves_total += s + 1;
-      if (s + 1 > kRefactorAfter) kinv_valid = 0;
+      if (worst_ratio > kStaleRatio) kinv_valid = 0;
       if (done) break;
       kinv_valid = 0;  // not converged with this inverse: rebuild it and solve again
       if (attempt == 1 && blockIdx.x == 0 && tid == 0) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
@@ -529,6 +535,27 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.ctrl[2] += 1;
       a.ctrl[4] = kinv_valid;
       a.ctrl[5] = solves_total;
+    }
+    // vertex box that the corrector source (E0^T P^T f, then curl) can touch: cells of the final P, grown
+    // by the E0 support (1.5 cells), the hat support (1 cell) and the curl stencil (1 cell)
+    int imin = 1 << 30, imax = -1, jmin = 1 << 30, jmax = -1;
+    for (int p = tid; p < nb; p += nthr) {
+      const int n0 = __ldcg(&a.pidx[4 * p]);
+      const int ci = n0 % a.ni, cj = n0 / a.ni;
+      imin = min(imin, ci);
+      imax = max(imax, ci);
+      jmin = min(jmin, cj);
+      jmax = max(jmax, cj);
+    }
+    imin = -(int)block_max(-(double)imin, red);
+    imax = (int)block_max((double)imax, red);
+    jmin = -(int)block_max(-(double)jmin, red);
+    jmax = (int)block_max((double)jmax, red);
+    if (tid == 0) {
+      a.ctrl[8] = a.i_lo + imin - 3;
+      a.ctrl[9] = a.i_lo + imax + 4;
+      a.ctrl[10] = a.j_lo + jmin - 3;
+      a.ctrl[11] = a.j_lo + jmax + 4;
     }
   }
 }
