@@ -325,6 +325,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
         !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
@@ -338,7 +339,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf);
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
-    c->fsi_grid = nsm / 2 > 0 ? nsm / 2 : 1;  // fewer CTAs -> cheaper grid-wide barriers
+    c->fsi_grid = nsm < 64 ? nsm : 64;  // enough CTAs for the 32x32 GEMM tiles; fewer -> cheaper barriers
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;

@@ -3,11 +3,12 @@
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
 //   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
-//   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = Kinv r with a float inverse Kinv,
+//   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = X r with a float inverse X,
 //      f += d, r = rhs - K f in double, until |d| <= 1e-10 |f|                            [all CTAs]
-//      Kinv (from a blocked float Cholesky and triangular inverse of K, CTA 0 + all CTAs) is kept
-//      across iterations and steps and rebuilt only when a solve reduces the correction by less than
-//      a factor 50 (the inverse has gone stale as the body moved).
+//      X is carried across iterations and steps; each iteration first refreshes it for the new K with
+//      two Newton-Schulz steps X <- 2X - X K X (tiled GEMMs over all CTAs; the error I - K X is squared
+//      each time).  It is rebuilt from scratch (blocked float Cholesky and triangular inverse in CTA 0,
+//      then W^T W over all CTAs) at the first step, when refinement stalls, or when it diverges.
 //   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta| (every CTA computes the same
 //      value in the same order, so all CTAs take the same branch without another barrier)
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
@@ -23,7 +24,8 @@ namespace {
 constexpr int kMaxSolves = 8;         // refinement solves per attempt
 constexpr double kStaleRatio = 0.02;  // |d_s| / |d_{s-1}| above this -> rebuild Kinv for the next iteration
 constexpr double kRefineTol = 1e-10;  // stop at |d| <= 1e-10 |f|; the next correction would be ~ratio times that
-constexpr int BS = 32;  // Cholesky / inverse block (one warp)
+constexpr int kNsSteps = 2;  // Newton-Schulz refreshes of the inverse per FSI iteration
+constexpr int BS = 32;       // Cholesky / inverse / GEMM tile (one warp wide)
 constexpr int kMaxBodies = 256;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -46,8 +48,9 @@ struct FsiArgs {
   double* rhs;   // [nf] right-hand side, then [nf] residual
   double* K;     // [nf][nf] double, both triangles
   double* f;     // [nf]
-  float* Kinv;   // [nf][nf]
-  float* W;      // [nf][nf] inverse Cholesky factor (lower)
+  float* Xa;     // [nf][nf] float inverse of K, ping-pong buffer a
+  float* Xb;     // [nf][nf] ping-pong buffer b (ctrl[7] says which one is current)
+  float* S;      // [nf][nf] scratch: K X, or the inverse Cholesky factor during a rebuild
   double* part;  // [2 * gridDim] per-CTA maxima
   int* ctrl;     // [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves of the last
                  // step, [6] Kinv rebuilds so far, [8..11] vertex box touched by the corrector source
@@ -98,6 +101,47 @@ __device__ double block_max(double x, double* red) {
   const double r = red[0];
   __syncthreads();
   return r;
+}
+
+// C = A B (Xc == nullptr) or C = 2 Xc - A B for n x n row-major matrices, A given as double (Ad) or float
+// (Af), B float.  32 x 32 output tiles are spread over the CTAs of the grid; each thread computes four
+// entries of its tile.  sm: 2 * 32 * 33 floats of shared memory.  All inputs may have been written earlier
+// in the same launch, so they are read with __ldcg.
+__device__ void gemm_tiles(int n, const double* __restrict__ Ad, const float* __restrict__ Af,
+                           const float* __restrict__ B, const float* __restrict__ Xc, float* __restrict__ C,
+                           float* sm) {
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int nt = (n + BS - 1) / BS;
+  float* As = sm;
+  float* Bs = sm + BS * (BS + 1);
+  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const int ti = t / nt, tj = t - ti * nt;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int kb = 0; kb < n; kb += BS) {
+      for (int e = tid; e < BS * BS; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31;
+        const int gi = ti * BS + r, gk = kb + c;
+        float av = 0.0f;
+        if (gi < n && gk < n) av = Ad ? (float)__ldcg(&Ad[(long)gi * n + gk]) : __ldcg(&Af[(long)gi * n + gk]);
+        As[r * (BS + 1) + c] = av;
+        const int bk = kb + r, gj = tj * BS + c;
+        Bs[r * (BS + 1) + c] = (bk < n && gj < n) ? __ldcg(&B[(long)bk * n + gj]) : 0.0f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < BS; ++k) {
+        const float b = Bs[k * (BS + 1) + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += As[(ty + 8 * q) * (BS + 1) + k] * b;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = ti * BS + ty + 8 * q, gj = tj * BS + lane;
+      if (gi < n && gj < n) C[(long)gi * n + gj] = Xc ? 2.0f * __ldcg(&Xc[(long)gi * n + gj]) - acc[q] : acc[q];
+    }
+  }
 }
 
 // Blocked right-looking Cholesky of the lower triangle of L (row stride ld) in shared memory.
@@ -274,6 +318,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     }
   }
   int kinv_valid = *(volatile int*)&a.ctrl[4];
+  int cur = *(volatile int*)&a.ctrl[7];
+  float* gsm = reinterpret_cast<float*>(dyn_smem);  // GEMM tiles (all CTAs) / Cholesky factor (CTA 0)
   __syncthreads();
 
   bool converged = false;
@@ -370,27 +416,38 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       }
     }
     grid.sync();
-    // ---- C: iterative refinement with the float inverse (rebuilt when missing or slow)
+    // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
     for (int attempt = 0; attempt < 2; ++attempt) {
-      if (!kinv_valid) {
+      if (kinv_valid) {
+        for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - X (K X): the error I - K X is squared
+          const float* X = cur ? a.Xb : a.Xa;
+          float* Xn = cur ? a.Xa : a.Xb;
+          gemm_tiles(nf, a.K, nullptr, X, nullptr, a.S, gsm);  // S = K X
+          grid.sync();
+          gemm_tiles(nf, nullptr, X, a.S, X, Xn, gsm);         // Xn = 2 X - X S
+          grid.sync();
+          cur ^= 1;
+        }
+      } else {
         float* Lf = reinterpret_cast<float*>(dyn_smem);
         if (blockIdx.x == 0) {
           for (int i = tid >> 5; i < nf; i += nthr >> 5)
             for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
           __syncthreads();
-          if (!chol_blocked(Lf, nf, ld, &sh_bad) && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
-          tri_inverse(Lf, nf, ld, a.W);
+          chol_blocked(Lf, nf, ld, &sh_bad);
+          tri_inverse(Lf, nf, ld, a.S);
         }
         grid.sync();
-        for (long i = wg; i < nf; i += nwg) {  // Kinv = W^T W, warp per row i, lanes over k <= i
+        float* Xc = cur ? a.Xb : a.Xa;
+        for (long i = wg; i < nf; i += nwg) {  // X = W^T W, warp per row i, lanes over k <= i
           for (int k0 = 0; k0 <= i; k0 += 32) {
             const int k = k0 + lane;
             float acc = 0.0f;
             if (k <= i)
-              for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.W[(long)m * nf + i]) * __ldcg(&a.W[(long)m * nf + k]);
+              for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.S[(long)m * nf + i]) * __ldcg(&a.S[(long)m * nf + k]);
             if (k <= i) {
-              a.Kinv[i * nf + k] = acc;
-              a.Kinv[(long)k * nf + i] = acc;
+              Xc[i * nf + k] = acc;
+              Xc[(long)k * nf + i] = acc;
             }
           }
         }
@@ -398,7 +455,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         kinv_valid = 1;
         if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
       }
-      bool done = false;
+      const float* Xinv = cur ? a.Xb : a.Xa;
+      bool done = false, bad = false;
       int s = 0;
       double gd_prev = 0.0, worst_ratio = 0.0;
       for (; s < kMaxSolves; ++s) {
@@ -406,7 +464,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         for (long i = wg; i < nf; i += nwg) {  // d = Kinv r, f += d
           const double* r = s == 0 ? a.rhs : res;
           float acc = 0.0f;
-          for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.Kinv[i * nf + k]) * (float)__ldcg(&r[k]);
+          for (int k = lane; k < nf; k += 32) acc += __ldcg(&Xinv[i * nf + k]) * (float)__ldcg(&r[k]);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
           if (lane == 0) {
@@ -429,9 +487,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           gd = fmax(gd, __ldcg(&a.part[2 * c]));
           gx = fmax(gx, __ldcg(&a.part[2 * c + 1]));
         }
-        if (!isfinite(gd)) {
-          if (tid == 0 && blockIdx.x == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
-          done = true;
+        if (!isfinite(gd)) {  // a diverged inverse: rebuild and retry
+          bad = true;
           break;
         }
         if (s > 0 && gd_prev > 0.0) worst_ratio = fmax(worst_ratio, gd / gd_prev);
@@ -451,10 +508,13 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         grid.sync();
       }
       solves_total += s + 1;
-      if (worst_ratio > kStaleRatio) kinv_valid = 0;
-      if (done) break;
+      if (done) {
+        if (worst_ratio > kStaleRatio) kinv_valid = 0;
+        break;
+      }
       kinv_valid = 0;  // not converged with this inverse: rebuild it and solve again
-      if (attempt == 1 && blockIdx.x == 0 && tid == 0) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
+      if (attempt == 1 && blockIdx.x == 0 && tid == 0)
+        dev_set_status(a.status, bad ? FSI_ERR_NONFINITE : FSI_ERR_NOT_CONVERGED);
     }
     // ---- D: dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta| (same in every CTA)
     double dmax = 0.0;
@@ -534,6 +594,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.ctrl[1] = it + 1;
       a.ctrl[2] += 1;
       a.ctrl[4] = kinv_valid;
+      a.ctrl[7] = cur;
       a.ctrl[5] = solves_total;
     }
     // vertex box that the corrector source (E0^T P^T f, then curl) can touch: cells of the final P, grown
@@ -564,7 +625,9 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
 
 size_t fsi_smem_bytes(int nf) {
   const size_t ld = (size_t)(nf | 1);
-  return (((size_t)nf * ld * 4 + 15) / 16) * 16 + 64;
+  const size_t chol = (((size_t)nf * ld * 4 + 15) / 16) * 16;
+  const size_t gemm = (size_t)2 * BS * (BS + 1) * 4;
+  return (chol > gemm ? chol : gemm) + 64;
 }
 
 int fsi_kernel_max_ctas_per_sm(int nf) {
@@ -607,8 +670,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.rhs = c->d_rhs;
   a.K = c->d_K;
   a.f = c->d_f;
-  a.Kinv = c->d_Kinv;
-  a.W = c->d_W;
+  a.Xa = c->d_Kinv;
+  a.Xb = c->d_W;
+  a.S = c->d_S;
   a.part = c->d_part;
   a.ctrl = c->d_ctrl;
   a.status = c->d_status;

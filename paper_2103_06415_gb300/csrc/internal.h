@@ -73,7 +73,8 @@ struct fsi_ctx {
   double* d_K;     // [nf*nf]
   double* d_f;     // [nf]
   float* d_Kinv;   // [nf*nf] float inverse of K used for iterative refinement
-  float* d_W;      // [nf*nf] inverse Cholesky factor
+  float* d_W;      // [nf*nf] second float-inverse buffer (Newton-Schulz ping-pong)
+  float* d_S;      // [nf*nf] scratch for K X or the inverse Cholesky factor
   double* d_part;  // [2*fsi_grid] per-CTA maxima
   int* d_ctrl;     // [0] converged flag, [1] iteration count, [2] step index, [3..6] bbox
   int* d_status;
