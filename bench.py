@@ -194,6 +194,7 @@ def main():
     cells = cells_per_step(w)
     value = cells * args.steps * world / (total_ms * 1e-3)
     stats = ctx.stats()
+    phases = {k: v / max(stats["steps_done"], 1) for k, v in ctx.phase_times().items()}
     hist_mixed = ctx.history(0)
 
     # FP64 path on the same workload (same steps) and the force error of the mixed path against it
@@ -269,7 +270,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": stats["launches_per_step"] * args.steps,
                 "fsi_solver": {"iterations_last_step": stats["last_iters"], "solves_last_step": stats["last_solves"],
-                               "inverse_rebuilds": stats["inverse_rebuilds"], "steps_run": stats["steps_done"]},
+                               "inverse_rebuilds": stats["inverse_rebuilds"], "steps_run": stats["steps_done"],
+                               "phase_ms_per_step": phases},
                 "clocks": clocks, "roofline": roof, "e2e": e2e}
         line.update(extra)
         if base is not None:

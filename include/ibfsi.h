@@ -169,6 +169,12 @@ fsi_status fsi_get_interp(fsi_ctx* ctx, int64_t* idx, double* w, int cap_points)
 
 fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);
 
+/* Tracing: accumulated wall time (ms) of the phases of the FSI-iteration kernel since the context was
+ * created, measured on the device: 0 body points / P / right-hand side, 1 assembly of P B0 P^T, 2 refresh
+ * of the float inverse, 3 rebuild of the float inverse, 4 refinement solves, 5 double residuals,
+ * 6 dtheta and convergence, 7 outputs.  out[0..n-1] (n <= 8 meaningful; synchronising). */
+fsi_status fsi_get_phase_times(fsi_ctx* ctx, double* out, int n);
+
 /* Live timing of one kernel class: runs n_steps (1..1024) ordinary time steps without a graph, records a
  * CUDA event pair on the context stream around every launch of that class and returns the mean launch
  * duration in ms and the number of timed launches.  The steps advance the simulation like fsi_advance.

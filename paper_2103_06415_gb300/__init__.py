@@ -153,6 +153,15 @@ class Context:
                                            ctypes.byref(n)), "fsi_profile_kernel")
         return ms.value, n.value
 
+    PHASES = ("points_rhs", "assemble_PB0PT", "inverse_refresh", "inverse_rebuild", "refine_solves",
+              "residuals", "dtheta", "outputs")
+
+    def phase_times(self):
+        """Accumulated device wall time (ms) per phase of the FSI-iteration kernel."""
+        out = np.zeros(8)
+        check(self._lib.fsi_get_phase_times(self._h, _dp(out), 8), "fsi_get_phase_times")
+        return dict(zip(self.PHASES, out.tolist()))
+
     def stats(self):
         s = _lib.Stats()
         check(self._lib.fsi_get_stats(self._h, ctypes.byref(s)), "fsi_get_stats")

@@ -76,6 +76,7 @@ SIGNATURES = {
     "fsi_get_interp": (_INT, [_P, _I64, _D, _INT]),
     "fsi_get_stats": (_INT, [_P, ctypes.POINTER(Stats)]),
     "fsi_profile_kernel": (_INT, [_P, _INT, _INT, _D, ctypes.POINTER(_INT)]),
+    "fsi_get_phase_times": (_INT, [_P, _D, _INT]),
     "fsi_destroy": (None, [_P]),
     "fsi_op_level_solve": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D]),
     "fsi_op_fma_rate": (_INT, [_INT, _D]),

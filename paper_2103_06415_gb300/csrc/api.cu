@@ -326,6 +326,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_phase = (unsigned long long*)ctx_alloc(c, 8 * sizeof(unsigned long long))) ||
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
@@ -444,6 +445,17 @@ extern "C" fsi_status fsi_profile_kernel(fsi_ctx* c, int kernel_class, int n_ste
   *launches = pairs;
   *avg_ms = pairs ? sum / pairs : 0.0;
   return st;
+}
+
+extern "C" fsi_status fsi_get_phase_times(fsi_ctx* c, double* ms, int n) {
+  if (!c || !ms || n < 1) return FSI_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k) ms[k] = 0.0;
+  if (!c->d_phase) return FSI_OK;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  unsigned long long ns[8];
+  FSI_CUDA_TRY(cudaMemcpy(ns, c->d_phase, sizeof(ns), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n && k < 8; ++k) ms[k] = (double)ns[k] * 1e-6;
+  return FSI_OK;
 }
 
 extern "C" fsi_status fsi_sync(fsi_ctx* c) {

@@ -52,6 +52,7 @@ struct FsiArgs {
   float* Xb;     // [nf][nf] ping-pong buffer b (ctrl[7] says which one is current)
   float* S;      // [nf][nf] scratch: K X, or the inverse Cholesky factor during a rebuild
   double* part;  // [2 * gridDim] per-CTA maxima
+  unsigned long long* phase_ns;  // [8] accumulated wall time per kernel phase
   int* ctrl;     // [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves of the last
                  // step, [6] Kinv rebuilds so far, [8..11] vertex box touched by the corrector source
   int* status;
@@ -75,6 +76,29 @@ __device__ void e0cs(const FsiArgs& a, int I, int J, double* u, double* v) {
   *u = su / (2.0 * a.h) + a.U;
   *v = -sv / (2.0 * a.h) + a.V;
 }
+
+// Wall time per phase of the kernel, accumulated in nanoseconds (%globaltimer) by thread 0 of CTA 0 at the
+// phase boundaries (after the grid barrier that ends the phase): 0 A, 1 B, 2 inverse refresh, 3 inverse
+// rebuild, 4 refinement solves, 5 double residuals, 6 dtheta/convergence, 7 outputs.
+struct PhaseClock {
+  unsigned long long* acc;
+  bool on;
+  unsigned long long* last;
+  __device__ PhaseClock(unsigned long long* a, bool o, unsigned long long* l) : acc(a), on(o && a), last(l) {
+    if (on) *last = now();
+  }
+  __device__ static unsigned long long now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+  }
+  __device__ void mark(int phase) {
+    if (!on) return;
+    const unsigned long long t = now();
+    acc[phase] += t - *last;
+    *last = t;
+  }
+};
 
 // Deterministic block reductions (fixed tree); all threads must call; result valid in every thread.
 __device__ double block_sum(double x, double* red) {
@@ -320,6 +344,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
   int kinv_valid = *(volatile int*)&a.ctrl[4];
   int cur = *(volatile int*)&a.ctrl[7];
   float* gsm = reinterpret_cast<float*>(dyn_smem);  // GEMM tiles (all CTAs) / Cholesky factor (CTA 0)
+  unsigned long long t_last = 0;
+  PhaseClock clk(a.phase_ns, blockIdx.x == 0 && tid == 0, &t_last);
   __syncthreads();
 
   bool converged = false;
@@ -376,6 +402,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.rhs[nb + p] = uby - ucy + svy * coef;
     }
     grid.sync();
+    clk.mark(0);
     // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles written)
     {
       const double kscale = a.ds / (a.h * a.h);
@@ -416,6 +443,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       }
     }
     grid.sync();
+    clk.mark(1);
     // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
     for (int attempt = 0; attempt < 2; ++attempt) {
       if (kinv_valid) {
@@ -428,6 +456,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           grid.sync();
           cur ^= 1;
         }
+        clk.mark(2);
       } else {
         float* Lf = reinterpret_cast<float*>(dyn_smem);
         if (blockIdx.x == 0) {
@@ -454,6 +483,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         grid.sync();
         kinv_valid = 1;
         if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
+        clk.mark(3);
       }
       const float* Xinv = cur ? a.Xb : a.Xa;
       bool done = false, bad = false;
@@ -482,6 +512,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           a.part[2 * blockIdx.x + 1] = xmax;
         }
         grid.sync();
+        clk.mark(4);
         double gd = 0.0, gx = 0.0;
         for (int c = 0; c < (int)gridDim.x; ++c) {
           gd = fmax(gd, __ldcg(&a.part[2 * c]));
@@ -506,6 +537,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           if (lane == 0) res[i] = __ldcg(&a.rhs[i]) - acc;
         }
         grid.sync();
+        clk.mark(5);
       }
       solves_total += s + 1;
       if (done) {
@@ -544,6 +576,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     }
     if (!finite && blockIdx.x == 0 && tid == 0) dev_set_status(a.status, FSI_ERR_NONFINITE);
     converged = (dmax <= a.tol) || !finite;
+    clk.mark(6);
     if (converged) break;
     // No barrier here: after the last barrier of phase C only f is read (phase D), and the next write of
     // f comes after the phase-A and phase-B barriers of the next iteration.
@@ -618,6 +651,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.ctrl[10] = a.j_lo + jmin - 3;
       a.ctrl[11] = a.j_lo + jmax + 4;
     }
+    clk.mark(7);
   }
 }
 
@@ -675,6 +709,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.S = c->d_S;
   a.part = c->d_part;
   a.ctrl = c->d_ctrl;
+  a.phase_ns = c->d_phase;
   a.status = c->d_status;
   a.hist = c->d_hist;
   a.hist_cap = c->hist_cap;

@@ -76,7 +76,8 @@ struct fsi_ctx {
   float* d_W;      // [nf*nf] second float-inverse buffer (Newton-Schulz ping-pong)
   float* d_S;      // [nf*nf] scratch for K X or the inverse Cholesky factor
   double* d_part;  // [2*fsi_grid] per-CTA maxima
-  int* d_ctrl;     // [0] converged flag, [1] iteration count, [2] step index, [3..6] bbox
+  int* d_ctrl;     // FSI control words (see fsi.cu)
+  unsigned long long* d_phase;  // [8] accumulated FSI kernel phase times (ns)
   int* d_status;
   double* d_hist;  // [cap][n_bodies][6]
   int hist_cap;
