@@ -129,37 +129,43 @@ __device__ double block_max(double x, double* red) {
 
 // C = A B (Xc == nullptr) or C = 2 Xc - A B for n x n row-major matrices, A given as double (Ad) or float
 // (Af), B float.  32 x 32 output tiles are spread over the CTAs of the grid; each thread computes four
-// entries of its tile.  sm: 2 * 32 * 33 floats of shared memory.  All inputs may have been written earlier
-// in the same launch, so they are read with __ldcg.
+// entries of its tile.  sm: 32 * (n + 1) + 33 * n floats of shared memory.  All inputs may have been
+// written earlier in the same launch, so they are read with __ldcg.
 __device__ void gemm_tiles(int n, const double* __restrict__ Ad, const float* __restrict__ Af,
                            const float* __restrict__ B, const float* __restrict__ Xc, float* __restrict__ C,
                            float* sm) {
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   const int nt = (n + BS - 1) / BS;
   float* As = sm;
-  float* Bs = sm + BS * (BS + 1);
+  const int lda = n + 1;
+  float* Bs = sm + BS * lda;
   for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
     const int ti = t / nt, tj = t - ti * nt;
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int kb = 0; kb < n; kb += BS) {
-      for (int e = tid; e < BS * BS; e += blockDim.x) {
-        const int r = e >> 5, c = e & 31;
-        const int gi = ti * BS + r, gk = kb + c;
-        float av = 0.0f;
-        if (gi < n && gk < n) av = Ad ? (float)__ldcg(&Ad[(long)gi * n + gk]) : __ldcg(&Af[(long)gi * n + gk]);
-        As[r * (BS + 1) + c] = av;
-        const int bk = kb + r, gj = tj * BS + c;
-        Bs[r * (BS + 1) + c] = (bk < n && gj < n) ? __ldcg(&B[(long)bk * n + gj]) : 0.0f;
-      }
-      __syncthreads();
+    // whole 32 x n row panel of A and n x 32 column panel of B, loads issued back to back (unrolled) so
+    // that many L2 round trips overlap
 #pragma unroll 8
-      for (int k = 0; k < BS; ++k) {
-        const float b = Bs[k * (BS + 1) + lane];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += As[(ty + 8 * q) * (BS + 1) + k] * b;
-      }
-      __syncthreads();
+    for (int e = tid; e < BS * n; e += blockDim.x) {
+      const int r = e / n, k = e - r * n;
+      const int gi = ti * BS + r;
+      float av = 0.0f;
+      if (gi < n) av = Ad ? (float)__ldcg(&Ad[(long)gi * n + k]) : __ldcg(&Af[(long)gi * n + k]);
+      As[r * lda + k] = av;
     }
+#pragma unroll 8
+    for (int e = tid; e < BS * n; e += blockDim.x) {
+      const int k = e >> 5, c = e & 31;
+      const int gj = tj * BS + c;
+      Bs[k * (BS + 1) + c] = gj < n ? __ldcg(&B[(long)k * n + gj]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < n; ++k) {
+      const float b = Bs[k * (BS + 1) + lane];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += As[(ty + 8 * q) * lda + k] * b;
+    }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gi = ti * BS + ty + 8 * q, gj = tj * BS + lane;
@@ -494,6 +500,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         for (long i = wg; i < nf; i += nwg) {  // d = Kinv r, f += d
           const double* r = s == 0 ? a.rhs : res;
           float acc = 0.0f;
+#pragma unroll 8
           for (int k = lane; k < nf; k += 32) acc += __ldcg(&Xinv[i * nf + k]) * (float)__ldcg(&r[k]);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -513,11 +520,9 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         }
         grid.sync();
         clk.mark(4);
-        double gd = 0.0, gx = 0.0;
-        for (int c = 0; c < (int)gridDim.x; ++c) {
-          gd = fmax(gd, __ldcg(&a.part[2 * c]));
-          gx = fmax(gx, __ldcg(&a.part[2 * c + 1]));
-        }
+        // every CTA reduces the per-CTA maxima the same way (one load per thread, fixed tree)
+        const double gd = block_max(tid < (int)gridDim.x ? __ldcg(&a.part[2 * tid]) : 0.0, red);
+        const double gx = block_max(tid < (int)gridDim.x ? __ldcg(&a.part[2 * tid + 1]) : 0.0, red);
         if (!isfinite(gd)) {  // a diverged inverse: rebuild and retry
           bad = true;
           break;
@@ -531,6 +536,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         if (s == kMaxSolves - 1) break;
         for (long i = wg; i < nf; i += nwg) {  // r = rhs - K f in double
           double acc = 0.0;
+#pragma unroll 8
           for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.K[i * nf + k]) * __ldcg(&a.f[k]);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -660,7 +666,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
 size_t fsi_smem_bytes(int nf) {
   const size_t ld = (size_t)(nf | 1);
   const size_t chol = (((size_t)nf * ld * 4 + 15) / 16) * 16;
-  const size_t gemm = (size_t)2 * BS * (BS + 1) * 4;
+  const size_t gemm = ((size_t)BS * (nf + 1) + (size_t)(BS + 1) * nf) * 4;
   return (chol > gemm ? chol : gemm) + 64;
 }
 
