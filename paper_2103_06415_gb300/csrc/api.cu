@@ -7,7 +7,7 @@
 #include <vector>
 #include "internal.h"
 
-int fsi_cluster_size(int nf, cudaStream_t stream);
+int fsi_kernel_max_ctas_per_sm(int nf);
 size_t fsi_smem_bytes(int nf);
 
 static thread_local char g_errmsg[512] = "";
@@ -335,8 +335,12 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_point_body, pb.data(), pb.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rpts, c->rigid_pts.data(), c->rigid_pts.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rur, c->rigid_ur.data(), c->rigid_ur.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    c->fsi_grid = fsi_cluster_size(c->nf, c->stream);  // one cluster of 16 (or 8) CTAs
-    if (c->fsi_grid < 1) return FSI_ERR_UNSUPPORTED;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf);
+    if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
+    c->fsi_grid = nsm < 64 ? nsm : 64;  // enough CTAs for the 32x32 GEMM tiles; fewer -> cheaper barriers
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;

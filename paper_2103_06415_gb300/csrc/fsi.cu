@@ -1,6 +1,5 @@
 // FSI iteration of one time step (Algorithm 2; Eqs. stress2 and dtheta2) in double precision, as one
-// kernel whose grid is a single thread-block cluster (16 CTAs where the device allows it, else 8), so every
-// phase boundary is a hardware cluster barrier instead of a grid-wide software barrier:
+// cooperative kernel over a fixed set of CTAs:
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
 //   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
@@ -316,7 +315,7 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 }
 
 __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
-  cg::cluster_group cl = cg::this_cluster();  // the whole grid is one cluster
+  cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
   __shared__ double b_th[kMaxBodies], b_ph[kMaxBodies], b_rphi[kMaxBodies], b_rth[kMaxBodies], b_jac[kMaxBodies];
@@ -408,37 +407,32 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.rhs[p] = ubx - ucx + svx * coef;
       a.rhs[nb + p] = uby - ucy + svy * coef;
     }
-    cl.sync();
+    grid.sync();
     clk.mark(0);
     // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles written)
     {
-      // P of this iteration staged in shared memory (reused by every entry of the CTA)
-      int* s_idx = reinterpret_cast<int*>(dyn_smem);
-      double* s_w = reinterpret_cast<double*>(dyn_smem + (((size_t)nb * 16 + 15) / 16) * 16);
-      for (int e = tid; e < 4 * nb; e += nthr) {
-        s_idx[e] = __ldcg(&a.pidx[e]);
-        s_w[e] = __ldcg(&a.pw[e]);
-      }
-      __syncthreads();
       const double kscale = a.ds / (a.h * a.h);
       const long n2 = 2L * a.n_sd;
-      const long ntri = (long)nf * (nf + 1) / 2;
-#pragma unroll 2
-      for (long e = gtid; e < ntri; e += gsize) {  // lower triangle, row r, column cidx <= r
-        int r = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-        if ((long)r * (r + 1) / 2 > e) --r;
-        if ((long)(r + 1) * (r + 2) / 2 <= e) ++r;
-        const int cidx = (int)(e - (long)r * (r + 1) / 2);
+      for (long e = gtid; e < (long)nf * nf; e += gsize) {
+        const int r = (int)(e / nf), cidx = (int)(e % nf);
+        if (cidx > r) continue;
         const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
         double acc = 0.0;
+        int ib[4];
+        double wb[4];
 #pragma unroll
+        for (int be = 0; be < 4; ++be) {
+          ib[be] = __ldcg(&a.pidx[4 * pb + be]);
+          wb[be] = __ldcg(&a.pw[4 * pb + be]);
+        }
         for (int al = 0; al < 4; ++al) {
-          const long row = (long)ca * a.n_sd + s_idx[4 * pa + al];
+          const long row = (long)ca * a.n_sd + __ldcg(&a.pidx[4 * pa + al]);
+          const double wa = __ldcg(&a.pw[4 * pa + al]);
           const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
           double t = 0.0;
 #pragma unroll
-          for (int be = 0; be < 4; ++be) t += s_w[4 * pb + be] * brow[s_idx[4 * pb + be]];
-          acc += s_w[4 * pa + al] * t;
+          for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
+          acc += wa * t;
         }
         double kv = kscale * acc;
         const int ba = a.point_body[pa], bbd = a.point_body[pb];
@@ -454,7 +448,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         a.K[(long)cidx * nf + r] = kv;
       }
     }
-    cl.sync();
+    grid.sync();
     clk.mark(1);
     // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -463,9 +457,9 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           const float* X = cur ? a.Xb : a.Xa;
           float* Xn = cur ? a.Xa : a.Xb;
           gemm_tiles(nf, a.K, nullptr, X, nullptr, a.S, gsm);  // S = K X
-          cl.sync();
+          grid.sync();
           gemm_tiles(nf, nullptr, X, a.S, X, Xn, gsm);         // Xn = 2 X - X S
-          cl.sync();
+          grid.sync();
           cur ^= 1;
         }
         clk.mark(2);
@@ -478,7 +472,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           chol_blocked(Lf, nf, ld, &sh_bad);
           tri_inverse(Lf, nf, ld, a.S);
         }
-        cl.sync();
+        grid.sync();
         float* Xc = cur ? a.Xb : a.Xa;
         for (long i = wg; i < nf; i += nwg) {  // X = W^T W, warp per row i, lanes over k <= i
           for (int k0 = 0; k0 <= i; k0 += 32) {
@@ -492,7 +486,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
             }
           }
         }
-        cl.sync();
+        grid.sync();
         kinv_valid = 1;
         if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
         clk.mark(3);
@@ -524,7 +518,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           a.part[2 * blockIdx.x] = dmax;
           a.part[2 * blockIdx.x + 1] = xmax;
         }
-        cl.sync();
+        grid.sync();
         clk.mark(4);
         // every CTA reduces the per-CTA maxima the same way (one load per thread, fixed tree)
         const double gd = block_max(tid < (int)gridDim.x ? __ldcg(&a.part[2 * tid]) : 0.0, red);
@@ -548,7 +542,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
           if (lane == 0) res[i] = __ldcg(&a.rhs[i]) - acc;
         }
-        cl.sync();
+        grid.sync();
         clk.mark(5);
       }
       solves_total += s + 1;
@@ -676,28 +670,11 @@ size_t fsi_smem_bytes(int nf) {
   return (chol > gemm ? chol : gemm) + 64;
 }
 
-// Largest cluster size (16 or 8 CTAs) that can be co-scheduled for k_fsi with this shared memory; 0 if none.
-int fsi_cluster_size(int nf, cudaStream_t stream) {
+int fsi_kernel_max_ctas_per_sm(int nf) {
   cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  for (int cs = 16; cs >= 8; cs /= 2) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = fsi_smem_bytes(nf);
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_fsi, &cfg) == cudaSuccess && n >= 1) return cs;
-    cudaGetLastError();
-  }
-  return 0;
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, fsi_smem_bytes(nf));
+  return n;
 }
 
 fsi_status launch_fsi(fsi_ctx* c) {
@@ -748,10 +725,8 @@ fsi_status launch_fsi(fsi_ctx* c) {
   cfg.dynamicSmemBytes = fsi_smem_bytes(c->nf);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;  // the whole grid is one thread-block cluster
-  attr[0].val.clusterDim.x = c->fsi_grid;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   prof_mark(c, KC_FSI);
