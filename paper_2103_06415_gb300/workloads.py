@@ -37,6 +37,15 @@ def flag_512x256_3lvl():
         ds=0.01)
 
 
+def flag_512x256_3lvl_reduced_omega0():
+    """flag_512x256_3lvl with Omega_0 cut to [-0.2,1.2]x[-0.25,0.35] (141 x 61 points, B0 2.4 GB); same
+    kernels and small-system size, for profiler captures that must hold only a few GB."""
+    w = flag_512x256_3lvl()
+    w["name"] = "flag_512x256_3lvl_reduced_omega0"
+    w["sd_box"] = (-0.2, 1.2, -0.25, 0.35)
+    return w
+
+
 def small_plate(nx=64, ny=32, n_levels=1):
     """A small torsional-plate case the oracle runs in seconds (several FFT tiles, ragged Omega_0 box)."""
     h = 1.0 / 16
