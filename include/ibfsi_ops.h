@@ -20,6 +20,23 @@ extern "C" {
 fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt, const double* rhs,
                               double* w_out, double* s_out);
 
+/* Allocation-free variant of fsi_op_level_solve for callers that cannot call cudaMalloc (for example code
+ * running under a framework whose allocator owns all device memory, or a callback that must not allocate).
+ * The paper has no counterpart: this is a service of this library.
+ * Same solve (zero boundary values), but inputs and outputs are DEVICE pointers supplied by the caller and
+ * the work is enqueued on `stream` (cudaStream_t; NULL = legacy default stream) without synchronising:
+ *   rhs_dev  [(ny-1) x (nx-1)] interior right-hand side, row-major, float (FP32) or double (FP64);
+ *   w_dev, s_dev  [(ny+1) x (nx+1)] vertex arrays of the same type: interior entries are overwritten, the
+ *                 boundary ring is left as it is.
+ * Scratch lives in a fixed 8 MiB device array inside the library (held by every device that loads it):
+ * sizes needing more -- e.g. FP64 above 512 x 512, FP32 above 1024 x 512 -- return FSI_ERR_UNSUPPORTED with
+ * the reason in fsi_last_error_message.  No device memory is allocated or freed by this call.
+ * The first call on a device takes the scratch address (cudaGetSymbolAddress) and sets kernel attributes;
+ * make that first call before any stream capture.  All calls share the scratch array: calls whose work
+ * overlaps on the GPU race and must be ordered by the caller (one stream, or events). */
+fsi_status fsi_op_level_solve_noalloc(int precision, int nx, int ny, double h, double re, double dt,
+                                      const void* rhs_dev, void* w_dev, void* s_dev, void* stream);
+
 /* Throughput of a project-written fused multiply-add loop on the current device (independent chains, all
  * SMs busy), used as the arithmetic roofline of the FP64 and FP32 paths.  *flops_per_s receives the
  * measured rate (2 flops per FMA).  precision: FSI_PREC_FP64 or FSI_PREC_FP32. */

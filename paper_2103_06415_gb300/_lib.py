@@ -80,6 +80,8 @@ SIGNATURES = {
     "fsi_destroy": (None, [_P]),
     "fsi_op_level_solve": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D]),
     "fsi_op_fma_rate": (_INT, [_INT, _D]),
+    "fsi_op_level_solve_noalloc": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         _P, _P, _P, _P]),
 }
 
 _lib = None

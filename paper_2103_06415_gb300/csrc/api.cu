@@ -16,6 +16,8 @@ void fsi_set_last_cuda_error(cudaError_t e, const char* what, const char* file, 
   snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
 }
 
+void fsi_set_last_message(const char* msg) { snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg); }
+
 extern "C" const char* fsi_last_error_message(void) { return g_errmsg; }
 
 extern "C" const char* fsi_status_string(int s) {

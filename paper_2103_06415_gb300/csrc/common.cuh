@@ -18,6 +18,7 @@ template <> struct C2<double> { using t = double2; };
   } while (0)
 
 void fsi_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void fsi_set_last_message(const char* msg);
 
 // First error wins: a kernel records a status code without trapping.
 __device__ __forceinline__ void dev_set_status(int* status, int code) {
