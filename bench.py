@@ -36,6 +36,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--offline", action="store_true",
+                    help="measure the offline stage instead (B0 for 8192 unknowns on a 1024^2 grid by both "
+                         "methods, then the FP64 Cholesky factor of B0 + tau I) and print one JSON line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: build the reduced-Omega_0 variant of the workload, run this many "
                          "eager (non-graph) steps and exit without timing (for ncu captures)")
@@ -115,6 +118,49 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def run_offline():
+    """Offline stage of the b0_1024 workload (Algorithm 1 sizes of config 3): B0 assembly by the lattice
+    Green's function (FP64) and by one DST solve per column (FP32 and FP64), then the FP64 Cholesky factor of
+    B0 + tau I.  Wall times include a synchronisation; the factor's flops are n^3/3."""
+    import torch
+    from paper_2103_06415_gb300 import build as _b
+    from paper_2103_06415_gb300 import workloads as wl
+    _b.build()
+    import paper_2103_06415_gb300 as lib
+    from runners import gpu_context
+    w = wl.b0_1024()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    out = {"metric": "offline stage: B0 assembly (8192 unknowns, 1024^2 grid) and FP64 Cholesky of B0 + tau I",
+           "workload": w["name"], "unknowns": 8192, "columns_per_s": {}, "seconds": {}}
+    n2 = 8192
+    for name, prec, method in (("green_fp64", 0, 0), ("columns_fp32", 1, 1), ("columns_fp64", 0, 1)):
+        c = gpu_context(w, precision=prec, b0_method=method, precompute=False)
+        torch.cuda.synchronize()
+        c.precompute()                       # warm-up (allocations, kernel attributes)
+        c.close()
+        c = gpu_context(w, precision=prec, b0_method=method, precompute=False)
+        c.precompute()
+        sec = c.stats()["b0_seconds"]
+        out["seconds"][name] = sec
+        out["columns_per_s"][name] = n2 / sec
+        if name == "green_fp64":
+            out["green_fill_gbs"] = n2 * n2 * 8 / sec / 1e9
+            tau, fsec = c.factor_operator(1e-10)
+            tau, fsec = c.factor_operator(1e-10)
+            flops = n2 ** 3 / 3.0
+            fp64 = lib.fma_rate(lib.FSI_PREC_FP64)
+            out["cholesky"] = {"seconds": fsec, "tflops": flops / fsec / 1e12, "tau": tau,
+                               "fp64_fma_peak_tflops_measured": fp64 / 1e12,
+                               "frac_of_measured_fp64": flops / fsec / fp64}
+        c.close()
+    out["hbm_peak_gbs"] = peaks.get("hbm_gbs")
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -135,6 +181,9 @@ def run_reference(args, w):
 def main():
     args = parse()
     w = workload()
+    if args.offline:
+        run_offline()
+        return
     if args.profile_steps > 0:
         from paper_2103_06415_gb300 import workloads as wl
         from paper_2103_06415_gb300 import build as _b

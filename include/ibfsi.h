@@ -76,6 +76,8 @@ typedef struct {
   double tol;
   int history_cap;
   int use_graph;
+  int b0_method; /* 0: B0 from the lattice Green's function of (C^T A C)^{-1} (all columns at once, double);
+                    1: one DST solve per column as in Algorithm 1, in the context's precision. Same matrix. */
 } fsi_exec_desc;
 
 /* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at
@@ -162,6 +164,15 @@ fsi_status fsi_set_field(fsi_ctx* ctx, int level, int which, const double* in);
  * the n_sd x-components (points row by row inside the box), then the n_sd y-components. */
 fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n,
                                     double* out);
+
+/* Double-precision Cholesky factor L L^T = B0 + tau I of the precomputed sub-domain matrix, with
+ * tau = tau_rel * max_i B0_ii (B0 at flow-grid spacing is only positive semi-definite; BASELINE config 3
+ * asks for this factor after the B0 assembly).  The factor (lower triangle, 8 (2 n_sd)^2 bytes) is kept on
+ * the device.  *tau_out and *seconds (wall time of the factorisation) may be NULL.  A non-positive pivot
+ * returns FSI_ERR_NONFINITE.  Requires fsi_precompute. */
+fsi_status fsi_factor_operator(fsi_ctx* ctx, double tau_rel, double* tau_out, double* seconds);
+/* Sampled entries of that factor: out[k] = L[rows[k], cols[k]] (zero above the diagonal). */
+fsi_status fsi_get_factor_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n, double* out);
 
 /* Interpolation map P of the last step's final FSI iterate (Eq. weights): for each body point p the four
  * Omega_0 point indices idx[4p..4p+3] and hat weights w[4p..4p+3] (synchronising). */

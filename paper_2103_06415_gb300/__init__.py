@@ -28,11 +28,11 @@ class Context:
     """
 
     def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
-                 stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True):
+                 stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0):
         self._lib = _lib.load()
         g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
         x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
-                          1 if use_graph else 0)
+                          1 if use_graph else 0, b0_method)
         h_ = ctypes.c_void_p()
         check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
         self._h = h_
@@ -134,6 +134,22 @@ class Context:
         check(self._lib.fsi_get_operator_entries(self._h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                                  cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(rows),
                                                  _dp(out)), "fsi_get_operator_entries")
+        return out
+
+    def factor_operator(self, tau_rel=1e-10):
+        """Cholesky factor of B0 + tau I on the device; returns (tau, seconds)."""
+        tau, sec = ctypes.c_double(), ctypes.c_double()
+        check(self._lib.fsi_factor_operator(self._h, tau_rel, ctypes.byref(tau), ctypes.byref(sec)),
+              "fsi_factor_operator")
+        return tau.value, sec.value
+
+    def factor_entries(self, rows, cols):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        out = np.zeros(len(rows))
+        check(self._lib.fsi_get_factor_entries(self._h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                               cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(rows),
+                                               _dp(out)), "fsi_get_factor_entries")
         return out
 
     def interp(self, n_points):

@@ -30,7 +30,8 @@ class GridDesc(ctypes.Structure):
 
 class ExecDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
-                ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("b0_method", ctypes.c_int)]
 
 
 class BodyDesc(ctypes.Structure):
@@ -74,6 +75,8 @@ SIGNATURES = {
     "fsi_set_field": (_INT, [_P, _INT, _INT, _D]),
     "fsi_get_operator_entries": (_INT, [_P, _I64, _I64, _INT, _D]),
     "fsi_get_interp": (_INT, [_P, _I64, _D, _INT]),
+    "fsi_factor_operator": (_INT, [_P, ctypes.c_double, _D, _D]),
+    "fsi_get_factor_entries": (_INT, [_P, _I64, _I64, _INT, _D]),
     "fsi_get_stats": (_INT, [_P, ctypes.POINTER(Stats)]),
     "fsi_profile_kernel": (_INT, [_P, _INT, _INT, _D, ctypes.POINTER(_INT)]),
     "fsi_get_phase_times": (_INT, [_P, _D, _INT]),

@@ -286,7 +286,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   if (c->nb > 0 && fsi_smem_bytes(c->nf) > 200 * 1024) return FSI_ERR_UNSUPPORTED;
   const size_t n2 = 2 * (size_t)c->n_sd;
   if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
-  fsi_status st = build_b0(c);
+  fsi_status st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
   if (st != FSI_OK) return st;
   c->have_b0 = 1;
   if (c->nb > 0) {

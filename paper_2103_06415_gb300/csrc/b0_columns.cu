@@ -1,0 +1,186 @@
+// Offline stage exactly as Algorithm 1 states it: column u of B0 is the action
+//   B0 e_u = E0 C (C^T A C)^{-1} C^T E0^T e_u                                   (Eq. action)
+// i.e. one DST-diagonalised solve (Lap^{-1} A_w^{-1}, finest level, zero boundary values) per unknown.
+// Columns are processed in batches: the source C^T E0^T e_u is a 6-vertex stencil (the transpose of the
+// E0 C row stencil), the three DST passes run with the batch on gridDim.y, and E0 C is applied at every
+// Omega_0 point of each solved streamfunction.  B0 is symmetric, so column u is stored as row u (coalesced).
+// The arithmetic precision of the solves is the context's (float or double); B0 is stored in double.
+#include <chrono>
+#include <vector>
+#include "dst.cuh"
+#include "internal.h"
+
+namespace {
+
+// E0 C row stencil of unknown comp at a vertex: u -> (dx in -1..1, dy = +-1, w3[dx] dy / 2h);
+// v -> (dx = +-1, dy in -1..1, -w3[dy] dx / 2h).
+__device__ __forceinline__ void stencil_entry(int comp, int t, double inv2h, int* dx, int* dy, double* w) {
+  const double w3[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+  const int d = t / 2 - 1, e = (t & 1) ? 1 : -1;
+  if (comp == 0) {
+    *dx = d;
+    *dy = e;
+    *w = w3[d + 1] * e * inv2h;
+  } else {
+    *dx = e;
+    *dy = d;
+    *w = -w3[d + 1] * e * inv2h;
+  }
+}
+
+// src[c] (interior layout, row stride ps, batch stride lvl) <- C^T E0^T e_{col0 + c}; the batch buffer is
+// zeroed before this kernel.
+template <typename T>
+__global__ void k_col_source(T* __restrict__ src, long lvl, long ps, int col0, int ncols, int n_sd, int ni,
+                             int i_lo, int j_lo, double inv2h) {
+  const int c = blockIdx.x * blockDim.y + threadIdx.y, t = threadIdx.x;  // t < 6
+  if (c >= ncols || t >= 6) return;
+  const int u = col0 + c, comp = u / n_sd, p = u - comp * n_sd;
+  const int I = i_lo + p % ni, J = j_lo + p / ni;
+  int dx, dy;
+  double w;
+  stencil_entry(comp, t, inv2h, &dx, &dy, &w);
+  src[(long)c * lvl + (long)(J + dy - 1) * ps + (I + dx - 1)] = T(w);
+}
+
+// row (col0 + c) of B0 <- E0 C s_c at every Omega_0 unknown r (stencil applied to the solved field)
+template <typename T>
+__global__ void k_col_gather(double* __restrict__ B0, const T* __restrict__ s, long lvl, long ps, int col0,
+                             int ncols, int n_sd, int ni, int i_lo, int j_lo, double inv2h) {
+  const int c = blockIdx.y;
+  const long n2 = 2L * n_sd;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols || r >= n2) return;
+  const int comp = r / n_sd, p = r - comp * n_sd;
+  const int I = i_lo + p % ni, J = j_lo + p / ni;
+  const T* sc = s + (long)c * lvl;
+  double acc = 0.0;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    int dx, dy;
+    double w;
+    stencil_entry(comp, t, inv2h, &dx, &dy, &w);
+    acc += w * (double)sc[(long)(J + dy) * ps + (I + dx)];
+  }
+  B0[(long)(col0 + c) * n2 + r] = acc;
+}
+
+template <typename T>
+void set_attrs() {
+  const int big = 200 * 1024;
+  cudaFuncSetAttribute(dst::k_xf<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xf<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xf<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_ysolve<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_ysolve<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_ysolve<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+struct Shape {
+  int nthr, per, nf;
+};
+Shape shape_for(int logL) {
+  const int L = 1 << logL;
+  Shape c;
+  c.nthr = L / 4;
+  if (c.nthr < 32) c.nthr = 32;
+  if (c.nthr > 256) c.nthr = 256;
+  c.per = 1;
+  while (4 * c.per * c.nthr < L) c.per *= 2;
+  c.nf = 4 * c.per * c.nthr / L;
+  return c;
+}
+
+template <typename T>
+fsi_status columns_t(fsi_ctx* c) {
+  using c2 = typename C2<T>::t;
+  const int Nx = c->Nx, Ny = c->Ny;
+  const long lvl = c->lvl_elems, ps = c->ps;
+  const long t1 = (long)Nx * c->ldT, t2 = (long)Ny * c->ldX;
+  const int n2 = 2 * c->n_sd;
+  const size_t per_col = ((size_t)3 * lvl + t1 + 2 * t2) * sizeof(T);
+  size_t Bz = ((size_t)2 << 30) / per_col;  // batch of columns in ~2 GiB of scratch
+  if (Bz > 256) Bz = 256;
+  if (Bz < 1) Bz = 1;
+  const int B = (int)Bz;
+  set_attrs<T>();
+  T *src = nullptr, *T1 = nullptr, *T2w = nullptr, *T2s = nullptr, *fw = nullptr, *fs = nullptr;
+  fsi_status st = FSI_OK;
+  if (cudaMalloc(&src, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&T1, (size_t)B * t1 * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&T2w, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&T2s, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&fw, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&fs, (size_t)B * lvl * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    st = FSI_ERR_OOM;
+  }
+  const Shape cx = shape_for(c->logLx), cy = shape_for(c->logLy);
+  const int Lx = 1 << c->logLx, Ly = 1 << c->logLy;
+  const c2* twx = (const c2*)c->twx;
+  const c2* twy = (const c2*)c->twy;
+  const double h = c->g.h, inv2h = 0.5 / h;
+  dst::SpecParams<T> sp = {};
+  sp.lx = c->lx;
+  sp.ly = c->ly;
+  sp.ring = nullptr;
+  sp.inv_h2 = 1.0 / (h * h);
+  sp.inv_dt = 1.0 / c->g.dt;
+  sp.inv_2re = 0.5 / c->g.re;
+  sp.norm = 4.0 / ((double)c->Mx * (double)c->My);
+  sp.Mx = c->Mx;
+  sp.My = c->My;
+  for (int col0 = 0; st == FSI_OK && col0 < n2; col0 += B) {
+    const int nc = n2 - col0 < B ? n2 - col0 : B;
+    if (cudaMemsetAsync(src, 0, (size_t)nc * lvl * sizeof(T), c->stream) != cudaSuccess) {
+      st = FSI_ERR_CUDA;
+      break;
+    }
+    k_col_source<T><<<(nc + 31) / 32, dim3(8, 32), 0, c->stream>>>(src, lvl, ps, col0, nc, c->n_sd, c->ni, c->i_lo,
+                                                                   c->j_lo, inv2h);
+    {
+      dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
+      const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
+      if (cx.per == 1) dst::k_xf<T, 1><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
+      else if (cx.per == 2) dst::k_xf<T, 2><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
+      else dst::k_xf<T, 4><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
+    }
+    {
+      dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf), nc);
+      const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
+      if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
+      else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
+      else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
+    }
+    {
+      dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
+      const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
+      if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
+      else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
+      else dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
+    }
+    k_col_gather<T><<<dim3((n2 + 255) / 256, nc), 256, 0, c->stream>>>(c->B0, fs, lvl, ps, col0, nc, c->n_sd, c->ni,
+                                                                      c->i_lo, c->j_lo, inv2h);
+    if (cudaGetLastError() != cudaSuccess) st = FSI_ERR_CUDA;
+  }
+  if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+  cudaFree(src);
+  cudaFree(T1);
+  cudaFree(T2w);
+  cudaFree(T2s);
+  cudaFree(fw);
+  cudaFree(fs);
+  return st;
+}
+
+}  // namespace
+
+fsi_status build_b0_columns(fsi_ctx* c) {
+  auto t0 = std::chrono::steady_clock::now();
+  const fsi_status st = c->prec == FSI_PREC_FP64 ? columns_t<double>(c) : columns_t<float>(c);
+  c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}

@@ -54,6 +54,7 @@ struct fsi_ctx {
   int have_sd;
   int i_lo, i_hi, j_lo, j_hi, ni, nj, n_sd;
   double* B0;  // (2 n_sd)^2 row-major, double
+  double* d_factor;  // (2 n_sd)^2 lower Cholesky factor of B0 + tau I (fsi_factor_operator), or NULL
   int have_b0;
   double b0_seconds;
   // bodies
@@ -108,6 +109,8 @@ fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void*
 fsi_status launch_fsi(fsi_ctx* c);
 // b0.cu
 fsi_status build_b0(fsi_ctx* c);
+// b0_columns.cu
+fsi_status build_b0_columns(fsi_ctx* c);
 
 void* ctx_alloc(fsi_ctx* c, size_t bytes);
 

@@ -37,6 +37,14 @@ def flag_512x256_3lvl():
         ds=0.01)
 
 
+def b0_1024():
+    """Offline benchmark: B0 for a 64 x 64-vertex Omega_0 (4096 points, 8192 unknowns) centred in a
+    1024 x 1024 grid, h = 1/256, Re 500, dt = h/4 (alpha = dt/(2 Re h^2) = 0.064); no bodies."""
+    h = 1.0 / 256
+    return dict(name="b0_1024", nx=1024, ny=1024, n_levels=1, x0=-2.0, y0=-2.0, h=h, re=500.0, dt=h / 4,
+                uinf=(1.0, 0.0), steps=0, sd_box=(-32 * h, 31 * h, -32 * h, 31 * h), bodies=[], ds=h)
+
+
 def flag_512x256_3lvl_reduced_omega0():
     """flag_512x256_3lvl with Omega_0 cut to [-0.2,1.2]x[-0.25,0.35] (141 x 61 points, B0 2.4 GB); same
     kernels and small-system size, for profiler captures that must hold only a few GB."""

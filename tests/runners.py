@@ -17,10 +17,10 @@ def oracle_sim(w):
                     w["sd_box"], bodies, w["ds"])
 
 
-def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None):
+def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0):
     import paper_2103_06415_gb300 as lib
     c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
-                    precision=precision, use_graph=use_graph, stream=stream)
+                    precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method)
     for b in w["bodies"]:
         if b["kind"] == "torsional":
             c.add_torsional(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"], b["stiffness"],
