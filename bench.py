@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--offline", action="store_true",
                     help="measure the offline stage instead (B0 for 8192 unknowns on a 1024^2 grid by both "
                          "methods, then the FP64 Cholesky factor of B0 + tau I) and print one JSON line")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="serving mode: stream this many config-4 requests through the continuous-batching "
+                         "server and print one JSON line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: build the reduced-Omega_0 variant of the workload, run this many "
                          "eager (non-graph) steps and exit without timing (for ncu captures)")
@@ -161,6 +164,47 @@ def run_offline():
     print(json.dumps(out), flush=True)
 
 
+def run_serving(n_req):
+    """Serving sample of BASELINE config 4: a Poisson stream (20 req/s, real time) of independent
+    torsional-plate runs on {128, 256, 512, 1024}^2 grids with steps drawn from [200, 400] (the config's
+    200-2000 range shortened so the sample ends in seconds), FP32 fluid / FP64 FSI, admitted under an HBM
+    budget and advanced together.  Prints aggregate cell-steps/s and per-step latency percentiles."""
+    import numpy as np
+    from paper_2103_06415_gb300 import build as _b
+    from paper_2103_06415_gb300 import workloads as wl
+    _b.build()
+    import paper_2103_06415_gb300 as lib
+    reqs = wl.serving_requests(n_req, steps=(200, 400))
+    srv = lib.Server(200 << 30)
+    t0 = time.perf_counter()
+    k, res, max_active = 0, [], 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k][0] <= now:
+            _, w, b, n = reqs[k]
+            srv.submit(w, b, n, precision=lib.FSI_PREC_FP32, tag=k)
+            k += 1
+        n_active = srv.step()
+        max_active = max(max_active, n_active)
+        res += srv.poll()
+        if k == len(reqs) and n_active == 0 and srv.stats()["queued"] == 0:
+            break
+        if n_active == 0 and k < len(reqs):
+            time.sleep(max(0.0, reqs[k][0] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    p50 = [r["p50_step_ms"] for r in res]
+    p99 = [r["p99_step_ms"] for r in res]
+    out = {"metric": "serving: aggregate FSI cell-steps/s and per-step latency (config 4 sample)",
+           "requests": n_req, "finished": len(res), "errors": sum(r["status"] != 0 for r in res),
+           "wall_s": wall, "cell_steps": st["cell_steps"], "value": st["cell_steps"] / wall,
+           "unit": "cell-steps/s", "max_active": max_active, "ticks": st["ticks"],
+           "p50_step_ms": float(np.median(p50)), "p99_step_ms": float(np.percentile(p99, 99)),
+           "mean_wait_ms": float(np.mean([r["wait_ms"] for r in res])), "dtype": "f32 fluid / f64 FSI"}
+    print(json.dumps(out), flush=True)
+    srv.close()
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -183,6 +227,9 @@ def main():
     w = workload()
     if args.offline:
         run_offline()
+        return
+    if args.serving > 0:
+        run_serving(args.serving)
         return
     if args.profile_steps > 0:
         from paper_2103_06415_gb300 import workloads as wl

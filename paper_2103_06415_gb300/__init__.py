@@ -201,3 +201,54 @@ def fma_rate(precision):
     r = ctypes.c_double()
     check(lib.fsi_op_fma_rate(precision, ctypes.byref(r)), "fsi_op_fma_rate")
     return r.value
+
+
+class Server:
+    """Continuous-batching server (include/ibfsi_server.h): runs are admitted as the HBM budget allows and
+    advanced together, one step of every resident run per tick."""
+
+    def __init__(self, hbm_budget_bytes, max_active=0):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        check(self._lib.fsi_server_create(int(hbm_budget_bytes), max_active, ctypes.byref(h)), "fsi_server_create")
+        self._h = h
+
+    def submit(self, w, body, n_steps, precision=FSI_PREC_FP32, tag=0):
+        """w: grid/sub-domain description (workloads dict keys); body: torsional body dict."""
+        g = _lib.GridDesc(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"],
+                          (ctypes.c_double * 2)(*w["uinf"]))
+        b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, body["n_pts"], w["ds"], (ctypes.c_double * 2)(*body["hinge"]),
+                          body["theta0"], body["theta"], 0.0, body["inertia"], body["damping"], body["stiffness"],
+                          None, None)
+        box = _lib.Box(*w["sd_box"])
+        req = _lib.Request(g, b, box, precision, n_steps, tag)
+        rid = ctypes.c_uint64()
+        check(self._lib.fsi_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)), "fsi_server_submit")
+        return rid.value
+
+    def step(self):
+        n = ctypes.c_int()
+        check(self._lib.fsi_server_step(self._h, ctypes.byref(n)), "fsi_server_step")
+        return n.value
+
+    def poll(self, cap=256):
+        buf = (_lib.Result * cap)()
+        n = ctypes.c_int()
+        check(self._lib.fsi_server_poll(self._h, buf, cap, ctypes.byref(n)), "fsi_server_poll")
+        return [{k: getattr(buf[i], k) for k, _ in _lib.Result._fields_} for i in range(n.value)]
+
+    def stats(self):
+        s = _lib.ServerStats()
+        check(self._lib.fsi_server_get_stats(self._h, ctypes.byref(s)), "fsi_server_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fsi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -120,3 +120,32 @@ def check(code, where):
     if code != 0:
         raise FsiError(code, where)
     return code
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", GridDesc), ("body", BodyDesc), ("box", Box), ("precision", ctypes.c_int),
+                ("n_steps", ctypes.c_int), ("tag", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("steps", ctypes.c_int),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("moment", ctypes.c_double),
+                ("theta", ctypes.c_double), ("phi", ctypes.c_double), ("mean_step_ms", ctypes.c_double),
+                ("p50_step_ms", ctypes.c_double), ("p99_step_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("finished", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("ticks", ctypes.c_longlong), ("run_steps", ctypes.c_longlong),
+                ("cell_steps", ctypes.c_double), ("busy_ms", ctypes.c_double)]
+
+
+SIGNATURES.update({
+    "fsi_server_create": (_INT, [ctypes.c_size_t, _INT, ctypes.POINTER(_P)]),
+    "fsi_server_submit": (_INT, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "fsi_server_step": (_INT, [_P, ctypes.POINTER(_INT)]),
+    "fsi_server_poll": (_INT, [_P, ctypes.POINTER(Result), _INT, ctypes.POINTER(_INT)]),
+    "fsi_server_get_stats": (_INT, [_P, ctypes.POINTER(ServerStats)]),
+    "fsi_server_destroy": (None, [_P]),
+})

@@ -65,6 +65,32 @@ def small_plate(nx=64, ny=32, n_levels=1):
         ds=h)
 
 
+def serving_grid(n, re=100.0):
+    """Serving request grid: n x n cells at the fixed h = 1/32 and dt = 0.002 of plate_128, domain
+    [-1, -1 + n/32] x [-n/64, n/64], Omega_0 = [-1.2, 1.2]^2 clipped."""
+    h = 1.0 / 32
+    return dict(name="serve_%d" % n, nx=n, ny=n, n_levels=1, x0=-1.0, y0=-n / 64.0, h=h, re=re, dt=0.002,
+                uinf=(1.0, 0.0), sd_box=(-1.2, 1.2, -1.2, 1.2), ds=h)
+
+
+def serving_requests(n_req, seed=SEED, sizes=(128, 256, 512, 1024), steps=(200, 2000), rate_hz=20.0):
+    """Poisson-arrival stream of independent torsional-plate runs (BASELINE config 4 distributions):
+    grid from `sizes`, Re ~ U[50, 300], stiffness log-uniform [0.05, 5], inertia ~ U[0.5, 2], angle of
+    attack ~ U[5, 40] deg, steps ~ U{steps}.  Returns [(arrival_s, grid dict, body dict, n_steps)]."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for _ in range(n_req):
+        t += rng.exponential(1.0 / rate_hz)
+        n = int(rng.choice(sizes))
+        w = serving_grid(n, re=float(rng.uniform(50.0, 300.0)))
+        body = dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=33,
+                    inertia=float(rng.uniform(0.5, 2.0)), damping=0.0,
+                    stiffness=float(np.exp(rng.uniform(np.log(0.05), np.log(5.0)))),
+                    theta=float(np.deg2rad(rng.uniform(5.0, 40.0))))
+        out.append((t, w, body, int(rng.integers(steps[0], steps[1] + 1))))
+    return out
+
+
 def random_field(shape, seed, smooth=True):
     """Seeded vertex field: a few low sine modes plus small noise (ring included)."""
     rng = np.random.default_rng(seed)

@@ -43,3 +43,17 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     h = ctypes.c_void_p()
     assert lib.fsi_create(ctypes.byref(g), None, ctypes.byref(h)) == 1
     assert lib.fsi_advance(None, 1) == 1
+
+
+def test_server_request_validation_without_a_gpu():
+    import paper_2103_06415_gb300 as p
+    from paper_2103_06415_gb300 import workloads as wl
+    srv = p.Server(2 << 30)
+    w = wl.serving_grid(128)
+    body = dict(hinge=(0.0, 0.0), theta0=0.0, n_pts=33, inertia=1.0, damping=0.0, stiffness=0.5, theta=0.3)
+    assert srv.submit(w, body, 10) == 1
+    with pytest.raises(p.FsiError):                       # a request that can never fit the budget
+        p.Server(1 << 20).submit(w, body, 10)
+    st = srv.stats()
+    assert st["queued"] == 1 and st["active"] == 0
+    srv.close()
