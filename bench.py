@@ -57,6 +57,20 @@ def cells_per_step(w):
     return w["n_levels"] * w["nx"] * w["ny"]
 
 
+def aggregate_replicas(local_ms, local_cell_steps, world):
+    """Replicas only: every rank runs its own copy of the workload with no data-path collective.  The job
+    time is the slowest rank's (MAX over ranks); the value is all ranks' cell-steps over that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms, local_cell_steps], dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(tmax[0]), float(t[1]) / (float(tmax[0]) * 1e-3)
+    return local_ms, local_cell_steps / (local_ms * 1e-3)
+
+
 def oracle_sample(w, budget_s):
     """Time the FP64 oracle as it stands on a bounded prefix of the workload (after one untimed step)."""
     import numpy as np  # noqa: F401
@@ -298,13 +312,8 @@ def main():
     clk = Clocks(local)
     times = timed_steps(ctx, stream, args.steps)
     clocks = clk.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     cells = cells_per_step(w)
-    value = cells * args.steps * world / (total_ms * 1e-3)
+    total_ms, value = aggregate_replicas(sum(times), cells * args.steps, world)
     stats = ctx.stats()
     phases = {k: v / max(stats["steps_done"], 1) for k, v in ctx.phase_times().items()}
     hist_mixed = ctx.history(0)
