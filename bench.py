@@ -174,6 +174,22 @@ def run_offline():
                                "fp64_fma_peak_tflops_measured": fp64 / 1e12,
                                "frac_of_measured_fp64": flops / fsec / fp64}
         c.close()
+    # second run: sixteen uneven boxes (256 ... 4096 points) on the same grid, built together
+    boxes = wl.b0_1024_uneven_boxes()
+    args = (w["nx"], w["ny"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], boxes)
+    uneven = {"boxes": len(boxes), "points": [], "seconds": {}, "columns_per_s": {}}
+    for name, prec, method in (("green_fp64", 0, 0), ("columns_fp32", 1, 1)):
+        lib.B0Set(*args, method=method, precision=prec).close()     # warm-up
+        s = lib.B0Set(*args, method=method, precision=prec)
+        uneven["points"] = [s.box(k)["n_sd"] for k in range(len(boxes))]
+        sec = s.stats()["seconds"]
+        s.close()
+        uneven["seconds"][name] = sec
+        uneven["columns_per_s"][name] = 2 * sum(uneven["points"]) / sec
+    uneven["unknowns_total"] = 2 * sum(uneven["points"])
+    uneven["b0_bytes_total"] = sum(8 * (2 * p) ** 2 for p in uneven["points"])
+    uneven["green_fill_gbs"] = uneven["b0_bytes_total"] / uneven["seconds"]["green_fp64"] / 1e9
+    out["uneven_subdomains"] = uneven
     out["hbm_peak_gbs"] = peaks.get("hbm_gbs")
     print(json.dumps(out), flush=True)
 

@@ -196,6 +196,28 @@ fsi_status fsi_profile_kernel(fsi_ctx* ctx, int kernel_class, int n_steps, doubl
 /* Free all device memory and the handle (synchronises the stream first). */
 void fsi_destroy(fsi_ctx* ctx);
 
+/* ---- Offline stage for several independent sub-domains on one grid ------------------------------------
+ * B0 (Algorithm 1, Eq. action; finest level, zero boundary values) for n_boxes Omega_0 boxes of different
+ * sizes on the same grid, built together: every kernel of the build runs once over all boxes (one lattice
+ * Green's function shared by all boxes with exec->b0_method = 0; batches of column solves that mix the
+ * boxes' columns with b0_method = 1).  Each box is snapped and clipped as in fsi_set_subdomain.  The
+ * matrices stay on the device, box k's (2 n_sd_k)^2 row-major block after box k-1's; the unknown
+ * ordering inside a box is that of fsi_get_operator_entries.  exec->precision selects the arithmetic of the
+ * column solves (B0 is stored in double); exec->stream as in fsi_create.  The call synchronises. */
+typedef struct fsi_b0_set fsi_b0_set;
+
+fsi_status fsi_b0_set_build(const fsi_grid_desc* grid, const fsi_exec_desc* exec, const fsi_box* boxes,
+                            int n_boxes, fsi_b0_set** out);
+/* Snapped extent of box k: vertex indices [i_lo, i_hi] x [j_lo, j_hi] and n_sd = points in the box.
+ * Any output pointer may be NULL. */
+fsi_status fsi_b0_set_box(const fsi_b0_set* set, int box, int* i_lo, int* i_hi, int* j_lo, int* j_hi, int* n_sd);
+/* Sampled entries of box k's matrix: out[m] = B0_k[rows[m], cols[m]] (synchronising). */
+fsi_status fsi_b0_set_entries(fsi_b0_set* set, int box, const int64_t* rows, const int64_t* cols, int n,
+                              double* out);
+/* Wall time of the build in seconds and device bytes held by the set.  Either pointer may be NULL. */
+fsi_status fsi_b0_set_stats(const fsi_b0_set* set, double* seconds, size_t* device_bytes);
+void fsi_b0_set_destroy(fsi_b0_set* set);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
 
-__all__ = ["Context", "level_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
+__all__ = ["Context", "B0Set", "level_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
 
 
 def _dp(a):
@@ -182,6 +182,55 @@ class Context:
         s = _lib.Stats()
         check(self._lib.fsi_get_stats(self._h, ctypes.byref(s)), "fsi_get_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+class B0Set:
+    """B0 of several independent Omega_0 boxes on one grid, built together (``fsi_b0_set_build``).
+
+    boxes: list of (x_lo, x_hi, y_lo, y_hi); method 0 = lattice Green's function, 1 = one DST solve per
+    column (Algorithm 1) in the given precision."""
+
+    def __init__(self, nx, ny, x0, y0, h, re, dt, boxes, method=0, precision=FSI_PREC_FP64, stream=None):
+        self._lib = _lib.load()
+        g = _lib.GridDesc(nx, ny, 1, x0, y0, h, re, dt, (ctypes.c_double * 2)(1.0, 0.0))
+        x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, 50, 1e-7, 16, 0, method)
+        arr = (_lib.Box * len(boxes))(*[_lib.Box(*b) for b in boxes])
+        h_ = ctypes.c_void_p()
+        check(self._lib.fsi_b0_set_build(ctypes.byref(g), ctypes.byref(x), arr, len(boxes), ctypes.byref(h_)),
+              "fsi_b0_set_build")
+        self._h = h_
+        self.n_boxes = len(boxes)
+
+    def box(self, k):
+        v = [ctypes.c_int() for _ in range(5)]
+        check(self._lib.fsi_b0_set_box(self._h, k, *[ctypes.byref(a) for a in v]), "fsi_b0_set_box")
+        i_lo, i_hi, j_lo, j_hi, n_sd = (a.value for a in v)
+        return dict(i_lo=i_lo, i_hi=i_hi, j_lo=j_lo, j_hi=j_hi, n_sd=n_sd)
+
+    def entries(self, k, rows, cols):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        out = np.zeros(len(rows))
+        check(self._lib.fsi_b0_set_entries(self._h, k, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(rows),
+                                           _dp(out)), "fsi_b0_set_entries")
+        return out
+
+    def stats(self):
+        sec, nbytes = ctypes.c_double(), ctypes.c_size_t()
+        check(self._lib.fsi_b0_set_stats(self._h, ctypes.byref(sec), ctypes.byref(nbytes)), "fsi_b0_set_stats")
+        return dict(seconds=sec.value, device_bytes=nbytes.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fsi_b0_set_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64):

@@ -149,3 +149,13 @@ SIGNATURES.update({
     "fsi_server_get_stats": (_INT, [_P, ctypes.POINTER(ServerStats)]),
     "fsi_server_destroy": (None, [_P]),
 })
+
+SIGNATURES.update({
+    "fsi_b0_set_build": (_INT, [ctypes.POINTER(GridDesc), ctypes.POINTER(ExecDesc), ctypes.POINTER(Box), _INT,
+                                ctypes.POINTER(_P)]),
+    "fsi_b0_set_box": (_INT, [_P, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_INT), ctypes.POINTER(_INT),
+                              ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    "fsi_b0_set_entries": (_INT, [_P, _INT, _I64, _I64, _INT, _D]),
+    "fsi_b0_set_stats": (_INT, [_P, _D, ctypes.POINTER(ctypes.c_size_t)]),
+    "fsi_b0_set_destroy": (None, [_P]),
+})

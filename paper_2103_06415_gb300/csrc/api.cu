@@ -249,21 +249,33 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
   return FSI_OK;
 }
 
+fsi_status snap_box(const fsi_grid_desc& g, const fsi_box& b, int* i_lo_, int* i_hi_, int* j_lo_, int* j_hi_) {
+  const double h = g.h;
+  if (!std::isfinite(b.x_lo) || !std::isfinite(b.x_hi) || !std::isfinite(b.y_lo) || !std::isfinite(b.y_hi))
+    return FSI_ERR_INVALID_ARG;
+  int i_lo = (int)std::ceil((b.x_lo - g.x0) / h - 1e-9), i_hi = (int)std::floor((b.x_hi - g.x0) / h + 1e-9);
+  int j_lo = (int)std::ceil((b.y_lo - g.y0) / h - 1e-9), j_hi = (int)std::floor((b.y_hi - g.y0) / h + 1e-9);
+  if (i_lo < 2) i_lo = 2;
+  if (j_lo < 2) j_lo = 2;
+  if (i_hi > g.nx - 2) i_hi = g.nx - 2;
+  if (j_hi > g.ny - 2) j_hi = g.ny - 2;
+  if (i_hi <= i_lo || j_hi <= j_lo) return FSI_ERR_INVALID_ARG;
+  *i_lo_ = i_lo;
+  *i_hi_ = i_hi;
+  *j_lo_ = j_lo;
+  *j_hi_ = j_hi;
+  return FSI_OK;
+}
+
 extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_boxes, const double* extra,
                                         int n_extra) {
   (void)extra;
   if (!c || !boxes) return FSI_ERR_INVALID_ARG;
   if (c->stage >= 1) return FSI_ERR_STATE;
   if (n_boxes != 1 || n_extra != 0) return FSI_ERR_UNSUPPORTED;
-  const fsi_box& b = boxes[0];
-  const double h = c->g.h;
-  int i_lo = (int)std::ceil((b.x_lo - c->g.x0) / h - 1e-9), i_hi = (int)std::floor((b.x_hi - c->g.x0) / h + 1e-9);
-  int j_lo = (int)std::ceil((b.y_lo - c->g.y0) / h - 1e-9), j_hi = (int)std::floor((b.y_hi - c->g.y0) / h + 1e-9);
-  if (i_lo < 2) i_lo = 2;
-  if (j_lo < 2) j_lo = 2;
-  if (i_hi > c->nx - 2) i_hi = c->nx - 2;
-  if (j_hi > c->ny - 2) j_hi = c->ny - 2;
-  if (i_hi <= i_lo || j_hi <= j_lo) return FSI_ERR_INVALID_ARG;
+  int i_lo, i_hi, j_lo, j_hi;
+  const fsi_status st = snap_box(c->g, boxes[0], &i_lo, &i_hi, &j_lo, &j_hi);
+  if (st != FSI_OK) return st;
   c->i_lo = i_lo;
   c->i_hi = i_hi;
   c->j_lo = j_lo;

@@ -9,50 +9,85 @@
 // E0 C is a 6-vertex stencil (u: w_dx (s[j+1] - s[j-1])/2h; v: -w_dy (s[i+1] - s[i-1])/2h), hence
 //   B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb) - T-+(ia-ib, ja+jb) + T++(ia+ib, ja+jb)
 // with 16 small tables (4 component blocks x 4 image terms) of stencil-convolved g.  The result equals the
-// column-by-column definition up to rounding order; the cost is one pass writing B0 plus two small
-// cosine contractions for g.
+// column-by-column definition up to rounding order; the cost is one pass writing B0 plus the two cosine
+// sums of g, each a batch of DCT-I rows done by FFT in double.  g depends on the grid only, so several Omega_0 boxes on one grid share it and
+// their tables and matrices are produced by one launch of each kernel.
 #include <chrono>
 #include <cmath>
 #include <vector>
+#include "dst.cuh"
 #include "internal.h"
 
 namespace {
 
-// T1[k][q] = sum_l d_kl cos(pi l q / My), k = 1..Nx (row k-1), q = 0..My
-__global__ void k_g_stage1(double* __restrict__ T1, int Nx, int Ny, int My, const double* __restrict__ lx,
-                           const double* __restrict__ ly, const double* __restrict__ cy, double inv_h2,
-                           double inv_dt, double inv_2re) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y + 1;
-  if (q > My) return;
-  const int period = 2 * My;
-  double acc = 0.0;
-  int idx = 0;  // (l*q) mod 2My, incremented
-  for (int l = 1; l <= Ny; ++l) {
-    idx += q;
-    if (idx >= period) idx -= period;
-    const double lam = (lx[k] + ly[l]) * inv_h2;
-    const double a = inv_dt + lam * inv_2re;
-    acc += cy[idx] / (lam * a);
+// DCT-I rows by FFT: out[r][q] = scale * sum_{l=1}^{M-1} x_r[l] cos(pi l q / M), q = 0..M.  The even
+// extension y (y[l] = y[2M-l] = x_r[l], y[0] = y[M] = 0) has the real DFT Y_q = 2 sum_l x_r[l] cos(pi l q/M),
+// so two rows packed as y_a + i y_b give Y_a = Re Z, Y_b = Im Z of one complex FFT of length L = 2M.
+// Rows come from `in` (element (r, l) at in[r*in_rs + (l-1)*in_es]) or, when in == NULL, from the spectral
+// Green's-function weights d_kl = 1/(lambda_kl a_kl) with k = r+1 (the first cosine sum of g).
+template <int PER>
+__global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, long in_rs, long in_es, int nrows,
+                                              int M, double* __restrict__ out, long out_rs, long out_es,
+                                              const double2* __restrict__ tw, int logL, double scale,
+                                              const double* __restrict__ lx, const double* __restrict__ ly,
+                                              double inv_h2, double inv_dt, double inv_2re) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  const int L = 1 << logL;
+  const int r0 = 2 * blockIdx.x;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int ll = l <= M ? l : L - l;
+    double a = 0.0, b = 0.0;
+    if (ll >= 1 && ll <= M - 1) {
+      for (int e = 0; e < 2; ++e) {
+        const int r = r0 + e;
+        double v = 0.0;
+        if (r < nrows) {
+          if (in) {
+            v = in[(long)r * in_rs + (long)(ll - 1) * in_es];
+          } else {
+            const double lam = (lx[r + 1] + ly[ll]) * inv_h2;
+            v = 1.0 / (lam * (inv_dt + lam * inv_2re));
+          }
+        }
+        if (e == 0) a = v;
+        else b = v;
+      }
+    }
+    buf[l] = make_double2(a, b);
   }
-  T1[(long)(k - 1) * (My + 1) + q] = acc;
+  __syncthreads();
+  dst::block_fft<double, PER>(buf, L, logL, tw);
+  for (int q = threadIdx.x; q <= M; q += blockDim.x) {
+    const double2 z = buf[q];
+    if (r0 < nrows) out[(long)r0 * out_rs + (long)q * out_es] = 0.5 * scale * z.x;
+    if (r0 + 1 < nrows) out[(long)(r0 + 1) * out_rs + (long)q * out_es] = 0.5 * scale * z.y;
+  }
 }
 
-// g[p][q] = norm * sum_k cos(pi k p/Mx) T1[k][q], p = 0..Mx, q = 0..My
-__global__ void k_g_stage2(double* __restrict__ g, const double* __restrict__ T1, int Nx, int Mx, int My,
-                           const double* __restrict__ cx, double norm) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  if (q > My) return;
-  const int period = 2 * Mx;
-  double acc = 0.0;
-  int idx = 0;
-  for (int k = 1; k <= Nx; ++k) {
-    idx += p;
-    if (idx >= period) idx -= period;
-    acc += cx[idx] * T1[(long)(k - 1) * (My + 1) + q];
+// launch: one CTA per row pair, L/(4 PER) threads (one complex row of length L per CTA)
+fsi_status launch_dct1(const double* in, long in_rs, long in_es, int nrows, int M, double* out, long out_rs,
+                       long out_es, const double2* tw, int logL, double scale, const double* lx, const double* ly,
+                       double inv_h2, double inv_dt, double inv_2re, cudaStream_t st) {
+  const int L = 1 << logL;
+  const int nthr = L / 4 < 256 ? L / 4 : 256;
+  const int per = L / (4 * nthr);
+  const size_t sm = (size_t)L * sizeof(double2);
+  const dim3 grid((nrows + 1) / 2);
+  static bool attrs = false;
+  if (!attrs) {
+    attrs = true;
+    cudaFuncSetAttribute(k_dct1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_dct1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_dct1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   }
-  g[(long)p * (My + 1) + q] = norm * acc;
+  switch (per) {
+    case 1: k_dct1<1><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re); break;
+    case 2: k_dct1<2><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re); break;
+    case 4: k_dct1<4><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re); break;
+    default: return FSI_ERR_UNSUPPORTED;
+  }
+  return cudaGetLastError() == cudaSuccess ? FSI_OK : FSI_ERR_CUDA;
 }
 
 __device__ __forceinline__ int fold(int p, int M) {
@@ -86,10 +121,12 @@ __device__ void make_stencil(int comp, double h, Stencil* s) {
     }
 }
 
-// tables[((ca*2+cb)*4 + term)][iy][ix] (x index contiguous), term bit0: x uses the sum index, bit1: y uses
-// the sum index
-__global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g, int Mx, int My, int ni, int nj,
-                         int i_lo, int j_lo, double h) {
+// Per box: tables[((ca*2+cb)*4 + term)][iy][ix] (x index contiguous), term bit0: x uses the sum index,
+// bit1: y uses the sum index.  blockIdx.y is the box.
+__global__ void k_tables(double* __restrict__ tab, const B0Box* __restrict__ bx, const double* __restrict__ g,
+                         int Mx, int My, double h) {
+  const B0Box b = bx[blockIdx.y];
+  const int ni = b.ni, nj = b.nj;
   const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
   const long per = (long)nx2 * ny2;
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,8 +139,8 @@ __global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g,
   make_stencil(ca, h, &sa);
   make_stencil(cb, h, &sb);
   const bool xs = term & 1, ys = term & 2;
-  const int X = xs ? ix + 2 * i_lo : ix - (ni - 1);
-  const int Y = ys ? iy + 2 * j_lo : iy - (nj - 1);
+  const int X = xs ? ix + 2 * b.i_lo : ix - (ni - 1);
+  const int Y = ys ? iy + 2 * b.j_lo : iy - (nj - 1);
   double acc = 0.0;
   for (int u = 0; u < 6; ++u)
     for (int v = 0; v < 6; ++v) {
@@ -111,32 +148,35 @@ __global__ void k_tables(double* __restrict__ tab, const double* __restrict__ g,
       const int py = ys ? Y + sa.dy[u] + sb.dy[v] : Y + sa.dy[u] - sb.dy[v];
       acc += sa.w[u] * sb.w[v] * g[(long)fold(px, Mx) * (My + 1) + fold(py, My)];
     }
-  tab[e] = acc;
+  tab[b.tab_off + e] = acc;
 }
 
-// One CTA per row a of B0: B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb) - T-+(ia-ib, ja+jb)
-// + T++(ia+ib, ja+jb); threads run along ib so stores and table reads are contiguous.
-__global__ void __launch_bounds__(256) k_fill(double* __restrict__ B0, const double* __restrict__ tab, int ni,
-                                              int nj, int n_sd) {
-  const long n2 = 2L * n_sd;
-  const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
-  const long per = (long)nx2 * ny2;
-  for (long a = blockIdx.x; a < n2; a += gridDim.x) {
+// One CTA per row a (over the rows of all boxes): B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb)
+// - T-+(ia-ib, ja+jb) + T++(ia+ib, ja+jb); threads run along ib so stores and table reads are contiguous.
+__global__ void __launch_bounds__(256) k_fill(double* __restrict__ out, const double* __restrict__ tab,
+                                              const B0Box* __restrict__ bx, int n_boxes, long n_rows) {
+  for (long ag = blockIdx.x; ag < n_rows; ag += gridDim.x) {
+    const B0Box b = bx[b0_find_box(bx, n_boxes, ag)];
+    const int ni = b.ni, nj = b.nj, n_sd = b.n_sd;
+    const long n2 = 2L * n_sd;
+    const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
+    const long per = (long)nx2 * ny2;
+    const long a = ag - b.row_off;
     const int ca = (int)(a / n_sd);
     const int pa = (int)(a - (long)ca * n_sd);
     const int ja = pa / ni, ia = pa - ja * ni;
-    double* row = B0 + a * n2;
+    double* row = out + b.out_off + a * n2;
     for (int cb = 0; cb < 2; ++cb) {
-      const double* t = tab + (long)((ca * 2 + cb) * 4) * per;
+      const double* t = tab + b.tab_off + (long)((ca * 2 + cb) * 4) * per;
       for (int jb = 0; jb < nj; ++jb) {
         const double* tmm = t + (long)(ja - jb + nj - 1) * nx2;
         const double* tpm = t + per + (long)(ja - jb + nj - 1) * nx2;
         const double* tmp = t + 2 * per + (long)(ja + jb) * nx2;
         const double* tpp = t + 3 * per + (long)(ja + jb) * nx2;
-        double* out = row + (long)cb * n_sd + (long)jb * ni;
+        double* o = row + (long)cb * n_sd + (long)jb * ni;
         for (int ib = threadIdx.x; ib < ni; ib += blockDim.x) {
           const int D = ia - ib + ni - 1, S = ia + ib;
-          out[ib] = tmm[D] - tpm[S] - tmp[D] + tpp[S];
+          o[ib] = tmm[D] - tpm[S] - tmp[D] + tpp[S];
         }
       }
     }
@@ -145,46 +185,75 @@ __global__ void __launch_bounds__(256) k_fill(double* __restrict__ B0, const dou
 
 }  // namespace
 
-fsi_status build_b0(fsi_ctx* c) {
-  auto t0 = std::chrono::steady_clock::now();
+fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   const int Nx = c->Nx, Ny = c->Ny, Mx = c->Mx, My = c->My;
   const double h = c->g.h;
-  std::vector<double> cx(2 * Mx), cy(2 * My);
-  for (int p = 0; p < 2 * Mx; ++p) cx[p] = std::cos(M_PI * (double)p / (double)Mx);
-  for (int q = 0; q < 2 * My; ++q) cy[q] = std::cos(M_PI * (double)q / (double)My);
-  double *d_cx = nullptr, *d_cy = nullptr, *d_T1 = nullptr, *d_g = nullptr, *d_tab = nullptr;
-  const int nx2 = 2 * c->ni - 1, ny2 = 2 * c->nj - 1;
-  const size_t tab_n = (size_t)16 * nx2 * ny2;
+  const int nb = (int)boxes.size();
+  b0_layout(boxes);
+  long tab_n = 0, rows = 0, max_tab = 0;
+  for (B0Box& b : boxes) {
+    const long t = 16L * (2 * b.ni - 1) * (2 * b.nj - 1);
+    b.tab_off = tab_n;
+    tab_n += t;
+    if (t > max_tab) max_tab = t;
+    rows += 2L * b.n_sd;
+  }
+  // twiddles exp(-2 pi i m / L) for the two DCT lengths L = 2 Mx, 2 My
+  std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);
+  for (int m = 0; m < 2 * Mx; ++m) {
+    twx[2 * m] = std::cos(-M_PI * (double)m / (double)Mx);
+    twx[2 * m + 1] = std::sin(-M_PI * (double)m / (double)Mx);
+  }
+  for (int m = 0; m < 2 * My; ++m) {
+    twy[2 * m] = std::cos(-M_PI * (double)m / (double)My);
+    twy[2 * m + 1] = std::sin(-M_PI * (double)m / (double)My);
+  }
+  double *d_twx = nullptr, *d_twy = nullptr, *d_T1 = nullptr, *d_g = nullptr, *d_tab = nullptr;
+  B0Box* d_bx = nullptr;
   fsi_status st = FSI_OK;
   do {
-    if (cudaMalloc(&d_cx, cx.size() * 8) != cudaSuccess || cudaMalloc(&d_cy, cy.size() * 8) != cudaSuccess ||
+    if (cudaMalloc(&d_twx, twx.size() * 8) != cudaSuccess || cudaMalloc(&d_twy, twy.size() * 8) != cudaSuccess ||
         cudaMalloc(&d_T1, (size_t)Nx * (My + 1) * 8) != cudaSuccess ||
         cudaMalloc(&d_g, (size_t)(Mx + 1) * (My + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&d_tab, tab_n * 8) != cudaSuccess) {
+        cudaMalloc(&d_tab, (size_t)tab_n * 8) != cudaSuccess ||
+        cudaMalloc(&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
+      cudaGetLastError();
       st = FSI_ERR_OOM;
       break;
     }
-    if (cudaMemcpyAsync(d_cx, cx.data(), cx.size() * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(d_cy, cy.data(), cy.size() * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    if (cudaMemcpyAsync(d_twx, twx.data(), twx.size() * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_twy, twy.data(), twy.size() * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_bx, boxes.data(), (size_t)nb * sizeof(B0Box), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess) {
       st = FSI_ERR_CUDA;
       break;
     }
-    k_g_stage1<<<dim3((My + 1 + 127) / 128, Nx), 128, 0, c->stream>>>(d_T1, Nx, Ny, My, c->lx, c->ly, d_cy,
-                                                                      1.0 / (h * h), 1.0 / c->g.dt, 0.5 / c->g.re);
-    k_g_stage2<<<dim3((My + 1 + 127) / 128, Mx + 1), 128, 0, c->stream>>>(d_g, d_T1, Nx, Mx, My, d_cx,
-                                                                          1.0 / ((double)Mx * (double)My));
-    k_tables<<<(unsigned)((tab_n + 127) / 128), 128, 0, c->stream>>>(d_tab, d_g, Mx, My, c->ni, c->nj, c->i_lo,
-                                                                     c->j_lo, h);
+    // T1[k-1][q] = sum_l d_kl cos(pi l q/My);  g[p][q] = sum_k cos(pi k p/Mx) T1[k-1][q] / (Mx My)
+    st = launch_dct1(nullptr, 0, 0, Nx, My, d_T1, My + 1, 1, (const double2*)d_twy, ilog2_exact(2 * My), 1.0, c->lx,
+                     c->ly, 1.0 / (h * h), 1.0 / c->g.dt, 0.5 / c->g.re, c->stream);
+    if (st != FSI_OK) break;
+    st = launch_dct1(d_T1, 1, My + 1, My + 1, Mx, d_g, 1, My + 1, (const double2*)d_twx, ilog2_exact(2 * Mx),
+                     1.0 / ((double)Mx * (double)My), nullptr, nullptr, 0.0, 0.0, 0.0, c->stream);
+    if (st != FSI_OK) break;
+    k_tables<<<dim3((unsigned)((max_tab + 127) / 128), nb), 128, 0, c->stream>>>(d_tab, d_bx, d_g, Mx, My, h);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
-    k_fill<<<nsm * 16, 256, 0, c->stream>>>(c->B0, d_tab, c->ni, c->nj, c->n_sd);
+    k_fill<<<nsm * 16, 256, 0, c->stream>>>(out, d_tab, d_bx, nb, rows);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
-  cudaFree(d_cx);
-  cudaFree(d_cy);
+  cudaFree(d_twx);
+  cudaFree(d_twy);
   cudaFree(d_T1);
   cudaFree(d_g);
   cudaFree(d_tab);
+  cudaFree(d_bx);
+  return st;
+}
+
+fsi_status build_b0(fsi_ctx* c) {
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<B0Box> one(1, ctx_box(c));
+  const fsi_status st = b0_green(c, one, c->B0);
   c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
 }

@@ -1,7 +1,7 @@
 // Offline stage exactly as Algorithm 1 states it: column u of B0 is the action
 //   B0 e_u = E0 C (C^T A C)^{-1} C^T E0^T e_u                                   (Eq. action)
 // i.e. one DST-diagonalised solve (Lap^{-1} A_w^{-1}, finest level, zero boundary values) per unknown.
-// Columns are processed in batches: the source C^T E0^T e_u is a 6-vertex stencil (the transpose of the
+// Columns are processed in batches (columns of several Omega_0 boxes on one grid may share a batch): the source C^T E0^T e_u is a 6-vertex stencil (the transpose of the
 // E0 C row stencil), the three DST passes run with the batch on gridDim.y, and E0 C is applied at every
 // Omega_0 point of each solved streamfunction.  B0 is symmetric, so column u is stored as row u (coalesced).
 // The arithmetic precision of the solves is the context's (float or double); B0 is stored in double.
@@ -28,31 +28,37 @@ __device__ __forceinline__ void stencil_entry(int comp, int t, double inv2h, int
   }
 }
 
-// src[c] (interior layout, row stride ps, batch stride lvl) <- C^T E0^T e_{col0 + c}; the batch buffer is
-// zeroed before this kernel.
+// src[c] (interior layout, row stride ps, batch stride lvl) <- C^T E0^T e_u for the global unknown
+// u = col0 + c of the concatenated boxes; the batch buffer is zeroed before this kernel.
 template <typename T>
-__global__ void k_col_source(T* __restrict__ src, long lvl, long ps, int col0, int ncols, int n_sd, int ni,
-                             int i_lo, int j_lo, double inv2h) {
+__global__ void k_col_source(T* __restrict__ src, long lvl, long ps, long col0, int ncols,
+                             const B0Box* __restrict__ bx, int n_boxes, double inv2h) {
   const int c = blockIdx.x * blockDim.y + threadIdx.y, t = threadIdx.x;  // t < 6
   if (c >= ncols || t >= 6) return;
-  const int u = col0 + c, comp = u / n_sd, p = u - comp * n_sd;
-  const int I = i_lo + p % ni, J = j_lo + p / ni;
+  const long ug = col0 + c;
+  const B0Box b = bx[b0_find_box(bx, n_boxes, ug)];
+  const int u = (int)(ug - b.row_off), comp = u / b.n_sd, p = u - comp * b.n_sd;
+  const int I = b.i_lo + p % b.ni, J = b.j_lo + p / b.ni;
   int dx, dy;
   double w;
   stencil_entry(comp, t, inv2h, &dx, &dy, &w);
   src[(long)c * lvl + (long)(J + dy - 1) * ps + (I + dx - 1)] = T(w);
 }
 
-// row (col0 + c) of B0 <- E0 C s_c at every Omega_0 unknown r (stencil applied to the solved field)
+// row u of its box's B0 <- E0 C s_c at every Omega_0 unknown r of that box (stencil applied to the solved
+// field); blockIdx.y is the column of the batch
 template <typename T>
-__global__ void k_col_gather(double* __restrict__ B0, const T* __restrict__ s, long lvl, long ps, int col0,
-                             int ncols, int n_sd, int ni, int i_lo, int j_lo, double inv2h) {
+__global__ void k_col_gather(double* __restrict__ out, const T* __restrict__ s, long lvl, long ps, long col0,
+                             int ncols, const B0Box* __restrict__ bx, int n_boxes, double inv2h) {
   const int c = blockIdx.y;
-  const long n2 = 2L * n_sd;
+  if (c >= ncols) return;
+  const long ug = col0 + c;
+  const B0Box b = bx[b0_find_box(bx, n_boxes, ug)];
+  const long n2 = 2L * b.n_sd;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols || r >= n2) return;
-  const int comp = r / n_sd, p = r - comp * n_sd;
-  const int I = i_lo + p % ni, J = j_lo + p / ni;
+  if (r >= n2) return;
+  const int comp = r / b.n_sd, p = r - comp * b.n_sd;
+  const int I = b.i_lo + p % b.ni, J = b.j_lo + p / b.ni;
   const T* sc = s + (long)c * lvl;
   double acc = 0.0;
 #pragma unroll
@@ -62,7 +68,7 @@ __global__ void k_col_gather(double* __restrict__ B0, const T* __restrict__ s, l
     stencil_entry(comp, t, inv2h, &dx, &dy, &w);
     acc += w * (double)sc[(long)(J + dy) * ps + (I + dx)];
   }
-  B0[(long)(col0 + c) * n2 + r] = acc;
+  out[b.out_off + (ug - b.row_off) * n2 + r] = acc;
 }
 
 template <typename T>
@@ -95,12 +101,18 @@ Shape shape_for(int logL) {
 }
 
 template <typename T>
-fsi_status columns_t(fsi_ctx* c) {
+fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   using c2 = typename C2<T>::t;
   const int Nx = c->Nx, Ny = c->Ny;
   const long lvl = c->lvl_elems, ps = c->ps;
   const long t1 = (long)Nx * c->ldT, t2 = (long)Ny * c->ldX;
-  const int n2 = 2 * c->n_sd;
+  b0_layout(boxes);
+  const int n_boxes = (int)boxes.size();
+  long n2 = 0, max_n2 = 0;  // all columns of all boxes; longest column
+  for (const B0Box& b : boxes) {
+    n2 += 2L * b.n_sd;
+    if (2L * b.n_sd > max_n2) max_n2 = 2L * b.n_sd;
+  }
   const size_t per_col = ((size_t)3 * lvl + t1 + 2 * t2) * sizeof(T);
   size_t Bz = ((size_t)2 << 30) / per_col;  // batch of columns in ~2 GiB of scratch
   if (Bz > 256) Bz = 256;
@@ -108,8 +120,9 @@ fsi_status columns_t(fsi_ctx* c) {
   const int B = (int)Bz;
   set_attrs<T>();
   T *src = nullptr, *T1 = nullptr, *T2w = nullptr, *T2s = nullptr, *fw = nullptr, *fs = nullptr;
+  B0Box* d_bx = nullptr;
   fsi_status st = FSI_OK;
-  if (cudaMalloc(&src, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
+  if (cudaMalloc(&d_bx, (size_t)n_boxes * sizeof(B0Box)) != cudaSuccess || cudaMalloc(&src, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
       cudaMalloc(&T1, (size_t)B * t1 * sizeof(T)) != cudaSuccess ||
       cudaMalloc(&T2w, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
       cudaMalloc(&T2s, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
@@ -117,6 +130,9 @@ fsi_status columns_t(fsi_ctx* c) {
       cudaMalloc(&fs, (size_t)B * lvl * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     st = FSI_ERR_OOM;
+  } else if (cudaMemcpyAsync(d_bx, boxes.data(), (size_t)n_boxes * sizeof(B0Box), cudaMemcpyHostToDevice,
+                             c->stream) != cudaSuccess) {
+    st = FSI_ERR_CUDA;
   }
   const Shape cx = shape_for(c->logLx), cy = shape_for(c->logLy);
   const int Lx = 1 << c->logLx, Ly = 1 << c->logLy;
@@ -133,14 +149,13 @@ fsi_status columns_t(fsi_ctx* c) {
   sp.norm = 4.0 / ((double)c->Mx * (double)c->My);
   sp.Mx = c->Mx;
   sp.My = c->My;
-  for (int col0 = 0; st == FSI_OK && col0 < n2; col0 += B) {
-    const int nc = n2 - col0 < B ? n2 - col0 : B;
+  for (long col0 = 0; st == FSI_OK && col0 < n2; col0 += B) {
+    const int nc = n2 - col0 < B ? (int)(n2 - col0) : B;
     if (cudaMemsetAsync(src, 0, (size_t)nc * lvl * sizeof(T), c->stream) != cudaSuccess) {
       st = FSI_ERR_CUDA;
       break;
     }
-    k_col_source<T><<<(nc + 31) / 32, dim3(8, 32), 0, c->stream>>>(src, lvl, ps, col0, nc, c->n_sd, c->ni, c->i_lo,
-                                                                   c->j_lo, inv2h);
+    k_col_source<T><<<(nc + 31) / 32, dim3(8, 32), 0, c->stream>>>(src, lvl, ps, col0, nc, d_bx, n_boxes, inv2h);
     {
       dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
       const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
@@ -162,8 +177,8 @@ fsi_status columns_t(fsi_ctx* c) {
       else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
       else dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
     }
-    k_col_gather<T><<<dim3((n2 + 255) / 256, nc), 256, 0, c->stream>>>(c->B0, fs, lvl, ps, col0, nc, c->n_sd, c->ni,
-                                                                      c->i_lo, c->j_lo, inv2h);
+    k_col_gather<T><<<dim3((unsigned)((max_n2 + 255) / 256), nc), 256, 0, c->stream>>>(out, fs, lvl, ps, col0, nc,
+                                                                                       d_bx, n_boxes, inv2h);
     if (cudaGetLastError() != cudaSuccess) st = FSI_ERR_CUDA;
   }
   if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
@@ -173,14 +188,20 @@ fsi_status columns_t(fsi_ctx* c) {
   cudaFree(T2s);
   cudaFree(fw);
   cudaFree(fs);
+  cudaFree(d_bx);
   return st;
 }
 
 }  // namespace
 
+fsi_status b0_columns(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
+  return c->prec == FSI_PREC_FP64 ? columns_t<double>(c, boxes, out) : columns_t<float>(c, boxes, out);
+}
+
 fsi_status build_b0_columns(fsi_ctx* c) {
   auto t0 = std::chrono::steady_clock::now();
-  const fsi_status st = c->prec == FSI_PREC_FP64 ? columns_t<double>(c) : columns_t<float>(c);
+  std::vector<B0Box> one(1, ctx_box(c));
+  const fsi_status st = b0_columns(c, one, c->B0);
   c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
 }

@@ -101,6 +101,53 @@ struct fsi_ctx {
   std::vector<void*> allocs;
 };
 
+// One Omega_0 box of a B0 build.  Several boxes on one grid are built together; their matrices are stored
+// one after another, box k's (2 n_sd)^2 row-major block starting at out_off.
+struct B0Box {
+  int i_lo, j_lo, ni, nj, n_sd, pad;
+  long row_off;  // first unknown of this box in the concatenated unknown list (prefix sum of 2 n_sd)
+  long out_off;  // first entry of this box's matrix (prefix sum of (2 n_sd)^2)
+  long tab_off;  // first entry of this box's stencil tables (Green's-function method)
+};
+
+// box holding the global unknown u (boxes sorted by row_off)
+__device__ __forceinline__ int b0_find_box(const B0Box* bx, int n, long u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bx[mid].row_off <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Fills row_off and out_off from the box order; returns the total number of matrix entries.
+inline long b0_layout(std::vector<B0Box>& boxes) {
+  long rows = 0, entries = 0;
+  for (B0Box& b : boxes) {
+    b.n_sd = b.ni * b.nj;
+    b.row_off = rows;
+    b.out_off = entries;
+    rows += 2L * b.n_sd;
+    entries += 4L * b.n_sd * b.n_sd;
+  }
+  return entries;
+}
+
+// the context's own Omega_0 as a single box
+inline B0Box ctx_box(const fsi_ctx* c) {
+  B0Box b = {};
+  b.i_lo = c->i_lo;
+  b.j_lo = c->j_lo;
+  b.ni = c->ni;
+  b.nj = c->nj;
+  b.n_sd = c->n_sd;
+  return b;
+}
+
+// Snap a box to grid vertices and clip it to >= 2 cells from the boundary; FSI_ERR_INVALID_ARG if empty.
+fsi_status snap_box(const fsi_grid_desc& g, const fsi_box& b, int* i_lo, int* i_hi, int* j_lo, int* j_hi);
+
 // fluid.cu
 fsi_status launch_predictor(fsi_ctx* c, int first);
 fsi_status launch_corrector(fsi_ctx* c);
@@ -109,8 +156,10 @@ fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void*
 fsi_status launch_fsi(fsi_ctx* c);
 // b0.cu
 fsi_status build_b0(fsi_ctx* c);
+fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
 // b0_columns.cu
 fsi_status build_b0_columns(fsi_ctx* c);
+fsi_status b0_columns(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
 
 void* ctx_alloc(fsi_ctx* c, size_t bytes);
 

@@ -45,6 +45,23 @@ def b0_1024():
                 uinf=(1.0, 0.0), steps=0, sd_box=(-32 * h, 31 * h, -32 * h, 31 * h), bodies=[], ds=h)
 
 
+B0_UNEVEN_SIDES = (16, 19, 22, 25, 28, 32, 35, 38, 41, 44, 48, 51, 54, 57, 60, 64)
+
+
+def b0_1024_uneven_boxes(sides=B0_UNEVEN_SIDES, n=1024):
+    """Sixteen square Omega_0 boxes of side s points (256 ... 4096 points each) on the b0_1024 grid, one per
+    cell of a 4 x 4 arrangement of the domain (box k centred in cell k), as (x_lo, x_hi, y_lo, y_hi)."""
+    w = b0_1024() if n == 1024 else None
+    h, x0, y0 = (w["h"], w["x0"], w["y0"]) if w else (1.0 / 256, -2.0, -2.0)
+    cell = n // 4
+    boxes = []
+    for k, s in enumerate(sides):
+        cx, cy = cell // 2 + cell * (k % 4), cell // 2 + cell * (k // 4)
+        i_lo, j_lo = cx - s // 2, cy - s // 2
+        boxes.append((x0 + i_lo * h, x0 + (i_lo + s - 1) * h, y0 + j_lo * h, y0 + (j_lo + s - 1) * h))
+    return boxes
+
+
 def flag_512x256_3lvl_reduced_omega0():
     """flag_512x256_3lvl with Omega_0 cut to [-0.2,1.2]x[-0.25,0.35] (141 x 61 points, B0 2.4 GB); same
     kernels and small-system size, for profiler captures that must hold only a few GB."""

@@ -82,3 +82,73 @@ def test_config3_size_b0_columns_and_factor():
             worst = max(worst, abs(li @ lj - bij) / bmax)
     print("config-3 factor: tau %.3e, %.3f s, sampled backward error %.2e" % (tau, sec, worst))
     assert worst < 1e-12
+
+
+def _set_boxes_small():
+    # three boxes of different sizes and positions on a 64 x 64 grid, h = 1/16, corner (-2, -2)
+    return [(-1.5, -1.0, -1.5, -0.75), (-0.25, 0.75, 0.0, 0.5), (0.75, 1.625, -1.75, -1.25)]
+
+
+def test_b0_set_matches_single_box_builds_and_oracle():
+    """Several uneven Omega_0 boxes built in one pass equal, box by box, the single-box build (bitwise for
+    the Green's-function method) and the oracle's columns; the column-solve method agrees to 1e-12."""
+    import paper_2103_06415_gb300 as p
+    from oracle import grid as og
+    boxes = _set_boxes_small()
+    grid = dict(nx=64, ny=64, x0=-2.0, y0=-2.0, h=1.0 / 16, re=100.0, dt=0.004)
+    sg = p.B0Set(grid["nx"], grid["ny"], grid["x0"], grid["y0"], grid["h"], grid["re"], grid["dt"], boxes)
+    sc = p.B0Set(grid["nx"], grid["ny"], grid["x0"], grid["y0"], grid["h"], grid["re"], grid["dt"], boxes, method=1)
+    sf = p.B0Set(grid["nx"], grid["ny"], grid["x0"], grid["y0"], grid["h"], grid["re"], grid["dt"], boxes, method=1,
+                 precision=p.FSI_PREC_FP32)
+    lev = og.Level(grid["nx"], grid["ny"], grid["h"], grid["x0"], grid["y0"])
+    sizes = set()
+    for k, b in enumerate(boxes):
+        info = sg.box(k)
+        sd = oib.Subdomain.from_box(lev, *b)
+        assert (info["i_lo"], info["i_hi"], info["j_lo"], info["j_hi"]) == (sd.i_lo, sd.i_hi, sd.j_lo, sd.j_hi)
+        n2 = 2 * info["n_sd"]
+        sizes.add(n2)
+        r, c = np.meshgrid(np.arange(n2), np.arange(n2), indexing="ij")
+        g = sg.entries(k, r.ravel(), c.ravel())
+        w = dict(grid, name="one", n_levels=1, uinf=(1.0, 0.0), sd_box=b, bodies=[], ds=grid["h"])
+        one = gpu_context(w)
+        assert np.array_equal(g, one.operator_entries(r.ravel(), c.ravel()))
+        one.close()
+        scale = np.max(np.abs(g))
+        assert np.max(np.abs(sc.entries(k, r.ravel(), c.ravel()) - g)) < 1e-12 * scale
+        assert np.max(np.abs(sf.entries(k, r.ravel(), c.ravel()) - g)) < 2e-5 * scale
+        G = g.reshape(n2, n2)
+        for col in (0, n2 // 2 + 1, n2 - 1):
+            ref = oib.b0_column(sd, col, grid["re"], grid["dt"])
+            assert np.max(np.abs(G[:, col] - ref)) < 1e-12 * np.max(np.abs(ref))
+    assert len(sizes) == 3
+    for s in (sg, sc, sf):
+        s.close()
+
+
+def test_config3_sixteen_uneven_subdomains_in_one_build():
+    """Sixteen boxes of 256 ... 4096 points on the 1024^2 grid (h = 1/256, Re 500, dt = h/4), built together by
+    both methods: sampled columns of the smallest, a middle and the largest box against the oracle."""
+    import paper_2103_06415_gb300 as p
+    from oracle import grid as og
+    w = wl.b0_1024()
+    boxes = wl.b0_1024_uneven_boxes()
+    args = (w["nx"], w["ny"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], boxes)
+    sg = p.B0Set(*args)
+    sf = p.B0Set(*args, method=1, precision=p.FSI_PREC_FP32)
+    n_pts = [sg.box(k)["n_sd"] for k in range(16)]
+    assert n_pts[0] == 256 and n_pts[-1] == 4096 and len(set(n_pts)) == 16
+    lev = og.Level(w["nx"], w["ny"], w["h"], w["x0"], w["y0"])
+    rng = np.random.default_rng(13)
+    for k in (0, 7, 15):
+        sd = oib.Subdomain.from_box(lev, *boxes[k])
+        n2 = 2 * sd.n_sd
+        for col in rng.choice(n2, size=2, replace=False):
+            ref = oib.b0_column(sd, int(col), w["re"], w["dt"])
+            got = sg.entries(k, np.arange(n2), np.full(n2, col))
+            assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+            f32 = sf.entries(k, np.arange(n2), np.full(n2, col))
+            assert np.max(np.abs(f32 - ref)) < 2e-5 * np.max(np.abs(ref))
+    print("16 uneven boxes: green %.3f s, columns fp32 %.3f s" % (sg.stats()["seconds"], sf.stats()["seconds"]))
+    sg.close()
+    sf.close()

@@ -45,6 +45,24 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert lib.fsi_advance(None, 1) == 1
 
 
+def test_b0_set_arguments_are_rejected_without_a_gpu():
+    from paper_2103_06415_gb300 import _lib
+    import ctypes
+    lib = _lib.load()
+    g = _lib.GridDesc(64, 64, 1, -2.0, -2.0, 1.0 / 16, 100.0, 0.004, (ctypes.c_double * 2)(1, 0))
+    x = _lib.ExecDesc(0, None, 50, 1e-7, 16, 0, 0)
+    good = (_lib.Box * 1)(_lib.Box(-1.0, 1.0, -1.0, 1.0))
+    empty = (_lib.Box * 1)(_lib.Box(5.0, 6.0, 5.0, 6.0))          # outside the grid after clipping
+    h = ctypes.c_void_p()
+    assert lib.fsi_b0_set_build(ctypes.byref(g), ctypes.byref(x), good, 0, ctypes.byref(h)) == 1
+    assert lib.fsi_b0_set_build(None, ctypes.byref(x), good, 1, ctypes.byref(h)) == 1
+    assert lib.fsi_b0_set_build(ctypes.byref(g), ctypes.byref(x), empty, 1, ctypes.byref(h)) == 1
+    x.b0_method = 7
+    assert lib.fsi_b0_set_build(ctypes.byref(g), ctypes.byref(x), good, 1, ctypes.byref(h)) == 1
+    assert not h.value
+    assert lib.fsi_b0_set_box(None, 0, None, None, None, None, None) == 1
+
+
 def test_server_request_validation_without_a_gpu():
     import paper_2103_06415_gb300 as p
     from paper_2103_06415_gb300 import workloads as wl
