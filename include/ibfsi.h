@@ -78,6 +78,11 @@ typedef struct {
   int use_graph;
   int b0_method; /* 0: B0 from the lattice Green's function of (C^T A C)^{-1} (all columns at once, double);
                     1: one DST solve per column as in Algorithm 1, in the context's precision. Same matrix. */
+  int dst_method; /* sine transforms of the fluid solves (Sec. 3.2.1): 0 FFT passes; 1 dense sine-matrix GEMMs
+                     on the tensor cores (compensated 3xTF32, FP32 precision only, nx in [128, 1024], ny in [128, 512],
+                     otherwise FSI_ERR_UNSUPPORTED); 2 autotune: time both for each of the three passes at
+                     fsi_create and keep the faster (decisions are cached per grid shape for the process, so
+                     equal grids take equal paths); FP64 contexts and unsupported sizes then use FFT. */
 } fsi_exec_desc;
 
 /* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at
@@ -112,6 +117,8 @@ typedef struct {
   int launches_per_step; /* kernels this library launches per time step */
   int last_solves;       /* refinement solves of the small system in the last step (all FSI iterations) */
   int inverse_rebuilds;  /* times the float inverse of the small system was rebuilt so far */
+  int dst_gemm[3];       /* 1 if pass p (0 forward x, 1 y solve, 2 inverse x) runs as a tensor-core GEMM */
+  double dst_us[2][3];   /* autotuner timings in microseconds: [0] FFT, [1] GEMM, per pass (0 = not timed) */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;

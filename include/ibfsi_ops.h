@@ -20,6 +20,12 @@ extern "C" {
 fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt, const double* rhs,
                               double* w_out, double* s_out);
 
+/* The same solve with a choice of sine-transform implementation (fsi_exec_desc.dst_method): 0 FFT passes,
+ * 1 tensor-core sine-matrix GEMMs (FP32 only, nx in [128, 1024], ny in [128, 512]; otherwise FSI_ERR_UNSUPPORTED),
+ * 2 autotuned per pass. */
+fsi_status fsi_op_level_solve_ex(int precision, int dst_method, int nx, int ny, double h, double re, double dt,
+                                 const double* rhs, double* w_out, double* s_out);
+
 /* Allocation-free variant of fsi_op_level_solve for callers that cannot call cudaMalloc (for example code
  * running under a framework whose allocator owns all device memory, or a callback that must not allocate).
  * The paper has no counterpart: this is a service of this library.

@@ -25,14 +25,16 @@ class Context:
 
     grid: nx, ny (powers of two), n_levels, x0, y0, h, re, dt, uinf=(U, V)
     precision: FSI_PREC_FP64 or FSI_PREC_FP32; stream: a cudaStream_t handle (int) or None.
+    dst_method: 0 FFT sine transforms, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotune per pass.
     """
 
     def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
-                 stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0):
+                 stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0,
+                 dst_method=0):
         self._lib = _lib.load()
         g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
         x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
-                          1 if use_graph else 0, b0_method)
+                          1 if use_graph else 0, b0_method, dst_method)
         h_ = ctypes.c_void_p()
         check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
         self._h = h_
@@ -181,7 +183,10 @@ class Context:
     def stats(self):
         s = _lib.Stats()
         check(self._lib.fsi_get_stats(self._h, ctypes.byref(s)), "fsi_get_stats")
-        return {k: getattr(s, k) for k, _ in s._fields_}
+        out = {k: getattr(s, k) for k, _ in s._fields_}
+        out["dst_gemm"] = list(s.dst_gemm)
+        out["dst_us"] = {"fft": list(s.dst_us)[:3], "gemm": list(s.dst_us)[3:]}
+        return out
 
 
 class B0Set:
@@ -233,15 +238,16 @@ class B0Set:
             pass
 
 
-def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64):
-    """``w = A_w^{-1} rhs``, ``s = (-lap_h)^{-1} w`` on one level with zero boundary values (interior arrays)."""
+def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64, dst_method=0):
+    """``w = A_w^{-1} rhs``, ``s = (-lap_h)^{-1} w`` on one level with zero boundary values (interior arrays).
+    dst_method: 0 FFT passes, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotuned per pass."""
     lib = _lib.load()
     rhs = np.ascontiguousarray(rhs, dtype=np.float64)
     ny1, nx1 = rhs.shape
     w = np.zeros_like(rhs)
     s = np.zeros_like(rhs)
-    check(lib.fsi_op_level_solve(precision, nx1 + 1, ny1 + 1, h, re, dt, _dp(rhs), _dp(w), _dp(s)),
-          "fsi_op_level_solve")
+    check(lib.fsi_op_level_solve_ex(precision, dst_method, nx1 + 1, ny1 + 1, h, re, dt, _dp(rhs), _dp(w), _dp(s)),
+          "fsi_op_level_solve_ex")
     return w, s
 
 

@@ -31,7 +31,7 @@ class GridDesc(ctypes.Structure):
 class ExecDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("b0_method", ctypes.c_int)]
+                ("b0_method", ctypes.c_int), ("dst_method", ctypes.c_int)]
 
 
 class BodyDesc(ctypes.Structure):
@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int64), ("last_iters", ctypes.c_int), ("max_iters_seen", ctypes.c_int),
                 ("n_sd", ctypes.c_int), ("nf", ctypes.c_int), ("b0_seconds", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int),
-                ("last_solves", ctypes.c_int), ("inverse_rebuilds", ctypes.c_int)]
+                ("last_solves", ctypes.c_int), ("inverse_rebuilds", ctypes.c_int),
+                ("dst_gemm", ctypes.c_int * 3), ("dst_us", ctypes.c_double * 6)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +83,8 @@ SIGNATURES = {
     "fsi_get_phase_times": (_INT, [_P, _D, _INT]),
     "fsi_destroy": (None, [_P]),
     "fsi_op_level_solve": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D]),
+    "fsi_op_level_solve_ex": (_INT, [_INT, _INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,
+                                     _D, _D]),
     "fsi_op_fma_rate": (_INT, [_INT, _D]),
     "fsi_op_level_solve_noalloc": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _P, _P, _P, _P]),

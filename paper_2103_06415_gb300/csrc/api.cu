@@ -3,6 +3,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 #include "internal.h"
@@ -165,6 +168,79 @@ static fsi_status create_impl(fsi_ctx* c) {
   return FSI_OK;
 }
 
+// Time each sine-transform pass of a level solve (level 0, zero right-hand side, zero fields) with CUDA
+// events around every launch of that pass; avg_us[p] for the current dst_gemm choice.
+static fsi_status time_dst_passes(fsi_ctx* c, int reps, double* avg_us) {
+  for (int k = 0; k < 3; ++k) TRY(launch_level_solve(c, 0, c->src, c->w_all, c->s_all, 0, 0));  // warm-up
+  for (int p = 0; p < 3; ++p) {
+    c->prof_ev.assign(2 * reps, nullptr);
+    fsi_status st = FSI_OK;
+    for (cudaEvent_t& e : c->prof_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) st = FSI_ERR_CUDA;
+    c->prof_class = KC_XF + p;
+    c->prof_used = 0;
+    for (int r = 0; st == FSI_OK && r < reps; ++r) st = launch_level_solve(c, 0, c->src, c->w_all, c->s_all, 0, 0);
+    c->prof_class = KC_NONE;
+    if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+    double sum = 0.0;
+    int n = 0;
+    for (int k = 0; st == FSI_OK && k + 1 < c->prof_used; k += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->prof_ev[k], c->prof_ev[k + 1]) != cudaSuccess) st = FSI_ERR_CUDA;
+      sum += ms;
+      ++n;
+    }
+    for (cudaEvent_t e : c->prof_ev)
+      if (e) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_used = 0;
+    if (st != FSI_OK) return st;
+    avg_us[p] = n ? 1e3 * sum / n : 0.0;
+  }
+  return FSI_OK;
+}
+
+// Choose FFT or tensor-core GEMM for each sine-transform pass (fsi_exec_desc.dst_method).  Autotuned
+// choices are cached per grid shape so every context of one process with that grid takes the same path.
+static fsi_status dst_select(fsi_ctx* c) {
+  const int m = c->x.dst_method;
+  if (m == 0 || c->prec != FSI_PREC_FP32 || !gemm_dst_supported(c->nx, c->ny)) return FSI_OK;
+  fsi_status st = gemm_dst_setup(c);
+  if (st != FSI_OK) {
+    gemm_dst_free(c);
+    return m == 1 ? st : FSI_OK;  // autotune falls back to the FFT passes
+  }
+  if (m == 1) {
+    c->dst_gemm[0] = c->dst_gemm[1] = c->dst_gemm[2] = 1;
+    return FSI_OK;
+  }
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, std::array<double, 6>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  const std::pair<int, int> key(c->nx, c->ny);
+  auto it = cache.find(key);
+  std::array<double, 6> us{};
+  if (it != cache.end()) {
+    us = it->second;
+  } else {
+    for (int impl = 0; impl < 2; ++impl) {
+      c->dst_gemm[0] = c->dst_gemm[1] = c->dst_gemm[2] = impl;
+      TRY(time_dst_passes(c, 20, &us[3 * impl]));
+    }
+    int dev_status = 0;
+    FSI_CUDA_TRY(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_status != 0) return (fsi_status)dev_status;
+    cache[key] = us;
+  }
+  for (int p = 0; p < 3; ++p) {
+    c->dst_us[0][p] = us[p];
+    c->dst_us[1][p] = us[3 + p];
+    c->dst_gemm[p] = us[3 + p] < us[p] ? 1 : 0;
+  }
+  c->launches_per_step = 0;
+  return FSI_OK;
+}
+
 extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc* exec, fsi_ctx** out) {
   if (!grid || !out) return FSI_ERR_INVALID_ARG;
   *out = nullptr;
@@ -176,9 +252,14 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
   c->g = *grid;
   memset(&c->x, 0, sizeof(c->x));
   if (exec) c->x = *exec;
-  if (c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32) {
+  if ((c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32) || c->x.dst_method < 0 ||
+      c->x.dst_method > 2) {
     delete c;
     return FSI_ERR_INVALID_ARG;
+  }
+  if (c->x.dst_method == 1 && (c->x.precision != FSI_PREC_FP32 || !gemm_dst_supported(grid->nx, grid->ny))) {
+    delete c;
+    return FSI_ERR_UNSUPPORTED;
   }
   if (c->x.max_iters <= 0) c->x.max_iters = 50;
   if (!(c->x.tol > 0)) c->x.tol = 1e-7;
@@ -197,7 +278,9 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
   }
   c->first_pending = 1;
   fsi_status st = create_impl(c);
+  if (st == FSI_OK) st = dst_select(c);
   if (st != FSI_OK) {
+    gemm_dst_free(c);
     ctx_free_all(c);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -618,6 +701,11 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   out->b0_seconds = c->b0_seconds;
   out->device_bytes = c->dev_bytes;
   out->launches_per_step = c->launches_per_step;
+  for (int p = 0; p < 3; ++p) {
+    out->dst_gemm[p] = c->dst_gemm[p];
+    out->dst_us[0][p] = c->dst_us[0][p];
+    out->dst_us[1][p] = c->dst_us[1][p];
+  }
   if (c->d_ctrl) {
     FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
     int ctrl[12];
@@ -634,6 +722,7 @@ extern "C" void fsi_destroy(fsi_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
+  gemm_dst_free(c);
   ctx_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -2,6 +2,7 @@
 // multidomain coupling (Sec. 5, far-field multidomain), the DST-diagonalised predictor solves
 // (Eq. predictor2) and the corrector (Eq. corrector2) with its surface-stress source.
 #include <cstdio>
+#include <type_traits>
 #include "dst.cuh"
 #include "internal.h"
 
@@ -198,6 +199,12 @@ __global__ void __launch_bounds__(256) k_src(T* __restrict__ src, long ps, int n
 }
 
 // ---------------------------------------------------------------------------------------------
+// Pass p of the sine transforms runs as a tensor-core GEMM (FP32 contexts that chose it; dst_gemm.cu).
+template <typename T>
+bool use_gemm(const fsi_ctx* c, int p) {
+  return std::is_same<T, float>::value && c->gd && c->dst_gemm[p];
+}
+
 template <typename T>
 fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ring, int mode) {
   using c2 = typename C2<T>::t;
@@ -208,7 +215,10 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
   const c2* twy = (const c2*)c->twy;
   // XF
   prof_mark(c, KC_XF);
-  {
+  if (use_gemm<T>(c, 0)) {
+    const fsi_status st = gemm_xf(c, (const float*)rhs);
+    if (st != FSI_OK) return st;
+  } else {
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
     const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
     switch (cx.per) {
@@ -237,18 +247,28 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     sp.norm = 4.0 / ((double)c->Mx * (double)c->My);
     sp.Mx = c->Mx;
     sp.My = c->My;
-    dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
-    const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
-    switch (cy.per) {
-      case 1: dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
-      case 2: dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
-      default: dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
+    if (use_gemm<T>(c, 1)) {
+      if constexpr (std::is_same<T, float>::value) {
+        const fsi_status st = gemm_ysolve(c, sp);
+        if (st != FSI_OK) return st;
+      }
+    } else {
+      dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
+      const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
+      switch (cy.per) {
+        case 1: dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
+        case 2: dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
+        default: dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
+      }
     }
   }
   prof_mark(c, KC_YSOLVE);
   // XI: 2*nf rows per CTA; rows j, j+1 of w share one FFT, rows j, j+1 of s another
   prof_mark(c, KC_XI);
-  {
+  if (use_gemm<T>(c, 2)) {
+    const fsi_status st = gemm_xi(c, (float*)w, (float*)s, mode);
+    if (st != FSI_OK) return st;
+  } else {
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
     const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
     switch (cx.per) {

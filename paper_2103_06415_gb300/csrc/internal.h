@@ -97,6 +97,11 @@ struct fsi_ctx {
   std::vector<cudaEvent_t> prof_ev;
   int prof_used;
   int launches_per_step;
+  // sine-transform passes: dst_gemm[p] = 1 runs pass p (0 forward x, 1 y solve, 2 inverse x) as a
+  // tensor-core GEMM (dst_gemm.cu) instead of the FFT pass; dst_us = autotuner timings [FFT, GEMM][pass]
+  int dst_gemm[3];
+  double dst_us[2][3];
+  struct GemmDst* gd;
   size_t dev_bytes;
   std::vector<void*> allocs;
 };
@@ -160,6 +165,15 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
 // b0_columns.cu
 fsi_status build_b0_columns(fsi_ctx* c);
 fsi_status b0_columns(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
+
+// dst_gemm.cu
+bool gemm_dst_supported(int nx, int ny);
+fsi_status gemm_dst_setup(fsi_ctx* c);
+void gemm_dst_free(fsi_ctx* c);
+fsi_status gemm_xf(fsi_ctx* c, const float* rhs);
+namespace dst { template <typename T> struct SpecParams; }
+fsi_status gemm_ysolve(fsi_ctx* c, const dst::SpecParams<float>& sp);
+fsi_status gemm_xi(fsi_ctx* c, float* fw, float* fs, int mode);
 
 void* ctx_alloc(fsi_ctx* c, size_t bytes);
 

@@ -5,6 +5,11 @@
 
 extern "C" fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt,
                                          const double* rhs, double* w_out, double* s_out) {
+  return fsi_op_level_solve_ex(precision, 0, nx, ny, h, re, dt, rhs, w_out, s_out);
+}
+
+extern "C" fsi_status fsi_op_level_solve_ex(int precision, int dst_method, int nx, int ny, double h, double re,
+                                            double dt, const double* rhs, double* w_out, double* s_out) {
   if (!rhs || !w_out || !s_out) return FSI_ERR_INVALID_ARG;
   fsi_grid_desc g = {};
   g.nx = nx;
@@ -15,6 +20,7 @@ extern "C" fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h
   g.dt = dt;
   fsi_exec_desc x = {};
   x.precision = precision;
+  x.dst_method = dst_method;
   fsi_ctx* c = nullptr;
   fsi_status st = fsi_create(&g, &x, &c);
   if (st != FSI_OK) return st;
