@@ -190,14 +190,17 @@ fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);
 /* Tracing: accumulated wall time (ms) of the phases of the FSI-iteration kernel since the context was
  * created, measured on the device: 0 body points / P / right-hand side, 1 assembly of P B0 P^T, 2 refresh
  * of the float inverse, 3 rebuild of the float inverse, 4 refinement solves, 5 double residuals,
- * 6 dtheta and convergence, 7 outputs.  out[0..n-1] (n <= 8 meaningful; synchronising). */
+ * 6 dtheta and convergence, 7 outputs; a finer split of 2, 4 and 5: 8 columns of X K, 9 rows of the new
+ * X, 10 reload of X, 11 d = X r, 12 residual rows and barrier, 13 residual gather.
+ * out[0..n-1] (n <= 16 meaningful; synchronising). */
 fsi_status fsi_get_phase_times(fsi_ctx* ctx, double* out, int n);
 
 /* Live timing of one kernel class: runs n_steps (1..1024) ordinary time steps without a graph, records a
  * CUDA event pair on the context stream around every launch of that class and returns the mean launch
  * duration in ms and the number of timed launches.  The steps advance the simulation like fsi_advance.
  * Classes: 1 forward-x DST pass, 2 y-solve DST pass, 3 inverse-x DST pass, 4 FSI iteration kernel,
- * 5 advection/right-hand side, 6 corrector source, 7 level boundary, 8 boundary-side DSTs, 9 injection. */
+ * 5 advection/right-hand side (with the fine-to-coarse injection), 6 corrector source, 7 level boundary
+ * with its side transforms. */
 fsi_status fsi_profile_kernel(fsi_ctx* ctx, int kernel_class, int n_steps, double* avg_ms, int* launches);
 
 /* Free all device memory and the handle (synchronises the stream first). */

@@ -161,8 +161,7 @@ class Context:
                                        n_points), "fsi_get_interp")
         return idx.reshape(-1, 4), w.reshape(-1, 4)
 
-    KERNEL_CLASSES = {"xf": 1, "ysolve": 2, "xi": 3, "fsi": 4, "rhs": 5, "src": 6, "ring": 7, "vecdst": 8,
-                      "inject": 9}
+    KERNEL_CLASSES = {"xf": 1, "ysolve": 2, "xi": 3, "fsi": 4, "rhs": 5, "src": 6, "ring": 7}
 
     def profile_kernel(self, name, n_steps):
         """Run n_steps eager steps timing every launch of one kernel class; returns (mean ms, launches)."""
@@ -172,12 +171,13 @@ class Context:
         return ms.value, n.value
 
     PHASES = ("points_rhs", "assemble_PB0PT", "inverse_refresh", "inverse_rebuild", "refine_solves",
-              "residuals", "dtheta", "outputs")
+              "residuals", "dtheta", "outputs", "ns_xk_columns", "ns_new_x_rows", "ns_reload_x", "solve_d",
+              "residual_rows_barrier", "residual_gather")
 
     def phase_times(self):
         """Accumulated device wall time (ms) per phase of the FSI-iteration kernel."""
-        out = np.zeros(8)
-        check(self._lib.fsi_get_phase_times(self._h, _dp(out), 8), "fsi_get_phase_times")
+        out = np.zeros(16)
+        check(self._lib.fsi_get_phase_times(self._h, _dp(out), 16), "fsi_get_phase_times")
         return dict(zip(self.PHASES, out.tolist()))
 
     def stats(self):

@@ -10,8 +10,9 @@
 #include <vector>
 #include "internal.h"
 
-int fsi_kernel_max_ctas_per_sm(int nf);
-size_t fsi_smem_bytes(int nf);
+int fsi_kernel_max_ctas_per_sm(int nf, int nb);
+size_t fsi_smem_bytes(int nf, int nb);
+int fsi_min_grid(int nf);
 
 static thread_local char g_errmsg[512] = "";
 
@@ -81,6 +82,15 @@ static fsi_status upload_d(fsi_ctx* c, const std::vector<double>& v, double** ou
   return FSI_OK;
 }
 
+static fsi_status upload_f(fsi_ctx* c, const std::vector<double>& v, void** out) {
+  std::vector<float> f(v.begin(), v.end());
+  *out = ctx_alloc(c, f.size() * 4);
+  if (!*out) return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaMemcpyAsync(*out, f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));  // f is a temporary
+  return FSI_OK;
+}
+
 #define TRY(x)                       \
   do {                               \
     fsi_status _s = (x);             \
@@ -129,6 +139,21 @@ static fsi_status create_impl(fsi_ctx* c) {
   TRY(upload_d(c, sxN, &c->sxN));
   TRY(upload_d(c, sy1, &c->sy1));
   TRY(upload_d(c, syN, &c->syN));
+  if (c->prec == FSI_PREC_FP64) {
+    c->lxT = c->lx;
+    c->lyT = c->ly;
+    c->sx1T = c->sx1;
+    c->sxNT = c->sxN;
+    c->sy1T = c->sy1;
+    c->syNT = c->syN;
+  } else {
+    TRY(upload_f(c, lx, &c->lxT));
+    TRY(upload_f(c, ly, &c->lyT));
+    TRY(upload_f(c, sx1, &c->sx1T));
+    TRY(upload_f(c, sxN, &c->sxNT));
+    TRY(upload_f(c, sy1, &c->sy1T));
+    TRY(upload_f(c, syN, &c->syNT));
+  }
   if (c->prec == FSI_PREC_FP64) {
     TRY(upload_twiddles<double>(c, 2 * c->Mx, &c->twx));
     TRY(upload_twiddles<double>(c, 2 * c->My, &c->twy));
@@ -377,8 +402,8 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   if (!c->have_sd) return FSI_ERR_STATE;
   c->n_bodies = (int)c->bodies.size();
   c->nf = 2 * c->nb;
-  if (c->n_bodies > 256) return FSI_ERR_UNSUPPORTED;
-  if (c->nb > 0 && fsi_smem_bytes(c->nf) > 200 * 1024) return FSI_ERR_UNSUPPORTED;
+  if (c->n_bodies > 64) return FSI_ERR_UNSUPPORTED;
+  if (c->nb > 0 && fsi_smem_bytes(c->nf, c->nb) > 200 * 1024) return FSI_ERR_UNSUPPORTED;
   const size_t n2 = 2 * (size_t)c->n_sd;
   if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
   fsi_status st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
@@ -417,13 +442,14 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_pidx = (int*)ctx_alloc(c, (size_t)c->nb * 4 * sizeof(int))) ||
         !(c->d_pw = (double*)ctx_alloc(c, (size_t)c->nb * 4 * 8)) ||
         !(c->d_sv = (double*)ctx_alloc(c, (size_t)c->nb * 2 * 8)) ||
-        !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 2 * 8)) ||
+        !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 3 * 8)) ||
         !(c->d_K = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)) ||
         !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
         !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
         !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
-        !(c->d_phase = (unsigned long long*)ctx_alloc(c, 8 * sizeof(unsigned long long))) ||
+        !(c->d_T = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_phase = (unsigned long long*)ctx_alloc(c, 16 * sizeof(unsigned long long))) ||
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
@@ -435,9 +461,10 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf);
+    const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf, c->nb);
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
-    c->fsi_grid = nsm < 64 ? nsm : 64;  // enough CTAs for the 32x32 GEMM tiles; fewer -> cheaper barriers
+    c->fsi_grid = nsm;  // one CTA per SM: spreads the B0 gathers and the FP64 work, fewest rows per CTA
+    if (c->fsi_grid < fsi_min_grid(c->nf)) return FSI_ERR_UNSUPPORTED;
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;
@@ -509,7 +536,7 @@ extern "C" fsi_status fsi_advance(fsi_ctx* c, int n_steps) {
 
 extern "C" fsi_status fsi_profile_kernel(fsi_ctx* c, int kernel_class, int n_steps, double* avg_ms,
                                          int* launches) {
-  if (!c || kernel_class < KC_XF || kernel_class > KC_INJECT || n_steps < 1 || n_steps > 1024 || !avg_ms ||
+  if (!c || kernel_class < KC_XF || kernel_class > KC_RING || n_steps < 1 || n_steps > 1024 || !avg_ms ||
       !launches)
     return FSI_ERR_INVALID_ARG;
   if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
@@ -549,9 +576,9 @@ extern "C" fsi_status fsi_get_phase_times(fsi_ctx* c, double* ms, int n) {
   for (int k = 0; k < n; ++k) ms[k] = 0.0;
   if (!c->d_phase) return FSI_OK;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  unsigned long long ns[8];
+  unsigned long long ns[16];
   FSI_CUDA_TRY(cudaMemcpy(ns, c->d_phase, sizeof(ns), cudaMemcpyDeviceToHost));
-  for (int k = 0; k < n && k < 8; ++k) ms[k] = (double)ns[k] * 1e-6;
+  for (int k = 0; k < n && k < 16; ++k) ms[k] = (double)ns[k] * 1e-6;
   return FSI_OK;
 }
 

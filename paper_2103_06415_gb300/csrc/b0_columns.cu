@@ -7,8 +7,7 @@
 // The arithmetic precision of the solves is the context's (float or double); B0 is stored in double.
 #include <chrono>
 #include <vector>
-#include "dst.cuh"
-#include "internal.h"
+#include "spec.cuh"
 
 namespace {
 
@@ -139,16 +138,7 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   const c2* twx = (const c2*)c->twx;
   const c2* twy = (const c2*)c->twy;
   const double h = c->g.h, inv2h = 0.5 / h;
-  dst::SpecParams<T> sp = {};
-  sp.lx = c->lx;
-  sp.ly = c->ly;
-  sp.ring = nullptr;
-  sp.inv_h2 = 1.0 / (h * h);
-  sp.inv_dt = 1.0 / c->g.dt;
-  sp.inv_2re = 0.5 / c->g.re;
-  sp.norm = 4.0 / ((double)c->Mx * (double)c->My);
-  sp.Mx = c->Mx;
-  sp.My = c->My;
+  const dst::SpecParams<T> sp = spec_params<T>(c, h, nullptr);
   for (long col0 = 0; st == FSI_OK && col0 < n2; col0 += B) {
     const int nc = n2 - col0 < B ? (int)(n2 - col0) : B;
     if (cudaMemsetAsync(src, 0, (size_t)nc * lvl * sizeof(T), c->stream) != cudaSuccess) {

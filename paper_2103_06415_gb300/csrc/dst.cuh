@@ -141,18 +141,20 @@ __device__ __forceinline__ void put_one(typename C2<T>::t* z, int L, int n, T a,
 
 // Diagonal scaling data for pass Y (Sec. 3.2.1): A_w = 1/dt + lambda/(2 Re), lambda = (lx_k + ly_l)/h^2
 // with lx_k = 4 sin^2(pi k/(2 Mx)).  Boundary-ring terms of a nested level enter as a rank-4 sum over the
-// sine transforms of the four ring sides (left/right along y, bottom/top along x).
+// sine transforms of the four ring sides (left/right along y, bottom/top along x).  Tables and constants
+// are in the precision of the pass (no double arithmetic per element in the FP32 path).
 template <typename T>
 struct SpecParams {
-  const double* lx;   // [Mx] (index k = 1..Nx used)
-  const double* ly;   // [My]
-  const double* sx1;  // sin(pi k/Mx)
-  const double* sxN;  // sin(pi k Nx/Mx)
-  const double* sy1;
-  const double* syN;
-  const T* ring;      // 8 spectra: wL wR (len Ny) wB wT (len Nx) sL sR sB sT, each stride ring_ld; NULL = no ring
+  const T* lx;   // [Mx] (index k = 1..Nx used)
+  const T* ly;   // [My]
+  const T* sx1;  // sin(pi k/Mx)
+  const T* sxN;  // sin(pi k Nx/Mx)
+  const T* sy1;
+  const T* syN;
+  const T* ring;  // 8 spectra: wL wR (len Ny) wB wT (len Nx) sL sR sB sT, each stride ring_ld; NULL = no ring
   long ring_ld;
-  double inv_h2, inv_dt, inv_2re, norm;  // norm = 4/(Mx My)
+  T inv_h2, inv_dt, inv_2re, norm;  // norm = 4/(Mx My)
+  T ring_w;                         // inv_2re * inv_h2
   int Mx, My;
 };
 
@@ -228,23 +230,23 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     T rh = (r & 1) ? T(0.5) * z.x : T(-0.5) * z.y;
     T wt, st;
     if (k <= nrows) {
-      const T lam = T((sp.lx[k] + sp.ly[l]) * sp.inv_h2);
-      const T aw = T(sp.inv_dt) + lam * T(sp.inv_2re);
+      const T lam = (sp.lx[k] + sp.ly[l]) * sp.inv_h2;
+      const T aw = sp.inv_dt + lam * sp.inv_2re;
       T bcs = T(0);
       if (ring) {
         const int Nx = nrows;
-        const T bw = T(sp.sx1[k]) * ring[0 * sp.ring_ld + l0] + T(sp.sxN[k]) * ring[1 * sp.ring_ld + l0] +
-                     ring[2 * sp.ring_ld + (k - 1)] * T(sp.sy1[l]) + ring[3 * sp.ring_ld + (k - 1)] * T(sp.syN[l]);
-        bcs = T(sp.sx1[k]) * ring[4 * sp.ring_ld + l0] + T(sp.sxN[k]) * ring[5 * sp.ring_ld + l0] +
-              ring[6 * sp.ring_ld + (k - 1)] * T(sp.sy1[l]) + ring[7 * sp.ring_ld + (k - 1)] * T(sp.syN[l]);
-        rh += bw * T(sp.inv_2re * sp.inv_h2);
-        bcs *= T(sp.inv_h2);
+        const T bw = sp.sx1[k] * ring[0 * sp.ring_ld + l0] + sp.sxN[k] * ring[1 * sp.ring_ld + l0] +
+                     ring[2 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[3 * sp.ring_ld + (k - 1)] * sp.syN[l];
+        bcs = sp.sx1[k] * ring[4 * sp.ring_ld + l0] + sp.sxN[k] * ring[5 * sp.ring_ld + l0] +
+              ring[6 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[7 * sp.ring_ld + (k - 1)] * sp.syN[l];
+        rh += bw * sp.ring_w;
+        bcs *= sp.inv_h2;
         (void)Nx;
       }
       wt = rh / aw;
       st = (wt + bcs) / lam;
-      wt *= T(sp.norm);
-      st *= T(sp.norm);
+      wt *= sp.norm;
+      st *= sp.norm;
     } else {
       wt = T(0);
       st = T(0);
@@ -314,32 +316,6 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
         fs[o] -= s;
       }
     }
-  }
-}
-
-// Plain DST of strided vectors (used for the four ring sides): vectors v = 2*blockIdx.x + {0, 1} are read
-// from srcs[v] with element stride es[v] and written contiguously to dsts[v].
-template <typename T, int PER>
-__global__ void __launch_bounds__(256) k_vec_dst(const T* const* __restrict__ srcs, const long* __restrict__ es,
-                                                 int nvec, int N, T* const* __restrict__ dsts,
-                                                 const typename C2<T>::t* __restrict__ tw, int logL) {
-  using c2 = typename C2<T>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2* buf = reinterpret_cast<c2*>(smem_raw);
-  const int L = 1 << logL;
-  const int v0 = blockIdx.x * 2;
-  zero_ends<T>(buf, 1, L);
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    const T a = (v0 < nvec) ? srcs[v0][(long)n * es[v0]] : T(0);
-    const T b = (v0 + 1 < nvec) ? srcs[v0 + 1][(long)n * es[v0 + 1]] : T(0);
-    put_pair<T>(buf, L, n, a, b);
-  }
-  __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tw);
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    const c2 z = buf[n + 1];
-    if (v0 < nvec) dsts[v0][n] = T(-0.5) * z.y;
-    if (v0 + 1 < nvec) dsts[v0 + 1][n] = T(0.5) * z.x;
   }
 }
 

@@ -11,8 +11,9 @@
 //   G3  f[y][x]      = sum_kx S_x[x][kx] T2f[y][kx]             (A = S_x, B = T2f; M = x,  N = y)
 // Products are compensated 3xTF32: each fp32 operand is split into tf32 hi + lo and the MMA chain
 // accumulates hi*hi + hi*lo + lo*hi in fp32 (about 2^-21 relative per product, the accuracy class of the
-// FP32 FFT); partial sums of 32 products are added in fp32 registers (see Pipe).  The sine matrices are split once on the host and streamed by TMA; data operands are read by
-// the threads, split in registers and written to shared memory in the swizzled operand layout.
+// FP32 FFT); partial sums of 32 products are added in fp32 registers (see Pipe).  The sine matrices are
+// split once on the host and streamed by TMA; data operands are read by the threads, split in registers
+// and written to shared memory in the swizzled operand layout.
 //
 // Bounded waits: every mbarrier wait gives up after 2 s of wall time; the kernel then records
 // FSI_ERR_TIMEOUT, stops issuing work, waits (bounded) for its own copies and MMAs in flight, frees its
@@ -31,30 +32,33 @@ namespace {
 
 constexpr int kThr = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr int kNT = 32;  // N tile of G1 and G3
+constexpr int kNT = 32;   // N tile of G1 and G3
+constexpr int kNS13 = 4;  // operand stages of G1 and G3
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   const uint32_t a = tc::smem_u32(p);
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
-// Per-CTA pipeline state in shared memory.  Two operand stages and two TMEM accumulators alternate: the
-// MMAs of stage t write accumulator t % 2 from zero, and the threads add it into fp32 registers one stage
-// later ("fold"), so the tensor core never accumulates more than 32 products of a sum (its fp32
-// accumulation error would otherwise grow with the transform length).
+// Per-CTA pipeline state in shared memory.  NS operand stages and two TMEM accumulators: the MMAs of stage
+// t write accumulator t % 2 from zero and the threads add it into fp32 registers one stage later ("fold"),
+// so the tensor core never accumulates more than 32 products of a sum (its fp32 accumulation error would
+// otherwise grow with the transform length).  TMA loads of the constant operand run NS-1 stages ahead.
+constexpr int kMaxStages = 4;
 struct Pipe {
-  uint64_t full[2];   // TMA tiles of stage s landed
-  uint64_t done[2];   // MMAs of stage s completed
-  uint32_t tmem;      // TMEM base address
-  int abort;          // a wait gave up
-  int tma_issued;     // stages whose TMA was issued (thread 0)
-  int tma_seen;       // stages whose TMA completion was observed (thread 0)
-  int committed;      // stages committed (thread 0)
+  uint64_t full[kMaxStages];  // TMA tiles of stage s landed
+  uint64_t done[kMaxStages];  // MMAs of stage s completed
+  uint32_t tmem;              // TMEM base address
+  int abort;                  // a wait gave up
+  int tma_issued;             // stages whose TMA was issued (thread 0)
+  int tma_seen;               // stages whose TMA completion was observed (thread 0)
+  int committed;              // stages committed (thread 0)
 };
 
+template <int NS>
 __device__ __forceinline__ void pipe_init(Pipe* p) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&p->full[s], 1);
       tc::mbar_init(&p->done[s], 1);
     }
@@ -69,21 +73,24 @@ __device__ __forceinline__ void pipe_init(Pipe* p) {
 // store(s, regs): split and write it into buffers s; mma(t, s, acc): thread 0 issues the MMAs of stage t
 // into TMEM column acc (accumulate from zero); fold(t, acc): every thread adds accumulator acc of stage t
 // into its registers (and writes results at the end of a sum).  Returns false if a wait gave up.
-template <class Tma, class Load, class Store, class Mma, class Fold>
+// Buffer reuse: at stage t the MMAs of stage t-1 (and so all earlier ones) are complete before the
+// barrier, so buffers t % NS (last read at t-NS) and (t-1) % NS (refilled by the TMA of stage t+NS-1)
+// are free.
+template <int NS, class Tma, class Load, class Store, class Mma, class Fold>
 __device__ __forceinline__ bool run_pipeline(Pipe* p, int T, uint32_t acc0, uint32_t acc1, Tma tma, Load load,
                                              Store store, Mma mma, Fold fold) {
-  if (threadIdx.x == 0 && T > 0) {
-    tma(0, 0, &p->full[0]);
-    p->tma_issued = 1;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < NS - 1 && t < T; ++t) tma(t, t, &p->full[t]);
+    p->tma_issued = T < NS - 1 ? T : NS - 1;
   }
   auto regs = load(0);
   for (int t = 0; t < T; ++t) {
-    const int s = t & 1;
-    store(s, regs);  // buffers s were last read by the MMAs of stage t-2, complete (waited at stage t-1)
+    const int s = t % NS;
+    store(s, regs);
     if (t + 1 < T) regs = load(t + 1);
     tc::fence_async_smem();
     if (t >= 1) {
-      if (!tc::mbar_wait(&p->done[(t - 1) & 1], (uint32_t)((t - 1) >> 1) & 1u, kWaitNs)) p->abort = 1;
+      if (!tc::mbar_wait(&p->done[(t - 1) % NS], (uint32_t)((t - 1) / NS) & 1u, kWaitNs)) p->abort = 1;
       tc::tc_fence_after();
       if (!p->abort) fold(t - 1, (t - 1) & 1 ? acc1 : acc0);
       tc::fence_async_smem();
@@ -92,23 +99,24 @@ __device__ __forceinline__ bool run_pipeline(Pipe* p, int T, uint32_t acc0, uint
     __syncthreads();
     if (p->abort) return false;
     if (threadIdx.x == 0) {
-      if (t + 1 < T) {  // buffers (t+1)&1 were last read by the MMAs of stage t-1, complete
-        tma(t + 1, (t + 1) & 1, &p->full[(t + 1) & 1]);
-        p->tma_issued = t + 2;
+      const int tn = t + NS - 1;
+      if (tn < T) {
+        tma(tn, tn % NS, &p->full[tn % NS]);
+        p->tma_issued = tn + 1;
       }
-      if (!tc::mbar_wait(&p->full[s], (uint32_t)(t >> 1) & 1u, kWaitNs)) {
+      if (!tc::mbar_wait(&p->full[s], (uint32_t)(t / NS) & 1u, kWaitNs)) {
         p->abort = 1;
       } else {
         p->tma_seen = t + 1;
         tc::tc_fence_after();
-        mma(t, s, s ? acc1 : acc0);
+        mma(t, s, (t & 1) ? acc1 : acc0);
         tc::mma_commit(&p->done[s]);
         p->committed = t + 1;
       }
     }
   }
   if (T > 0) {
-    if (!tc::mbar_wait(&p->done[(T - 1) & 1], (uint32_t)((T - 1) >> 1) & 1u, kWaitNs)) p->abort = 1;
+    if (!tc::mbar_wait(&p->done[(T - 1) % NS], (uint32_t)((T - 1) / NS) & 1u, kWaitNs)) p->abort = 1;
     tc::tc_fence_after();
     if (!p->abort) fold(T - 1, (T - 1) & 1 ? acc1 : acc0);
   }
@@ -117,14 +125,15 @@ __device__ __forceinline__ bool run_pipeline(Pipe* p, int T, uint32_t acc0, uint
 }
 
 // Error path: wait (bounded) for this CTA's copies and MMAs in flight, record the status.
+template <int NS>
 __device__ __forceinline__ void pipe_abort_cleanup(Pipe* p, int* status) {
   if (threadIdx.x == 0) {
     dev_set_status(status, FSI_ERR_TIMEOUT);
     for (int t = p->tma_seen; t < p->tma_issued; ++t)
-      tc::mbar_wait(&p->full[t & 1], (uint32_t)(t >> 1) & 1u, kWaitNs / 4);
+      tc::mbar_wait(&p->full[t % NS], (uint32_t)(t / NS) & 1u, kWaitNs / 8);
     if (p->committed > 0) {
       const int t = p->committed - 1;
-      tc::mbar_wait(&p->done[t & 1], (uint32_t)(t >> 1) & 1u, kWaitNs / 4);
+      tc::mbar_wait(&p->done[t % NS], (uint32_t)(t / NS) & 1u, kWaitNs / 4);
     }
   }
   __syncthreads();
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g1(const __grid_constant__ CUtensor
     tc::tma_prefetch_desc(&mSh);
     tc::tma_prefetch_desc(&mSl);
   }
-  pipe_init(&pipe);
+  pipe_init<kNS13>(&pipe);
   if (warp == 0) tc::tmem_alloc(&pipe.tmem, 64);
   tc::tc_fence_before();
   __syncthreads();
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g1(const __grid_constant__ CUtensor
 #pragma unroll
     for (int j = 0; j < 16; ++j) sum[j] += v[j];
   };
-  if (run_pipeline(&pipe, a.PX / 32, 0u, 32u, tma, load, store, mma, fold)) {
+  if (run_pipeline<kNS13>(&pipe, a.PX / 32, 0u, 32u, tma, load, store, mma, fold)) {
     const int y = m0 + 32 * q + lane;
     if (y < a.Ny) {
 #pragma unroll
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g1(const __grid_constant__ CUtensor
       }
     }
   } else {
-    pipe_abort_cleanup(&pipe, a.status);
+    pipe_abort_cleanup<kNS13>(&pipe, a.status);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g3(const __grid_constant__ CUtensor
     tc::tma_prefetch_desc(&mSh);
     tc::tma_prefetch_desc(&mSl);
   }
-  pipe_init(&pipe);
+  pipe_init<kNS13>(&pipe);
   if (warp == 0) tc::tmem_alloc(&pipe.tmem, 64);
   tc::tc_fence_before();
   __syncthreads();
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g3(const __grid_constant__ CUtensor
 #pragma unroll
     for (int j = 0; j < 16; ++j) sum[j] += v[j];
   };
-  if (run_pipeline(&pipe, a.PX / 32, 0u, 32u, tma, load, store, mma, fold)) {
+  if (run_pipeline<kNS13>(&pipe, a.PX / 32, 0u, 32u, tma, load, store, mma, fold)) {
     const int x = m0 + 32 * q + lane;
     if (x < a.Nx) {
 #pragma unroll
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g3(const __grid_constant__ CUtensor
       }
     }
   } else {
-    pipe_abort_cleanup(&pipe, a.status);
+    pipe_abort_cleanup<kNS13>(&pipe, a.status);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -360,29 +369,30 @@ struct G2Args {
 // Spectral solve of one entry, as in the FFT y pass (dst::k_ysolve): k, l are 1-based frequencies.
 __device__ __forceinline__ void spectral(const dst::SpecParams<float>& sp, int k, int l, float rh, float& wt,
                                          float& st) {
-  const float lam = float((sp.lx[k] + sp.ly[l]) * sp.inv_h2);
-  const float aw = float(sp.inv_dt) + lam * float(sp.inv_2re);
+  const float lam = (sp.lx[k] + sp.ly[l]) * sp.inv_h2;
+  const float aw = sp.inv_dt + lam * sp.inv_2re;
   float bcs = 0.f;
   if (sp.ring) {
     const float* ring = sp.ring;
     const int l0 = l - 1;
-    const float bw = float(sp.sx1[k]) * ring[0 * sp.ring_ld + l0] + float(sp.sxN[k]) * ring[1 * sp.ring_ld + l0] +
-                     ring[2 * sp.ring_ld + (k - 1)] * float(sp.sy1[l]) + ring[3 * sp.ring_ld + (k - 1)] * float(sp.syN[l]);
-    bcs = float(sp.sx1[k]) * ring[4 * sp.ring_ld + l0] + float(sp.sxN[k]) * ring[5 * sp.ring_ld + l0] +
-          ring[6 * sp.ring_ld + (k - 1)] * float(sp.sy1[l]) + ring[7 * sp.ring_ld + (k - 1)] * float(sp.syN[l]);
-    rh += bw * float(sp.inv_2re * sp.inv_h2);
-    bcs *= float(sp.inv_h2);
+    const float bw = sp.sx1[k] * ring[0 * sp.ring_ld + l0] + sp.sxN[k] * ring[1 * sp.ring_ld + l0] +
+                     ring[2 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[3 * sp.ring_ld + (k - 1)] * sp.syN[l];
+    bcs = sp.sx1[k] * ring[4 * sp.ring_ld + l0] + sp.sxN[k] * ring[5 * sp.ring_ld + l0] +
+          ring[6 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[7 * sp.ring_ld + (k - 1)] * sp.syN[l];
+    rh += bw * sp.ring_w;
+    bcs *= sp.inv_h2;
   }
   wt = rh / aw;
   st = (wt + bcs) / lam;
-  wt *= float(sp.norm);
-  st *= float(sp.norm);
+  wt *= sp.norm;
+  st *= sp.norm;
 }
 
 // G2: CTA bx owns x-frequencies kx in [16 bx, +16) and the whole y range (PY = 128 MT <= 512).  One stage
 // sequence of 3 MT KB stages: forward R^ = S_y T1^T (the spectral solve writes W^ and S^ as split B operands
 // into shared memory at the end of each M tile), then T2w = S_y W^, then T2s = S_y S^.
 constexpr int kNT2 = 16;
+template <int NS>
 __global__ void __launch_bounds__(kThr, 1) k_g2(const __grid_constant__ CUtensorMap mSh,
                                                 const __grid_constant__ CUtensorMap mSl, G2Args a) {
   constexpr int NT = kNT2;
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g2(const __grid_constant__ CUtensor
   __shared__ Pipe pipe;
   uint8_t* sm = align1024(smem_raw);
   const int MT = a.PY / 128, KB = a.PY / 32, TP = MT * KB;
-  uint8_t* bw_hi = sm + 2 * STAGE;  // W^ as K-major tiles [KB][NT rows][128 B]
+  uint8_t* bw_hi = sm + NS * STAGE;  // W^ as K-major tiles [KB][NT rows][128 B]
   uint8_t* bw_lo = bw_hi + (size_t)KB * BB;
   uint8_t* bs_hi = bw_lo + (size_t)KB * BB;  // S^
   uint8_t* bs_lo = bs_hi + (size_t)KB * BB;
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g2(const __grid_constant__ CUtensor
     tc::tma_prefetch_desc(&mSh);
     tc::tma_prefetch_desc(&mSl);
   }
-  pipe_init(&pipe);
+  pipe_init<NS>(&pipe);
   if (warp == 0) tc::tmem_alloc(&pipe.tmem, 32);
   tc::tc_fence_before();
   __syncthreads();
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(kThr, 1) k_g2(const __grid_constant__ CUtensor
 #pragma unroll
     for (int j = 0; j < 8; ++j) sum[j] = 0.f;
   };
-  if (!run_pipeline(&pipe, 3 * TP, 0u, 16u, tma, load, store, mma, fold)) pipe_abort_cleanup(&pipe, a.status);
+  if (!run_pipeline<NS>(&pipe, 3 * TP, 0u, 16u, tma, load, store, mma, fold)) pipe_abort_cleanup<NS>(&pipe, a.status);
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 32);
@@ -540,9 +550,12 @@ bool encode(CUtensorMap* m, void* base, int P, int box_rows) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t g1_smem() { return 2 * (2 * 128 * 128 + 2 * kNT * 128) + 1024; }
+size_t g1_smem() { return kNS13 * (2 * 128 * 128 + 2 * kNT * 128) + 1024; }
 size_t g3_smem() { return g1_smem(); }
-size_t g2_smem(int PY) { return 2 * (2 * 128 * 128 + 2 * kNT2 * 128) + 4 * (size_t)(PY / 32) * kNT2 * 128 + 1024; }
+int g2_stages(int PY) { return PY <= 256 ? 4 : 2; }
+size_t g2_smem(int PY) {
+  return g2_stages(PY) * (2 * 128 * 128 + 2 * kNT2 * 128) + 4 * (size_t)(PY / 32) * kNT2 * 128 + 1024;
+}
 
 }  // namespace
 
@@ -565,7 +578,8 @@ fsi_status gemm_dst_setup(fsi_ctx* c) {
   std::call_once(attrs, [] {
     cudaFuncSetAttribute(k_g1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g1_smem());
     cudaFuncSetAttribute(k_g3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem());
-    cudaFuncSetAttribute(k_g2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g2_smem(512));
+    cudaFuncSetAttribute(k_g2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g2_smem(256));
+    cudaFuncSetAttribute(k_g2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g2_smem(512));
   });
   GemmDst* g = new (std::nothrow) GemmDst();
   if (!g) return FSI_ERR_OOM;
@@ -613,7 +627,10 @@ fsi_status gemm_ysolve(fsi_ctx* c, const dst::SpecParams<float>& sp) {
   G2Args a = {(const float*)c->T1, c->ldT, (float*)c->T2w, (float*)c->T2s, c->ldX, c->Nx, c->Ny, c->ny, sp,
               c->d_status};
   const dim3 grid(c->nx / kNT2);
-  k_g2<<<grid, kThr, g2_smem(c->ny), c->stream>>>(c->gd->sy128_hi, c->gd->sy128_lo, a);
+  if (g2_stages(c->ny) == 4)
+    k_g2<4><<<grid, kThr, g2_smem(c->ny), c->stream>>>(c->gd->sy128_hi, c->gd->sy128_lo, a);
+  else
+    k_g2<2><<<grid, kThr, g2_smem(c->ny), c->stream>>>(c->gd->sy128_hi, c->gd->sy128_lo, a);
   FSI_CUDA_TRY(cudaGetLastError());
   return FSI_OK;
 }

@@ -3,8 +3,7 @@
 // (Eq. predictor2) and the corrector (Eq. corrector2) with its surface-stress source.
 #include <cstdio>
 #include <type_traits>
-#include "dst.cuh"
-#include "internal.h"
+#include "spec.cuh"
 
 namespace {
 
@@ -40,162 +39,247 @@ void set_smem_limits() {
   cudaFuncSetAttribute(dst::k_xi<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_vec_dst<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_vec_dst<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_vec_dst<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // ---------------------------------------------------------------------------------------------
-// O1: coarse vorticity strictly inside a finer level <- coincident value of the finest such level.
-template <typename T>
-__global__ void k_inject(T* __restrict__ w_all, long lvl, long ps, int nx, int ny) {
-  const int g = blockIdx.z + 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I < 1 || I >= nx || J < 1 || J >= ny) return;
-  int gi = g, ii = I, jj = J;
-  // descend while strictly inside the next finer level
-  while (gi > 0 && abs(2 * ii - nx) < nx / 2 && abs(2 * jj - ny) < ny / 2) {
-    ii = 2 * ii - nx / 2;
-    jj = 2 * jj - ny / 2;
-    --gi;
-  }
-  if (gi == g) return;
-  w_all[(long)g * lvl + (long)J * ps + I] = w_all[(long)gi * lvl + (long)jj * ps + ii];
-}
-
 // O2: advection N = div(u w) with vertex-averaged velocities (reading R7) and
-// rhs = w/dt + lap_h w/(2 Re) - 3/2 N^n + 1/2 N^{n-1}.
+// rhs = w/dt + lap_h w/(2 Re) - 3/2 N^n + 1/2 N^{n-1}.  Block (32, 8) = one tile of interior vertices; the
+// tile of w and s with a one-vertex halo is staged in shared memory (each value read once from L2).
+// Per-level constants in the field precision (computed on the host).
 template <typename T>
-__global__ void k_rhs(const T* __restrict__ w_all, const T* __restrict__ s_all, T* __restrict__ np_all,
-                      T* __restrict__ rhs_all, long lvl, long ps, int nx, int ny, double h0, double dt, double re,
-                      double U, double V, int first) {
+struct RhsConst {
+  T i2h[12], inv_h2[12];  // 1/(2 h_g), 1/h_g^2 for level g (at most 12 levels)
+  T inv_dt, half_inv_re, U, V;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const T* __restrict__ s_all,
+                                             T* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps, int nx,
+                                             int ny, RhsConst<T> k, int first) {
+  __shared__ T tw[10][35], ts[10][35];
   const int g = blockIdx.z;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
-  if (i >= nx || j >= ny) return;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;  // tile vertex (i0 + 1, j0 + 1) at smem (1, 1)
   const T* w = w_all + (long)g * lvl;
   const T* s = s_all + (long)g * lvl;
-  const T h = T(h0 * (double)(1 << g));
-  const T i2h = T(0.5) / h;
-  const long o = (long)j * ps + i;
-  const T wc = w[o], we = w[o + 1], ww = w[o - 1], wn = w[o + ps], wsx = w[o - ps];
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  for (int e = t; e < 10 * 34; e += 256) {
+    const int r = e / 34, c = e - r * 34;
+    const int I = i0 + c, J = j0 + r;  // vertex indices 0..nx, 0..ny
+    T wv = T(0), sv = T(0);
+    if (I <= nx && J <= ny) {
+      // O1 on the fly: a vertex strictly inside a finer level takes the vorticity of the finest level that
+      // contains it (the coarse array itself is overwritten by this level's solve before any other use)
+      int gi = g, ii = I, jj = J;
+      while (gi > 0 && abs(2 * ii - nx) < nx / 2 && abs(2 * jj - ny) < ny / 2) {
+        ii = 2 * ii - nx / 2;
+        jj = 2 * jj - ny / 2;
+        --gi;
+      }
+      wv = w_all[(long)gi * lvl + (long)jj * ps + ii];
+      sv = s[(long)J * ps + I];
+    }
+    tw[r][c] = wv;
+    ts[r][c] = sv;
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x + 1, j = j0 + threadIdx.y + 1;
+  if (i >= nx || j >= ny) return;
+  const int x = threadIdx.x + 1, y = threadIdx.y + 1;
+  const T i2h = k.i2h[g];
+  const T wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
   // ubar at (i+-1, j) = (s[j+1] - s[j-1])/(2h) + U ; vbar at (i, j+-1) = -(s[i+1] - s[i-1])/(2h) + V
-  const T ue = (s[o + ps + 1] - s[o - ps + 1]) * i2h + T(U);
-  const T uw = (s[o + ps - 1] - s[o - ps - 1]) * i2h + T(U);
-  const T vn = -(s[o + ps + 1] - s[o + ps - 1]) * i2h + T(V);
-  const T vs = -(s[o - ps + 1] - s[o - ps - 1]) * i2h + T(V);
+  const T ue = (ts[y + 1][x + 1] - ts[y - 1][x + 1]) * i2h + k.U;
+  const T uw = (ts[y + 1][x - 1] - ts[y - 1][x - 1]) * i2h + k.U;
+  const T vn = -(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + k.V;
+  const T vs = -(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
   const T n = (ue * we - uw * ww) * i2h + (vn * wn - vs * wsx) * i2h;
-  const T lap = (we + ww + wn + wsx - T(4) * wc) / (h * h);
+  const T lap = (we + ww + wn + wsx - T(4) * wc) * k.inv_h2[g];
+  const long o = (long)j * ps + i;
   T* np = np_all + (long)g * lvl;
   const long oi = (long)(j - 1) * ps + (i - 1);
   const T nold = first ? n : np[o];
   np[o] = n;
-  rhs_all[(long)g * lvl + oi] = wc * T(1.0 / dt) + lap * T(0.5 / re) - T(1.5) * n + T(0.5) * nold;
+  rhs_all[(long)g * lvl + oi] = wc * k.inv_dt + lap * k.half_inv_re - T(1.5) * n + T(0.5) * nold;
 }
 
-// O3 boundary of level g from level g+1 (injection at coincident vertices, midpoint average otherwise).
+// O3 and the boundary-side transforms of a nested level in one launch.  Ring vectors: side 0 = left/right
+// columns (j = 1..ny-1) of w then s, side 1 = bottom/top rows (i = 1..nx-1) of w then s.  A block takes a
+// group of vectors of one side, computes them from the coarse level (injection at coincident vertices,
+// midpoint average otherwise; reading R5), writes them into the
+// fine level's boundary ring and their unnormalised DST-I into the ring spectra (8 x ring_ld: wL wR wB wT
+// sL sR sB sT).  Block 0 also writes the eight corner values.  blockDim = 256, 4 PER 256 = nf L per block.
 template <typename T>
-__global__ void k_ring(T* __restrict__ wf, T* __restrict__ sf, const T* __restrict__ wc, const T* __restrict__ sc,
-                       long ps, int nx, int ny) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb = nx + 1, nside = ny - 1;
-  int i, j;
-  if (t < nb) {
-    i = t;
-    j = 0;
-  } else if (t < 2 * nb) {
-    i = t - nb;
-    j = ny;
-  } else if (t < 2 * nb + nside) {
-    i = 0;
-    j = t - 2 * nb + 1;
-  } else if (t < 2 * nb + 2 * nside) {
-    i = nx;
-    j = t - 2 * nb - nside + 1;
-  } else {
-    return;
-  }
-  const int a = i + nx / 2, b = j + ny / 2;  // position in half-coarse units
+__device__ __forceinline__ T ring_value(const T* __restrict__ c, long ps, int nx, int ny, int i, int j) {
+  const int a = i + nx / 2, b = j + ny / 2;
   const int I0 = a >> 1, J0 = b >> 1;
   const int I1 = I0 + (a & 1), J1 = J0 + (b & 1);
-  const long o00 = (long)J0 * ps + I0, o11 = (long)J1 * ps + I1;
-  const T w = T(0.5) * (wc[o00] + wc[o11]);
-  const T s = T(0.5) * (sc[o00] + sc[o11]);
-  wf[(long)j * ps + i] = w;
-  sf[(long)j * ps + i] = s;
+  return T(0.5) * (c[(long)J0 * ps + I0] + c[(long)J1 * ps + I1]);
+}
+
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restrict__ sf, const T* __restrict__ wc,
+                                                  const T* __restrict__ sc, long ps, int nx, int ny,
+                                                  T* __restrict__ ring, long ring_ld,
+                                                  const typename C2<T>::t* __restrict__ twx,
+                                                  const typename C2<T>::t* __restrict__ twy, int logLx, int logLy,
+                                                  int nblk_y) {
+  using c2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2* buf = reinterpret_cast<c2*>(smem_raw);
+  const int side = (int)blockIdx.x < nblk_y ? 0 : 1;
+  const int logL = side ? logLx : logLy, L = 1 << logL;
+  const int N = side ? nx - 1 : ny - 1;
+  const int nf = 4 * PER * (int)blockDim.x / L;
+  const int v0 = 2 * nf * (side ? (int)blockIdx.x - nblk_y : (int)blockIdx.x);
+  if (blockIdx.x == 0 && threadIdx.x < 8) {  // corners (i, j) in {0, nx} x {0, ny} of w and s
+    const int q = threadIdx.x & 3;
+    const int i = (q & 1) ? nx : 0, j = (q & 2) ? ny : 0;
+    if (threadIdx.x < 4) wf[(long)j * ps + i] = ring_value(wc, ps, nx, ny, i, j);
+    else sf[(long)j * ps + i] = ring_value(sc, ps, nx, ny, i, j);
+  }
+  dst::zero_ends<T>(buf, nf, L);
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, n = idx - f * N;
+    T ab[2];
+    for (int e = 0; e < 2; ++e) {
+      const int v = v0 + 2 * f + e;
+      ab[e] = T(0);
+      if (v < 4) {
+        const int i = side ? n + 1 : ((v & 1) ? nx : 0);
+        const int j = side ? ((v & 1) ? ny : 0) : n + 1;
+        const bool is_w = v < 2;
+        const T val = ring_value(is_w ? wc : sc, ps, nx, ny, i, j);
+        (is_w ? wf : sf)[(long)j * ps + i] = val;
+        ab[e] = val;
+      }
+    }
+    dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
+  }
+  __syncthreads();
+  dst::block_fft<T, PER>(buf, L, logL, side ? twx : twy);
+  const int dmap[2][4] = {{0, 1, 4, 5}, {2, 3, 6, 7}};
+  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
+    const int f = idx / N, n = idx - f * N;
+    const int va = v0 + 2 * f;
+    const c2 z = buf[(long)f * L + n + 1];
+    if (va < 4) ring[dmap[side][va] * ring_ld + n] = T(-0.5) * z.y;
+    if (va + 1 < 4) ring[dmap[side][va + 1] * ring_ld + n] = T(0.5) * z.x;
+  }
 }
 
 // O5 source: src = (ds/h^2) curl_h(E0^T P^T f) on the level-0 vertices near the body.  Deterministic
-// gather: every vertex sums over all body points with a fixed order and reduction tree (no atomics), so a
-// run gives the same bits every time.  Face weights: P row (hat, 4 nodes) times the E0 stencil
-// (1/6, 2/3, 1/6) x (1/2, 1/2).
-__device__ __forceinline__ double wx3(int d) { return d == 0 ? 2.0 / 3.0 : ((d == 1 || d == -1) ? 1.0 / 6.0 : 0.0); }
+// gather (no atomics): every vertex sums the contributions of the body points in point order, so a run
+// gives the same bits every time.
+//
+// Face weights of one body point with hat cell (ci, cj) and hat weights w_ab (node (ci + a, cj + b)):
+// E0 puts a u-value at vertex (vi, vj) on the u-faces (vi + d, vj +- 1/2) with weight wx3(d) / 2,
+// wx3 = (1/6, 2/3, 1/6), and a v-value on the v-faces (vi +- 1/2, vj + d) likewise.  With
+//   U_b(d) = sum_a w_ab wx3(d - a)   and   V_a(e) = sum_b w_ab wx3(e - b),   d, e in -1..2,
+// the u-face (i, j + 1/2) receives (1/2) sum_{b : j - cj - b in {-1, 0}} U_b(i - ci) fx and the v-face
+// (i + 1/2, j) receives (1/2) sum_{a : i - ci - a in {-1, 0}} V_a(j - cj) fy.  The tables are built once
+// per point (times the stress) in shared memory.
+template <typename T>
+__device__ __forceinline__ T wx3t(int d) { return d == 0 ? T(2.0 / 3.0) : ((d == 1 || d == -1) ? T(1.0 / 6.0) : T(0)); }
 
-// Contribution of body point p to the four faces around vertex (i, j) that enter the curl.
-__device__ __forceinline__ void point_faces(int i, int j, int ci, int cj, const double* w, double fxp, double fyp,
-                                            double* fve, double* fvw, double* fun, double* fus) {
-  if (i < ci - 2 || i > ci + 4 || j < cj - 2 || j > cj + 4) return;
-  double ve = 0.0, vw = 0.0, un = 0.0, us = 0.0;
-#pragma unroll
-  for (int b = 0; b < 2; ++b)
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int vi = ci + a, vj = cj + b;
-      const double wp = w[2 * b + a];
-      // u-face (fi, fj+1/2): wx3(fi - vi) * 1/2 if fj - vj in {-1, 0}; v-face (fi+1/2, fj) likewise
-      const int dn = j - vj, ds_ = j - 1 - vj;
-      un += wp * wx3(i - vi) * ((dn == 0 || dn == -1) ? 0.5 : 0.0);
-      us += wp * wx3(i - vi) * ((ds_ == 0 || ds_ == -1) ? 0.5 : 0.0);
-      const int de = i - vi, dw = i - 1 - vi;
-      ve += wp * ((de == 0 || de == -1) ? 0.5 : 0.0) * wx3(j - vj);
-      vw += wp * ((dw == 0 || dw == -1) ? 0.5 : 0.0) * wx3(j - vj);
-    }
-  *fve += ve * fyp;
-  *fvw += vw * fyp;
-  *fun += un * fxp;
-  *fus += us * fxp;
+struct SrcPoint {
+  int ci, cj;
+};
+
+// u-face (fi, fj + 1/2) value of point p (tables ut[b][d + 1] = U_b(d) fx / 2)
+template <typename T>
+__device__ __forceinline__ T u_face(const T* ut, int ci, int cj, int fi, int fj) {
+  const int d = fi - ci;
+  if (d < -1 || d > 2) return T(0);
+  T v = T(0);
+  const int e = fj - cj;  // b with e - b in {-1, 0}: b = e or b = e + 1
+  if (e == 0 || e == 1) v += ut[e * 4 + d + 1];
+  if (e == -1 || e == 0) v += ut[(e + 1) * 4 + d + 1];
+  return v;
+}
+// v-face (fi + 1/2, fj) value of point p (tables vt[a][e + 1] = V_a(e) fy / 2)
+template <typename T>
+__device__ __forceinline__ T v_face(const T* vt, int ci, int cj, int fi, int fj) {
+  const int e = fj - cj;
+  if (e < -1 || e > 2) return T(0);
+  T v = T(0);
+  const int d = fi - ci;
+  if (d == 0 || d == 1) v += vt[d * 4 + e + 1];
+  if (d == -1 || d == 0) v += vt[(d + 1) * 4 + e + 1];
+  return v;
 }
 
-// One warp per vertex: lanes take body points p = lane, lane + 32, ... and the four face sums are reduced
-// with a fixed shuffle tree.  Vertices outside the box written by the FSI kernel (ctrl[8..11]) are set to
-// zero.  Grid: x covers the Omega_0 box grown by 3 cells in tiles of 32 vertices, y its rows.
+// Thread per vertex over tiles of 32 x 4 vertices covering the Omega_0 box grown by 3 cells.  Vertices
+// outside the box written by the FSI kernel (ctrl[8..11]) are set to zero.  A tile that meets the box
+// keeps, in point order, the points whose face support can reach it, with their face tables.
 template <typename T>
-__global__ void __launch_bounds__(256) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
+__global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
                                              int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
-                                             double scale, double h) {
+                                             T coef) {
+  extern __shared__ __align__(16) unsigned char src_smem[];
+  T* tab = reinterpret_cast<T*>(src_smem);                  // [nb][16]: ut (8) then vt (8)
+  SrcPoint* pt = reinterpret_cast<SrcPoint*>(tab + 16 * nb);  // [nb]
+  __shared__ int wcount[4], n_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int j = j_lo - 3 + blockIdx.y;
-  const int i0 = i_lo - 3 + blockIdx.x * 32;
-  if (j < 1 || j > ny - 1 || j > j_hi + 3) return;
+  const int ti0 = i_lo - 3 + blockIdx.x * 32, tj0 = j_lo - 3 + blockIdx.y * 4;
+  const int i = ti0 + lane, j = tj0 + wid;
   const int bi0 = box[0], bi1 = box[1], bj0 = box[2], bj1 = box[3];
-  const bool row_in = j >= bj0 && j <= bj1;
-  if (tid < 32) {
-    const int i = i0 + tid;
-    if (i >= 1 && i <= nx - 1 && i <= i_hi + 3 && !(row_in && i >= bi0 && i <= bi1))
-      src[(long)(j - 1) * ps + (i - 1)] = T(0);
-  }
-  if (!row_in) return;
-  for (int v = wid; v < 32; v += blockDim.x >> 5) {
-    const int i = i0 + v;
-    if (i < 1 || i > nx - 1 || i > i_hi + 3 || i < bi0 || i > bi1) continue;  // warp-uniform
-    double fve = 0.0, fvw = 0.0, fun = 0.0, fus = 0.0;
-    for (int p = lane; p < nb; p += 32) {
+  const bool tile_hits = ti0 <= bi1 && ti0 + 31 >= bi0 && tj0 <= bj1 && tj0 + 3 >= bj0;  // block-uniform
+  const bool valid = i >= 1 && i <= nx - 1 && i <= i_hi + 3 && j >= 1 && j <= ny - 1 && j <= j_hi + 3;
+  const bool inside = i >= bi0 && i <= bi1 && j >= bj0 && j <= bj1;
+  if (valid && !inside) src[(long)(j - 1) * ps + (i - 1)] = T(0);
+  if (!tile_hits) return;
+  // select (in point order) the points whose faces enter the curl at some vertex of this tile: vertex
+  // offsets i - ci and j - cj in -1..2
+  if (tid == 0) n_sel = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 128) {
+    const int p = base + tid;
+    int ci = 0, cj = 0;
+    bool take = false;
+    if (p < nb) {
       const int n0 = pidx[4 * p];
-      const double w[4] = {pw[4 * p], pw[4 * p + 1], pw[4 * p + 2], pw[4 * p + 3]};
-      point_faces(i, j, n0 % ni + i_lo, n0 / ni + j_lo, w, f[p], f[nb + p], &fve, &fvw, &fun, &fus);
+      ci = n0 % ni + i_lo;
+      cj = n0 / ni + j_lo;
+      take = ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fve += __shfl_xor_sync(0xffffffffu, fve, o);
-      fvw += __shfl_xor_sync(0xffffffffu, fvw, o);
-      fun += __shfl_xor_sync(0xffffffffu, fun, o);
-      fus += __shfl_xor_sync(0xffffffffu, fus, o);
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    int off = n_sel;
+    for (int w = 0; w < wid; ++w) off += wcount[w];
+    if (take) {
+      const int q = off + __popc(m & ((1u << lane) - 1u));
+      pt[q].ci = ci;
+      pt[q].cj = cj;
+      const T w00 = T(pw[4 * p]), w10 = T(pw[4 * p + 1]), w01 = T(pw[4 * p + 2]), w11 = T(pw[4 * p + 3]);
+      const T fx = T(0.5) * T(f[p]), fy = T(0.5) * T(f[nb + p]);
+      T* t = tab + 16 * q;
+      for (int d = -1; d <= 2; ++d) {
+        t[0 * 4 + d + 1] = (w00 * wx3t<T>(d) + w10 * wx3t<T>(d - 1)) * fx;  // U_0(d)
+        t[1 * 4 + d + 1] = (w01 * wx3t<T>(d) + w11 * wx3t<T>(d - 1)) * fx;  // U_1(d)
+        t[8 + 0 * 4 + d + 1] = (w00 * wx3t<T>(d) + w01 * wx3t<T>(d - 1)) * fy;  // V_0(e = d)
+        t[8 + 1 * 4 + d + 1] = (w10 * wx3t<T>(d) + w11 * wx3t<T>(d - 1)) * fy;  // V_1(e = d)
+      }
     }
-    // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
-    if (lane == 0) src[(long)(j - 1) * ps + (i - 1)] = T(scale * ((fve - fvw) - (fun - fus)) / h);
+    __syncthreads();
+    if (tid == 0) n_sel += wcount[0] + wcount[1] + wcount[2] + wcount[3];
+    __syncthreads();
   }
+  if (!valid || !inside) return;
+  T fve = 0, fvw = 0, fun = 0, fus = 0;
+  const int ns = n_sel;
+  for (int q = 0; q < ns; ++q) {
+    const int ci = pt[q].ci, cj = pt[q].cj;
+    if (i < ci - 1 || i > ci + 2 || j < cj - 1 || j > cj + 2) continue;
+    const T* t = tab + 16 * q;
+    fun += u_face<T>(t, ci, cj, i, j);
+    fus += u_face<T>(t, ci, cj, i, j - 1);
+    fve += v_face<T>(t + 8, ci, cj, i, j);
+    fvw += v_face<T>(t + 8, ci, cj, i - 1, j);
+  }
+  // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
+  src[(long)(j - 1) * ps + (i - 1)] = coef * ((fve - fvw) - (fun - fus));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -231,22 +315,8 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
   // Y
   prof_mark(c, KC_YSOLVE);
   {
-    dst::SpecParams<T> sp;
-    sp.lx = c->lx;
-    sp.ly = c->ly;
-    sp.sx1 = c->sx1;
-    sp.sxN = c->sxN;
-    sp.sy1 = c->sy1;
-    sp.syN = c->syN;
-    sp.ring = use_ring ? (const T*)c->ring : nullptr;
-    sp.ring_ld = c->ring_ld;
     const double h = c->g.h * (double)(1 << g);
-    sp.inv_h2 = 1.0 / (h * h);
-    sp.inv_dt = 1.0 / c->g.dt;
-    sp.inv_2re = 0.5 / c->g.re;
-    sp.norm = 4.0 / ((double)c->Mx * (double)c->My);
-    sp.Mx = c->Mx;
-    sp.My = c->My;
+    const dst::SpecParams<T> sp = spec_params<T>(c, h, use_ring ? (const T*)c->ring : nullptr);
     if (use_gemm<T>(c, 1)) {
       if constexpr (std::is_same<T, float>::value) {
         const fsi_status st = gemm_ysolve(c, sp);
@@ -290,31 +360,29 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g) {
   T* sf = (T*)c->s_all + (long)g * c->lvl_elems;
   const T* wc = (const T*)c->w_all + (long)(g + 1) * c->lvl_elems;
   const T* sc = (const T*)c->s_all + (long)(g + 1) * c->lvl_elems;
-  const int nring = 2 * (c->nx + 1) + 2 * (c->ny - 1);
-  prof_mark(c, KC_RING);
-  k_ring<T><<<(nring + 127) / 128, 128, 0, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny);
-  prof_mark(c, KC_RING);
-  c->launches_per_step += 3;
-  // four vectors of length Ny (wL, wR, sL, sR) and four of length Nx (wB, wT, sB, sT)
-  for (int side = 0; side < 2; ++side) {
-    const int logL = side == 0 ? c->logLy : c->logLx;
-    const int N = side == 0 ? c->Ny : c->Nx;
-    const int L = 1 << logL;
-    const int nthr = L / 4 < 256 ? L / 4 : 256;
-    const int per = L / (4 * nthr);
-    const size_t sm = (size_t)(1 << logL) * sizeof(c2);
-    const T* const* srcs = (const T* const*)(c->ring_src + (long)g * 8 + side * 4);
-    const long* es = c->ring_es + (long)g * 8 + side * 4;
-    T* const* dsts = (T* const*)(c->ring_dst + (long)g * 8 + side * 4);
-    const c2* tw = (const c2*)(side == 0 ? c->twy : c->twx);
-    prof_mark(c, KC_VECDST);
-    switch (per) {
-      case 1: dst::k_vec_dst<T, 1><<<2, nthr, sm, c->stream>>>(srcs, es, 4, N, dsts, tw, logL); break;
-      case 2: dst::k_vec_dst<T, 2><<<2, nthr, sm, c->stream>>>(srcs, es, 4, N, dsts, tw, logL); break;
-      default: dst::k_vec_dst<T, 4><<<2, nthr, sm, c->stream>>>(srcs, es, 4, N, dsts, tw, logL); break;
-    }
-    prof_mark(c, KC_VECDST);
+  const int Lmax = c->logLx > c->logLy ? (1 << c->logLx) : (1 << c->logLy);
+  const int per = Lmax <= 1024 ? 1 : Lmax / 1024;
+  const int nf_y = 4 * per * 256 / (1 << c->logLy), nf_x = 4 * per * 256 / (1 << c->logLx);
+  const int nblk_y = (4 + 2 * nf_y - 1) / (2 * nf_y), nblk_x = (4 + 2 * nf_x - 1) / (2 * nf_x);
+  const size_t sm = (size_t)4 * per * 256 * sizeof(c2);
+  const c2* twx = (const c2*)c->twx;
+  const c2* twy = (const c2*)c->twy;
+  static bool attrs = false;  // per instantiation
+  if (!attrs) {
+    attrs = true;
+    cudaFuncSetAttribute(k_ring_dst<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   }
+  prof_mark(c, KC_RING);
+  const dim3 grid(nblk_y + nblk_x);
+  switch (per) {
+    case 1: k_ring_dst<T, 1><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
+    case 2: k_ring_dst<T, 2><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
+    default: k_ring_dst<T, 4><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
+  }
+  prof_mark(c, KC_RING);
+  c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());
   return FSI_OK;
 }
@@ -323,19 +391,22 @@ template <typename T>
 fsi_status predictor_t(fsi_ctx* c, int first) {
   T* w_all = (T*)c->w_all;
   T* s_all = (T*)c->s_all;
-  if (c->G > 1) {
-    dim3 b(32, 8), gr((c->nx + 31) / 32, (c->ny + 7) / 8, c->G - 1);
-    prof_mark(c, KC_INJECT);
-    k_inject<T><<<gr, b, 0, c->stream>>>(w_all, c->lvl_elems, c->ps, c->nx, c->ny);
-    prof_mark(c, KC_INJECT);
-    c->launches_per_step += 1;
-  }
   {
     dim3 b(32, 8), gr((c->Nx + 31) / 32, (c->Ny + 7) / 8, c->G);
     c->launches_per_step += 1;
     prof_mark(c, KC_RHS);
+    RhsConst<T> k = {};
+    for (int g = 0; g < c->G; ++g) {
+      const double hg = c->g.h * (double)(1 << g);
+      k.i2h[g] = T(0.5 / hg);
+      k.inv_h2[g] = T(1.0 / (hg * hg));
+    }
+    k.inv_dt = T(1.0 / c->g.dt);
+    k.half_inv_re = T(0.5 / c->g.re);
+    k.U = T(c->g.uinf[0]);
+    k.V = T(c->g.uinf[1]);
     k_rhs<T><<<gr, b, 0, c->stream>>>(w_all, s_all, (T*)c->nprev_all, (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx,
-                                      c->ny, c->g.h, c->g.dt, c->g.re, c->g.uinf[0], c->g.uinf[1], first);
+                                      c->ny, k, first);
     prof_mark(c, KC_RHS);
   }
   FSI_CUDA_TRY(cudaGetLastError());
@@ -354,13 +425,18 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
 
 template <typename T>
 fsi_status corrector_t(fsi_ctx* c) {
-  dim3 b(32, 8);
   const int wi = c->ni + 6, wj = c->nj + 6;
-  dim3 gr((wi + 31) / 32, wj);
+  dim3 gr((wi + 31) / 32, (wj + 3) / 4);
   const double scale = c->ds / (c->g.h * c->g.h);
+  const size_t sm = (size_t)c->nb * (16 * sizeof(T) + sizeof(SrcPoint));
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    attr = true;
+    cudaFuncSetAttribute(k_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
   prof_mark(c, KC_SRC);
-  k_src<T><<<gr, 256, 0, c->stream>>>((T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
-                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, scale, c->g.h);
+  k_src<T><<<gr, 128, sm, c->stream>>>((T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
+                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h));
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());

@@ -1,14 +1,17 @@
 // FSI iteration of one time step (Algorithm 2; Eqs. stress2 and dtheta2) in double precision, as one
-// cooperative kernel over a fixed set of CTAs:
+// cooperative kernel over a fixed set of CTAs.  Every CTA keeps the float inverse X of the small system in
+// shared memory and computes every small vector step (P, right-hand side, refinement, dtheta) itself, so
+// grid barriers are needed only where a CTA needs matrix rows another CTA produced:
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
-//      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                                   [all CTAs]
-//   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)          [all CTAs]
-//   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = X r with a float inverse X,
-//      f += d, r = rhs - K f in double, until |d| <= 1e-10 |f|                            [all CTAs]
-//      X is carried across iterations and steps; each iteration first refreshes it for the new K with
-//      two Newton-Schulz steps X <- 2X - X K X (tiled GEMMs over all CTAs; the error I - K X is squared
-//      each time).  It is rebuilt from scratch (blocked float Cholesky and triangular inverse in CTA 0,
-//      then W^T W over all CTAs) at the first step, when refinement stalls, or when it diverges.
+//      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                              [every CTA, all points]
+//   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)    [entries over all CTAs]
+//   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = X r with the float inverse X,
+//      f += d, r = rhs - K f in double, until |d| <= 1e-10 |f|.  d and f are computed in full by every
+//      CTA; each CTA computes the residual rows it owns.  X is carried across iterations and steps and
+//      refreshed for each new K by two Newton-Schulz steps X <- 2X - (X K) X (each squares the error
+//      I - K X), the products split by owned columns of X K and owned rows of the new X.  It is rebuilt
+//      from scratch (blocked float Cholesky and triangular inverse in CTA 0, then W^T W over all CTAs) at
+//      the first step, when refinement stalls, or when it diverges.
 //   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta| (every CTA computes the same
 //      value in the same order, so all CTAs take the same branch without another barrier)
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
@@ -21,12 +24,14 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kMaxSolves = 8;         // refinement solves per attempt
+constexpr int kMaxSolves = 12;        // refinement solves per attempt
 constexpr double kStaleRatio = 0.02;  // |d_s| / |d_{s-1}| above this -> rebuild Kinv for the next iteration
 constexpr double kRefineTol = 1e-10;  // stop at |d| <= 1e-10 |f|; the next correction would be ~ratio times that
-constexpr int kNsSteps = 2;  // Newton-Schulz refreshes of the inverse per FSI iteration
+constexpr int kNsSteps = 2;  // Newton-Schulz steps per refresh of the inverse
+constexpr double kNsTrigger = 0.01;  // refinement contraction |d_s| / |d_{s-1}| above this -> refresh X
 constexpr int BS = 32;       // Cholesky / inverse / GEMM tile (one warp wide)
-constexpr int kMaxBodies = 256;
+constexpr int kMaxBodies = 64;
+constexpr int kMaxR = 4;     // rows (and columns) of the small system owned by one CTA
 constexpr unsigned FULL = 0xffffffffu;
 
 struct FsiArgs {
@@ -34,6 +39,7 @@ struct FsiArgs {
   int fp64;
   long ps;
   double x0, y0, h, dt, ds, U, V, tol;
+  double two_dt, four_dt2;  // 2/dt and 4/dt^2 (no FP64 divisions per point or entry)
   int max_iters;
   int n_sd, ni, nj, i_lo, j_lo;
   const double* B0;
@@ -45,14 +51,15 @@ struct FsiArgs {
   const double* rur;
   int* pidx;
   double* pw;
-  double* rhs;   // [nf] right-hand side, then [nf] residual
+  double* rhs;   // [3][nf] residual rows of the refinement (two buffers), right-hand side
   double* K;     // [nf][nf] double, both triangles
   double* f;     // [nf]
   float* Xa;     // [nf][nf] float inverse of K, ping-pong buffer a
   float* Xb;     // [nf][nf] ping-pong buffer b (ctrl[7] says which one is current)
-  float* S;      // [nf][nf] scratch: K X, or the inverse Cholesky factor during a rebuild
+  float* S;      // [nf][nf] float copy of K (Newton-Schulz operand)
+  float* T;      // [nf][nf] scratch: X K, or the inverse Cholesky factor during a rebuild
   double* part;  // [2 * gridDim] per-CTA maxima
-  unsigned long long* phase_ns;  // [8] accumulated wall time per kernel phase
+  unsigned long long* phase_ns;  // [16] accumulated wall time per kernel phase
   int* ctrl;     // [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves of the last
                  // step, [6] Kinv rebuilds so far, [8..11] vertex box touched by the corrector source
   int* status;
@@ -77,101 +84,69 @@ __device__ void e0cs(const FsiArgs& a, int I, int J, double* u, double* v) {
   *v = -sv / (2.0 * a.h) + a.V;
 }
 
-// Wall time per phase of the kernel, accumulated in nanoseconds (%globaltimer) by thread 0 of CTA 0 at the
-// phase boundaries (after the grid barrier that ends the phase): 0 A, 1 B, 2 inverse refresh, 3 inverse
-// rebuild, 4 refinement solves, 5 double residuals, 6 dtheta/convergence, 7 outputs.
+// Wall time per phase of the kernel in nanoseconds (%globaltimer), kept by thread 0 of CTA 0 in shared
+// memory and added to the global totals once at the end of the launch.  Phases: 0 A, 1 B, 2 inverse
+// refresh, 3 inverse rebuild, 4 refinement solves, 5 double residuals, 6 dtheta/convergence, 7 outputs;
+// sub-phases (split of 2, 4 and 5): 8 X K columns, 9 new X rows, 10 reload of X, 11 d = X r,
+// 12 residual rows and barrier, 13 residual gather.
+constexpr int kPhases = 16;
 struct PhaseClock {
-  unsigned long long* acc;
+  unsigned long long* acc;  // shared [kPhases]
   bool on;
-  unsigned long long* last;
-  __device__ PhaseClock(unsigned long long* a, bool o, unsigned long long* l) : acc(a), on(o && a), last(l) {
-    if (on) *last = now();
-  }
+  unsigned long long last, sub_last;
   __device__ static unsigned long long now() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
   }
+  __device__ PhaseClock(unsigned long long* a, bool o) : acc(a), on(o) {
+    if (on) {
+      for (int k = 0; k < kPhases; ++k) acc[k] = 0;
+      last = sub_last = now();
+    }
+  }
   __device__ void mark(int phase) {
     if (!on) return;
     const unsigned long long t = now();
-    acc[phase] += t - *last;
-    *last = t;
+    acc[phase] += t - last;
+    last = sub_last = t;
+  }
+  __device__ void sub(int phase) {
+    if (!on) return;
+    const unsigned long long t = now();
+    acc[phase] += t - sub_last;
+    sub_last = t;
+  }
+  __device__ void flush(unsigned long long* global) {
+    if (!on || !global) return;
+    for (int k = 0; k < kPhases; ++k) global[k] += acc[k];
   }
 };
 
 // Deterministic block reductions (fixed tree); all threads must call; result valid in every thread.
+// Warp shuffle tree, then the warp results in warp order: two barriers per reduction.
 __device__ double block_sum(double x, double* red) {
-  const int tid = threadIdx.x;
-  red[tid] = x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  if (lane == 0) red[wid] = x;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (tid < s) red[tid] += red[tid + s];
-    __syncthreads();
-  }
-  const double r = red[0];
+  double r = red[0];
+  for (int w = 1; w < nw; ++w) r += red[w];
   __syncthreads();
   return r;
 }
 
 __device__ double block_max(double x, double* red) {
-  const int tid = threadIdx.x;
-  red[tid] = x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(FULL, x, o));
+  if (lane == 0) red[wid] = x;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
-    __syncthreads();
-  }
-  const double r = red[0];
+  double r = red[0];
+  for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
-}
-
-// C = A B (Xc == nullptr) or C = 2 Xc - A B for n x n row-major matrices, A given as double (Ad) or float
-// (Af), B float.  32 x 32 output tiles are spread over the CTAs of the grid; each thread computes four
-// entries of its tile.  sm: 32 * (n + 1) + 33 * n floats of shared memory.  All inputs may have been
-// written earlier in the same launch, so they are read with __ldcg.
-__device__ void gemm_tiles(int n, const double* __restrict__ Ad, const float* __restrict__ Af,
-                           const float* __restrict__ B, const float* __restrict__ Xc, float* __restrict__ C,
-                           float* sm) {
-  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int nt = (n + BS - 1) / BS;
-  float* As = sm;
-  const int lda = n + 1;
-  float* Bs = sm + BS * lda;
-  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
-    const int ti = t / nt, tj = t - ti * nt;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    // whole 32 x n row panel of A and n x 32 column panel of B, loads issued back to back (unrolled) so
-    // that many L2 round trips overlap
-#pragma unroll 8
-    for (int e = tid; e < BS * n; e += blockDim.x) {
-      const int r = e / n, k = e - r * n;
-      const int gi = ti * BS + r;
-      float av = 0.0f;
-      if (gi < n) av = Ad ? (float)__ldcg(&Ad[(long)gi * n + k]) : __ldcg(&Af[(long)gi * n + k]);
-      As[r * lda + k] = av;
-    }
-#pragma unroll 8
-    for (int e = tid; e < BS * n; e += blockDim.x) {
-      const int k = e >> 5, c = e & 31;
-      const int gj = tj * BS + c;
-      Bs[k * (BS + 1) + c] = gj < n ? __ldcg(&B[(long)k * n + gj]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < n; ++k) {
-      const float b = Bs[k * (BS + 1) + lane];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += As[(ty + 8 * q) * lda + k] * b;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gi = ti * BS + ty + 8 * q, gj = tj * BS + lane;
-      if (gi < n && gj < n) C[(long)gi * n + gj] = Xc ? 2.0f * __ldcg(&Xc[(long)gi * n + gj]) - acc[q] : acc[q];
-    }
-  }
 }
 
 // Blocked right-looking Cholesky of the lower triangle of L (row stride ld) in shared memory.
@@ -314,21 +289,103 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
+// Shared-memory layout of the kernel (byte offsets, 16-byte aligned): X (or the Cholesky factor in CTA 0
+// during a rebuild), owned K rows, the vectors rhs, f, r, the hat weights, a float4 work row, hat indices.
+struct FsiLayout {
+  size_t xs, krow, vec, pw, work, rf, pidx, total;
+};
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+__host__ __device__ inline FsiLayout fsi_layout(int nf, int nb) {
+  FsiLayout L;
+  const size_t xn = (size_t)nf * (size_t)(nf | 1);  // >= nf * nf
+  L.xs = 0;
+  L.krow = L.xs + al16(xn * 4);
+  L.vec = L.krow + al16((size_t)kMaxR * nf * 8);
+  L.pw = L.vec + al16((size_t)3 * nf * 8);
+  L.work = L.pw + al16((size_t)4 * nb * 8);
+  L.rf = L.work + al16((size_t)nf * 16);
+  L.pidx = L.rf + al16((size_t)nf * 4);
+  L.total = L.pidx + al16((size_t)4 * nb * 4);
+  return L;
+}
+
+// dst (row stride ldd) <- the n x n row-major matrix src (n even, 8-byte aligned), eight float2 loads in
+// flight per thread; the (row, column) of a thread's element advances by a fixed step (no division)
+__device__ void copy_to_smem(float* dst, int ldd, const float* src, int n) {
+  const float2* s2 = reinterpret_cast<const float2*>(src);
+  const int h = n >> 1, total = n * h, st = blockDim.x;
+  const int dr = st / h, dc = st - dr * h;
+  int e = threadIdx.x, r = e / h, c = e - r * h;
+  auto advance = [&](int& rr, int& cc) {
+    rr += dr;
+    cc += dc;
+    if (cc >= h) {
+      cc -= h;
+      ++rr;
+    }
+  };
+  for (; e + 7 * st < total; e += 8 * st) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(s2 + e + u * st);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float* d = dst + (long)r * ldd + 2 * c;
+      d[0] = v[u].x;
+      d[1] = v[u].y;
+      advance(r, c);
+    }
+  }
+  for (; e < total; e += st) {
+    const float2 v = __ldcg(s2 + e);
+    float* d = dst + (long)r * ldd + 2 * c;
+    d[0] = v.x;
+    d[1] = v.y;
+    advance(r, c);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
   __shared__ double b_th[kMaxBodies], b_ph[kMaxBodies], b_rphi[kMaxBodies], b_rth[kMaxBodies], b_jac[kMaxBodies];
   __shared__ double b_tp[kMaxBodies];  // angle of the iterate that produced the current f (S, P of the solve)
+  __shared__ double b_sn[kMaxBodies], b_cs[kMaxBodies];  // sin, cos of theta0 + theta^(k)
+  __shared__ double b_ijac[kMaxBodies], b_kc[kMaxBodies];  // 1/J and (2 ds/dt)/J
   __shared__ int sh_bad;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  __shared__ unsigned long long sh_phase[kPhases];
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
   const long gtid = (long)blockIdx.x * nthr + tid;
   const long gsize = (long)gridDim.x * nthr;
   const long wg = gtid >> 5, nwg = gsize >> 5;
   const int nb = a.nb, nf = a.nf;
   const int ld = nf | 1;
   const double dt = a.dt;
-  double* res = a.rhs + nf;
+  // residual rows published to the other CTAs, double-buffered by solve parity: a CTA may write the rows of
+  // solve s+1 while another is still reading those of solve s (one barrier per solve)
+  double* const res0 = a.rhs;
+  double* const res1 = a.rhs + nf;
+  // rows (and columns) of the small system owned by this CTA: [r0, r0 + nr)
+  const int R = (nf + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int r0 = min(nf, (int)blockIdx.x * R);
+  const int nr = min(nf, r0 + R) - r0;
+  const FsiLayout L = fsi_layout(nf, nb);
+  float* Xs = reinterpret_cast<float*>(dyn_smem + L.xs);
+  double* Krow = reinterpret_cast<double*>(dyn_smem + L.krow);
+  double* rhs_s = reinterpret_cast<double*>(dyn_smem + L.vec);
+  double* f_s = rhs_s + nf;
+  double* r_s = f_s + nf;
+  double* pw_s = reinterpret_cast<double*>(dyn_smem + L.pw);
+  float4* work4 = reinterpret_cast<float4*>(dyn_smem + L.work);
+  float* rf = reinterpret_cast<float*>(dyn_smem + L.rf);  // float copy of the vector X is applied to
+  int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
 
   // per-CTA copy of the structural state (identical in every CTA)
   for (int bi = tid; bi < a.n_bodies; bi += nthr) {
@@ -339,77 +396,102 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       b_rphi[bi] = b.inertia * (4.0 * s.theta / (dt * dt) + 4.0 * s.phi / dt + s.phidot) +
                    b.damping * (2.0 * s.theta / dt + s.phi);
       b_rth[bi] = s.phi + 2.0 / dt * s.theta;
+      b_ijac[bi] = 1.0 / b_jac[bi];
+      b_kc[bi] = (2.0 * a.ds / dt) / b_jac[bi];
       b_th[bi] = s.theta;
       b_ph[bi] = s.phi;
       b_tp[bi] = s.theta;
     } else {
-      b_jac[bi] = 1.0;
+      b_jac[bi] = b_ijac[bi] = 1.0;
+      b_kc[bi] = 0.0;
       b_rphi[bi] = b_rth[bi] = b_th[bi] = b_ph[bi] = b_tp[bi] = 0.0;
     }
   }
   int kinv_valid = *(volatile int*)&a.ctrl[4];
   int cur = *(volatile int*)&a.ctrl[7];
-  float* gsm = reinterpret_cast<float*>(dyn_smem);  // GEMM tiles (all CTAs) / Cholesky factor (CTA 0)
-  unsigned long long t_last = 0;
-  PhaseClock clk(a.phase_ns, blockIdx.x == 0 && tid == 0, &t_last);
+  if (kinv_valid) copy_to_smem(Xs, ld, cur ? a.Xb : a.Xa, nf);
+  PhaseClock clk(sh_phase, blockIdx.x == 0 && tid == 0 && a.phase_ns);
   __syncthreads();
 
   bool converged = false;
   int it = 0, solves_total = 0;
   for (; it < a.max_iters; ++it) {
-    // ---- A: body points, P, right-hand side
-    for (long p = gtid; p < nb; p += gsize) {
-      const int bi = a.point_body[p];
-      const BodyDev b = a.bodies[bi];
-      double x, y, svx = 0.0, svy = 0.0, ucx, ucy, coef = 0.0;
-      if (b.type == FSI_BODY_TORSIONAL) {
-        const double th_k = b_th[bi], ph_k = b_ph[bi];
-        const int j = (int)p - b.off;
-        double sn, cs;
-        sincos(b.theta0 + th_k, &sn, &cs);
-        x = b.hx + (double)j * a.ds * cs;
-        y = b.hy + (double)j * a.ds * sn;
-        svx = (double)j * a.ds * (-sn);
-        svy = (double)j * a.ds * cs;
-        ucx = svx * ph_k;
-        ucy = svy * ph_k;
-        const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
-        const double rthk = b_rth[bi] - 2.0 / dt * th_k + ph_k;
-        coef = rthk - 2.0 / dt * rphik / b_jac[bi];
-      } else {
-        x = a.rpts[2 * p];
-        y = a.rpts[2 * p + 1];
-        ucx = a.rur[2 * p];
-        ucy = a.rur[2 * p + 1];
+    // ---- A: body points, P, right-hand side.  Points are split over the CTAs (four threads per point, one
+    // per hat vertex; FP64 throughput per SM is low on sm_103), published, then every CTA takes all of them.
+    for (int bi = tid; bi < a.n_bodies; bi += nthr)
+      if (a.bodies[bi].type == FSI_BODY_TORSIONAL) sincos(a.bodies[bi].theta0 + b_th[bi], &b_sn[bi], &b_cs[bi]);
+    __syncthreads();
+    {
+      const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
+      const int p0 = (int)blockIdx.x * per;
+      for (int t0 = 0; t0 < 4 * per; t0 += nthr) {  // whole CTA per pass: every lane joins the shuffles
+        const int t = t0 + tid;
+        const int p = p0 + (t >> 2), q = t & 3;
+        const bool act = t < 4 * per && p < nb;
+        double ubx = 0.0, uby = 0.0, svx = 0.0, svy = 0.0, ucx = 0.0, ucy = 0.0, coef = 0.0;
+        if (act) {
+          const int bi = a.point_body[p];
+          const BodyDev b = a.bodies[bi];
+          double x, y;
+          if (b.type == FSI_BODY_TORSIONAL) {
+            const double th_k = b_th[bi], ph_k = b_ph[bi];
+            const int j = p - b.off;
+            const double sn = b_sn[bi], cs = b_cs[bi];
+            x = b.hx + (double)j * a.ds * cs;
+            y = b.hy + (double)j * a.ds * sn;
+            svx = (double)j * a.ds * (-sn);
+            svy = (double)j * a.ds * cs;
+            ucx = svx * ph_k;
+            ucy = svy * ph_k;
+            const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
+            const double rthk = b_rth[bi] - a.two_dt * th_k + ph_k;
+            coef = rthk - a.two_dt * rphik * b_ijac[bi];
+          } else {
+            x = a.rpts[2 * p];
+            y = a.rpts[2 * p + 1];
+            ucx = a.rur[2 * p];
+            ucy = a.rur[2 * p + 1];
+          }
+          const double xl = a.x0 + a.i_lo * a.h, yl = a.y0 + a.j_lo * a.h;
+          const double fx = (x - xl) / a.h, fy = (y - yl) / a.h;
+          int ci = (int)floor(fx), cj = (int)floor(fy);
+          if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(a.ni - 1) && fy <= (double)(a.nj - 1))) {
+            if (q == 0) dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
+            ci = 0;
+            cj = 0;
+          }
+          ci = min(max(ci, 0), a.ni - 2);
+          cj = min(max(cj, 0), a.nj - 2);
+          const double rx = fx - ci, ry = fy - cj;
+          const int aa = q & 1, bb = q >> 1;
+          const double wq = (aa ? rx : 1.0 - rx) * (bb ? ry : 1.0 - ry);
+          a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
+          a.pw[4 * p + q] = wq;
+          double u, v;
+          e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
+          ubx = wq * u;
+          uby = wq * v;
+        }
+        // sum over the four hat vertices in the fixed order ((q0 + q1) + (q2 + q3))
+        ubx += __shfl_xor_sync(FULL, ubx, 1);
+        uby += __shfl_xor_sync(FULL, uby, 1);
+        ubx += __shfl_xor_sync(FULL, ubx, 2);
+        uby += __shfl_xor_sync(FULL, uby, 2);
+        if (act && q == 0) {
+          a.rhs[2 * nf + p] = ubx - ucx + svx * coef;
+          a.rhs[2 * nf + nb + p] = uby - ucy + svy * coef;
+        }
       }
-      const double xl = a.x0 + a.i_lo * a.h, yl = a.y0 + a.j_lo * a.h;
-      const double fx = (x - xl) / a.h, fy = (y - yl) / a.h;
-      int ci = (int)floor(fx), cj = (int)floor(fy);
-      if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(a.ni - 1) && fy <= (double)(a.nj - 1))) {
-        dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
-        ci = 0;
-        cj = 0;
-      }
-      ci = min(max(ci, 0), a.ni - 2);
-      cj = min(max(cj, 0), a.nj - 2);
-      const double rx = fx - ci, ry = fy - cj;
-      const double wts[4] = {(1.0 - rx) * (1.0 - ry), rx * (1.0 - ry), (1.0 - rx) * ry, rx * ry};
-      double ubx = 0.0, uby = 0.0;
-      for (int q = 0; q < 4; ++q) {
-        const int aa = q & 1, bb = q >> 1;
-        a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
-        a.pw[4 * p + q] = wts[q];
-        double u, v;
-        e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
-        ubx += wts[q] * u;
-        uby += wts[q] * v;
-      }
-      a.rhs[p] = ubx - ucx + svx * coef;
-      a.rhs[nb + p] = uby - ucy + svy * coef;
     }
     grid.sync();
+    for (int e = tid; e < 4 * nb; e += nthr) {
+      pidx_s[e] = __ldcg(&a.pidx[e]);
+      pw_s[e] = __ldcg(&a.pw[e]);
+    }
+    for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
+    __syncthreads();
     clk.mark(0);
-    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles written)
+    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles, double and float copies)
     {
       const double kscale = a.ds / (a.h * a.h);
       const long n2 = 2L * a.n_sd;
@@ -422,12 +504,12 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         double wb[4];
 #pragma unroll
         for (int be = 0; be < 4; ++be) {
-          ib[be] = __ldcg(&a.pidx[4 * pb + be]);
-          wb[be] = __ldcg(&a.pw[4 * pb + be]);
+          ib[be] = pidx_s[4 * pb + be];
+          wb[be] = pw_s[4 * pb + be];
         }
         for (int al = 0; al < 4; ++al) {
-          const long row = (long)ca * a.n_sd + __ldcg(&a.pidx[4 * pa + al]);
-          const double wa = __ldcg(&a.pw[4 * pa + al]);
+          const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
+          const double wa = pw_s[4 * pa + al];
           const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
           double t = 0.0;
 #pragma unroll
@@ -438,39 +520,105 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         const int ba = a.point_body[pa], bbd = a.point_body[pb];
         if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
           const BodyDev b = a.bodies[ba];
-          double sn, cs;
-          sincos(b.theta0 + b_th[ba], &sn, &cs);
+          const double sn = b_sn[ba], cs = b_cs[ba];
           const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
           const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
-          kv += (2.0 * a.ds / dt) / b_jac[ba] * sa * sb;
+          kv += b_kc[ba] * sa * sb;
         }
         a.K[(long)r * nf + cidx] = kv;
         a.K[(long)cidx * nf + r] = kv;
+        a.S[(long)r * nf + cidx] = (float)kv;
+        a.S[(long)cidx * nf + r] = (float)kv;
       }
     }
     grid.sync();
+    for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
     clk.mark(1);
     // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      if (kinv_valid) {
-        for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - X (K X): the error I - K X is squared
-          const float* X = cur ? a.Xb : a.Xa;
-          float* Xn = cur ? a.Xa : a.Xb;
-          gemm_tiles(nf, a.K, nullptr, X, nullptr, a.S, gsm);  // S = K X
-          grid.sync();
-          gemm_tiles(nf, nullptr, X, a.S, X, Xn, gsm);         // Xn = 2 X - X S
-          grid.sync();
-          cur ^= 1;
+    // Newton-Schulz refresh of the float inverse for the current K: X <- 2X - (X K) X, kNsSteps times
+    auto ns_refresh = [&]() {
+      for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - (X K) X: the error I - K X is squared
+        float* Xn = cur ? a.Xa : a.Xb;
+        // (a) owned columns of T = X K: T[i][r0 + c] = sum_m X[i][m] K[m][r0 + c]
+        for (int m = tid; m < nf; m += nthr) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float* kr = a.S + (long)m * nf + r0;
+          if (nr > 0) v.x = __ldcg(kr);
+          if (nr > 1) v.y = __ldcg(kr + 1);
+          if (nr > 2) v.z = __ldcg(kr + 2);
+          if (nr > 3) v.w = __ldcg(kr + 3);
+          work4[m] = v;
         }
-        clk.mark(2);
-      } else {
-        float* Lf = reinterpret_cast<float*>(dyn_smem);
+        __syncthreads();
+        if (nr > 0) {
+          for (int i = tid; i < nf; i += nthr) {  // thread per row i (odd row stride: no bank conflicts)
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float* xr = Xs + (long)i * ld;
+  #pragma unroll 4
+            for (int m = 0; m < nf; ++m) {
+              const float xv = xr[m];
+              const float4 kv = work4[m];
+              acc.x += xv * kv.x;
+              acc.y += xv * kv.y;
+              acc.z += xv * kv.z;
+              acc.w += xv * kv.w;
+            }
+            float* tr = a.T + (long)i * nf + r0;
+            tr[0] = acc.x;
+            if (nr > 1) tr[1] = acc.y;
+            if (nr > 2) tr[2] = acc.z;
+            if (nr > 3) tr[3] = acc.w;
+          }
+        }
+        grid.sync();
+        clk.sub(8);
+        // (b) owned rows of the new X: Xn[r0 + c][j] = 2 X[r0 + c][j] - sum_m T[r0 + c][m] X[m][j]
+        for (int m = tid; m < nf; m += nthr) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (nr > 0) v.x = __ldcg(&a.T[(long)r0 * nf + m]);
+          if (nr > 1) v.y = __ldcg(&a.T[(long)(r0 + 1) * nf + m]);
+          if (nr > 2) v.z = __ldcg(&a.T[(long)(r0 + 2) * nf + m]);
+          if (nr > 3) v.w = __ldcg(&a.T[(long)(r0 + 3) * nf + m]);
+          work4[m] = v;
+        }
+        __syncthreads();
+        if (nr > 0) {
+          for (int j = tid; j < nf; j += nthr) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  #pragma unroll 4
+            for (int m = 0; m < nf; ++m) {
+              const float xv = Xs[(long)m * ld + j];
+              const float4 tv = work4[m];
+              acc.x += tv.x * xv;
+              acc.y += tv.y * xv;
+              acc.z += tv.z * xv;
+              acc.w += tv.w * xv;
+            }
+            Xn[(long)r0 * nf + j] = 2.0f * Xs[(long)r0 * ld + j] - acc.x;
+            if (nr > 1) Xn[(long)(r0 + 1) * nf + j] = 2.0f * Xs[(long)(r0 + 1) * ld + j] - acc.y;
+            if (nr > 2) Xn[(long)(r0 + 2) * nf + j] = 2.0f * Xs[(long)(r0 + 2) * ld + j] - acc.z;
+            if (nr > 3) Xn[(long)(r0 + 3) * nf + j] = 2.0f * Xs[(long)(r0 + 3) * ld + j] - acc.w;
+          }
+        }
+        grid.sync();
+        clk.sub(9);
+        copy_to_smem(Xs, ld, Xn, nf);  // (c) every CTA takes the whole new X
+        __syncthreads();
+        clk.sub(10);
+        cur ^= 1;
+      }
+      clk.mark(2);
+    };
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      bool fresh = false;  // X was refreshed or rebuilt for this K
+      if (!kinv_valid) {
+        float* Lf = Xs;  // CTA 0 factors in the space of X, which is being rebuilt
         if (blockIdx.x == 0) {
           for (int i = tid >> 5; i < nf; i += nthr >> 5)
             for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
           __syncthreads();
           chol_blocked(Lf, nf, ld, &sh_bad);
-          tri_inverse(Lf, nf, ld, a.S);
+          tri_inverse(Lf, nf, ld, a.T);
         }
         grid.sync();
         float* Xc = cur ? a.Xb : a.Xa;
@@ -479,7 +627,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
             const int k = k0 + lane;
             float acc = 0.0f;
             if (k <= i)
-              for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.S[(long)m * nf + i]) * __ldcg(&a.S[(long)m * nf + k]);
+              for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.T[(long)m * nf + i]) * __ldcg(&a.T[(long)m * nf + k]);
             if (k <= i) {
               Xc[i * nf + k] = acc;
               Xc[(long)k * nf + i] = acc;
@@ -487,62 +635,75 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
           }
         }
         grid.sync();
+        copy_to_smem(Xs, ld, Xc, nf);
+        __syncthreads();
         kinv_valid = 1;
+        fresh = true;
         if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
         clk.mark(3);
       }
-      const float* Xinv = cur ? a.Xb : a.Xa;
       bool done = false, bad = false;
       int s = 0;
       double gd_prev = 0.0, worst_ratio = 0.0;
       for (; s < kMaxSolves; ++s) {
+        const double* r = s == 0 ? rhs_s : r_s;
+        for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
+        __syncthreads();
         double dmax = 0.0, xmax = 0.0;
-        for (long i = wg; i < nf; i += nwg) {  // d = Kinv r, f += d
-          const double* r = s == 0 ? a.rhs : res;
-          float acc = 0.0f;
-#pragma unroll 8
-          for (int k = lane; k < nf; k += 32) acc += __ldcg(&Xinv[i * nf + k]) * (float)__ldcg(&r[k]);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-          if (lane == 0) {
-            const double xi = (s == 0 ? 0.0 : a.f[i]) + (double)acc;
-            a.f[i] = xi;
-            dmax = fmax(dmax, fabs((double)acc));
-            xmax = fmax(xmax, fabs(xi));
-            if (!isfinite(xi)) dmax = INFINITY;
+        for (int i = tid; i < nf; i += nthr) {  // d = X r, f += d (every CTA, all rows; thread per row)
+          const float* xr = Xs + (long)i * ld;
+          float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // four chains, summed in a fixed order
+          int k = 0;
+          for (; k + 3 < nf; k += 4) {
+            p0 += xr[k] * rf[k];
+            p1 += xr[k + 1] * rf[k + 1];
+            p2 += xr[k + 2] * rf[k + 2];
+            p3 += xr[k + 3] * rf[k + 3];
           }
+          for (; k < nf; ++k) p0 += xr[k] * rf[k];
+          const float acc = (p0 + p1) + (p2 + p3);
+          const double xi = (s == 0 ? 0.0 : f_s[i]) + (double)acc;
+          f_s[i] = xi;
+          dmax = fmax(dmax, fabs((double)acc));
+          xmax = fmax(xmax, fabs(xi));
+          if (!isfinite(xi)) dmax = INFINITY;
         }
-        dmax = block_max(dmax, red);
-        xmax = block_max(xmax, red);
-        if (tid == 0) {
-          a.part[2 * blockIdx.x] = dmax;
-          a.part[2 * blockIdx.x + 1] = xmax;
-        }
-        grid.sync();
+        const double gd = block_max(dmax, red);
+        const double gx = block_max(xmax, red);
+        clk.sub(11);
         clk.mark(4);
-        // every CTA reduces the per-CTA maxima the same way (one load per thread, fixed tree)
-        const double gd = block_max(tid < (int)gridDim.x ? __ldcg(&a.part[2 * tid]) : 0.0, red);
-        const double gx = block_max(tid < (int)gridDim.x ? __ldcg(&a.part[2 * tid + 1]) : 0.0, red);
         if (!isfinite(gd)) {  // a diverged inverse: rebuild and retry
           bad = true;
           break;
         }
-        if (s > 0 && gd_prev > 0.0) worst_ratio = fmax(worst_ratio, gd / gd_prev);
+        const double ratio = (s > 0 && gd_prev > 0.0) ? gd / gd_prev : 0.0;
         gd_prev = gd;
         if (gd <= kRefineTol * gx) {
+          if (s > 0) worst_ratio = fmax(worst_ratio, ratio);
           done = true;
           break;
         }
         if (s == kMaxSolves - 1) break;
-        for (long i = wg; i < nf; i += nwg) {  // r = rhs - K f in double
+        if (!fresh && s > 0 && ratio > kNsTrigger) {  // X is stale for this K: refresh it, keep f and r
+          ns_refresh();
+          fresh = true;
+          gd_prev = 0.0;  // the next correction is the first one made with the new X: no ratio for it
+        } else if (s > 0) {
+          worst_ratio = fmax(worst_ratio, ratio);
+        }
+        for (int c = wid; c < nr; c += nw) {  // owned residual rows r = rhs - K f in double
+          const double* kr = Krow + (long)c * nf;
           double acc = 0.0;
-#pragma unroll 8
-          for (int k = lane; k < nf; k += 32) acc += __ldcg(&a.K[i * nf + k]) * __ldcg(&a.f[k]);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-          if (lane == 0) res[i] = __ldcg(&a.rhs[i]) - acc;
+          for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          acc = warp_sum(acc);
+          if (lane == 0) ((s & 1) ? res1 : res0)[r0 + c] = rhs_s[r0 + c] - acc;
         }
         grid.sync();
+        clk.sub(12);
+        const double* rg = (s & 1) ? res1 : res0;
+        for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&rg[k]);
+        __syncthreads();
+        clk.sub(13);
         clk.mark(5);
       }
       solves_total += s + 1;
@@ -560,21 +721,19 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
       if (b.type != FSI_BODY_TORSIONAL) continue;
-      double sn, cs;
-      sincos(b.theta0 + b_th[bi], &sn, &cs);
+      const double sn = b_sn[bi], cs = b_cs[bi];
       double part = 0.0;
       for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
         const double q = (double)(p - b.off) * a.ds;
-        const double fxp = __ldcg(&a.f[p]), fyp = __ldcg(&a.f[nb + p]);
-        part += q * (-sn) * fxp + q * cs * fyp;
+        part += q * (-sn) * f_s[p] + q * cs * f_s[nb + p];
       }
       const double sf = block_sum(part, red);
-      const double dth = (b_rphi[bi] - b_jac[bi] * b_th[bi] + a.ds * sf) / b_jac[bi];
+      const double dth = (b_rphi[bi] - b_jac[bi] * b_th[bi] + a.ds * sf) * b_ijac[bi];
       __syncthreads();
       if (tid == 0) {
         b_tp[bi] = b_th[bi];
         b_th[bi] += dth;
-        b_ph[bi] = 2.0 / dt * b_th[bi] - b_rth[bi];
+        b_ph[bi] = a.two_dt * b_th[bi] - b_rth[bi];
       }
       if (!isfinite(dth)) finite = false;
       dmax = fmax(dmax, fabs(dth));
@@ -584,13 +743,15 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     converged = (dmax <= a.tol) || !finite;
     clk.mark(6);
     if (converged) break;
-    // No barrier here: after the last barrier of phase C only f is read (phase D), and the next write of
-    // f comes after the phase-A and phase-B barriers of the next iteration.
+    // No barrier here: shared-memory state is CTA-local; the global K, its float copy and the residual
+    // rows are next written after this CTA passes the phase-B barrier of the next iteration, which every
+    // CTA reaches only after its last read of them in this iteration.
   }
 
   // ---- Newmark update, forces, history (CTA 0)
   if (blockIdx.x == 0) {
     if (tid == 0 && !converged) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
+    for (int k = tid; k < nf; k += nthr) a.f[k] = f_s[k];  // surface stress for the corrector
     const int slot = a.ctrl[2] % a.hist_cap;
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
@@ -598,7 +759,7 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       if (b.type == FSI_BODY_TORSIONAL) sincos(b.theta0 + b_tp[bi], &sn, &cs);  // S of the final solve
       double px = 0.0, py = 0.0, pm = 0.0;
       for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
-        const double fxp = __ldcg(&a.f[p]), fyp = __ldcg(&a.f[nb + p]);
+        const double fxp = f_s[p], fyp = f_s[nb + p];
         const double q = (double)(p - b.off) * a.ds;
         px += fxp;
         py += fyp;
@@ -612,8 +773,8 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
         s.moment = b.type == FSI_BODY_TORSIONAL ? a.ds * sm : 0.0;
         if (b.type == FSI_BODY_TORSIONAL) {
           const double th_new = b_th[bi];
-          const double ph_new = 2.0 / dt * th_new - b_rth[bi];
-          s.phidot = 4.0 / (dt * dt) * (th_new - s.theta) - 4.0 / dt * s.phi - s.phidot;
+          const double ph_new = a.two_dt * th_new - b_rth[bi];
+          s.phidot = a.four_dt2 * (th_new - s.theta) - 2.0 * a.two_dt * s.phi - s.phidot;
           s.theta = th_new;
           s.phi = ph_new;
           s.theta_k = th_new;
@@ -640,17 +801,33 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
     // by the E0 support (1.5 cells), the hat support (1 cell) and the curl stencil (1 cell)
     int imin = 1 << 30, imax = -1, jmin = 1 << 30, jmax = -1;
     for (int p = tid; p < nb; p += nthr) {
-      const int n0 = __ldcg(&a.pidx[4 * p]);
+      const int n0 = pidx_s[4 * p];
       const int ci = n0 % a.ni, cj = n0 / a.ni;
       imin = min(imin, ci);
       imax = max(imax, ci);
       jmin = min(jmin, cj);
       jmax = max(jmax, cj);
     }
-    imin = -(int)block_max(-(double)imin, red);
-    imax = (int)block_max((double)imax, red);
-    jmin = -(int)block_max(-(double)jmin, red);
-    jmax = (int)block_max((double)jmax, red);
+    {
+      __shared__ int bx[4][8];
+      imin = __reduce_min_sync(FULL, imin);
+      imax = __reduce_max_sync(FULL, imax);
+      jmin = __reduce_min_sync(FULL, jmin);
+      jmax = __reduce_max_sync(FULL, jmax);
+      if (lane == 0) {
+        bx[0][wid] = imin;
+        bx[1][wid] = imax;
+        bx[2][wid] = jmin;
+        bx[3][wid] = jmax;
+      }
+      __syncthreads();
+      for (int w = 0; w < nw; ++w) {
+        imin = min(imin, bx[0][w]);
+        imax = max(imax, bx[1][w]);
+        jmin = min(jmin, bx[2][w]);
+        jmax = max(jmax, bx[3][w]);
+      }
+    }
     if (tid == 0) {
       a.ctrl[8] = a.i_lo + imin - 3;
       a.ctrl[9] = a.i_lo + imax + 4;
@@ -658,24 +835,28 @@ __global__ void __launch_bounds__(256) k_fsi(FsiArgs a) {
       a.ctrl[11] = a.j_lo + jmax + 4;
     }
     clk.mark(7);
+    clk.flush(a.phase_ns);
   }
 }
 
 }  // namespace
 
-size_t fsi_smem_bytes(int nf) {
-  const size_t ld = (size_t)(nf | 1);
-  const size_t chol = (((size_t)nf * ld * 4 + 15) / 16) * 16;
-  const size_t gemm = ((size_t)BS * (nf + 1) + (size_t)(BS + 1) * nf) * 4;
-  return (chol > gemm ? chol : gemm) + 64;
-}
+size_t fsi_smem_bytes(int nf, int nb) { return fsi_layout(nf, nb).total; }
 
-int fsi_kernel_max_ctas_per_sm(int nf) {
-  cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+// CTAs of the FSI kernel per SM at this size (0: does not fit)
+int fsi_kernel_max_ctas_per_sm(int nf, int nb) {
+  const size_t bytes = fsi_smem_bytes(nf, nb);
+  if (cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, fsi_smem_bytes(nf));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, bytes);
   return n;
 }
+
+// every CTA owns at most kMaxR rows of the small system
+int fsi_min_grid(int nf) { return (nf + kMaxR - 1) / kMaxR; }
 
 fsi_status launch_fsi(fsi_ctx* c) {
   FsiArgs a;
@@ -690,6 +871,8 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.U = c->g.uinf[0];
   a.V = c->g.uinf[1];
   a.tol = c->x.tol;
+  a.two_dt = 2.0 / c->g.dt;
+  a.four_dt2 = 4.0 / (c->g.dt * c->g.dt);
   a.max_iters = c->x.max_iters;
   a.n_sd = c->n_sd;
   a.ni = c->ni;
@@ -713,6 +896,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.Xa = c->d_Kinv;
   a.Xb = c->d_W;
   a.S = c->d_S;
+  a.T = c->d_T;
   a.part = c->d_part;
   a.ctrl = c->d_ctrl;
   a.phase_ns = c->d_phase;
@@ -722,7 +906,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = fsi_smem_bytes(c->nf);
+  cfg.dynamicSmemBytes = fsi_smem_bytes(c->nf, c->nb);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -46,6 +46,7 @@ struct fsi_ctx {
   long ring_ld;
   // tables (double)
   double *lx, *ly, *sx1, *sxN, *sy1, *syN;
+  void *lxT, *lyT, *sx1T, *sxNT, *sy1T, *syNT;  // the same tables in the context precision
   void *twx, *twy;  // complex twiddles in precision prec (length Lx, Ly)
   // ring DST pointer tables, per level: [G][8] src pointers, strides, dst pointers
   void **ring_src, **ring_dst;
@@ -75,7 +76,8 @@ struct fsi_ctx {
   double* d_f;     // [nf]
   float* d_Kinv;   // [nf*nf] float inverse of K used for iterative refinement
   float* d_W;      // [nf*nf] second float-inverse buffer (Newton-Schulz ping-pong)
-  float* d_S;      // [nf*nf] scratch for K X or the inverse Cholesky factor
+  float* d_S;      // [nf*nf] float copy of K
+  float* d_T;      // [nf*nf] scratch: X K, or the inverse Cholesky factor
   double* d_part;  // [2*fsi_grid] per-CTA maxima
   int* d_ctrl;     // FSI control words (see fsi.cu)
   unsigned long long* d_phase;  // [8] accumulated FSI kernel phase times (ns)
@@ -178,6 +180,5 @@ fsi_status gemm_xi(fsi_ctx* c, float* fw, float* fs, int mode);
 void* ctx_alloc(fsi_ctx* c, size_t bytes);
 
 // kernel classes for fsi_profile_kernel
-enum { KC_NONE = 0, KC_XF = 1, KC_YSOLVE = 2, KC_XI = 3, KC_FSI = 4, KC_RHS = 5, KC_SRC = 6, KC_RING = 7,
-       KC_VECDST = 8, KC_INJECT = 9 };
+enum { KC_NONE = 0, KC_XF = 1, KC_YSOLVE = 2, KC_XI = 3, KC_FSI = 4, KC_RHS = 5, KC_SRC = 6, KC_RING = 7 };
 void prof_mark(fsi_ctx* c, int cls);  // records one event if cls is being profiled

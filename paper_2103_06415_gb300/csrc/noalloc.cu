@@ -30,8 +30,8 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Tables for one call: twiddles exp(-2 pi i m / L) for both lengths and lambda_k = 4 sin^2(pi k / 2M).
 template <typename T>
-__global__ void k_noalloc_tables(typename C2<T>::t* twx, int Lx, typename C2<T>::t* twy, int Ly, double* lx,
-                                 int Mx, double* ly, int My) {
+__global__ void k_noalloc_tables(typename C2<T>::t* twx, int Lx, typename C2<T>::t* twy, int Ly, T* lx,
+                                 int Mx, T* ly, int My) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < Lx) {
     double s, c;
@@ -47,11 +47,11 @@ __global__ void k_noalloc_tables(typename C2<T>::t* twx, int Lx, typename C2<T>:
   }
   if (t <= Mx) {
     const double s = sinpi((double)t / (2.0 * Mx));
-    lx[t] = 4.0 * s * s;
+    lx[t] = T(4.0 * s * s);
   }
   if (t <= My) {
     const double s = sinpi((double)t / (2.0 * My));
-    ly[t] = 4.0 * s * s;
+    ly[t] = T(4.0 * s * s);
   }
 }
 
@@ -116,8 +116,8 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
   off[3] = off[2] + align256((size_t)Ny * ldX * sizeof(T));
   off[4] = off[3] + align256((size_t)Lx * sizeof(c2));
   off[5] = off[4] + align256((size_t)Ly * sizeof(c2));
-  off[6] = off[5] + align256((size_t)(Mx + 1) * sizeof(double));
-  off[7] = off[6] + align256((size_t)(My + 1) * sizeof(double));
+  off[6] = off[5] + align256((size_t)(Mx + 1) * sizeof(T));
+  off[7] = off[6] + align256((size_t)(My + 1) * sizeof(T));
   if (off[7] > kScratchBytes) {
     char msg[160];
     snprintf(msg, sizeof(msg), "fsi_op_level_solve_noalloc: %dx%d needs %zu bytes of scratch, limit %zu", nx, ny,
@@ -133,8 +133,8 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
   T* T2s = reinterpret_cast<T*>(base + off[2]);
   c2* twx = reinterpret_cast<c2*>(base + off[3]);
   c2* twy = reinterpret_cast<c2*>(base + off[4]);
-  double* lx = reinterpret_cast<double*>(base + off[5]);
-  double* ly = reinterpret_cast<double*>(base + off[6]);
+  T* lx = reinterpret_cast<T*>(base + off[5]);
+  T* ly = reinterpret_cast<T*>(base + off[6]);
   const int nt = (Lx > Ly ? Lx : Ly) + 1;
   k_noalloc_tables<T><<<(nt + 255) / 256, 256, 0, st>>>(twx, Lx, twy, Ly, lx, Mx, ly, My);
   const Shape cx = shape_for(logLx), cy = shape_for(logLy);
@@ -150,10 +150,11 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
     sp.lx = lx;
     sp.ly = ly;
     sp.ring = nullptr;
-    sp.inv_h2 = 1.0 / (h * h);
-    sp.inv_dt = 1.0 / dt;
-    sp.inv_2re = 0.5 / re;
-    sp.norm = 4.0 / ((double)Mx * (double)My);
+    sp.inv_h2 = T(1.0 / (h * h));
+    sp.inv_dt = T(1.0 / dt);
+    sp.inv_2re = T(0.5 / re);
+    sp.norm = T(4.0 / ((double)Mx * (double)My));
+    sp.ring_w = T(0);
     sp.Mx = Mx;
     sp.My = My;
     dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf));
