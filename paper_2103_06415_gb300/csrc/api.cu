@@ -13,6 +13,7 @@
 int fsi_kernel_max_ctas_per_sm(int nf, int nb);
 size_t fsi_smem_bytes(int nf, int nb);
 int fsi_min_grid(int nf);
+int fsi_float_ld(int nf);
 
 static thread_local char g_errmsg[512] = "";
 
@@ -445,10 +446,10 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 3 * 8)) ||
         !(c->d_K = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)) ||
         !(c->d_f = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
-        !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
-        !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
-        !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
-        !(c->d_T = (float*)ctx_alloc(c, (size_t)c->nf * c->nf * 4)) ||
+        !(c->d_Kinv = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
+        !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
+        !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
+        !(c->d_T = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
         !(c->d_phase = (unsigned long long*)ctx_alloc(c, 16 * sizeof(unsigned long long))) ||
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))

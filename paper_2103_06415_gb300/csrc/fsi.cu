@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 #include <cmath>
 #include "internal.h"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -124,17 +125,21 @@ struct PhaseClock {
 };
 
 // Deterministic block reductions (fixed tree); all threads must call; result valid in every thread.
-// Warp shuffle tree, then the warp results in warp order: two barriers per reduction.
+// Warp shuffle tree, then warp 0 combines the warp results in warp order and broadcasts: two barriers per
+// reduction, FP64 work only in the first step and in warp 0 (FP64 throughput per SM is low on sm_103).
 __device__ double block_sum(double x, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
   if (lane == 0) red[wid] = x;
   __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < nw; ++w) r += red[w];
+  if (wid == 0) {
+    double r = red[0];
+    for (int w = 1; w < nw; ++w) r += red[w];
+    if (lane == 0) red[32] = r;
+  }
   __syncthreads();
-  return r;
+  return red[32];
 }
 
 __device__ double block_max(double x, double* red) {
@@ -143,10 +148,34 @@ __device__ double block_max(double x, double* red) {
   for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(FULL, x, o));
   if (lane == 0) red[wid] = x;
   __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
+  if (wid == 0) {
+    double r = red[0];
+    for (int w = 1; w < nw; ++w) r = fmax(r, red[w]);
+    if (lane == 0) red[32] = r;
+  }
   __syncthreads();
-  return r;
+  return red[32];
+}
+
+// Block-wide maxima of two non-negative floats given as bit patterns (integer order = float order; +inf
+// and NaN patterns sort above every finite value).  One barrier pair.
+__device__ void block_max2_bits(unsigned& a, unsigned& b, unsigned* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = __reduce_max_sync(FULL, a);
+  b = __reduce_max_sync(FULL, b);
+  if (lane == 0) {
+    red[wid] = a;
+    red[32 + wid] = b;
+  }
+  __syncthreads();
+  unsigned ra = red[0], rb = red[32];
+  for (int w = 1; w < nw; ++w) {
+    ra = max(ra, red[w]);
+    rb = max(rb, red[32 + w]);
+  }
+  __syncthreads();
+  a = ra;
+  b = rb;
 }
 
 // Blocked right-looking Cholesky of the lower triangle of L (row stride ld) in shared memory.
@@ -295,54 +324,45 @@ struct FsiLayout {
   size_t xs, krow, vec, pw, work, rf, pidx, total;
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+// Row stride (floats) of the float matrices X, X K and K in global and shared memory: a multiple of 4 (rows
+// start on 16 bytes) with an odd number of 16-byte units, so that threads reading consecutive rows with
+// 128-bit loads hit distinct banks.  Columns nf .. ldx-1 stay zero.
+__host__ __device__ inline int fsi_ldx(int nf) {
+  int l = (nf + 3) / 4 * 4;
+  if (((l / 4) & 1) == 0) l += 4;
+  return l;
+}
 __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb) {
   FsiLayout L;
-  const size_t xn = (size_t)nf * (size_t)(nf | 1);  // >= nf * nf
+  const size_t lx = (size_t)fsi_ldx(nf);
+  const size_t xa = (size_t)nf * lx, xb = (size_t)nf * (size_t)(nf | 1);  // X, or the Cholesky factor
   L.xs = 0;
-  L.krow = L.xs + al16(xn * 4);
+  L.krow = L.xs + al16((xa > xb ? xa : xb) * 4);
   L.vec = L.krow + al16((size_t)kMaxR * nf * 8);
   L.pw = L.vec + al16((size_t)3 * nf * 8);
   L.work = L.pw + al16((size_t)4 * nb * 8);
-  L.rf = L.work + al16((size_t)nf * 16);
-  L.pidx = L.rf + al16((size_t)nf * 4);
+  L.rf = L.work + al16(lx * 16);
+  L.pidx = L.rf + al16(lx * 4);
   L.total = L.pidx + al16((size_t)4 * nb * 4);
   return L;
 }
 
-// dst (row stride ldd) <- the n x n row-major matrix src (n even, 8-byte aligned), eight float2 loads in
-// flight per thread; the (row, column) of a thread's element advances by a fixed step (no division)
-__device__ void copy_to_smem(float* dst, int ldd, const float* src, int n) {
-  const float2* s2 = reinterpret_cast<const float2*>(src);
-  const int h = n >> 1, total = n * h, st = blockDim.x;
-  const int dr = st / h, dc = st - dr * h;
-  int e = threadIdx.x, r = e / h, c = e - r * h;
-  auto advance = [&](int& rr, int& cc) {
-    rr += dr;
-    cc += dc;
-    if (cc >= h) {
-      cc -= h;
-      ++rr;
-    }
-  };
-  for (; e + 7 * st < total; e += 8 * st) {
-    float2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcg(s2 + e + u * st);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      float* d = dst + (long)r * ldd + 2 * c;
-      d[0] = v[u].x;
-      d[1] = v[u].y;
-      advance(r, c);
+// Xs <- the nf x ldx float matrix src by bulk asynchronous copies (thread 0 issues, every thread waits).
+// The caller guarantees that no thread still reads Xs.  A copy that does not land within the wait limit
+// records FSI_ERR_TIMEOUT.
+__device__ void load_x(float* Xs, const float* src, int nf, int ldx, uint64_t* bar, uint32_t* phase, int* status) {
+  const uint32_t bytes = (uint32_t)nf * (uint32_t)ldx * 4u;
+  if (threadIdx.x == 0) {
+    tc::fence_proxy_async_all();
+    tc::mbar_arrive_expect_tx(bar, bytes);
+    const uint32_t chunk = 32768u;
+    for (uint32_t o = 0; o < bytes; o += chunk) {
+      const uint32_t n = bytes - o < chunk ? bytes - o : chunk;
+      tc::bulk_g2s(reinterpret_cast<char*>(Xs) + o, reinterpret_cast<const char*>(src) + o, n, bar);
     }
   }
-  for (; e < total; e += st) {
-    const float2 v = __ldcg(s2 + e);
-    float* d = dst + (long)r * ldd + 2 * c;
-    d[0] = v.x;
-    d[1] = v.y;
-    advance(r, c);
-  }
+  if (!tc::mbar_wait(bar, *phase, 2000000000ull)) dev_set_status(status, FSI_ERR_TIMEOUT);
+  *phase ^= 1u;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -355,6 +375,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
+  __shared__ unsigned redu[64];
   __shared__ double b_th[kMaxBodies], b_ph[kMaxBodies], b_rphi[kMaxBodies], b_rth[kMaxBodies], b_jac[kMaxBodies];
   __shared__ double b_tp[kMaxBodies];  // angle of the iterate that produced the current f (S, P of the solve)
   __shared__ double b_sn[kMaxBodies], b_cs[kMaxBodies];  // sin, cos of theta0 + theta^(k)
@@ -366,7 +387,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   const long gsize = (long)gridDim.x * nthr;
   const long wg = gtid >> 5, nwg = gsize >> 5;
   const int nb = a.nb, nf = a.nf;
-  const int ld = nf | 1;
+  const int ld = nf | 1;        // row stride of the Cholesky factor during a rebuild
+  const int lx = fsi_ldx(nf);   // row stride of X, X K and the float K
   const double dt = a.dt;
   // residual rows published to the other CTAs, double-buffered by solve parity: a CTA may write the rows of
   // solve s+1 while another is still reading those of solve s (one barrier per solve)
@@ -409,7 +431,15 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   }
   int kinv_valid = *(volatile int*)&a.ctrl[4];
   int cur = *(volatile int*)&a.ctrl[7];
-  if (kinv_valid) copy_to_smem(Xs, ld, cur ? a.Xb : a.Xa, nf);
+  __shared__ uint64_t xbar;  // bulk copies of X into shared memory
+  uint32_t xphase = 0;
+  if (tid == 0) {
+    tc::mbar_init(&xbar, 1);
+    tc::fence_mbar_init();
+  }
+  for (int k = nf + tid; k < lx; k += nthr) rf[k] = 0.0f;
+  __syncthreads();
+  if (kinv_valid) load_x(Xs, cur ? a.Xb : a.Xa, nf, lx, &xbar, &xphase, a.status);
   PhaseClock clk(sh_phase, blockIdx.x == 0 && tid == 0 && a.phase_ns);
   __syncthreads();
 
@@ -527,8 +557,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
         a.K[(long)r * nf + cidx] = kv;
         a.K[(long)cidx * nf + r] = kv;
-        a.S[(long)r * nf + cidx] = (float)kv;
-        a.S[(long)cidx * nf + r] = (float)kv;
+        a.S[(long)r * lx + cidx] = (float)kv;
+        a.S[(long)cidx * lx + r] = (float)kv;
       }
     }
     grid.sync();
@@ -540,30 +570,29 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - (X K) X: the error I - K X is squared
         float* Xn = cur ? a.Xa : a.Xb;
         // (a) owned columns of T = X K: T[i][r0 + c] = sum_m X[i][m] K[m][r0 + c]
-        for (int m = tid; m < nf; m += nthr) {
+        for (int m = tid; m < lx; m += nthr) {  // entries m >= nf stay zero
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float* kr = a.S + (long)m * nf + r0;
-          if (nr > 0) v.x = __ldcg(kr);
-          if (nr > 1) v.y = __ldcg(kr + 1);
-          if (nr > 2) v.z = __ldcg(kr + 2);
-          if (nr > 3) v.w = __ldcg(kr + 3);
+          const float* kr = a.S + (long)m * lx + r0;
+          if (m < nf && nr > 0) v.x = __ldcg(kr);
+          if (m < nf && nr > 1) v.y = __ldcg(kr + 1);
+          if (m < nf && nr > 2) v.z = __ldcg(kr + 2);
+          if (m < nf && nr > 3) v.w = __ldcg(kr + 3);
           work4[m] = v;
         }
         __syncthreads();
         if (nr > 0) {
-          for (int i = tid; i < nf; i += nthr) {  // thread per row i (odd row stride: no bank conflicts)
+          for (int i = tid; i < nf; i += nthr) {  // thread per row i, 128-bit loads (conflict-free stride)
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float* xr = Xs + (long)i * ld;
-  #pragma unroll 4
-            for (int m = 0; m < nf; ++m) {
-              const float xv = xr[m];
-              const float4 kv = work4[m];
-              acc.x += xv * kv.x;
-              acc.y += xv * kv.y;
-              acc.z += xv * kv.z;
-              acc.w += xv * kv.w;
+            const float4* xr = reinterpret_cast<const float4*>(Xs + (long)i * lx);
+            for (int m4 = 0; m4 < lx / 4; ++m4) {
+              const float4 xv = xr[m4];
+              const float4 k0 = work4[4 * m4], k1 = work4[4 * m4 + 1], k2 = work4[4 * m4 + 2], k3 = work4[4 * m4 + 3];
+              acc.x += xv.x * k0.x + xv.y * k1.x + xv.z * k2.x + xv.w * k3.x;
+              acc.y += xv.x * k0.y + xv.y * k1.y + xv.z * k2.y + xv.w * k3.y;
+              acc.z += xv.x * k0.z + xv.y * k1.z + xv.z * k2.z + xv.w * k3.z;
+              acc.w += xv.x * k0.w + xv.y * k1.w + xv.z * k2.w + xv.w * k3.w;
             }
-            float* tr = a.T + (long)i * nf + r0;
+            float* tr = a.T + (long)i * lx + r0;
             tr[0] = acc.x;
             if (nr > 1) tr[1] = acc.y;
             if (nr > 2) tr[2] = acc.z;
@@ -575,34 +604,34 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         // (b) owned rows of the new X: Xn[r0 + c][j] = 2 X[r0 + c][j] - sum_m T[r0 + c][m] X[m][j]
         for (int m = tid; m < nf; m += nthr) {
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (nr > 0) v.x = __ldcg(&a.T[(long)r0 * nf + m]);
-          if (nr > 1) v.y = __ldcg(&a.T[(long)(r0 + 1) * nf + m]);
-          if (nr > 2) v.z = __ldcg(&a.T[(long)(r0 + 2) * nf + m]);
-          if (nr > 3) v.w = __ldcg(&a.T[(long)(r0 + 3) * nf + m]);
+          if (nr > 0) v.x = __ldcg(&a.T[(long)r0 * lx + m]);
+          if (nr > 1) v.y = __ldcg(&a.T[(long)(r0 + 1) * lx + m]);
+          if (nr > 2) v.z = __ldcg(&a.T[(long)(r0 + 2) * lx + m]);
+          if (nr > 3) v.w = __ldcg(&a.T[(long)(r0 + 3) * lx + m]);
           work4[m] = v;
         }
         __syncthreads();
         if (nr > 0) {
           for (int j = tid; j < nf; j += nthr) {
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  #pragma unroll 4
+#pragma unroll 4
             for (int m = 0; m < nf; ++m) {
-              const float xv = Xs[(long)m * ld + j];
+              const float xv = Xs[(long)m * lx + j];
               const float4 tv = work4[m];
               acc.x += tv.x * xv;
               acc.y += tv.y * xv;
               acc.z += tv.z * xv;
               acc.w += tv.w * xv;
             }
-            Xn[(long)r0 * nf + j] = 2.0f * Xs[(long)r0 * ld + j] - acc.x;
-            if (nr > 1) Xn[(long)(r0 + 1) * nf + j] = 2.0f * Xs[(long)(r0 + 1) * ld + j] - acc.y;
-            if (nr > 2) Xn[(long)(r0 + 2) * nf + j] = 2.0f * Xs[(long)(r0 + 2) * ld + j] - acc.z;
-            if (nr > 3) Xn[(long)(r0 + 3) * nf + j] = 2.0f * Xs[(long)(r0 + 3) * ld + j] - acc.w;
+            Xn[(long)r0 * lx + j] = 2.0f * Xs[(long)r0 * lx + j] - acc.x;
+            if (nr > 1) Xn[(long)(r0 + 1) * lx + j] = 2.0f * Xs[(long)(r0 + 1) * lx + j] - acc.y;
+            if (nr > 2) Xn[(long)(r0 + 2) * lx + j] = 2.0f * Xs[(long)(r0 + 2) * lx + j] - acc.z;
+            if (nr > 3) Xn[(long)(r0 + 3) * lx + j] = 2.0f * Xs[(long)(r0 + 3) * lx + j] - acc.w;
           }
         }
         grid.sync();
         clk.sub(9);
-        copy_to_smem(Xs, ld, Xn, nf);  // (c) every CTA takes the whole new X
+        load_x(Xs, Xn, nf, lx, &xbar, &xphase, a.status);  // (c) every CTA takes the whole new X
         __syncthreads();
         clk.sub(10);
         cur ^= 1;
@@ -629,13 +658,13 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             if (k <= i)
               for (int m = (int)i; m < nf; ++m) acc += __ldcg(&a.T[(long)m * nf + i]) * __ldcg(&a.T[(long)m * nf + k]);
             if (k <= i) {
-              Xc[i * nf + k] = acc;
-              Xc[(long)k * nf + i] = acc;
+              Xc[i * lx + k] = acc;
+              Xc[(long)k * lx + i] = acc;
             }
           }
         }
         grid.sync();
-        copy_to_smem(Xs, ld, Xc, nf);
+        load_x(Xs, Xc, nf, lx, &xbar, &xphase, a.status);
         __syncthreads();
         kinv_valid = 1;
         fresh = true;
@@ -649,27 +678,28 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         const double* r = s == 0 ? rhs_s : r_s;
         for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
         __syncthreads();
-        double dmax = 0.0, xmax = 0.0;
+        unsigned dbits = 0u, xbits = 0u;  // max |d|, max |f| as float bit patterns
         for (int i = tid; i < nf; i += nthr) {  // d = X r, f += d (every CTA, all rows; thread per row)
-          const float* xr = Xs + (long)i * ld;
+          const float4* xr = reinterpret_cast<const float4*>(Xs + (long)i * lx);
+          const float4* r4 = reinterpret_cast<const float4*>(rf);
           float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // four chains, summed in a fixed order
-          int k = 0;
-          for (; k + 3 < nf; k += 4) {
-            p0 += xr[k] * rf[k];
-            p1 += xr[k + 1] * rf[k + 1];
-            p2 += xr[k + 2] * rf[k + 2];
-            p3 += xr[k + 3] * rf[k + 3];
+          for (int k4 = 0; k4 < lx / 4; ++k4) {
+            const float4 xv = xr[k4], rv = r4[k4];
+            p0 += xv.x * rv.x;
+            p1 += xv.y * rv.y;
+            p2 += xv.z * rv.z;
+            p3 += xv.w * rv.w;
           }
-          for (; k < nf; ++k) p0 += xr[k] * rf[k];
           const float acc = (p0 + p1) + (p2 + p3);
           const double xi = (s == 0 ? 0.0 : f_s[i]) + (double)acc;
           f_s[i] = xi;
-          dmax = fmax(dmax, fabs((double)acc));
-          xmax = fmax(xmax, fabs(xi));
-          if (!isfinite(xi)) dmax = INFINITY;
+          const float xf = (float)xi;
+          dbits = max(dbits, isfinite(xf) ? __float_as_uint(fabsf(acc)) : 0x7f800000u);
+          xbits = max(xbits, __float_as_uint(fabsf(xf)));
         }
-        const double gd = block_max(dmax, red);
-        const double gx = block_max(xmax, red);
+        block_max2_bits(dbits, xbits, redu);
+        const double gd = (double)__uint_as_float(dbits);
+        const double gx = (double)__uint_as_float(xbits);
         clk.sub(11);
         clk.mark(4);
         if (!isfinite(gd)) {  // a diverged inverse: rebuild and retry
@@ -842,6 +872,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
 }  // namespace
 
 size_t fsi_smem_bytes(int nf, int nb) { return fsi_layout(nf, nb).total; }
+
+// row stride (floats) of the float nf x nf matrices of the FSI kernel
+int fsi_float_ld(int nf) { return fsi_ldx(nf); }
 
 // CTAs of the FSI kernel per SM at this size (0: does not fit)
 int fsi_kernel_max_ctas_per_sm(int nf, int nb) {

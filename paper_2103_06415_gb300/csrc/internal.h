@@ -74,10 +74,10 @@ struct fsi_ctx {
   double* d_rhs;   // [nf]
   double* d_K;     // [nf*nf]
   double* d_f;     // [nf]
-  float* d_Kinv;   // [nf*nf] float inverse of K used for iterative refinement
-  float* d_W;      // [nf*nf] second float-inverse buffer (Newton-Schulz ping-pong)
-  float* d_S;      // [nf*nf] float copy of K
-  float* d_T;      // [nf*nf] scratch: X K, or the inverse Cholesky factor
+  float* d_Kinv;   // [nf][ldx] float inverse of K used for iterative refinement (ldx: fsi_float_ld)
+  float* d_W;      // [nf][ldx] second float-inverse buffer (Newton-Schulz ping-pong)
+  float* d_S;      // [nf][ldx] float copy of K
+  float* d_T;      // [nf][ldx] scratch: X K, or the inverse Cholesky factor
   double* d_part;  // [2*fsi_grid] per-CTA maxima
   int* d_ctrl;     // FSI control words (see fsi.cu)
   unsigned long long* d_phase;  // [8] accumulated FSI kernel phase times (ns)
