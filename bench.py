@@ -316,8 +316,10 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         for e0, e1 in evs:
-            flush.zero_()
-            torch.cuda.current_stream().synchronize()
+            # the L2 flush runs on the run's own stream: while the GPU executes it, the host enqueues the
+            # start event, the step's graph and the end event, so the events bracket device work only
+            with torch.cuda.stream(stream):
+                flush.zero_()
             e0.record(stream)
             c.advance(1)
             e1.record(stream)
@@ -376,14 +378,15 @@ def main():
                      "unit": "GB/s", "frac": ys_gbs / hbm, "algorithmic_bytes_per_launch": bytes_ys,
                      "avg_launch_ms": ys_ms}
         # k_fsi: the FSI iteration kernel (one launch per step).  Algorithmic flops per launch from the
-        # solver counters of the timing pass: per FSI iteration the double assembly of P B0 P^T (16 FMA per
-        # lower-triangle entry) and two Newton-Schulz refreshes (2 GEMMs of 2 nf^3 flops each); per
-        # refinement solve a float GEMV (2 nf^2) and per residual a double GEMV (2 nf^2).
+        # solver counters of the timing pass.
         st2 = ctx.stats()
         nf = st2["nf"]
         iters = max(st2["last_iters"], 1)
         solves = max(st2["last_solves"], iters)
-        flops = (iters * (16 * 2 * nf * (nf + 1) / 2 + 2 * 2 * 2 * nf ** 3)
+        refreshes = st2.get("last_refreshes", 1)
+        # per launch: P B0 P^T (16 FMA per lower-triangle entry) per iteration, 2 Newton-Schulz steps of two
+        # nf^3 products per refresh, X r per solve and K f per residual
+        flops = (iters * 16 * 2 * nf * (nf + 1) / 2 + refreshes * 2 * 2 * 2 * nf ** 3
                  + solves * 2 * nf * nf + max(solves - iters, 0) * 2 * nf * nf)
         fsi_ms = shares["fsi"][0]
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -395,9 +398,10 @@ def main():
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (DESIGN.md)",
                 "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                         "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-                "traffic": 1.654e6,
+                "traffic": 1.681664e6,
                 "traffic_note": "dram read+write bytes per launch from one ncu capture of the same kernel on "
-                                "the reduced-Omega_0 variant (same nf); B0 gathers dominate it",
+                                "the reduced-Omega_0 variant (same nf, B0 gathers of the same point set "
+                                "dominate it; profiles/k_fsi_and_dst_passes_reduced_omega0.md)",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
                 "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
                 "secondary": secondary}

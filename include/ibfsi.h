@@ -119,6 +119,7 @@ typedef struct {
   int inverse_rebuilds;  /* times the float inverse of the small system was rebuilt so far */
   int dst_gemm[3];       /* 1 if pass p (0 forward x, 1 y solve, 2 inverse x) runs as a tensor-core GEMM */
   double dst_us[2][3];   /* autotuner timings in microseconds: [0] FFT, [1] GEMM, per pass (0 = not timed) */
+  int last_refreshes;    /* Newton-Schulz refreshes of the float inverse in the last step */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;

@@ -736,8 +736,9 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   }
   if (c->d_ctrl) {
     FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    int ctrl[12];
+    int ctrl[16];
     FSI_CUDA_TRY(cudaMemcpy(ctrl, c->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    out->last_refreshes = ctrl[12];
     out->last_iters = ctrl[1];
     out->last_solves = ctrl[5];
     out->inverse_rebuilds = ctrl[6];

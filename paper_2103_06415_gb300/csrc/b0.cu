@@ -10,8 +10,9 @@
 //   B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb) - T-+(ia-ib, ja+jb) + T++(ia+ib, ja+jb)
 // with 16 small tables (4 component blocks x 4 image terms) of stencil-convolved g.  The result equals the
 // column-by-column definition up to rounding order; the cost is one pass writing B0 plus the two cosine
-// sums of g, each a batch of DCT-I rows done by FFT in double.  g depends on the grid only, so several Omega_0 boxes on one grid share it and
-// their tables and matrices are produced by one launch of each kernel.
+// sums of g, each a batch of DCT-I rows done by FFT in double.  g depends on the grid only, so several
+// Omega_0 boxes on one grid share it and their tables and matrices are produced by one launch of each
+// kernel.
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, lon
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* buf = reinterpret_cast<double2*>(smem_raw);
   const int L = 1 << logL;
+  const double2* tws = dst::stage_twiddles<double>(buf + L, tw, L, (size_t)2 * L * sizeof(double2));
   const int r0 = 2 * blockIdx.x;
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
     const int ll = l <= M ? l : L - l;
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, lon
     buf[l] = make_double2(a, b);
   }
   __syncthreads();
-  dst::block_fft<double, PER>(buf, L, logL, tw);
+  dst::block_fft<double, PER>(buf, L, logL, tws);
   for (int q = threadIdx.x; q <= M; q += blockDim.x) {
     const double2 z = buf[q];
     if (r0 < nrows) out[(long)r0 * out_rs + (long)q * out_es] = 0.5 * scale * z.x;
@@ -72,14 +74,14 @@ fsi_status launch_dct1(const double* in, long in_rs, long in_es, int nrows, int 
   const int L = 1 << logL;
   const int nthr = L / 4 < 256 ? L / 4 : 256;
   const int per = L / (4 * nthr);
-  const size_t sm = (size_t)L * sizeof(double2);
+  const size_t sm = dst::pass_smem<double>((size_t)L, L);
   const dim3 grid((nrows + 1) / 2);
   static bool attrs = false;
   if (!attrs) {
     attrs = true;
-    cudaFuncSetAttribute(k_dct1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_dct1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_dct1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_dct1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dct1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dct1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   switch (per) {
     case 1: k_dct1<1><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re); break;
@@ -151,52 +153,63 @@ __global__ void k_tables(double* __restrict__ tab, const B0Box* __restrict__ bx,
   tab[b.tab_off + e] = acc;
 }
 
-// One CTA per row a (over the rows of all boxes): B0[a][b] = T--(ia-ib, ja-jb) - T+-(ia+ib, ja-jb)
-// - T-+(ia-ib, ja+jb) + T++(ia+ib, ja+jb); threads run along ib so stores and table reads are contiguous.
+// One CTA per (box, ca, ja, cb, jb): the ni x ni block B0[(ca, ja, ia)][(cb, jb, ib)].  With
+// r1 = ja - jb + nj - 1, r2 = ja + jb, D = ia - ib + ni - 1, S = ia + ib:
+//   B0 = (T--[r1][D] - T-+[r2][D]) - (T+-[r1][S] - T++[r2][S]) = U[D] - V[S],
+// U and V built once per block in shared memory, so each entry costs one FP64 subtraction (FP64 throughput
+// per SM is low on sm_103; the block then writes at HBM speed).  blockIdx.x runs over the blocks of all
+// boxes (blk_off = prefix sums of 4 nj^2).
 __global__ void __launch_bounds__(256) k_fill(double* __restrict__ out, const double* __restrict__ tab,
-                                              const B0Box* __restrict__ bx, int n_boxes, long n_rows) {
-  for (long ag = blockIdx.x; ag < n_rows; ag += gridDim.x) {
-    const B0Box b = bx[b0_find_box(bx, n_boxes, ag)];
-    const int ni = b.ni, nj = b.nj, n_sd = b.n_sd;
-    const long n2 = 2L * n_sd;
-    const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
-    const long per = (long)nx2 * ny2;
-    const long a = ag - b.row_off;
-    const int ca = (int)(a / n_sd);
-    const int pa = (int)(a - (long)ca * n_sd);
-    const int ja = pa / ni, ia = pa - ja * ni;
-    double* row = out + b.out_off + a * n2;
-    for (int cb = 0; cb < 2; ++cb) {
-      const double* t = tab + b.tab_off + (long)((ca * 2 + cb) * 4) * per;
-      for (int jb = 0; jb < nj; ++jb) {
-        const double* tmm = t + (long)(ja - jb + nj - 1) * nx2;
-        const double* tpm = t + per + (long)(ja - jb + nj - 1) * nx2;
-        const double* tmp = t + 2 * per + (long)(ja + jb) * nx2;
-        const double* tpp = t + 3 * per + (long)(ja + jb) * nx2;
-        double* o = row + (long)cb * n_sd + (long)jb * ni;
-        for (int ib = threadIdx.x; ib < ni; ib += blockDim.x) {
-          const int D = ia - ib + ni - 1, S = ia + ib;
-          o[ib] = tmm[D] - tpm[S] - tmp[D] + tpp[S];
-        }
-      }
-    }
+                                              const B0Box* __restrict__ bx, const long* __restrict__ blk_off,
+                                              int n_boxes) {
+  extern __shared__ __align__(16) unsigned char fill_smem[];
+  const long blk = blockIdx.x;
+  int lo = 0, hi = n_boxes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (blk_off[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const B0Box b = bx[lo];
+  const int ni = b.ni, nj = b.nj, n_sd = b.n_sd;
+  const long n2 = 2L * n_sd;
+  const int nx2 = 2 * ni - 1, ny2 = 2 * nj - 1;
+  const long per = (long)nx2 * ny2;
+  long r = blk - blk_off[lo];
+  const int jb = (int)(r % nj);
+  r /= nj;
+  const int ja = (int)(r % nj);
+  r /= nj;
+  const int cb = (int)(r & 1), ca = (int)(r >> 1);
+  double* U = reinterpret_cast<double*>(fill_smem);
+  double* V = U + nx2;
+  const double* t = tab + b.tab_off + (long)((ca * 2 + cb) * 4) * per;
+  const long r1 = (long)(ja - jb + nj - 1) * nx2, r2 = (long)(ja + jb) * nx2;
+  for (int d = threadIdx.x; d < nx2; d += blockDim.x) {
+    U[d] = t[r1 + d] - t[2 * per + r2 + d];
+    V[d] = t[per + r1 + d] - t[3 * per + r2 + d];
+  }
+  __syncthreads();
+  double* o = out + b.out_off + ((long)ca * n_sd + (long)ja * ni) * n2 + (long)cb * n_sd + (long)jb * ni;
+  for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
+    const int ia = e / ni, ib = e - ia * ni;
+    o[(long)ia * n2 + ib] = U[ia - ib + ni - 1] - V[ia + ib];
   }
 }
 
 }  // namespace
 
 fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
-  const int Nx = c->Nx, Ny = c->Ny, Mx = c->Mx, My = c->My;
+  const int Nx = c->Nx, Mx = c->Mx, My = c->My;
   const double h = c->g.h;
   const int nb = (int)boxes.size();
   b0_layout(boxes);
-  long tab_n = 0, rows = 0, max_tab = 0;
+  long tab_n = 0, max_tab = 0;
   for (B0Box& b : boxes) {
     const long t = 16L * (2 * b.ni - 1) * (2 * b.nj - 1);
     b.tab_off = tab_n;
     tab_n += t;
     if (t > max_tab) max_tab = t;
-    rows += 2L * b.n_sd;
   }
   // twiddles exp(-2 pi i m / L) for the two DCT lengths L = 2 Mx, 2 My
   std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);
@@ -210,6 +223,7 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   }
   double *d_twx = nullptr, *d_twy = nullptr, *d_T1 = nullptr, *d_g = nullptr, *d_tab = nullptr;
   B0Box* d_bx = nullptr;
+  long* d_off = nullptr;
   fsi_status st = FSI_OK;
   do {
     if (cudaMalloc(&d_twx, twx.size() * 8) != cudaSuccess || cudaMalloc(&d_twy, twy.size() * 8) != cudaSuccess ||
@@ -236,9 +250,27 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
                      1.0 / ((double)Mx * (double)My), nullptr, nullptr, 0.0, 0.0, 0.0, c->stream);
     if (st != FSI_OK) break;
     k_tables<<<dim3((unsigned)((max_tab + 127) / 128), nb), 128, 0, c->stream>>>(d_tab, d_bx, d_g, Mx, My, h);
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
-    k_fill<<<nsm * 16, 256, 0, c->stream>>>(out, d_tab, d_bx, nb, rows);
+    {
+      std::vector<long> off(nb + 1, 0);
+      int max_ni = 1;
+      for (int k = 0; k < nb; ++k) {
+        off[k + 1] = off[k] + 4L * boxes[k].nj * boxes[k].nj;
+        if (boxes[k].ni > max_ni) max_ni = boxes[k].ni;
+      }
+      if (cudaMalloc(&d_off, (size_t)(nb + 1) * sizeof(long)) != cudaSuccess) {
+        cudaGetLastError();
+        st = FSI_ERR_OOM;
+        break;
+      }
+      if (cudaMemcpyAsync(d_off, off.data(), (size_t)(nb + 1) * sizeof(long), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess) {
+        st = FSI_ERR_CUDA;
+        break;
+      }
+      const size_t sm = (size_t)2 * (2 * max_ni - 1) * sizeof(double);
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_fill<<<(unsigned)off[nb], 256, sm, c->stream>>>(out, d_tab, d_bx, d_off, nb);
+    }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
   cudaFree(d_twx);
@@ -247,6 +279,7 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   cudaFree(d_g);
   cudaFree(d_tab);
   cudaFree(d_bx);
+  cudaFree(d_off);
   return st;
 }
 

@@ -148,21 +148,21 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     k_col_source<T><<<(nc + 31) / 32, dim3(8, 32), 0, c->stream>>>(src, lvl, ps, col0, nc, d_bx, n_boxes, inv2h);
     {
       dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
-      const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
+      const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
       if (cx.per == 1) dst::k_xf<T, 1><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
       else if (cx.per == 2) dst::k_xf<T, 2><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
       else dst::k_xf<T, 4><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
     }
     {
       dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf), nc);
-      const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
+      const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
       if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
       else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
       else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
     }
     {
       dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
-      const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
+      const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
       if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
       else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
       else dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);

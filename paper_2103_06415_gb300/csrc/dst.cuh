@@ -11,7 +11,8 @@
 
 namespace dst {
 
-// Twiddle table tw[m] = exp(-2 pi i m / L), m < L (host-computed in double).
+// Twiddle table tw[m] = exp(-2 pi i m / L), m < L (host-computed in double); the passes below copy it into
+// shared memory (stage_twiddles) before their first barrier, so the stages read it there.
 template <typename T, int PER>
 __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int logL,
                                           const typename C2<T>::t* __restrict__ tw) {
@@ -106,6 +107,27 @@ __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int log
   }
 }
 
+// Copies the twiddles to tws when the launch gave the kernel room for them (dynamic shared memory of at
+// least end_bytes, tws + L being the end of that area) and returns the table the stages should read.
+template <typename T>
+__device__ __forceinline__ const typename C2<T>::t* stage_twiddles(typename C2<T>::t* tws,
+                                                                   const typename C2<T>::t* __restrict__ tw, int L,
+                                                                   size_t end_bytes) {
+  unsigned dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  if ((size_t)dyn < end_bytes) return tw;
+  for (int m = threadIdx.x; m < L; m += blockDim.x) tws[m] = tw[m];
+  return tws;
+}
+
+// Dynamic shared memory of a pass: its buffers (base_elems complex entries) plus the twiddles when the sum
+// stays within limit_bytes.
+template <typename T>
+inline size_t pass_smem(size_t base_elems, int L, size_t limit_bytes = 200 * 1024) {
+  const size_t e = sizeof(typename C2<T>::t);
+  return (base_elems + L) * e <= limit_bytes ? (base_elems + L) * e : base_elems * e;
+}
+
 // Pack rows r0 (real part) and r1 (imag part) of length N into the odd extension in buffer f.
 // Rows beyond nrows read as zero.  Caller syncs afterwards.
 template <typename T>
@@ -168,6 +190,7 @@ __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = 1 << logL;
+  const c2* tws = stage_twiddles<T>(buf + (long)nf * L, tw, L, ((size_t)nf + 1) * L * sizeof(c2));
   const int row0 = blockIdx.x * 2 * nf;
   in += (long)blockIdx.y * in_bs;
   out += (long)blockIdx.y * out_bs;
@@ -180,7 +203,7 @@ __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld
     put_pair<T>(buf + (long)f * L, L, n, a, b);
   }
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tw);
+  block_fft<T, PER>(buf, L, logL, tws);
   const int nr = 2 * nf;
   for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
     const int r = idx % nr, k = idx / nr;
@@ -205,6 +228,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   c2* buf2 = buf + (long)nf * (1 << logL);
   const int L = 1 << logL;
+  const c2* tws = stage_twiddles<T>(buf + 3L * nf * L, tw, L, (3 * (size_t)nf + 1) * L * sizeof(c2));
   const int row0 = blockIdx.x * 2 * nf;
   in += (long)blockIdx.y * in_bs;
   outw += (long)blockIdx.y * out_bs;
@@ -219,7 +243,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     put_pair<T>(buf + (long)f * L, L, n, a, b);
   }
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tw);
+  block_fft<T, PER>(buf, L, logL, tws);
   const int nr = 2 * nf;
   const T* ring = sp.ring;
   for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     put_one<T>(buf2 + (long)(nf + (r >> 1)) * L, L, l0, st, r & 1);
   }
   __syncthreads();
-  block_fft<T, 2 * PER>(buf2, L, logL, tw);
+  block_fft<T, 2 * PER>(buf2, L, logL, tws);
   for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
     const int r = idx % nr, j = idx / nr;
     const int k = row0 + r;
@@ -282,6 +306,7 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = 1 << logL;
+  const c2* tws = stage_twiddles<T>(buf + 2L * nf * L, tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
   const int row0 = blockIdx.x * 2 * nf;
   inw += (long)blockIdx.y * in_bs;
   ins += (long)blockIdx.y * in_bs;
@@ -298,7 +323,7 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
                 v1 ? ins[(long)(r0 + 1) * in_ld + n] : T(0));
   }
   __syncthreads();
-  block_fft<T, 2 * PER>(buf, L, logL, tw);
+  block_fft<T, 2 * PER>(buf, L, logL, tws);
   for (int idx = threadIdx.x; idx < 2 * nf * N; idx += blockDim.x) {
     const int f2 = idx / N, i = idx - f2 * N;  // f2 = local row
     const int r = row0 + f2;

@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restr
     if (threadIdx.x < 4) wf[(long)j * ps + i] = ring_value(wc, ps, nx, ny, i, j);
     else sf[(long)j * ps + i] = ring_value(sc, ps, nx, ny, i, j);
   }
+  const c2* tws =
+      dst::stage_twiddles<T>(buf + (long)nf * L, side ? twx : twy, L, ((size_t)nf * L + L) * sizeof(c2));
   dst::zero_ends<T>(buf, nf, L);
   for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
     const int f = idx / N, n = idx - f * N;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restr
     dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
   }
   __syncthreads();
-  dst::block_fft<T, PER>(buf, L, logL, side ? twx : twy);
+  dst::block_fft<T, PER>(buf, L, logL, tws);
   const int dmap[2][4] = {{0, 1, 4, 5}, {2, 3, 6, 7}};
   for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
     const int f = idx / N, n = idx - f * N;
@@ -304,7 +306,7 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     if (st != FSI_OK) return st;
   } else {
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
-    const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
+    const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     switch (cx.per) {
       case 1: dst::k_xf<T, 1><<<grid, cx.nthr, sm, c->stream>>>(rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf); break;
       case 2: dst::k_xf<T, 2><<<grid, cx.nthr, sm, c->stream>>>(rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf); break;
@@ -324,7 +326,7 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
       }
     } else {
       dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
-      const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
+      const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
       switch (cy.per) {
         case 1: dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
         case 2: dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
@@ -340,7 +342,7 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     if (st != FSI_OK) return st;
   } else {
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
-    const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
+    const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
     switch (cx.per) {
       case 1: dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
       case 2: dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
@@ -364,15 +366,15 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g) {
   const int per = Lmax <= 1024 ? 1 : Lmax / 1024;
   const int nf_y = 4 * per * 256 / (1 << c->logLy), nf_x = 4 * per * 256 / (1 << c->logLx);
   const int nblk_y = (4 + 2 * nf_y - 1) / (2 * nf_y), nblk_x = (4 + 2 * nf_x - 1) / (2 * nf_x);
-  const size_t sm = (size_t)4 * per * 256 * sizeof(c2);
+  const size_t sm = dst::pass_smem<T>((size_t)4 * per * 256, Lmax);
   const c2* twx = (const c2*)c->twx;
   const c2* twy = (const c2*)c->twy;
   static bool attrs = false;  // per instantiation
   if (!attrs) {
     attrs = true;
-    cudaFuncSetAttribute(k_ring_dst<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_ring_dst<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_ring_dst<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   prof_mark(c, KC_RING);
   const dim3 grid(nblk_y + nblk_x);

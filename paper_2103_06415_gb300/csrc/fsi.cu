@@ -62,7 +62,8 @@ struct FsiArgs {
   double* part;  // [2 * gridDim] per-CTA maxima
   unsigned long long* phase_ns;  // [16] accumulated wall time per kernel phase
   int* ctrl;     // [1] iterations of the last step, [2] step index, [4] Kinv valid, [5] solves of the last
-                 // step, [6] Kinv rebuilds so far, [8..11] vertex box touched by the corrector source
+                 // step, [6] Kinv rebuilds so far, [7] current X buffer, [8..11] vertex box touched by the
+                 // corrector source, [12] Newton-Schulz refreshes in the last step
   int* status;
   double* hist;
   int hist_cap;
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   __syncthreads();
 
   bool converged = false;
-  int it = 0, solves_total = 0;
+  int it = 0, solves_total = 0, refreshes = 0;
   for (; it < a.max_iters; ++it) {
     // ---- A: body points, P, right-hand side.  Points are split over the CTAs (four threads per point, one
     // per hat vertex; FP64 throughput per SM is low on sm_103), published, then every CTA takes all of them.
@@ -716,6 +717,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         if (s == kMaxSolves - 1) break;
         if (!fresh && s > 0 && ratio > kNsTrigger) {  // X is stale for this K: refresh it, keep f and r
           ns_refresh();
+          ++refreshes;
           fresh = true;
           gd_prev = 0.0;  // the next correction is the first one made with the new X: no ratio for it
         } else if (s > 0) {
@@ -826,6 +828,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       a.ctrl[4] = kinv_valid;
       a.ctrl[7] = cur;
       a.ctrl[5] = solves_total;
+      a.ctrl[12] = refreshes;
     }
     // vertex box that the corrector source (E0^T P^T f, then curl) can touch: cells of the final P, grown
     // by the E0 support (1.5 cells), the hat support (1 cell) and the curl stencil (1 cell)

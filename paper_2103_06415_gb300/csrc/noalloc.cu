@@ -140,7 +140,7 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
   const Shape cx = shape_for(logLx), cy = shape_for(logLy);
   {  // forward x, transposed into T1
     dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf));
-    const size_t sm = (size_t)cx.nf * Lx * sizeof(c2);
+    const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     if (cx.per == 1) dst::k_xf<T, 1><<<grid, cx.nthr, sm, st>>>(rhs, Nx, 0, Ny, Nx, T1, ldT, 0, twx, logLx, cx.nf);
     else if (cx.per == 2) dst::k_xf<T, 2><<<grid, cx.nthr, sm, st>>>(rhs, Nx, 0, Ny, Nx, T1, ldT, 0, twx, logLx, cx.nf);
     else dst::k_xf<T, 4><<<grid, cx.nthr, sm, st>>>(rhs, Nx, 0, Ny, Nx, T1, ldT, 0, twx, logLx, cx.nf);
@@ -158,14 +158,14 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
     sp.Mx = Mx;
     sp.My = My;
     dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf));
-    const size_t sm = (size_t)3 * cy.nf * Ly * sizeof(c2);
+    const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
     if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
     else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
     else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
   }
   {  // inverse x into the interior of the caller's vertex arrays (row stride nx + 1)
     dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf));
-    const size_t sm = (size_t)2 * cx.nf * Lx * sizeof(c2);
+    const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
     const long fld = nx + 1;
     if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, st>>>(T2w, T2s, ldX, 0, Ny, Nx, w, s, fld, 0, 0, twx, logLx, cx.nf);
     else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, st>>>(T2w, T2s, ldX, 0, Ny, Nx, w, s, fld, 0, 0, twx, logLx, cx.nf);
