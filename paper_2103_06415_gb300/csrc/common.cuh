@@ -25,6 +25,27 @@ __device__ __forceinline__ void dev_set_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Programmatic dependent launch: a kernel launched with pdl_launch may be set up by the GPU before its
+// predecessor in the stream has finished; it waits (griddepcontrol.wait) until that predecessor has
+// completed and its writes are visible.  Launched without the attribute, the wait is a no-op.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Row stride (in elements) for a vertex array of nx+1 columns, padded so rows start 32-byte aligned
 // for both float and double.
 static inline long padded_stride(int ncols) { return ((long)ncols + 7) / 8 * 8; }

@@ -186,6 +186,7 @@ template <typename T, int PER>
 __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                             T* __restrict__ out, long out_ld, long out_bs,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
+  pdl_enter();
   using c2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
                                                 T* __restrict__ outw, T* __restrict__ outs, long out_ld,
                                                 long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
                                                 int nf, SpecParams<T> sp) {
+  pdl_enter();
   using c2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
                                             long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
                                             long f_ld, long f_bs, int mode,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
+  pdl_enter();
   using c2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);

@@ -56,6 +56,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const T* __restrict__ s_all,
                                              T* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps, int nx,
                                              int ny, RhsConst<T> k, int first) {
+  pdl_enter();
   __shared__ T tw[10][35], ts[10][35];
   const int g = blockIdx.z;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;  // tile vertex (i0 + 1, j0 + 1) at smem (1, 1)
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restr
                                                   const typename C2<T>::t* __restrict__ twx,
                                                   const typename C2<T>::t* __restrict__ twy, int logLx, int logLy,
                                                   int nblk_y) {
+  pdl_enter();
   using c2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int n
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
                                              int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
                                              T coef) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char src_smem[];
   T* tab = reinterpret_cast<T*>(src_smem);                  // [nb][16]: ut (8) then vt (8)
   SrcPoint* pt = reinterpret_cast<SrcPoint*>(tab + 16 * nb);  // [nb]
@@ -308,9 +311,9 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
     const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     switch (cx.per) {
-      case 1: dst::k_xf<T, 1><<<grid, cx.nthr, sm, c->stream>>>(rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf); break;
-      case 2: dst::k_xf<T, 2><<<grid, cx.nthr, sm, c->stream>>>(rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf); break;
-      default: dst::k_xf<T, 4><<<grid, cx.nthr, sm, c->stream>>>(rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf); break;
+      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 1>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
+      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 2>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
+      default: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 4>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
     }
   }
   prof_mark(c, KC_XF);
@@ -328,9 +331,9 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
       dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
       const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
       switch (cy.per) {
-        case 1: dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
-        case 2: dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
-        default: dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>((const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp); break;
+        case 1: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 1>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
+        case 2: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 2>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
+        default: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 4>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
       }
     }
   }
@@ -344,9 +347,9 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
     const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
     switch (cx.per) {
-      case 1: dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
-      case 2: dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
-      default: dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>((const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf); break;
+      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 1>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
+      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 2>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
+      default: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 4>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
     }
   }
   prof_mark(c, KC_XI);
@@ -379,9 +382,9 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g) {
   prof_mark(c, KC_RING);
   const dim3 grid(nblk_y + nblk_x);
   switch (per) {
-    case 1: k_ring_dst<T, 1><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
-    case 2: k_ring_dst<T, 2><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
-    default: k_ring_dst<T, 4><<<grid, 256, sm, c->stream>>>(wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y); break;
+    case 1: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 1>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
+    case 2: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 2>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
+    default: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 4>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
   }
   prof_mark(c, KC_RING);
   c->launches_per_step += 1;
@@ -407,8 +410,8 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
     k.half_inv_re = T(0.5 / c->g.re);
     k.U = T(c->g.uinf[0]);
     k.V = T(c->g.uinf[1]);
-    k_rhs<T><<<gr, b, 0, c->stream>>>(w_all, s_all, (T*)c->nprev_all, (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx,
-                                      c->ny, k, first);
+    FSI_CUDA_TRY(pdl_launch(k_rhs<T>, gr, dim3(b), 0, c->stream, w_all, s_all, (T*)c->nprev_all, (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx,
+                                      c->ny, k, first));
     prof_mark(c, KC_RHS);
   }
   FSI_CUDA_TRY(cudaGetLastError());
@@ -437,8 +440,8 @@ fsi_status corrector_t(fsi_ctx* c) {
     cudaFuncSetAttribute(k_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   prof_mark(c, KC_SRC);
-  k_src<T><<<gr, 128, sm, c->stream>>>((T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
-                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h));
+  FSI_CUDA_TRY(pdl_launch(k_src<T>, gr, dim3(128), sm, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
+                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h)));
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());
