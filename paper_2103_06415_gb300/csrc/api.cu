@@ -464,7 +464,11 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf, c->nb);
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
-    c->fsi_grid = nsm;  // one CTA per SM: spreads the B0 gathers and the FP64 work, fewest rows per CTA
+    // two rows of the small system per CTA (at most one CTA per SM): small systems leave SMs free for
+    // the kernels of other runs on the same GPU
+    c->fsi_grid = (c->nf + 1) / 2;
+    if (c->fsi_grid < 8) c->fsi_grid = 8;
+    if (c->fsi_grid > nsm) c->fsi_grid = nsm;
     if (c->fsi_grid < fsi_min_grid(c->nf)) return FSI_ERR_UNSUPPORTED;
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
