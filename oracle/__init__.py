@@ -18,10 +18,12 @@ Module map
               weights, action; Algorithm 1)
   fsi.py   -- torsional / rigid bodies, FSI iteration, one time step and runs
               (Eqs. predictor2-corrector2, Algorithm 2, App. A)
+  beam.py  -- deformable flag: corotational Euler-Bernoulli beam, lumped mass,
+              trapezoidal Newmark (Sec. 2.1 Eq. beam, App. A)
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 except the multidomain level coupling, which is only pinned loosely (Lamb-Oseen
 convergence); see the header of ``grid.py``.
 """
 
-from . import grid, ib, fsi  # noqa: F401
+from . import grid, ib, fsi, beam  # noqa: F401

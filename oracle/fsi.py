@@ -14,6 +14,10 @@ and corrector2; the structural right-hand sides follow App. A:
       finest level with homogeneous boundary values (reading R6)
   O6  Newmark update of the structure and the force outputs
 
+Bodies: rigid (prescribed velocity), torsional plate (App. A, reading R3) and the
+deformable flag of ``oracle/beam.py`` (App. A with J_d, S_d, reading R18).  The
+iteration stops on max abs of the structural update (reading R14).
+
 Scaling of the coupling (reading R2): the fluid forcing on faces is
 ``-(ds/h^2) E^T f``; ``f`` is the force per unit length exerted by the fluid on
 the body, so the total force on a body is ``ds * sum_j f_j`` and
@@ -163,11 +167,12 @@ class Sim:
         u, v = grid.faces_from_s(self.s[0], lev)
         e0q = sd.e0(u + self.uinf[0], v + self.uinf[1])       # E0 (C s* + q_inf)
         offs = self._body_offsets()
-        tors = [(b, o) for b, o in zip(self.bodies, offs) if b.kind == "torsional"]
-        theta_k = {id(b): b.theta for b, _ in tors}
-        phi_k = {id(b): b.phi for b, _ in tors}
+        moving = [(b, o) for b, o in zip(self.bodies, offs) if b.kind != "rigid"]
+        # iterate state: theta (torsional) or chi (deformable), and its rate phi or zeta
+        state_k = {id(b): (b.theta if b.kind == "torsional" else b.chi.copy()) for b, _ in moving}
+        rate_k = {id(b): (b.phi if b.kind == "torsional" else b.zeta.copy()) for b, _ in moving}
         for it in range(self.max_iters):
-            pts = np.concatenate([b.points(theta_k.get(id(b))) for b in self.bodies])
+            pts = np.concatenate([b.points(state_k.get(id(b))) for b in self.bodies])
             idx, wts = sd.p_rows(pts)
             cols = np.unique(np.concatenate([idx.ravel(), idx.ravel() + sd.n_sd]))
             pos = {c: k for k, c in enumerate(cols)}
@@ -178,13 +183,26 @@ class Sim:
                     pd[nb + p, pos[idx[p, k] + sd.n_sd]] += wts[p, k]
             kmat = (ds / lev.h ** 2) * pd @ self.b0_cols(cols)[cols, :] @ pd.T
             rhs = pd @ e0q[cols]                                   # P E0 (C s* + q_inf)
-            svec = {}
+            svec, dstate = {}, {}
             for b, o in zip(self.bodies, offs):
                 if b.kind == "rigid":
                     rhs[o:o + b.n_pts] -= b.ur[:, 0]
                     rhs[nb + o:nb + o + b.n_pts] -= b.ur[:, 1]
                     continue
-                th, ph = theta_k[id(b)], phi_k[id(b)]
+                if b.kind == "deformable":
+                    # App. A with J_d = 4 M/dt^2 + K(chi^(k)) and the load map T (reading R18):
+                    # K += (2 ds/dt) T J_d^-1 T^T,  r^c(k) = T ((2/dt)(chi^(k) + J_d^-1 r^zeta(k)) - r^chi)
+                    chi = state_k[id(b)]
+                    rint, ktan = b.internal(chi)
+                    m = b.mass()
+                    jd = np.diag(4.0 / dt ** 2 * m) + ktan
+                    rz = self._r_phi[id(b)] - 4.0 / dt ** 2 * m * chi - rint      # r^zeta(k)
+                    tm = b.t_matrix(nb, o)
+                    kmat += (2.0 * ds / dt) * tm @ np.linalg.solve(jd, tm.T)
+                    rhs -= tm @ (2.0 / dt * (chi + np.linalg.solve(jd, rz)) - self._r_theta[id(b)])
+                    dstate[id(b)] = (jd, rz, tm)
+                    continue
+                th, ph = state_k[id(b)], rate_k[id(b)]
                 rx, ry = b.r(th)
                 sv = np.zeros(2 * nb)
                 sv[o:o + b.n_pts] = b.q() * rx
@@ -198,17 +216,25 @@ class Sim:
                 rhs += sv * (r_theta - 2.0 / dt * r_phi / jac)
             f = np.linalg.solve(kmat, rhs)
             dmax = 0.0
-            for b, _ in tors:
-                th = theta_k[id(b)]
+            for b, _ in moving:
+                if b.kind == "deformable":
+                    jd, rz, tm = dstate[id(b)]
+                    dchi = np.linalg.solve(jd, rz + ds * tm.T @ f)                  # Eq. dchi2
+                    state_k[id(b)] = state_k[id(b)] + dchi
+                    rate_k[id(b)] = 2.0 / dt * state_k[id(b)] - self._r_theta[id(b)]
+                    dmax = max(dmax, float(np.max(np.abs(dchi))))
+                    continue
+                th = state_k[id(b)]
                 jac = b.jac(dt)
                 dth = (self._r_phi[id(b)] - jac * th + ds * svec[id(b)] @ f) / jac   # Eq. dtheta2
-                theta_k[id(b)] = th + dth
-                phi_k[id(b)] = 2.0 / dt * theta_k[id(b)] - self._r_theta[id(b)]
+                state_k[id(b)] = th + dth
+                rate_k[id(b)] = 2.0 / dt * state_k[id(b)] - self._r_theta[id(b)]
                 dmax = max(dmax, abs(dth))
             self.last_p = (idx, wts)
             self.last_svec = svec
+            self.last_dmax = dmax
             if dmax <= self.tol:
-                return f, theta_k, phi_k, it + 1
+                return f, state_k, rate_k, it + 1
         raise NotConverged("FSI iteration did not converge")
 
     # -- O5: corrector (Eq. corrector2) --------------------------------------------------
@@ -235,7 +261,8 @@ class Sim:
         dt = self.dt
         self._r_phi, self._r_theta = {}, {}
         for b in self.bodies:
-            if b.kind == "torsional":
+            if b.kind != "rigid":
+                # torsional: r^{phidot}_n, r^theta_n; deformable: r^zeta_n, r^chi_n (App. A)
                 self._r_phi[id(b)], self._r_theta[id(b)] = b.rhs_terms(dt)
         self.predictor()
         n_it = 0
@@ -244,7 +271,7 @@ class Sim:
             self.corrector(f)
             self.f = f
             for b in self.bodies:
-                if b.kind == "torsional":
+                if b.kind != "rigid":
                     b.advance(theta_k[id(b)], self._r_theta[id(b)], dt)
         rec = {"iters": n_it, "bodies": []}
         offs = self._body_offsets()
@@ -254,6 +281,10 @@ class Sim:
             mom = 0.0
             if b.kind == "torsional" and self.last_svec:
                 mom = self.ds * float(self.last_svec[id(b)] @ self.f)       # ds S f, S at the last iterate
+            if b.kind == "deformable":
+                tip, tip_rate = b.tip_deflection()
+                rec["bodies"].append({"fx": fx, "fy": fy, "moment": 0.0, "theta": tip, "phi": tip_rate})
+                continue
             rec["bodies"].append({"fx": fx, "fy": fy, "moment": mom,
                                   "theta": getattr(b, "theta", 0.0), "phi": getattr(b, "phi", 0.0)})
         self.history.append(rec)
