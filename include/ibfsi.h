@@ -89,7 +89,16 @@ typedef struct {
  * hinge + j*ds*(cos(theta0+theta), sin(theta0+theta)), rotating about the hinge on a spring
  * (inertia, damping, stiffness; Eq. newtons with g_t = 0); theta_init, phi_init = initial deflection and
  * angular velocity.  RIGID: n_pts fixed points pts[2*j], pts[2*j+1] with prescribed velocity ur (same
- * layout; NULL = stationary).  DEFORMABLE returns FSI_ERR_UNSUPPORTED.
+ * layout; NULL = stationary).
+ * DEFORMABLE (Eq. beam, App. A): a flag clamped at hinge, undeformed along the angle theta0, discretised as
+ * n_pts - 1 two-dimensional corotational Euler-Bernoulli beam elements of length ds whose nodes are the
+ * body points (node 0 is the clamp).  Material per unit length: mass_per_length (mass ratio, > 0),
+ * bending_stiffness EI (> 0), stretching_stiffness EA (> 0).  Lumped mass (mass_per_length*ds per free node,
+ * half at the tip; rotary inertia mass*ds^2/12), trapezoidal Newmark in time, J_d = 4M/dt^2 + K(chi) at the
+ * iterate (Eqs. stress2, dchi2).  theta_init = initial tip slope: the flag starts at rest in the
+ * inextensible shape with slope angle theta_init*(2 s/L - s^2/L^2) along its length L; phi_init must be 0.
+ * For this type fsi_get_deflection and history fields 3, 4 report the tip displacement normal to the
+ * undeformed flag and its rate.  n_pts >= 2.
  * All bodies of one context must use the same ds (the surface-stress regularisation weight). */
 typedef struct {
   int type;
@@ -100,6 +109,7 @@ typedef struct {
   double inertia, damping, stiffness;
   const double* pts;
   const double* ur;
+  double mass_per_length, bending_stiffness, stretching_stiffness; /* DEFORMABLE only */
 } fsi_body_desc;
 
 typedef struct {
@@ -154,9 +164,18 @@ fsi_status fsi_sync(fsi_ctx* ctx);
 
 /* Outputs of the last completed step for one body (synchronising).  fx, fy = ds * sum of the surface
  * stress (force by the fluid on the body; c_d = 2 fx, c_l = 2 fy at unit density, speed and chord);
- * moment = ds * S f about the hinge (0 for rigid bodies).  Any output pointer may be NULL. */
+ * moment = ds * S f about the hinge (0 for rigid and deformable bodies).  Any output pointer may be NULL.
+ * fsi_get_deflection: theta, phi of a torsional body; tip displacement and its rate for a deformable one;
+ * 0 for a rigid one. */
 fsi_status fsi_get_forces(fsi_ctx* ctx, int body, double* fx, double* fy, double* moment);
 fsi_status fsi_get_deflection(fsi_ctx* ctx, int body, double* theta, double* phi);
+
+/* State of a DEFORMABLE body after the last completed step (synchronising): chi = node positions and
+ * rotations (x, y, theta) of nodes 1..n_pts-1 (3*(n_pts-1) values, node-major), zeta = their rates,
+ * zetadot = their second derivatives.  cap = capacity of each non-NULL output array in values;
+ * *n_dof receives 3*(n_pts-1).  Other body types: FSI_ERR_INVALID_ARG. */
+fsi_status fsi_get_beam_state(fsi_ctx* ctx, int body, double* chi, double* zeta, double* zetadot, int cap,
+                              int* n_dof);
 
 /* Per-step history of one body: field 0 fx, 1 fy, 2 moment, 3 theta, 4 phi, 5 FSI iterations.
  * Copies the last min(cap, kept) steps, oldest first; *n receives the count (synchronising). */

@@ -48,6 +48,20 @@ fsi_status fsi_op_level_solve_noalloc(int precision, int nx, int ny, double h, d
  * measured rate (2 flops per FMA).  precision: FSI_PREC_FP64 or FSI_PREC_FP32. */
 fsi_status fsi_op_fma_rate(int precision, double* flops_per_s);
 
+/* The structural linearisation of a deformable body as the FSI kernel runs it (Eq. beam; App. A with
+ * J_d = 4M/dt^2 + K(chi); the element, mass and state conventions of the DEFORMABLE body in ibfsi.h), in one
+ * GPU launch: for a flag of n_el elements of length ds clamped at (cx, cy),
+ *   r_zeta = M ((4/dt^2)(chi_n - chi) + (4/dt) zeta_n + zetadot_n) - R(chi)      (FP64)
+ *   x = J_d(chi)^-1 b                                                           (J_d factored in FP32)
+ * chi, chi_n, zeta_n, zetadot_n, b, r_zeta, x: 3*n_el doubles (x, y, theta of nodes 1..n_el);
+ * ref: per element psi, c, s of a reference chord from which the element's rotation is measured (3*n_el
+ * doubles; the chord at chi_n, psi measured from the undeformed direction).  Host pointers; r_zeta or x may
+ * be NULL.  n_el in [1, 1000]; mu, ei, ea, ds, dt > 0.  Runs on the current device, synchronously. */
+fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double ei, double ea, double cx, double cy,
+                             double dt, const double* chi, const double* chi_n, const double* zeta_n,
+                             const double* zetadot_n, const double* ref, const double* b, double* r_zeta,
+                             double* x);
+
 #ifdef __cplusplus
 }
 #endif

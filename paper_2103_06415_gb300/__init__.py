@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
 
-__all__ = ["Context", "B0Set", "level_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
+__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
 
 
 def _dp(a):
@@ -63,6 +63,17 @@ class Context:
     def add_torsional(self, hinge, theta0, n_pts, ds, inertia, damping, stiffness, theta_init, phi_init=0.0):
         b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, n_pts, ds, (ctypes.c_double * 2)(*hinge), theta0, theta_init,
                           phi_init, inertia, damping, stiffness, None, None)
+        bid = ctypes.c_int()
+        check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
+        self.n_bodies += 1
+        return bid.value
+
+    def add_deformable(self, clamp, theta0, n_pts, ds, mass_per_length, bending_stiffness, stretching_stiffness,
+                       tip_angle=0.0):
+        """Clamped flag of ``n_pts - 1`` corotational beam elements (Eq. beam, App. A); starts at rest with
+        tip slope ``tip_angle``.  Deflection outputs are the tip displacement and its rate."""
+        b = _lib.BodyDesc(_lib.FSI_BODY_DEFORMABLE, n_pts, ds, (ctypes.c_double * 2)(*clamp), theta0, tip_angle,
+                          0.0, 0.0, 0.0, 0.0, None, None, mass_per_length, bending_stiffness, stretching_stiffness)
         bid = ctypes.c_int()
         check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
         self.n_bodies += 1
@@ -118,6 +129,15 @@ class Context:
             check(self._lib.fsi_get_history(self._h, body, field, _dp(out), cap, ctypes.byref(n)), "fsi_get_history")
             cols.append(out[: n.value])
         return np.stack(cols, axis=1)
+
+    def beam_state(self, body=0):
+        """(chi, zeta, zetadot) of a flag: [n_pts - 1, 3] arrays of (x, y, theta) of nodes 1.. and rates."""
+        n = ctypes.c_int()
+        check(self._lib.fsi_get_beam_state(self._h, body, None, None, None, 0, ctypes.byref(n)), "fsi_get_beam_state")
+        out = [np.zeros(n.value) for _ in range(3)]
+        check(self._lib.fsi_get_beam_state(self._h, body, _dp(out[0]), _dp(out[1]), _dp(out[2]), n.value,
+                                           ctypes.byref(n)), "fsi_get_beam_state")
+        return tuple(o.reshape(-1, 3) for o in out)
 
     def field(self, level, which):
         out = np.zeros((self.ny + 1, self.nx + 1))
@@ -249,6 +269,19 @@ def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64, dst_method=0):
     check(lib.fsi_op_level_solve_ex(precision, dst_method, nx1 + 1, ny1 + 1, h, re, dt, _dp(rhs), _dp(w), _dp(s)),
           "fsi_op_level_solve_ex")
     return w, s
+
+
+def beam_solve(n_el, ds, mu, ei, ea, clamp, dt, chi, chi_n, zeta_n, zetadot_n, ref, b):
+    """Structural linearisation of a flag on the GPU (see ``fsi_op_beam_solve``): returns (r_zeta, x) with
+    r_zeta = M((4/dt^2)(chi_n - chi) + (4/dt) zeta_n + zetadot_n) - R(chi) and x = J_d(chi)^-1 b."""
+    lib = _lib.load()
+    arrs = [np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (chi, chi_n, zeta_n, zetadot_n, ref, b)]
+    nd = 3 * n_el
+    assert all(v.size == nd for v in arrs)
+    rz, x = np.zeros(nd), np.zeros(nd)
+    check(lib.fsi_op_beam_solve(n_el, ds, mu, ei, ea, clamp[0], clamp[1], dt, *[_dp(v) for v in arrs], _dp(rz),
+                                _dp(x)), "fsi_op_beam_solve")
+    return rz, x
 
 
 def fma_rate(precision):

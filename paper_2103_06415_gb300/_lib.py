@@ -39,7 +39,8 @@ class BodyDesc(ctypes.Structure):
                 ("hinge", ctypes.c_double * 2), ("theta0", ctypes.c_double), ("theta_init", ctypes.c_double),
                 ("phi_init", ctypes.c_double), ("inertia", ctypes.c_double), ("damping", ctypes.c_double),
                 ("stiffness", ctypes.c_double), ("pts", ctypes.POINTER(ctypes.c_double)),
-                ("ur", ctypes.POINTER(ctypes.c_double))]
+                ("ur", ctypes.POINTER(ctypes.c_double)), ("mass_per_length", ctypes.c_double),
+                ("bending_stiffness", ctypes.c_double), ("stretching_stiffness", ctypes.c_double)]
 
 
 class Box(ctypes.Structure):
@@ -72,6 +73,7 @@ SIGNATURES = {
     "fsi_get_forces": (_INT, [_P, _INT, _D, _D, _D]),
     "fsi_get_deflection": (_INT, [_P, _INT, _D, _D]),
     "fsi_get_history": (_INT, [_P, _INT, _INT, _D, _INT, ctypes.POINTER(_INT)]),
+    "fsi_get_beam_state": (_INT, [_P, _INT, _D, _D, _D, _INT, ctypes.POINTER(_INT)]),
     "fsi_get_field": (_INT, [_P, _INT, _INT, _D]),
     "fsi_set_field": (_INT, [_P, _INT, _INT, _D]),
     "fsi_get_operator_entries": (_INT, [_P, _I64, _I64, _INT, _D]),
@@ -86,6 +88,7 @@ SIGNATURES = {
     "fsi_op_level_solve_ex": (_INT, [_INT, _INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,
                                      _D, _D]),
     "fsi_op_fma_rate": (_INT, [_INT, _D]),
+    "fsi_op_beam_solve": (_INT, [_INT] + [ctypes.c_double] * 7 + [_D] * 8),
     "fsi_op_level_solve_noalloc": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _P, _P, _P, _P]),
 }

@@ -10,8 +10,11 @@
 #include <vector>
 #include "internal.h"
 
-int fsi_kernel_max_ctas_per_sm(int nf, int nb);
-size_t fsi_smem_bytes(int nf, int nb);
+int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c);
+size_t fsi_smem_bytes(const fsi_ctx* c);
+bool fsi_smem_fits(const fsi_ctx* c);
+double beam_initial_state(const BodyHost& h, double ds, double tip, double* chi, double* zeta, double* zdot,
+                          double* ref);
 int fsi_min_grid(int nf);
 int fsi_float_ld(int nf);
 
@@ -319,8 +322,8 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
 extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body_id) {
   if (!c || !b) return FSI_ERR_INVALID_ARG;
   if (c->stage >= 1) return FSI_ERR_STATE;
-  if (b->type == FSI_BODY_DEFORMABLE) return FSI_ERR_UNSUPPORTED;
-  if (b->type != FSI_BODY_RIGID && b->type != FSI_BODY_TORSIONAL) return FSI_ERR_INVALID_ARG;
+  if (b->type != FSI_BODY_RIGID && b->type != FSI_BODY_TORSIONAL && b->type != FSI_BODY_DEFORMABLE)
+    return FSI_ERR_INVALID_ARG;
   if (b->n_pts < 1 || !(b->ds > 0)) return FSI_ERR_INVALID_ARG;
   if (!c->bodies.empty() && std::fabs(b->ds - c->ds) > 1e-15 * c->ds) return FSI_ERR_UNSUPPORTED;
   BodyHost h = {};
@@ -338,6 +341,37 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
     h.theta = b->theta_init;
     h.phi = b->phi_init;
     h.phidot = (-b->stiffness * b->theta_init - b->damping * b->phi_init) / b->inertia;
+    for (int j = 0; j < b->n_pts; ++j) {
+      c->rigid_pts.push_back(0.0);
+      c->rigid_pts.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+    }
+  } else if (b->type == FSI_BODY_DEFORMABLE) {
+    if (b->n_pts < 2 || !(b->mass_per_length > 0) || !(b->bending_stiffness > 0) || !(b->stretching_stiffness > 0) ||
+        b->phi_init != 0.0 || !std::isfinite(b->theta_init) || !std::isfinite(b->theta0) ||
+        !std::isfinite(b->hinge[0]) || !std::isfinite(b->hinge[1]) || !std::isfinite(b->mass_per_length) ||
+        !std::isfinite(b->bending_stiffness) || !std::isfinite(b->stretching_stiffness))
+      return FSI_ERR_INVALID_ARG;
+    h.hx = b->hinge[0];
+    h.hy = b->hinge[1];
+    h.theta0 = b->theta0;
+    h.mu = b->mass_per_length;
+    h.ei = b->bending_stiffness;
+    h.ea = b->stretching_stiffness;
+    h.el_off = c->ne_tot;
+    const int ne = b->n_pts - 1;
+    const size_t o = c->beam_chi.size();
+    c->beam_chi.resize(o + 3 * ne);
+    c->beam_zeta.resize(o + 3 * ne);
+    c->beam_zdot.resize(o + 3 * ne);
+    c->beam_ref.resize(o + 3 * ne);
+    h.theta = beam_initial_state(h, b->ds, b->theta_init, &c->beam_chi[o], &c->beam_zeta[o], &c->beam_zdot[o],
+                                 &c->beam_ref[o]);
+    c->n_def += 1;
+    c->ne_tot += ne;
+    c->nd_tot += 3 * ne;
+    if (3 * ne > c->nd_max) c->nd_max = 3 * ne;
     for (int j = 0; j < b->n_pts; ++j) {
       c->rigid_pts.push_back(0.0);
       c->rigid_pts.push_back(0.0);
@@ -404,7 +438,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   c->n_bodies = (int)c->bodies.size();
   c->nf = 2 * c->nb;
   if (c->n_bodies > 64) return FSI_ERR_UNSUPPORTED;
-  if (c->nb > 0 && fsi_smem_bytes(c->nf, c->nb) > 200 * 1024) return FSI_ERR_UNSUPPORTED;
+  if (c->nb > 0 && !fsi_smem_fits(c)) return FSI_ERR_UNSUPPORTED;
   const size_t n2 = 2 * (size_t)c->n_sd;
   if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
   fsi_status st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
@@ -426,6 +460,12 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
       d.inertia = h.inertia;
       d.damping = h.damping;
       d.stiffness = h.stiffness;
+      d.el_off = h.el_off;
+      d.mu = h.mu;
+      d.ei = h.ei;
+      d.ea = h.ea;
+      d.ca0 = std::cos(h.theta0);
+      d.sa0 = std::sin(h.theta0);
       bd.push_back(d);
       BodyState s = {};
       s.theta = h.theta;
@@ -459,10 +499,21 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_point_body, pb.data(), pb.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rpts, c->rigid_pts.data(), c->rigid_pts.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_rur, c->rigid_ur.data(), c->rigid_ur.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    if (c->n_def > 0) {
+      const size_t nd = (size_t)c->nd_tot;
+      if (!(c->d_bchi = (double*)ctx_alloc(c, nd * 8)) || !(c->d_bzeta = (double*)ctx_alloc(c, nd * 8)) ||
+          !(c->d_bzdot = (double*)ctx_alloc(c, nd * 8)) || !(c->d_bref = (double*)ctx_alloc(c, nd * 8)) ||
+          !(c->d_G = (double*)ctx_alloc(c, (size_t)c->nf * c->nf * 8)))
+        return FSI_ERR_OOM;
+      FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bchi, c->beam_chi.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
+      FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bzeta, c->beam_zeta.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
+      FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bzdot, c->beam_zdot.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
+      FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bref, c->beam_ref.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
+    }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = fsi_kernel_max_ctas_per_sm(c->nf, c->nb);
+    const int per_sm = fsi_kernel_max_ctas_per_sm(c);
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
     // two rows of the small system per CTA (at most one CTA per SM): small systems leave SMs free for
     // the kernels of other runs on the same GPU
@@ -619,6 +670,31 @@ extern "C" fsi_status fsi_get_deflection(fsi_ctx* c, int body, double* theta, do
   if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
   if (theta) *theta = s.theta;
   if (phi) *phi = s.phi;
+  return st;
+}
+
+extern "C" fsi_status fsi_get_beam_state(fsi_ctx* c, int body, double* chi, double* zeta, double* zetadot, int cap,
+                                         int* n_dof) {
+  if (!c || body < 0 || body >= (int)c->bodies.size()) return FSI_ERR_INVALID_ARG;
+  const BodyHost& h = c->bodies[body];
+  if (h.type != FSI_BODY_DEFORMABLE) return FSI_ERR_INVALID_ARG;
+  const int nd = 3 * (h.n - 1);
+  const size_t o = 3 * (size_t)h.el_off;
+  if (n_dof) *n_dof = nd;
+  if ((chi || zeta || zetadot) && cap < nd) return FSI_ERR_INVALID_ARG;
+  if (!c->d_bchi) {  // before fsi_precompute: the initial state
+    for (int k = 0; k < nd; ++k) {
+      if (chi) chi[k] = c->beam_chi[o + k];
+      if (zeta) zeta[k] = c->beam_zeta[o + k];
+      if (zetadot) zetadot[k] = c->beam_zdot[o + k];
+    }
+    return FSI_OK;
+  }
+  fsi_status st = fsi_sync(c);
+  if (st != FSI_OK && st != FSI_ERR_NOT_CONVERGED) return st;
+  if (chi) FSI_CUDA_TRY(cudaMemcpy(chi, c->d_bchi + o, nd * 8, cudaMemcpyDeviceToHost));
+  if (zeta) FSI_CUDA_TRY(cudaMemcpy(zeta, c->d_bzeta + o, nd * 8, cudaMemcpyDeviceToHost));
+  if (zetadot) FSI_CUDA_TRY(cudaMemcpy(zetadot, c->d_bzdot + o, nd * 8, cudaMemcpyDeviceToHost));
   return st;
 }
 

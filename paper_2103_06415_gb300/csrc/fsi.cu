@@ -15,9 +15,15 @@
 //   D  dtheta = J^{-1}(r^phidot(k) + ds S f), convergence on max |dtheta| (every CTA computes the same
 //      value in the same order, so all CTAs take the same branch without another barrier)
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
+// Deformable bodies (beam.cuh): during A, warps 4-7 of every CTA build J_d(chi^(k)) and r^zeta(k) of each
+// flag, factor J_d and solve for y = J_d^-1 r^zeta(k) and for the columns T J_d^-1 T^T e_r of the rows the
+// CTA owns (published for B); after the A barrier every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from
+// the right-hand side; B adds (2 ds/dt) T J_d^-1 T^T to K; D solves dchi = J_d^-1 (r^zeta(k) + ds T^T f)
+// (Eq. dchi2) and the convergence test takes max |dchi| as well.
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
+#include "beam.cuh"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -33,6 +39,7 @@ constexpr double kNsTrigger = 0.01;  // refinement contraction |d_s| / |d_{s-1}|
 constexpr int BS = 32;       // Cholesky / inverse / GEMM tile (one warp wide)
 constexpr int kMaxBodies = 64;
 constexpr int kMaxR = 4;     // rows (and columns) of the small system owned by one CTA
+constexpr int kMaxRhs = 1 + kMaxR;  // structural solves per flag in phase A: y and the owned columns
 constexpr unsigned FULL = 0xffffffffu;
 
 struct FsiArgs {
@@ -67,6 +74,13 @@ struct FsiArgs {
   int* status;
   double* hist;
   int hist_cap;
+  // deformable bodies: free dofs (x, y, theta of nodes 1..n-1) and elements, context-wide numbering
+  int n_def, nd_tot, ne_tot, nd_max;
+  double* bchi;   // [nd_tot] chi_n (updated at the end of the step)
+  double* bzeta;  // [nd_tot] zeta_n
+  double* bzdot;  // [nd_tot] zetadot_n
+  double* bref;   // [ne_tot][3] chord rotation psi and unit chord (c, s) at chi_n
+  double* G;      // [nf][nf] column-major: column r = T J_d^-1 T^T e_r for deformable rows r
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -320,9 +334,17 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 }
 
 // Shared-memory layout of the kernel (byte offsets, 16-byte aligned): X (or the Cholesky factor in CTA 0
-// during a rebuild), owned K rows, the vectors rhs, f, r, the hat weights, a float4 work row, hat indices.
+// during a rebuild), owned K rows, the vectors rhs, f, r, the hat weights, a float4 work row, hat indices;
+// for deformable bodies the iterate chi^(k), r^zeta(k), the element end forces, the factor blocks of J_d
+// (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
+// right-hand sides of the structural solves.
 struct FsiLayout {
-  size_t xs, krow, vec, pw, work, rf, pidx, total;
+  size_t xs, krow, vec, pw, work, rf, pidx;
+  size_t chi, rz, fab, mi, bm, ey, ys;
+  size_t total;
+};
+struct BeamDims {
+  int nd, ne, nd_max;  // free dofs and elements of all flags, dofs of the largest flag
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 // Row stride (floats) of the float matrices X, X K and K in global and shared memory: a multiple of 4 (rows
@@ -333,7 +355,7 @@ __host__ __device__ inline int fsi_ldx(int nf) {
   if (((l / 4) & 1) == 0) l += 4;
   return l;
 }
-__host__ __device__ inline FsiLayout fsi_layout(int nf, int nb) {
+__host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
   FsiLayout L;
   const size_t lx = (size_t)fsi_ldx(nf);
   const size_t xa = (size_t)nf * lx, xb = (size_t)nf * (size_t)(nf | 1);  // X, or the Cholesky factor
@@ -344,7 +366,14 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb) {
   L.work = L.pw + al16((size_t)4 * nb * 8);
   L.rf = L.work + al16(lx * 16);
   L.pidx = L.rf + al16(lx * 4);
-  L.total = L.pidx + al16((size_t)4 * nb * 4);
+  L.chi = L.pidx + al16((size_t)4 * nb * 4);
+  L.rz = L.chi + al16((size_t)bd.nd * 8);
+  L.fab = L.rz + al16((size_t)bd.nd * 8);
+  L.mi = L.fab + al16((size_t)6 * bd.ne * 8);
+  L.bm = L.mi + al16((size_t)6 * bd.ne * 4);
+  L.ey = L.bm + al16((size_t)9 * bd.ne * 4);
+  L.ys = L.ey + al16((size_t)12 * bd.ne * 4);
+  L.total = L.ys + al16((size_t)kMaxRhs * bd.nd_max * 4);
   return L;
 }
 
@@ -365,6 +394,9 @@ __device__ void load_x(float* Xs, const float* src, int nf, int ldx, uint64_t* b
   if (!tc::mbar_wait(bar, *phase, 2000000000ull)) dev_set_status(status, FSI_ERR_TIMEOUT);
   *phase ^= 1u;
 }
+
+// Barrier of warps 4-7 only (named barrier 1), used while warps 0-3 work on the body points.
+__device__ __forceinline__ void named_sync_upper() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -399,7 +431,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   const int R = (nf + (int)gridDim.x - 1) / (int)gridDim.x;
   const int r0 = min(nf, (int)blockIdx.x * R);
   const int nr = min(nf, r0 + R) - r0;
-  const FsiLayout L = fsi_layout(nf, nb);
+  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max});
   float* Xs = reinterpret_cast<float*>(dyn_smem + L.xs);
   double* Krow = reinterpret_cast<double*>(dyn_smem + L.krow);
   double* rhs_s = reinterpret_cast<double*>(dyn_smem + L.vec);
@@ -409,6 +441,29 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   float4* work4 = reinterpret_cast<float4*>(dyn_smem + L.work);
   float* rf = reinterpret_cast<float*>(dyn_smem + L.rf);  // float copy of the vector X is applied to
   int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
+  double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
+  double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
+  double* fab_s = reinterpret_cast<double*>(dyn_smem + L.fab);  // element end forces [ne][6]
+  float* mi_s = reinterpret_cast<float*>(dyn_smem + L.mi);
+  float* bm_s = reinterpret_cast<float*>(dyn_smem + L.bm);
+  float* ey_s = reinterpret_cast<float*>(dyn_smem + L.ey);
+  float* ys_s = reinterpret_cast<float*>(dyn_smem + L.ys);
+  // rows owned by this CTA that are x / y rows of a free flag node: their structural column is solved here
+  __shared__ int g_body[kMaxR], g_dof[kMaxR];
+  if (tid < kMaxR) {
+    g_body[tid] = -1;
+    g_dof[tid] = 0;
+    if (tid < nr && a.n_def > 0) {
+      const int r = r0 + tid, ca = r / nb, p = r % nb;
+      const int bi = a.point_body[p];
+      const BodyDev b = a.bodies[bi];
+      if (b.type == FSI_BODY_DEFORMABLE && p > b.off) {
+        g_body[tid] = bi;
+        g_dof[tid] = 3 * (p - b.off - 1) + ca;
+      }
+    }
+  }
+  for (int g = tid; g < a.nd_tot; g += nthr) chi_s[g] = a.bchi[g];
 
   // per-CTA copy of the structural state (identical in every CTA)
   for (int bi = tid; bi < a.n_bodies; bi += nthr) {
@@ -455,7 +510,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     {
       const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
       const int p0 = (int)blockIdx.x * per;
-      for (int t0 = 0; t0 < 4 * per; t0 += nthr) {  // whole CTA per pass: every lane joins the shuffles
+      // warps 0-3 take the points (every lane of them joins the shuffles); warps 4-7 the flags
+      for (int t0 = 0; wid < 4 && t0 < 4 * per; t0 += 128) {
         const int t = t0 + tid;
         const int p = p0 + (t >> 2), q = t & 3;
         const bool act = t < 4 * per && p < nb;
@@ -477,6 +533,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
             const double rthk = b_rth[bi] - a.two_dt * th_k + ph_k;
             coef = rthk - a.two_dt * rphik * b_ijac[bi];
+          } else if (b.type == FSI_BODY_DEFORMABLE) {  // node j of the flag at chi^(k); node 0 is the clamp
+            const int j = p - b.off;
+            x = j == 0 ? b.hx : chi_s[3 * (b.el_off + j - 1)];
+            y = j == 0 ? b.hy : chi_s[3 * (b.el_off + j - 1) + 1];
           } else {
             x = a.rpts[2 * p];
             y = a.rpts[2 * p + 1];
@@ -513,6 +573,67 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           a.rhs[2 * nf + nb + p] = uby - ucy + svy * coef;
         }
       }
+      if (wid >= 4 && a.n_def > 0) {
+        // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
+        // r^zeta(k), J_d blocks, the factorization, y = J_d^-1 r^zeta(k) and the structural columns of the
+        // owned rows.
+        const int st = tid - 128;
+        for (int bi = 0; bi < a.n_bodies; ++bi) {
+          const BodyDev b = a.bodies[bi];
+          if (b.type != FSI_BODY_DEFORMABLE) continue;
+          const int N = b.n - 1, e0 = b.el_off, d0 = 3 * e0, ld = 3 * N;
+          float* ey = ey_s + 12 * e0;  // element tangents [N][aa 6 | bb 6], later [Em 9N | y 3N]
+          const beam::Flag F{N,
+                             b.hx,
+                             b.hy,
+                             b.mu,
+                             a.ds,
+                             beam::ElemParams{a.ds, b.ea / a.ds, 2.0 * b.ei / a.ds},
+                             a.four_dt2,
+                             2.0 * a.two_dt,
+                             chi_s + d0,
+                             a.bref + 3 * e0,
+                             a.bchi + d0,
+                             a.bzeta + d0,
+                             a.bzdot + d0,
+                             fab_s + 6 * e0,
+                             ey,
+                             mi_s + 6 * e0,
+                             bm_s + 9 * e0,
+                             rz_s + d0,
+                             ys_s};
+          beam::flag_elements(F, st, 128);
+          named_sync_upper();
+          int nrhs = 1, rdof[kMaxR], rrow[kMaxR];  // owned structural columns of this flag
+#pragma unroll
+          for (int c = 0; c < kMaxR; ++c)
+            if (g_body[c] == bi) {
+              rdof[nrhs - 1] = g_dof[c];
+              rrow[nrhs - 1] = r0 + c;
+              ++nrhs;
+            }
+          beam::flag_assemble(F, st, 128);
+          for (int q = st; q < ld; q += 128)  // unit right-hand sides of the owned columns
+            for (int j = 1; j < nrhs; ++j) ys_s[j * ld + q] = q == rdof[j - 1] ? 1.f : 0.f;
+          named_sync_upper();
+          if (wid == 4) {
+            const beam::Factor FF = beam::flag_factor_view(F);
+            beam::factor(FF);
+            beam::solve(FF, ys_s, ld, nrhs);
+          }
+          named_sync_upper();
+          float* ysol = ey + 9 * N;
+          for (int q = st; q < ld; q += 128) ysol[q] = ys_s[q];
+          for (int j = 1; j < nrhs; ++j) {
+            double* col = a.G + (long)rrow[j - 1] * nf;
+            for (int i = st; i < N; i += 128) {
+              col[b.off + 1 + i] = (double)ys_s[j * ld + 3 * i];
+              col[nb + b.off + 1 + i] = (double)ys_s[j * ld + 3 * i + 1];
+            }
+          }
+          named_sync_upper();
+        }
+      }
     }
     grid.sync();
     for (int e = tid; e < 4 * nb; e += nthr) {
@@ -521,6 +642,19 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     }
     for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
     __syncthreads();
+    if (a.n_def > 0) {  // flags: rhs -= T ((2/dt)(chi^(k) + y) - r^chi), r^chi = (2/dt) chi_n + zeta_n
+      for (int bi = 0; bi < a.n_bodies; ++bi) {
+        const BodyDev b = a.bodies[bi];
+        if (b.type != FSI_BODY_DEFORMABLE) continue;
+        const int N = b.n - 1, d0 = 3 * b.el_off;
+        const float* ysol = ey_s + 12 * b.el_off + 9 * N;
+        for (int q = tid; q < 2 * N; q += nthr) {
+          const int i = q >> 1, c = q & 1, g = d0 + 3 * i + c;
+          rhs_s[c * nb + b.off + 1 + i] -= a.two_dt * (chi_s[g] - a.bchi[g] + (double)ysol[3 * i + c]) - a.bzeta[g];
+        }
+      }
+      __syncthreads();
+    }
     clk.mark(0);
     // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles, double and float copies)
     {
@@ -555,6 +689,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
           const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
           kv += b_kc[ba] * sa * sb;
+        } else if (ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
+          kv += a.ds * a.two_dt * __ldcg(&a.G[(long)cidx * nf + r]);  // (2 ds/dt) T J_d^-1 T^T
         }
         a.K[(long)r * nf + cidx] = kv;
         a.K[(long)cidx * nf + r] = kv;
@@ -747,11 +883,37 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       if (attempt == 1 && blockIdx.x == 0 && tid == 0)
         dev_set_status(a.status, bad ? FSI_ERR_NONFINITE : FSI_ERR_NOT_CONVERGED);
     }
-    // ---- D: dtheta per torsional body (Eq. dtheta2), convergence on max |dtheta| (same in every CTA)
+    // ---- D: dtheta per torsional body (Eq. dtheta2), dchi per flag (Eq. dchi2), convergence on the largest
+    // update (same in every CTA)
     double dmax = 0.0;
     bool finite = true;
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
+      if (b.type == FSI_BODY_DEFORMABLE) {  // dchi = J_d^-1 (r^zeta(k) + ds T^T f)
+        const int N = b.n - 1, e0 = b.el_off, d0 = 3 * e0;
+        for (int q = tid; q < 3 * N; q += nthr) {
+          const int i = q / 3, k = q - 3 * i;
+          double v = rz_s[d0 + q];
+          if (k < 2) v += a.ds * f_s[k * nb + b.off + 1 + i];
+          ys_s[q] = (float)v;
+        }
+        __syncthreads();
+        if (wid == 0) {
+          const beam::Factor F{mi_s + 6 * e0, bm_s + 9 * e0, ey_s + 12 * e0, mi_s + 6 * (e0 + beam::meet(N)), N};
+          beam::solve(F, ys_s, 3 * N, 1);
+        }
+        __syncthreads();
+        double dm = 0.0;
+        for (int q = tid; q < 3 * N; q += nthr) {
+          const double d = (double)ys_s[q];
+          chi_s[d0 + q] += d;
+          dm = isfinite(d) ? fmax(dm, fabs(d)) : INFINITY;
+        }
+        dm = block_max(dm, red);
+        if (!isfinite(dm)) finite = false;
+        dmax = fmax(dmax, dm);
+        continue;
+      }
       if (b.type != FSI_BODY_TORSIONAL) continue;
       const double sn = b_sn[bi], cs = b_cs[bi];
       double part = 0.0;
@@ -798,6 +960,38 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         pm += q * (-sn) * fxp + q * cs * fyp;
       }
       const double sx = block_sum(px, red), sy = block_sum(py, red), sm = block_sum(pm, red);
+      double tipd = 0.0, tipr = 0.0;
+      if (b.type == FSI_BODY_DEFORMABLE) {
+        const int N = b.n - 1, e0 = b.el_off, d0 = 3 * e0;
+        for (int q = tid; q < 3 * N; q += nthr) {  // trapezoidal Newmark update to chi_{n+1}
+          const int g = d0 + q;
+          const double cn = chi_s[g], dc = cn - a.bchi[g], zo = a.bzeta[g];
+          a.bzdot[g] = a.four_dt2 * dc - 2.0 * a.two_dt * zo - a.bzdot[g];
+          a.bzeta[g] = a.two_dt * dc - zo;
+          a.bchi[g] = cn;
+        }
+        for (int e = tid; e < N; e += nthr) {  // reference chords at chi_{n+1} for the next step
+          double xa = b.hx, ya = b.hy;
+          if (e > 0) {
+            xa = chi_s[d0 + 3 * (e - 1)];
+            ya = chi_s[d0 + 3 * (e - 1) + 1];
+          }
+          const double dx = chi_s[d0 + 3 * e] - xa, dy = chi_s[d0 + 3 * e + 1] - ya;
+          const double il = beam::rsqrt_d(fma(dx, dx, dy * dy));
+          const double c = dx * il, sc = dy * il;
+          double* rf = a.bref + 3 * (e0 + e);
+          rf[0] += beam::chord_rotation(rf[1], rf[2], c, sc);
+          rf[1] = c;
+          rf[2] = sc;
+        }
+        __syncthreads();
+        if (tid == 0) {  // tip displacement normal to the undeformed flag, and its rate
+          const int gt = d0 + 3 * (N - 1);
+          const double len = (double)N * a.ds;
+          tipd = (chi_s[gt] - (b.hx + len * b.ca0)) * (-b.sa0) + (chi_s[gt + 1] - (b.hy + len * b.sa0)) * b.ca0;
+          tipr = a.bzeta[gt] * (-b.sa0) + a.bzeta[gt + 1] * b.ca0;
+        }
+      }
       if (tid == 0) {
         BodyState& s = a.st[bi];
         s.fx = a.ds * sx;
@@ -811,13 +1005,16 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           s.phi = ph_new;
           s.theta_k = th_new;
           s.phi_k = ph_new;
+        } else if (b.type == FSI_BODY_DEFORMABLE) {
+          s.theta = tipd;
+          s.phi = tipr;
         }
         double* hrow = a.hist + ((long)slot * a.n_bodies + bi) * 6;
         hrow[0] = s.fx;
         hrow[1] = s.fy;
         hrow[2] = s.moment;
-        hrow[3] = b.type == FSI_BODY_TORSIONAL ? s.theta : 0.0;
-        hrow[4] = b.type == FSI_BODY_TORSIONAL ? s.phi : 0.0;
+        hrow[3] = b.type != FSI_BODY_RIGID ? s.theta : 0.0;
+        hrow[4] = b.type != FSI_BODY_RIGID ? s.phi : 0.0;
         hrow[5] = (double)(it + 1);
         if (!isfinite(s.fx) || !isfinite(s.fy)) dev_set_status(a.status, FSI_ERR_NONFINITE);
       }
@@ -874,14 +1071,28 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
 
 }  // namespace
 
-size_t fsi_smem_bytes(int nf, int nb) { return fsi_layout(nf, nb).total; }
+static BeamDims beam_dims(const fsi_ctx* c) { return BeamDims{c->nd_tot, c->ne_tot, c->nd_max}; }
+
+size_t fsi_smem_bytes(const fsi_ctx* c) { return fsi_layout(c->nf, c->nb, beam_dims(c)).total; }
+
+// dynamic plus static shared memory of the FSI kernel within the per-block opt-in limit of the device
+bool fsi_smem_fits(const fsi_ctx* c) {
+  cudaFuncAttributes fa;
+  int dev = 0, optin = 0;
+  if (cudaFuncGetAttributes(&fa, k_fsi) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return fsi_smem_bytes(c) + fa.sharedSizeBytes <= (size_t)optin;
+}
 
 // row stride (floats) of the float nf x nf matrices of the FSI kernel
 int fsi_float_ld(int nf) { return fsi_ldx(nf); }
 
 // CTAs of the FSI kernel per SM at this size (0: does not fit)
-int fsi_kernel_max_ctas_per_sm(int nf, int nb) {
-  const size_t bytes = fsi_smem_bytes(nf, nb);
+int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c) {
+  const size_t bytes = fsi_smem_bytes(c);
   if (cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -939,10 +1150,19 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.status = c->d_status;
   a.hist = c->d_hist;
   a.hist_cap = c->hist_cap;
+  a.n_def = c->n_def;
+  a.nd_tot = c->nd_tot;
+  a.ne_tot = c->ne_tot;
+  a.nd_max = c->nd_max;
+  a.bchi = c->d_bchi;
+  a.bzeta = c->d_bzeta;
+  a.bzdot = c->d_bzdot;
+  a.bref = c->d_bref;
+  a.G = c->d_G;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = fsi_smem_bytes(c->nf, c->nb);
+  cfg.dynamicSmemBytes = fsi_smem_bytes(c);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

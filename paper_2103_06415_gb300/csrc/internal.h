@@ -14,12 +14,16 @@ struct BodyHost {
   int type, off, n;
   double hx, hy, theta0, inertia, damping, stiffness;
   double theta, phi, phidot;
+  double mu, ei, ea;  // deformable: mass per length, bending and stretching stiffness
+  int el_off;         // deformable: first element in the context-wide element numbering
 };
 
-// Device-side body record (double).
+// Device-side body record (double).  Deformable bodies: elements el_off .. el_off + n - 2, free degrees of
+// freedom 3*el_off .. 3*(el_off + n - 1) - 1 (x, y, theta of nodes 1 .. n-1).
 struct BodyDev {
-  int type, off, n, pad;
+  int type, off, n, el_off;
   double hx, hy, theta0, inertia, damping, stiffness;
+  double mu, ei, ea, ca0, sa0;  // deformable: material, cos / sin of the undeformed direction
 };
 
 // Mutable per-body state on the device.
@@ -82,6 +86,12 @@ struct fsi_ctx {
   int* d_ctrl;     // FSI control words (see fsi.cu)
   unsigned long long* d_phase;  // [8] accumulated FSI kernel phase times (ns)
   int* d_status;
+  // deformable bodies (device state, FP64): chi, zeta, zetadot per free dof; per element the chord
+  // rotation and direction at chi_n (reference for the rotation increment); G = columns of T J_d^-1 T^T
+  // for the small system ([nf][nf], column-major, zero outside deformable blocks)
+  int n_def, nd_tot, ne_tot, nd_max;
+  std::vector<double> beam_chi, beam_zeta, beam_zdot, beam_ref;
+  double *d_bchi, *d_bzeta, *d_bzdot, *d_bref, *d_G;
   double* d_hist;  // [cap][n_bodies][6]
   int hist_cap;
   long long steps_done;

@@ -9,9 +9,11 @@ Configurations (their readings are listed in the design doc):
   flat plate of chord 1 hinged at its leading edge (0,0) on a torsional spring (inertia 1, stiffness 0.5,
   no damping), initial angle 20 deg, 33 points at ds = h; Omega_0 = [-1.2,1.2]^2.
 * ``flag_512x256_3lvl`` -- 3 nested levels of 512x256 cells, finest h = 1/100 on [-1,4.12]x[-1.28,1.28],
-  Re 200, dt 5e-4; body: a torsional plate of 101 points (length 1) hinged at (0,0) standing in for the
-  clamped flag (inertia 0.1/3 = mass ratio 0.1 plate about its end, spring 1e-3 = bending stiffness / L),
-  initial deflection 0.1 rad; Omega_0 = [-0.2,1.2]x[-0.7,0.7] (141 x 141 points).
+  Re 200, dt 5e-4; body: a flag of length 1 clamped at (0,0) along +x, 101 points (100 beam elements at
+  ds = h), mass ratio 0.1, bending stiffness 1e-3, stretching stiffness 1e3, initial tip slope 0.1 rad;
+  Omega_0 = [-0.2,1.2]x[-0.7,0.7] (141 x 141 points).
+* ``flag_512x256_3lvl_torsional`` -- the same grid with a torsional plate of 101 points standing in for
+  the flag (inertia 0.1/3, spring 1e-3, initial angle 0.1 rad).
 """
 
 import numpy as np
@@ -32,9 +34,17 @@ def flag_512x256_3lvl():
     return dict(
         name="flag_512x256_3lvl", nx=512, ny=256, n_levels=3, x0=-1.0, y0=-1.28, h=0.01, re=200.0, dt=5e-4,
         uinf=(1.0, 0.0), steps=2000, sd_box=(-0.2, 1.2, -0.7, 0.7),
-        bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=101, inertia=0.1 / 3.0, damping=0.0,
-                     stiffness=1e-3, theta=0.1)],
+        bodies=[dict(kind="deformable", clamp=(0.0, 0.0), theta0=0.0, n_pts=101, mass=0.1, ei=1e-3, ea=1e3,
+                     tip_angle=0.1)],
         ds=0.01)
+
+
+def flag_512x256_3lvl_torsional():
+    w = flag_512x256_3lvl()
+    w["name"] = "flag_512x256_3lvl_torsional"
+    w["bodies"] = [dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=101, inertia=0.1 / 3.0, damping=0.0,
+                        stiffness=1e-3, theta=0.1)]
+    return w
 
 
 def b0_1024():
@@ -80,6 +90,33 @@ def small_plate(nx=64, ny=32, n_levels=1):
         bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=9, inertia=0.05, damping=0.0,
                      stiffness=0.5, theta=np.deg2rad(20.0))],
         ds=h)
+
+
+def small_flag(nx=64, ny=32, n_levels=1, n_pts=9, tip_angle=0.1):
+    """A small clamped flag the oracle runs in seconds: length (n_pts - 1) h, mass ratio 0.1, bending
+    stiffness 1e-3, stretching stiffness 1e3."""
+    h = 1.0 / 16
+    return dict(
+        name="small_flag_%dx%d_%dlvl" % (nx, ny, n_levels), nx=nx, ny=ny, n_levels=n_levels, x0=-1.0, y0=-1.0,
+        h=h, re=100.0, dt=0.004, uinf=(1.0, 0.0), steps=20, sd_box=(-0.6, 0.8, -0.7, 0.8),
+        bodies=[dict(kind="deformable", clamp=(0.0, 0.0), theta0=0.0, n_pts=n_pts, mass=0.1, ei=1e-3, ea=1e3,
+                     tip_angle=tip_angle)],
+        ds=h)
+
+
+def small_mixed_bodies():
+    """Two flags and a torsional plate sharing one Omega_0 (body and element offsets all non-zero)."""
+    w = small_flag(nx=64, ny=48)
+    w["name"] = "small_mixed_bodies"
+    w["y0"] = -1.5
+    w["sd_box"] = (-0.6, 0.9, -1.0, 1.0)
+    w["bodies"] = [
+        dict(kind="deformable", clamp=(0.0, 0.55), theta0=0.2, n_pts=6, mass=0.2, ei=2e-3, ea=5e2, tip_angle=-0.05),
+        dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=7, inertia=0.05, damping=0.0, stiffness=0.5,
+             theta=np.deg2rad(15.0)),
+        dict(kind="deformable", clamp=(0.0, -0.55), theta0=-0.1, n_pts=9, mass=0.1, ei=1e-3, ea=1e3, tip_angle=0.1),
+    ]
+    return w
 
 
 def serving_grid(n, re=100.0):

@@ -2,29 +2,35 @@
 
 import numpy as np
 
+from oracle import beam as obeam
 from oracle import fsi as ofsi
 
 
-def oracle_sim(w):
+def oracle_sim(w, **kw):
     bodies = []
     for b in w["bodies"]:
         if b["kind"] == "torsional":
             bodies.append(ofsi.TorsionalBody(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"],
                                              b["stiffness"], b["theta"]))
+        elif b["kind"] == "deformable":
+            bodies.append(obeam.Beam(b["clamp"], b["theta0"], b["n_pts"] - 1, w["ds"], b["mass"], b["ei"], b["ea"],
+                                     tip_angle=b["tip_angle"]))
         else:
             bodies.append(ofsi.RigidBody(b["pts"], b.get("ur")))
     return ofsi.Sim(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["n_levels"], w["re"], w["dt"], w["uinf"],
-                    w["sd_box"], bodies, w["ds"])
+                    w["sd_box"], bodies, w["ds"], **kw)
 
 
-def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0):
+def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0, **kw):
     import paper_2103_06415_gb300 as lib
     c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
-                    precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method)
+                    precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method, **kw)
     for b in w["bodies"]:
         if b["kind"] == "torsional":
             c.add_torsional(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"], b["stiffness"],
                             b["theta"])
+        elif b["kind"] == "deformable":
+            c.add_deformable(b["clamp"], b["theta0"], b["n_pts"], w["ds"], b["mass"], b["ei"], b["ea"], b["tip_angle"])
         else:
             c.add_rigid(b["pts"], w["ds"], b.get("ur"))
     if w.get("sd_box") is not None:

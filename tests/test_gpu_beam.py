@@ -1,0 +1,181 @@
+"""Deformable bodies (Eq. beam, App. A) on the GPU against the FP64 oracle (needs a GB300 and the library).
+
+The GPU factors J_d in FP32 (the FP64 structural residual fixes where the FSI iteration converges; J_d only
+steers the path there), so iterates differ from the oracle's by a little more than FP64 rounding.  Runs
+are therefore compared at a tight iteration tolerance (1e-12 on max |dchi|, both sides), where they agree
+to 1e-9, and at the default tolerance, where both sit within ~1e-7 of the same fixed point.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2103_06415_gb300 import workloads as wl
+
+from runners import gpu_context, oracle_history, oracle_sim, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2103_06415_gb300 as p
+    return p
+
+
+def _run(w, n, precision=0, tol=1e-7, use_graph=True):
+    sim, ctx = oracle_sim(w, tol=tol), gpu_context(w, precision=precision, tol=tol, use_graph=use_graph)
+    for _ in range(n):
+        sim.step()
+    ctx.advance(n)
+    return sim, ctx
+
+
+def _oracle_state(sim, body):
+    b = sim.bodies[body]
+    return b.chi.reshape(-1, 3), b.zeta.reshape(-1, 3), b.zetadot.reshape(-1, 3)
+
+
+def _ref_chords(bm, chi_n):
+    nd = bm.nodes(chi_n)
+    d = nd[1:, :2] - nd[:-1, :2]
+    length = np.hypot(d[:, 0], d[:, 1])
+    ca, sa = np.cos(bm.alpha0), np.sin(bm.alpha0)
+    psi = np.arctan2(-d[:, 0] * sa + d[:, 1] * ca, d[:, 0] * ca + d[:, 1] * sa)
+    return np.stack([psi, d[:, 0] / length, d[:, 1] / length], axis=1)
+
+
+@pytest.mark.parametrize("n_el,tip", [(1, 0.05), (2, 0.1), (8, 0.1), (100, 0.3), (101, -0.2), (400, 0.5)])
+def test_beam_linearisation_matches_oracle(lib, n_el, tip):
+    """r^zeta(k) (FP64) and J_d^-1 b (FP32 factor) of the kernel's structural routines vs the oracle."""
+    from oracle import beam as ob
+    dt, ds = 5e-4, 1.0 / n_el
+    bm = ob.Beam((0.1, -0.2), 0.3, n_el, ds, 0.1, 1e-3, 1e3, tip_angle=tip)
+    rng = np.random.default_rng(n_el)
+    chi_n = bm.chi.copy()
+    zeta_n = 0.1 * rng.standard_normal(bm.ndof)
+    zdot_n = rng.standard_normal(bm.ndof)
+    chi = chi_n + 1e-4 * rng.standard_normal(bm.ndof)
+    b = rng.standard_normal(bm.ndof)
+    rz, x = lib.beam_solve(n_el, ds, 0.1, 1e-3, 1e3, (0.1, -0.2), dt, chi, chi_n, zeta_n, zdot_n,
+                           _ref_chords(bm, chi_n), b)
+    m = bm.mass()
+    rint, k = bm.internal(chi)
+    inertia = m * (4.0 / dt ** 2 * (chi_n - chi) + 4.0 / dt * zeta_n + zdot_n)
+    rz_ref = inertia - rint
+    assert np.max(np.abs(rz - rz_ref)) < 1e-13 * max(np.max(np.abs(inertia)), np.max(np.abs(rint)))
+    x_ref = np.linalg.solve(np.diag(4.0 / dt ** 2 * m) + k, b)
+    assert rel_err(x, x_ref) < 2e-5
+
+
+def test_initial_state_matches_oracle(lib):
+    w = wl.small_flag(tip_angle=0.3)
+    sim = oracle_sim(w)
+    ctx = gpu_context(w, precompute=False)
+    chi, zeta, zdot = ctx.beam_state(0)
+    rchi, rzeta, rzdot = _oracle_state(sim, 0)
+    assert np.max(np.abs(chi - rchi)) < 1e-15
+    assert np.all(zeta == 0.0)
+    assert rel_err(zdot, rzdot) < 1e-12
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_flag_run_matches_oracle_at_tight_tolerance(lib, use_graph):
+    w = wl.small_flag()
+    n = 12
+    sim, ctx = _run(w, n, tol=1e-12, use_graph=use_graph)
+    hist, ref = ctx.history(0), oracle_history(sim)
+    for k in (0, 1, 3, 4):                                   # fx, fy, tip displacement, tip rate
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-9, k
+    assert np.all(hist[:, 2] == 0.0)
+    chi, zeta, zdot = ctx.beam_state(0)
+    rchi, rzeta, rzdot = _oracle_state(sim, 0)
+    assert np.max(np.abs(chi - rchi)) < 1e-12
+    assert rel_err(zeta, rzeta) < 1e-9
+    assert rel_err(zdot, rzdot) < 1e-8
+    idx, wts = ctx.interp(sim.nb)
+    ridx, rw = sim.last_p
+    assert np.array_equal(idx, ridx)
+    assert np.max(np.abs(wts - rw)) < 1e-12
+    assert rel_err(ctx.field(0, 0), sim.w[0]) < 1e-9
+
+
+def test_flag_run_at_default_tolerance_is_within_the_iteration_tolerance(lib):
+    w = wl.small_flag()
+    n = 12
+    sim, ctx = _run(w, n)
+    hist, ref = ctx.history(0), oracle_history(sim)
+    assert np.max(np.abs(hist[:, 5] - ref[:, 5])) <= 1          # FSI iterations per step
+    for k in (0, 1, 3, 4):
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-5, k
+    chi, _, _ = ctx.beam_state(0)
+    assert np.max(np.abs(chi - _oracle_state(sim, 0)[0])) < 1e-7
+
+
+def test_mixed_bodies_match_oracle(lib):
+    """Two flags and a torsional plate in one Omega_0: non-zero point, element and dof offsets."""
+    w = wl.small_mixed_bodies()
+    n = 8
+    sim, ctx = _run(w, n, tol=1e-12)
+    for body in range(3):
+        hist, ref = ctx.history(body), oracle_history(sim, body)
+        for k in range(5):
+            if np.max(np.abs(ref[:, k])) > 0:
+                assert rel_err(hist[:, k], ref[:, k]) < 1e-9, (body, k)
+    for body in (0, 2):
+        chi, _, _ = ctx.beam_state(body)
+        assert np.max(np.abs(chi - _oracle_state(sim, body)[0])) < 1e-12
+
+
+def test_flag_fp32_fluid_path_error_vs_oracle(lib):
+    w = wl.small_flag()
+    n = 12
+    sim, ctx = _run(w, n, precision=1)
+    hist, ref = ctx.history(0), oracle_history(sim)
+    for k in (0, 1, 3, 4):
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-4, k
+
+
+def test_flag_no_slip_after_corrector_gpu(lib):
+    """P E0 (C s + q_inf) equals the node velocities T zeta_{n+1} (Eq. corrector2)."""
+    from oracle import grid as og
+    w = wl.small_flag()
+    sim, ctx = _run(w, 5, tol=1e-12)
+    s = ctx.field(0, 1)
+    lev = sim.levels[0]
+    u, v = og.faces_from_s(s, lev)
+    e0q = sim.sd.e0(u + 1.0, v)
+    idx, wts = ctx.interp(sim.nb)
+    ub = np.concatenate([(wts * e0q[idx]).sum(1), (wts * e0q[idx + sim.sd.n_sd]).sum(1)])
+    _, zeta, _ = ctx.beam_state(0)
+    vel = np.zeros((sim.nb, 2))
+    vel[1:] = zeta[:, :2]
+    target = np.concatenate([vel[:, 0], vel[:, 1]])
+    assert np.max(np.abs(ub - target)) < 1e-10 * max(1.0, np.max(np.abs(ub)))
+
+
+def test_deformable_arguments_are_validated(lib):
+    w = wl.small_flag()
+    c = lib.Context(w["nx"], w["ny"], 1, w["x0"], w["y0"], w["h"], w["re"], w["dt"])
+    for bad in (dict(n_pts=1), dict(mass=0.0), dict(ei=-1.0), dict(ea=0.0)):
+        kw = dict(n_pts=9, mass=0.1, ei=1e-3, ea=1e3)
+        kw.update(bad)
+        with pytest.raises(lib.FsiError):
+            c.add_deformable((0.0, 0.0), 0.0, kw["n_pts"], w["ds"], kw["mass"], kw["ei"], kw["ea"])
+    c.close()
+
+
+def test_config2_flag_mixed_vs_fp64(lib):
+    """The 512 x 256 x 3-level flag (101 points): FP32 fluid + FP32 J_d against the FP64 path."""
+    w = wl.flag_512x256_3lvl()
+    n = 20
+    out = []
+    for prec in (0, 1):
+        ctx = gpu_context(w, precision=prec)
+        ctx.advance(n)
+        out.append((ctx.history(0), ctx.beam_state(0)[0]))
+        ctx.close()
+    (h64, c64), (h32, c32) = out
+    for k in (0, 1, 3, 4):
+        assert rel_err(h32[:, k], h64[:, k]) < 1e-5, k
+    assert np.max(np.abs(c32 - c64)) < 1e-6
+    assert np.all(h64[:, 5] <= 6)
