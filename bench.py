@@ -385,9 +385,13 @@ def main():
         solves = max(st2["last_solves"], iters)
         refreshes = st2.get("last_refreshes", 1)
         # per launch: P B0 P^T (16 FMA per lower-triangle entry) per iteration, 2 Newton-Schulz steps of two
-        # nf^3 products per refresh, X r per solve and K f per residual
+        # nf^3 products per refresh, X r per solve and K f per residual; for each flag of N elements per
+        # iteration: elements (~250 flops each), the block factorization (~100 per block) and the
+        # structural solves (y, one column of T J_d^-1 T^T per translational row, dchi: 54 flops per block)
+        n_el = sum(b["n_pts"] - 1 for b in w["bodies"] if b["kind"] == "deformable")
         flops = (iters * 16 * 2 * nf * (nf + 1) / 2 + refreshes * 2 * 2 * 2 * nf ** 3
-                 + solves * 2 * nf * nf + max(solves - iters, 0) * 2 * nf * nf)
+                 + solves * 2 * nf * nf + max(solves - iters, 0) * 2 * nf * nf
+                 + iters * n_el * (250 + 100 + (2 + 2 * n_el) * 54))
         fsi_ms = shares["fsi"][0]
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, derived
@@ -398,10 +402,8 @@ def main():
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (DESIGN.md)",
                 "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                         "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-                "traffic": 1.681664e6,
-                "traffic_note": "dram read+write bytes per launch from one ncu capture of the same kernel on "
-                                "the reduced-Omega_0 variant (same nf, B0 gathers of the same point set "
-                                "dominate it; profiles/k_fsi_and_dst_passes_reduced_omega0.md)",
+                "traffic": None,
+                "traffic_note": "no ncu capture of this version of the kernel yet",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
                 "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
                 "secondary": secondary}
@@ -429,7 +431,7 @@ def main():
                 "p50_ms": statistics.median(times), "p99_ms": float(np.percentile(times, 99)),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if prec == lib.FSI_PREC_FP32 else "f64", "data": "synthetic",
-                "config": {"workload": w["name"] + " (torsional-plate stand-in for the flag)",
+                "config": {"workload": w["name"] + " (clamped flag, corotational beam elements)",
                            "levels": w["n_levels"], "nx": w["nx"], "ny": w["ny"], "cells_per_step": cells,
                            "body_points": sum(b["n_pts"] for b in w["bodies"]), "n_sd": stats["n_sd"],
                            "b0_seconds": b0_s, "l2": "flushed between timed steps (512 MiB write)",

@@ -13,8 +13,10 @@
 // the internal forces and the structural residual r^zeta(k) are FP64, because the fixed point of the FSI
 // iteration is defined by them; J_d = 4M/dt^2 + K is assembled, factored and solved in FP32.  A different
 // J_d changes only the path of the iteration: at its fixed point J_d^-1 (r^zeta + ds T^T f) = 0, and the
-// terms that J_d^-1 adds to the small matrix and to its right-hand side cancel.  With the Jacobi-scaled
-// condition number of J_d of a few tens, the FP32 solves are accurate to ~1e-7 relative.
+// terms that J_d^-1 adds to the small matrix and to its right-hand side cancel.  The kernel applies the
+// FP32 solves only to residuals that vanish at the fixed point (r^zeta + ds T^T f_prev), so their float
+// errors vanish there too.  With the Jacobi-scaled condition number of J_d of a few tens, the FP32 solves
+// are accurate to ~1e-7 relative.
 //
 // J_d is block tridiagonal (3 x 3 blocks: D_i on the diagonal, B_i = J_{i+1,i} below it) and is factored
 // from both ends at once (two lanes of one warp in lockstep, m = (N-1)/2 the meeting block):
@@ -304,7 +306,9 @@ struct Flag {
   float* mi;                              // [N][6] D_i (assembly), factor blocks afterwards
   float* bm;                              // [N][9] B_i
   double* rz;                             // [3N] r^zeta(k)
-  float* y0;                              // [3N] float copy of r^zeta(k) (first right-hand side), may be NULL
+  float* y0;                              // [3N] first right-hand side r^zeta(k) + ds T^T f (float), or NULL
+  const double* f;                        // surface stress of nodes 1..N: x at f[i], y at f[fstride + i]; or NULL
+  int fstride;
 };
 
 // Pass 1: element end forces (FP64) and tangent blocks (FP32).
@@ -361,7 +365,7 @@ __device__ inline void flag_assemble(const Flag& F, int t, int nt) {
       const double rz =
           (k < 2 ? mt : mr) * (F.four_dt2 * (F.chi_n[g] - F.chi[g]) + F.four_dt * F.zeta_n[g] + F.zdot_n[g]) - R;
       F.rz[g] = rz;
-      if (F.y0) F.y0[g] = (float)rz;
+      if (F.y0) F.y0[g] = (float)(k < 2 && F.f ? rz + F.ds * F.f[k * F.fstride + i] : rz);
     }
   }
 }

@@ -97,7 +97,9 @@ extern "C" fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double e
                    nullptr,
                    nullptr,
                    nullptr,
-                   nullptr};
+                   nullptr,
+                   nullptr,
+                   0};
   a.chi = d;
   a.b = d + 5 * nd;
   a.rz_out = d + 6 * nd;

@@ -16,10 +16,12 @@
 //      value in the same order, so all CTAs take the same branch without another barrier)
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
 // Deformable bodies (beam.cuh): during A, warps 4-7 of every CTA build J_d(chi^(k)) and r^zeta(k) of each
-// flag, factor J_d and solve for y = J_d^-1 r^zeta(k) and for the columns T J_d^-1 T^T e_r of the rows the
-// CTA owns (published for B); after the A barrier every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from
-// the right-hand side; B adds (2 ds/dt) T J_d^-1 T^T to K; D solves dchi = J_d^-1 (r^zeta(k) + ds T^T f)
-// (Eq. dchi2) and the convergence test takes max |dchi| as well.
+// flag, factor J_d and solve for y = J_d^-1 (r^zeta(k) + ds T^T f_prev) (f_prev: the last surface stress)
+// and for the columns T J_d^-1 T^T e_r of the rows the CTA owns (published for B); after the A barrier
+// every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from the right-hand side; B adds (2 ds/dt) T J_d^-1 T^T
+// to K; C starts from f_prev with the residual rows rhs + (2 ds/dt) T J_d^-1 T^T f_prev - K f_prev (the
+// same system as Eq. stress2, in a form whose FP32 structural solves act on vanishing residuals); D solves
+// dchi = J_d^-1 (r^zeta(k) + ds T^T f) (Eq. dchi2) and the convergence test takes max |dchi| as well.
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
@@ -464,6 +466,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     }
   }
   for (int g = tid; g < a.nd_tot; g += nthr) chi_s[g] = a.bchi[g];
+  // with flags the small system is solved for the correction to the previous surface stress f_prev (the
+  // last iterate, or the last step's f): see the refinement below
+  if (a.n_def > 0)
+    for (int k = tid; k < nf; k += nthr) f_s[k] = a.f[k];
 
   // per-CTA copy of the structural state (identical in every CTA)
   for (int bi = tid; bi < a.n_bodies; bi += nthr) {
@@ -575,8 +581,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
-        // r^zeta(k), J_d blocks, the factorization, y = J_d^-1 r^zeta(k) and the structural columns of the
-        // owned rows.
+        // r^zeta(k), J_d blocks, the factorization, y = J_d^-1 (r^zeta(k) + ds T^T f_prev) and the structural
+        // columns of the owned rows.
         const int st = tid - 128;
         for (int bi = 0; bi < a.n_bodies; ++bi) {
           const BodyDev b = a.bodies[bi];
@@ -601,7 +607,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
                              mi_s + 6 * e0,
                              bm_s + 9 * e0,
                              rz_s + d0,
-                             ys_s};
+                             ys_s,
+                             f_s + b.off + 1,
+                             nb};
           beam::flag_elements(F, st, 128);
           named_sync_upper();
           int nrhs = 1, rdof[kMaxR], rrow[kMaxR];  // owned structural columns of this flag
@@ -700,6 +708,31 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     }
     grid.sync();
     for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
+    // Flags.  The structural right-hand side was formed from J_d^-1 (r^zeta(k) + ds T^T f_prev) instead of
+    // J_d^-1 r^zeta(k); the two differ by (2 ds/dt) T J_d^-1 T^T f_prev, which the owned residual rows add
+    // back here with the same entries of T J_d^-1 T^T that K holds.  Both FP32 structural solves then act
+    // on quantities that vanish at the fixed point, whose float errors therefore vanish with them.
+    __shared__ double gfp_s[kMaxR];
+    if (a.n_def > 0) {
+      for (int c = wid; c < kMaxR; c += nw) {
+        double acc = 0.0;
+        if (c < nr) {
+          const int r = r0 + c;
+          const BodyDev b = a.bodies[a.point_body[r % nb]];
+          if (b.type == FSI_BODY_DEFORMABLE)
+            for (int q = lane; q < 2 * b.n; q += 32) {
+              const int m = q < b.n ? b.off + q : nb + b.off + q - b.n;
+              const long gi = r < m ? (long)r * nf + m : (long)m * nf + r;  // the entry phase B used
+              acc += __ldcg(&a.G[gi]) * f_s[m];
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) gfp_s[c] = a.ds * a.two_dt * acc;
+      }
+    } else if (tid < kMaxR) {
+      gfp_s[tid] = 0.0;
+    }
+    __syncthreads();
     clk.mark(1);
     // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
     // Newton-Schulz refresh of the float inverse for the current K: X <- 2X - (X K) X, kNsSteps times
@@ -811,8 +844,25 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       bool done = false, bad = false;
       int s = 0;
       double gd_prev = 0.0, worst_ratio = 0.0;
+      const bool warm = a.n_def > 0;  // start from f_prev: one residual (and barrier) before the first solve
+      if (warm) {
+        if (attempt > 0) {
+          for (int k = tid; k < nf; k += nthr) f_s[k] = 0.0;
+          __syncthreads();
+        }
+        for (int c = wid; c < nr; c += nw) {
+          const double* kr = Krow + (long)c * nf;
+          double acc = 0.0;
+          for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          acc = warp_sum(acc);
+          if (lane == 0) res1[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
+        }
+        grid.sync();
+        for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&res1[k]);
+        __syncthreads();
+      }
       for (; s < kMaxSolves; ++s) {
-        const double* r = s == 0 ? rhs_s : r_s;
+        const double* r = (s == 0 && !warm) ? rhs_s : r_s;
         for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
         __syncthreads();
         unsigned dbits = 0u, xbits = 0u;  // max |d|, max |f| as float bit patterns
@@ -828,7 +878,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             p3 += xv.w * rv.w;
           }
           const float acc = (p0 + p1) + (p2 + p3);
-          const double xi = (s == 0 ? 0.0 : f_s[i]) + (double)acc;
+          const double xi = (s == 0 && !warm ? 0.0 : f_s[i]) + (double)acc;
           f_s[i] = xi;
           const float xf = (float)xi;
           dbits = max(dbits, isfinite(xf) ? __float_as_uint(fabsf(acc)) : 0x7f800000u);
@@ -864,7 +914,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           double acc = 0.0;
           for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
           acc = warp_sum(acc);
-          if (lane == 0) ((s & 1) ? res1 : res0)[r0 + c] = rhs_s[r0 + c] - acc;
+          if (lane == 0) ((s & 1) ? res1 : res0)[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
         }
         grid.sync();
         clk.sub(12);

@@ -106,9 +106,9 @@ def small_flag(nx=64, ny=32, n_levels=1, n_pts=9, tip_angle=0.1):
 
 def small_mixed_bodies():
     """Two flags and a torsional plate sharing one Omega_0 (body and element offsets all non-zero)."""
-    w = small_flag(nx=64, ny=48)
+    w = small_flag(nx=64, ny=64)
     w["name"] = "small_mixed_bodies"
-    w["y0"] = -1.5
+    w["y0"] = -2.0
     w["sd_box"] = (-0.6, 0.9, -1.0, 1.0)
     w["bodies"] = [
         dict(kind="deformable", clamp=(0.0, 0.55), theta0=0.2, n_pts=6, mass=0.2, ei=2e-3, ea=5e2, tip_angle=-0.05),
