@@ -211,7 +211,8 @@ fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);
  * created, measured on the device: 0 body points / P / right-hand side, 1 assembly of P B0 P^T, 2 refresh
  * of the float inverse, 3 rebuild of the float inverse, 4 refinement solves, 5 double residuals,
  * 6 dtheta and convergence, 7 outputs; a finer split of 2, 4 and 5: 8 columns of X K, 9 rows of the new
- * X, 10 reload of X, 11 d = X r, 12 residual rows and barrier, 13 residual gather.
+ * X, 10 reload of X, 11 d = X r, 12 residual rows and barrier, 13 residual gather; inside 0, measured on
+ * their own threads: 14 the body points (warps 0-3), 15 the linearisation and solves of the flags (warps 4-7).
  * out[0..n-1] (n <= 16 meaningful; synchronising). */
 fsi_status fsi_get_phase_times(fsi_ctx* ctx, double* out, int n);
 

@@ -192,7 +192,7 @@ class Context:
 
     PHASES = ("points_rhs", "assemble_PB0PT", "inverse_refresh", "inverse_rebuild", "refine_solves",
               "residuals", "dtheta", "outputs", "ns_xk_columns", "ns_new_x_rows", "ns_reload_x", "solve_d",
-              "residual_rows_barrier", "residual_gather")
+              "residual_rows_barrier", "residual_gather", "a_points_warps0_3", "a_flags_warps4_7")
 
     def phase_times(self):
         """Accumulated device wall time (ms) per phase of the FSI-iteration kernel."""

@@ -18,14 +18,16 @@
 // errors vanish there too.  With the Jacobi-scaled condition number of J_d of a few tens, the FP32 solves
 // are accurate to ~1e-7 relative.
 //
-// J_d is block tridiagonal (3 x 3 blocks: D_i on the diagonal, B_i = J_{i+1,i} below it) and is factored
-// from both ends at once (two lanes of one warp in lockstep, m = (N-1)/2 the meeting block):
-//   top     S_0 = D_0,      F_i = B_i S_i^-1,        S_{i+1} = D_{i+1} - F_i B_i^T          (i < m)
-//   bottom  T_{N-1} = D_{N-1}, H_{i-1} = B_{i-1}^T T_i^-1, T_{i-1} = D_{i-1} - H_{i-1} B_{i-1} (i > m)
-//   middle  Z = S_m + T_m - D_m
-// and a solve J x = b runs forward from both ends (y_i = b_i - F_{i-1} y_{i-1}, w_i = b_i - H_i w_{i+1}),
-// takes x_m = Z^-1 (y_m + w_m - b_m), then substitutes back outwards (x_i = S_i^-1 (y_i - B_i^T x_{i+1}),
-// x_i = T_i^-1 (w_i - B_{i-1} x_{i-1})): chains of about N/2 block steps instead of N.
+// J_d is block tridiagonal (3 x 3 blocks: D_i on the diagonal, R_i = J_{i,i+1} to the right) and is factored
+// by block cyclic reduction (a block Cholesky factorization in nested-dissection order): at level l
+// (stride s = 2^l) the active rows are those with (i + 1) % s == 0; every other one ((i + 1)/s odd) is
+// eliminated, in parallel, and its two active neighbours k absorb it:
+//   D_k -= J_{k,r} D_r^-1 J_{r,k},   R_k <- -J_{k,r'} D_{r'}^-1 J_{r',k+2s}     (r = k - s, r' = k + s)
+// until the one row left at the top has no neighbour.  A solve reduces the right-hand sides level by level
+// (b_k -= J_{k,r} D_r^-1 b_r) and substitutes back from the top (x_r = D_r^-1 (b_r - J_{r,r-s} x_{r-s}
+// - J_{r,r+s} x_{r+s})).  The dependent chain is about 2 log2(N) parallel steps, where a sequential
+// (Thomas or twisted) factorization has N or N/2: measured on GB300 a sequential 3 x 3 block step costs
+// ~200 cycles of latency, so the chain length is what sets the time.
 #pragma once
 #include <cmath>
 #include "internal.h"
@@ -120,7 +122,7 @@ __device__ __forceinline__ void inv3s(const float S[6], float Si[6]) {
   const float c11 = S[0] * S[5] - S[2] * S[2];
   const float c12 = S[1] * S[2] - S[0] * S[4];
   const float c22 = S[0] * S[3] - S[1] * S[1];
-  const float id = 1.0f / (S[0] * c00 + S[1] * c01 + S[2] * c02);
+  const float id = __frcp_rn(S[0] * c00 + S[1] * c01 + S[2] * c02);
   Si[0] = c00 * id;
   Si[1] = c01 * id;
   Si[2] = c02 * id;
@@ -138,155 +140,182 @@ __device__ __forceinline__ void mul_fs(const float Bk[9], const float Si[6], flo
       E[3 * p + q] = Bk[3 * p] * Si[sidx(0, q)] + Bk[3 * p + 1] * Si[sidx(1, q)] + Bk[3 * p + 2] * Si[sidx(2, q)];
 }
 
-// S = D - E * Bk^T (symmetric result)
-__device__ __forceinline__ void schur(const float D[6], const float E[9], const float Bk[9], float S[6]) {
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = p; q < 3; ++q)
-      S[sidx(p, q)] =
-          D[sidx(p, q)] - (E[3 * p] * Bk[3 * q] + E[3 * p + 1] * Bk[3 * q + 1] + E[3 * p + 2] * Bk[3 * q + 2]);
-}
-
-__device__ __forceinline__ void load_block(const float* src, bool transpose, float out[9]) {
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) out[3 * p + q] = transpose ? src[3 * q + p] : src[3 * p + q];
-}
-
-// Factor arrays of one body (shared memory, N blocks): Mi[N][6] (D_i on entry; S_i^-1 / T_i^-1 on exit,
-// entry m then holds Z^-1 through Zi), Bm[N][9] (B_i, i < N-1), Em[N][9] (F_i for i < m, H_i for
-// m <= i < N-1).
-struct Factor {
-  float* Mi;
-  const float* Bm;
-  float* Em;
-  float* Zi;
+// Block cyclic reduction arrays of one flag (shared memory, N blocks):
+//   D[N][6]  diagonal blocks (symmetric); replaced by their inverse at the level the row is eliminated
+//   R[N][9]  R_i = J_{i,i+s} for the current level (zero where there is no right neighbour); frozen once
+//            row i is eliminated
+//   L[N][9]  L_i = J_{i,i-s} at the level row i is eliminated (copied before the left neighbour moves on)
+struct Bcr {
+  float* D;
+  float* R;
+  float* L;
   int N;
 };
 
-__host__ __device__ __forceinline__ int meet(int N) { return (N - 1) / 2; }
-
-// Twisted factorization: lanes 0 (top) and 1 (bottom) of the calling warp; the other lanes only join the
-// shuffle.  The whole warp must call.
-__device__ inline void factor(const Factor& F) {
-  const int lane = threadIdx.x & 31;
-  const int N = F.N, m = meet(N);
-  const bool top = lane == 0;
-  const int steps = top ? m : N - 1 - m;
-  const int nmax = N - 1 - m;  // >= m
-  float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Dm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int i0 = top ? 0 : N - 1;
-  if (lane < 2) {
+__device__ __forceinline__ void load9(const float* p, float a[9]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      S[k] = F.Mi[6 * i0 + k];
-      Dm[k] = F.Mi[6 * m + k];
-    }
-  }
-  for (int t = 0; t < nmax; ++t) {
-    if (lane < 2 && t < steps) {
-      const int i = top ? t : N - 1 - t;
-      const int nx = top ? i + 1 : i - 1;
-      float Si[6], Bk[9], E[9], Dn[6];
-      load_block(F.Bm + 9 * (top ? i : i - 1), !top, Bk);
+  for (int k = 0; k < 9; ++k) a[k] = p[k];
+}
+__device__ __forceinline__ void load6(const float* p, float a[6]) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Dn[k] = F.Mi[6 * nx + k];
-      inv3s(S, Si);
-      mul_fs(Bk, Si, E);
-      schur(Dn, E, Bk, S);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) F.Mi[6 * i + k] = Si[k];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) F.Em[9 * (top ? i : i - 1) + k] = E[k];
-    }
-  }
-  // Z = S_m + T_m - D_m (lane 1 hands T_m to lane 0)
-  float Z[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float tm = __shfl_down_sync(0xffffffffu, S[k], 1);
-    Z[k] = S[k] + tm - Dm[k];
-  }
-  if (lane == 0) {
-    float Zi[6];
-    inv3s(Z, Zi);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) F.Zi[k] = Zi[k];
-  }
-  __syncwarp();
+  for (int k = 0; k < 6; ++k) a[k] = p[k];
 }
 
-// Solve J x = b for RHS r = lane / 2 < nrhs (lanes 2r: top, 2r+1: bottom) in place: Y[r] (stride ldy,
-// 3N floats) holds b on entry and x on exit.  The whole warp must call; Mi, Bm, Em, Zi from factor().
-__device__ inline void solve(const Factor& F, float* Y, int ldy, int nrhs) {
-  const int lane = threadIdx.x & 31;
-  const int N = F.N, m = meet(N);
-  const int rr = lane >> 1;
-  const bool top = (lane & 1) == 0;
-  const bool act = rr < nrhs;
-  float* y = Y + (long)(act ? rr : 0) * ldy;
-  const int steps = top ? m : N - 1 - m;
-  const int nmax = N - 1 - m;
-  float v[3] = {0.f, 0.f, 0.f}, bm[3] = {0.f, 0.f, 0.f};
-  const int i0 = top ? 0 : N - 1;
-  if (act) {
+// Rows of level s (a power of two): eliminated i = (2m + 1) s - 1, kept k = (2m + 2) s - 1 (m = 0, 1, ...).
+
+// Factorization, by threads t = 0..nt-1 of a group with barrier sync() (all of them must call).
+template <class Sync>
+__device__ __forceinline__ void bcr_factor(const Bcr& B, int t, int nt, Sync sync) {
+  const int N = B.N;
+  for (int s = 1; s <= N; s <<= 1) {
+    const int n_el = (N / s + 1) >> 1;  // rows (2m+1)s - 1 < N
+    for (int mm = t; mm < n_el; mm += nt) {  // eliminated rows: invert D, keep J_{i,i-s}
+      const int i = (2 * mm + 1) * s - 1;
+      float d[6], di[6];
+      load6(B.D + 6 * i, d);
+      inv3s(d, di);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      v[k] = y[3 * i0 + k];
-      bm[k] = y[3 * m + k];
-    }
-  }
-  for (int t = 0; t < nmax; ++t) {  // forward from both ends
-    if (act && t < steps) {
-      const int i = top ? t + 1 : N - 2 - t;  // block being reduced
-      const float* E = F.Em + 9 * (top ? i - 1 : i);
-      float b[3], nv[3];
+      for (int k = 0; k < 6; ++k) B.D[6 * i + k] = di[k];
+      if (i - s >= 0) {
+        float r[9];
+        load9(B.R + 9 * (i - s), r);  // J_{i-s,i}
 #pragma unroll
-      for (int k = 0; k < 3; ++k) b[k] = y[3 * i + k];
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int p = 0; p < 3; ++p) nv[p] = b[p] - (E[3 * p] * v[0] + E[3 * p + 1] * v[1] + E[3 * p + 2] * v[2]);
+          for (int q = 0; q < 3; ++q) B.L[9 * i + 3 * p + q] = r[3 * q + p];
+      } else {  // no left neighbour: zero, so that the solve may read it with weight zero
 #pragma unroll
-      for (int k = 0; k < 3; ++k) v[k] = nv[k];
-      if (i != m) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) y[3 * i + k] = v[k];
+        for (int k = 0; k < 9; ++k) B.L[9 * i + k] = 0.f;
       }
     }
-  }
-  // middle block: x_m = Z^-1 (y_m + w_m - b_m); the bottom lane's w_m comes by shuffle
-  float xm[3];
+    sync();
+    const int n_kept = N / (2 * s);  // rows (2m+2)s - 1 < N
+    for (int mm = t; mm < n_kept; mm += nt) {  // kept rows absorb their eliminated neighbours
+      const int k = (2 * mm + 2) * s - 1;
+      const int r = k - s, r2 = k + s;
+      float d[6], rr[9], dinv[6];
+      load6(B.D + 6 * k, d);
+      load9(B.R + 9 * r, rr);  // J_{r,k}
+      load6(B.D + 6 * r, dinv);
+      {  // D_k -= J_{k,r} Dinv_r J_{r,k} = rr^T Dinv rr
+        float a[9];  // a = Dinv rr
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float w = __shfl_down_sync(0xffffffffu, v[k], 1);
-    xm[k] = v[k] + w - bm[k];
-  }
-  float x[3];
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-  for (int p = 0; p < 3; ++p) x[p] = F.Zi[sidx(p, 0)] * xm[0] + F.Zi[sidx(p, 1)] * xm[1] + F.Zi[sidx(p, 2)] * xm[2];
+          for (int q = 0; q < 3; ++q)
+            a[3 * p + q] = dinv[sidx(p, 0)] * rr[q] + dinv[sidx(p, 1)] * rr[3 + q] + dinv[sidx(p, 2)] * rr[6 + q];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) x[k] = __shfl_sync(0xffffffffu, x[k], lane & ~1);
-  if (act && top) {
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) y[3 * m + k] = x[k];
-  }
-  for (int t = 0; t < nmax; ++t) {  // back substitution outwards
-    if (act && t < steps) {
-      const int i = top ? m - 1 - t : m + 1 + t;
-      float C[9];
-      load_block(F.Bm + 9 * (top ? i : i - 1), top, C);  // top: B_i^T, bottom: B_{i-1}
-      const float* Si = F.Mi + 6 * i;
-      float g[3];
+          for (int q = p; q < 3; ++q) d[sidx(p, q)] -= rr[p] * a[q] + rr[3 + p] * a[3 + q] + rr[6 + p] * a[6 + q];
+      }
+      float nr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (r2 < N) {
+        float rk[9], dinv2[6], e[9];
+        load9(B.R + 9 * k, rk);  // J_{k,r2}
+        load6(B.D + 6 * r2, dinv2);
+        mul_fs(rk, dinv2, e);  // e = J_{k,r2} Dinv_{r2}
 #pragma unroll
-      for (int p = 0; p < 3; ++p) g[p] = y[3 * i + p] - (C[3 * p] * x[0] + C[3 * p + 1] * x[1] + C[3 * p + 2] * x[2]);
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int p = 0; p < 3; ++p) x[p] = Si[sidx(p, 0)] * g[0] + Si[sidx(p, 1)] * g[1] + Si[sidx(p, 2)] * g[2];
+          for (int q = p; q < 3; ++q)
+            d[sidx(p, q)] -= e[3 * p] * rk[3 * q] + e[3 * p + 1] * rk[3 * q + 1] + e[3 * p + 2] * rk[3 * q + 2];
+        if (k + 2 * s < N) {  // new coupling J_{k,k+2s} = -e J_{r2,r2+s}
+          float r2r[9];
+          load9(B.R + 9 * r2, r2r);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) y[3 * i + k] = x[k];
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              nr[3 * p + q] = -(e[3 * p] * r2r[q] + e[3 * p + 1] * r2r[3 + q] + e[3 * p + 2] * r2r[6 + q]);
+        }
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < 6; ++k2) B.D[6 * k + k2] = d[k2];
+#pragma unroll
+      for (int k2 = 0; k2 < 9; ++k2) B.R[9 * k + k2] = nr[k2];
     }
+    sync();
   }
-  __syncwarp();
+}
+
+// y_out = S y for symmetric S
+__device__ __forceinline__ void symv(const float S[6], const float y[3], float out[3]) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) out[p] = S[sidx(p, 0)] * y[0] + S[sidx(p, 1)] * y[1] + S[sidx(p, 2)] * y[2];
+}
+
+// Solve J x = b for nrhs <= 8 right-hand sides Y[j] (stride ldy, 3N floats each; b on entry, x on exit) with
+// the factor of bcr_factor, by threads t = 0..nt-1 of a group with barrier sync() (all of them must call;
+// nt a multiple of 8).  Each (row, right-hand side) pair of a level is one thread's work item; a missing
+// neighbour is read at a valid index with weight zero so that both neighbours' loads issue at once.
+template <class Sync>
+__device__ __forceinline__ void bcr_solve(const Bcr& B, float* Y, int ldy, int nrhs, int t, int nt, Sync sync) {
+  const int N = B.N;
+  int top = 1;
+  while (top * 2 <= N) top <<= 1;
+  // work mapping: one right-hand side -> all threads on rows; several -> 8 groups, group j = right-hand side j
+  const int j = nrhs == 1 ? 0 : (t & 7);
+  const int m0 = nrhs == 1 ? t : (t >> 3), dm = nrhs == 1 ? nt : (nt >> 3);
+  const bool on = j < nrhs;
+  float* y = Y + (long)(on ? j : 0) * ldy;
+  for (int s = 1; s <= N; s <<= 1) {  // reduction: kept rows take b_k -= J_{k,r} Dinv_r b_r from both sides
+    const int n_kept = N / (2 * s);
+    for (int mm = m0; on && mm < n_kept; mm += dm) {
+      const int k = (2 * mm + 2) * s - 1;
+      const int r = k - s, r2 = k + s;
+      const bool has2 = r2 < N;
+      const int q2 = has2 ? r2 : r;
+      float d1[6], c1[9], y1[3], d2[6], c2[9], y2[3], bk[3];
+      load6(B.D + 6 * r, d1);
+      load9(B.R + 9 * r, c1);  // J_{r,k}; J_{k,r} = c1^T
+      load6(B.D + 6 * q2, d2);
+      load9(B.L + 9 * q2, c2);  // J_{r2,k}; J_{k,r2} = c2^T
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        y1[p] = y[3 * r + p];
+        y2[p] = y[3 * q2 + p];
+        bk[p] = y[3 * k + p];
+      }
+      const float w2 = has2 ? 1.f : 0.f;
+      float u1[3], u2[3];
+      symv(d1, y1, u1);
+      symv(d2, y2, u2);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+        y[3 * k + p] = bk[p] - (c1[p] * u1[0] + c1[3 + p] * u1[1] + c1[6 + p] * u1[2]) -
+                       w2 * (c2[p] * u2[0] + c2[3 + p] * u2[1] + c2[6 + p] * u2[2]);
+    }
+    sync();
+  }
+  for (int s = top; s >= 1; s >>= 1) {  // back substitution from the top level down
+    const int n_el = (N / s + 1) >> 1;
+    for (int mm = m0; on && mm < n_el; mm += dm) {
+      const int r = (2 * mm + 1) * s - 1;
+      const bool has1 = r - s >= 0, has2 = r + s < N;
+      const int k1 = has1 ? r - s : r, k2 = has2 ? r + s : r;
+      float cl[9], cr[9], di[6], g[3], x1[3], x2[3];
+      load9(B.L + 9 * r, cl);
+      load9(B.R + 9 * r, cr);
+      load6(B.D + 6 * r, di);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        g[p] = y[3 * r + p];
+        x1[p] = y[3 * k1 + p];
+        x2[p] = y[3 * k2 + p];
+      }
+      const float w1 = has1 ? 1.f : 0.f, w2 = has2 ? 1.f : 0.f;
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+        g[p] -= w1 * (cl[3 * p] * x1[0] + cl[3 * p + 1] * x1[1] + cl[3 * p + 2] * x1[2]) +
+                w2 * (cr[3 * p] * x2[0] + cr[3 * p + 1] * x2[1] + cr[3 * p + 2] * x2[2]);
+      float x[3];
+      symv(di, g, x);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) y[3 * r + p] = x[p];
+    }
+    sync();
+  }
 }
 
 // --- one flag's linearisation at chi^(k), run by threads t = 0..nt-1 of a group that synchronises between
@@ -300,11 +329,11 @@ struct Flag {
   double four_dt2, four_dt;               // 4/dt^2, 4/dt
   const double* chi;                      // [3N] iterate chi^(k)
   const double* ref;                      // [N][3] reference chord of the step: psi, c, s
-  const double *chi_n, *zeta_n, *zdot_n;  // [3N] state of step n
+  const double* cn;                       // [3N] M ((4/dt^2) chi_n + (4/dt) zeta_n + zetadot_n), r^zeta_n
   double* fab;                            // [N][6] element end forces (scratch)
-  float* ey;                              // [N][12] element tangents (scratch; [Em | y] after the factorization)
+  float* ey;                              // [N][12] element tangents (scratch; [L | y] after the factorization)
   float* mi;                              // [N][6] D_i (assembly), factor blocks afterwards
-  float* bm;                              // [N][9] B_i
+  float* bm;                              // [N][9] R_i = J_{i,i+1}
   double* rz;                             // [3N] r^zeta(k)
   float* y0;                              // [3N] first right-hand side r^zeta(k) + ds T^T f (float), or NULL
   const double* f;                        // surface stress of nodes 1..N: x at f[i], y at f[fstride + i]; or NULL
@@ -312,7 +341,7 @@ struct Flag {
 };
 
 // Pass 1: element end forces (FP64) and tangent blocks (FP32).
-__device__ inline void flag_elements(const Flag& F, int t, int nt) {
+__device__ __forceinline__ void flag_elements(const Flag& F, int t, int nt) {
   for (int e = t; e < F.N; e += nt) {
     double xa = F.hx, ya = F.hy, ta = 0.0;
     if (e > 0) {
@@ -335,20 +364,28 @@ __device__ inline void flag_elements(const Flag& F, int t, int nt) {
       F.ey[12 * e + k] = kaa[k];
       F.ey[12 * e + 6 + k] = kbb[k];
     }
-    if (e > 0) {
+    if (e > 0) {  // R_{e-1} = J_{e-1,e} (free nodes) = K_ab = K_ba^T of element e
 #pragma unroll
-      for (int k = 0; k < 9; ++k) F.bm[9 * (e - 1) + k] = kba[k];
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) F.bm[9 * (e - 1) + 3 * p + q] = kba[3 * q + p];
     }
   }
 }
 
+// Lumped mass of free node i (of N) for dof k: mass_per_length * ds (half at the tip) on the translations,
+// times ds^2/12 on the rotation.
+__host__ __device__ __forceinline__ double node_mass(double mu, double ds, int N, int i, int k) {
+  const double mt = mu * ds * (i == N - 1 ? 0.5 : 1.0);
+  return k < 2 ? mt : mt * ds * ds * (1.0 / 12.0);
+}
+
 // Pass 2 (after a barrier): diagonal blocks D_i = K_bb(element i) + K_aa(element i+1) + 4M_i/dt^2 and
-// r^zeta(k) = M ((4/dt^2)(chi_n - chi^(k)) + (4/dt) zeta_n + zetadot_n) - R(chi^(k)) per free node i.
-__device__ inline void flag_assemble(const Flag& F, int t, int nt) {
+// r^zeta(k) = r^zeta_n - (4/dt^2) M chi^(k) - R(chi^(k)) per free node i (App. A).
+__device__ __forceinline__ void flag_assemble(const Flag& F, int t, int nt) {
   const int N = F.N;
   for (int i = t; i < N; i += nt) {
-    const double mt = F.mu * F.ds * (i == N - 1 ? 0.5 : 1.0);
-    const double mr = mt * F.ds * F.ds * (1.0 / 12.0);
+    const double mt = node_mass(F.mu, F.ds, N, i, 0), mr = node_mass(F.mu, F.ds, N, i, 2);
     float D[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) D[k] = F.ey[12 * i + 6 + k] + (i + 1 < N ? F.ey[12 * (i + 1) + k] : 0.f);
@@ -357,21 +394,22 @@ __device__ inline void flag_assemble(const Flag& F, int t, int nt) {
     D[5] += (float)(F.four_dt2 * mr);
 #pragma unroll
     for (int k = 0; k < 6; ++k) F.mi[6 * i + k] = D[k];
+    if (i == N - 1) {  // the tip has no right neighbour
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F.bm[9 * i + k] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int g = 3 * i + k;
       double R = F.fab[6 * i + 3 + k];
       if (i + 1 < N) R += F.fab[6 * (i + 1) + k];
-      const double rz =
-          (k < 2 ? mt : mr) * (F.four_dt2 * (F.chi_n[g] - F.chi[g]) + F.four_dt * F.zeta_n[g] + F.zdot_n[g]) - R;
+      const double rz = F.cn[g] - (k < 2 ? mt : mr) * F.four_dt2 * F.chi[g] - R;
       F.rz[g] = rz;
       if (F.y0) F.y0[g] = (float)(k < 2 && F.f ? rz + F.ds * F.f[k * F.fstride + i] : rz);
     }
   }
 }
 
-__device__ __forceinline__ Factor flag_factor_view(const Flag& F) {
-  return Factor{F.mi, F.bm, F.ey, F.mi + 6 * meet(F.N), F.N};
-}
+__device__ __forceinline__ Bcr flag_bcr(const Flag& F) { return Bcr{F.mi, F.bm, F.ey, F.N}; }
 
 }  // namespace beam

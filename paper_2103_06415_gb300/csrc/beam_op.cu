@@ -7,7 +7,8 @@
 namespace {
 
 struct OpArgs {
-  beam::Flag F;  // chi_n, zeta_n, zdot_n, ref point to global memory; the rest is set in the kernel
+  beam::Flag F;  // ref points to global memory; the rest is set in the kernel
+  const double *chi_n, *zeta_n, *zdot_n;
   const double* chi;
   const double* b;
   double* rz_out;
@@ -19,7 +20,8 @@ __global__ void __launch_bounds__(128) k_beam_op(OpArgs a) {
   const int N = a.F.N, nd = 3 * N, t = threadIdx.x;
   double* chi = reinterpret_cast<double*>(sm);
   double* rz = chi + nd;
-  double* fab = rz + nd;
+  double* cn = rz + nd;
+  double* fab = cn + nd;
   float* ey = reinterpret_cast<float*>(fab + 6 * N);
   float* mi = ey + 12 * N;
   float* bm = mi + 6 * N;
@@ -32,19 +34,21 @@ __global__ void __launch_bounds__(128) k_beam_op(OpArgs a) {
   F.bm = bm;
   F.rz = rz;
   F.y0 = nullptr;
-  for (int g = t; g < nd; g += 128) chi[g] = a.chi[g];
+  F.cn = cn;
+  for (int g = t; g < nd; g += 128) {
+    chi[g] = a.chi[g];
+    cn[g] = beam::node_mass(F.mu, F.ds, N, g / 3, g % 3) *
+            (F.four_dt2 * a.chi_n[g] + F.four_dt * a.zeta_n[g] + a.zdot_n[g]);
+  }
   __syncthreads();
   beam::flag_elements(F, t, 128);
   __syncthreads();
   beam::flag_assemble(F, t, 128);
   for (int g = t; g < nd; g += 128) y[g] = (float)a.b[g];
   __syncthreads();
-  if (t < 32) {
-    const beam::Factor FF = beam::flag_factor_view(F);
-    beam::factor(FF);
-    beam::solve(FF, y, nd, 1);
-  }
-  __syncthreads();
+  const beam::Bcr B = beam::flag_bcr(F);
+  beam::bcr_factor(B, t, 128, []() { __syncthreads(); });
+  beam::bcr_solve(B, y, nd, 1, t, 128, []() { __syncthreads(); });
   for (int g = t; g < nd; g += 128) {
     a.rz_out[g] = rz[g];
     a.x_out[g] = (double)y[g];
@@ -77,7 +81,7 @@ extern "C" fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double e
     fsi_set_last_cuda_error(e, "fsi_op_beam_solve: cudaMalloc", __FILE__, __LINE__);
     return FSI_ERR_OOM;
   }
-  const size_t smem = nd * 8 * 2 + (size_t)n_el * (6 * 8 + (12 + 6 + 9) * 4) + nd * 4;
+  const size_t smem = nd * 8 * 3 + (size_t)n_el * (6 * 8 + (12 + 6 + 9) * 4) + nd * 4;
   OpArgs a;
   a.F = beam::Flag{n_el,
                    cx,
@@ -89,9 +93,7 @@ extern "C" fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double e
                    4.0 / dt,
                    nullptr,
                    d + 4 * nd,
-                   d + nd,
-                   d + 2 * nd,
-                   d + 3 * nd,
+                   nullptr,
                    nullptr,
                    nullptr,
                    nullptr,
@@ -100,6 +102,9 @@ extern "C" fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double e
                    nullptr,
                    nullptr,
                    0};
+  a.chi_n = d + nd;
+  a.zeta_n = d + 2 * nd;
+  a.zdot_n = d + 3 * nd;
   a.chi = d;
   a.b = d + 5 * nd;
   a.rz_out = d + 6 * nd;

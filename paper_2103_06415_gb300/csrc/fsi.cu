@@ -337,12 +337,13 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 
 // Shared-memory layout of the kernel (byte offsets, 16-byte aligned): X (or the Cholesky factor in CTA 0
 // during a rebuild), owned K rows, the vectors rhs, f, r, the hat weights, a float4 work row, hat indices;
-// for deformable bodies the iterate chi^(k), r^zeta(k), the element end forces, the factor blocks of J_d
+// for deformable bodies the iterate chi^(k), r^zeta(k), the step constants r^zeta_n and r^chi_n, the
+// reference chords, the element end forces, the factor blocks of J_d
 // (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
 // right-hand sides of the structural solves.
 struct FsiLayout {
   size_t xs, krow, vec, pw, work, rf, pidx;
-  size_t chi, rz, fab, mi, bm, ey, ys;
+  size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys;
   size_t total;
 };
 struct BeamDims {
@@ -370,7 +371,10 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
   L.pidx = L.rf + al16(lx * 4);
   L.chi = L.pidx + al16((size_t)4 * nb * 4);
   L.rz = L.chi + al16((size_t)bd.nd * 8);
-  L.fab = L.rz + al16((size_t)bd.nd * 8);
+  L.cn = L.rz + al16((size_t)bd.nd * 8);
+  L.rchi = L.cn + al16((size_t)bd.nd * 8);
+  L.ref = L.rchi + al16((size_t)bd.nd * 8);
+  L.fab = L.ref + al16((size_t)3 * bd.ne * 8);
   L.mi = L.fab + al16((size_t)6 * bd.ne * 8);
   L.bm = L.mi + al16((size_t)6 * bd.ne * 4);
   L.ey = L.bm + al16((size_t)9 * bd.ne * 4);
@@ -445,6 +449,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
   double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
   double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
+  double* cn_s = reinterpret_cast<double*>(dyn_smem + L.cn);      // r^zeta_n of every free dof
+  double* rchi_s = reinterpret_cast<double*>(dyn_smem + L.rchi);  // r^chi_n = (2/dt) chi_n + zeta_n
+  double* ref_s = reinterpret_cast<double*>(dyn_smem + L.ref);    // reference chords [ne][3]
   double* fab_s = reinterpret_cast<double*>(dyn_smem + L.fab);  // element end forces [ne][6]
   float* mi_s = reinterpret_cast<float*>(dyn_smem + L.mi);
   float* bm_s = reinterpret_cast<float*>(dyn_smem + L.bm);
@@ -466,6 +473,18 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     }
   }
   for (int g = tid; g < a.nd_tot; g += nthr) chi_s[g] = a.bchi[g];
+  for (int e = tid; e < 3 * a.ne_tot; e += nthr) ref_s[e] = a.bref[e];
+  for (int bi = 0; bi < a.n_bodies && a.n_def > 0; ++bi) {  // step constants of App. A, FP64
+    const BodyDev b = a.bodies[bi];
+    if (b.type != FSI_BODY_DEFORMABLE) continue;
+    const int N = b.n - 1, d0 = 3 * b.el_off;
+    for (int q = tid; q < 3 * N; q += nthr) {
+      const int g = d0 + q;
+      cn_s[g] = beam::node_mass(b.mu, a.ds, N, q / 3, q % 3) *
+                (a.four_dt2 * a.bchi[g] + 2.0 * a.two_dt * a.bzeta[g] + a.bzdot[g]);
+      rchi_s[g] = a.two_dt * a.bchi[g] + a.bzeta[g];
+    }
+  }
   // with flags the small system is solved for the correction to the previous surface stress f_prev (the
   // last iterate, or the last step's f): see the refinement below
   if (a.n_def > 0)
@@ -516,6 +535,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     {
       const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
       const int p0 = (int)blockIdx.x * per;
+      // side timers of CTA 0 (slots 14: warps 0-3 on the points, 15: warps 4-7 on the flags)
+      const bool side_clock = blockIdx.x == 0 && (tid == 0 || tid == 128) && a.phase_ns;
+      const unsigned long long ta0 = side_clock ? PhaseClock::now() : 0ull;
       // warps 0-3 take the points (every lane of them joins the shuffles); warps 4-7 the flags
       for (int t0 = 0; wid < 4 && t0 < 4 * per; t0 += 128) {
         const int t = t0 + tid;
@@ -579,6 +601,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           a.rhs[2 * nf + nb + p] = uby - ucy + svy * coef;
         }
       }
+      if (side_clock && tid == 0) sh_phase[14] += PhaseClock::now() - ta0;
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
         // r^zeta(k), J_d blocks, the factorization, y = J_d^-1 (r^zeta(k) + ds T^T f_prev) and the structural
@@ -598,10 +621,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
                              a.four_dt2,
                              2.0 * a.two_dt,
                              chi_s + d0,
-                             a.bref + 3 * e0,
-                             a.bchi + d0,
-                             a.bzeta + d0,
-                             a.bzdot + d0,
+                             ref_s + 3 * e0,
+                             cn_s + d0,
                              fab_s + 6 * e0,
                              ey,
                              mi_s + 6 * e0,
@@ -624,12 +645,11 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           for (int q = st; q < ld; q += 128)  // unit right-hand sides of the owned columns
             for (int j = 1; j < nrhs; ++j) ys_s[j * ld + q] = q == rdof[j - 1] ? 1.f : 0.f;
           named_sync_upper();
-          if (wid == 4) {
-            const beam::Factor FF = beam::flag_factor_view(F);
-            beam::factor(FF);
-            beam::solve(FF, ys_s, ld, nrhs);
+          {
+            const beam::Bcr B = beam::flag_bcr(F);
+            beam::bcr_factor(B, st, 128, []() { named_sync_upper(); });
+            beam::bcr_solve(B, ys_s, ld, nrhs, st, 128, []() { named_sync_upper(); });
           }
-          named_sync_upper();
           float* ysol = ey + 9 * N;
           for (int q = st; q < ld; q += 128) ysol[q] = ys_s[q];
           for (int j = 1; j < nrhs; ++j) {
@@ -641,6 +661,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           }
           named_sync_upper();
         }
+        if (side_clock) sh_phase[15] += PhaseClock::now() - ta0;
       }
     }
     grid.sync();
@@ -650,7 +671,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     }
     for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
     __syncthreads();
-    if (a.n_def > 0) {  // flags: rhs -= T ((2/dt)(chi^(k) + y) - r^chi), r^chi = (2/dt) chi_n + zeta_n
+    if (a.n_def > 0) {  // flags: rhs -= T ((2/dt)(chi^(k) + y) - r^chi_n)
       for (int bi = 0; bi < a.n_bodies; ++bi) {
         const BodyDev b = a.bodies[bi];
         if (b.type != FSI_BODY_DEFORMABLE) continue;
@@ -658,7 +679,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         const float* ysol = ey_s + 12 * b.el_off + 9 * N;
         for (int q = tid; q < 2 * N; q += nthr) {
           const int i = q >> 1, c = q & 1, g = d0 + 3 * i + c;
-          rhs_s[c * nb + b.off + 1 + i] -= a.two_dt * (chi_s[g] - a.bchi[g] + (double)ysol[3 * i + c]) - a.bzeta[g];
+          rhs_s[c * nb + b.off + 1 + i] -= a.two_dt * (chi_s[g] + (double)ysol[3 * i + c]) - rchi_s[g];
         }
       }
       __syncthreads();
@@ -948,11 +969,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           ys_s[q] = (float)v;
         }
         __syncthreads();
-        if (wid == 0) {
-          const beam::Factor F{mi_s + 6 * e0, bm_s + 9 * e0, ey_s + 12 * e0, mi_s + 6 * (e0 + beam::meet(N)), N};
-          beam::solve(F, ys_s, 3 * N, 1);
-        }
-        __syncthreads();
+        beam::bcr_solve(beam::Bcr{mi_s + 6 * e0, bm_s + 9 * e0, ey_s + 12 * e0, N}, ys_s, 3 * N, 1, tid, nthr,
+                        []() { __syncthreads(); });
         double dm = 0.0;
         for (int q = tid; q < 3 * N; q += nthr) {
           const double d = (double)ys_s[q];

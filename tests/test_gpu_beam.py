@@ -1,9 +1,9 @@
 """Deformable bodies (Eq. beam, App. A) on the GPU against the FP64 oracle (needs a GB300 and the library).
 
-The GPU factors J_d in FP32 (the FP64 structural residual fixes where the FSI iteration converges; J_d only
-steers the path there), so iterates differ from the oracle's by a little more than FP64 rounding.  Runs
-are therefore compared at a tight iteration tolerance (1e-12 on max |dchi|, both sides), where they agree
-to 1e-9, and at the default tolerance, where both sit within ~1e-7 of the same fixed point.
+The GPU factors J_d in FP32 but applies those solves only to residuals that vanish at the fixed point
+(the FP64 structural residual fixes where the FSI iteration converges), so its iterates follow the
+oracle's to FP64-level differences: runs are compared at the default iteration tolerance and at a tight
+one (1e-12 on max |dchi|, both sides).
 """
 
 import numpy as np
@@ -60,9 +60,10 @@ def test_beam_linearisation_matches_oracle(lib, n_el, tip):
                            _ref_chords(bm, chi_n), b)
     m = bm.mass()
     rint, k = bm.internal(chi)
-    inertia = m * (4.0 / dt ** 2 * (chi_n - chi) + 4.0 / dt * zeta_n + zdot_n)
-    rz_ref = inertia - rint
-    assert np.max(np.abs(rz - rz_ref)) < 1e-13 * max(np.max(np.abs(inertia)), np.max(np.abs(rint)))
+    r_zeta_n = m * (4.0 / dt ** 2 * chi_n + 4.0 / dt * zeta_n + zdot_n)          # App. A
+    rz_ref = r_zeta_n - 4.0 / dt ** 2 * m * chi - rint
+    scale = max(np.max(np.abs(r_zeta_n)), np.max(np.abs(rint)))               # rounding scale of the sum
+    assert np.max(np.abs(rz - rz_ref)) < 1e-14 * scale
     x_ref = np.linalg.solve(np.diag(4.0 / dt ** 2 * m) + k, b)
     assert rel_err(x, x_ref) < 2e-5
 
@@ -84,12 +85,13 @@ def test_flag_run_matches_oracle_at_tight_tolerance(lib, use_graph):
     n = 12
     sim, ctx = _run(w, n, tol=1e-12, use_graph=use_graph)
     hist, ref = ctx.history(0), oracle_history(sim)
+    assert np.array_equal(hist[:, 5], ref[:, 5])           # FSI iterations per step
     for k in (0, 1, 3, 4):                                   # fx, fy, tip displacement, tip rate
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-9, k
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
     assert np.all(hist[:, 2] == 0.0)
     chi, zeta, zdot = ctx.beam_state(0)
     rchi, rzeta, rzdot = _oracle_state(sim, 0)
-    assert np.max(np.abs(chi - rchi)) < 1e-12
+    assert np.max(np.abs(chi - rchi)) < 1e-13
     assert rel_err(zeta, rzeta) < 1e-9
     assert rel_err(zdot, rzdot) < 1e-8
     idx, wts = ctx.interp(sim.nb)
@@ -106,9 +108,9 @@ def test_flag_run_at_default_tolerance_is_within_the_iteration_tolerance(lib):
     hist, ref = ctx.history(0), oracle_history(sim)
     assert np.max(np.abs(hist[:, 5] - ref[:, 5])) <= 1          # FSI iterations per step
     for k in (0, 1, 3, 4):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-5, k
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-8, k
     chi, _, _ = ctx.beam_state(0)
-    assert np.max(np.abs(chi - _oracle_state(sim, 0)[0])) < 1e-7
+    assert np.max(np.abs(chi - _oracle_state(sim, 0)[0])) < 1e-9
 
 
 def test_mixed_bodies_match_oracle(lib):
