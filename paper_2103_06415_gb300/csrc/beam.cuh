@@ -131,6 +131,7 @@ __device__ __forceinline__ void inv3s(const float S[6], float Si[6]) {
   Si[5] = c22 * id;
 }
 
+
 // E = Bk * Si (full x sym)
 __device__ __forceinline__ void mul_fs(const float Bk[9], const float Si[6], float E[9]) {
 #pragma unroll

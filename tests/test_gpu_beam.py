@@ -44,9 +44,12 @@ def _ref_chords(bm, chi_n):
     return np.stack([psi, d[:, 0] / length, d[:, 1] / length], axis=1)
 
 
-@pytest.mark.parametrize("n_el,tip", [(1, 0.05), (2, 0.1), (8, 0.1), (100, 0.3), (101, -0.2), (400, 0.5)])
+@pytest.mark.parametrize("n_el,tip", [(1, 0.05), (2, 0.1), (3, 0.1), (4, -0.1), (5, 0.2), (8, 0.1), (31, 0.2),
+                                      (32, 0.3), (63, 0.1), (64, 0.2), (65, 0.3), (100, 0.3), (101, -0.2),
+                                      (127, 0.4), (128, 0.4), (400, 0.5)])
 def test_beam_linearisation_matches_oracle(lib, n_el, tip):
-    """r^zeta(k) (FP64) and J_d^-1 b (FP32 factor) of the kernel's structural routines vs the oracle."""
+    """r^zeta(k) (FP64) and J_d^-1 b (FP32 factor) of the kernel's structural routines vs the oracle; sizes
+    around the powers of two where the levels of the cyclic reduction change."""
     from oracle import beam as ob
     dt, ds = 5e-4, 1.0 / n_el
     bm = ob.Beam((0.1, -0.2), 0.3, n_el, ds, 0.1, 1e-3, 1e3, tip_angle=tip)
