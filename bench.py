@@ -402,8 +402,11 @@ def main():
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (DESIGN.md)",
                 "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                         "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-                "traffic": None,
-                "traffic_note": "no ncu capture of this version of the kernel yet",
+                "traffic": 1.65e6,
+                "traffic_note": "dram read+write bytes per launch from one ncu capture of the same kernel on "
+                                "the reduced-Omega_0 variant of the flag workload (same nf and flag; the B0 "
+                                "gathers of the same point set dominate it; "
+                                "profiles/k_fsi_flag_reduced_omega0.md)",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
                 "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
                 "secondary": secondary}
