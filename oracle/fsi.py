@@ -9,7 +9,8 @@ and corrector2; the structural right-hand sides follow App. A:
   O2  advection term and right-hand side on every level (App. A, AB2 + CN)
   O3  predictor, coarse to fine: ``s* = (C^T A C)^{-1} r`` (Eq. predictor2)
   O4  FSI iteration on the finest level (Eqs. stress2, dtheta2) with
-      ``P B0 P^T`` in place of ``E C (C^T A C)^{-1} C^T E^T`` (Eq. operatorapprox)
+      ``P B0 P^T`` in place of ``E C (C^T A C)^{-1} C^T E^T`` (Eq. operatorapprox);
+      with a drop tolerance the filtered ``B0'`` of Eq. filtereq (then K is not symmetric)
   O5  corrector ``s = s* - (C^T A C)^{-1} C^T E0^T P^T f`` (Eq. corrector2) on the
       finest level with homogeneous boundary values (reading R6)
   O6  Newmark update of the structure and the force outputs
@@ -102,13 +103,14 @@ class Sim:
     """A full run: nested levels, one sub-domain box, bodies, FP64 state."""
 
     def __init__(self, nx, ny, h, x0, y0, n_levels, re, dt, uinf, sd_box, bodies, ds,
-                 tol=1e-7, max_iters=50):
+                 tol=1e-7, max_iters=50, drop_tol=0.0):
         self.levels = grid.make_levels(nx, ny, h, x0, y0, n_levels)
         self.re, self.dt = float(re), float(dt)
         self.uinf = np.asarray(uinf, dtype=np.float64)
         self.ds = float(ds)
         self.bodies = list(bodies)
         self.tol, self.max_iters = float(tol), int(max_iters)
+        self.drop_tol = float(drop_tol)      # Eq. filtereq: B0' in place of B0 in the small system
         self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box) if sd_box is not None else None
         self.w = [np.zeros(l.shape) for l in self.levels]
         self.s = [np.zeros(l.shape) for l in self.levels]
@@ -127,7 +129,7 @@ class Sim:
         for k, c in enumerate(cols):
             c = int(c)
             if c not in self._b0:
-                self._b0[c] = ib.b0_column(self.sd, c, self.re, self.dt)
+                self._b0[c] = ib.b0_column(self.sd, c, self.re, self.dt, self.drop_tol)
             out[:, k] = self._b0[c]
         return out
 

@@ -10,7 +10,8 @@ Test infrastructure only (see ``oracle/__init__.py``).
                     spacing h (Sec. 3.1.1), and the operators
                     ``E0`` (Eq. ibsdinterp), ``E0^T`` and ``P`` (Eq. weights).
 * ``b0_column``  -- column j of ``B0 = E0 C (C^T A C)^{-1} C^T E0^T`` computed as the
-                    action on the canonical vector e_j (Eq. action, Algorithm 1).
+                    action on the canonical vector e_j (Eq. action, Algorithm 1), optionally
+                    filtered by the drop tolerance of Eq. filtereq (``drop_filter``).
 
 Unknown ordering of sub-domain vectors: the ``n_sd`` x-components first, then
 the ``n_sd`` y-components; points are numbered row by row (j-major) inside the box.
@@ -127,8 +128,17 @@ class Subdomain:
         return idx, wts
 
 
-def b0_column(sd, col, re, dt):
-    """Column ``col`` of ``B0``: ``E0 C Lap^{-1} A_w^{-1} C^T E0^T e_col`` (Eq. action).
+def drop_filter(b, col, drop_tol):
+    """Eq. filtereq applied to column ``col`` as it is built (Algorithm 1): keep ``b_i`` where
+    ``|b_i| > drop_tol |b_col|`` (the column's own diagonal, strict inequality: reading R8), else 0."""
+    if drop_tol <= 0.0:
+        return b
+    return np.where(np.abs(b) > drop_tol * abs(b[col]), b, 0.0)
+
+
+def b0_column(sd, col, re, dt, drop_tol=0.0):
+    """Column ``col`` of ``B0``: ``E0 C Lap^{-1} A_w^{-1} C^T E0^T e_col`` (Eq. action), filtered by
+    ``drop_filter`` when ``drop_tol > 0`` (the sparse ``B0'`` of Eq. filtereq).
 
     The solves use the finest level with homogeneous boundary values (reading R6).
     """
@@ -142,7 +152,7 @@ def b0_column(sd, col, re, dt):
     s = np.zeros(lev.shape)
     s[1:-1, 1:-1] = grid.solve_lap(w, zero, lev)
     qu, qv = grid.faces_from_s(s, lev)
-    return sd.e0(qu, qv)
+    return drop_filter(sd.e0(qu, qv), col, drop_tol)
 
 
 def b0_dense(sd, re, dt):
