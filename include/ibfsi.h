@@ -130,6 +130,8 @@ typedef struct {
   int dst_gemm[3];       /* 1 if pass p (0 forward x, 1 y solve, 2 inverse x) runs as a tensor-core GEMM */
   double dst_us[2][3];   /* autotuner timings in microseconds: [0] FFT, [1] GEMM, per pass (0 = not timed) */
   int last_refreshes;    /* Newton-Schulz refreshes of the float inverse in the last step */
+  int64_t b0_nnz;        /* stored nonzero entries of B0: (2 n_sd)^2 dense, the kept entries of B0' sparse */
+  int b0_window;         /* sparse B0': half-width (Omega_0 points) of each column's window; 0 dense */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;
@@ -152,8 +154,13 @@ fsi_status fsi_add_body(fsi_ctx* ctx, const fsi_body_desc* body, int* body_id);
 fsi_status fsi_set_subdomain(fsi_ctx* ctx, const fsi_box* boxes, int n_boxes, const double* extra_pts,
                              int n_extra);
 
-/* Offline stage (Algorithm 1): build the dense B0 (2 n_sd x 2 n_sd, double) on the device.
- * drop_tol must be 0 (the dense operator); sparse filtering (Eq. filtereq) returns FSI_ERR_UNSUPPORTED. */
+/* Offline stage (Algorithm 1): build B0 (2 n_sd x 2 n_sd, double) on the device.
+ * drop_tol = 0: the dense operator.  0 < drop_tol < 1: the sparse B0' of Eq. filtereq (the paper uses 0.007),
+ * entry (i, j) kept when |b_ij| > drop_tol |b_jj| (the column's own diagonal), stored per column as a window
+ * of (2w+1)^2 Omega_0 points around the column's point (w: the largest extent of a kept entry, found by a
+ * scan; fsi_stats.b0_window, .b0_nnz); the small system then uses B0' and is not symmetric.  The sparse
+ * operator is built from the lattice Green's function only (b0_method 0; method 1 returns
+ * FSI_ERR_UNSUPPORTED).  drop_tol < 0, >= 1 or NaN: FSI_ERR_INVALID_ARG. */
 fsi_status fsi_precompute(fsi_ctx* ctx, double drop_tol);
 
 /* Online stage (Algorithm 2): enqueue n_steps time steps on the context stream.  Asynchronous. */
@@ -187,8 +194,9 @@ fsi_status fsi_get_field(fsi_ctx* ctx, int level, int which, double* out);
 /* Overwrite a vertex field (same layout) from the host, e.g. to start from a given state. */
 fsi_status fsi_set_field(fsi_ctx* ctx, int level, int which, const double* in);
 
-/* Sampled entries of B0: out[k] = B0[rows[k], cols[k]] for k < n (synchronising).  Unknown ordering:
- * the n_sd x-components (points row by row inside the box), then the n_sd y-components. */
+/* Sampled entries of B0 (or of the sparse B0', zero where dropped): out[k] = B0[rows[k], cols[k]] for
+ * k < n (synchronising).  Unknown ordering: the n_sd x-components (points row by row inside the box),
+ * then the n_sd y-components. */
 fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n,
                                     double* out);
 
@@ -196,7 +204,7 @@ fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int
  * tau = tau_rel * max_i B0_ii (B0 at flow-grid spacing is only positive semi-definite; BASELINE config 3
  * asks for this factor after the B0 assembly).  The factor (lower triangle, 8 (2 n_sd)^2 bytes) is kept on
  * the device.  *tau_out and *seconds (wall time of the factorisation) may be NULL.  A non-positive pivot
- * returns FSI_ERR_NONFINITE.  Requires fsi_precompute. */
+ * returns FSI_ERR_NONFINITE.  Requires fsi_precompute with the dense operator (sparse: FSI_ERR_UNSUPPORTED). */
 fsi_status fsi_factor_operator(fsi_ctx* ctx, double tau_rel, double* tau_out, double* seconds);
 /* Sampled entries of that factor: out[k] = L[rows[k], cols[k]] (zero above the diagonal). */
 fsi_status fsi_get_factor_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n, double* out);

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("n_sd", ctypes.c_int), ("nf", ctypes.c_int), ("b0_seconds", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int),
                 ("last_solves", ctypes.c_int), ("inverse_rebuilds", ctypes.c_int),
-                ("dst_gemm", ctypes.c_int * 3), ("dst_us", ctypes.c_double * 6), ("last_refreshes", ctypes.c_int)]
+                ("dst_gemm", ctypes.c_int * 3), ("dst_us", ctypes.c_double * 6), ("last_refreshes", ctypes.c_int),
+                ("b0_nnz", ctypes.c_int64), ("b0_window", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

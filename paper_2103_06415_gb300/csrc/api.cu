@@ -431,8 +431,8 @@ extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_
 }
 
 extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
-  if (!c) return FSI_ERR_INVALID_ARG;
-  if (drop_tol != 0.0) return FSI_ERR_UNSUPPORTED;
+  if (!c || !(drop_tol >= 0.0) || !(drop_tol < 1.0)) return FSI_ERR_INVALID_ARG;
+  if (drop_tol > 0.0 && c->x.b0_method != 0) return FSI_ERR_UNSUPPORTED;
   if (c->stage >= 1) return FSI_ERR_STATE;
   if (!c->have_sd) return FSI_ERR_STATE;
   c->n_bodies = (int)c->bodies.size();
@@ -440,8 +440,13 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   if (c->n_bodies > 64) return FSI_ERR_UNSUPPORTED;
   if (c->nb > 0 && !fsi_smem_fits(c)) return FSI_ERR_UNSUPPORTED;
   const size_t n2 = 2 * (size_t)c->n_sd;
-  if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
-  fsi_status st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
+  fsi_status st = FSI_OK;
+  if (drop_tol > 0.0) {  // sparse B0' (Eq. filtereq) in the windowed column format
+    st = build_b0_window(c, drop_tol);
+  } else {
+    if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
+    st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
+  }
   if (st != FSI_OK) return st;
   c->have_b0 = 1;
   if (c->nb > 0) {
@@ -481,6 +486,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_rpts = (double*)ctx_alloc(c, c->rigid_pts.size() * 8)) ||
         !(c->d_rur = (double*)ctx_alloc(c, c->rigid_ur.size() * 8)) ||
         !(c->d_pidx = (int*)ctx_alloc(c, (size_t)c->nb * 4 * sizeof(int))) ||
+        !(c->d_pcij = (int*)ctx_alloc(c, (size_t)c->nb * 2 * sizeof(int))) ||
         !(c->d_pw = (double*)ctx_alloc(c, (size_t)c->nb * 4 * 8)) ||
         !(c->d_sv = (double*)ctx_alloc(c, (size_t)c->nb * 2 * 8)) ||
         !(c->d_rhs = (double*)ctx_alloc(c, (size_t)c->nf * 3 * 8)) ||
@@ -779,8 +785,9 @@ extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, 
              cudaMemcpyAsync(dc, cols, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
     st = FSI_ERR_CUDA;
   } else {
-    k_gather_b0<<<(n + 255) / 256, 256, 0, c->stream>>>(c->B0, n2, dr, dc, n, dout);
-    if (cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+    if (c->Bw) st = b0_window_entries(c, dr, dc, n, dout);
+    else k_gather_b0<<<(n + 255) / 256, 256, 0, c->stream>>>(c->B0, n2, dr, dc, n, dout);
+    if (st != FSI_OK || cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       st = FSI_ERR_CUDA;
   }
@@ -809,6 +816,8 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   out->b0_seconds = c->b0_seconds;
   out->device_bytes = c->dev_bytes;
   out->launches_per_step = c->launches_per_step;
+  out->b0_nnz = c->Bw ? c->b0_nnz : (int64_t)(2 * (int64_t)c->n_sd) * (2 * (int64_t)c->n_sd);
+  out->b0_window = c->Bw ? c->bw : 0;
   for (int p = 0; p < 3; ++p) {
     out->dst_gemm[p] = c->dst_gemm[p];
     out->dst_us[0][p] = c->dst_us[0][p];

@@ -199,11 +199,13 @@ __global__ void __launch_bounds__(256) k_fill(double* __restrict__ out, const do
 
 }  // namespace
 
-fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
+// The 16 stencil tables of every box (layout of k_tables) into a new device array *tab_out (caller frees
+// it with cudaFree), tab_off of each box set; boxes must have their layout (b0_layout) filled in.
+fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_out) {
   const int Nx = c->Nx, Mx = c->Mx, My = c->My;
   const double h = c->g.h;
   const int nb = (int)boxes.size();
-  b0_layout(boxes);
+  *tab_out = nullptr;
   long tab_n = 0, max_tab = 0;
   for (B0Box& b : boxes) {
     const long t = 16L * (2 * b.ni - 1) * (2 * b.nj - 1);
@@ -211,7 +213,6 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     tab_n += t;
     if (t > max_tab) max_tab = t;
   }
-  // twiddles exp(-2 pi i m / L) for the two DCT lengths L = 2 Mx, 2 My
   std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);
   for (int m = 0; m < 2 * Mx; ++m) {
     twx[2 * m] = std::cos(-M_PI * (double)m / (double)Mx);
@@ -223,7 +224,6 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   }
   double *d_twx = nullptr, *d_twy = nullptr, *d_T1 = nullptr, *d_g = nullptr, *d_tab = nullptr;
   B0Box* d_bx = nullptr;
-  long* d_off = nullptr;
   fsi_status st = FSI_OK;
   do {
     if (cudaMalloc(&d_twx, twx.size() * 8) != cudaSuccess || cudaMalloc(&d_twy, twy.size() * 8) != cudaSuccess ||
@@ -242,7 +242,6 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
       st = FSI_ERR_CUDA;
       break;
     }
-    // T1[k-1][q] = sum_l d_kl cos(pi l q/My);  g[p][q] = sum_k cos(pi k p/Mx) T1[k-1][q] / (Mx My)
     st = launch_dct1(nullptr, 0, 0, Nx, My, d_T1, My + 1, 1, (const double2*)d_twy, ilog2_exact(2 * My), 1.0, c->lx,
                      c->ly, 1.0 / (h * h), 1.0 / c->g.dt, 0.5 / c->g.re, c->stream);
     if (st != FSI_OK) break;
@@ -250,33 +249,54 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
                      1.0 / ((double)Mx * (double)My), nullptr, nullptr, 0.0, 0.0, 0.0, c->stream);
     if (st != FSI_OK) break;
     k_tables<<<dim3((unsigned)((max_tab + 127) / 128), nb), 128, 0, c->stream>>>(d_tab, d_bx, d_g, Mx, My, h);
-    {
-      std::vector<long> off(nb + 1, 0);
-      int max_ni = 1;
-      for (int k = 0; k < nb; ++k) {
-        off[k + 1] = off[k] + 4L * boxes[k].nj * boxes[k].nj;
-        if (boxes[k].ni > max_ni) max_ni = boxes[k].ni;
-      }
-      if (cudaMalloc(&d_off, (size_t)(nb + 1) * sizeof(long)) != cudaSuccess) {
-        cudaGetLastError();
-        st = FSI_ERR_OOM;
-        break;
-      }
-      if (cudaMemcpyAsync(d_off, off.data(), (size_t)(nb + 1) * sizeof(long), cudaMemcpyHostToDevice, c->stream) !=
-          cudaSuccess) {
-        st = FSI_ERR_CUDA;
-        break;
-      }
-      const size_t sm = (size_t)2 * (2 * max_ni - 1) * sizeof(double);
-      if (sm > 48 * 1024) cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_fill<<<(unsigned)off[nb], 256, sm, c->stream>>>(out, d_tab, d_bx, d_off, nb);
-    }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
   cudaFree(d_twx);
   cudaFree(d_twy);
   cudaFree(d_T1);
   cudaFree(d_g);
+  cudaFree(d_bx);
+  if (st == FSI_OK) {
+    *tab_out = d_tab;
+  } else {
+    cudaFree(d_tab);
+  }
+  return st;
+}
+
+fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
+  const int nb = (int)boxes.size();
+  b0_layout(boxes);
+  double* d_tab = nullptr;
+  fsi_status st = b0_green_tables(c, boxes, &d_tab);
+  if (st != FSI_OK) return st;
+  B0Box* d_bx = nullptr;
+  long* d_off = nullptr;
+  do {
+    std::vector<long> off(nb + 1, 0);
+    int max_ni = 1;
+    for (int k = 0; k < nb; ++k) {
+      off[k + 1] = off[k] + 4L * boxes[k].nj * boxes[k].nj;
+      if (boxes[k].ni > max_ni) max_ni = boxes[k].ni;
+    }
+    if (cudaMalloc(&d_off, (size_t)(nb + 1) * sizeof(long)) != cudaSuccess ||
+        cudaMalloc(&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
+      cudaGetLastError();
+      st = FSI_ERR_OOM;
+      break;
+    }
+    if (cudaMemcpyAsync(d_off, off.data(), (size_t)(nb + 1) * sizeof(long), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_bx, boxes.data(), (size_t)nb * sizeof(B0Box), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess) {
+      st = FSI_ERR_CUDA;
+      break;
+    }
+    const size_t sm = (size_t)2 * (2 * max_ni - 1) * sizeof(double);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fill<<<(unsigned)off[nb], 256, sm, c->stream>>>(out, d_tab, d_bx, d_off, nb);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+  } while (0);
   cudaFree(d_tab);
   cudaFree(d_bx);
   cudaFree(d_off);

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double* __restrict__ L, long
 extern "C" fsi_status fsi_factor_operator(fsi_ctx* c, double tau_rel, double* tau_out, double* seconds) {
   if (!c || tau_rel < 0) return FSI_ERR_INVALID_ARG;
   if (!c->have_b0) return FSI_ERR_STATE;
+  if (!c->B0) return FSI_ERR_UNSUPPORTED;  // the sparse B0' is not factored
   const long n = 2L * c->n_sd;
   auto t0 = std::chrono::steady_clock::now();
   if (!c->d_factor) {

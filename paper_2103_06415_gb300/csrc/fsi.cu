@@ -83,6 +83,10 @@ struct FsiArgs {
   double* bzdot;  // [nd_tot] zetadot_n
   double* bref;   // [ne_tot][3] chord rotation psi and unit chord (c, s) at chi_n
   double* G;      // [nf][nf] column-major: column r = T J_d^-1 T^T e_r for deformable rows r
+  // sparse B0' (windowed columns, b0w_lookup) in place of the dense B0, or NULL
+  const double* Bw;
+  int bw;
+  int* pcij;      // [nb][2] hat cell (ci, cj) of every point, for the window lookups
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -342,7 +346,7 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 // (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
 // right-hand sides of the structural solves.
 struct FsiLayout {
-  size_t xs, krow, vec, pw, work, rf, pidx;
+  size_t xs, krow, vec, pw, work, rf, pidx, pcij;
   size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys;
   size_t total;
 };
@@ -369,7 +373,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
   L.work = L.pw + al16((size_t)4 * nb * 8);
   L.rf = L.work + al16(lx * 16);
   L.pidx = L.rf + al16(lx * 4);
-  L.chi = L.pidx + al16((size_t)4 * nb * 4);
+  L.pcij = L.pidx + al16((size_t)4 * nb * 4);
+  L.chi = L.pcij + al16((size_t)2 * nb * 4);
   L.rz = L.chi + al16((size_t)bd.nd * 8);
   L.cn = L.rz + al16((size_t)bd.nd * 8);
   L.rchi = L.cn + al16((size_t)bd.nd * 8);
@@ -447,6 +452,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   float4* work4 = reinterpret_cast<float4*>(dyn_smem + L.work);
   float* rf = reinterpret_cast<float*>(dyn_smem + L.rf);  // float copy of the vector X is applied to
   int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
+  int* pcij_s = reinterpret_cast<int*>(dyn_smem + L.pcij);
   double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
   double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
   double* cn_s = reinterpret_cast<double*>(dyn_smem + L.cn);      // r^zeta_n of every free dof
@@ -586,6 +592,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           const double wq = (aa ? rx : 1.0 - rx) * (bb ? ry : 1.0 - ry);
           a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
           a.pw[4 * p + q] = wq;
+          if (q == 0) {
+            a.pcij[2 * p] = ci;
+            a.pcij[2 * p + 1] = cj;
+          }
           double u, v;
           e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
           ubx = wq * u;
@@ -669,6 +679,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       pidx_s[e] = __ldcg(&a.pidx[e]);
       pw_s[e] = __ldcg(&a.pw[e]);
     }
+    for (int e = tid; e < 2 * nb; e += nthr) pcij_s[e] = __ldcg(&a.pcij[e]);
     for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
     __syncthreads();
     if (a.n_def > 0) {  // flags: rhs -= T ((2/dt)(chi^(k) + y) - r^chi_n)
@@ -685,13 +696,17 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       __syncthreads();
     }
     clk.mark(0);
-    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (both triangles, double and float copies)
+    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (double and float copies; both triangles from
+    // the lower one for the dense B0, every entry for the sparse B0', which is not symmetric)
     {
       const double kscale = a.ds / (a.h * a.h);
       const long n2 = 2L * a.n_sd;
+      const bool dense = a.Bw == nullptr;
+      const int bw = a.bw, side = 2 * bw + 1;
+      const long carea = (long)side * side;
       for (long e = gtid; e < (long)nf * nf; e += gsize) {
         const int r = (int)(e / nf), cidx = (int)(e % nf);
-        if (cidx > r) continue;
+        if (dense && cidx > r) continue;
         const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
         double acc = 0.0;
         int ib[4];
@@ -701,14 +716,30 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           ib[be] = pidx_s[4 * pb + be];
           wb[be] = pw_s[4 * pb + be];
         }
-        for (int al = 0; al < 4; ++al) {
-          const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
-          const double wa = pw_s[4 * pa + al];
-          const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
-          double t = 0.0;
+        if (dense) {
+          for (int al = 0; al < 4; ++al) {
+            const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
+            const double wa = pw_s[4 * pa + al];
+            const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
+            double t = 0.0;
 #pragma unroll
-          for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
-          acc += wa * t;
+            for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
+            acc += wa * t;
+          }
+        } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
+          const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
+          for (int al = 0; al < 4; ++al) {
+            const double wa = pw_s[4 * pa + al];
+            double t = 0.0;
+#pragma unroll
+            for (int be = 0; be < 4; ++be) {
+              const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+              if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
+                t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
+                                   (long)(dj + bw) * side + (di + bw)];
+            }
+            acc += wa * t;
+          }
         }
         double kv = kscale * acc;
         const int ba = a.point_body[pa], bbd = a.point_body[pb];
@@ -719,12 +750,15 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
           kv += b_kc[ba] * sa * sb;
         } else if (ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
-          kv += a.ds * a.two_dt * __ldcg(&a.G[(long)cidx * nf + r]);  // (2 ds/dt) T J_d^-1 T^T
+          // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
+          kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
         }
         a.K[(long)r * nf + cidx] = kv;
-        a.K[(long)cidx * nf + r] = kv;
         a.S[(long)r * lx + cidx] = (float)kv;
-        a.S[(long)cidx * lx + r] = (float)kv;
+        if (dense) {
+          a.K[(long)cidx * nf + r] = kv;
+          a.S[(long)cidx * lx + r] = (float)kv;
+        }
       }
     }
     grid.sync();
@@ -835,7 +869,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         float* Lf = Xs;  // CTA 0 factors in the space of X, which is being rebuilt
         if (blockIdx.x == 0) {
           for (int i = tid >> 5; i < nf; i += nthr >> 5)
-            for (int k = lane; k <= i; k += 32) Lf[(long)i * ld + k] = (float)__ldcg(&a.K[(long)i * nf + k]);
+            for (int k = lane; k <= i; k += 32)  // the symmetric part of K (K itself for the dense B0)
+              Lf[(long)i * ld + k] =
+                  (float)(0.5 * (__ldcg(&a.K[(long)i * nf + k]) + __ldcg(&a.K[(long)k * nf + i])));
           __syncthreads();
           chol_blocked(Lf, nf, ld, &sh_bad);
           tri_inverse(Lf, nf, ld, a.T);
@@ -1227,6 +1263,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.bzdot = c->d_bzdot;
   a.bref = c->d_bref;
   a.G = c->d_G;
+  a.Bw = c->Bw;
+  a.bw = c->bw;
+  a.pcij = c->d_pcij;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);

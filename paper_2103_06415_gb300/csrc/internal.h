@@ -58,7 +58,10 @@ struct fsi_ctx {
   // sub-domain
   int have_sd;
   int i_lo, i_hi, j_lo, j_hi, ni, nj, n_sd;
-  double* B0;  // (2 n_sd)^2 row-major, double
+  double* B0;  // (2 n_sd)^2 row-major, double (NULL when the sparse B0' is used)
+  double* Bw;  // sparse B0' in the windowed column format of b0_sparse.cu, or NULL
+  int bw;      // window half-width of Bw (Omega_0 points)
+  long long b0_nnz;  // kept entries of B0' (sparse build)
   double* d_factor;  // (2 n_sd)^2 lower Cholesky factor of B0 + tau I (fsi_factor_operator), or NULL
   int have_b0;
   double b0_seconds;
@@ -73,6 +76,7 @@ struct fsi_ctx {
   double *d_rpts, *d_rur;
   // FSI workspace
   int* d_pidx;     // [nb*4] Omega_0 point index
+  int* d_pcij;     // [nb*2] hat cell (ci, cj) of every point
   double* d_pw;    // [nb*4]
   double* d_sv;    // [nb*2] torsional S entries (Q_j R)
   double* d_rhs;   // [nf]
@@ -127,6 +131,19 @@ struct B0Box {
   long tab_off;  // first entry of this box's stencil tables (Green's-function method)
 };
 
+// Entry (row, col) of the sparse B0' in the windowed column format of b0_sparse.cu (unknown ordering of
+// B0: the n_sd x-components, then the n_sd y-components, points row by row): column col keeps, for each
+// component of the row, the (2w+1)^2 Omega_0 points within w of its own point.
+__host__ __device__ __forceinline__ double b0w_lookup(const double* Wv, int w, int ni, int n_sd, long row, long col) {
+  const int ca = row >= n_sd, cb = col >= n_sd;
+  const int pa = (int)(row - (long)ca * n_sd), pb = (int)(col - (long)cb * n_sd);
+  const int ja = pa / ni, ia = pa - ja * ni, jb = pb / ni, ib = pb - jb * ni;
+  const int dj = ja - jb, di = ia - ib;
+  if (dj > w || dj < -w || di > w || di < -w) return 0.0;
+  const long side = 2 * w + 1;
+  return Wv[col * 2 * side * side + ca * side * side + (dj + w) * side + (di + w)];
+}
+
 // box holding the global unknown u (boxes sorted by row_off)
 __device__ __forceinline__ int b0_find_box(const B0Box* bx, int n, long u) {
   int lo = 0, hi = n - 1;
@@ -174,6 +191,10 @@ fsi_status launch_fsi(fsi_ctx* c);
 // b0.cu
 fsi_status build_b0(fsi_ctx* c);
 fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
+fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_out);
+// b0_sparse.cu
+fsi_status build_b0_window(fsi_ctx* c, double drop_tol);
+fsi_status b0_window_entries(fsi_ctx* c, const int64_t* d_rows, const int64_t* d_cols, int n, double* d_out);
 // b0_columns.cu
 fsi_status build_b0_columns(fsi_ctx* c);
 fsi_status b0_columns(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);

@@ -21,7 +21,7 @@ def oracle_sim(w, **kw):
                     w["sd_box"], bodies, w["ds"], **kw)
 
 
-def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0, **kw):
+def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0, drop_tol=0.0, **kw):
     import paper_2103_06415_gb300 as lib
     c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
                     precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method, **kw)
@@ -36,7 +36,7 @@ def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0
     if w.get("sd_box") is not None:
         c.set_subdomain(*w["sd_box"])
         if precompute:
-            c.precompute()
+            c.precompute(drop_tol)
     return c
 
 

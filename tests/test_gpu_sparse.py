@@ -1,0 +1,104 @@
+"""Sparse B0' (Sec. 3.3, Eq. filtereq, reading R8) on the GPU against the FP64 oracle (needs a GB300).
+
+The windowed column store must hold exactly the entries the filter keeps (same values as the dense
+operator's), the FSI runs that use it must follow the oracle's runs with the same filter, and at the
+paper's drop tolerance the forces must stay within 2 % of the dense operator's."""
+
+import numpy as np
+import pytest
+
+from oracle import ib as oib
+from paper_2103_06415_gb300 import workloads as wl
+
+from runners import gpu_context, oracle_history, oracle_sim, rel_err
+
+pytestmark = pytest.mark.gpu
+
+EPS = 0.007
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2103_06415_gb300 as p
+    return p
+
+
+@pytest.mark.parametrize("eps", [EPS, 0.05])
+def test_windowed_b0_equals_filtered_oracle_columns(lib, eps):
+    w = wl.small_plate()
+    sim = oracle_sim(w)
+    n2 = 2 * sim.sd.n_sd
+    ref = np.stack([oib.b0_column(sim.sd, c, sim.re, sim.dt, eps) for c in range(n2)], axis=1)
+    ctx = gpu_context(w, drop_tol=eps)
+    rows, cols = np.meshgrid(np.arange(n2), np.arange(n2), indexing="ij")
+    got = ctx.operator_entries(rows.ravel(), cols.ravel()).reshape(n2, n2)
+    assert np.array_equal(got != 0.0, ref != 0.0)                 # the same kept pattern, bit for bit
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    st = ctx.stats()
+    assert st["b0_nnz"] == int(np.count_nonzero(ref)) and st["b0_window"] >= 1
+    ctx.close()
+
+
+def test_sparse_plate_run_matches_oracle(lib):
+    w = wl.small_plate()
+    n = 12
+    sim = oracle_sim(w, drop_tol=EPS)
+    for _ in range(n):
+        sim.step()
+    ctx = gpu_context(w, drop_tol=EPS)
+    ctx.advance(n)
+    hist, ref = ctx.history(0), oracle_history(sim)
+    assert np.array_equal(hist[:, 5], ref[:, 5])
+    for k in range(5):
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+
+
+def test_sparse_flag_run_matches_oracle(lib):
+    w = wl.small_flag()
+    n = 10
+    sim = oracle_sim(w, drop_tol=EPS, tol=1e-12)
+    for _ in range(n):
+        sim.step()
+    ctx = gpu_context(w, drop_tol=EPS, tol=1e-12)
+    ctx.advance(n)
+    hist, ref = ctx.history(0), oracle_history(sim)
+    for k in (0, 1, 3, 4):
+        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+    chi, _, _ = ctx.beam_state(0)
+    assert np.max(np.abs(chi - sim.bodies[0].chi.reshape(-1, 3))) < 1e-13
+
+
+def test_config2_sparse_against_dense(lib):
+    """flag_512x256_3lvl: B0' at the paper's tolerance stores a small fraction of B0 and keeps the force and
+    deflection histories within 2 % of the dense operator's."""
+    w = wl.flag_512x256_3lvl()
+    n = 20
+    out = []
+    for eps in (0.0, EPS):
+        ctx = gpu_context(w, precision=1, drop_tol=eps)
+        ctx.advance(n)
+        out.append((ctx.history(0), ctx.stats()))
+        ctx.close()
+    (hd, sd), (hs, ss) = out
+    n2 = 2 * sd["n_sd"]
+    assert sd["b0_nnz"] == n2 * n2 and sd["b0_window"] == 0
+    assert ss["b0_nnz"] < 0.05 * n2 * n2
+    for k in (0, 1, 3):
+        assert rel_err(hs[:, k], hd[:, k]) < 0.02, k
+
+
+def test_sparse_arguments(lib):
+    w = wl.small_plate()
+    for bad in (-0.1, 1.0, float("nan")):
+        c = gpu_context(w, precompute=False)
+        with pytest.raises(lib.FsiError):
+            c.precompute(bad)
+        c.close()
+    c = gpu_context(w, precompute=False, b0_method=1)
+    with pytest.raises(lib.FsiError):
+        c.precompute(EPS)
+    c.close()
+    c = gpu_context(w, drop_tol=EPS)
+    with pytest.raises(lib.FsiError):
+        c.factor_operator(1e-10)
+    c.close()
