@@ -298,11 +298,11 @@ def main():
         dist.init_process_group("gloo")
     prec = lib.FSI_PREC_FP32 if args.precision == "fp32" else lib.FSI_PREC_FP64
 
-    def make(p):
+    def make(p, drop_tol=0.0):
         st = torch.cuda.Stream()
         t0 = time.perf_counter()
         c = gpu_context(w, precision=p, precompute=False, stream=st.cuda_stream)
-        c.precompute()
+        c.precompute(drop_tol)
         return c, st, time.perf_counter() - t0
 
     ctx, stream, b0_s = make(prec)
@@ -354,6 +354,20 @@ def main():
         extra["mixed_vs_fp64_rel_l2"] = errs
         extra["mixed_within_1e-5"] = bool(max(errs.values()) <= 1e-5)
         ctx64.close()
+        # the same run with the sparse B0' of Eq. filtereq at the paper's drop tolerance (0.007)
+        ctxs, streams, b0_sp = make(prec, 0.007)
+        ctxs.advance(args.warmup)
+        tsp = timed_steps(ctxs, streams, args.steps)
+        sts = ctxs.stats()
+        n2 = 2 * sts["n_sd"]
+        side = 2 * sts["b0_window"] + 1
+        extra["sparse_b0"] = {"drop_tol": 0.007, "value": cells * args.steps / (sum(tsp) * 1e-3),
+                              "unit": "cell-steps/s", "ms_per_step": statistics.mean(tsp),
+                              "kept_entries": sts["b0_nnz"], "dense_entries": n2 * n2,
+                              "window_half_width": sts["b0_window"],
+                              "bytes": n2 * 2 * side * side * 8, "dense_bytes": n2 * n2 * 8,
+                              "build_s": b0_sp}
+        ctxs.close()
 
     # dominant-kernel roofline: live CUDA-event timing of each launch of the class on the context stream
     roof = None
