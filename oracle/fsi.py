@@ -103,7 +103,7 @@ class Sim:
     """A full run: nested levels, one sub-domain box, bodies, FP64 state."""
 
     def __init__(self, nx, ny, h, x0, y0, n_levels, re, dt, uinf, sd_box, bodies, ds,
-                 tol=1e-7, max_iters=50, drop_tol=0.0):
+                 tol=1e-7, max_iters=50, drop_tol=0.0, coupling="subdomain"):
         self.levels = grid.make_levels(nx, ny, h, x0, y0, n_levels)
         self.re, self.dt = float(re), float(dt)
         self.uinf = np.asarray(uinf, dtype=np.float64)
@@ -111,6 +111,10 @@ class Sim:
         self.bodies = list(bodies)
         self.tol, self.max_iters = float(tol), int(max_iters)
         self.drop_tol = float(drop_tol)      # Eq. filtereq: B0' in place of B0 in the small system
+        # "subdomain": E ~ P E0 (Eq. operatorapprox); "true": E at the body points, the small matrix
+        # E C (C^T A C)^-1 C^T E^T built column by column (the comparator of Sec. 5.1)
+        self.coupling = coupling
+        self.last_pts = None
         self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box) if sd_box is not None else None
         self.w = [np.zeros(l.shape) for l in self.levels]
         self.s = [np.zeros(l.shape) for l in self.levels]
@@ -167,7 +171,7 @@ class Sim:
     def fsi(self):
         lev, sd, dt, ds, nb = self.levels[0], self.sd, self.dt, self.ds, self.nb
         u, v = grid.faces_from_s(self.s[0], lev)
-        e0q = sd.e0(u + self.uinf[0], v + self.uinf[1])       # E0 (C s* + q_inf)
+        e0q = sd.e0(u + self.uinf[0], v + self.uinf[1]) if self.coupling != "true" else None  # E0 (C s* + q_inf)
         offs = self._body_offsets()
         moving = [(b, o) for b, o in zip(self.bodies, offs) if b.kind != "rigid"]
         # iterate state: theta (torsional) or chi (deformable), and its rate phi or zeta
@@ -175,16 +179,22 @@ class Sim:
         rate_k = {id(b): (b.phi if b.kind == "torsional" else b.zeta.copy()) for b, _ in moving}
         for it in range(self.max_iters):
             pts = np.concatenate([b.points(state_k.get(id(b))) for b in self.bodies])
-            idx, wts = sd.p_rows(pts)
-            cols = np.unique(np.concatenate([idx.ravel(), idx.ravel() + sd.n_sd]))
-            pos = {c: k for k, c in enumerate(cols)}
-            pd = np.zeros((2 * nb, len(cols)))
-            for p in range(nb):
-                for k in range(4):
-                    pd[p, pos[idx[p, k]]] += wts[p, k]
-                    pd[nb + p, pos[idx[p, k] + sd.n_sd]] += wts[p, k]
-            kmat = (ds / lev.h ** 2) * pd @ self.b0_cols(cols)[cols, :] @ pd.T
-            rhs = pd @ e0q[cols]                                   # P E0 (C s* + q_inf)
+            if self.coupling == "true":
+                kmat = (ds / lev.h ** 2) * np.stack(
+                    [ib.ke_column(lev, pts, m, self.re, self.dt) for m in range(2 * nb)], axis=1)
+                rhs = ib.e_points(lev, pts, u + self.uinf[0], v + self.uinf[1])   # E (C s* + q_inf)
+                idx = wts = None
+            else:
+                idx, wts = sd.p_rows(pts)
+                cols = np.unique(np.concatenate([idx.ravel(), idx.ravel() + sd.n_sd]))
+                pos = {c: k for k, c in enumerate(cols)}
+                pd = np.zeros((2 * nb, len(cols)))
+                for p in range(nb):
+                    for k in range(4):
+                        pd[p, pos[idx[p, k]]] += wts[p, k]
+                        pd[nb + p, pos[idx[p, k] + sd.n_sd]] += wts[p, k]
+                kmat = (ds / lev.h ** 2) * pd @ self.b0_cols(cols)[cols, :] @ pd.T
+                rhs = pd @ e0q[cols]                                   # P E0 (C s* + q_inf)
             svec, dstate = {}, {}
             for b, o in zip(self.bodies, offs):
                 if b.kind == "rigid":
@@ -233,6 +243,7 @@ class Sim:
                 rate_k[id(b)] = 2.0 / dt * state_k[id(b)] - self._r_theta[id(b)]
                 dmax = max(dmax, abs(dth))
             self.last_p = (idx, wts)
+            self.last_pts = pts
             self.last_svec = svec
             self.last_dmax = dmax
             if dmax <= self.tol:
@@ -243,13 +254,16 @@ class Sim:
 
     def corrector(self, f):
         lev, sd, nb = self.levels[0], self.sd, self.nb
-        idx, wts = self.last_p
-        g = np.zeros(2 * sd.n_sd)
-        for p in range(nb):                                  # P^T f
-            for k in range(4):
-                g[idx[p, k]] += wts[p, k] * f[p]
-                g[idx[p, k] + sd.n_sd] += wts[p, k] * f[nb + p]
-        u, v = sd.e0t(g)
+        if self.coupling == "true":
+            u, v = ib.et_points(lev, self.last_pts, f)          # E^T f at the last iterate's points
+        else:
+            idx, wts = self.last_p
+            g = np.zeros(2 * sd.n_sd)
+            for p in range(nb):                                  # P^T f
+                for k in range(4):
+                    g[idx[p, k]] += wts[p, k] * f[p]
+                    g[idx[p, k] + sd.n_sd] += wts[p, k] * f[nb + p]
+            u, v = sd.e0t(g)
         src = (self.ds / lev.h ** 2) * grid.curl_faces(u, v, lev)
         zero = np.zeros(lev.shape)
         dw = grid.solve_aw(src, zero, lev, self.re, self.dt)

@@ -12,6 +12,9 @@ Test infrastructure only (see ``oracle/__init__.py``).
 * ``b0_column``  -- column j of ``B0 = E0 C (C^T A C)^{-1} C^T E0^T`` computed as the
                     action on the canonical vector e_j (Eq. action, Algorithm 1), optionally
                     filtered by the drop tolerance of Eq. filtereq (``drop_filter``).
+* ``e_points``, ``et_points``, ``ke_column`` -- the true IB interpolation ``E`` at the body
+                    points themselves (Sec. 2.2, the operator the sub-domain approach replaces),
+                    its transpose, and a column of ``E C (C^T A C)^{-1} C^T E^T``.
 
 Unknown ordering of sub-domain vectors: the ``n_sd`` x-components first, then
 the ``n_sd`` y-components; points are numbered row by row (j-major) inside the box.
@@ -158,3 +161,56 @@ def b0_column(sd, col, re, dt, drop_tol=0.0):
 def b0_dense(sd, re, dt):
     """All columns of ``B0`` (Algorithm 1 with zero drop tolerance); small grids only."""
     return np.stack([b0_column(sd, c, re, dt) for c in range(2 * sd.n_sd)], axis=1)
+
+
+# -- true E at the body points (Sec. 2.2; the comparator of Sec. 5.1) ---------------------------
+
+def _face_weights(lev, pts, comp):
+    """Face indices and delta weights of every body point: u faces sit at (x_i, y_{j+1/2}), v faces at
+    (x_{i+1/2}, y_j); the 3-point delta reaches 1.5 cells, so 4 x 4 candidate faces per point."""
+    X = (np.asarray(pts)[:, 0] - lev.x0) / lev.h
+    Y = (np.asarray(pts)[:, 1] - lev.y0) / lev.h
+    ox, oy = (0.0, 0.5) if comp == 0 else (0.5, 0.0)
+    i0 = np.floor(X - ox).astype(np.int64) - 1
+    j0 = np.floor(Y - oy).astype(np.int64) - 1
+    d = np.arange(4)
+    I = i0[:, None, None] + d[None, None, :]
+    J = j0[:, None, None] + d[None, :, None]
+    w = delta3(I + ox - X[:, None, None]) * delta3(J + oy - Y[:, None, None])
+    return I, J, w
+
+
+def e_points(lev, pts, u, v):
+    """``E q``: the face fluxes interpolated to the body points, (x components, then y components)."""
+    I, J, w = _face_weights(lev, pts, 0)
+    ub = np.sum(w * u[J, I], axis=(1, 2))
+    I, J, w = _face_weights(lev, pts, 1)
+    vb = np.sum(w * v[J, I], axis=(1, 2))
+    return np.concatenate([ub, vb])
+
+
+def et_points(lev, pts, f):
+    """``E^T f``: a body-point vector spread onto the faces (same weights, transposed)."""
+    nb = len(pts)
+    u = np.zeros((lev.ny, lev.nx + 1))
+    v = np.zeros((lev.ny + 1, lev.nx))
+    I, J, w = _face_weights(lev, pts, 0)
+    np.add.at(u, (J, I), w * np.asarray(f)[:nb, None, None])
+    I, J, w = _face_weights(lev, pts, 1)
+    np.add.at(v, (J, I), w * np.asarray(f)[nb:, None, None])
+    return u, v
+
+
+def ke_column(lev, pts, col, re, dt):
+    """Column ``col`` of ``E C Lap^{-1} A_w^{-1} C^T E^T`` at the body points (the finest level with
+    homogeneous boundary values, reading R6)."""
+    e = np.zeros(2 * len(pts))
+    e[col] = 1.0
+    u, v = et_points(lev, pts, e)
+    src = grid.curl_faces(u, v, lev)
+    zero = np.zeros(lev.shape)
+    w = grid.solve_aw(src, zero, lev, re, dt)
+    s = np.zeros(lev.shape)
+    s[1:-1, 1:-1] = grid.solve_lap(w, zero, lev)
+    qu, qv = grid.faces_from_s(s, lev)
+    return e_points(lev, pts, qu, qv)
