@@ -83,6 +83,17 @@ typedef struct {
                      otherwise FSI_ERR_UNSUPPORTED); 2 autotune: time both for each of the three passes at
                      fsi_create and keep the faster (decisions are cached per grid shape for the process, so
                      equal grids take equal paths); FP64 contexts and unsupported sizes then use FFT. */
+  int coupling; /* 0: the sub-domain method (E0, P and the precomputed B0 of Sec. 3).  1: the true E and E^T
+                   at the body points (Sec. 2.2), the comparator of Sec. 5.1: each FSI iteration solves the
+                   small system matrix-free by conjugate gradients with one finest-level (C^T A C)^-1 per
+                   Krylov iteration (homogeneous boundary values); fsi_precompute then builds no B0, the
+                   sub-domain box only bounds the body points (outside: FSI_ERR_BODY_OUTSIDE_SUBDOMAIN), and
+                   only TORSIONAL and RIGID bodies (at most 1024 points) are supported (else
+                   FSI_ERR_UNSUPPORTED at fsi_precompute).  With use_graph the FSI and Krylov loops run as
+                   device-side graph loops (no host round trip per iteration). */
+  double krylov_tol; /* coupling 1: stop when |r| <= krylov_tol |rhs| (<= 0 -> 1e-10 FP64, 1e-5 FP32) */
+  int krylov_max_iters; /* coupling 1: Krylov iterations per FSI iteration (<= 0 -> 2 nf + 20); reaching it
+                           without convergence latches FSI_ERR_NOT_CONVERGED */
 } fsi_exec_desc;
 
 /* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at
@@ -124,7 +135,8 @@ typedef struct {
   int nf;              /* number of surface-stress unknowns (2 x body points) */
   double b0_seconds;   /* wall time of the last fsi_precompute */
   size_t device_bytes; /* device memory held by the context */
-  int launches_per_step; /* kernels this library launches per time step */
+  int launches_per_step; /* kernels this library launches per time step (coupling 1: of the last step,
+                            the loops' launches counted from the device's iteration counters) */
   int last_solves;       /* refinement solves of the small system in the last step (all FSI iterations) */
   int inverse_rebuilds;  /* times the float inverse of the small system was rebuilt so far */
   int dst_gemm[3];       /* 1 if pass p (0 forward x, 1 y solve, 2 inverse x) runs as a tensor-core GEMM */
@@ -132,6 +144,8 @@ typedef struct {
   int last_refreshes;    /* Newton-Schulz refreshes of the float inverse in the last step */
   int64_t b0_nnz;        /* stored nonzero entries of B0: (2 n_sd)^2 dense, the kept entries of B0' sparse */
   int b0_window;         /* sparse B0': half-width (Omega_0 points) of each column's window; 0 dense */
+  int last_krylov_iters;     /* coupling 1: Krylov iterations of the last step (all FSI iterations) */
+  int64_t krylov_iters_total; /* coupling 1: Krylov iterations since the context was created */
 } fsi_stats;
 
 typedef struct fsi_ctx fsi_ctx;
@@ -196,7 +210,7 @@ fsi_status fsi_set_field(fsi_ctx* ctx, int level, int which, const double* in);
 
 /* Sampled entries of B0 (or of the sparse B0', zero where dropped): out[k] = B0[rows[k], cols[k]] for
  * k < n (synchronising).  Unknown ordering: the n_sd x-components (points row by row inside the box),
- * then the n_sd y-components. */
+ * then the n_sd y-components.  coupling 1 (no B0): FSI_ERR_UNSUPPORTED. */
 fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n,
                                     double* out);
 
@@ -210,7 +224,8 @@ fsi_status fsi_factor_operator(fsi_ctx* ctx, double tau_rel, double* tau_out, do
 fsi_status fsi_get_factor_entries(fsi_ctx* ctx, const int64_t* rows, const int64_t* cols, int n, double* out);
 
 /* Interpolation map P of the last step's final FSI iterate (Eq. weights): for each body point p the four
- * Omega_0 point indices idx[4p..4p+3] and hat weights w[4p..4p+3] (synchronising). */
+ * Omega_0 point indices idx[4p..4p+3] and hat weights w[4p..4p+3] (synchronising).  coupling 1 (no P):
+ * FSI_ERR_UNSUPPORTED. */
 fsi_status fsi_get_interp(fsi_ctx* ctx, int64_t* idx, double* w, int cap_points);
 
 fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);

@@ -11,9 +11,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
+from ._lib import COUPLING_SUBDOMAIN, COUPLING_TRUE_E, FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
 
-__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError"]
+__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError",
+           "COUPLING_SUBDOMAIN", "COUPLING_TRUE_E"]
 
 
 def _dp(a):
@@ -26,15 +27,17 @@ class Context:
     grid: nx, ny (powers of two), n_levels, x0, y0, h, re, dt, uinf=(U, V)
     precision: FSI_PREC_FP64 or FSI_PREC_FP32; stream: a cudaStream_t handle (int) or None.
     dst_method: 0 FFT sine transforms, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotune per pass.
+    coupling: COUPLING_SUBDOMAIN (the method) or COUPLING_TRUE_E (the true-E comparator; krylov_tol and
+    krylov_max_iters control its conjugate-gradient solve, 0 = library defaults).
     """
 
     def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
                  stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0,
-                 dst_method=0):
+                 dst_method=0, coupling=COUPLING_SUBDOMAIN, krylov_tol=0.0, krylov_max_iters=0):
         self._lib = _lib.load()
         g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
         x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
-                          1 if use_graph else 0, b0_method, dst_method)
+                          1 if use_graph else 0, b0_method, dst_method, coupling, krylov_tol, krylov_max_iters)
         h_ = ctypes.c_void_p()
         check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
         self._h = h_

@@ -11,6 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libibfsi.so")
 
 FSI_PREC_FP64 = 0
+COUPLING_SUBDOMAIN = 0  # E0, P and the precomputed B0 (Sec. 3)
+COUPLING_TRUE_E = 1     # E, E^T at the body points, Krylov solve per FSI iteration (Sec. 2.2)
 FSI_PREC_FP32 = 1
 FSI_BODY_RIGID = 0
 FSI_BODY_TORSIONAL = 1
@@ -31,7 +33,8 @@ class GridDesc(ctypes.Structure):
 class ExecDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("b0_method", ctypes.c_int), ("dst_method", ctypes.c_int)]
+                ("b0_method", ctypes.c_int), ("dst_method", ctypes.c_int), ("coupling", ctypes.c_int),
+                ("krylov_tol", ctypes.c_double), ("krylov_max_iters", ctypes.c_int)]
 
 
 class BodyDesc(ctypes.Structure):
@@ -54,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("launches_per_step", ctypes.c_int),
                 ("last_solves", ctypes.c_int), ("inverse_rebuilds", ctypes.c_int),
                 ("dst_gemm", ctypes.c_int * 3), ("dst_us", ctypes.c_double * 6), ("last_refreshes", ctypes.c_int),
-                ("b0_nnz", ctypes.c_int64), ("b0_window", ctypes.c_int)]
+                ("b0_nnz", ctypes.c_int64), ("b0_window", ctypes.c_int), ("last_krylov_iters", ctypes.c_int),
+                ("krylov_iters_total", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

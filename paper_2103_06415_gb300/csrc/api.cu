@@ -290,6 +290,11 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
     delete c;
     return FSI_ERR_UNSUPPORTED;
   }
+  if (c->x.coupling != 0 && c->x.coupling != 1) {
+    delete c;
+    return FSI_ERR_INVALID_ARG;
+  }
+  if (!(c->x.krylov_tol > 0)) c->x.krylov_tol = c->x.precision == FSI_PREC_FP64 ? 1e-10 : 1e-5;
   if (c->x.max_iters <= 0) c->x.max_iters = 50;
   if (!(c->x.tol > 0)) c->x.tol = 1e-7;
   if (c->x.history_cap <= 0) c->x.history_cap = 1 << 16;
@@ -438,10 +443,18 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   c->n_bodies = (int)c->bodies.size();
   c->nf = 2 * c->nb;
   if (c->n_bodies > 64) return FSI_ERR_UNSUPPORTED;
-  if (c->nb > 0 && !fsi_smem_fits(c)) return FSI_ERR_UNSUPPORTED;
+  const int true_e = c->x.coupling == 1;
+  if (true_e) {  // true E at the body points: no B0; torsional and rigid bodies
+    if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024) return FSI_ERR_UNSUPPORTED;
+    if (c->x.krylov_max_iters <= 0) c->x.krylov_max_iters = 2 * c->nf + 20;
+  } else if (c->nb > 0 && !fsi_smem_fits(c)) {
+    return FSI_ERR_UNSUPPORTED;
+  }
   const size_t n2 = 2 * (size_t)c->n_sd;
   fsi_status st = FSI_OK;
-  if (drop_tol > 0.0) {  // sparse B0' (Eq. filtereq) in the windowed column format
+  if (true_e) {
+    c->b0_seconds = 0.0;
+  } else if (drop_tol > 0.0) {  // sparse B0' (Eq. filtereq) in the windowed column format
     st = build_b0_window(c, drop_tol);
   } else {
     if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
@@ -516,6 +529,22 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
       FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bzdot, c->beam_zdot.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
       FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bref, c->beam_ref.data(), nd * 8, cudaMemcpyHostToDevice, c->stream));
     }
+    if (true_e) {
+      const size_t nf = (size_t)c->nf;
+      if (!(c->te_w = ctx_alloc(c, (size_t)c->lvl_elems * c->esz)) ||
+          !(c->te_s = ctx_alloc(c, (size_t)c->lvl_elems * c->esz)) ||
+          !(c->d_te_pt = ctx_alloc(c, (size_t)c->nb * true_e_point_bytes())) ||
+          !(c->d_te_r = (double*)ctx_alloc(c, nf * 8)) || !(c->d_te_p = (double*)ctx_alloc(c, nf * 8)) ||
+          !(c->d_te_scal = (double*)ctx_alloc(c, 8 * 8)) || !(c->d_te_ctl = (int*)ctx_alloc(c, 16 * sizeof(int))) ||
+          !(c->d_te_total = (unsigned long long*)ctx_alloc(c, sizeof(unsigned long long))))
+        return FSI_ERR_OOM;
+      for (int k = 0; k < 2; ++k)
+        if (!c->te_stream[k]) FSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->te_stream[k], cudaStreamNonBlocking));
+      TRY(true_e_setup(c));
+      FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      c->stage = 1;
+      return FSI_OK;
+    }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -538,10 +567,12 @@ void prof_mark(fsi_ctx* c, int cls) {
   cudaEventRecord(c->prof_ev[c->prof_used++], c->stream);
 }
 
-static fsi_status enqueue_step(fsi_ctx* c, int first) {
+static fsi_status enqueue_step(fsi_ctx* c, int first, int capture = 0) {
   c->launches_per_step = 0;
   TRY(launch_predictor(c, first));
-  if (c->nb > 0) {
+  if (c->nb > 0 && c->x.coupling == 1) {
+    TRY(launch_true_e(c, capture));
+  } else if (c->nb > 0) {
     TRY(launch_fsi(c));
     TRY(launch_corrector(c));
   }
@@ -553,7 +584,7 @@ static fsi_status build_graph(fsi_ctx* c) {
     cudaGetLastError();
     return FSI_ERR_CUDA;
   }
-  fsi_status st = enqueue_step(c, 0);
+  fsi_status st = enqueue_step(c, 0, 1);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (st != FSI_OK || e != cudaSuccess || !g) {
@@ -770,6 +801,7 @@ __global__ static void k_gather_b0(const double* B0, long n2, const int64_t* row
 extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, const int64_t* cols, int n,
                                                double* out) {
   if (!c || n < 0 || (n > 0 && (!rows || !cols || !out))) return FSI_ERR_INVALID_ARG;
+  if (c->x.coupling == 1) return FSI_ERR_UNSUPPORTED;
   if (!c->have_b0) return FSI_ERR_STATE;
   const long n2 = 2L * c->n_sd;
   for (int k = 0; k < n; ++k)
@@ -798,6 +830,7 @@ extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, 
 }
 
 extern "C" fsi_status fsi_get_interp(fsi_ctx* c, int64_t* idx, double* w, int cap_points) {
+  if (c && c->x.coupling == 1) return FSI_ERR_UNSUPPORTED;
   if (!c || !idx || !w || cap_points < c->nb || !c->d_pidx) return FSI_ERR_INVALID_ARG;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   std::vector<int> pi((size_t)c->nb * 4);
@@ -832,6 +865,15 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
     out->last_solves = ctrl[5];
     out->inverse_rebuilds = ctrl[6];
   }
+  if (c->d_te_ctl) {  // true-E loops: prep + post per FSI iteration, source + 3 passes + update per Krylov step
+    int tctl[16];
+    unsigned long long total = 0;
+    FSI_CUDA_TRY(cudaMemcpy(tctl, c->d_te_ctl, sizeof(tctl), cudaMemcpyDeviceToHost));
+    FSI_CUDA_TRY(cudaMemcpy(&total, c->d_te_total, sizeof(total), cudaMemcpyDeviceToHost));
+    out->last_krylov_iters = tctl[5];
+    out->krylov_iters_total = (int64_t)total;
+    out->launches_per_step = c->launches_per_step + 2 * out->last_iters + 5 * tctl[5];
+  }
   return FSI_OK;
 }
 
@@ -841,6 +883,8 @@ extern "C" void fsi_destroy(fsi_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   gemm_dst_free(c);
+  for (int k = 0; k < 2; ++k)
+    if (c->te_stream[k]) cudaStreamDestroy(c->te_stream[k]);
   ctx_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -31,6 +31,7 @@ struct BodyState {
   double theta, phi, phidot;
   double theta_k, phi_k, r_phi, r_theta, jac;
   double fx, fy, moment;
+  double theta_p;  // true-E coupling: angle of the iterate whose S produced the current f
 };
 
 struct fsi_ctx {
@@ -96,6 +97,14 @@ struct fsi_ctx {
   int n_def, nd_tot, ne_tot, nd_max;
   std::vector<double> beam_chi, beam_zeta, beam_zdot, beam_ref;
   double *d_bchi, *d_bzeta, *d_bzdot, *d_bref, *d_G;
+  // true-E coupling (true_e.cu): level-0 w, s of the operator application (zero ring), point face windows,
+  // CG vectors r and p, scalars, control words, CG iterations since creation, capture streams of the loops
+  void *te_w, *te_s;
+  void* d_te_pt;
+  double *d_te_r, *d_te_p, *d_te_scal;
+  int* d_te_ctl;
+  unsigned long long* d_te_total;
+  cudaStream_t te_stream[2];
   double* d_hist;  // [cap][n_bodies][6]
   int hist_cap;
   long long steps_done;
@@ -188,6 +197,10 @@ fsi_status launch_corrector(fsi_ctx* c);
 fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void* s, int use_ring, int mode);
 // fsi.cu
 fsi_status launch_fsi(fsi_ctx* c);
+// true_e.cu
+fsi_status launch_true_e(fsi_ctx* c, int capture);
+fsi_status true_e_setup(fsi_ctx* c);
+size_t true_e_point_bytes();
 // b0.cu
 fsi_status build_b0(fsi_ctx* c);
 fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
