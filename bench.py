@@ -42,6 +42,14 @@ def parse():
     ap.add_argument("--serving", type=int, default=0,
                     help="serving mode: stream this many config-4 requests through the continuous-batching "
                          "server and print one JSON line")
+    ap.add_argument("--no-comparator", action="store_true",
+                    help="skip the true-E comparator runs (Sec. 5.1 speed-up experiment)")
+    ap.add_argument("--comparator-only", action="store_true",
+                    help="run only the true-E comparator and print its JSON object")
+    ap.add_argument("--comparator-case", default="",
+                    help="comparator workload to run (default: both); e.g. plate_128")
+    ap.add_argument("--comparator-runs", default="",
+                    help="comma-separated comparator runs (default: all), e.g. fp64_true_e")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: build the reduced-Omega_0 variant of the workload, run this many "
                          "eager (non-graph) steps and exit without timing (for ncu captures)")
@@ -235,6 +243,64 @@ def run_serving(n_req):
     srv.close()
 
 
+def run_comparator(args, timed_steps):
+    """The speed-up experiment of Sec. 5.1 (Table eldgerror): mean step time of the sub-domain method against
+    the true E, E^T at the body points (matrix-free conjugate gradients, one finest-level (C^T A C)^-1 per
+    Krylov iteration), on the torsional plates of the flag grid and of plate_128 (body points at ds = h, and
+    at the paper's ds = 2h), FP64 and FP32, with the
+    relative L2 difference of the deflection angle between the two couplings over the timed steps."""
+    import numpy as np
+    import torch
+    import paper_2103_06415_gb300 as lib
+    from paper_2103_06415_gb300 import workloads as wl
+    from runners import gpu_context
+
+    k = max(3, min(args.steps, 20))
+    out = {"steps": k, "warmup": 3, "note": "true E: Krylov tolerance = relative residual of the CG solve "
+                                            "(library default 1e-10 FP64, 1e-5 FP32; 1e-5 is also PETSc's "
+                                            "default GMRES tolerance)"}
+    cases = ([args.comparator_case] if args.comparator_case
+             else ["flag_512x256_3lvl_torsional", "plate_128", "plate_128_ds2h"])
+    only = set(x for x in args.comparator_runs.split(",") if x)
+    for name in cases:
+        w = getattr(wl, name)()
+        res = {}
+        runs = [("fp64_subdomain", lib.FSI_PREC_FP64, 0, 0.0), ("fp64_true_e", lib.FSI_PREC_FP64, 1, 0.0),
+                ("fp64_true_e_ktol1e-5", lib.FSI_PREC_FP64, 1, 1e-5), ("fp32_subdomain", lib.FSI_PREC_FP32, 0, 0.0),
+                ("fp32_true_e", lib.FSI_PREC_FP32, 1, 0.0)]
+        hist = {}
+        for tag, prec, coupling, ktol in runs:
+            if only and tag not in only:
+                continue
+            st = torch.cuda.Stream()
+            c = gpu_context(w, precision=prec, stream=st.cuda_stream, coupling=coupling, krylov_tol=ktol)
+            c.advance(3)
+            c.sync()
+            kry0 = c.stats()["krylov_iters_total"]
+            t = timed_steps(c, st, k)
+            sts = c.stats()
+            h = c.history(0)[-k:]
+            hist[tag] = h
+            r = {"ms_per_step": float(np.mean(t)), "p50_ms": float(np.median(t)),
+                 "fsi_iters_per_step": float(np.mean(h[:, 5])), "launches_last_step": sts["launches_per_step"]}
+            if coupling == 1:
+                r["krylov_iters_per_step"] = (sts["krylov_iters_total"] - kry0) / k
+                r["krylov_tol"] = ktol if ktol > 0 else (1e-10 if prec == lib.FSI_PREC_FP64 else 1e-5)
+            res[tag] = r
+            c.close()
+        for num, den, key in (("fp64_true_e", "fp64_subdomain", "fp64_speedup"),
+                              ("fp32_true_e", "fp32_subdomain", "fp32_speedup"),
+                              ("fp64_true_e_ktol1e-5", "fp64_subdomain", "fp64_speedup_ktol1e-5")):
+            if num in res and den in res:
+                res[key] = res[num]["ms_per_step"] / res[den]["ms_per_step"]
+        if "fp64_subdomain" in hist and "fp64_true_e" in hist:
+            a, b = hist["fp64_subdomain"][:, 3], hist["fp64_true_e"][:, 3]
+            res["theta_rel_l2_subdomain_vs_true_e"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        res["body_points"] = sum(bb["n_pts"] for bb in w["bodies"])
+        out[name] = res
+    return out
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -276,6 +342,24 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if args.comparator_only:
+        import torch
+        from paper_2103_06415_gb300 import build as _b
+        _b.build()
+
+        def timed_steps(c, stream, k):
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            torch.cuda.synchronize()
+            for e0, e1 in evs:
+                e0.record(stream)
+                c.advance(1)
+                e1.record(stream)
+            c.sync()
+            torch.cuda.synchronize()
+            return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+        print(json.dumps({"true_e_comparator": run_comparator(args, timed_steps)}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,6 +452,9 @@ def main():
                               "bytes": n2 * 2 * side * side * 8, "dense_bytes": n2 * n2 * 8,
                               "build_s": b0_sp}
         ctxs.close()
+
+    if rank == 0 and not args.no_comparator:
+        extra["true_e_comparator"] = run_comparator(args, timed_steps)
 
     # dominant-kernel roofline: live CUDA-event timing of each launch of the class on the context stream
     roof = None

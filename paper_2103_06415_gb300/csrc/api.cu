@@ -535,6 +535,7 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
           !(c->te_s = ctx_alloc(c, (size_t)c->lvl_elems * c->esz)) ||
           !(c->d_te_pt = ctx_alloc(c, (size_t)c->nb * true_e_point_bytes())) ||
           !(c->d_te_r = (double*)ctx_alloc(c, nf * 8)) || !(c->d_te_p = (double*)ctx_alloc(c, nf * 8)) ||
+          !(c->d_te_q = (double*)ctx_alloc(c, nf * 8)) ||
           !(c->d_te_scal = (double*)ctx_alloc(c, 8 * 8)) || !(c->d_te_ctl = (int*)ctx_alloc(c, 16 * sizeof(int))) ||
           !(c->d_te_total = (unsigned long long*)ctx_alloc(c, sizeof(unsigned long long))))
         return FSI_ERR_OOM;
@@ -865,14 +866,15 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
     out->last_solves = ctrl[5];
     out->inverse_rebuilds = ctrl[6];
   }
-  if (c->d_te_ctl) {  // true-E loops: prep + post per FSI iteration, source + 3 passes + update per Krylov step
+  if (c->d_te_ctl) {  // true-E loops: prep + post per FSI iteration; source, 3 passes, interpolation, update
+                      // per Krylov iteration
     int tctl[16];
     unsigned long long total = 0;
     FSI_CUDA_TRY(cudaMemcpy(tctl, c->d_te_ctl, sizeof(tctl), cudaMemcpyDeviceToHost));
     FSI_CUDA_TRY(cudaMemcpy(&total, c->d_te_total, sizeof(total), cudaMemcpyDeviceToHost));
     out->last_krylov_iters = tctl[5];
     out->krylov_iters_total = (int64_t)total;
-    out->launches_per_step = c->launches_per_step + 2 * out->last_iters + 5 * tctl[5];
+    out->launches_per_step = c->launches_per_step + 2 * out->last_iters + 6 * tctl[5];
   }
   return FSI_OK;
 }

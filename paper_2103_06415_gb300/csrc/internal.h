@@ -32,6 +32,7 @@ struct BodyState {
   double theta_k, phi_k, r_phi, r_theta, jac;
   double fx, fy, moment;
   double theta_p;  // true-E coupling: angle of the iterate whose S produced the current f
+  double kc;       // true-E coupling: (2 ds/dt) / J of the step
 };
 
 struct fsi_ctx {
@@ -98,10 +99,10 @@ struct fsi_ctx {
   std::vector<double> beam_chi, beam_zeta, beam_zdot, beam_ref;
   double *d_bchi, *d_bzeta, *d_bzdot, *d_bref, *d_G;
   // true-E coupling (true_e.cu): level-0 w, s of the operator application (zero ring), point face windows,
-  // CG vectors r and p, scalars, control words, CG iterations since creation, capture streams of the loops
+  // CG vectors r, p and q = K p, scalars, control words, CG iterations since creation, capture streams of the loops
   void *te_w, *te_s;
   void* d_te_pt;
-  double *d_te_r, *d_te_p, *d_te_scal;
+  double *d_te_r, *d_te_p, *d_te_q, *d_te_scal;
   int* d_te_ctl;
   unsigned long long* d_te_total;
   cudaStream_t te_stream[2];

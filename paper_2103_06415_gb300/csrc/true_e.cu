@@ -6,11 +6,14 @@
 // without forming the matrix.  The paper runs GMRES with one (C^T A C)^-1 per Krylov iteration (Sec. 3, the
 // bottleneck the sub-domain method removes); the operator is symmetric positive definite, so conjugate
 // gradients reach the same unique solution, also with one (C^T A C)^-1 per iteration.  One CG iteration:
-//   k_te_src  -- E^T p spread onto the faces and its curl, on the vertex box of Omega_0 grown by 3 cells
-//                (Omega_0 holds the range of motion, so the support never leaves the box);
+//   k_te_src   -- E^T p spread onto the faces and its curl, on the vertex box of Omega_0 grown by 3 cells
+//                 (Omega_0 holds the range of motion, so the support never leaves the box);
 //   the three sine-transform passes of the finest level with homogeneous boundary values (as the
-//                corrector);
-//   k_te_cg   -- E C s at the body points, the structural rank-one terms, the CG update (one CTA).
+//                 corrector);
+//   k_te_apply -- (ds/h^2) E C s at the body points (several CTAs);
+//   k_te_cg    -- the structural rank-one terms and the CG update (one CTA).
+// FP64 issues at a low rate on this part, so the point work is spread over 16 lanes per point and over
+// several CTAs, and reductions are combined by one warp.
 // The FSI and CG loops run on the device as CUDA-graph WHILE nodes whose conditions the kernels set (a step
 // needs no host round trip); eager steps read the same flags on the host after each iteration.  Every loop is
 // bounded by an iteration counter that the kernel setting its condition increments.
@@ -19,18 +22,23 @@
 
 namespace {
 
-constexpr int kThr = 512;  // threads of the one-CTA kernels
+constexpr int kThr = 256;            // one-CTA kernels (CG update, FSI update, step end)
+constexpr int kPtThr = 128;          // point kernels: 16 lanes per point, 8 points per CTA
+constexpr int kPtCta = kPtThr / 16;
+constexpr int kMaxB = 64;            // bodies per context
+constexpr int kSrcChunk = 64;        // selected points whose face contributions one source CTA stages at a time
+constexpr unsigned FULL = 0xffffffffu;
 
-// 4 x 4 face window of one body point for each velocity component: u faces (iu + d, ju + e) at
-// (x_{iu+d}, y_{ju+e+1/2}), v faces (iv + d, jv + e) at (x_{iv+d+1/2}, y_{jv+e}); weight wx[d] * wy[e].
+// 4 x 4 face windows of one body point: u faces (iu + d, ju + e) at (x_{iu+d}, y_{ju+e+1/2}) with weight
+// w[d] * w[4 + e]; v faces (iv + d, jv + e) at (x_{iv+d+1/2}, y_{jv+e}) with weight w[8 + d] * w[12 + e].
 struct TePoint {
   int iu, ju, iv, jv;
-  double wxu[4], wyu[4], wxv[4], wyv[4];
+  double w[16];
 };
 
 // control words
 enum { TC_CG_IT = 0, TC_CG_DONE, TC_FSI_IT, TC_FSI_DONE, TC_CG_STEP, TC_CG_LAST, TC_N };
-// scalars: 0 r.r, 1 threshold on r.r
+// scalars: r.r and the stopping threshold on r.r
 enum { TS_RR = 0, TS_THR, TS_N };
 
 struct TeArgs {
@@ -38,7 +46,8 @@ struct TeArgs {
   const void* ts;  // level-0 streamfunction of the operator application
   int fp64;
   long ps;
-  double x0, y0, h, dt, ds, U, V, tol, ktol, two_dt, four_dt2, kscale;  // kscale = ds / h^2
+  double x0, y0, h, inv_h, dt, ds, U, V, tol, ktol, two_dt, four_dt2;
+  double kscale_h;  // ds / h^3: (ds / h^2) E C with the 1/h of C
   int max_iters, kmax;
   int nb, nf, n_bodies;
   int i_lo, i_hi, j_lo, j_hi;  // Omega_0 vertex box: every body point must lie inside
@@ -48,7 +57,7 @@ struct TeArgs {
   const double* rpts;
   const double* rur;
   TePoint* pt;
-  double *f, *r, *p, *rhs, *sv;
+  double *f, *r, *p, *q, *rhs, *sv;
   double* scal;
   int* ctl;
   unsigned long long* cg_total;
@@ -64,16 +73,26 @@ __device__ __forceinline__ double load_s(const void* s, int fp64, long o) {
   return fp64 ? ((const double*)s)[o] : (double)((const float*)s)[o];
 }
 
-// deterministic block sum (every thread receives the result)
+// deterministic block sum, result in every thread (red: 33 doubles).  FP64 issues at a low rate on this
+// part, so the partials are combined by one warp, not by every thread.
 __device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();  // red may still be read after a previous call
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;
+  if (wid == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__device__ __forceinline__ double group16_sum(double v) {
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, 16);
+  return v;
 }
 
 // 3-point discrete delta in grid units (Sec. 2.2, reading R1); explicit roundings (no contraction).
@@ -88,188 +107,247 @@ __device__ double delta3(double r) {
   return 0.0;
 }
 
-// window of the faces offset (ox, oy) cells from the vertices, around the point at grid coordinates (X, Y)
-__device__ void face_window(double X, double Y, double ox, double oy, int* i0, int* j0, double* wx, double* wy) {
-  const int a = (int)floor(X - ox) - 1, b = (int)floor(Y - oy) - 1;
-  *i0 = a;
-  *j0 = b;
-  for (int d = 0; d < 4; ++d) {
-    wx[d] = delta3(__dsub_rn(__dadd_rn((double)(a + d), ox), X));
-    wy[d] = delta3(__dsub_rn(__dadd_rn((double)(b + d), oy), Y));
-  }
-}
-
 // ---------------------------------------------------------------------------------------------------------
-// Start of an FSI iteration: body points of the iterate, their face windows, S, the right-hand side
-// r^c(k) = E (C s* + q_inf) - u_rigid - S phi^(k) + S (r^theta(k) - (2/dt) r^phi(k) / J), and the CG start
-// from the current f.  On the first iteration of a step the structural terms of the step are set up.
-__global__ void __launch_bounds__(kThr) k_te_prep(TeArgs a) {
+// Start of an FSI iteration (8 points per CTA, 16 lanes per point): body points of the iterate, their face
+// windows and delta weights (one weight per lane), S, and the right-hand side
+//   r^c(k) = E (C s* + q_inf) - u_rigid - S phi^(k) + S (r^theta(k) - (2/dt) r^phi(k) / J).
+// Every CTA derives the structural terms of the step from the body state; CTA 0 stores them and starts the
+// CG solve from the current f.
+__global__ void __launch_bounds__(kPtThr) k_te_prep(TeArgs a) {
+  __shared__ double b_th[kMaxB], b_ph[kMaxB], b_jac[kMaxB], b_rphi[kMaxB], b_rth[kMaxB], b_sn[kMaxB], b_cs[kMaxB];
   const int tid = threadIdx.x, nb = a.nb;
-  if (a.ctl[TC_FSI_IT] == 0) {
-    for (int bi = tid; bi < a.n_bodies; bi += kThr) {
-      const BodyDev b = a.bodies[bi];
-      BodyState& s = a.st[bi];
-      if (b.type == FSI_BODY_TORSIONAL) {
-        const double dt = a.dt;
-        s.jac = 4.0 * b.inertia / (dt * dt) + 2.0 * b.damping / dt + b.stiffness;
-        s.r_phi = b.inertia * (4.0 * s.theta / (dt * dt) + 4.0 * s.phi / dt + s.phidot) +
-                  b.damping * (2.0 * s.theta / dt + s.phi);
-        s.r_theta = s.phi + 2.0 / dt * s.theta;
-      }
-      s.theta_k = s.theta;
-      s.phi_k = s.phi;
-      s.theta_p = s.theta;
-    }
-    __syncthreads();
-  }
-  for (int p = tid; p < nb; p += kThr) {
-    const int bi = a.point_body[p];
+  const bool first = a.ctl[TC_FSI_IT] == 0;
+  for (int bi = tid; bi < a.n_bodies; bi += kPtThr) {
     const BodyDev b = a.bodies[bi];
-    double x, y, svx = 0.0, svy = 0.0, ux = 0.0, uy = 0.0;
+    const BodyState s = a.st[bi];
+    double jac = 1.0, rphi = 0.0, rth = 0.0, th = 0.0, ph = 0.0;
     if (b.type == FSI_BODY_TORSIONAL) {
-      const BodyState s = a.st[bi];
-      double sn, cs;
-      sincos(b.theta0 + s.theta_k, &sn, &cs);
-      const double q = (double)(p - b.off) * a.ds;
-      x = __dadd_rn(b.hx, __dmul_rn(q, cs));
-      y = __dadd_rn(b.hy, __dmul_rn(q, sn));
-      svx = q * (-sn);
-      svy = q * cs;
-      const double rphik = s.r_phi - s.jac * s.theta_k;
-      const double rthk = s.r_theta - a.two_dt * s.theta_k + s.phi_k;
-      const double coef = rthk - a.two_dt * rphik / s.jac;
-      ux = svx * s.phi_k - svx * coef;
-      uy = svy * s.phi_k - svy * coef;
-    } else {
-      x = a.rpts[2 * p];
-      y = a.rpts[2 * p + 1];
-      ux = a.rur[2 * p];
-      uy = a.rur[2 * p + 1];
+      const double dt = a.dt;
+      jac = 4.0 * b.inertia / (dt * dt) + 2.0 * b.damping / dt + b.stiffness;
+      rphi = b.inertia * (4.0 * s.theta / (dt * dt) + 4.0 * s.phi / dt + s.phidot) +
+             b.damping * (2.0 * s.theta / dt + s.phi);
+      rth = s.phi + 2.0 / dt * s.theta;
+      th = first ? s.theta : s.theta_k;
+      ph = first ? s.phi : s.phi_k;
     }
-    double X = (x - a.x0) / a.h, Y = (y - a.y0) / a.h;
-    if (!(X >= (double)a.i_lo && X <= (double)a.i_hi && Y >= (double)a.j_lo && Y <= (double)a.j_hi)) {
-      dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
-      X = fmin(fmax(isfinite(X) ? X : (double)a.i_lo, (double)a.i_lo), (double)a.i_hi);
-      Y = fmin(fmax(isfinite(Y) ? Y : (double)a.j_lo, (double)a.j_lo), (double)a.j_hi);
+    b_th[bi] = th;
+    b_ph[bi] = ph;
+    b_jac[bi] = jac;
+    b_rphi[bi] = rphi;
+    b_rth[bi] = rth;
+    sincos(b.theta0 + th, &b_sn[bi], &b_cs[bi]);
+    if (blockIdx.x == 0 && first) {
+      BodyState& w = a.st[bi];
+      w.jac = jac;
+      w.kc = (2.0 * a.ds / a.dt) / jac;
+      w.r_phi = rphi;
+      w.r_theta = rth;
+      w.theta_k = s.theta;
+      w.phi_k = s.phi;
+      w.theta_p = s.theta;
     }
-    TePoint P;
-    face_window(X, Y, 0.0, 0.5, &P.iu, &P.ju, P.wxu, P.wyu);
-    face_window(X, Y, 0.5, 0.0, &P.iv, &P.jv, P.wxv, P.wyv);
-    a.pt[p] = P;
-    // E (C s* + q_inf): u = (s[J+1][I] - s[J][I]) / h + U on u faces, v = -(s[J][I+1] - s[J][I]) / h + V
-    double eu = 0.0, ev = 0.0;
-    for (int e = 0; e < 4; ++e)
-      for (int d = 0; d < 4; ++d) {
-        const long I = P.iu + d, J = P.ju + e;
-        const double u = (load_s(a.s0, a.fp64, (J + 1) * a.ps + I) - load_s(a.s0, a.fp64, J * a.ps + I)) / a.h + a.U;
-        eu = __dadd_rn(eu, __dmul_rn(__dmul_rn(P.wxu[d], P.wyu[e]), u));
-      }
-    for (int e = 0; e < 4; ++e)
-      for (int d = 0; d < 4; ++d) {
-        const long I = P.iv + d, J = P.jv + e;
-        const double v = -(load_s(a.s0, a.fp64, J * a.ps + I + 1) - load_s(a.s0, a.fp64, J * a.ps + I)) / a.h + a.V;
-        ev = __dadd_rn(ev, __dmul_rn(__dmul_rn(P.wxv[d], P.wyv[e]), v));
-      }
-    a.rhs[p] = eu - ux;
-    a.rhs[nb + p] = ev - uy;
-    a.sv[p] = svx;
-    a.sv[nb + p] = svy;
   }
-  for (int k = tid; k < a.nf; k += kThr) a.p[k] = a.f[k];  // the first application is K f (CG start)
-  if (tid == 0) {
-    a.ctl[TC_CG_IT] = 0;
-    a.ctl[TC_CG_DONE] = 0;
-    if (a.use_cond) cudaGraphSetConditional(a.h_cg, 1u);
+  __syncthreads();
+  const int l = tid & 15, d = l & 3, e = l >> 2;
+  const int p = blockIdx.x * kPtCta + (tid >> 4);
+  const bool act = p < nb;
+  const int pp = act ? p : nb - 1;
+  const int bi = a.point_body[pp];
+  const BodyDev b = a.bodies[bi];
+  double x, y, svx = 0.0, svy = 0.0, ux = 0.0, uy = 0.0;
+  if (b.type == FSI_BODY_TORSIONAL) {
+    const double sn = b_sn[bi], cs = b_cs[bi];
+    const double q = (double)(pp - b.off) * a.ds;
+    x = __dadd_rn(b.hx, __dmul_rn(q, cs));
+    y = __dadd_rn(b.hy, __dmul_rn(q, sn));
+    svx = q * (-sn);
+    svy = q * cs;
+    const double th_k = b_th[bi], ph_k = b_ph[bi];
+    const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
+    const double rthk = b_rth[bi] - a.two_dt * th_k + ph_k;
+    const double coef = rthk - a.two_dt * rphik / b_jac[bi];
+    ux = svx * ph_k - svx * coef;
+    uy = svy * ph_k - svy * coef;
+  } else {
+    x = a.rpts[2 * pp];
+    y = a.rpts[2 * pp + 1];
+    ux = a.rur[2 * pp];
+    uy = a.rur[2 * pp + 1];
+  }
+  double X = (x - a.x0) / a.h, Y = (y - a.y0) / a.h;
+  if (!(X >= (double)a.i_lo && X <= (double)a.i_hi && Y >= (double)a.j_lo && Y <= (double)a.j_hi)) {
+    if (act && l == 0) dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
+    X = fmin(fmax(isfinite(X) ? X : (double)a.i_lo, (double)a.i_lo), (double)a.i_hi);
+    Y = fmin(fmax(isfinite(Y) ? Y : (double)a.j_lo, (double)a.j_lo), (double)a.j_hi);
+  }
+  // windows: u faces offset (0, 1/2) from the vertices, v faces (1/2, 0)
+  const int iu = (int)floor(X) - 1, ju = (int)floor(Y - 0.5) - 1;
+  const int iv = (int)floor(X - 0.5) - 1, jv = (int)floor(Y) - 1;
+  // lane l evaluates weight l: 0-3 x of u, 4-7 y of u, 8-11 x of v, 12-15 y of v
+  const int k = l & 3, which = l >> 2;
+  double r;
+  if (which == 0) r = __dsub_rn((double)(iu + k), X);
+  else if (which == 1) r = __dsub_rn(__dadd_rn((double)(ju + k), 0.5), Y);
+  else if (which == 2) r = __dsub_rn(__dadd_rn((double)(iv + k), 0.5), X);
+  else r = __dsub_rn((double)(jv + k), Y);
+  const double wl = delta3(r);
+  const double wxu = __shfl_sync(FULL, wl, d, 16), wyu = __shfl_sync(FULL, wl, 4 + e, 16);
+  const double wxv = __shfl_sync(FULL, wl, 8 + d, 16), wyv = __shfl_sync(FULL, wl, 12 + e, 16);
+  // face (d, e) terms of E (C s* + q_inf): u = (s[J+1][I] - s[J][I]) / h + U, v = -(s[J][I+1] - s[J][I]) / h + V
+  const long Iu = iu + d, Ju = ju + e, Iv = iv + d, Jv = jv + e;
+  const double du = load_s(a.s0, a.fp64, (Ju + 1) * a.ps + Iu) - load_s(a.s0, a.fp64, Ju * a.ps + Iu);
+  const double dv = load_s(a.s0, a.fp64, Jv * a.ps + Iv + 1) - load_s(a.s0, a.fp64, Jv * a.ps + Iv);
+  const double eu = group16_sum(__dmul_rn(__dmul_rn(wxu, wyu), du * a.inv_h + a.U));
+  const double ev = group16_sum(__dmul_rn(__dmul_rn(wxv, wyv), -dv * a.inv_h + a.V));
+  if (act) {
+    TePoint* P = a.pt + p;
+    P->w[l] = wl;
+    if (l == 0) {
+      P->iu = iu;
+      P->ju = ju;
+      P->iv = iv;
+      P->jv = jv;
+      a.rhs[p] = eu - ux;
+      a.rhs[nb + p] = ev - uy;
+      a.sv[p] = svx;
+      a.sv[nb + p] = svy;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int m = tid; m < a.nf; m += kPtThr) a.p[m] = a.f[m];  // the first application is K f (CG start)
+    if (tid == 0) {
+      a.ctl[TC_CG_IT] = 0;
+      a.ctl[TC_CG_DONE] = 0;
+      if (a.use_cond) cudaGraphSetConditional(a.h_cg, 1u);
+    }
   }
 }
 
-// curl of E^T v (scaled by pre) at the interior vertices of the box [wi0, wi1] x [wj0, wj1]:
-// src(i, j) = pre ((Fv(i+1/2, j) - Fv(i-1/2, j)) / h - (Fu(i, j+1/2) - Fu(i, j-1/2)) / h), where the face
-// values F sum w f over the points in point order.  Threads of a 32 x 4 tile, one vertex each.
+// curl of E^T v (scaled by pre_h = pre / h) at the interior vertices of the box [wi0, wi1] x [wj0, wj1]:
+// src(i, j) = pre ((Fv(i+1/2, j) - Fv(i-1/2, j)) - (Fu(i, j+1/2) - Fu(i, j-1/2))) / h, the face values F summing
+// (weight * v) over the points in point order.  A CTA takes a 32 x 4 tile: it selects (in point order) the
+// points whose faces enter its curls, stages their 32 face contributions in chunks, and each thread sums
+// those of its vertex.
 template <typename T>
 __global__ void __launch_bounds__(128) k_te_src(T* __restrict__ src, long ps, int wi0, int wi1, int wj0, int wj1,
                                                 const TePoint* __restrict__ pt, const double* __restrict__ vec,
-                                                int nb, double h, double pre) {
+                                                int nb, double pre_h) {
   extern __shared__ __align__(16) unsigned char te_smem[];
-  TePoint* sp = reinterpret_cast<TePoint*>(te_smem);
-  double* sf = reinterpret_cast<double*>(sp + nb);
-  for (int k = threadIdx.x; k < nb; k += 128) sp[k] = pt[k];
-  for (int k = threadIdx.x; k < 2 * nb; k += 128) sf[k] = vec[k];
+  double* sc = reinterpret_cast<double*>(te_smem);          // [kSrcChunk][32] face contributions
+  int* si = reinterpret_cast<int*>(sc + kSrcChunk * 32);    // [nb][4] windows of the selected points
+  int* sp = si + 4 * nb;                                     // [nb] their point indices
+  __shared__ int wcount[4], n_sel;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ti0 = wi0 + (int)blockIdx.x * 32, tj0 = wj0 + (int)blockIdx.y * 4;
+  if (tid == 0) n_sel = 0;
   __syncthreads();
-  const int i = wi0 + (int)blockIdx.x * 32 + (threadIdx.x & 31);
-  const int j = wj0 + (int)blockIdx.y * 4 + (threadIdx.x >> 5);
-  if (i > wi1 || j > wj1) return;
-  double fun = 0.0, fus = 0.0, fve = 0.0, fvw = 0.0;
-  for (int q = 0; q < nb; ++q) {
-    const TePoint& P = sp[q];
-    const int du = i - P.iu;
-    if (du >= 0 && du < 4) {
-      const double fx = sf[q];
-      const int en = j - P.ju, es = j - 1 - P.ju;
-      if (en >= 0 && en < 4) fun = __dadd_rn(fun, __dmul_rn(__dmul_rn(P.wxu[du], P.wyu[en]), fx));
-      if (es >= 0 && es < 4) fus = __dadd_rn(fus, __dmul_rn(__dmul_rn(P.wxu[du], P.wyu[es]), fx));
+  // a point's faces enter the curls at vertices i in [iu - 1, iu + 4], j in [ju - 1, ju + 4] (superset)
+  for (int base = 0; base < nb; base += 128) {
+    const int p = base + tid;
+    int iu = 0, ju = 0;
+    bool take = false;
+    if (p < nb) {
+      iu = pt[p].iu;
+      ju = pt[p].ju;
+      take = iu - 1 <= ti0 + 31 && iu + 4 >= ti0 && ju - 1 <= tj0 + 3 && ju + 4 >= tj0;
     }
-    const int ev = j - P.jv;
-    if (ev >= 0 && ev < 4) {
-      const double fy = sf[nb + q];
-      const int de = i - P.iv, dw = i - 1 - P.iv;
-      if (de >= 0 && de < 4) fve = __dadd_rn(fve, __dmul_rn(__dmul_rn(P.wxv[de], P.wyv[ev]), fy));
-      if (dw >= 0 && dw < 4) fvw = __dadd_rn(fvw, __dmul_rn(__dmul_rn(P.wxv[dw], P.wyv[ev]), fy));
+    const unsigned m = __ballot_sync(FULL, take);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    int off = n_sel;
+    for (int w = 0; w < wid; ++w) off += wcount[w];
+    if (take) {
+      const int q = off + __popc(m & ((1u << lane) - 1u));
+      si[4 * q] = iu;
+      si[4 * q + 1] = ju;
+      si[4 * q + 2] = pt[p].iv;
+      si[4 * q + 3] = pt[p].jv;
+      sp[q] = p;
+    }
+    __syncthreads();
+    if (tid == 0) n_sel += wcount[0] + wcount[1] + wcount[2] + wcount[3];
+    __syncthreads();
+  }
+  const int ns = n_sel;
+  const int i = ti0 + lane, j = tj0 + wid;
+  double fun = 0.0, fus = 0.0, fve = 0.0, fvw = 0.0;
+  for (int c0 = 0; c0 < ns; c0 += kSrcChunk) {
+    const int nc = ns - c0 < kSrcChunk ? ns - c0 : kSrcChunk;
+    __syncthreads();  // the previous chunk's contributions have been read
+    for (int t = tid; t < 16 * nc; t += 128) {
+      const int qq = t >> 4, l = t & 15, d = l & 3, e = l >> 2;
+      const int p = sp[c0 + qq];
+      const double* w = pt[p].w;
+      sc[32 * qq + l] = __dmul_rn(__dmul_rn(w[d], w[4 + e]), vec[p]);             // u face (iu + d, ju + e)
+      sc[32 * qq + 16 + l] = __dmul_rn(__dmul_rn(w[8 + d], w[12 + e]), vec[nb + p]);  // v face (iv + d, jv + e)
+    }
+    __syncthreads();
+    for (int qq = 0; qq < nc; ++qq) {
+      const int* wv = si + 4 * (c0 + qq);
+      const double* cq = sc + 32 * qq;
+      const int du = i - wv[0];
+      if ((unsigned)du < 4u) {
+        const int en = j - wv[1], es = j - 1 - wv[1];
+        if ((unsigned)en < 4u) fun += cq[en * 4 + du];
+        if ((unsigned)es < 4u) fus += cq[es * 4 + du];
+      }
+      const int ev = j - wv[3];
+      if ((unsigned)ev < 4u) {
+        const int de = i - wv[2], dw = i - 1 - wv[2];
+        if ((unsigned)de < 4u) fve += cq[16 + ev * 4 + de];
+        if ((unsigned)dw < 4u) fvw += cq[16 + ev * 4 + dw];
+      }
     }
   }
-  const double c = __dsub_rn(__ddiv_rn(__dsub_rn(fve, fvw), h), __ddiv_rn(__dsub_rn(fun, fus), h));
-  src[(long)(j - 1) * ps + (i - 1)] = T(__dmul_rn(pre, c));
+  if (i <= wi1 && j <= wj1) src[(long)(j - 1) * ps + (i - 1)] = T(pre_h * ((fve - fvw) - (fun - fus)));
 }
 
-// One CG iteration after the operator application: q = (ds/h^2) E C s_t + sum_b kc_b S_b (S_b . p) with
-// p the applied vector, then (iteration 0) r = rhs - q, p = r, or (later) the CG update of f, r and p.
+// E C s_t at the body points (8 points per CTA, 16 lanes per point): q = (ds / h^3) sum w (s differences).
+__global__ void __launch_bounds__(kPtThr) k_te_apply(TeArgs a) {
+  const int tid = threadIdx.x, nb = a.nb, l = tid & 15, d = l & 3, e = l >> 2;
+  const int p = blockIdx.x * kPtCta + (tid >> 4);
+  const int pp = p < nb ? p : nb - 1;
+  const TePoint* P = a.pt + pp;
+  const long Iu = P->iu + d, Ju = P->ju + e, Iv = P->iv + d, Jv = P->jv + e;
+  const double du = load_s(a.ts, a.fp64, (Ju + 1) * a.ps + Iu) - load_s(a.ts, a.fp64, Ju * a.ps + Iu);
+  const double dv = load_s(a.ts, a.fp64, Jv * a.ps + Iv + 1) - load_s(a.ts, a.fp64, Jv * a.ps + Iv);
+  const double qu = group16_sum((P->w[d] * P->w[4 + e]) * du);
+  const double qv = group16_sum(-(P->w[8 + d] * P->w[12 + e]) * dv);
+  if (p < nb && l == 0) {
+    a.q[p] = a.kscale_h * qu;
+    a.q[nb + p] = a.kscale_h * qv;
+  }
+}
+
+// One CG iteration after the operator application: q += sum_b kc_b S_b (S_b . p) (the structural rank-one
+// terms, kc = (2 ds/dt)/J), then (iteration 0) r = rhs - q, p = r, or (later) the CG update of f, r and p.
 // Sets the CG loop condition on every path.
 __global__ void __launch_bounds__(kThr) k_te_cg(TeArgs a) {
-  extern __shared__ double q[];  // [nf]
-  __shared__ double red[32];
+  __shared__ double red[33];
+  __shared__ double s_div;
   const int tid = threadIdx.x, nb = a.nb, nf = a.nf;
   const int it = a.ctl[TC_CG_IT];
-  for (int p = tid; p < nb; p += kThr) {
-    const TePoint P = a.pt[p];
-    double qu = 0.0, qv = 0.0;
-    for (int e = 0; e < 4; ++e)
-      for (int d = 0; d < 4; ++d) {
-        const long I = P.iu + d, J = P.ju + e;
-        const double u = (load_s(a.ts, a.fp64, (J + 1) * a.ps + I) - load_s(a.ts, a.fp64, J * a.ps + I)) / a.h;
-        qu = __dadd_rn(qu, __dmul_rn(__dmul_rn(P.wxu[d], P.wyu[e]), u));
-      }
-    for (int e = 0; e < 4; ++e)
-      for (int d = 0; d < 4; ++d) {
-        const long I = P.iv + d, J = P.jv + e;
-        const double v = -(load_s(a.ts, a.fp64, J * a.ps + I + 1) - load_s(a.ts, a.fp64, J * a.ps + I)) / a.h;
-        qv = __dadd_rn(qv, __dmul_rn(__dmul_rn(P.wxv[d], P.wyv[e]), v));
-      }
-    q[p] = a.kscale * qu;
-    q[nb + p] = a.kscale * qv;
-  }
-  __syncthreads();
-  for (int bi = 0; bi < a.n_bodies; ++bi) {  // structural rank-one terms (2 ds/dt)/J S S^T p
+  for (int bi = 0; bi < a.n_bodies; ++bi) {
     const BodyDev b = a.bodies[bi];
     if (b.type != FSI_BODY_TORSIONAL) continue;
     double part = 0.0;
-    for (int p = b.off + tid; p < b.off + b.n; p += kThr) part += a.sv[p] * a.p[p] + a.sv[nb + p] * a.p[nb + p];
-    const double dot = block_sum(part, red);
-    const double kc = (2.0 * a.ds / a.dt) / a.st[bi].jac;
-    for (int p = b.off + tid; p < b.off + b.n; p += kThr) {
-      q[p] += kc * a.sv[p] * dot;
-      q[nb + p] += kc * a.sv[nb + p] * dot;
+    for (int m = b.off + tid; m < b.off + b.n; m += kThr) part += a.sv[m] * a.p[m] + a.sv[nb + m] * a.p[nb + m];
+    const double dot = block_sum(part, red) * a.st[bi].kc;
+    for (int m = b.off + tid; m < b.off + b.n; m += kThr) {
+      a.q[m] += a.sv[m] * dot;
+      a.q[nb + m] += a.sv[nb + m] * dot;
     }
-    __syncthreads();
   }
+  __syncthreads();
   bool done;
   if (it == 0) {
     double prr = 0.0, pbb = 0.0;
-    for (int k = tid; k < nf; k += kThr) {
-      const double rk = a.rhs[k] - q[k];
-      a.r[k] = rk;
-      a.p[k] = rk;
+    for (int m = tid; m < nf; m += kThr) {
+      const double rk = a.rhs[m] - a.q[m];
+      a.r[m] = rk;
+      a.p[m] = rk;
       prr += rk * rk;
-      pbb += a.rhs[k] * a.rhs[k];
+      pbb += a.rhs[m] * a.rhs[m];
     }
     const double rr = block_sum(prr, red), bb = block_sum(pbb, red);
     const double thr = a.ktol * a.ktol * (bb > 0.0 ? bb : rr);
@@ -280,20 +358,24 @@ __global__ void __launch_bounds__(kThr) k_te_cg(TeArgs a) {
     }
   } else {
     double ppq = 0.0;
-    for (int k = tid; k < nf; k += kThr) ppq += a.p[k] * q[k];
+    for (int m = tid; m < nf; m += kThr) ppq += a.p[m] * a.q[m];
     const double pq = block_sum(ppq, red);
     const double rr = a.scal[TS_RR];
-    const double alpha = rr / pq;
+    if (tid == 0) s_div = rr / pq;
+    __syncthreads();
+    const double alpha = s_div;
     double prr = 0.0;
-    for (int k = tid; k < nf; k += kThr) {
-      a.f[k] += alpha * a.p[k];
-      const double rk = a.r[k] - alpha * q[k];
-      a.r[k] = rk;
+    for (int m = tid; m < nf; m += kThr) {
+      a.f[m] += alpha * a.p[m];
+      const double rk = a.r[m] - alpha * a.q[m];
+      a.r[m] = rk;
       prr += rk * rk;
     }
     const double rn = block_sum(prr, red);
-    const double beta = rn / rr;
-    for (int k = tid; k < nf; k += kThr) a.p[k] = a.r[k] + beta * a.p[k];
+    if (tid == 0) s_div = rn / rr;
+    __syncthreads();
+    const double beta = s_div;
+    for (int m = tid; m < nf; m += kThr) a.p[m] = a.r[m] + beta * a.p[m];
     done = !(pq > 0.0) || !(rn > a.scal[TS_THR]);
     __syncthreads();
     if (tid == 0) a.scal[TS_RR] = rn;
@@ -314,7 +396,7 @@ __global__ void __launch_bounds__(kThr) k_te_cg(TeArgs a) {
 // End of an FSI iteration (Eq. dtheta2): dtheta = (r^phi(k) + ds S f) / J for every torsional body,
 // convergence on max |dtheta|; sets the FSI loop condition on every path.
 __global__ void __launch_bounds__(kThr) k_te_post(TeArgs a) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int tid = threadIdx.x, nb = a.nb;
   double dmax = 0.0;
   bool finite = true;
@@ -322,7 +404,7 @@ __global__ void __launch_bounds__(kThr) k_te_post(TeArgs a) {
     const BodyDev b = a.bodies[bi];
     if (b.type != FSI_BODY_TORSIONAL) continue;
     double part = 0.0;
-    for (int p = b.off + tid; p < b.off + b.n; p += kThr) part += a.sv[p] * a.f[p] + a.sv[nb + p] * a.f[nb + p];
+    for (int m = b.off + tid; m < b.off + b.n; m += kThr) part += a.sv[m] * a.f[m] + a.sv[nb + m] * a.f[nb + m];
     const double sf = block_sum(part, red);
     BodyState& s = a.st[bi];
     const double dth = (s.r_phi - s.jac * s.theta_k + a.ds * sf) / s.jac;
@@ -350,7 +432,7 @@ __global__ void __launch_bounds__(kThr) k_te_post(TeArgs a) {
 
 // Newmark update of the torsional bodies, forces, moment about the hinge (S of the final solve), history.
 __global__ void __launch_bounds__(kThr) k_te_finish(TeArgs a) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int tid = threadIdx.x, nb = a.nb;
   const int slot = a.ctrl[2] % a.hist_cap;
   const int iters = a.ctl[TC_FSI_IT];
@@ -359,9 +441,9 @@ __global__ void __launch_bounds__(kThr) k_te_finish(TeArgs a) {
     double sn = 0.0, cs = 0.0;
     if (b.type == FSI_BODY_TORSIONAL) sincos(b.theta0 + a.st[bi].theta_p, &sn, &cs);
     double px = 0.0, py = 0.0, pm = 0.0;
-    for (int p = b.off + tid; p < b.off + b.n; p += kThr) {
-      const double fxp = a.f[p], fyp = a.f[nb + p];
-      const double q = (double)(p - b.off) * a.ds;
+    for (int m = b.off + tid; m < b.off + b.n; m += kThr) {
+      const double fxp = a.f[m], fyp = a.f[nb + m];
+      const double q = (double)(m - b.off) * a.ds;
       px += fxp;
       py += fyp;
       pm += q * (-sn) * fxp + q * cs * fyp;
@@ -410,6 +492,7 @@ TeArgs te_args(fsi_ctx* c) {
   a.x0 = c->g.x0;
   a.y0 = c->g.y0;
   a.h = c->g.h;
+  a.inv_h = 1.0 / c->g.h;
   a.dt = c->g.dt;
   a.ds = c->ds;
   a.U = c->g.uinf[0];
@@ -418,7 +501,7 @@ TeArgs te_args(fsi_ctx* c) {
   a.ktol = c->x.krylov_tol;
   a.two_dt = 2.0 / c->g.dt;
   a.four_dt2 = 4.0 / (c->g.dt * c->g.dt);
-  a.kscale = c->ds / (c->g.h * c->g.h);
+  a.kscale_h = c->ds / (c->g.h * c->g.h * c->g.h);
   a.max_iters = c->x.max_iters;
   a.kmax = c->x.krylov_max_iters;
   a.nb = c->nb;
@@ -437,6 +520,7 @@ TeArgs te_args(fsi_ctx* c) {
   a.f = c->d_f;
   a.r = c->d_te_r;
   a.p = c->d_te_p;
+  a.q = c->d_te_q;
   a.rhs = c->d_rhs;
   a.sv = c->d_sv;
   a.scal = c->d_te_scal;
@@ -449,6 +533,8 @@ TeArgs te_args(fsi_ctx* c) {
   return a;
 }
 
+size_t src_smem(int nb) { return (size_t)kSrcChunk * 32 * sizeof(double) + (size_t)nb * 5 * sizeof(int); }
+
 // curl of E^T vec (times pre) into the source buffer; the vertex box is the interior part of Omega_0 grown by
 // 3 cells, which holds the support of every point inside Omega_0
 template <typename T>
@@ -456,9 +542,8 @@ fsi_status launch_src(fsi_ctx* c, const double* vec, double pre) {
   const int wi0 = c->i_lo - 3 < 1 ? 1 : c->i_lo - 3, wi1 = c->i_hi + 3 > c->nx - 1 ? c->nx - 1 : c->i_hi + 3;
   const int wj0 = c->j_lo - 3 < 1 ? 1 : c->j_lo - 3, wj1 = c->j_hi + 3 > c->ny - 1 ? c->ny - 1 : c->j_hi + 3;
   const dim3 grid((wi1 - wi0 + 32) / 32, (wj1 - wj0 + 4) / 4);
-  const size_t sm = (size_t)c->nb * (sizeof(TePoint) + 2 * sizeof(double));
-  k_te_src<T><<<grid, 128, sm, c->stream>>>((T*)c->src, c->ps, wi0, wi1, wj0, wj1, (const TePoint*)c->d_te_pt, vec,
-                                            c->nb, c->g.h, pre);
+  k_te_src<T><<<grid, 128, src_smem(c->nb), c->stream>>>((T*)c->src, c->ps, wi0, wi1, wj0, wj1,
+                                                           (const TePoint*)c->d_te_pt, vec, c->nb, pre / c->g.h);
   FSI_CUDA_TRY(cudaGetLastError());
   c->launches_per_step += 1;
   return FSI_OK;
@@ -468,20 +553,29 @@ fsi_status launch_src_any(fsi_ctx* c, const double* vec, double pre) {
   return c->prec == FSI_PREC_FP64 ? launch_src<double>(c, vec, pre) : launch_src<float>(c, vec, pre);
 }
 
-fsi_status launch_one(fsi_ctx* c, void (*k)(TeArgs), const TeArgs& a, size_t smem) {
-  k<<<1, kThr, smem, c->stream>>>(a);
+fsi_status launch_one(fsi_ctx* c, void (*k)(TeArgs), const TeArgs& a) {
+  k<<<1, kThr, 0, c->stream>>>(a);
   FSI_CUDA_TRY(cudaGetLastError());
   c->launches_per_step += 1;
   return FSI_OK;
 }
 
-// one CG iteration: operator application to p, then the update
+fsi_status launch_points(fsi_ctx* c, void (*k)(TeArgs), const TeArgs& a) {
+  k<<<(c->nb + kPtCta - 1) / kPtCta, kPtThr, 0, c->stream>>>(a);
+  FSI_CUDA_TRY(cudaGetLastError());
+  c->launches_per_step += 1;
+  return FSI_OK;
+}
+
+// one CG iteration: operator application to p (source, the three passes, interpolation), then the update
 fsi_status cg_iteration(fsi_ctx* c, const TeArgs& a) {
   fsi_status st = launch_src_any(c, c->d_te_p, 1.0);
   if (st != FSI_OK) return st;
   st = launch_level_solve(c, 0, c->src, c->te_w, c->te_s, 0, 0);
   if (st != FSI_OK) return st;
-  return launch_one(c, k_te_cg, a, (size_t)c->nf * sizeof(double));
+  st = launch_points(c, k_te_apply, a);
+  if (st != FSI_OK) return st;
+  return launch_one(c, k_te_cg, a);
 }
 
 fsi_status read_flag(fsi_ctx* c, int which, int* v) {
@@ -534,7 +628,7 @@ fsi_status capture_while(fsi_ctx* c, cudaStream_t inner, cudaGraphConditionalHan
 
 fsi_status fsi_loop_eager(fsi_ctx* c, const TeArgs& a) {
   for (int it = 0; it < c->x.max_iters; ++it) {
-    fsi_status st = launch_one(c, k_te_prep, a, 0);
+    fsi_status st = launch_points(c, k_te_prep, a);
     if (st != FSI_OK) return st;
     for (int k = 0; k < c->x.krylov_max_iters; ++k) {
       st = cg_iteration(c, a);
@@ -544,7 +638,7 @@ fsi_status fsi_loop_eager(fsi_ctx* c, const TeArgs& a) {
       if (st != FSI_OK) return st;
       if (done) break;
     }
-    st = launch_one(c, k_te_post, a, 0);
+    st = launch_one(c, k_te_post, a);
     if (st != FSI_OK) return st;
     int done = 0;
     st = read_flag(c, TC_FSI_DONE, &done);
@@ -561,11 +655,11 @@ fsi_status fsi_loop_graph(fsi_ctx* c, TeArgs& a) {
   return capture_while(c, c->te_stream[0], a.h_fsi, [&]() -> fsi_status {
     fsi_status s = new_handle(c, &a.h_cg);  // on the FSI loop's body graph, before prep (which sets it)
     if (s != FSI_OK) return s;
-    s = launch_one(c, k_te_prep, a, 0);
+    s = launch_points(c, k_te_prep, a);
     if (s != FSI_OK) return s;
     s = capture_while(c, c->te_stream[1], a.h_cg, [&]() -> fsi_status { return cg_iteration(c, a); });
     if (s != FSI_OK) return s;
-    return launch_one(c, k_te_post, a, 0);
+    return launch_one(c, k_te_post, a);
   });
 }
 
@@ -585,16 +679,14 @@ fsi_status launch_true_e(fsi_ctx* c, int capture) {
   if (st != FSI_OK) return st;
   st = launch_level_solve(c, 0, c->src, c->w_all, c->s_all, 0, 1);
   if (st != FSI_OK) return st;
-  return launch_one(c, k_te_finish, a, 0);
+  return launch_one(c, k_te_finish, a);
 }
 
-// kernel attributes (dynamic shared memory of the source and CG kernels for nb points)
+// kernel attributes (dynamic shared memory of the source kernel for nb points)
 fsi_status true_e_setup(fsi_ctx* c) {
-  const int src_sm = (int)((size_t)c->nb * (sizeof(TePoint) + 2 * sizeof(double)));
-  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, src_sm));
-  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, src_sm));
-  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_cg, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)c->nf * sizeof(double))));
+  const int sm = (int)src_smem(c->nb);
+  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   return FSI_OK;
 }
 

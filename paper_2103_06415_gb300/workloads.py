@@ -8,6 +8,7 @@ Configurations (their readings are listed in the design doc):
 * ``plate_128``  -- single level 128x128 cells on [-1,3]x[-2,2] (h = 1/32), Re 100, dt 0.002, one rigid
   flat plate of chord 1 hinged at its leading edge (0,0) on a torsional spring (inertia 1, stiffness 0.5,
   no damping), initial angle 20 deg, 33 points at ds = h; Omega_0 = [-1.2,1.2]^2.
+* ``plate_128_ds2h`` -- plate_128 with 17 points at ds = 2h (the paper's body spacing).
 * ``flag_512x256_3lvl`` -- 3 nested levels of 512x256 cells, finest h = 1/100 on [-1,4.12]x[-1.28,1.28],
   Re 200, dt 5e-4; body: a flag of length 1 clamped at (0,0) along +x, 101 points (100 beam elements at
   ds = h), mass ratio 0.1, bending stiffness 1e-3, stretching stiffness 1e3, initial tip slope 0.1 rad;
@@ -28,6 +29,16 @@ def plate_128():
         bodies=[dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=33, inertia=1.0, damping=0.0,
                      stiffness=0.5, theta=np.deg2rad(20.0))],
         ds=1.0 / 32)
+
+
+def plate_128_ds2h():
+    """plate_128 with the body points at twice the grid spacing, the paper's choice for its experiments
+    (Sec. 5): 17 points at ds = 2h = 1/16 on the same chord."""
+    w = plate_128()
+    w["name"] = "plate_128_ds2h"
+    w["bodies"][0]["n_pts"] = 17
+    w["ds"] = 2.0 / 32
+    return w
 
 
 def flag_512x256_3lvl():

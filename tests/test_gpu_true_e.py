@@ -116,10 +116,11 @@ def test_true_e_fp32_fluid_vs_fp64(lib):
 
 
 def test_true_e_close_to_subdomain_on_plate_128(lib):
-    """Sec. 5.1 / Table eldgerror: the sub-domain approximation stays within about 2 % of the true E in the
-    deflection angle (relative L2 error over the run, Eq. errortheta) once the impulsive start has passed."""
+    """Sec. 5.1 / Table eldgerror: the sub-domain approximation stays within 2 % of the true E in the
+    deflection angle and the lift (relative L2 error, Eq. errortheta) once the impulsive start has passed
+    (steps 500-1500 of plate_128, t = 1-3)."""
     w = wl.plate_128()
-    n = 300
+    n = 1500
     hist = []
     for coupling in (0, 1):
         ctx = gpu_context(w, coupling=coupling)
@@ -127,9 +128,10 @@ def test_true_e_close_to_subdomain_on_plate_128(lib):
         hist.append(ctx.history(0))
         ctx.close()
     sub, tru = hist
-    th = slice(100, n)
-    err_theta = np.linalg.norm(sub[th, 3] - tru[th, 3]) / np.linalg.norm(tru[th, 3])
-    assert err_theta < 0.02, err_theta
+    win = slice(500, n)
+    for k, bound in ((3, 0.02), (1, 0.02)):                 # theta, lift
+        err = np.linalg.norm(sub[win, k] - tru[win, k]) / np.linalg.norm(tru[win, k])
+        assert err < bound, (k, err)
     assert np.all(tru[:, 5] <= 6)
 
 
