@@ -20,10 +20,12 @@ Module map
               (Eqs. predictor2-corrector2, Algorithm 2, App. A)
   beam.py  -- deformable flag: corotational Euler-Bernoulli beam, lumped mass,
               trapezoidal Newmark (Sec. 2.1 Eq. beam, App. A)
+  kinematics.py -- prescribed heave/pitch of a driven plate and the passive plate hinged to it
+              (Sec. 5.1, Eq. newtonseldg)
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 except the multidomain level coupling, which is only pinned loosely (Lamb-Oseen
 convergence); see the header of ``grid.py``.
 """
 
-from . import grid, ib, fsi, beam  # noqa: F401
+from . import grid, ib, fsi, beam, kinematics  # noqa: F401

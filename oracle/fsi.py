@@ -48,6 +48,14 @@ class TorsionalBody:
         # reading R11: f_0 = 0, g_t = 0, so the initial acceleration balances the spring and damper
         self.phidot = (-self.stiffness * self.theta - self.damping * self.phi) / self.inertia
 
+    def g(self, theta):
+        """Moment of body forces (g_t of Eq. newtons): zero for a plate on a fixed hinge (reading R17)."""
+        return 0.0
+
+    def u_known(self, theta):
+        """Point velocities apart from theta' S: zero on a fixed hinge."""
+        return 0.0, 0.0
+
     def points(self, theta):
         j = np.arange(self.n_pts, dtype=np.float64) * self.ds
         a = self.theta0 + theta
@@ -125,6 +133,7 @@ class Sim:
         self.history = []
         self.last_p = None
         self.last_svec = {}
+        self.t = 0.0                          # time of the current state (bodies with kinematics)
 
     # -- B0 columns, computed on first use and cached (Eq. action) ---------------------
 
@@ -170,6 +179,9 @@ class Sim:
 
     def fsi(self):
         lev, sd, dt, ds, nb = self.levels[0], self.sd, self.dt, self.ds, self.nb
+        for b in self.bodies:                       # prescribed kinematics at t_{n+1}
+            if hasattr(b, "at_time"):
+                b.at_time(self.t + dt)
         u, v = grid.faces_from_s(self.s[0], lev)
         e0q = sd.e0(u + self.uinf[0], v + self.uinf[1]) if self.coupling != "true" else None  # E0 (C s* + q_inf)
         offs = self._body_offsets()
@@ -220,8 +232,11 @@ class Sim:
                 sv[o:o + b.n_pts] = b.q() * rx
                 sv[nb + o:nb + o + b.n_pts] = b.q() * ry
                 svec[id(b)] = sv
+                ukx, uky = b.u_known(th)                                 # moving hinge (reading R20)
+                rhs[o:o + b.n_pts] -= ukx
+                rhs[nb + o:nb + o + b.n_pts] -= uky
                 jac = b.jac(dt)
-                r_phi = self._r_phi[id(b)] - jac * th                    # r^{phidot}(k)
+                r_phi = self._r_phi[id(b)] + b.g(th) - jac * th          # r^{phidot}(k), g at the iterate
                 r_theta = self._r_theta[id(b)] - 2.0 / dt * th + ph      # r^{theta}(k)
                 kmat += (2.0 * ds / dt) / jac * np.outer(sv, sv)
                 rhs -= sv * ph                                           # r^c(k) = R^T Q^T phi^(k)
@@ -238,7 +253,7 @@ class Sim:
                     continue
                 th = state_k[id(b)]
                 jac = b.jac(dt)
-                dth = (self._r_phi[id(b)] - jac * th + ds * svec[id(b)] @ f) / jac   # Eq. dtheta2
+                dth = (self._r_phi[id(b)] + b.g(th) - jac * th + ds * svec[id(b)] @ f) / jac   # Eq. dtheta2
                 state_k[id(b)] = th + dth
                 rate_k[id(b)] = 2.0 / dt * state_k[id(b)] - self._r_theta[id(b)]
                 dmax = max(dmax, abs(dth))
@@ -304,4 +319,5 @@ class Sim:
             rec["bodies"].append({"fx": fx, "fy": fy, "moment": mom,
                                   "theta": getattr(b, "theta", 0.0), "phi": getattr(b, "phi", 0.0)})
         self.history.append(rec)
+        self.t += dt
         return rec

@@ -9,6 +9,8 @@ Configurations (their readings are listed in the design doc):
   flat plate of chord 1 hinged at its leading edge (0,0) on a torsional spring (inertia 1, stiffness 0.5,
   no damping), initial angle 20 deg, 33 points at ds = h; Omega_0 = [-1.2,1.2]^2.
 * ``plate_128_ds2h`` -- plate_128 with 17 points at ds = 2h (the paper's body spacing).
+* ``e1_flapping`` -- the flapping torsionally connected plates of Sec. 5.1 (cases 1, 2 of Table kineparams)
+  on 5 levels of 512 x 512; ``small_flapping`` the same pair on a 64 x 64 grid.
 * ``flag_512x256_3lvl`` -- 3 nested levels of 512x256 cells, finest h = 1/100 on [-1,4.12]x[-1.28,1.28],
   Re 200, dt 5e-4; body: a flag of length 1 clamped at (0,0) along +x, 101 points (100 beam elements at
   ds = h), mass ratio 0.1, bending stiffness 1e-3, stretching stiffness 1e3, initial tip slope 0.1 rad;
@@ -56,6 +58,48 @@ def flag_512x256_3lvl_torsional():
     w["bodies"] = [dict(kind="torsional", hinge=(0.0, 0.0), theta0=0.0, n_pts=101, inertia=0.1 / 3.0, damping=0.0,
                         stiffness=1e-3, theta=0.1)]
     return w
+
+
+def _flapping_pair(n_pts, ds, a0, beta, sigma_t, sigma_r, theta=0.0):
+    """Driven plate (reference point at the origin, from 0.5 above it to the hinge 0.55 below it at
+    alpha1 = 0) and the passive plate hinged at its end (Sec. 5.1): both 1.05 long, n_pts - 1 segments of
+    ds.  The hinge point is kept once, on the passive plate (two coincident points would make two rows of
+    the interpolation equal and the small system singular), so the driven plate has n_pts - 1 points; passive plate of
+    mass pi/4 (density ratio 5 for the 5:1 ellipse of unit chord), moment of inertia 0.2886 about the
+    hinge, centre of mass 0.55 from the hinge, spring 456, damper 3.95 (all made dimensionless with
+    the flapping frequency f and the chord)."""
+    return [dict(kind="driven", ref=(0.0, 0.0), s_lo=-0.5, n_pts=n_pts - 1, a0=a0, beta=beta, sigma_t=sigma_t,
+                 sigma_r=sigma_r, freq=1.0),
+            dict(kind="hinged", driver=0, l1=0.55, n_pts=n_pts, inertia=0.2886, damping=3.95, stiffness=456.0,
+                 mass=np.pi / 4.0, l2=0.55, theta=theta)]
+
+
+def e1_flapping(case=1):
+    """Flapping of torsionally connected plates (Sec. 5.1, Table kineparams): A0 = 1.4, beta = pi/4,
+    sigma_t = sigma_r = 3.770 (case 1) or 0.628 (case 2), Re_r = 100, so Re = f c^2 / nu
+    = Re_r tanh(sigma_r) / (2 pi beta sigma_r); dt = 0.00489 tau_r with tau_r = tanh(sigma_r) / (2 pi beta
+    sigma_r) periods; hovering (no free stream).  Five levels of 512 x 512 cells over the paper's finest
+    domain [-3.15, 3.15] x [-4.65, 1.65] (h = 0.0123; the paper's 600 x 600 at 0.0105 is not a power of
+    two); Omega_0 = [-1.89, 1.89] x [-1.66, 0.65]; plates at ds = 1.05/43 (about 2h, the paper's body
+    spacing): 43 driven points and 44 passive points (the hinge point on the passive plate)."""
+    sig = 3.770 if case == 1 else 0.628
+    beta = np.pi / 4.0
+    tau_r = np.tanh(sig) / (2.0 * np.pi * beta * sig)
+    h = 6.3 / 512
+    return dict(name="e1_flapping_case%d" % case, nx=512, ny=512, n_levels=5, x0=-3.15, y0=-4.65, h=h,
+                re=100.0 * tau_r, dt=0.00489 * tau_r, uinf=(0.0, 0.0), steps=int(round(1.0 / (0.00489 * tau_r))),
+                sd_box=(-1.89, 1.89, -1.66, 0.65), bodies=_flapping_pair(44, 1.05 / 43, 1.4, beta, sig, sig),
+                ds=1.05 / 43, l1=0.55)
+
+
+def small_flapping(a0=1.4, beta=np.pi / 4.0, sigma=0.628, dt=0.004):
+    """The flapping pair on a 64 x 64 grid (h = 1/16) the oracle runs in seconds: 16 driven and 17 passive
+    points."""
+    h = 1.0 / 16
+    tau_r = np.tanh(sigma) / (2.0 * np.pi * np.pi / 4.0 * sigma)
+    return dict(name="small_flapping", nx=64, ny=64, n_levels=1, x0=-2.0, y0=-2.75, h=h, re=100.0 * tau_r, dt=dt,
+                uinf=(0.0, 0.0), steps=10, sd_box=(-1.6, 1.6, -2.0, 0.7),
+                bodies=_flapping_pair(17, 1.05 / 16, a0, beta, sigma, sigma), ds=1.05 / 16, l1=0.55)
 
 
 def b0_1024():

@@ -7,9 +7,16 @@ from oracle import fsi as ofsi
 
 
 def oracle_sim(w, **kw):
+    from oracle import kinematics as okin
     bodies = []
     for b in w["bodies"]:
-        if b["kind"] == "torsional":
+        if b["kind"] == "driven":
+            kin = okin.FlappingKinematics(b["a0"], b["beta"], b["sigma_t"], b["sigma_r"], b["freq"])
+            bodies.append(okin.DrivenPlate(b["ref"], b["s_lo"], b["n_pts"], w["ds"], kin))
+        elif b["kind"] == "hinged":
+            bodies.append(okin.HingedPlate(bodies[b["driver"]], b["l1"], b["n_pts"], w["ds"], b["inertia"],
+                                           b["damping"], b["stiffness"], b["mass"], b["l2"], b["theta"]))
+        elif b["kind"] == "torsional":
             bodies.append(ofsi.TorsionalBody(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"],
                                              b["stiffness"], b["theta"]))
         elif b["kind"] == "deformable":
