@@ -52,7 +52,7 @@ typedef enum {
                         force reductions stay in double */
 } fsi_precision;
 
-typedef enum { FSI_BODY_RIGID = 0, FSI_BODY_TORSIONAL = 1, FSI_BODY_DEFORMABLE = 2 } fsi_body_type;
+typedef enum { FSI_BODY_RIGID = 0, FSI_BODY_TORSIONAL = 1, FSI_BODY_DEFORMABLE = 2, FSI_BODY_DRIVEN = 3 } fsi_body_type;
 
 /* Fluid grid (Sec. 2.2; multidomain of Sec. 5).  Level 0 is the finest: nx x ny cells of spacing h with
  * lower-left corner (x0, y0).  Level g has the same cell counts, spacing 2^g h and the same centre.
@@ -110,6 +110,18 @@ typedef struct {
  * inextensible shape with slope angle theta_init*(2 s/L - s^2/L^2) along its length L; phi_init must be 0.
  * For this type fsi_get_deflection and history fields 3, 4 report the tip displacement normal to the
  * undeformed flag and its rate.  n_pts >= 2.
+ * DRIVEN (Sec. 5.1): a rigid plate with prescribed heave and pitch.  hinge = its reference point (the pitch
+ * axis); at time t it is displaced by (X1(t), 0) and the plate lies along (sin, -cos)(alpha1(t)) (straight
+ * down at alpha1 = 0), points j = 0..n_pts-1 at s_lo + j*ds along it.  kinematics = {A0, beta, sigma_t,
+ * sigma_r, f}: X1 = (A0/2) G_t(f t)/max G_t C(f t), alpha1 = -beta G_r(f t)/max G_r with
+ * G_t(tau) = int_0^tau tanh(sigma_t cos(2 pi u)) du, G_r = tanh(sigma_r cos(2 pi tau)),
+ * C(tau) = (tanh(8 tau - 2) + tanh 2)/(1 + tanh 2).  A0 >= 0, beta finite, sigma_t, sigma_r, f > 0.
+ * A TORSIONAL body with driver = k > 0 is hinged on the DRIVEN body with id k - 1 (added before it), at
+ * hinge_offset (L1) along that plate from its reference point; its points lie along the driven plate's
+ * direction turned by theta (theta0 must be 0), and its equation carries the pseudo-force moment of
+ * Eq. newtonseldg, -mass cg_offset cos(alpha1 + theta) X1'' - (inertia + mass hinge_offset cg_offset cos theta)
+ * alpha1'' - mass hinge_offset cg_offset sin theta alpha1'^2, with inertia about the hinge, mass >= 0 and
+ * cg_offset (L2) the distance of its centre of mass from the hinge.  driver = 0: a fixed hinge.
  * All bodies of one context must use the same ds (the surface-stress regularisation weight). */
 typedef struct {
   int type;
@@ -121,6 +133,10 @@ typedef struct {
   const double* pts;
   const double* ur;
   double mass_per_length, bending_stiffness, stretching_stiffness; /* DEFORMABLE only */
+  double kinematics[5];   /* DRIVEN: A0, beta, sigma_t, sigma_r, f */
+  double s_lo;            /* DRIVEN: position of point 0 along the plate from the reference point */
+  int driver;             /* TORSIONAL: 0 fixed hinge; k > 0 hinged on the DRIVEN body k - 1 */
+  double hinge_offset, mass, cg_offset; /* TORSIONAL with a driver: L1, plate mass, L2 */
 } fsi_body_desc;
 
 typedef struct {

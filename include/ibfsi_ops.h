@@ -62,6 +62,14 @@ fsi_status fsi_op_beam_solve(int n_el, double ds, double mu, double ei, double e
                              const double* zetadot_n, const double* ref, const double* b, double* r_zeta,
                              double* x);
 
+/* The prescribed kinematics of a DRIVEN plate (Sec. 5.1; the formulas of the DRIVEN body in ibfsi.h) as the
+ * library evaluates them on the host for every step: out = {X1, X1', X1'', alpha1, alpha1', alpha1''} at
+ * time t (derivatives in t), G_t by composite 16-point Gauss-Legendre quadrature over 16 panels of the
+ * fractional period.  params = {A0, beta, sigma_t, sigma_r, f} (host, 5 doubles); out: host, 6 doubles.
+ * Host computation only: no GPU is used.  Invalid params (A0 < 0, sigma or f <= 0, non-finite values):
+ * FSI_ERR_INVALID_ARG. */
+fsi_status fsi_op_flapping_kinematics(const double* params, double t, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import COUPLING_SUBDOMAIN, COUPLING_TRUE_E, FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
 
-__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError",
+__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "flapping_kinematics", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError",
            "COUPLING_SUBDOMAIN", "COUPLING_TRUE_E"]
 
 
@@ -63,9 +63,15 @@ class Context:
 
     # -- setup -------------------------------------------------------------------------------
 
-    def add_torsional(self, hinge, theta0, n_pts, ds, inertia, damping, stiffness, theta_init, phi_init=0.0):
+    def add_torsional(self, hinge, theta0, n_pts, ds, inertia, damping, stiffness, theta_init, phi_init=0.0,
+                      driver=None, hinge_offset=0.0, mass=0.0, cg_offset=0.0):
+        """Torsional plate (App. A).  driver: id of a driven plate carrying the hinge at hinge_offset along
+        it (Eq. newtonseldg; mass and cg_offset enter the pseudo-force moment, inertia is about the hinge)."""
         b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, n_pts, ds, (ctypes.c_double * 2)(*hinge), theta0, theta_init,
                           phi_init, inertia, damping, stiffness, None, None)
+        if driver is not None:
+            b.driver = driver + 1
+            b.hinge_offset, b.mass, b.cg_offset = hinge_offset, mass, cg_offset
         bid = ctypes.c_int()
         check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
         self.n_bodies += 1
@@ -77,6 +83,17 @@ class Context:
         tip slope ``tip_angle``.  Deflection outputs are the tip displacement and its rate."""
         b = _lib.BodyDesc(_lib.FSI_BODY_DEFORMABLE, n_pts, ds, (ctypes.c_double * 2)(*clamp), theta0, tip_angle,
                           0.0, 0.0, 0.0, 0.0, None, None, mass_per_length, bending_stiffness, stretching_stiffness)
+        bid = ctypes.c_int()
+        check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
+        self.n_bodies += 1
+        return bid.value
+
+    def add_driven(self, ref, s_lo, n_pts, ds, a0, beta, sigma_t, sigma_r, freq=1.0):
+        """Rigid plate with the prescribed heave and pitch of Sec. 5.1 (reference point ref, points at
+        s_lo + j ds along (sin, -cos)(alpha1))."""
+        b = _lib.BodyDesc(_lib.FSI_BODY_DRIVEN, n_pts, ds, (ctypes.c_double * 2)(*ref), 0, 0, 0, 0, 0, 0, None, None)
+        b.kinematics = (ctypes.c_double * 5)(a0, beta, sigma_t, sigma_r, freq)
+        b.s_lo = s_lo
         bid = ctypes.c_int()
         check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
         self.n_bodies += 1
@@ -272,6 +289,16 @@ def level_solve(rhs, h, re, dt, precision=FSI_PREC_FP64, dst_method=0):
     check(lib.fsi_op_level_solve_ex(precision, dst_method, nx1 + 1, ny1 + 1, h, re, dt, _dp(rhs), _dp(w), _dp(s)),
           "fsi_op_level_solve_ex")
     return w, s
+
+
+def flapping_kinematics(params, t):
+    """(X1, X1', X1'', alpha1, alpha1', alpha1'') of a driven plate at time t as the library evaluates them
+    (host computation; params = A0, beta, sigma_t, sigma_r, f)."""
+    lib = _lib.load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(6)
+    check(lib.fsi_op_flapping_kinematics(_dp(p), float(t), _dp(out)), "fsi_op_flapping_kinematics")
+    return out
 
 
 def beam_solve(n_el, ds, mu, ei, ea, clamp, dt, chi, chi_n, zeta_n, zetadot_n, ref, b):

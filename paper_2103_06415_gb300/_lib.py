@@ -17,6 +17,7 @@ FSI_PREC_FP32 = 1
 FSI_BODY_RIGID = 0
 FSI_BODY_TORSIONAL = 1
 FSI_BODY_DEFORMABLE = 2
+FSI_BODY_DRIVEN = 3
 
 STATUS = {
     0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "UNSUPPORTED", 4: "BODY_OUTSIDE_SUBDOMAIN",
@@ -43,7 +44,9 @@ class BodyDesc(ctypes.Structure):
                 ("phi_init", ctypes.c_double), ("inertia", ctypes.c_double), ("damping", ctypes.c_double),
                 ("stiffness", ctypes.c_double), ("pts", ctypes.POINTER(ctypes.c_double)),
                 ("ur", ctypes.POINTER(ctypes.c_double)), ("mass_per_length", ctypes.c_double),
-                ("bending_stiffness", ctypes.c_double), ("stretching_stiffness", ctypes.c_double)]
+                ("bending_stiffness", ctypes.c_double), ("stretching_stiffness", ctypes.c_double),
+                ("kinematics", ctypes.c_double * 5), ("s_lo", ctypes.c_double), ("driver", ctypes.c_int),
+                ("hinge_offset", ctypes.c_double), ("mass", ctypes.c_double), ("cg_offset", ctypes.c_double)]
 
 
 class Box(ctypes.Structure):
@@ -93,6 +96,7 @@ SIGNATURES = {
     "fsi_op_level_solve_ex": (_INT, [_INT, _INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,
                                      _D, _D]),
     "fsi_op_fma_rate": (_INT, [_INT, _D]),
+    "fsi_op_flapping_kinematics": (_INT, [_D, ctypes.c_double, _D]),
     "fsi_op_beam_solve": (_INT, [_INT] + [ctypes.c_double] * 7 + [_D] * 8),
     "fsi_op_level_solve_noalloc": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _P, _P, _P, _P]),

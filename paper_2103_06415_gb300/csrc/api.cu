@@ -327,7 +327,8 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
 extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body_id) {
   if (!c || !b) return FSI_ERR_INVALID_ARG;
   if (c->stage >= 1) return FSI_ERR_STATE;
-  if (b->type != FSI_BODY_RIGID && b->type != FSI_BODY_TORSIONAL && b->type != FSI_BODY_DEFORMABLE)
+  if (b->type != FSI_BODY_RIGID && b->type != FSI_BODY_TORSIONAL && b->type != FSI_BODY_DEFORMABLE &&
+      b->type != FSI_BODY_DRIVEN)
     return FSI_ERR_INVALID_ARG;
   if (b->n_pts < 1 || !(b->ds > 0)) return FSI_ERR_INVALID_ARG;
   if (!c->bodies.empty() && std::fabs(b->ds - c->ds) > 1e-15 * c->ds) return FSI_ERR_UNSUPPORTED;
@@ -335,8 +336,10 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
   h.type = b->type;
   h.n = b->n_pts;
   h.off = c->nb;
+  h.driver = -1;
   if (b->type == FSI_BODY_TORSIONAL) {
     if (!(b->inertia > 0) || b->stiffness < 0 || b->damping < 0) return FSI_ERR_INVALID_ARG;
+    if (b->driver < 0 || b->driver > (int)c->bodies.size()) return FSI_ERR_INVALID_ARG;
     h.hx = b->hinge[0];
     h.hy = b->hinge[1];
     h.theta0 = b->theta0;
@@ -346,6 +349,22 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
     h.theta = b->theta_init;
     h.phi = b->phi_init;
     h.phidot = (-b->stiffness * b->theta_init - b->damping * b->phi_init) / b->inertia;
+    if (b->driver > 0) {  // hinged on a driven plate: pseudo-force moment of Eq. newtonseldg at t = 0
+      const BodyHost& d = c->bodies[b->driver - 1];
+      if (d.type != FSI_BODY_DRIVEN || b->theta0 != 0.0 || !(b->mass >= 0) || !std::isfinite(b->mass) ||
+          !std::isfinite(b->hinge_offset) || !std::isfinite(b->cg_offset))
+        return FSI_ERR_INVALID_ARG;
+      h.driver = b->driver - 1;
+      h.l1 = b->hinge_offset;
+      h.mass = b->mass;
+      h.l2 = b->cg_offset;
+      double q[6];
+      flapping_state(d.kin, 0.0, q);
+      const double th = b->theta_init, ml = h.mass * h.l1 * h.l2;
+      const double g = -h.mass * h.l2 * std::cos(q[3] + th) * q[2] - (b->inertia + ml * std::cos(th)) * q[5] -
+                       ml * std::sin(th) * q[4] * q[4];
+      h.phidot += g / b->inertia;
+    }
     for (int j = 0; j < b->n_pts; ++j) {
       c->rigid_pts.push_back(0.0);
       c->rigid_pts.push_back(0.0);
@@ -377,6 +396,20 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
     c->ne_tot += ne;
     c->nd_tot += 3 * ne;
     if (3 * ne > c->nd_max) c->nd_max = 3 * ne;
+    for (int j = 0; j < b->n_pts; ++j) {
+      c->rigid_pts.push_back(0.0);
+      c->rigid_pts.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+      c->rigid_ur.push_back(0.0);
+    }
+  } else if (b->type == FSI_BODY_DRIVEN) {
+    if (!flapping_params_ok(b->kinematics) || !std::isfinite(b->s_lo) || !std::isfinite(b->hinge[0]) ||
+        !std::isfinite(b->hinge[1]))
+      return FSI_ERR_INVALID_ARG;
+    h.hx = b->hinge[0];
+    h.hy = b->hinge[1];
+    for (int k = 0; k < 5; ++k) h.kin[k] = b->kinematics[k];
+    h.s_lo = b->s_lo;
     for (int j = 0; j < b->n_pts; ++j) {
       c->rigid_pts.push_back(0.0);
       c->rigid_pts.push_back(0.0);
@@ -484,6 +517,11 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
       d.ea = h.ea;
       d.ca0 = std::cos(h.theta0);
       d.sa0 = std::sin(h.theta0);
+      d.driver = h.driver;
+      d.s_lo = h.s_lo;
+      d.l1 = h.l1;
+      d.mass = h.mass;
+      d.l2 = h.l2;
       bd.push_back(d);
       BodyState s = {};
       s.theta = h.theta;
@@ -513,6 +551,12 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
+    bool driven = false;
+    for (const BodyHost& h : c->bodies) driven = driven || h.type == FSI_BODY_DRIVEN;
+    if (driven) {  // per-step kinematics table, filled ahead of the steps by fsi_advance
+      c->kin_cap = 1024;
+      if (!(c->d_kin = (double*)ctx_alloc(c, (size_t)c->kin_cap * c->n_bodies * 6 * 8))) return FSI_ERR_OOM;
+    }
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_bodies, bd.data(), bd.size() * sizeof(BodyDev), cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_state, bs.data(), bs.size() * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
     FSI_CUDA_TRY(cudaMemcpyAsync(c->d_point_body, pb.data(), pb.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -608,6 +652,10 @@ extern "C" fsi_status fsi_advance(fsi_ctx* c, int n_steps) {
   if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
   if (c->nb > 0 && !c->have_b0) return FSI_ERR_STATE;
   for (int n = 0; n < n_steps; ++n) {
+    if (c->d_kin && (n == 0 || c->steps_done % c->kin_cap == 0)) {  // kinematics of the next steps
+      const long long left = n_steps - n, room = c->kin_cap - c->steps_done % c->kin_cap;
+      TRY(upload_kinematics(c, c->steps_done, (int)(left < room ? left : room)));
+    }
     if (c->first_pending) {
       TRY(enqueue_step(c, 1));
       c->first_pending = 0;
@@ -642,6 +690,8 @@ extern "C" fsi_status fsi_profile_kernel(fsi_ctx* c, int kernel_class, int n_ste
   c->prof_class = kernel_class;
   c->prof_used = 0;
   for (int n = 0; st == FSI_OK && n < n_steps; ++n) {
+    if (c->d_kin) st = upload_kinematics(c, c->steps_done, 1);
+    if (st != FSI_OK) break;
     st = enqueue_step(c, c->first_pending);
     c->first_pending = 0;
     c->steps_done++;

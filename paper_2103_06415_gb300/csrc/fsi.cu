@@ -87,6 +87,9 @@ struct FsiArgs {
   const double* Bw;
   int bw;
   int* pcij;      // [nb][2] hat cell (ci, cj) of every point, for the window lookups
+  // prescribed kinematics ([kin_cap][n_bodies][6], slot = step mod kin_cap) or NULL; nkb = n_bodies when set
+  const double* kin;
+  int kin_cap, nkb;
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -347,11 +350,12 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 // right-hand sides of the structural solves.
 struct FsiLayout {
   size_t xs, krow, vec, pw, work, rf, pidx, pcij;
-  size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys;
+  size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys, kb;
   size_t total;
 };
 struct BeamDims {
   int nd, ne, nd_max;  // free dofs and elements of all flags, dofs of the largest flag
+  int nkb;             // bodies with a per-step kinematics block (all bodies when a driven plate exists)
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 // Row stride (floats) of the float matrices X, X K and K in global and shared memory: a multiple of 4 (rows
@@ -384,7 +388,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
   L.bm = L.mi + al16((size_t)6 * bd.ne * 4);
   L.ey = L.bm + al16((size_t)9 * bd.ne * 4);
   L.ys = L.ey + al16((size_t)12 * bd.ne * 4);
-  L.total = L.ys + al16((size_t)kMaxRhs * bd.nd_max * 4);
+  L.kb = L.ys + al16((size_t)kMaxRhs * bd.nd_max * 4);
+  L.total = L.kb + al16((size_t)bd.nkb * KB_N * 8);
   return L;
 }
 
@@ -442,7 +447,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   const int R = (nf + (int)gridDim.x - 1) / (int)gridDim.x;
   const int r0 = min(nf, (int)blockIdx.x * R);
   const int nr = min(nf, r0 + R) - r0;
-  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max});
+  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max, a.nkb});
   float* Xs = reinterpret_cast<float*>(dyn_smem + L.xs);
   double* Krow = reinterpret_cast<double*>(dyn_smem + L.krow);
   double* rhs_s = reinterpret_cast<double*>(dyn_smem + L.vec);
@@ -463,6 +468,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   float* bm_s = reinterpret_cast<float*>(dyn_smem + L.bm);
   float* ey_s = reinterpret_cast<float*>(dyn_smem + L.ey);
   float* ys_s = reinterpret_cast<float*>(dyn_smem + L.ys);
+  // per-body kinematics block of this step (KB_* in internal.h), NULL without driven bodies
+  double* kb_s = a.nkb > 0 ? reinterpret_cast<double*>(dyn_smem + L.kb) : nullptr;
   // rows owned by this CTA that are x / y rows of a free flag node: their structural column is solved here
   __shared__ int g_body[kMaxR], g_dof[kMaxR];
   if (tid < kMaxR) {
@@ -515,6 +522,40 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       b_kc[bi] = 0.0;
       b_rphi[bi] = b_rth[bi] = b_th[bi] = b_ph[bi] = b_tp[bi] = 0.0;
     }
+    if (kb_s) {  // prescribed kinematics at the end of this step (Sec. 5.1, Eq. newtonseldg)
+      const BodyDev b = a.bodies[bi];
+      double* k = kb_s + bi * KB_N;
+      for (int m = 0; m < KB_N; ++m) k[m] = 0.0;
+      const int src = b.type == FSI_BODY_DRIVEN ? bi : (b.type == FSI_BODY_TORSIONAL ? b.driver : -1);
+      k[KB_X] = b.hx;
+      k[KB_Y] = b.hy;
+      k[KB_T0] = b.theta0;
+      if (src >= 0) {
+        const double* q = a.kin + ((long)(a.ctrl[2] % a.kin_cap) * a.n_bodies + src) * 6;
+        double sa, ca;
+        sincos(q[3], &sa, &ca);
+        if (b.type == FSI_BODY_DRIVEN) {  // reference point, its velocity, plate direction (sin, -cos)(alpha1)
+          k[KB_X] = b.hx + q[0];
+          k[KB_VX] = q[1];
+          k[KB_SA] = sa;
+          k[KB_CA] = ca;
+          k[KB_AD] = q[4];
+        } else {  // hinge at l1 along the driven plate, its velocity, rest direction alpha1 - pi/2, g terms
+          const BodyDev d = a.bodies[src];
+          k[KB_X] = d.hx + q[0] + b.l1 * sa;
+          k[KB_Y] = d.hy - b.l1 * ca;
+          k[KB_VX] = q[1] + b.l1 * q[4] * ca;
+          k[KB_VY] = b.l1 * q[4] * sa;
+          k[KB_AD] = q[4];
+          k[KB_T0] = q[3] - 0.5 * M_PI;
+          const double ml = b.mass * b.l1 * b.l2;
+          k[KB_GX] = -b.mass * b.l2 * q[2];
+          k[KB_GI] = -b.inertia * q[5];
+          k[KB_GC] = -ml * q[5];
+          k[KB_GS] = -ml * q[4] * q[4];
+        }
+      }
+    }
   }
   int kinv_valid = *(volatile int*)&a.ctrl[4];
   int cur = *(volatile int*)&a.ctrl[7];
@@ -536,7 +577,17 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     // ---- A: body points, P, right-hand side.  Points are split over the CTAs (four threads per point, one
     // per hat vertex; FP64 throughput per SM is low on sm_103), published, then every CTA takes all of them.
     for (int bi = tid; bi < a.n_bodies; bi += nthr)
-      if (a.bodies[bi].type == FSI_BODY_TORSIONAL) sincos(a.bodies[bi].theta0 + b_th[bi], &b_sn[bi], &b_cs[bi]);
+      if (a.bodies[bi].type == FSI_BODY_TORSIONAL) {
+        if (kb_s) {  // moving hinge: rest direction of this step and g at the iterate
+          double* k = kb_s + bi * KB_N;
+          sincos(k[KB_T0] + b_th[bi], &b_sn[bi], &b_cs[bi]);
+          double st, ct;
+          sincos(b_th[bi], &st, &ct);
+          k[KB_G] = k[KB_GX] * (-b_sn[bi]) + k[KB_GI] + k[KB_GC] * ct + k[KB_GS] * st;  // cos(alpha1 + theta) = -sin
+        } else {
+          sincos(a.bodies[bi].theta0 + b_th[bi], &b_sn[bi], &b_cs[bi]);
+        }
+      }
     __syncthreads();
     {
       const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -558,19 +609,32 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             const double th_k = b_th[bi], ph_k = b_ph[bi];
             const int j = p - b.off;
             const double sn = b_sn[bi], cs = b_cs[bi];
-            x = b.hx + (double)j * a.ds * cs;
-            y = b.hy + (double)j * a.ds * sn;
+            const double* k = kb_s ? kb_s + bi * KB_N : nullptr;
+            x = (k ? k[KB_X] : b.hx) + (double)j * a.ds * cs;
+            y = (k ? k[KB_Y] : b.hy) + (double)j * a.ds * sn;
             svx = (double)j * a.ds * (-sn);
             svy = (double)j * a.ds * cs;
             ucx = svx * ph_k;
             ucy = svy * ph_k;
-            const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
+            double rphik = b_rphi[bi] - b_jac[bi] * th_k;
+            if (k) {  // moving hinge: its velocity and alpha1' q R, and g at the iterate
+              ucx += k[KB_VX] + k[KB_AD] * svx;
+              ucy += k[KB_VY] + k[KB_AD] * svy;
+              rphik += k[KB_G];
+            }
             const double rthk = b_rth[bi] - a.two_dt * th_k + ph_k;
             coef = rthk - a.two_dt * rphik * b_ijac[bi];
           } else if (b.type == FSI_BODY_DEFORMABLE) {  // node j of the flag at chi^(k); node 0 is the clamp
             const int j = p - b.off;
             x = j == 0 ? b.hx : chi_s[3 * (b.el_off + j - 1)];
             y = j == 0 ? b.hy : chi_s[3 * (b.el_off + j - 1) + 1];
+          } else if (b.type == FSI_BODY_DRIVEN) {  // prescribed heave and pitch (Sec. 5.1)
+            const double* k = kb_s + bi * KB_N;
+            const double sj = b.s_lo + (double)(p - b.off) * a.ds;
+            x = k[KB_X] + sj * k[KB_SA];
+            y = k[KB_Y] - sj * k[KB_CA];
+            ucx = k[KB_VX] + sj * k[KB_AD] * k[KB_CA];
+            ucy = sj * k[KB_AD] * k[KB_SA];
           } else {
             x = a.rpts[2 * p];
             y = a.rpts[2 * p + 1];
@@ -1026,7 +1090,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         part += q * (-sn) * f_s[p] + q * cs * f_s[nb + p];
       }
       const double sf = block_sum(part, red);
-      const double dth = (b_rphi[bi] - b_jac[bi] * b_th[bi] + a.ds * sf) * b_ijac[bi];
+      const double gk = kb_s ? kb_s[bi * KB_N + KB_G] : 0.0;  // pseudo-force moment at the iterate
+      const double dth = (b_rphi[bi] + gk - b_jac[bi] * b_th[bi] + a.ds * sf) * b_ijac[bi];
       __syncthreads();
       if (tid == 0) {
         b_tp[bi] = b_th[bi];
@@ -1054,7 +1119,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
       double sn = 0.0, cs = 0.0;
-      if (b.type == FSI_BODY_TORSIONAL) sincos(b.theta0 + b_tp[bi], &sn, &cs);  // S of the final solve
+      if (b.type == FSI_BODY_TORSIONAL)  // S of the final solve
+        sincos((kb_s ? kb_s[bi * KB_N + KB_T0] : b.theta0) + b_tp[bi], &sn, &cs);
       double px = 0.0, py = 0.0, pm = 0.0;
       for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
         const double fxp = f_s[p], fyp = f_s[nb + p];
@@ -1117,8 +1183,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         hrow[0] = s.fx;
         hrow[1] = s.fy;
         hrow[2] = s.moment;
-        hrow[3] = b.type != FSI_BODY_RIGID ? s.theta : 0.0;
-        hrow[4] = b.type != FSI_BODY_RIGID ? s.phi : 0.0;
+        const bool moving = b.type == FSI_BODY_TORSIONAL || b.type == FSI_BODY_DEFORMABLE;
+        hrow[3] = moving ? s.theta : 0.0;
+        hrow[4] = moving ? s.phi : 0.0;
         hrow[5] = (double)(it + 1);
         if (!isfinite(s.fx) || !isfinite(s.fy)) dev_set_status(a.status, FSI_ERR_NONFINITE);
       }
@@ -1175,7 +1242,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
 
 }  // namespace
 
-static BeamDims beam_dims(const fsi_ctx* c) { return BeamDims{c->nd_tot, c->ne_tot, c->nd_max}; }
+static BeamDims beam_dims(const fsi_ctx* c) {
+  return BeamDims{c->nd_tot, c->ne_tot, c->nd_max, c->d_kin ? c->n_bodies : 0};
+}
 
 size_t fsi_smem_bytes(const fsi_ctx* c) { return fsi_layout(c->nf, c->nb, beam_dims(c)).total; }
 
@@ -1266,6 +1335,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.Bw = c->Bw;
   a.bw = c->bw;
   a.pcij = c->d_pcij;
+  a.kin = c->d_kin;
+  a.kin_cap = c->kin_cap > 0 ? c->kin_cap : 1;
+  a.nkb = c->d_kin ? c->n_bodies : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);

@@ -16,15 +16,30 @@ struct BodyHost {
   double theta, phi, phidot;
   double mu, ei, ea;  // deformable: mass per length, bending and stretching stiffness
   int el_off;         // deformable: first element in the context-wide element numbering
+  double kin[5];      // driven: A0, beta, sigma_t, sigma_r, f
+  double s_lo;        // driven: position of point 0 along the plate
+  int driver;         // torsional: index of the driven body carrying the hinge, -1 fixed hinge
+  double l1, mass, l2;  // torsional with a driver: hinge offset on the driven plate, mass, centre of mass
 };
 
 // Device-side body record (double).  Deformable bodies: elements el_off .. el_off + n - 2, free degrees of
 // freedom 3*el_off .. 3*(el_off + n - 1) - 1 (x, y, theta of nodes 1 .. n-1).
+// Driven plates: (hx, hy) is the reference point, points at s_lo + j ds along (sin, -cos)(alpha1).  Torsional
+// bodies with driver >= 0: hinge at l1 along that driven plate, pseudo-force moment with mass and l2.
 struct BodyDev {
   int type, off, n, el_off;
   double hx, hy, theta0, inertia, damping, stiffness;
   double mu, ei, ea, ca0, sa0;  // deformable: material, cos / sin of the undeformed direction
+  int driver;
+  double s_lo, l1, mass, l2;
 };
+
+// Per-body data of one step derived from the kinematics table (FSI kernels with driven bodies): for a
+// driven plate the reference point, its velocity and the plate direction; for a torsional body the hinge,
+// its velocity, alpha1', the rest direction theta0 (alpha1 - pi/2 on a driver) and the coefficients of the
+// pseudo-force moment g(theta) = gx cos(alpha1 + theta) + gi + gc cos(theta) + gs sin(theta).
+// KB_G holds g at the current FSI iterate.
+enum { KB_X = 0, KB_Y, KB_VX, KB_VY, KB_SA, KB_CA, KB_AD, KB_T0, KB_GX, KB_GI, KB_GC, KB_GS, KB_G, KB_N };
 
 // Mutable per-body state on the device.
 struct BodyState {
@@ -33,6 +48,8 @@ struct BodyState {
   double fx, fy, moment;
   double theta_p;  // true-E coupling: angle of the iterate whose S produced the current f
   double kc;       // true-E coupling: (2 ds/dt) / J of the step
+  double gk;       // true-E coupling: pseudo-force moment at the current iterate (hinged plates)
+  double t0;       // true-E coupling: rest direction of the step (alpha1 - pi/2 on a driven plate)
 };
 
 struct fsi_ctx {
@@ -106,6 +123,10 @@ struct fsi_ctx {
   int* d_te_ctl;
   unsigned long long* d_te_total;
   cudaStream_t te_stream[2];
+  // prescribed kinematics: [kin_cap][n_bodies][6] per step (X1, X1', X1'', alpha1, alpha1', alpha1'' at the
+  // step's end time, driven bodies only; slot = step mod kin_cap), NULL without driven bodies
+  double* d_kin;
+  int kin_cap;
   double* d_hist;  // [cap][n_bodies][6]
   int hist_cap;
   long long steps_done;
@@ -198,6 +219,10 @@ fsi_status launch_corrector(fsi_ctx* c);
 fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void* s, int use_ring, int mode);
 // fsi.cu
 fsi_status launch_fsi(fsi_ctx* c);
+// kinematics.cu
+bool flapping_params_ok(const double* k);
+void flapping_state(const double* k, double t, double* out);
+fsi_status upload_kinematics(fsi_ctx* c, long long first, int n);
 // true_e.cu
 fsi_status launch_true_e(fsi_ctx* c, int capture);
 fsi_status true_e_setup(fsi_ctx* c);

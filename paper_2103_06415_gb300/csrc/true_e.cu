@@ -67,6 +67,8 @@ struct TeArgs {
   int hist_cap;
   cudaGraphConditionalHandle h_fsi, h_cg;
   int use_cond;
+  const double* kin;  // prescribed kinematics [kin_cap][n_bodies][6] or NULL
+  int kin_cap;
 };
 
 __device__ __forceinline__ double load_s(const void* s, int fp64, long o) {
@@ -115,12 +117,20 @@ __device__ double delta3(double r) {
 // CG solve from the current f.
 __global__ void __launch_bounds__(kPtThr) k_te_prep(TeArgs a) {
   __shared__ double b_th[kMaxB], b_ph[kMaxB], b_jac[kMaxB], b_rphi[kMaxB], b_rth[kMaxB], b_sn[kMaxB], b_cs[kMaxB];
+  // moving hinges and driven plates (Sec. 5.1): reference point or hinge, its velocity, alpha1', and for a
+  // driven plate its direction (sin, -cos)(alpha1)
+  __shared__ double b_hx[kMaxB], b_hy[kMaxB], b_vx[kMaxB], b_vy[kMaxB], b_ad[kMaxB], b_sa[kMaxB], b_ca[kMaxB];
   const int tid = threadIdx.x, nb = a.nb;
   const bool first = a.ctl[TC_FSI_IT] == 0;
   for (int bi = tid; bi < a.n_bodies; bi += kPtThr) {
     const BodyDev b = a.bodies[bi];
     const BodyState s = a.st[bi];
-    double jac = 1.0, rphi = 0.0, rth = 0.0, th = 0.0, ph = 0.0;
+    double jac = 1.0, rphi = 0.0, rth = 0.0, th = 0.0, ph = 0.0, t0 = b.theta0, g = 0.0;
+    b_hx[bi] = b.hx;
+    b_hy[bi] = b.hy;
+    b_vx[bi] = b_vy[bi] = b_ad[bi] = b_sa[bi] = b_ca[bi] = 0.0;
+    const int src = b.type == FSI_BODY_DRIVEN ? bi : (b.type == FSI_BODY_TORSIONAL ? b.driver : -1);
+    const double* q = (a.kin && src >= 0) ? a.kin + ((long)(a.ctrl[2] % a.kin_cap) * a.n_bodies + src) * 6 : nullptr;
     if (b.type == FSI_BODY_TORSIONAL) {
       const double dt = a.dt;
       jac = 4.0 * b.inertia / (dt * dt) + 2.0 * b.damping / dt + b.stiffness;
@@ -130,21 +140,46 @@ __global__ void __launch_bounds__(kPtThr) k_te_prep(TeArgs a) {
       th = first ? s.theta : s.theta_k;
       ph = first ? s.phi : s.phi_k;
     }
+    if (q) {
+      double sa, ca;
+      sincos(q[3], &sa, &ca);
+      if (b.type == FSI_BODY_DRIVEN) {
+        b_hx[bi] = b.hx + q[0];
+        b_vx[bi] = q[1];
+        b_sa[bi] = sa;
+        b_ca[bi] = ca;
+        b_ad[bi] = q[4];
+      } else {  // hinge at l1 along the driven plate; g of Eq. newtonseldg at the iterate
+        const BodyDev d = a.bodies[src];
+        b_hx[bi] = d.hx + q[0] + b.l1 * sa;
+        b_hy[bi] = d.hy - b.l1 * ca;
+        b_vx[bi] = q[1] + b.l1 * q[4] * ca;
+        b_vy[bi] = b.l1 * q[4] * sa;
+        b_ad[bi] = q[4];
+        t0 = q[3] - 0.5 * M_PI;
+        const double ml = b.mass * b.l1 * b.l2;
+        g = -b.mass * b.l2 * cos(q[3] + th) * q[2] - (b.inertia + ml * cos(th)) * q[5] - ml * sin(th) * q[4] * q[4];
+      }
+    }
     b_th[bi] = th;
     b_ph[bi] = ph;
     b_jac[bi] = jac;
-    b_rphi[bi] = rphi;
+    b_rphi[bi] = rphi + g;
     b_rth[bi] = rth;
-    sincos(b.theta0 + th, &b_sn[bi], &b_cs[bi]);
-    if (blockIdx.x == 0 && first) {
+    sincos(t0 + th, &b_sn[bi], &b_cs[bi]);
+    if (blockIdx.x == 0) {
       BodyState& w = a.st[bi];
-      w.jac = jac;
-      w.kc = (2.0 * a.ds / a.dt) / jac;
-      w.r_phi = rphi;
-      w.r_theta = rth;
-      w.theta_k = s.theta;
-      w.phi_k = s.phi;
-      w.theta_p = s.theta;
+      w.gk = g;
+      w.t0 = t0;
+      if (first) {
+        w.jac = jac;
+        w.kc = (2.0 * a.ds / a.dt) / jac;
+        w.r_phi = rphi;
+        w.r_theta = rth;
+        w.theta_k = s.theta;
+        w.phi_k = s.phi;
+        w.theta_p = s.theta;
+      }
     }
   }
   __syncthreads();
@@ -158,16 +193,23 @@ __global__ void __launch_bounds__(kPtThr) k_te_prep(TeArgs a) {
   if (b.type == FSI_BODY_TORSIONAL) {
     const double sn = b_sn[bi], cs = b_cs[bi];
     const double q = (double)(pp - b.off) * a.ds;
-    x = __dadd_rn(b.hx, __dmul_rn(q, cs));
-    y = __dadd_rn(b.hy, __dmul_rn(q, sn));
+    x = __dadd_rn(b_hx[bi], __dmul_rn(q, cs));
+    y = __dadd_rn(b_hy[bi], __dmul_rn(q, sn));
     svx = q * (-sn);
     svy = q * cs;
     const double th_k = b_th[bi], ph_k = b_ph[bi];
     const double rphik = b_rphi[bi] - b_jac[bi] * th_k;
     const double rthk = b_rth[bi] - a.two_dt * th_k + ph_k;
     const double coef = rthk - a.two_dt * rphik / b_jac[bi];
-    ux = svx * ph_k - svx * coef;
-    uy = svy * ph_k - svy * coef;
+    // moving hinge: its velocity and alpha1' q R are known parts of the point velocities
+    ux = svx * ph_k - svx * coef + b_vx[bi] + b_ad[bi] * svx;
+    uy = svy * ph_k - svy * coef + b_vy[bi] + b_ad[bi] * svy;
+  } else if (b.type == FSI_BODY_DRIVEN) {  // prescribed heave and pitch
+    const double sj = b.s_lo + (double)(pp - b.off) * a.ds;
+    x = b_hx[bi] + sj * b_sa[bi];
+    y = b_hy[bi] - sj * b_ca[bi];
+    ux = b_vx[bi] + sj * b_ad[bi] * b_ca[bi];
+    uy = sj * b_ad[bi] * b_sa[bi];
   } else {
     x = a.rpts[2 * pp];
     y = a.rpts[2 * pp + 1];
@@ -407,7 +449,7 @@ __global__ void __launch_bounds__(kThr) k_te_post(TeArgs a) {
     for (int m = b.off + tid; m < b.off + b.n; m += kThr) part += a.sv[m] * a.f[m] + a.sv[nb + m] * a.f[nb + m];
     const double sf = block_sum(part, red);
     BodyState& s = a.st[bi];
-    const double dth = (s.r_phi - s.jac * s.theta_k + a.ds * sf) / s.jac;
+    const double dth = (s.r_phi + s.gk - s.jac * s.theta_k + a.ds * sf) / s.jac;
     __syncthreads();
     if (tid == 0) {
       s.theta_p = s.theta_k;
@@ -439,7 +481,7 @@ __global__ void __launch_bounds__(kThr) k_te_finish(TeArgs a) {
   for (int bi = 0; bi < a.n_bodies; ++bi) {
     const BodyDev b = a.bodies[bi];
     double sn = 0.0, cs = 0.0;
-    if (b.type == FSI_BODY_TORSIONAL) sincos(b.theta0 + a.st[bi].theta_p, &sn, &cs);
+    if (b.type == FSI_BODY_TORSIONAL) sincos(a.st[bi].t0 + a.st[bi].theta_p, &sn, &cs);
     double px = 0.0, py = 0.0, pm = 0.0;
     for (int m = b.off + tid; m < b.off + b.n; m += kThr) {
       const double fxp = a.f[m], fyp = a.f[nb + m];
@@ -530,6 +572,8 @@ TeArgs te_args(fsi_ctx* c) {
   a.ctrl = c->d_ctrl;
   a.hist = c->d_hist;
   a.hist_cap = c->hist_cap;
+  a.kin = c->d_kin;
+  a.kin_cap = c->kin_cap > 0 ? c->kin_cap : 1;
   return a;
 }
 

@@ -33,7 +33,13 @@ def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0
     c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
                     precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method, **kw)
     for b in w["bodies"]:
-        if b["kind"] == "torsional":
+        if b["kind"] == "driven":
+            c.add_driven(b["ref"], b["s_lo"], b["n_pts"], w["ds"], b["a0"], b["beta"], b["sigma_t"], b["sigma_r"],
+                         b["freq"])
+        elif b["kind"] == "hinged":
+            c.add_torsional((0.0, 0.0), 0.0, b["n_pts"], w["ds"], b["inertia"], b["damping"], b["stiffness"],
+                            b["theta"], driver=b["driver"], hinge_offset=b["l1"], mass=b["mass"], cg_offset=b["l2"])
+        elif b["kind"] == "torsional":
             c.add_torsional(b["hinge"], b["theta0"], b["n_pts"], w["ds"], b["inertia"], b["damping"], b["stiffness"],
                             b["theta"])
         elif b["kind"] == "deformable":
