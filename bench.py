@@ -247,8 +247,9 @@ def run_comparator(args, timed_steps):
     """The speed-up experiment of Sec. 5.1 (Table eldgerror): mean step time of the sub-domain method against
     the true E, E^T at the body points (matrix-free conjugate gradients, one finest-level (C^T A C)^-1 per
     Krylov iteration), on the torsional plates of the flag grid and of plate_128 (body points at ds = h, and
-    at the paper's ds = 2h), FP64 and FP32, with the
-    relative L2 difference of the deflection angle between the two couplings over the timed steps."""
+    at the paper's ds = 2h) and on the flapping plates of Sec. 5.1 (cases 1, 2), FP64 and FP32, with the
+    relative L2 difference of the deflection angle and the lift between the two couplings over the timed
+    steps."""
     import numpy as np
     import torch
     import paper_2103_06415_gb300 as lib
@@ -260,10 +261,15 @@ def run_comparator(args, timed_steps):
                                             "(library default 1e-10 FP64, 1e-5 FP32; 1e-5 is also PETSc's "
                                             "default GMRES tolerance)"}
     cases = ([args.comparator_case] if args.comparator_case
-             else ["flag_512x256_3lvl_torsional", "plate_128", "plate_128_ds2h"])
+             else ["flag_512x256_3lvl_torsional", "plate_128", "plate_128_ds2h", "e1_flapping_case1",
+                   "e1_flapping_case2"])
     only = set(x for x in args.comparator_runs.split(",") if x)
     for name in cases:
-        w = getattr(wl, name)()
+        # the flapping plates of Sec. 5.1 (E1): sub-domain runs with the sparse B0' (eps = 0.007; the dense
+        # operator of the 58 k-point Omega_0 would hold 107 GB)
+        w = wl.e1_flapping(int(name[-1])) if name.startswith("e1_") else getattr(wl, name)()
+        drop = 0.007 if name.startswith("e1_") else 0.0
+        last = len(w["bodies"]) - 1
         res = {}
         runs = [("fp64_subdomain", lib.FSI_PREC_FP64, 0, 0.0), ("fp64_true_e", lib.FSI_PREC_FP64, 1, 0.0),
                 ("fp64_true_e_ktol1e-5", lib.FSI_PREC_FP64, 1, 1e-5), ("fp32_subdomain", lib.FSI_PREC_FP32, 0, 0.0),
@@ -273,13 +279,15 @@ def run_comparator(args, timed_steps):
             if only and tag not in only:
                 continue
             st = torch.cuda.Stream()
-            c = gpu_context(w, precision=prec, stream=st.cuda_stream, coupling=coupling, krylov_tol=ktol)
+            c = gpu_context(w, precision=prec, stream=st.cuda_stream, coupling=coupling, krylov_tol=ktol,
+                            drop_tol=drop if coupling == 0 else 0.0)
             c.advance(3)
             c.sync()
             kry0 = c.stats()["krylov_iters_total"]
             t = timed_steps(c, st, k)
             sts = c.stats()
-            h = c.history(0)[-k:]
+            h = c.history(last)[-k:].copy()
+            h[:, 1] = sum(c.history(b)[-k:, 1] for b in range(last + 1))    # lift of all bodies
             hist[tag] = h
             r = {"ms_per_step": float(np.mean(t)), "p50_ms": float(np.median(t)),
                  "fsi_iters_per_step": float(np.mean(h[:, 5])), "launches_last_step": sts["launches_per_step"]}
@@ -294,8 +302,12 @@ def run_comparator(args, timed_steps):
             if num in res and den in res:
                 res[key] = res[num]["ms_per_step"] / res[den]["ms_per_step"]
         if "fp64_subdomain" in hist and "fp64_true_e" in hist:
-            a, b = hist["fp64_subdomain"][:, 3], hist["fp64_true_e"][:, 3]
-            res["theta_rel_l2_subdomain_vs_true_e"] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+            for col, key in ((3, "theta"), (1, "lift")):
+                a, b = hist["fp64_subdomain"][:, col], hist["fp64_true_e"][:, col]
+                res[key + "_rel_l2_subdomain_vs_true_e"] = float(np.linalg.norm(a - b) /
+                                                                 max(np.linalg.norm(b), 1e-300))
+        if drop > 0:
+            res["subdomain_drop_tol"] = drop
         res["body_points"] = sum(bb["n_pts"] for bb in w["bodies"])
         out[name] = res
     return out
