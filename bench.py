@@ -259,7 +259,10 @@ def run_comparator(args, timed_steps):
     k = max(3, min(args.steps, 20))
     out = {"steps": k, "warmup": 3, "note": "true E: Krylov tolerance = relative residual of the CG solve "
                                             "(library default 1e-10 FP64, 1e-5 FP32; 1e-5 is also PETSc's "
-                                            "default GMRES tolerance)"}
+                                            "default GMRES tolerance). The *_rel_l2 differences cover only the "
+                                            "timed steps right after the impulsive start, where the lift is "
+                                            "still transient; the comparison over 0 < t/T < 3 of Sec. 5.1 is "
+                                            "a separate long run (DESIGN.md, E1 table)"}
     cases = ([args.comparator_case] if args.comparator_case
              else ["flag_512x256_3lvl_torsional", "plate_128", "plate_128_ds2h", "e1_flapping_case1",
                    "e1_flapping_case2"])

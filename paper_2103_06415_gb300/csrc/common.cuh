@@ -46,6 +46,18 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Raise, never lower, a kernel's dynamic shared-memory limit to `bytes`.  The limit belongs to the kernel for
+// the whole process, and contexts of different sizes launch the same kernels: lowering it for a small
+// context would make a larger one's next launch fail.
+template <typename K>
+inline cudaError_t raise_smem_limit(K kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Row stride (in elements) for a vertex array of nx+1 columns, padded so rows start 32-byte aligned
 // for both float and double.
 static inline long padded_stride(int ncols) { return ((long)ncols + 7) / 8 * 8; }

@@ -1266,7 +1266,7 @@ int fsi_float_ld(int nf) { return fsi_ldx(nf); }
 // CTAs of the FSI kernel per SM at this size (0: does not fit)
 int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c) {
   const size_t bytes = fsi_smem_bytes(c);
-  if (cudaFuncSetAttribute(k_fsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+  if (raise_smem_limit(k_fsi, bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1348,6 +1348,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  FSI_CUDA_TRY(raise_smem_limit(k_fsi, cfg.dynamicSmemBytes));
   prof_mark(c, KC_FSI);
   FSI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fsi, a));
   prof_mark(c, KC_FSI);

@@ -586,6 +586,7 @@ fsi_status launch_src(fsi_ctx* c, const double* vec, double pre) {
   const int wi0 = c->i_lo - 3 < 1 ? 1 : c->i_lo - 3, wi1 = c->i_hi + 3 > c->nx - 1 ? c->nx - 1 : c->i_hi + 3;
   const int wj0 = c->j_lo - 3 < 1 ? 1 : c->j_lo - 3, wj1 = c->j_hi + 3 > c->ny - 1 ? c->ny - 1 : c->j_hi + 3;
   const dim3 grid((wi1 - wi0 + 32) / 32, (wj1 - wj0 + 4) / 4);
+  FSI_CUDA_TRY(raise_smem_limit(k_te_src<T>, src_smem(c->nb)));
   k_te_src<T><<<grid, 128, src_smem(c->nb), c->stream>>>((T*)c->src, c->ps, wi0, wi1, wj0, wj1,
                                                            (const TePoint*)c->d_te_pt, vec, c->nb, pre / c->g.h);
   FSI_CUDA_TRY(cudaGetLastError());
@@ -729,8 +730,8 @@ fsi_status launch_true_e(fsi_ctx* c, int capture) {
 // kernel attributes (dynamic shared memory of the source kernel for nb points)
 fsi_status true_e_setup(fsi_ctx* c) {
   const int sm = (int)src_smem(c->nb);
-  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  FSI_CUDA_TRY(cudaFuncSetAttribute(k_te_src<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  FSI_CUDA_TRY(raise_smem_limit(k_te_src<double>, (size_t)sm));
+  FSI_CUDA_TRY(raise_smem_limit(k_te_src<float>, (size_t)sm));
   return FSI_OK;
 }
 

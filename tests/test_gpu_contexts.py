@@ -1,0 +1,28 @@
+"""Several contexts of different sizes in one process (needs a GB300 and the library): kernels whose dynamic
+shared memory depends on the run keep working for the larger run after a smaller one was set up."""
+
+import numpy as np
+import pytest
+
+from paper_2103_06415_gb300 import workloads as wl
+
+from runners import gpu_context
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_larger_context_runs_after_a_smaller_one_is_set_up(coupling):
+    big = wl.small_flapping() if coupling == 1 else wl.small_flag()    # more shared memory per launch
+    small = wl.small_plate()
+    ref = gpu_context(big, coupling=coupling)
+    ref.advance(6)
+    h_ref = ref.history(len(big["bodies"]) - 1)
+    ref.close()
+    c_big = gpu_context(big, coupling=coupling)
+    c_small = gpu_context(small, coupling=coupling)
+    c_small.advance(2)
+    c_big.advance(6)
+    assert np.array_equal(c_big.history(len(big["bodies"]) - 1), h_ref)
+    c_small.close()
+    c_big.close()
