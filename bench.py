@@ -531,7 +531,7 @@ def main():
     # advance + read the forces back to the host (synchronising), destroy
     e2e = None
     if rank == 0:
-        ke = max(10, args.steps // 4)
+        ke = max(10, args.steps)
         t0 = time.perf_counter()
         c2 = gpu_context(w, precision=prec, precompute=False)
         c2.precompute()
