@@ -193,6 +193,19 @@ fsi_status fsi_set_subdomain(fsi_ctx* ctx, const fsi_box* boxes, int n_boxes, co
  * FSI_ERR_UNSUPPORTED).  drop_tol < 0, >= 1 or NaN: FSI_ERR_INVALID_ARG. */
 fsi_status fsi_precompute(fsi_ctx* ctx, double drop_tol);
 
+/* Save the operator built by fsi_precompute (dense B0 or the filtered B0') to the file at path (host byte
+ * order; a header with the grid, Omega_0, Re, dt and drop tolerance, then the doubles).  The operator depends
+ * only on those, not on the bodies, so it can be reused by later runs (see fsi_load_operator).  Before
+ * fsi_precompute: FSI_ERR_STATE; coupling 1 (no operator): FSI_ERR_UNSUPPORTED; file errors:
+ * FSI_ERR_INVALID_ARG (fsi_last_error_message says which).  Synchronising. */
+fsi_status fsi_save_operator(fsi_ctx* ctx, const char* path);
+
+/* Offline stage from a file written by fsi_save_operator, in place of fsi_precompute: the file's grid (nx, ny,
+ * h), Omega_0 vertex box, Re and dt must equal this context's exactly (else FSI_ERR_INVALID_ARG, as for a
+ * missing or truncated file); the operator's format (dense or filtered) is the file's.  Bodies are set up as
+ * by fsi_precompute.  coupling 1: FSI_ERR_UNSUPPORTED. */
+fsi_status fsi_load_operator(fsi_ctx* ctx, const char* path);
+
 /* Online stage (Algorithm 2): enqueue n_steps time steps on the context stream.  Asynchronous. */
 fsi_status fsi_advance(fsi_ctx* ctx, int n_steps);
 

@@ -119,6 +119,14 @@ class Context:
     def precompute(self, drop_tol=0.0):
         check(self._lib.fsi_precompute(self._h, drop_tol), "fsi_precompute")
 
+    def save_operator(self, path):
+        """Write the precomputed operator (B0 or B0') to a file for runs with the same grid, Omega_0, Re, dt."""
+        check(self._lib.fsi_save_operator(self._h, str(path).encode()), "fsi_save_operator")
+
+    def load_operator(self, path):
+        """Offline stage from a file written by save_operator (in place of precompute)."""
+        check(self._lib.fsi_load_operator(self._h, str(path).encode()), "fsi_load_operator")
+
     # -- online ------------------------------------------------------------------------------
 
     def advance(self, n_steps):

@@ -468,7 +468,9 @@ extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_
   return FSI_OK;
 }
 
-extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
+// Offline stage: the operator is built (load == NULL) or read from a file written by fsi_save_operator,
+// then the bodies are set up on the device.
+static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load) {
   if (!c || !(drop_tol >= 0.0) || !(drop_tol < 1.0)) return FSI_ERR_INVALID_ARG;
   if (drop_tol > 0.0 && c->x.b0_method != 0) return FSI_ERR_UNSUPPORTED;
   if (c->stage >= 1) return FSI_ERR_STATE;
@@ -485,8 +487,14 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   }
   const size_t n2 = 2 * (size_t)c->n_sd;
   fsi_status st = FSI_OK;
+  if (load && true_e) return FSI_ERR_UNSUPPORTED;
+  c->drop_tol = drop_tol;
   if (true_e) {
     c->b0_seconds = 0.0;
+  } else if (load) {
+    const auto t0 = std::chrono::steady_clock::now();
+    st = load_operator_data(c, load);
+    c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   } else if (drop_tol > 0.0) {  // sparse B0' (Eq. filtereq) in the windowed column format
     st = build_b0_window(c, drop_tol);
   } else {
@@ -605,6 +613,13 @@ extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) {
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;
   return FSI_OK;
+}
+
+extern "C" fsi_status fsi_precompute(fsi_ctx* c, double drop_tol) { return precompute_impl(c, drop_tol, nullptr); }
+
+extern "C" fsi_status fsi_load_operator(fsi_ctx* c, const char* path) {
+  if (!path) return FSI_ERR_INVALID_ARG;
+  return precompute_impl(c, 0.0, path);
 }
 
 void prof_mark(fsi_ctx* c, int cls) {

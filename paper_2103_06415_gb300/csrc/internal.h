@@ -81,6 +81,7 @@ struct fsi_ctx {
   double* Bw;  // sparse B0' in the windowed column format of b0_sparse.cu, or NULL
   int bw;      // window half-width of Bw (Omega_0 points)
   long long b0_nnz;  // kept entries of B0' (sparse build)
+  double drop_tol;    // filter of the operator in use (0: dense)
   double* d_factor;  // (2 n_sd)^2 lower Cholesky factor of B0 + tau I (fsi_factor_operator), or NULL
   int have_b0;
   double b0_seconds;
@@ -234,6 +235,8 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
 // b0_sparse.cu
 fsi_status build_b0_window(fsi_ctx* c, double drop_tol);
 fsi_status b0_window_entries(fsi_ctx* c, const int64_t* d_rows, const int64_t* d_cols, int n, double* d_out);
+// operator_io.cu
+fsi_status load_operator_data(fsi_ctx* c, const char* path);
 // b0_columns.cu
 fsi_status build_b0_columns(fsi_ctx* c);
 fsi_status b0_columns(fsi_ctx* c, std::vector<B0Box>& boxes, double* out);
