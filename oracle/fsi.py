@@ -93,11 +93,13 @@ class RigidBody:
 
     kind = "rigid"
 
-    def __init__(self, pts, ur=None):
+    def __init__(self, pts, ur=None, appended=False):
         self.pts = np.asarray(pts, dtype=np.float64)
         self.n_pts = len(self.pts)
         self.ur = np.zeros_like(self.pts) if ur is None else np.asarray(ur, dtype=np.float64)
         self.ds = None
+        # appended: the points join Omega_0 and are interpolated with E itself (Sec. 3.1.1)
+        self.appended = bool(appended)
 
     def points(self, theta=None):
         return self.pts
@@ -123,7 +125,17 @@ class Sim:
         # E C (C^T A C)^-1 C^T E^T built column by column (the comparator of Sec. 5.1)
         self.coupling = coupling
         self.last_pts = None
-        self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box) if sd_box is not None else None
+        # exact points of stationary bodies appended to Omega_0 (Sec. 3.1.1), in body order
+        app = [b.pts for b in self.bodies if getattr(b, "appended", False)]
+        extra = np.concatenate(app) if app else None
+        self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box, extra=extra) if sd_box is not None else None
+        self.appended = np.full(sum(b.n_pts for b in self.bodies), -1, dtype=np.int64)
+        o = e = 0
+        for b in self.bodies:
+            if getattr(b, "appended", False):
+                self.appended[o:o + b.n_pts] = e + np.arange(b.n_pts)
+                e += b.n_pts
+            o += b.n_pts
         self.w = [np.zeros(l.shape) for l in self.levels]
         self.s = [np.zeros(l.shape) for l in self.levels]
         self.nprev = [None] * len(self.levels)
@@ -197,7 +209,7 @@ class Sim:
                 rhs = ib.e_points(lev, pts, u + self.uinf[0], v + self.uinf[1])   # E (C s* + q_inf)
                 idx = wts = None
             else:
-                idx, wts = sd.p_rows(pts)
+                idx, wts = sd.p_rows(pts, self.appended)
                 cols = np.unique(np.concatenate([idx.ravel(), idx.ravel() + sd.n_sd]))
                 pos = {c: k for k, c in enumerate(cols)}
                 pd = np.zeros((2 * nb, len(cols)))

@@ -43,28 +43,33 @@ def hat(r, dr):
 
 
 class Subdomain:
-    """Omega_0: the vertices ``i_lo..i_hi`` x ``j_lo..j_hi`` of the finest level (Sec. 3.1.1)."""
+    """Omega_0: the vertices ``i_lo..i_hi`` x ``j_lo..j_hi`` of the finest level (Sec. 3.1.1), followed by
+    ``extra`` appended points -- the exact points of stationary bodies, interpolated with E itself
+    (Sec. 3.1.1: such points may be added to the sub-domain with weight one).  Unknowns: the x components
+    of the ``n_box`` vertices (row by row) and of the extra points, then the y components likewise."""
 
-    def __init__(self, lev, i_lo, i_hi, j_lo, j_hi):
+    def __init__(self, lev, i_lo, i_hi, j_lo, j_hi, extra=None):
         if i_lo < 2 or j_lo < 2 or i_hi > lev.nx - 2 or j_hi > lev.ny - 2 or i_hi <= i_lo or j_hi <= j_lo:
             raise ValueError("sub-domain must lie at least 2 cells inside the grid")
         self.lev = lev
         self.i_lo, self.i_hi, self.j_lo, self.j_hi = int(i_lo), int(i_hi), int(j_lo), int(j_hi)
         self.ni = self.i_hi - self.i_lo + 1
         self.nj = self.j_hi - self.j_lo + 1
-        self.n_sd = self.ni * self.nj
+        self.n_box = self.ni * self.nj
+        self.extra = np.zeros((0, 2)) if extra is None else np.asarray(extra, dtype=np.float64).reshape(-1, 2)
+        self.n_sd = self.n_box + len(self.extra)
         jj, ii = np.meshgrid(np.arange(self.j_lo, self.j_hi + 1), np.arange(self.i_lo, self.i_hi + 1), indexing="ij")
         self.pi = ii.ravel()
         self.pj = jj.ravel()
 
     @classmethod
-    def from_box(cls, lev, x_lo, x_hi, y_lo, y_hi):
+    def from_box(cls, lev, x_lo, x_hi, y_lo, y_hi, extra=None):
         """Snap a physical box to vertices, clipped to >= 2 cells from the boundary (reading R10)."""
         i_lo = max(int(np.ceil((x_lo - lev.x0) / lev.h - 1e-9)), 2)
         i_hi = min(int(np.floor((x_hi - lev.x0) / lev.h + 1e-9)), lev.nx - 2)
         j_lo = max(int(np.ceil((y_lo - lev.y0) / lev.h - 1e-9)), 2)
         j_hi = min(int(np.floor((y_hi - lev.y0) / lev.h + 1e-9)), lev.ny - 2)
-        return cls(lev, i_lo, i_hi, j_lo, j_hi)
+        return cls(lev, i_lo, i_hi, j_lo, j_hi, extra)
 
     # -- E0 (Eq. ibsdinterp): weights d(x_face - x_k) d(y_face - y_k) --------------------
 
@@ -86,29 +91,50 @@ class Subdomain:
         return I, J, w
 
     def e0(self, u, v):
-        """``E0 q``: interpolate face fluxes to all Omega_0 points -> vector of length ``2 n_sd``."""
+        """``E0 q``: interpolate face fluxes to all Omega_0 points -> vector of length ``2 n_sd`` (E itself
+        at the appended points)."""
         I, J, w = self._u_window()
         u0 = np.sum(w * u[J, I], axis=(1, 2))
         I, J, w = self._v_window()
         v0 = np.sum(w * v[J, I], axis=(1, 2))
-        return np.concatenate([u0, v0])
+        nx_ = len(self.extra)
+        ex = e_points(self.lev, self.extra, u, v) if nx_ else np.zeros(0)
+        return np.concatenate([u0, ex[:nx_], v0, ex[nx_:]])
 
     def e0t(self, g):
         """``E0^T g``: spread a sub-domain vector onto the faces (same weights, transposed)."""
         lev = self.lev
+        nb_, n = self.n_box, self.n_sd
         u = np.zeros((lev.ny, lev.nx + 1))
         v = np.zeros((lev.ny + 1, lev.nx))
         I, J, w = self._u_window()
-        np.add.at(u, (J, I), w * g[: self.n_sd, None, None])
+        np.add.at(u, (J, I), w * g[:nb_, None, None])
         I, J, w = self._v_window()
-        np.add.at(v, (J, I), w * g[self.n_sd:, None, None])
+        np.add.at(v, (J, I), w * g[n:n + nb_, None, None])
+        if len(self.extra):
+            ue, ve = et_points(lev, self.extra, np.concatenate([g[nb_:n], g[n + nb_:]]))
+            u += ue
+            v += ve
         return u, v
 
     # -- P (Eqs. sdapprox3, weights): 4 tensor-cell neighbours, hat weights --------------
 
-    def p_rows(self, pts):
-        """For each body point: the 4 Omega_0 point indices and hat weights (reading R9)."""
+    def p_rows(self, pts, appended=None):
+        """For each body point: the 4 Omega_0 point indices and hat weights (reading R9).  A point with
+        ``appended[p] = e >= 0`` is extra point e itself: index n_box + e with weight one (the others zero)."""
         lev = self.lev
+        if appended is not None and np.any(np.asarray(appended) >= 0):
+            app = np.asarray(appended)
+            idx = np.zeros((len(pts), 4), dtype=np.int64)
+            wts = np.zeros((len(pts), 4))
+            box = np.nonzero(app < 0)[0]
+            if len(box):
+                bi, bw = self.p_rows(np.asarray(pts)[box])
+                idx[box], wts[box] = bi, bw
+            for p in np.nonzero(app >= 0)[0]:
+                idx[p, :] = self.n_box + app[p]
+                wts[p, 0] = 1.0
+            return idx, wts
         x_lo = lev.x0 + self.i_lo * lev.h
         y_lo = lev.y0 + self.j_lo * lev.h
         x_hi = lev.x0 + self.i_hi * lev.h

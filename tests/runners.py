@@ -23,7 +23,7 @@ def oracle_sim(w, **kw):
             bodies.append(obeam.Beam(b["clamp"], b["theta0"], b["n_pts"] - 1, w["ds"], b["mass"], b["ei"], b["ea"],
                                      tip_angle=b["tip_angle"]))
         else:
-            bodies.append(ofsi.RigidBody(b["pts"], b.get("ur")))
+            bodies.append(ofsi.RigidBody(b["pts"], b.get("ur"), b.get("appended", False)))
     return ofsi.Sim(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["n_levels"], w["re"], w["dt"], w["uinf"],
                     w["sd_box"], bodies, w["ds"], **kw)
 
