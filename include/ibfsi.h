@@ -137,6 +137,13 @@ typedef struct {
   double s_lo;            /* DRIVEN: position of point 0 along the plate from the reference point */
   int driver;             /* TORSIONAL: 0 fixed hinge; k > 0 hinged on the DRIVEN body k - 1 */
   double hinge_offset, mass, cg_offset; /* TORSIONAL with a driver: L1, plate mass, L2 */
+  int append_to_subdomain; /* RIGID: nonzero appends the (fixed) points to Omega_0 (Sec. 3.1.1): they are
+                              interpolated with E itself and get their own rows and columns in B0 (one
+                              finest-level solve per appended unknown at fsi_precompute, in the context's
+                              precision).  Points must lie >= 2 cells inside the grid (else
+                              FSI_ERR_BODY_OUTSIDE_SUBDOMAIN at fsi_precompute), anywhere relative to the box.
+                              Dense operator only: with drop_tol > 0, fsi_save_operator or fsi_load_operator
+                              FSI_ERR_UNSUPPORTED.  Ignored with coupling 1. */
 } fsi_body_desc;
 
 typedef struct {

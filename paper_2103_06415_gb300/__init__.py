@@ -99,7 +99,9 @@ class Context:
         self.n_bodies += 1
         return bid.value
 
-    def add_rigid(self, pts, ds, ur=None):
+    def add_rigid(self, pts, ds, ur=None, append=False):
+        """Rigid points with prescribed velocity ur (default 0).  append: the (fixed) points join Omega_0 and
+        are interpolated with E itself (Sec. 3.1.1)."""
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
         urp = None
         if ur is not None:
@@ -107,6 +109,7 @@ class Context:
             urp = _dp(ur)
         b = _lib.BodyDesc(_lib.FSI_BODY_RIGID, len(pts), ds, (ctypes.c_double * 2)(0, 0), 0, 0, 0, 0, 0, 0,
                           _dp(pts), urp)
+        b.append_to_subdomain = 1 if append else 0
         bid = ctypes.c_int()
         check(self._lib.fsi_add_body(self._h, ctypes.byref(b), ctypes.byref(bid)), "fsi_add_body")
         self.n_bodies += 1

@@ -46,7 +46,8 @@ class BodyDesc(ctypes.Structure):
                 ("ur", ctypes.POINTER(ctypes.c_double)), ("mass_per_length", ctypes.c_double),
                 ("bending_stiffness", ctypes.c_double), ("stretching_stiffness", ctypes.c_double),
                 ("kinematics", ctypes.c_double * 5), ("s_lo", ctypes.c_double), ("driver", ctypes.c_int),
-                ("hinge_offset", ctypes.c_double), ("mass", ctypes.c_double), ("cg_offset", ctypes.c_double)]
+                ("hinge_offset", ctypes.c_double), ("mass", ctypes.c_double), ("cg_offset", ctypes.c_double),
+                ("append_to_subdomain", ctypes.c_int)]
 
 
 class Box(ctypes.Structure):

@@ -418,6 +418,7 @@ extern "C" fsi_status fsi_add_body(fsi_ctx* c, const fsi_body_desc* b, int* body
     }
   } else {
     if (!b->pts) return FSI_ERR_INVALID_ARG;
+    h.append = b->append_to_subdomain != 0;
     for (int j = 0; j < 2 * b->n_pts; ++j) {
       c->rigid_pts.push_back(b->pts[j]);
       c->rigid_ur.push_back(b->ur ? b->ur[j] : 0.0);
@@ -463,7 +464,7 @@ extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_
   c->j_hi = j_hi;
   c->ni = i_hi - i_lo + 1;
   c->nj = j_hi - j_lo + 1;
-  c->n_sd = c->ni * c->nj;
+  c->n_box = c->n_sd = c->ni * c->nj;
   c->have_sd = 1;
   return FSI_OK;
 }
@@ -479,6 +480,17 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
   c->nf = 2 * c->nb;
   if (c->n_bodies > 64) return FSI_ERR_UNSUPPORTED;
   const int true_e = c->x.coupling == 1;
+  // appended points (Sec. 3.1.1): the fixed points of RIGID bodies flagged append_to_subdomain
+  c->n_app = 0;
+  c->app_pts.clear();
+  if (!true_e)
+    for (const BodyHost& hb : c->bodies)
+      if (hb.type == FSI_BODY_RIGID && hb.append) {
+        for (int j = 0; j < 2 * hb.n; ++j) c->app_pts.push_back(c->rigid_pts[2 * (size_t)hb.off + j]);
+        c->n_app += hb.n;
+      }
+  c->n_sd = c->n_box + c->n_app;
+  if (c->n_app > 0 && (drop_tol > 0.0 || load)) return FSI_ERR_UNSUPPORTED;
   if (true_e) {  // true E at the body points: no B0; torsional and rigid bodies
     if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024) return FSI_ERR_UNSUPPORTED;
     if (c->x.krylov_max_iters <= 0) c->x.krylov_max_iters = 2 * c->nf + 20;
@@ -499,7 +511,12 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
     st = build_b0_window(c, drop_tol);
   } else {
     if (!(c->B0 = (double*)ctx_alloc(c, n2 * n2 * 8))) return FSI_ERR_OOM;
-    st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
+    if (c->n_app > 0) {
+      st = setup_appended(c);
+      if (st == FSI_OK) st = build_appended_b0(c);
+    } else {
+      st = c->x.b0_method == 1 ? build_b0_columns(c) : build_b0(c);
+    }
   }
   if (st != FSI_OK) return st;
   c->have_b0 = 1;
@@ -559,6 +576,18 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
+    if (c->n_app > 0) {  // Omega_0 index of every body point, then the body point of every appended index
+      std::vector<int> ai(c->nb + c->n_app, -1);
+      int e = 0;
+      for (const BodyHost& hb : c->bodies)
+        if (hb.type == FSI_BODY_RIGID && hb.append)
+          for (int j = 0; j < hb.n; ++j, ++e) {
+            ai[hb.off + j] = e;
+            ai[c->nb + e] = hb.off + j;
+          }
+      if (!(c->d_app_idx = (int*)ctx_alloc(c, ai.size() * sizeof(int)))) return FSI_ERR_OOM;
+      FSI_CUDA_TRY(cudaMemcpyAsync(c->d_app_idx, ai.data(), ai.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    }
     bool driven = false;
     for (const BodyHost& h : c->bodies) driven = driven || h.type == FSI_BODY_DRIVEN;
     if (driven) {  // per-step kinematics table, filled ahead of the steps by fsi_advance

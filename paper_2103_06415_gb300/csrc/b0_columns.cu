@@ -11,22 +11,6 @@
 
 namespace {
 
-// E0 C row stencil of unknown comp at a vertex: u -> (dx in -1..1, dy = +-1, w3[dx] dy / 2h);
-// v -> (dx = +-1, dy in -1..1, -w3[dy] dx / 2h).
-__device__ __forceinline__ void stencil_entry(int comp, int t, double inv2h, int* dx, int* dy, double* w) {
-  const double w3[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
-  const int d = t / 2 - 1, e = (t & 1) ? 1 : -1;
-  if (comp == 0) {
-    *dx = d;
-    *dy = e;
-    *w = w3[d + 1] * e * inv2h;
-  } else {
-    *dx = e;
-    *dy = d;
-    *w = -w3[d + 1] * e * inv2h;
-  }
-}
-
 // src[c] (interior layout, row stride ps, batch stride lvl) <- C^T E0^T e_u for the global unknown
 // u = col0 + c of the concatenated boxes; the batch buffer is zeroed before this kernel.
 template <typename T>
@@ -40,7 +24,7 @@ __global__ void k_col_source(T* __restrict__ src, long lvl, long ps, long col0, 
   const int I = b.i_lo + p % b.ni, J = b.j_lo + p / b.ni;
   int dx, dy;
   double w;
-  stencil_entry(comp, t, inv2h, &dx, &dy, &w);
+  e0c_stencil(comp, t, inv2h, &dx, &dy, &w);
   src[(long)c * lvl + (long)(J + dy - 1) * ps + (I + dx - 1)] = T(w);
 }
 
@@ -64,7 +48,7 @@ __global__ void k_col_gather(double* __restrict__ out, const T* __restrict__ s, 
   for (int t = 0; t < 6; ++t) {
     int dx, dy;
     double w;
-    stencil_entry(comp, t, inv2h, &dx, &dy, &w);
+    e0c_stencil(comp, t, inv2h, &dx, &dy, &w);
     acc += w * (double)sc[(long)(J + dy) * ps + (I + dx)];
   }
   out[b.out_off + (ug - b.row_off) * n2 + r] = acc;

@@ -219,7 +219,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
                                              int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
-                                             T coef) {
+                                             T coef, int n_box) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char src_smem[];
   T* tab = reinterpret_cast<T*>(src_smem);                  // [nb][16]: ut (8) then vt (8)
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int n
       const int n0 = pidx[4 * p];
       ci = n0 % ni + i_lo;
       cj = n0 / ni + j_lo;
-      take = ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;
+      take = n0 < n_box && ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;  // appended: elsewhere
     }
     const unsigned m = __ballot_sync(0xffffffffu, take);
     if (lane == 0) wcount[wid] = __popc(m);
@@ -441,10 +441,12 @@ fsi_status corrector_t(fsi_ctx* c) {
   }
   prof_mark(c, KC_SRC);
   FSI_CUDA_TRY(pdl_launch(k_src<T>, gr, dim3(128), sm, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
-                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h)));
+                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h), c->n_box));
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());
+  const fsi_status st = launch_appended_source(c);  // E^T f of the appended points (appended.cu)
+  if (st != FSI_OK) return st;
   return level_solve_t<T>(c, 0, (const T*)c->src, (T*)c->w_all, (T*)c->s_all, 0, 1);
 }
 

@@ -90,6 +90,10 @@ struct FsiArgs {
   // prescribed kinematics ([kin_cap][n_bodies][6], slot = step mod kin_cap) or NULL; nkb = n_bodies when set
   const double* kin;
   int kin_cap, nkb;
+  // appended points: Omega_0 index of every body point (-1: interpolated by P) and their face windows
+  int n_box;
+  const int* app_idx;
+  const FaceWindow* app_win;
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -641,29 +645,49 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             ucx = a.rur[2 * p];
             ucy = a.rur[2 * p + 1];
           }
+          const int ap = a.app_idx ? a.app_idx[p] : -1;
+          if (ap >= 0) {  // appended point (Sec. 3.1.1): its own unknown, weight one; E (C s* + q_inf) at it
+            a.pidx[4 * p + q] = a.n_box + ap;
+            a.pw[4 * p + q] = q == 0 ? 1.0 : 0.0;
+            if (q == 0) {
+              a.pcij[2 * p] = 0;
+              a.pcij[2 * p + 1] = 0;
+            }
+            const FaceWindow W = a.app_win[ap];  // lane q takes row q of both 4 x 4 face windows
+            for (int d = 0; d < 4; ++d) {
+              const long Iu = W.iu + d, Ju = W.ju + q, Iv = W.iv + d, Jv = W.jv + q;
+              const double u = (load_s(a, (Ju + 1) * a.ps + Iu) - load_s(a, Ju * a.ps + Iu)) / a.h + a.U;
+              const double v = -(load_s(a, Jv * a.ps + Iv + 1) - load_s(a, Jv * a.ps + Iv)) / a.h + a.V;
+              ubx += (W.w[d] * W.w[4 + q]) * u;
+              uby += (W.w[8 + d] * W.w[12 + q]) * v;
+            }
+          }
           const double xl = a.x0 + a.i_lo * a.h, yl = a.y0 + a.j_lo * a.h;
           const double fx = (x - xl) / a.h, fy = (y - yl) / a.h;
           int ci = (int)floor(fx), cj = (int)floor(fy);
-          if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(a.ni - 1) && fy <= (double)(a.nj - 1))) {
+          if (ap >= 0) {
+          } else if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(a.ni - 1) && fy <= (double)(a.nj - 1))) {
             if (q == 0) dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
             ci = 0;
             cj = 0;
           }
           ci = min(max(ci, 0), a.ni - 2);
           cj = min(max(cj, 0), a.nj - 2);
-          const double rx = fx - ci, ry = fy - cj;
-          const int aa = q & 1, bb = q >> 1;
-          const double wq = (aa ? rx : 1.0 - rx) * (bb ? ry : 1.0 - ry);
-          a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
-          a.pw[4 * p + q] = wq;
-          if (q == 0) {
-            a.pcij[2 * p] = ci;
-            a.pcij[2 * p + 1] = cj;
+          if (ap < 0) {
+            const double rx = fx - ci, ry = fy - cj;
+            const int aa = q & 1, bb = q >> 1;
+            const double wq = (aa ? rx : 1.0 - rx) * (bb ? ry : 1.0 - ry);
+            a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
+            a.pw[4 * p + q] = wq;
+            if (q == 0) {
+              a.pcij[2 * p] = ci;
+              a.pcij[2 * p + 1] = cj;
+            }
+            double u, v;
+            e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
+            ubx = wq * u;
+            uby = wq * v;
           }
-          double u, v;
-          e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
-          ubx = wq * u;
-          uby = wq * v;
         }
         // sum over the four hat vertices in the fixed order ((q0 + q1) + (q2 + q3))
         ubx += __shfl_xor_sync(FULL, ubx, 1);
@@ -1203,6 +1227,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     int imin = 1 << 30, imax = -1, jmin = 1 << 30, jmax = -1;
     for (int p = tid; p < nb; p += nthr) {
       const int n0 = pidx_s[4 * p];
+      if (n0 >= a.n_box) continue;  // appended point: its source is written by its own kernel
       const int ci = n0 % a.ni, cj = n0 / a.ni;
       imin = min(imin, ci);
       imax = max(imax, ci);
@@ -1338,6 +1363,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.kin = c->d_kin;
   a.kin_cap = c->kin_cap > 0 ? c->kin_cap : 1;
   a.nkb = c->d_kin ? c->n_bodies : 0;
+  a.n_box = c->n_box;
+  a.app_idx = c->n_app > 0 ? c->d_app_idx : nullptr;
+  a.app_win = c->d_app_win;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);

@@ -20,6 +20,7 @@ struct BodyHost {
   double s_lo;        // driven: position of point 0 along the plate
   int driver;         // torsional: index of the driven body carrying the hinge, -1 fixed hinge
   double l1, mass, l2;  // torsional with a driver: hinge offset on the driven plate, mass, centre of mass
+  int append;           // rigid: the points are appended to Omega_0
 };
 
 // Device-side body record (double).  Deformable bodies: elements el_off .. el_off + n - 2, free degrees of
@@ -33,6 +34,43 @@ struct BodyDev {
   int driver;
   double s_lo, l1, mass, l2;
 };
+
+// 4 x 4 face windows of a point for the 3-point delta (E and E^T at an arbitrary point, Sec. 2.2): u faces
+// (iu + d, ju + e) at (x_{iu+d}, y_{ju+e+1/2}) with weight w[d] * w[4 + e]; v faces (iv + d, jv + e) at
+// (x_{iv+d+1/2}, y_{jv+e}) with weight w[8 + d] * w[12 + e].
+struct FaceWindow {
+  int iu, ju, iv, jv;
+  double w[16];
+};
+
+// 3-point discrete delta in grid units (Sec. 2.2, reading R1) with explicit roundings (no contraction).
+__device__ __forceinline__ double delta3_rn(double r) {
+  r = fabs(r);
+  if (r <= 0.5) return __ddiv_rn(__dadd_rn(1.0, sqrt(__dsub_rn(1.0, __dmul_rn(3.0, __dmul_rn(r, r))))), 3.0);
+  if (r <= 1.5) {
+    const double a = __dsub_rn(1.0, r);
+    const double q = fmax(0.0, __dsub_rn(1.0, __dmul_rn(3.0, __dmul_rn(a, a))));
+    return __ddiv_rn(__dsub_rn(__dsub_rn(5.0, __dmul_rn(3.0, r)), sqrt(q)), 6.0);
+  }
+  return 0.0;
+}
+
+// E0 C row stencil of velocity component comp at an Omega_0 vertex (Eq. ibsdinterp with the delta weights
+// (1/6, 2/3, 1/6) x (1/2, 1/2) on the faces next to the vertex), term t < 6: u -> s at (dx in -1..1, dy =
+// +-1) with weight w3[dx] dy / 2h; v -> (dx = +-1, dy in -1..1) with weight -w3[dy] dx / 2h.
+__host__ __device__ __forceinline__ void e0c_stencil(int comp, int t, double inv2h, int* dx, int* dy, double* w) {
+  const double w3[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+  const int d = t / 2 - 1, e = (t & 1) ? 1 : -1;
+  if (comp == 0) {
+    *dx = d;
+    *dy = e;
+    *w = w3[d + 1] * e * inv2h;
+  } else {
+    *dx = e;
+    *dy = d;
+    *w = -w3[d + 1] * e * inv2h;
+  }
+}
 
 // Per-body data of one step derived from the kinematics table (FSI kernels with driven bodies): for a
 // driven plate the reference point, its velocity and the plate direction; for a torsional body the hinge,
@@ -77,6 +115,14 @@ struct fsi_ctx {
   // sub-domain
   int have_sd;
   int i_lo, i_hi, j_lo, j_hi, ni, nj, n_sd;
+  // appended points (exact points of RIGID bodies flagged append, Sec. 3.1.1): unknowns n_box .. n_sd - 1 of
+  // each component follow the box's n_box = ni * nj points; their face windows, the Omega_0 index of every
+  // body point (-1: interpolated by P), and the vertex box their corrector source covers
+  int n_box, n_app;
+  std::vector<double> app_pts;
+  FaceWindow* d_app_win;
+  int* d_app_idx;
+  int app_box[4];
   double* B0;  // (2 n_sd)^2 row-major, double (NULL when the sparse B0' is used)
   double* Bw;  // sparse B0' in the windowed column format of b0_sparse.cu, or NULL
   int bw;      // window half-width of Bw (Omega_0 points)
@@ -200,14 +246,14 @@ inline long b0_layout(std::vector<B0Box>& boxes) {
   return entries;
 }
 
-// the context's own Omega_0 as a single box
+// the context's own Omega_0 box (without appended points)
 inline B0Box ctx_box(const fsi_ctx* c) {
   B0Box b = {};
   b.i_lo = c->i_lo;
   b.j_lo = c->j_lo;
   b.ni = c->ni;
   b.nj = c->nj;
-  b.n_sd = c->n_sd;
+  b.n_sd = c->ni * c->nj;
   return b;
 }
 
@@ -235,6 +281,10 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
 // b0_sparse.cu
 fsi_status build_b0_window(fsi_ctx* c, double drop_tol);
 fsi_status b0_window_entries(fsi_ctx* c, const int64_t* d_rows, const int64_t* d_cols, int n, double* d_out);
+// appended.cu
+fsi_status setup_appended(fsi_ctx* c);       // face windows and indices of the appended points
+fsi_status build_appended_b0(fsi_ctx* c);    // B0 with appended points (box part by the chosen method)
+fsi_status launch_appended_source(fsi_ctx* c);  // corrector source of the appended points' stress
 // operator_io.cu
 fsi_status load_operator_data(fsi_ctx* c, const char* path);
 // b0_columns.cu

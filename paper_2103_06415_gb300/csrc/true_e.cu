@@ -29,12 +29,7 @@ constexpr int kMaxB = 64;            // bodies per context
 constexpr int kSrcChunk = 64;        // selected points whose face contributions one source CTA stages at a time
 constexpr unsigned FULL = 0xffffffffu;
 
-// 4 x 4 face windows of one body point: u faces (iu + d, ju + e) at (x_{iu+d}, y_{ju+e+1/2}) with weight
-// w[d] * w[4 + e]; v faces (iv + d, jv + e) at (x_{iv+d+1/2}, y_{jv+e}) with weight w[8 + d] * w[12 + e].
-struct TePoint {
-  int iu, ju, iv, jv;
-  double w[16];
-};
+using TePoint = FaceWindow;  // the 4 x 4 face windows of one body point (internal.h)
 
 // control words
 enum { TC_CG_IT = 0, TC_CG_DONE, TC_FSI_IT, TC_FSI_DONE, TC_CG_STEP, TC_CG_LAST, TC_N };
@@ -95,18 +90,6 @@ __device__ double block_sum(double v, double* red) {
 __device__ __forceinline__ double group16_sum(double v) {
   for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, 16);
   return v;
-}
-
-// 3-point discrete delta in grid units (Sec. 2.2, reading R1); explicit roundings (no contraction).
-__device__ double delta3(double r) {
-  r = fabs(r);
-  if (r <= 0.5) return __ddiv_rn(__dadd_rn(1.0, sqrt(__dsub_rn(1.0, __dmul_rn(3.0, __dmul_rn(r, r))))), 3.0);
-  if (r <= 1.5) {
-    const double a = __dsub_rn(1.0, r);
-    const double q = fmax(0.0, __dsub_rn(1.0, __dmul_rn(3.0, __dmul_rn(a, a))));
-    return __ddiv_rn(__dsub_rn(__dsub_rn(5.0, __dmul_rn(3.0, r)), sqrt(q)), 6.0);
-  }
-  return 0.0;
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -232,7 +215,7 @@ __global__ void __launch_bounds__(kPtThr) k_te_prep(TeArgs a) {
   else if (which == 1) r = __dsub_rn(__dadd_rn((double)(ju + k), 0.5), Y);
   else if (which == 2) r = __dsub_rn(__dadd_rn((double)(iv + k), 0.5), X);
   else r = __dsub_rn((double)(jv + k), Y);
-  const double wl = delta3(r);
+  const double wl = delta3_rn(r);
   const double wxu = __shfl_sync(FULL, wl, d, 16), wyu = __shfl_sync(FULL, wl, 4 + e, 16);
   const double wxv = __shfl_sync(FULL, wl, 8 + d, 16), wyv = __shfl_sync(FULL, wl, 12 + e, 16);
   // face (d, e) terms of E (C s* + q_inf): u = (s[J+1][I] - s[J][I]) / h + U, v = -(s[J][I+1] - s[J][I]) / h + V

@@ -45,7 +45,7 @@ def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0
         elif b["kind"] == "deformable":
             c.add_deformable(b["clamp"], b["theta0"], b["n_pts"], w["ds"], b["mass"], b["ei"], b["ea"], b["tip_angle"])
         else:
-            c.add_rigid(b["pts"], w["ds"], b.get("ur"))
+            c.add_rigid(b["pts"], w["ds"], b.get("ur"), b.get("appended", False))
     if w.get("sd_box") is not None:
         c.set_subdomain(*w["sd_box"])
         if precompute:
