@@ -213,6 +213,16 @@ fsi_status fsi_save_operator(fsi_ctx* ctx, const char* path);
  * by fsi_precompute.  coupling 1: FSI_ERR_UNSUPPORTED. */
 fsi_status fsi_load_operator(fsi_ctx* ctx, const char* path);
 
+/* Checkpoint of a run (synchronising): the fields and previous advection term of every level, the body and
+ * flag state, the last surface stress, the float inverse of the small system with its control words, the
+ * interpolation map of the last step, the history ring and the step counters -- everything the next step
+ * reads.  fsi_load_state restores it into a context set up the same way (same grid, precision, coupling,
+ * bodies and history capacity; after its offline stage): n steps, save, load, n steps then equal 2n steps
+ * bit for bit.  A file of another shape, a missing or a truncated file: FSI_ERR_INVALID_ARG, and the
+ * context is left unchanged.  Before the offline stage (with bodies): FSI_ERR_STATE. */
+fsi_status fsi_save_state(fsi_ctx* ctx, const char* path);
+fsi_status fsi_load_state(fsi_ctx* ctx, const char* path);
+
 /* Online stage (Algorithm 2): enqueue n_steps time steps on the context stream.  Asynchronous. */
 fsi_status fsi_advance(fsi_ctx* ctx, int n_steps);
 

@@ -126,6 +126,14 @@ class Context:
         """Write the precomputed operator (B0 or B0') to a file for runs with the same grid, Omega_0, Re, dt."""
         check(self._lib.fsi_save_operator(self._h, str(path).encode()), "fsi_save_operator")
 
+    def save_state(self, path):
+        """Checkpoint the run (everything the next step reads) to a file."""
+        check(self._lib.fsi_save_state(self._h, str(path).encode()), "fsi_save_state")
+
+    def load_state(self, path):
+        """Resume from a checkpoint written by a context set up the same way (after precompute)."""
+        check(self._lib.fsi_load_state(self._h, str(path).encode()), "fsi_load_state")
+
     def load_operator(self, path):
         """Offline stage from a file written by save_operator (in place of precompute)."""
         check(self._lib.fsi_load_operator(self._h, str(path).encode()), "fsi_load_operator")

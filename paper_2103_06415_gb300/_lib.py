@@ -100,6 +100,8 @@ SIGNATURES = {
     "fsi_op_flapping_kinematics": (_INT, [_D, ctypes.c_double, _D]),
     "fsi_save_operator": (_INT, [_P, ctypes.c_char_p]),
     "fsi_load_operator": (_INT, [_P, ctypes.c_char_p]),
+    "fsi_save_state": (_INT, [_P, ctypes.c_char_p]),
+    "fsi_load_state": (_INT, [_P, ctypes.c_char_p]),
     "fsi_op_beam_solve": (_INT, [_INT] + [ctypes.c_double] * 7 + [_D] * 8),
     "fsi_op_level_solve_noalloc": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _P, _P, _P, _P]),
