@@ -472,6 +472,7 @@ extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_
 // Offline stage: the operator is built (load == NULL) or read from a file written by fsi_save_operator,
 // then the bodies are set up on the device.
 static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load) {
+  NvtxRange range(load ? "fsi_load_operator" : "fsi_precompute");
   if (!c || !(drop_tol >= 0.0) || !(drop_tol < 1.0)) return FSI_ERR_INVALID_ARG;
   if (drop_tol > 0.0 && c->x.b0_method != 0) return FSI_ERR_UNSUPPORTED;
   if (c->stage >= 1) return FSI_ERR_STATE;
@@ -657,6 +658,7 @@ void prof_mark(fsi_ctx* c, int cls) {
 }
 
 static fsi_status enqueue_step(fsi_ctx* c, int first, int capture = 0) {
+  NvtxRange range(capture ? "capture step graph" : "enqueue step");
   c->launches_per_step = 0;
   TRY(launch_predictor(c, first));
   if (c->nb > 0 && c->x.coupling == 1) {
@@ -693,6 +695,7 @@ static fsi_status build_graph(fsi_ctx* c) {
 
 extern "C" fsi_status fsi_advance(fsi_ctx* c, int n_steps) {
   if (!c || n_steps < 0) return FSI_ERR_INVALID_ARG;
+  NvtxRange range("fsi_advance");
   if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
   if (c->nb > 0 && !c->have_b0) return FSI_ERR_STATE;
   for (int n = 0; n < n_steps; ++n) {

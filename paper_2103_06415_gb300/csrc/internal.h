@@ -1,7 +1,16 @@
 // Internal context layout and launcher declarations (not part of the C ABI).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <vector>
 #include "common.cuh"
+
+// NVTX range for the lifetime of a scope (host; a no-op unless a profiler injects an NVTX handler)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct LevelBufs {
   void* w;      // vertex vorticity [(ny+1) x ps]

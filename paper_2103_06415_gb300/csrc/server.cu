@@ -158,6 +158,7 @@ extern "C" fsi_status fsi_server_submit(fsi_server* s, const fsi_request* req, u
 
 extern "C" fsi_status fsi_server_step(fsi_server* s, int* n_active) {
   if (!s) return FSI_ERR_INVALID_ARG;
+  NvtxRange range("fsi_server_step");
   // 1. admission in arrival order while the budget allows
   while (!s->queue.empty() && (int)s->active.size() < s->max_active &&
          s->in_use + s->queue.front()->bytes <= s->budget) {

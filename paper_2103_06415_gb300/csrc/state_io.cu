@@ -87,6 +87,7 @@ StateHeader header_of(const fsi_ctx* c, int n_blobs) {
 
 extern "C" fsi_status fsi_save_state(fsi_ctx* c, const char* path) {
   if (!c || !path) return FSI_ERR_INVALID_ARG;
+  NvtxRange range("fsi_save_state");
   if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   const std::vector<Blob> bl = blobs(c);
@@ -121,6 +122,7 @@ extern "C" fsi_status fsi_save_state(fsi_ctx* c, const char* path) {
 
 extern "C" fsi_status fsi_load_state(fsi_ctx* c, const char* path) {
   if (!c || !path) return FSI_ERR_INVALID_ARG;
+  NvtxRange range("fsi_load_state");
   if (c->nb > 0 && c->stage < 1) return FSI_ERR_STATE;
   FILE* f = fopen(path, "rb");
   if (!f) {
