@@ -60,14 +60,23 @@ __global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const 
   __shared__ T tw[10][35], ts[10][35];
   const int g = blockIdx.z;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;  // tile vertex (i0 + 1, j0 + 1) at smem (1, 1)
-  const T* w = w_all + (long)g * lvl;
   const T* s = s_all + (long)g * lvl;
   const int t = threadIdx.y * 32 + threadIdx.x;
-  for (int e = t; e < 10 * 34; e += 256) {
+  const int i = i0 + threadIdx.x + 1, j = j0 + threadIdx.y + 1;
+  const bool inner = i < nx && j < ny;
+  const long o = (long)j * ps + i;
+  T* np = np_all + (long)g * lvl;
+  // every global load of the thread is issued before any is consumed: N^{n-1} of its vertex and its (at
+  // most two) elements of the 10 x 34 tile of w and s
+  const T nprev = (inner && !first) ? np[o] : T(0);
+  T wv[2], sv[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = t + 256 * q;
     const int r = e / 34, c = e - r * 34;
     const int I = i0 + c, J = j0 + r;  // vertex indices 0..nx, 0..ny
-    T wv = T(0), sv = T(0);
-    if (I <= nx && J <= ny) {
+    wv[q] = sv[q] = T(0);
+    if (e < 10 * 34 && I <= nx && J <= ny) {
       // O1 on the fly: a vertex strictly inside a finer level takes the vorticity of the finest level that
       // contains it (the coarse array itself is overwritten by this level's solve before any other use)
       int gi = g, ii = I, jj = J;
@@ -76,15 +85,21 @@ __global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const 
         jj = 2 * jj - ny / 2;
         --gi;
       }
-      wv = w_all[(long)gi * lvl + (long)jj * ps + ii];
-      sv = s[(long)J * ps + I];
+      wv[q] = w_all[(long)gi * lvl + (long)jj * ps + ii];
+      sv[q] = s[(long)J * ps + I];
     }
-    tw[r][c] = wv;
-    ts[r][c] = sv;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = t + 256 * q;
+    if (e < 10 * 34) {
+      const int r = e / 34, c = e - r * 34;
+      tw[r][c] = wv[q];
+      ts[r][c] = sv[q];
+    }
   }
   __syncthreads();
-  const int i = i0 + threadIdx.x + 1, j = j0 + threadIdx.y + 1;
-  if (i >= nx || j >= ny) return;
+  if (!inner) return;
   const int x = threadIdx.x + 1, y = threadIdx.y + 1;
   const T i2h = k.i2h[g];
   const T wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
@@ -95,10 +110,8 @@ __global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const 
   const T vs = -(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
   const T n = (ue * we - uw * ww) * i2h + (vn * wn - vs * wsx) * i2h;
   const T lap = (we + ww + wn + wsx - T(4) * wc) * k.inv_h2[g];
-  const long o = (long)j * ps + i;
-  T* np = np_all + (long)g * lvl;
   const long oi = (long)(j - 1) * ps + (i - 1);
-  const T nold = first ? n : np[o];
+  const T nold = first ? n : nprev;
   np[o] = n;
   rhs_all[(long)g * lvl + oi] = wc * k.inv_dt + lap * k.half_inv_re - T(1.5) * n + T(0.5) * nold;
 }
