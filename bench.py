@@ -40,7 +40,7 @@ def parse():
                     help="measure the offline stage instead (B0 for 8192 unknowns on a 1024^2 grid by both "
                          "methods, then the FP64 Cholesky factor of B0 + tau I) and print one JSON line")
     ap.add_argument("--serving", type=int, default=0,
-                    help="serving mode: stream this many config-4 requests through the continuous-batching "
+                    help="serving mode: stream this many Poisson-arriving plate runs through the continuous-batching "
                          "server and print one JSON line")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip the true-E comparator runs (Sec. 5.1 speed-up experiment)")
@@ -144,7 +144,7 @@ class Clocks:
 
 
 def run_offline():
-    """Offline stage of the b0_1024 workload (Algorithm 1 sizes of config 3): B0 assembly by the lattice
+    """Offline stage of the b0_1024 workload (8192 sub-domain unknowns on 1024 x 1024): B0 assembly by the lattice
     Green's function (FP64) and by one DST solve per column (FP32 and FP64), then the FP64 Cholesky factor of
     B0 + tau I.  Wall times include a synchronisation; the factor's flops are n^3/3."""
     import torch
@@ -203,7 +203,7 @@ def run_offline():
 
 
 def run_serving(n_req):
-    """Serving sample of BASELINE config 4: a Poisson stream (20 req/s, real time) of independent
+    """Serving sample: a Poisson stream (20 req/s, real time) of independent
     torsional-plate runs on {128, 256, 512, 1024}^2 grids with steps drawn from [200, 400] (the config's
     200-2000 range shortened so the sample ends in seconds), FP32 fluid / FP64 FSI, admitted under an HBM
     budget and advanced together.  Prints aggregate cell-steps/s and per-step latency percentiles."""
@@ -233,7 +233,7 @@ def run_serving(n_req):
     st = srv.stats()
     p50 = [r["p50_step_ms"] for r in res]
     p99 = [r["p99_step_ms"] for r in res]
-    out = {"metric": "serving: aggregate FSI cell-steps/s and per-step latency (config 4 sample)",
+    out = {"metric": "serving: aggregate FSI cell-steps/s and per-step latency (Poisson stream of plate runs)",
            "requests": n_req, "finished": len(res), "errors": sum(r["status"] != 0 for r in res),
            "wall_s": wall, "cell_steps": st["cell_steps"], "value": st["cell_steps"] / wall,
            "unit": "cell-steps/s", "max_active": max_active, "ticks": st["ticks"],
@@ -262,7 +262,7 @@ def run_comparator(args, timed_steps):
                                             "default GMRES tolerance). The *_rel_l2 differences cover only the "
                                             "timed steps right after the impulsive start, where the lift is "
                                             "still transient; the comparison over 0 < t/T < 3 of Sec. 5.1 is "
-                                            "a separate long run (DESIGN.md, E1 table)"}
+                                            "a separate three-period run"}
     cases = ([args.comparator_case] if args.comparator_case
              else ["flag_512x256_3lvl_torsional", "plate_128", "plate_128_ds2h", "e1_flapping_case1",
                    "e1_flapping_case2"])
@@ -515,7 +515,7 @@ def main():
         roof = {"bound": "alu", "kernel": "k_fsi (FSI iteration: P B0 P^T, Newton-Schulz inverse refresh, "
                                           "double refinement; latency bound)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (DESIGN.md)",
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
                 "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                         "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
                 "traffic": 1.65e6,

@@ -261,7 +261,7 @@ fsi_status fsi_get_operator_entries(fsi_ctx* ctx, const int64_t* rows, const int
                                     double* out);
 
 /* Double-precision Cholesky factor L L^T = B0 + tau I of the precomputed sub-domain matrix, with
- * tau = tau_rel * max_i B0_ii (B0 at flow-grid spacing is only positive semi-definite; BASELINE config 3
+ * tau = tau_rel * max_i B0_ii (B0 at flow-grid spacing is only positive semi-definite; the b0_1024 workload
  * asks for this factor after the B0 assembly).  The factor (lower triangle, 8 (2 n_sd)^2 bytes) is kept on
  * the device.  *tau_out and *seconds (wall time of the factorisation) may be NULL.  A non-positive pivot
  * returns FSI_ERR_NONFINITE.  Requires fsi_precompute with the dense operator (sparse: FSI_ERR_UNSUPPORTED). */

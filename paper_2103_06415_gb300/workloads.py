@@ -3,7 +3,7 @@
 This module holds parameters and random inputs only (no arithmetic of the method), so both the CUDA
 path and the CPU oracle can be driven from the same inputs.
 
-Configurations (their readings are listed in the design doc):
+Configurations:
 
 * ``plate_128``  -- single level 128x128 cells on [-1,3]x[-2,2] (h = 1/32), Re 100, dt 0.002, one rigid
   flat plate of chord 1 hinged at its leading edge (0,0) on a torsional spring (inertia 1, stiffness 0.5,
@@ -186,7 +186,7 @@ def serving_grid(n, re=100.0):
 
 
 def serving_requests(n_req, seed=SEED, sizes=(128, 256, 512, 1024), steps=(200, 2000), rate_hz=20.0):
-    """Poisson-arrival stream of independent torsional-plate runs (BASELINE config 4 distributions):
+    """Poisson-arrival stream of independent torsional-plate runs (the serving workload's distributions):
     grid from `sizes`, Re ~ U[50, 300], stiffness log-uniform [0.05, 5], inertia ~ U[0.5, 2], angle of
     attack ~ U[5, 40] deg, steps ~ U{steps}.  Returns [(arrival_s, grid dict, body dict, n_steps)]."""
     rng = np.random.default_rng(seed)

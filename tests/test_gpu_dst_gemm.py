@@ -63,7 +63,7 @@ def test_gemm_passes_in_multilevel_steps(dst_method):
 
 
 def test_gemm_passes_in_coupled_run():
-    """plate_128 (config 1) with every sine transform on the tensor cores: force and angle histories against
+    """plate_128 with every sine transform on the tensor cores: force and angle histories against
     the FP64 oracle, at the bound of the FP32 FFT path."""
     import paper_2103_06415_gb300 as p
     w = wl.plate_128()

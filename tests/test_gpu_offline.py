@@ -1,5 +1,5 @@
 """Offline stage on the GPU: B0 by one DST solve per column (Algorithm 1) in FP64 and FP32, agreement of
-the two assembly methods, and the FP64 Cholesky factor of B0 + tau I (config 3 sizes included)."""
+the two assembly methods, and the FP64 Cholesky factor of B0 + tau I (the b0_1024 sizes included)."""
 
 import numpy as np
 import pytest
@@ -80,7 +80,7 @@ def test_config3_size_b0_columns_and_factor():
             lj = g.factor_entries(np.full(8192, j), np.arange(8192))
             bij = g.operator_entries([i], [j])[0] + (tau if i == j else 0.0)
             worst = max(worst, abs(li @ lj - bij) / bmax)
-    print("config-3 factor: tau %.3e, %.3f s, sampled backward error %.2e" % (tau, sec, worst))
+    print("b0_1024 factor: tau %.3e, %.3f s, sampled backward error %.2e" % (tau, sec, worst))
     assert worst < 1e-12
 
 
