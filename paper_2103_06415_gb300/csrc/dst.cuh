@@ -180,40 +180,138 @@ struct SpecParams {
   int Mx, My;
 };
 
+// The twiddle table for shared memory, held in registers between its load and its store (entries
+// m = tid + q * blockDim.x, NQ >= L / blockDim.x of them per thread), so that a pass can load this constant
+// table before it waits for its predecessor and store it once its own loads are in flight.  The table goes
+// to shared memory when the launch gave the kernel room for it (dynamic shared memory of at least
+// end_bytes, the table ending there); otherwise the stages read it from global memory.
+template <typename T, int NQ>
+struct TwiddleStage {
+  using c2 = typename C2<T>::t;
+  c2 v[NQ];
+  bool on;
+  __device__ __forceinline__ void load(const c2* __restrict__ tw, int L, size_t end_bytes) {
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    on = (size_t)dyn >= end_bytes;
+    if (on) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int m = threadIdx.x + q * blockDim.x;
+        if (m < L) v[q] = tw[m];
+      }
+    }
+  }
+  __device__ __forceinline__ const c2* store(c2* tws, const c2* tw, int L) const {
+    if (!on) return tw;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int m = threadIdx.x + q * blockDim.x;
+      if (m < L) tws[m] = v[q];
+    }
+    return tws;
+  }
+};
+
+// Rows row and row + 1 of a transposed output at offset off (row + 1 next to row): the DST pair read off one
+// complex transform z (row: -Im(z)/2, row + 1: Re(z)/2), one vector store when both rows exist and the
+// address is aligned for it.
+template <typename T>
+__device__ __forceinline__ void store_pair(T* __restrict__ out, long off, int row, int nrows,
+                                           typename C2<T>::t z) {
+  using c2 = typename C2<T>::t;
+  const T a = T(-0.5) * z.y, b = T(0.5) * z.x;
+  T* p = out + off;
+  if (row + 1 < nrows && (reinterpret_cast<uintptr_t>(p) & (sizeof(c2) - 1)) == 0) {
+    c2 v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<c2*>(p) = v;
+  } else {
+    if (row < nrows) p[0] = a;
+    if (row + 1 < nrows) p[1] = b;
+  }
+}
+
+// The passes below are bound by latency (a level is a few hundred kB and sits in L2), so each issues all
+// the global loads of a pair of rows before its first shared-memory store: a thread owns the entries
+// n = tid + m * blockDim.x, m < 2 PER, of every row of its CTA (N < L/2 <= 2 PER blockDim.x), and a pair of
+// rows packed into one complex transform is read and written by the same thread.
+
 // Pass XF: rows j of `in` (row stride in_ld, nrows rows of length N) -> unnormalised DST along the row ->
 // transposed store out[k*out_ld + j] (k = 0..N-1).  blockIdx.y indexes a batch with element strides.
 template <typename T, int PER>
 __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                             T* __restrict__ out, long out_ld, long out_bs,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
-  pdl_enter();
   using c2 = typename C2<T>::t;
+  constexpr int NC = 2 * PER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = 1 << logL;
-  const c2* tws = stage_twiddles<T>(buf + (long)nf * L, tw, L, ((size_t)nf + 1) * L * sizeof(c2));
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  TwiddleStage<T, 4 * PER> ts;
+  ts.load(tw, L, ((size_t)nf + 1) * L * sizeof(c2));
+  pdl_enter();
   const int row0 = blockIdx.x * 2 * nf;
   in += (long)blockIdx.y * in_bs;
   out += (long)blockIdx.y * out_bs;
   zero_ends<T>(buf, nf, L);
-  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
-    const int f = idx / N, n = idx - f * N;
+  for (int f = 0; f < nf; ++f) {
     const int r0 = row0 + 2 * f;
-    const T a = (r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
-    const T b = (r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
-    put_pair<T>(buf + (long)f * L, L, n, a, b);
-  }
-  __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tws);
-  const int nr = 2 * nf;
-  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
-    const int r = idx % nr, k = idx / nr;
-    const int row = row0 + r;
-    if (row < nrows) {
-      const c2 z = buf[(long)(r >> 1) * L + k + 1];
-      out[(long)k * out_ld + row] = (r & 1) ? T(0.5) * z.x : T(-0.5) * z.y;
+    T a[NC], b[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      a[m] = (n < N && r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
+      b[m] = (n < N && r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      if (n < N) put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
     }
   }
+  const c2* tws = ts.store(buf + (long)nf * L, tw, L);
+  __syncthreads();
+  block_fft<T, PER>(buf, L, logL, tws);
+  const int lognf = __ffs(nf) - 1;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const int idx = tid + q * nthr;  // nf * N < 2 PER blockDim.x
+    if (idx < nf * N) {
+      const int f = idx & (nf - 1), k = idx >> lognf;
+      const int row = row0 + 2 * f;
+      store_pair<T>(out, (long)k * out_ld + row, row, nrows, buf[(long)f * L + k + 1]);
+    }
+  }
+}
+
+// Per-row terms of the diagonal solve of pass Y at x-frequency k (1-based; rows beyond nrows are inactive).
+// The boundary sine tables sx1, sxN, sy1, syN and the ring are read only when sp.ring is set (callers
+// without a ring may leave them null).
+template <typename T>
+struct YRow {
+  T lx, sx1, sxN, wb, wt, sb, st;  // wb..st: the bottom/top ring spectra of w and s at k
+  bool on;
+};
+
+template <typename T>
+__device__ __forceinline__ YRow<T> y_row(const SpecParams<T>& sp, int k, int nrows) {
+  YRow<T> r;
+  r.on = k <= nrows;
+  const int kk = r.on ? k : 1;
+  r.lx = sp.lx[kk];
+  r.sx1 = r.sxN = r.wb = r.wt = r.sb = r.st = T(0);
+  if (sp.ring) {  // the boundary sine tables exist only with a ring
+    r.sx1 = sp.sx1[kk];
+    r.sxN = sp.sxN[kk];
+    r.wb = sp.ring[2 * sp.ring_ld + (kk - 1)];
+    r.wt = sp.ring[3 * sp.ring_ld + (kk - 1)];
+    r.sb = sp.ring[6 * sp.ring_ld + (kk - 1)];
+    r.st = sp.ring[7 * sp.ring_ld + (kk - 1)];
+  }
+  return r;
 }
 
 // Pass Y: rows k of `in` (x-frequency k+1; nrows = Nx rows of length N = Ny) -> DST along y -> diagonal
@@ -224,74 +322,119 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
                                                 T* __restrict__ outw, T* __restrict__ outs, long out_ld,
                                                 long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
                                                 int nf, SpecParams<T> sp) {
-  pdl_enter();
   using c2 = typename C2<T>::t;
+  constexpr int NC = 2 * PER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
-  c2* buf2 = buf + (long)nf * (1 << logL);
   const int L = 1 << logL;
-  const c2* tws = stage_twiddles<T>(buf + 3L * nf * L, tw, L, (3 * (size_t)nf + 1) * L * sizeof(c2));
+  c2* buf2 = buf + (long)nf * L;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   const int row0 = blockIdx.x * 2 * nf;
+  // constant tables (set up with the context): loaded before the wait for the predecessor
+  TwiddleStage<T, 4 * PER> ts;
+  ts.load(tw, L, (3 * (size_t)nf + 1) * L * sizeof(c2));
+  T lyv[NC], sy1v[NC], syNv[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    const int l = tid + m * nthr + 1;
+    const int ll = l <= N ? l : 1;
+    lyv[m] = sp.ly[ll];
+    sy1v[m] = sp.ring ? sp.sy1[ll] : T(0);
+    syNv[m] = sp.ring ? sp.syN[ll] : T(0);
+  }
+  pdl_enter();
   in += (long)blockIdx.y * in_bs;
   outw += (long)blockIdx.y * out_bs;
   outs += (long)blockIdx.y * out_bs;
+  const T* ring = sp.ring;
+  T rc[NC][4];  // left/right ring spectra of w and s at this thread's columns
+  if (ring) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int l0 = tid + m * nthr;
+      const int ll = l0 < N ? l0 : 0;
+      rc[m][0] = ring[0 * sp.ring_ld + ll];
+      rc[m][1] = ring[1 * sp.ring_ld + ll];
+      rc[m][2] = ring[4 * sp.ring_ld + ll];
+      rc[m][3] = ring[5 * sp.ring_ld + ll];
+    }
+  }
+  YRow<T> rows0[2] = {y_row<T>(sp, row0 + 1, nrows), y_row<T>(sp, row0 + 2, nrows)};
   zero_ends<T>(buf, nf, L);
   zero_ends<T>(buf2, 2 * nf, L);
-  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
-    const int f = idx / N, n = idx - f * N;
+  for (int f = 0; f < nf; ++f) {
     const int r0 = row0 + 2 * f;
-    const T a = (r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
-    const T b = (r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
-    put_pair<T>(buf + (long)f * L, L, n, a, b);
+    T a[NC], b[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      a[m] = (n < N && r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
+      b[m] = (n < N && r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      if (n < N) put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
+    }
   }
+  const c2* tws = ts.store(buf + 3L * nf * L, tw, L);
   __syncthreads();
   block_fft<T, PER>(buf, L, logL, tws);
-  const int nr = 2 * nf;
-  const T* ring = sp.ring;
-  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
-    const int r = idx / N, l0 = idx - r * N;  // l0 = l-1
-    const int k = row0 + r + 1;              // x-frequency
-    const int l = l0 + 1;
-    const c2 z = buf[(long)(r >> 1) * L + l];
-    T rh = (r & 1) ? T(0.5) * z.x : T(-0.5) * z.y;
-    T wt, st;
-    if (k <= nrows) {
-      const T lam = (sp.lx[k] + sp.ly[l]) * sp.inv_h2;
-      const T aw = sp.inv_dt + lam * sp.inv_2re;
-      T bcs = T(0);
-      if (ring) {
-        const int Nx = nrows;
-        const T bw = sp.sx1[k] * ring[0 * sp.ring_ld + l0] + sp.sxN[k] * ring[1 * sp.ring_ld + l0] +
-                     ring[2 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[3 * sp.ring_ld + (k - 1)] * sp.syN[l];
-        bcs = sp.sx1[k] * ring[4 * sp.ring_ld + l0] + sp.sxN[k] * ring[5 * sp.ring_ld + l0] +
-              ring[6 * sp.ring_ld + (k - 1)] * sp.sy1[l] + ring[7 * sp.ring_ld + (k - 1)] * sp.syN[l];
-        rh += bw * sp.ring_w;
-        bcs *= sp.inv_h2;
-        (void)Nx;
-      }
-      wt = rh / aw;
-      st = (wt + bcs) / lam;
-      wt *= sp.norm;
-      st *= sp.norm;
+  for (int f = 0; f < nf; ++f) {
+    YRow<T> rw[2];
+    if (f == 0) {
+      rw[0] = rows0[0];
+      rw[1] = rows0[1];
     } else {
-      wt = T(0);
-      st = T(0);
+      rw[0] = y_row<T>(sp, row0 + 2 * f + 1, nrows);
+      rw[1] = y_row<T>(sp, row0 + 2 * f + 2, nrows);
     }
-    // neighbouring rows of the same field share one complex FFT (w~ rows in buffers 0..nf-1, s~ rows in
-    // nf..2nf-1): s~ is smaller than w~ by ~1/lambda, so packing w~ with s~ would bury s~ in rounding.
-    put_one<T>(buf2 + (long)(r >> 1) * L, L, l0, wt, r & 1);
-    put_one<T>(buf2 + (long)(nf + (r >> 1)) * L, L, l0, st, r & 1);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int l0 = tid + m * nthr;
+      if (l0 >= N) continue;
+      const c2 z = buf[(long)f * L + l0 + 1];
+      T wv[2], sv[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        T rh = e ? T(0.5) * z.x : T(-0.5) * z.y;
+        if (rw[e].on) {
+          const T lam = (rw[e].lx + lyv[m]) * sp.inv_h2;
+          const T aw = sp.inv_dt + lam * sp.inv_2re;
+          T bcs = T(0);
+          if (ring) {
+            const T bw = rw[e].sx1 * rc[m][0] + rw[e].sxN * rc[m][1] + rw[e].wb * sy1v[m] + rw[e].wt * syNv[m];
+            bcs = rw[e].sx1 * rc[m][2] + rw[e].sxN * rc[m][3] + rw[e].sb * sy1v[m] + rw[e].st * syNv[m];
+            rh += bw * sp.ring_w;
+            bcs *= sp.inv_h2;
+          }
+          const T wt = rh / aw;
+          const T st = (wt + bcs) / lam;
+          wv[e] = wt * sp.norm;
+          sv[e] = st * sp.norm;
+        } else {
+          wv[e] = T(0);
+          sv[e] = T(0);
+        }
+      }
+      // the w~ rows of a pair share one complex transform (buffers 0..nf-1), the s~ rows another
+      // (nf..2nf-1): s~ is smaller than w~ by ~1/lambda, so packing w~ with s~ would bury s~ in rounding.
+      put_pair<T>(buf2 + (long)f * L, L, l0, wv[0], wv[1]);
+      put_pair<T>(buf2 + (long)(nf + f) * L, L, l0, sv[0], sv[1]);
+    }
   }
   __syncthreads();
   block_fft<T, 2 * PER>(buf2, L, logL, tws);
-  for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
-    const int r = idx % nr, j = idx / nr;
-    const int k = row0 + r;
-    if (k < nrows) {
-      const c2 zw = buf2[(long)(r >> 1) * L + j + 1];
-      const c2 zs = buf2[(long)(nf + (r >> 1)) * L + j + 1];
-      outw[(long)j * out_ld + k] = (r & 1) ? T(0.5) * zw.x : T(-0.5) * zw.y;
-      outs[(long)j * out_ld + k] = (r & 1) ? T(0.5) * zs.x : T(-0.5) * zs.y;
+  const int lognf = __ffs(nf) - 1;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const int idx = tid + q * nthr;  // nf * N < 2 PER blockDim.x
+    if (idx < nf * N) {
+      const int f = idx & (nf - 1), j = idx >> lognf;
+      const int row = row0 + 2 * f;
+      const long o = (long)j * out_ld + row;
+      store_pair<T>(outw, o, row, nrows, buf2[(long)f * L + j + 1]);
+      store_pair<T>(outs, o, row, nrows, buf2[(long)(nf + f) * L + j + 1]);
     }
   }
 }
@@ -304,44 +447,84 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
                                             long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
                                             long f_ld, long f_bs, int mode,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
-  pdl_enter();
   using c2 = typename C2<T>::t;
+  constexpr int NC = 2 * PER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = 1 << logL;
-  const c2* tws = stage_twiddles<T>(buf + 2L * nf * L, tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  TwiddleStage<T, 4 * PER> ts;
+  ts.load(tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
+  pdl_enter();
   const int row0 = blockIdx.x * 2 * nf;
   inw += (long)blockIdx.y * in_bs;
   ins += (long)blockIdx.y * in_bs;
   fw += (long)blockIdx.y * f_bs;
   fs += (long)blockIdx.y * f_bs;
+  // mode 1 subtracts from the fields: the old values under the first pair of rows load with the inputs
+  T old[NC][4];
+  if (mode != 0) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int i = tid + m * nthr;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const bool ok = i < N && row0 + e < nrows;
+        const long o = (long)(row0 + e + 1) * f_ld + 1 + i;
+        old[m][e] = ok ? fw[o] : T(0);
+        old[m][2 + e] = ok ? fs[o] : T(0);
+      }
+    }
+  }
   zero_ends<T>(buf, 2 * nf, L);
-  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
-    const int f = idx / N, n = idx - f * N;
+  for (int f = 0; f < nf; ++f) {
     const int r0 = row0 + 2 * f;
     const bool v0 = r0 < nrows, v1 = r0 + 1 < nrows;
-    put_pair<T>(buf + (long)f * L, L, n, v0 ? inw[(long)r0 * in_ld + n] : T(0),
-                v1 ? inw[(long)(r0 + 1) * in_ld + n] : T(0));
-    put_pair<T>(buf + (long)(nf + f) * L, L, n, v0 ? ins[(long)r0 * in_ld + n] : T(0),
-                v1 ? ins[(long)(r0 + 1) * in_ld + n] : T(0));
+    T a[NC], b[NC], c[NC], d[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      a[m] = (n < N && v0) ? inw[(long)r0 * in_ld + n] : T(0);
+      b[m] = (n < N && v1) ? inw[(long)(r0 + 1) * in_ld + n] : T(0);
+      c[m] = (n < N && v0) ? ins[(long)r0 * in_ld + n] : T(0);
+      d[m] = (n < N && v1) ? ins[(long)(r0 + 1) * in_ld + n] : T(0);
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int n = tid + m * nthr;
+      if (n < N) {
+        put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
+        put_pair<T>(buf + (long)(nf + f) * L, L, n, c[m], d[m]);
+      }
+    }
   }
+  const c2* tws = ts.store(buf + 2L * nf * L, tw, L);
   __syncthreads();
   block_fft<T, 2 * PER>(buf, L, logL, tws);
-  for (int idx = threadIdx.x; idx < 2 * nf * N; idx += blockDim.x) {
-    const int f2 = idx / N, i = idx - f2 * N;  // f2 = local row
-    const int r = row0 + f2;
-    if (r < nrows) {
-      const c2 zw = buf[(long)(f2 >> 1) * L + i + 1];
-      const c2 zs = buf[(long)(nf + (f2 >> 1)) * L + i + 1];
-      const long o = (long)(r + 1) * f_ld + 1 + i;
-      const T w = (f2 & 1) ? T(0.5) * zw.x : T(-0.5) * zw.y;
-      const T s = (f2 & 1) ? T(0.5) * zs.x : T(-0.5) * zs.y;
-      if (mode == 0) {
-        fw[o] = w;
-        fs[o] = s;
-      } else {
-        fw[o] -= w;
-        fs[o] -= s;
+  for (int f = 0; f < nf; ++f) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const int i = tid + m * nthr;
+      if (i >= N) continue;
+      const c2 zw = buf[(long)f * L + i + 1];
+      const c2 zs = buf[(long)(nf + f) * L + i + 1];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int r = row0 + 2 * f + e;
+        if (r >= nrows) continue;
+        const long o = (long)(r + 1) * f_ld + 1 + i;
+        const T w = e ? T(0.5) * zw.x : T(-0.5) * zw.y;
+        const T s = e ? T(0.5) * zs.x : T(-0.5) * zs.y;
+        if (mode == 0) {
+          fw[o] = w;
+          fs[o] = s;
+        } else if (f == 0) {
+          fw[o] = old[m][e] - w;
+          fs[o] = old[m][2 + e] - s;
+        } else {
+          fw[o] -= w;
+          fs[o] -= s;
+        }
       }
     }
   }
