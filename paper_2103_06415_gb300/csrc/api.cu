@@ -120,7 +120,7 @@ static fsi_status create_impl(fsi_ctx* c) {
   const size_t E = c->esz;
   const size_t lvl = (size_t)c->G * c->lvl_elems * E;
   if (!(c->w_all = ctx_alloc(c, lvl)) || !(c->s_all = ctx_alloc(c, lvl)) || !(c->nprev_all = ctx_alloc(c, lvl)) ||
-      !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)c->Nx * c->ldT * E)) ||
+      !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)c->G * c->Nx * c->ldT * E)) ||
       !(c->T2w = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) || !(c->T2s = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) ||
       !(c->src = ctx_alloc(c, (size_t)c->lvl_elems * E)) || !(c->ring = ctx_alloc(c, (size_t)8 * c->ring_ld * E)))
     return FSI_ERR_OOM;

@@ -307,51 +307,75 @@ bool use_gemm(const fsi_ctx* c, int p) {
   return std::is_same<T, float>::value && c->gd && c->dst_gemm[p];
 }
 
+// Pass XF of nlev levels in one launch (blockIdx.y = level): right-hand sides lvl_elems apart, x-transforms
+// to the scratch slots T1 + level * Nx * ldT.  The tensor-core variant takes one level.
 template <typename T>
-fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ring, int mode) {
+fsi_status xf_pass(fsi_ctx* c, const T* rhs, int nlev) {
   using c2 = typename C2<T>::t;
   set_smem_limits<T>();
-  const FftCfg cx = fft_cfg(c->logLx), cy = fft_cfg(c->logLy);
-  const int Lx = 1 << c->logLx, Ly = 1 << c->logLy;
+  const FftCfg cx = fft_cfg(c->logLx);
+  const int Lx = 1 << c->logLx;
   const c2* twx = (const c2*)c->twx;
-  const c2* twy = (const c2*)c->twy;
-  // XF
   prof_mark(c, KC_XF);
   if (use_gemm<T>(c, 0)) {
+    if (nlev != 1) return FSI_ERR_UNSUPPORTED;  // one level per tensor-core pass
     const fsi_status st = gemm_xf(c, (const float*)rhs);
     if (st != FSI_OK) return st;
   } else {
-    dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
+    dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), nlev);
     const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
+    const long ib = c->lvl_elems, ob = (long)c->Nx * c->ldT;
     switch (cx.per) {
-      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 1>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
-      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 2>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
-      default: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 4>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, 0, c->Ny, c->Nx, (T*)c->T1, c->ldT, 0, twx, c->logLx, cx.nf)); break;
+      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 1>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
+      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 2>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
+      default: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 4>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
     }
   }
   prof_mark(c, KC_XF);
-  // Y
+  c->launches_per_step += 1;
+  return FSI_OK;
+}
+
+// Pass Y of level g (spacing h 2^g) from the x-transforms at t1, with the ring spectra when use_ring.
+template <typename T>
+fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
+  using c2 = typename C2<T>::t;
+  set_smem_limits<T>();
+  const FftCfg cy = fft_cfg(c->logLy);
+  const int Ly = 1 << c->logLy;
+  const c2* twy = (const c2*)c->twy;
   prof_mark(c, KC_YSOLVE);
-  {
-    const double h = c->g.h * (double)(1 << g);
-    const dst::SpecParams<T> sp = spec_params<T>(c, h, use_ring ? (const T*)c->ring : nullptr);
-    if (use_gemm<T>(c, 1)) {
-      if constexpr (std::is_same<T, float>::value) {
-        const fsi_status st = gemm_ysolve(c, sp);
-        if (st != FSI_OK) return st;
-      }
-    } else {
-      dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
-      const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-      switch (cy.per) {
-        case 1: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 1>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-        case 2: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 2>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-        default: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 4>, grid, dim3(cy.nthr), sm, c->stream, (const T*)c->T1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-      }
+  const double h = c->g.h * (double)(1 << g);
+  const dst::SpecParams<T> sp = spec_params<T>(c, h, use_ring ? (const T*)c->ring : nullptr);
+  if (use_gemm<T>(c, 1)) {
+    if (t1 != (const T*)c->T1) return FSI_ERR_UNSUPPORTED;  // the tensor-core pass reads slot 0
+    if constexpr (std::is_same<T, float>::value) {
+      const fsi_status st = gemm_ysolve(c, sp);
+      if (st != FSI_OK) return st;
+    }
+  } else {
+    dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
+    const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
+    switch (cy.per) {
+      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 1>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
+      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 2>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
+      default: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 4>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
     }
   }
   prof_mark(c, KC_YSOLVE);
-  // XI: 2*nf rows per CTA; rows j, j+1 of w share one FFT, rows j, j+1 of s another
+  c->launches_per_step += 1;
+  return FSI_OK;
+}
+
+// Pass XI into the level fields w, s (mode 0 store, 1 subtract).  2*nf rows per CTA; rows j, j+1 of w share
+// one FFT, rows j, j+1 of s another.
+template <typename T>
+fsi_status xi_pass(fsi_ctx* c, T* w, T* s, int mode) {
+  using c2 = typename C2<T>::t;
+  set_smem_limits<T>();
+  const FftCfg cx = fft_cfg(c->logLx);
+  const int Lx = 1 << c->logLx;
+  const c2* twx = (const c2*)c->twx;
   prof_mark(c, KC_XI);
   if (use_gemm<T>(c, 2)) {
     const fsi_status st = gemm_xi(c, (float*)w, (float*)s, mode);
@@ -367,8 +391,16 @@ fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ri
   }
   prof_mark(c, KC_XI);
   FSI_CUDA_TRY(cudaGetLastError());
-  c->launches_per_step += 3;
+  c->launches_per_step += 1;
   return FSI_OK;
+}
+
+template <typename T>
+fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ring, int mode) {
+  fsi_status st = xf_pass<T>(c, rhs, 1);
+  if (st == FSI_OK) st = y_pass<T>(c, g, (const T*)c->T1, use_ring);
+  if (st == FSI_OK) st = xi_pass<T>(c, w, s, mode);
+  return st;
 }
 
 template <typename T>
@@ -428,14 +460,29 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
     prof_mark(c, KC_RHS);
   }
   FSI_CUDA_TRY(cudaGetLastError());
+  // The x-transforms need only each level's own right-hand side (the coarser level's solution enters
+  // through the ring terms of pass Y), so the FFT path takes all levels in one launch, each into its own
+  // scratch slot; the chain of dependent launches per step is two shorter for three levels.
+  const bool batch = c->G > 1 && !use_gemm<T>(c, 0) && !use_gemm<T>(c, 1);
+  if (batch) {
+    const fsi_status st = xf_pass<T>(c, (const T*)c->rhs_all, c->G);
+    if (st != FSI_OK) return st;
+  }
   for (int g = c->G - 1; g >= 0; --g) {
     const int ring = g < c->G - 1;
     if (ring) {
       fsi_status st = ring_spectra_t<T>(c, g);
       if (st != FSI_OK) return st;
     }
-    fsi_status st = level_solve_t<T>(c, g, (const T*)c->rhs_all + (long)g * c->lvl_elems,
-                                     w_all + (long)g * c->lvl_elems, s_all + (long)g * c->lvl_elems, ring, 0);
+    T* wg = w_all + (long)g * c->lvl_elems;
+    T* sg = s_all + (long)g * c->lvl_elems;
+    fsi_status st;
+    if (batch) {
+      st = y_pass<T>(c, g, (const T*)c->T1 + (long)g * c->Nx * c->ldT, ring);
+      if (st == FSI_OK) st = xi_pass<T>(c, wg, sg, 0);
+    } else {
+      st = level_solve_t<T>(c, g, (const T*)c->rhs_all + (long)g * c->lvl_elems, wg, sg, ring, 0);
+    }
     if (st != FSI_OK) return st;
   }
   return FSI_OK;
