@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <vector>
+#include "dst.cuh"
 #include "internal.h"
 
 int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c);
@@ -65,13 +66,17 @@ static void ctx_free_all(fsi_ctx* c) {
 
 static bool pow2_ok(int n) { return n >= 16 && (n & (n - 1)) == 0 && n <= 2048; }
 
+// Complex twiddles of length L in the stage order of dst::block_fft (entry p: m = twiddle_exponent(p, log2 L)).
 template <typename T>
 static fsi_status upload_twiddles(fsi_ctx* c, int L, void** out) {
   std::vector<T> tw(2 * (size_t)L);
-  for (int m = 0; m < L; ++m) {
+  int logL = 0;
+  while ((1 << logL) < L) ++logL;
+  for (int p = 0; p < L; ++p) {
+    const int m = dst::twiddle_exponent(p, logL);
     const double a = -2.0 * M_PI * (double)m / (double)L;
-    tw[2 * m] = (T)std::cos(a);
-    tw[2 * m + 1] = (T)std::sin(a);
+    tw[2 * p] = (T)std::cos(a);
+    tw[2 * p + 1] = (T)std::sin(a);
   }
   *out = ctx_alloc(c, tw.size() * sizeof(T));
   if (!*out) return FSI_ERR_OOM;

@@ -213,14 +213,17 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
     tab_n += t;
     if (t > max_tab) max_tab = t;
   }
-  std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);
-  for (int m = 0; m < 2 * Mx; ++m) {
-    twx[2 * m] = std::cos(-M_PI * (double)m / (double)Mx);
-    twx[2 * m + 1] = std::sin(-M_PI * (double)m / (double)Mx);
+  std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);  // stage order of dst::block_fft
+  const int logLx = ilog2_exact(2 * Mx), logLy = ilog2_exact(2 * My);
+  for (int p = 0; p < 2 * Mx; ++p) {
+    const int m = dst::twiddle_exponent(p, logLx);
+    twx[2 * p] = std::cos(-M_PI * (double)m / (double)Mx);
+    twx[2 * p + 1] = std::sin(-M_PI * (double)m / (double)Mx);
   }
-  for (int m = 0; m < 2 * My; ++m) {
-    twy[2 * m] = std::cos(-M_PI * (double)m / (double)My);
-    twy[2 * m + 1] = std::sin(-M_PI * (double)m / (double)My);
+  for (int p = 0; p < 2 * My; ++p) {
+    const int m = dst::twiddle_exponent(p, logLy);
+    twy[2 * p] = std::cos(-M_PI * (double)m / (double)My);
+    twy[2 * p + 1] = std::sin(-M_PI * (double)m / (double)My);
   }
   double *d_twx = nullptr, *d_twy = nullptr, *d_T1 = nullptr, *d_g = nullptr, *d_tab = nullptr;
   B0Box* d_bx = nullptr;

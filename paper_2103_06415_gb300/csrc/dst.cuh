@@ -11,8 +11,27 @@
 
 namespace dst {
 
-// Twiddle table tw[m] = exp(-2 pi i m / L), m < L (host-computed in double); the passes below copy it into
-// shared memory (stage_twiddles) before their first barrier, so the stages read it there.
+// Twiddle table of length L in stage order: entry p holds exp(-2 pi i m / L) with m = twiddle_exponent(p,
+// logL).  A radix-4 stage with ns = 4^s > 1 (s >= 1) reads its three twiddles w_r(k) = exp(-2 pi i r k /
+// (4 ns)), r = 1..3, k < ns, from the block at ns - 4, laid out [r - 1][k]; a final radix-2 stage (odd
+// logL) reads exp(-2 pi i k / L), k < L/2, from the block at L/2 - 4.  The threads of a warp read
+// consecutive k (or the same k), so these shared-memory loads are free of bank conflicts, which the
+// natural-order table (index r k L/(4 ns), a power-of-two stride) is not.  The blocks fill L - 4 entries.
+__host__ __device__ inline int twiddle_exponent(int p, int logL) {
+  for (int logNs = 2; logL - logNs >= 2; logNs += 2) {
+    const int ns = 1 << logNs;
+    const int q = p - (ns - 4);
+    if (q < 3 * ns) return (q / ns + 1) * ((q % ns) << (logL - logNs - 2));
+  }
+  if (logL & 1) {
+    const int q = p - ((1 << (logL - 1)) - 4);
+    if (q >= 0 && q < (1 << (logL - 1))) return q;
+  }
+  return 0;
+}
+
+// The passes below copy the table into shared memory before their first barrier, so the stages read it
+// there.
 template <typename T, int PER>
 __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int logL,
                                           const typename C2<T>::t* __restrict__ tw) {
@@ -38,12 +57,12 @@ __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int log
         const int b = tid + q * nthr;
         const int f = b >> logLr, j = b & (Lr - 1);
         const int k = j & ((1 << logNs) - 1);
-        const int tstep = k << (logL - logNs - 2);
         c2* a = &v[4 * q];
         if (logNs > 0) {
+          const c2* tws = tw + ((1 << logNs) - 4) + k;  // stage block [r - 1][k]
 #pragma unroll
           for (int r = 1; r < 4; ++r) {
-            const c2 w = tw[r * tstep];
+            const c2 w = tws[(r - 1) << logNs];
             const T re = a[r].x * w.x - a[r].y * w.y;
             const T im = a[r].x * w.y + a[r].y * w.x;
             a[r].x = re;
@@ -57,6 +76,12 @@ __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int log
         c2* x = buf + ((long)f << logL);
         const int o = ((j >> logNs) << (logNs + 2)) + k;
         const int ns = 1 << logNs;
+        if (sizeof(T) == 4 && logNs == 0) {  // the four outputs are adjacent: two 16-byte stores
+          float4* x4 = reinterpret_cast<float4*>(x + o);
+          x4[0] = make_float4(a0x + a2x, a0y + a2y, a1x + dy, a1y - dx);
+          x4[1] = make_float4(a0x - a2x, a0y - a2y, a1x - dy, a1y + dx);
+          continue;
+        }
         x[o].x = a0x + a2x;
         x[o].y = a0y + a2y;
         x[o + ns].x = a1x + dy;
@@ -87,7 +112,7 @@ __device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int log
         const int k = j & ((1 << logNs) - 1);
         c2 a0 = v[2 * q], a1 = v[2 * q + 1];
         if (logNs > 0) {
-          const c2 w = tw[k << (logL - logNs - 1)];
+          const c2 w = tw[(1 << (logL - 1)) - 4 + k];  // logNs = logL - 1: the final radix-2 stage
           const T re = a1.x * w.x - a1.y * w.y;
           const T im = a1.x * w.y + a1.y * w.x;
           a1.x = re;

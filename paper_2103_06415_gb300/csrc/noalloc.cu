@@ -28,20 +28,21 @@ unsigned char* g_scratch_dev[kMaxDevices] = {nullptr};
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Tables for one call: twiddles exp(-2 pi i m / L) for both lengths and lambda_k = 4 sin^2(pi k / 2M).
+// Tables for one call: twiddles exp(-2 pi i m / L) for both lengths (stage order of dst::block_fft) and
+// lambda_k = 4 sin^2(pi k / 2M).
 template <typename T>
-__global__ void k_noalloc_tables(typename C2<T>::t* twx, int Lx, typename C2<T>::t* twy, int Ly, T* lx,
-                                 int Mx, T* ly, int My) {
+__global__ void k_noalloc_tables(typename C2<T>::t* twx, int Lx, int logLx, typename C2<T>::t* twy, int Ly,
+                                 int logLy, T* lx, int Mx, T* ly, int My) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < Lx) {
     double s, c;
-    sincospi(-2.0 * (double)t / (double)Lx, &s, &c);
+    sincospi(-2.0 * (double)dst::twiddle_exponent(t, logLx) / (double)Lx, &s, &c);
     twx[t].x = (T)c;
     twx[t].y = (T)s;
   }
   if (t < Ly) {
     double s, c;
-    sincospi(-2.0 * (double)t / (double)Ly, &s, &c);
+    sincospi(-2.0 * (double)dst::twiddle_exponent(t, logLy) / (double)Ly, &s, &c);
     twy[t].x = (T)c;
     twy[t].y = (T)s;
   }
@@ -136,7 +137,7 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
   T* lx = reinterpret_cast<T*>(base + off[5]);
   T* ly = reinterpret_cast<T*>(base + off[6]);
   const int nt = (Lx > Ly ? Lx : Ly) + 1;
-  k_noalloc_tables<T><<<(nt + 255) / 256, 256, 0, st>>>(twx, Lx, twy, Ly, lx, Mx, ly, My);
+  k_noalloc_tables<T><<<(nt + 255) / 256, 256, 0, st>>>(twx, Lx, logLx, twy, Ly, logLy, lx, Mx, ly, My);
   const Shape cx = shape_for(logLx), cy = shape_for(logLy);
   {  // forward x, transposed into T1
     dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf));
