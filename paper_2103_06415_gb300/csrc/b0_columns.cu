@@ -145,8 +145,8 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
       else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
     }
     {
-      dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
-      const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
+      dim3 grid(dst::xi_blocks(Ny, cx.nf), nc);
+      const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
       if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
       else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
       else dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);

@@ -466,7 +466,8 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
 
 // Pass XI: rows j of inw and ins (length N = Nx) -> DST along x -> w, s rows written to the level fields
 // (row j+1, columns 1..N of a vertex array with row stride f_ld).  mode 0: store, 1: subtract.
-// A CTA takes 2*nf rows; rows j, j+1 of w share one FFT (buffer f), rows j, j+1 of s another (nf + f).
+// blockIdx.x = 2 * (row block) + field: a CTA takes 2*nf rows of one field (0: w, 1: s), so w and s run on
+// different CTAs (twice the CTAs, one transform buffer per row pair); rows j, j+1 share one FFT.
 template <typename T, int PER>
 __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* __restrict__ ins, long in_ld,
                                             long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
@@ -479,15 +480,14 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
   const int L = 1 << logL;
   const int tid = threadIdx.x, nthr = blockDim.x;
   TwiddleStage<T, 4 * PER> ts;
-  ts.load(tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
+  ts.load(tw, L, ((size_t)nf + 1) * L * sizeof(c2));
   pdl_enter();
-  const int row0 = blockIdx.x * 2 * nf;
-  inw += (long)blockIdx.y * in_bs;
-  ins += (long)blockIdx.y * in_bs;
-  fw += (long)blockIdx.y * f_bs;
-  fs += (long)blockIdx.y * f_bs;
-  // mode 1 subtracts from the fields: the old values under the first pair of rows load with the inputs
-  T old[NC][4];
+  const int field = blockIdx.x & 1;
+  const int row0 = (blockIdx.x >> 1) * 2 * nf;
+  const T* in = (field ? ins : inw) + (long)blockIdx.y * in_bs;
+  T* fo = (field ? fs : fw) + (long)blockIdx.y * f_bs;
+  // mode 1 subtracts from the field: the old values under the first pair of rows load with the inputs
+  T old[NC][2];
   if (mode != 0) {
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
@@ -495,64 +495,53 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const bool ok = i < N && row0 + e < nrows;
-        const long o = (long)(row0 + e + 1) * f_ld + 1 + i;
-        old[m][e] = ok ? fw[o] : T(0);
-        old[m][2 + e] = ok ? fs[o] : T(0);
+        old[m][e] = ok ? fo[(long)(row0 + e + 1) * f_ld + 1 + i] : T(0);
       }
     }
   }
-  zero_ends<T>(buf, 2 * nf, L);
+  zero_ends<T>(buf, nf, L);
   for (int f = 0; f < nf; ++f) {
     const int r0 = row0 + 2 * f;
-    const bool v0 = r0 < nrows, v1 = r0 + 1 < nrows;
-    T a[NC], b[NC], c[NC], d[NC];
+    T a[NC], b[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int n = tid + m * nthr;
-      a[m] = (n < N && v0) ? inw[(long)r0 * in_ld + n] : T(0);
-      b[m] = (n < N && v1) ? inw[(long)(r0 + 1) * in_ld + n] : T(0);
-      c[m] = (n < N && v0) ? ins[(long)r0 * in_ld + n] : T(0);
-      d[m] = (n < N && v1) ? ins[(long)(r0 + 1) * in_ld + n] : T(0);
+      a[m] = (n < N && r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
+      b[m] = (n < N && r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
     }
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int n = tid + m * nthr;
-      if (n < N) {
-        put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
-        put_pair<T>(buf + (long)(nf + f) * L, L, n, c[m], d[m]);
-      }
+      if (n < N) put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
     }
   }
-  const c2* tws = ts.store(buf + 2L * nf * L, tw, L);
+  const c2* tws = ts.store(buf + (long)nf * L, tw, L);
   __syncthreads();
-  block_fft<T, 2 * PER>(buf, L, logL, tws);
+  block_fft<T, PER>(buf, L, logL, tws);
   for (int f = 0; f < nf; ++f) {
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int i = tid + m * nthr;
       if (i >= N) continue;
-      const c2 zw = buf[(long)f * L + i + 1];
-      const c2 zs = buf[(long)(nf + f) * L + i + 1];
+      const c2 z = buf[(long)f * L + i + 1];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int r = row0 + 2 * f + e;
         if (r >= nrows) continue;
         const long o = (long)(r + 1) * f_ld + 1 + i;
-        const T w = e ? T(0.5) * zw.x : T(-0.5) * zw.y;
-        const T s = e ? T(0.5) * zs.x : T(-0.5) * zs.y;
-        if (mode == 0) {
-          fw[o] = w;
-          fs[o] = s;
-        } else if (f == 0) {
-          fw[o] = old[m][e] - w;
-          fs[o] = old[m][2 + e] - s;
-        } else {
-          fw[o] -= w;
-          fs[o] -= s;
-        }
+        const T v = e ? T(0.5) * z.x : T(-0.5) * z.y;
+        if (mode == 0)
+          fo[o] = v;
+        else if (f == 0)
+          fo[o] = old[m][e] - v;
+        else
+          fo[o] -= v;
       }
     }
   }
 }
+
+// CTAs of pass XI for nrows rows: a row block per field.
+inline unsigned xi_blocks(int nrows, int nf) { return 2u * (unsigned)((nrows + 2 * nf - 1) / (2 * nf)); }
 
 }  // namespace dst

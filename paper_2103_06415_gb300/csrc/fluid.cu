@@ -367,8 +367,8 @@ fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
   return FSI_OK;
 }
 
-// Pass XI into the level fields w, s (mode 0 store, 1 subtract).  2*nf rows per CTA; rows j, j+1 of w share
-// one FFT, rows j, j+1 of s another.
+// Pass XI into the level fields w, s (mode 0 store, 1 subtract): 2*nf rows of one field per CTA, rows
+// j, j+1 sharing one FFT.
 template <typename T>
 fsi_status xi_pass(fsi_ctx* c, T* w, T* s, int mode) {
   using c2 = typename C2<T>::t;
@@ -381,8 +381,8 @@ fsi_status xi_pass(fsi_ctx* c, T* w, T* s, int mode) {
     const fsi_status st = gemm_xi(c, (float*)w, (float*)s, mode);
     if (st != FSI_OK) return st;
   } else {
-    dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), 1);
-    const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
+    dim3 grid(dst::xi_blocks(c->Ny, cx.nf), 1);
+    const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     switch (cx.per) {
       case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 1>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
       case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 2>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;

@@ -165,8 +165,8 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
     else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
   }
   {  // inverse x into the interior of the caller's vertex arrays (row stride nx + 1)
-    dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf));
-    const size_t sm = dst::pass_smem<T>((size_t)2 * cx.nf * Lx, Lx);
+    dim3 grid(dst::xi_blocks(Ny, cx.nf));
+    const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     const long fld = nx + 1;
     if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, st>>>(T2w, T2s, ldX, 0, Ny, Nx, w, s, fld, 0, 0, twx, logLx, cx.nf);
     else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, st>>>(T2w, T2s, ldX, 0, Ny, Nx, w, s, fld, 0, 0, twx, logLx, cx.nf);
