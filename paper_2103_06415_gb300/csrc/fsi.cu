@@ -418,6 +418,32 @@ __device__ void load_x(float* Xs, const float* src, int nf, int ldx, uint64_t* b
 // Barrier of warps 4-7 only (named barrier 1), used while warps 0-3 work on the body points.
 __device__ __forceinline__ void named_sync_upper() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// Barrier of warps 0-3 only (named barrier 2), used while warps 4-7 work on the flags.
+__device__ __forceinline__ void named_sync_lower() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+// Barrier of warps 0-3 of every CTA while warps 4-7 still work on the flags: named barrier 2 inside the CTA,
+// an arrival counter in global memory across CTAs (all CTAs of the cooperative launch are resident).  The
+// counter grows by gridDim.x per use (target = uses so far * gridDim.x) and CTA 0 resets it at the end of
+// the launch.  A wait that does not end within the limit records FSI_ERR_TIMEOUT and goes on, so that every
+// CTA keeps to the same sequence of barriers.
+__device__ void lower_grid_barrier(int* cnt, int target, int* status) {
+  named_sync_lower();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1);
+    unsigned spins = 0;
+    while (*(volatile int*)cnt < target) {
+      if (++spins > (1u << 22)) {
+        dev_set_status(status, FSI_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  named_sync_lower();
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -575,6 +601,100 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   PhaseClock clk(sh_phase, blockIdx.x == 0 && tid == 0 && a.phase_ns);
   __syncthreads();
 
+  // Entries e0, e0 + stride, ... of K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (double and float copies;
+  // both triangles from the lower one for the dense B0, every entry for the sparse B0', which is not
+  // symmetric).  with_g = false leaves out the flags' (2 ds/dt) T J_d^-1 T^T, which add_flag_g adds later.
+  const bool dense = a.Bw == nullptr;
+  auto assemble = [&](long e0, long stride, bool with_g) {
+    const double kscale = a.ds / (a.h * a.h);
+    const long n2 = 2L * a.n_sd;
+    const int bw = a.bw, side = 2 * bw + 1;
+    const long carea = (long)side * side;
+    for (long e = e0; e < (long)nf * nf; e += stride) {
+      const int r = (int)(e / nf), cidx = (int)(e % nf);
+      if (dense && cidx > r) continue;
+      const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
+      double acc = 0.0;
+      int ib[4];
+      double wb[4];
+#pragma unroll
+      for (int be = 0; be < 4; ++be) {
+        ib[be] = pidx_s[4 * pb + be];
+        wb[be] = pw_s[4 * pb + be];
+      }
+      if (dense) {
+        for (int al = 0; al < 4; ++al) {
+          const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
+          const double wa = pw_s[4 * pa + al];
+          const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
+          double t = 0.0;
+#pragma unroll
+          for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
+          acc += wa * t;
+        }
+      } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
+        const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
+        for (int al = 0; al < 4; ++al) {
+          const double wa = pw_s[4 * pa + al];
+          double t = 0.0;
+#pragma unroll
+          for (int be = 0; be < 4; ++be) {
+            const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+            if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
+              t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
+                                 (long)(dj + bw) * side + (di + bw)];
+          }
+          acc += wa * t;
+        }
+      }
+      double kv = kscale * acc;
+      const int ba = a.point_body[pa], bbd = a.point_body[pb];
+      if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
+        const BodyDev b = a.bodies[ba];
+        const double sn = b_sn[ba], cs = b_cs[ba];
+        const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
+        const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
+        kv += b_kc[ba] * sa * sb;
+      } else if (with_g && ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
+        // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
+        kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
+      }
+      a.K[(long)r * nf + cidx] = kv;
+      a.S[(long)r * lx + cidx] = (float)kv;
+      if (dense) {
+        a.K[(long)cidx * nf + r] = kv;
+        a.S[(long)cidx * lx + r] = (float)kv;
+      }
+    }
+  };
+  // The flags' (2 ds/dt) T J_d^-1 T^T added to the entries assemble(.., with_g = false) wrote (all threads,
+  // after a grid barrier: the columns of G and those entries come from other CTAs).
+  auto add_flag_g = [&]() {
+    for (int bi = 0; bi < a.n_bodies; ++bi) {
+      const BodyDev b = a.bodies[bi];
+      if (b.type != FSI_BODY_DEFORMABLE) continue;
+      const long m = 2L * b.n;
+      for (long e = gtid; e < m * m; e += gsize) {
+        const int rl = (int)(e / m), cl = (int)(e % m);
+        const int r = rl < b.n ? b.off + rl : nb + b.off + rl - b.n;
+        const int cidx = cl < b.n ? b.off + cl : nb + b.off + cl - b.n;
+        if (dense && cidx > r) continue;
+        const double kv = __ldcg(&a.K[(long)r * nf + cidx]) +
+                          a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
+        a.K[(long)r * nf + cidx] = kv;
+        a.S[(long)r * lx + cidx] = (float)kv;
+        if (dense) {
+          a.K[(long)cidx * nf + r] = kv;
+          a.S[(long)cidx * lx + r] = (float)kv;
+        }
+      }
+    }
+  };
+  // With flags, warps 0-3 assemble the P B0 P^T part of K under the flags' structural work on warps 4-7
+  // (which takes longer than the body points): after a barrier of warps 0-3 only, since the published
+  // points are all that part needs.
+  const bool overlap_b = a.n_def > 0;
+
   bool converged = false;
   int it = 0, solves_total = 0, refreshes = 0;
   for (; it < a.max_iters; ++it) {
@@ -700,6 +820,16 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
       }
       if (side_clock && tid == 0) sh_phase[14] += PhaseClock::now() - ta0;
+      if (overlap_b && wid < 4) {
+        lower_grid_barrier(&a.ctrl[15], (it + 1) * (int)gridDim.x, a.status);
+        for (int e = tid; e < 4 * nb; e += 128) {
+          pidx_s[e] = __ldcg(&a.pidx[e]);
+          pw_s[e] = __ldcg(&a.pw[e]);
+        }
+        for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
+        named_sync_lower();
+        assemble((long)blockIdx.x * 128 + tid, (long)gridDim.x * 128, false);
+      }
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
         // r^zeta(k), J_d blocks, the factorization, y = J_d^-1 (r^zeta(k) + ds T^T f_prev) and the structural
@@ -763,11 +893,13 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
     }
     grid.sync();
-    for (int e = tid; e < 4 * nb; e += nthr) {
-      pidx_s[e] = __ldcg(&a.pidx[e]);
-      pw_s[e] = __ldcg(&a.pw[e]);
+    if (!overlap_b) {
+      for (int e = tid; e < 4 * nb; e += nthr) {
+        pidx_s[e] = __ldcg(&a.pidx[e]);
+        pw_s[e] = __ldcg(&a.pw[e]);
+      }
+      for (int e = tid; e < 2 * nb; e += nthr) pcij_s[e] = __ldcg(&a.pcij[e]);
     }
-    for (int e = tid; e < 2 * nb; e += nthr) pcij_s[e] = __ldcg(&a.pcij[e]);
     for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
     __syncthreads();
     if (a.n_def > 0) {  // flags: rhs -= T ((2/dt)(chi^(k) + y) - r^chi_n)
@@ -784,71 +916,11 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       __syncthreads();
     }
     clk.mark(0);
-    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (double and float copies; both triangles from
-    // the lower one for the dense B0, every entry for the sparse B0', which is not symmetric)
-    {
-      const double kscale = a.ds / (a.h * a.h);
-      const long n2 = 2L * a.n_sd;
-      const bool dense = a.Bw == nullptr;
-      const int bw = a.bw, side = 2 * bw + 1;
-      const long carea = (long)side * side;
-      for (long e = gtid; e < (long)nf * nf; e += gsize) {
-        const int r = (int)(e / nf), cidx = (int)(e % nf);
-        if (dense && cidx > r) continue;
-        const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
-        double acc = 0.0;
-        int ib[4];
-        double wb[4];
-#pragma unroll
-        for (int be = 0; be < 4; ++be) {
-          ib[be] = pidx_s[4 * pb + be];
-          wb[be] = pw_s[4 * pb + be];
-        }
-        if (dense) {
-          for (int al = 0; al < 4; ++al) {
-            const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
-            const double wa = pw_s[4 * pa + al];
-            const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
-            double t = 0.0;
-#pragma unroll
-            for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
-            acc += wa * t;
-          }
-        } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
-          const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
-          for (int al = 0; al < 4; ++al) {
-            const double wa = pw_s[4 * pa + al];
-            double t = 0.0;
-#pragma unroll
-            for (int be = 0; be < 4; ++be) {
-              const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
-              if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
-                t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
-                                   (long)(dj + bw) * side + (di + bw)];
-            }
-            acc += wa * t;
-          }
-        }
-        double kv = kscale * acc;
-        const int ba = a.point_body[pa], bbd = a.point_body[pb];
-        if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
-          const BodyDev b = a.bodies[ba];
-          const double sn = b_sn[ba], cs = b_cs[ba];
-          const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
-          const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
-          kv += b_kc[ba] * sa * sb;
-        } else if (ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
-          // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
-          kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
-        }
-        a.K[(long)r * nf + cidx] = kv;
-        a.S[(long)r * lx + cidx] = (float)kv;
-        if (dense) {
-          a.K[(long)cidx * nf + r] = kv;
-          a.S[(long)cidx * lx + r] = (float)kv;
-        }
-      }
-    }
+    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (with flags, only the flags' term is left here)
+    if (overlap_b)
+      add_flag_g();
+    else
+      assemble(gtid, gsize, true);
     grid.sync();
     for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
     // Flags.  The structural right-hand side was formed from J_d^-1 (r^zeta(k) + ds T^T f_prev) instead of
@@ -1137,6 +1209,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
 
   // ---- Newmark update, forces, history (CTA 0)
   if (blockIdx.x == 0) {
+    // every CTA passed its last barrier of warps 0-3 before the grid barrier that followed it
+    if (tid == 0) a.ctrl[15] = 0;
     if (tid == 0 && !converged) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
     for (int k = tid; k < nf; k += nthr) a.f[k] = f_s[k];  // surface stress for the corrector
     const int slot = a.ctrl[2] % a.hist_cap;
