@@ -20,8 +20,9 @@
 // and for the columns T J_d^-1 T^T e_r of the rows the CTA owns (published for B).  Meanwhile warps 0-3,
 // once every CTA's warps 0-3 have published their points (a barrier of their own), assemble the
 // (ds/h^2) P B0 P^T part of K; after the A barrier every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from
-// the right-hand side, and B only adds (2 ds/dt) T J_d^-1 T^T to the flags' entries of K; C starts from f_prev with the residual rows rhs + (2 ds/dt) T J_d^-1 T^T f_prev - K f_prev (the
-// same system as Eq. stress2, in a form whose FP32 structural solves act on vanishing residuals); D solves
+// the right-hand side, and B only adds (2 ds/dt) T J_d^-1 T^T to the flags' entries of K; C starts from
+// f_prev with the residual rows rhs + (2 ds/dt) T J_d^-1 T^T f_prev - K f_prev (the same system as
+// Eq. stress2, in a form whose FP32 structural solves act on vanishing residuals); D solves
 // dchi = J_d^-1 (r^zeta(k) + ds T^T f) (Eq. dchi2) and the convergence test takes max |dchi| as well.
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
