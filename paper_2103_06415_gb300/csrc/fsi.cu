@@ -603,98 +603,68 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   PhaseClock clk(sh_phase, blockIdx.x == 0 && tid == 0 && a.phase_ns);
   __syncthreads();
 
-  // Entries e0, e0 + stride, ... of K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (double and float copies;
-  // both triangles from the lower one for the dense B0, every entry for the sparse B0', which is not
-  // symmetric).  with_g = false leaves out the flags' (2 ds/dt) T J_d^-1 T^T, which add_flag_g adds later.
+  // Entry (r, c) of K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S; with_g = false leaves out the flags'
+  // (2 ds/dt) T J_d^-1 T^T.
   const bool dense = a.Bw == nullptr;
-  auto assemble = [&](long e0, long stride, bool with_g) {
+  auto k_entry = [&](int r, int cidx, bool with_g) -> double {
     const double kscale = a.ds / (a.h * a.h);
     const long n2 = 2L * a.n_sd;
     const int bw = a.bw, side = 2 * bw + 1;
     const long carea = (long)side * side;
-    for (long e = e0; e < (long)nf * nf; e += stride) {
-      const int r = (int)(e / nf), cidx = (int)(e % nf);
-      if (dense && cidx > r) continue;
-      const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
-      double acc = 0.0;
-      int ib[4];
-      double wb[4];
+    const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
+    double acc = 0.0;
+    int ib[4];
+    double wb[4];
 #pragma unroll
-      for (int be = 0; be < 4; ++be) {
-        ib[be] = pidx_s[4 * pb + be];
-        wb[be] = pw_s[4 * pb + be];
+    for (int be = 0; be < 4; ++be) {
+      ib[be] = pidx_s[4 * pb + be];
+      wb[be] = pw_s[4 * pb + be];
+    }
+    if (dense) {
+      for (int al = 0; al < 4; ++al) {
+        const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
+        const double wa = pw_s[4 * pa + al];
+        const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
+        double t = 0.0;
+#pragma unroll
+        for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
+        acc += wa * t;
       }
-      if (dense) {
-        for (int al = 0; al < 4; ++al) {
-          const long row = (long)ca * a.n_sd + pidx_s[4 * pa + al];
-          const double wa = pw_s[4 * pa + al];
-          const double* brow = a.B0 + row * n2 + (long)cb * a.n_sd;
-          double t = 0.0;
+    } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
+      const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
+      for (int al = 0; al < 4; ++al) {
+        const double wa = pw_s[4 * pa + al];
+        double t = 0.0;
 #pragma unroll
-          for (int be = 0; be < 4; ++be) t += wb[be] * brow[ib[be]];
-          acc += wa * t;
+        for (int be = 0; be < 4; ++be) {
+          const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+          if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
+            t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
+                               (long)(dj + bw) * side + (di + bw)];
         }
-      } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
-        const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
-        for (int al = 0; al < 4; ++al) {
-          const double wa = pw_s[4 * pa + al];
-          double t = 0.0;
-#pragma unroll
-          for (int be = 0; be < 4; ++be) {
-            const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
-            if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
-              t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
-                                 (long)(dj + bw) * side + (di + bw)];
-          }
-          acc += wa * t;
-        }
-      }
-      double kv = kscale * acc;
-      const int ba = a.point_body[pa], bbd = a.point_body[pb];
-      if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
-        const BodyDev b = a.bodies[ba];
-        const double sn = b_sn[ba], cs = b_cs[ba];
-        const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
-        const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
-        kv += b_kc[ba] * sa * sb;
-      } else if (with_g && ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
-        // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
-        kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
-      }
-      a.K[(long)r * nf + cidx] = kv;
-      a.S[(long)r * lx + cidx] = (float)kv;
-      if (dense) {
-        a.K[(long)cidx * nf + r] = kv;
-        a.S[(long)cidx * lx + r] = (float)kv;
+        acc += wa * t;
       }
     }
-  };
-  // The flags' (2 ds/dt) T J_d^-1 T^T added to the entries assemble(.., with_g = false) wrote (all threads,
-  // after a grid barrier: the columns of G and those entries come from other CTAs).
-  auto add_flag_g = [&]() {
-    for (int bi = 0; bi < a.n_bodies; ++bi) {
-      const BodyDev b = a.bodies[bi];
-      if (b.type != FSI_BODY_DEFORMABLE) continue;
-      const long m = 2L * b.n;
-      for (long e = gtid; e < m * m; e += gsize) {
-        const int rl = (int)(e / m), cl = (int)(e % m);
-        const int r = rl < b.n ? b.off + rl : nb + b.off + rl - b.n;
-        const int cidx = cl < b.n ? b.off + cl : nb + b.off + cl - b.n;
-        if (dense && cidx > r) continue;
-        const double kv = __ldcg(&a.K[(long)r * nf + cidx]) +
-                          a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
-        a.K[(long)r * nf + cidx] = kv;
-        a.S[(long)r * lx + cidx] = (float)kv;
-        if (dense) {
-          a.K[(long)cidx * nf + r] = kv;
-          a.S[(long)cidx * lx + r] = (float)kv;
-        }
-      }
+    double kv = kscale * acc;
+    const int ba = a.point_body[pa], bbd = a.point_body[pb];
+    if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
+      const BodyDev b = a.bodies[ba];
+      const double sn = b_sn[ba], cs = b_cs[ba];
+      const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
+      const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
+      kv += b_kc[ba] * sa * sb;
+    } else if (with_g && ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
+      // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
+      kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
     }
+    return kv;
   };
-  // With flags, warps 0-3 assemble the P B0 P^T part of K under the flags' structural work on warps 4-7
-  // (which takes longer than the body points): after a barrier of warps 0-3 only, since the published
-  // points are all that part needs.
+  // With flags, K is assembled by owned rows: warps 0-3 compute the rows of their CTA without the flags'
+  // term under the flags' structural work on warps 4-7 (which takes longer than the body points), after a
+  // barrier of warps 0-3 only (the published points are all this needs); the flags' term then comes from
+  // the CTA's own columns of T J_d^-1 T^T (entry (r, c) from column r), and the rows are published before
+  // the grid barrier that ends phase A, so phase B needs no barrier of its own.  Without flags, every
+  // thread takes entries of the lower triangle (dense B0, both triangles written) or all entries (B0').
   const bool overlap_b = a.n_def > 0;
 
   bool converged = false;
@@ -830,7 +800,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
         for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
         named_sync_lower();
-        assemble((long)blockIdx.x * 128 + tid, (long)gridDim.x * 128, false);
+        for (int e = tid; e < nr * nf; e += 128) Krow[e] = k_entry(r0 + e / nf, e % nf, false);
       }
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
@@ -894,6 +864,19 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         if (side_clock) sh_phase[15] += PhaseClock::now() - ta0;
       }
     }
+    if (overlap_b) {  // owned rows: the flags' term from this CTA's columns of T J_d^-1 T^T, then publish
+      __syncthreads();
+      for (int e = tid; e < nr * nf; e += nthr) {
+        const int r = r0 + e / nf, cidx = e % nf;
+        double kv = Krow[e];
+        const int ba = a.point_body[r % nb];
+        if (ba == a.point_body[cidx % nb] && a.bodies[ba].type == FSI_BODY_DEFORMABLE)
+          kv += a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
+        Krow[e] = kv;
+        a.K[(long)r * nf + cidx] = kv;
+        a.S[(long)r * lx + cidx] = (float)kv;
+      }
+    }
     grid.sync();
     if (!overlap_b) {
       for (int e = tid; e < 4 * nb; e += nthr) {
@@ -918,13 +901,22 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       __syncthreads();
     }
     clk.mark(0);
-    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (with flags, only the flags' term is left here)
-    if (overlap_b)
-      add_flag_g();
-    else
-      assemble(gtid, gsize, true);
-    grid.sync();
-    for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
+    // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (with flags already assembled by owned rows)
+    if (!overlap_b) {
+      for (long e = gtid; e < (long)nf * nf; e += gsize) {
+        const int r = (int)(e / nf), cidx = (int)(e % nf);
+        if (dense && cidx > r) continue;
+        const double kv = k_entry(r, cidx, true);
+        a.K[(long)r * nf + cidx] = kv;
+        a.S[(long)r * lx + cidx] = (float)kv;
+        if (dense) {
+          a.K[(long)cidx * nf + r] = kv;
+          a.S[(long)cidx * lx + r] = (float)kv;
+        }
+      }
+      grid.sync();
+      for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
+    }
     // Flags.  The structural right-hand side was formed from J_d^-1 (r^zeta(k) + ds T^T f_prev) instead of
     // J_d^-1 r^zeta(k); the two differ by (2 ds/dt) T J_d^-1 T^T f_prev, which the owned residual rows add
     // back here with the same entries of T J_d^-1 T^T that K holds.  Both FP32 structural solves then act
@@ -939,7 +931,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           if (b.type == FSI_BODY_DEFORMABLE)
             for (int q = lane; q < 2 * b.n; q += 32) {
               const int m = q < b.n ? b.off + q : nb + b.off + q - b.n;
-              const long gi = r < m ? (long)r * nf + m : (long)m * nf + r;  // the entry phase B used
+              // the entry K holds: column r (owned-row assembly) or column min(r, m) (lower triangle)
+              const long gi = overlap_b || r < m ? (long)r * nf + m : (long)m * nf + r;
               acc += __ldcg(&a.G[gi]) * f_s[m];
             }
         }
