@@ -518,7 +518,7 @@ def main():
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
                 "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                         "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-                "traffic": 2.71e6,
+                "traffic": 3.80e6,
                 "traffic_note": "dram read+write bytes per launch from one ncu capture of the same kernel on "
                                 "the reduced-Omega_0 variant of the flag workload (same nf and flag; the B0 "
                                 "gathers of the same point set dominate it; "
