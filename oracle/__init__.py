@@ -23,9 +23,13 @@ Module map
   kinematics.py -- prescribed heave/pitch of a driven plate and the passive plate hinged to it
               (Sec. 5.1, Eq. newtonseldg)
 
-Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-except the multidomain level coupling, which is only pinned loosely (Lamb-Oseen
-convergence); see the header of ``grid.py``.
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``.
+The multidomain level coupling is pinned by a Lamb-Oseen vortex
+(``tests/test_oracle_multidomain.py``): error against the closed form falling
+with the number of levels and at second order in h and in dt, the coarse level
+carrying the fine level's accuracy inside it, and the finer rings holding the
+coarser level at the same time; each of those fails for a planted wrong sweep
+order, ring time level or injection order.
 """
 
 from . import grid, ib, fsi, beam, kinematics  # noqa: F401

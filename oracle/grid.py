@@ -26,9 +26,13 @@ Multidomain (Sec. 5 intro, Colonius & Taira far-field scheme; reading R5):
 coarse vorticity strictly inside a finer level is replaced by injection from the
 coincident fine vertex; the coarsest level has zero boundary values; every other
 level takes its boundary ``w`` and ``s`` from the next coarser level (injection
-at coincident vertices, linear interpolation at midpoints).  Parity of this
-coupling against an outside reference is only loosely pinned (Lamb-Oseen
-convergence test); everything else in this file is pinned exactly.
+at coincident vertices, linear interpolation at midpoints).  Each step the
+sweep runs coarse to fine, so a finer level's ring holds the coarser level at
+t^{n+1}.  The coupling is pinned by a Lamb-Oseen vortex, an exact
+Navier-Stokes solution (``tests/test_oracle_multidomain.py``: error vs the
+number of levels, second order in h and in dt, fine accuracy of the coarse
+level inside the finer one, rings at the new time); the rest of this file by
+``tests/test_oracle_pins.py``.
 """
 
 import numpy as np
