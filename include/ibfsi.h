@@ -276,6 +276,23 @@ fsi_status fsi_get_interp(fsi_ctx* ctx, int64_t* idx, double* w, int cap_points)
 
 fsi_status fsi_get_stats(fsi_ctx* ctx, fsi_stats* out);
 
+/* The small system K of the last FSI iteration (Eq. stress2: (ds/h^2) P B0 P^T plus the structural terms of
+ * the bodies; unknown ordering: the x-components of all body points in body order, then the y-components),
+ * row-major nf x nf doubles into out (cap >= nf*nf values; *nf_out receives nf; synchronising).  With the
+ * dense B0 and no deformable body K is symmetric; a deformable body's FP32 structural columns and the sparse
+ * B0' make it symmetric only to rounding, or not at all.  coupling 1 or before the first step (no K):
+ * FSI_ERR_STATE; cap too small: FSI_ERR_INVALID_ARG. */
+fsi_status fsi_get_small_system(fsi_ctx* ctx, double* out, int64_t cap, int* nf_out);
+
+/* Failure-detection hook (not part of the method): the FSI kernel's cross-CTA wait of the warps that assemble
+ * the small system while the flags are linearised (used with DEFORMABLE bodies) polls a global arrival
+ * counter a bounded number of times and latches FSI_ERR_TIMEOUT when the bound is reached.  This sets the
+ * bound (polls of about 64 ns; 0 restores the default, about 4 M polls) and a number of arrivals the wait
+ * requires beyond the kernel's own (0 in normal runs; > 0 makes every such wait run out, as if CTAs had
+ * stopped arriving, without any fault).  Takes effect from the next step (a captured step graph is
+ * rebuilt).  missing_arrivals outside [0, 1024]: FSI_ERR_INVALID_ARG.  Synchronising. */
+fsi_status fsi_debug_set_wait_limit(fsi_ctx* ctx, unsigned spin_limit, int missing_arrivals);
+
 /* Tracing: accumulated wall time (ms) of the phases of the FSI-iteration kernel since the context was
  * created, measured on the device: 0 body points / P / right-hand side, 1 assembly of P B0 P^T, 2 refresh
  * of the float inverse, 3 rebuild of the float inverse, 4 refinement solves, 5 double residuals,

@@ -38,7 +38,9 @@ fsi_status fsi_op_level_solve_ex(int precision, int dst_method, int nx, int ny, 
  * sizes needing more -- e.g. FP64 above 512 x 512, FP32 above 1024 x 512 -- return FSI_ERR_UNSUPPORTED with
  * the reason in fsi_last_error_message.  No device memory is allocated or freed by this call.
  * The first call on a device takes the scratch address (cudaGetSymbolAddress) and sets kernel attributes;
- * make that first call before any stream capture.  All calls share the scratch array: calls whose work
+ * make that first call before any stream capture.  The address and attributes are cached per device for the
+ * life of the process: after cudaDeviceReset (or any teardown of the device's primary context) they are
+ * stale, so do not call this entry point again in that process.  All calls share the scratch array: calls whose work
  * overlaps on the GPU race and must be ordered by the caller (one stream, or events). */
 fsi_status fsi_op_level_solve_noalloc(int precision, int nx, int ny, double h, double re, double dt,
                                       const void* rhs_dev, void* w_dev, void* s_dev, void* stream);

@@ -247,6 +247,14 @@ class Context:
         out["dst_us"] = {"fft": list(s.dst_us)[:3], "gemm": list(s.dst_us)[3:]}
         return out
 
+    def small_system(self):
+        """K of the last FSI iteration (Eq. stress2), nf x nf, x-components of all points then y."""
+        nf = self.stats()["nf"]
+        out = np.zeros((nf, nf))
+        n = ctypes.c_int()
+        check(self._lib.fsi_get_small_system(self._h, _dp(out), nf * nf, ctypes.byref(n)), "fsi_get_small_system")
+        return out
+
 
 class B0Set:
     """B0 of several independent Omega_0 boxes on one grid, built together (``fsi_b0_set_build``).

@@ -90,6 +90,8 @@ SIGNATURES = {
     "fsi_factor_operator": (_INT, [_P, ctypes.c_double, _D, _D]),
     "fsi_get_factor_entries": (_INT, [_P, _I64, _I64, _INT, _D]),
     "fsi_get_stats": (_INT, [_P, ctypes.POINTER(Stats)]),
+    "fsi_get_small_system": (_INT, [_P, _D, ctypes.c_int64, ctypes.POINTER(_INT)]),
+    "fsi_debug_set_wait_limit": (_INT, [_P, ctypes.c_uint, _INT]),
     "fsi_profile_kernel": (_INT, [_P, _INT, _INT, _D, ctypes.POINTER(_INT)]),
     "fsi_get_phase_times": (_INT, [_P, _D, _INT]),
     "fsi_destroy": (None, [_P]),

@@ -981,6 +981,31 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   return FSI_OK;
 }
 
+extern "C" fsi_status fsi_debug_set_wait_limit(fsi_ctx* c, unsigned spin_limit, int missing_arrivals) {
+  if (!c || missing_arrivals < 0 || missing_arrivals > 1024) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->wait_spins = spin_limit;
+  c->wait_missing = missing_arrivals;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);  // the captured step holds the old kernel arguments
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  c->graph_ok = 0;
+  c->graph_failed = 0;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_get_small_system(fsi_ctx* c, double* out, int64_t cap, int* nf_out) {
+  if (!c || !out || !nf_out) return FSI_ERR_INVALID_ARG;
+  if (c->x.coupling == 1 || !c->d_K || c->steps_done == 0) return FSI_ERR_STATE;
+  *nf_out = c->nf;
+  const int64_t n = (int64_t)c->nf * c->nf;
+  if (cap < n) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  FSI_CUDA_TRY(cudaMemcpy(out, c->d_K, (size_t)n * 8, cudaMemcpyDeviceToHost));
+  return FSI_OK;
+}
+
 extern "C" void fsi_destroy(fsi_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);

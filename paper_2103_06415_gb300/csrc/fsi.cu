@@ -4,7 +4,9 @@
 // grid barriers are needed only where a CTA needs matrix rows another CTA produced:
 //   A  body points at theta^(k), the hat map P (Eq. weights), rhs = P E0 (C s* + q_inf) - r^c(k)
 //      + S^T (r^theta(k) - (2/dt) J^{-1} r^phidot(k))                              [every CTA, all points]
-//   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry)    [entries over all CTAs]
+//   B  K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S  (16 B0 lookups per entry): without flags, entries
+//      over all CTAs (the lower triangle mirrored for the dense B0); with flags, K is already assembled by
+//      owned rows during A and B does nothing
 //   C  f = K^{-1} rhs to double accuracy by iterative refinement: d = X r with the float inverse X,
 //      f += d, r = rhs - K f in double, until |d| <= 1e-10 |f|.  d and f are computed in full by every
 //      CTA; each CTA computes the residual rows it owns.  X is carried across iterations and steps and
@@ -17,10 +19,12 @@
 // repeated until max |dtheta| <= tol, then the Newmark update and force outputs (CTA 0).
 // Deformable bodies (beam.cuh): during A, warps 4-7 of every CTA build J_d(chi^(k)) and r^zeta(k) of each
 // flag, factor J_d and solve for y = J_d^-1 (r^zeta(k) + ds T^T f_prev) (f_prev: the last surface stress)
-// and for the columns T J_d^-1 T^T e_r of the rows the CTA owns (published for B).  Meanwhile warps 0-3,
-// once every CTA's warps 0-3 have published their points (a barrier of their own), assemble the
-// (ds/h^2) P B0 P^T part of K; after the A barrier every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from
-// the right-hand side, and B only adds (2 ds/dt) T J_d^-1 T^T to the flags' entries of K; C starts from
+// and for the columns T J_d^-1 T^T e_r of the rows r the CTA owns.  Meanwhile warps 0-3, once every CTA's
+// warps 0-3 have published their points (a barrier of their own), assemble the CTA's owned rows of
+// (ds/h^2) P B0 P^T; the CTA then adds to entry (r, c) of its rows the flags' term (2 ds/dt) T J_d^-1 T^T
+// from its own column r and publishes the rows before the grid barrier that ends A.  K is then symmetric
+// only to the rounding of those FP32 columns and of the two summation orders of (r, c) and (c, r).  After
+// the A barrier every CTA subtracts T((2/dt)(chi^(k) + y) - r^chi) from the right-hand side; C starts from
 // f_prev with the residual rows rhs + (2 ds/dt) T J_d^-1 T^T f_prev - K f_prev (the same system as
 // Eq. stress2, in a form whose FP32 structural solves act on vanishing residuals); D solves
 // dchi = J_d^-1 (r^zeta(k) + ds T^T f) (Eq. dchi2) and the convergence test takes max |dchi| as well.
@@ -96,6 +100,10 @@ struct FsiArgs {
   int n_box;
   const int* app_idx;
   const FaceWindow* app_win;
+  // bounded wait of the warps 0-3 barrier: poll limit, and arrivals it waits for beyond the grid's (a test
+  // sets these to make the wait run out; 0 in normal runs)
+  unsigned lb_spins;
+  int lb_missing;
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -428,14 +436,16 @@ __device__ __forceinline__ void named_sync_lower() { asm volatile("bar.sync 2, 1
 // counter grows by gridDim.x per use (target = uses so far * gridDim.x) and CTA 0 resets it at the end of
 // the launch.  A wait that does not end within the limit records FSI_ERR_TIMEOUT and goes on, so that every
 // CTA keeps to the same sequence of barriers.
-__device__ void lower_grid_barrier(int* cnt, int target, int* status) {
+// spin_limit bounds the wait (polls of about 64 ns each); a test may lower it and add arrivals that never
+// come, so that the wait runs out (the failure-detection path, with no copies in flight).
+__device__ void lower_grid_barrier(int* cnt, int target, int* status, unsigned spin_limit) {
   named_sync_lower();
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(cnt, 1);
     unsigned spins = 0;
     while (*(volatile int*)cnt < target) {
-      if (++spins > (1u << 22)) {
+      if (++spins > spin_limit) {
         dev_set_status(status, FSI_ERR_TIMEOUT);
         break;
       }
@@ -793,7 +803,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
       if (side_clock && tid == 0) sh_phase[14] += PhaseClock::now() - ta0;
       if (overlap_b && wid < 4) {
-        lower_grid_barrier(&a.ctrl[15], (it + 1) * (int)gridDim.x, a.status);
+        lower_grid_barrier(&a.ctrl[15], (it + 1) * (int)gridDim.x + a.lb_missing, a.status, a.lb_spins);
         for (int e = tid; e < 4 * nb; e += 128) {
           pidx_s[e] = __ldcg(&a.pidx[e]);
           pw_s[e] = __ldcg(&a.pw[e]);
@@ -1024,7 +1034,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         float* Lf = Xs;  // CTA 0 factors in the space of X, which is being rebuilt
         if (blockIdx.x == 0) {
           for (int i = tid >> 5; i < nf; i += nthr >> 5)
-            for (int k = lane; k <= i; k += 32)  // the symmetric part of K (K itself for the dense B0)
+            for (int k = lane; k <= i; k += 32)  // the symmetric part of K (K itself for the dense B0
+                                                 // without flags; with flags K is symmetric only to FP32
+                                                 // rounding of its structural columns)
               Lf[(long)i * ld + k] =
                   (float)(0.5 * (__ldcg(&a.K[(long)i * nf + k]) + __ldcg(&a.K[(long)k * nf + i])));
           __syncthreads();
@@ -1435,6 +1447,8 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.n_box = c->n_box;
   a.app_idx = c->n_app > 0 ? c->d_app_idx : nullptr;
   a.app_win = c->d_app_win;
+  a.lb_spins = c->wait_spins ? c->wait_spins : (1u << 22);
+  a.lb_missing = c->wait_missing;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
   cfg.blockDim = dim3(256);

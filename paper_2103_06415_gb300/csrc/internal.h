@@ -188,6 +188,10 @@ struct fsi_ctx {
   long long steps_done;
   int max_iters_seen;
   int fsi_grid;  // CTAs of the cooperative FSI kernel
+  // bounded cross-CTA wait of the FSI kernel (fsi_debug_set_wait_limit): poll limit (0: default) and
+  // arrivals it waits for that never come (0 in normal runs)
+  unsigned wait_spins;
+  int wait_missing;
   // graph
   cudaGraph_t graph;
   cudaGraphExec_t gexec;

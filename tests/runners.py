@@ -61,3 +61,11 @@ def oracle_history(sim, body=0):
 def rel_err(a, b):
     a, b = np.asarray(a, float), np.asarray(b, float)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def check_rel(tag, got, ref, tol):
+    """Assert rel_err(got, ref) < tol and print the measured error (tag) for the record."""
+    err = rel_err(got, ref)
+    print("PARITY %s rel %.3e (bound %.0e)" % (tag, err, tol))
+    assert err < tol, (tag, err)
+    return err

@@ -61,3 +61,73 @@ def test_no_slip_after_corrector_at_full_size(lib, setup, precision, bound):
     scale = max(1.0, np.max(np.abs(ub)))
     assert np.max(np.abs(ub - vel)) < bound * scale
     ctx.close()
+
+
+N_FULL = 12
+
+
+@pytest.fixture(scope="module")
+def full_size_runs(lib, setup):
+    """The headline workload at full size, FP64 on the GPU (the bench's CUDA graph, the 101-CTA FSI kernel
+    with owned-row assembly and the warps 0-3 barrier) and in the oracle, N_FULL steps from the same
+    start, at an FSI tolerance of 1e-12 on both sides (so the iteration counts are decided far from the
+    threshold and must agree)."""
+    from runners import oracle_sim
+    w, lev, sd = setup
+    sim = oracle_sim(w, tol=1e-12)
+    for _ in range(N_FULL):
+        sim.step()
+    ctx = gpu_context(w, precision=0, tol=1e-12)
+    ctx.advance(N_FULL)
+    nb = w["bodies"][0]["n_pts"]
+    out = dict(sim=sim, hist=ctx.history(0), state=ctx.beam_state(0), interp=ctx.interp(nb),
+               fields=[(ctx.field(g, 0), ctx.field(g, 1)) for g in range(w["n_levels"])])
+    ctx.close()
+    return out
+
+
+def test_full_size_fsi_iterations_and_interpolation_map(full_size_runs):
+    from runners import oracle_history
+    r = full_size_runs
+    ref = oracle_history(r["sim"])
+    assert np.array_equal(r["hist"][:, 5], ref[:, 5])               # FSI iterations per step
+    idx, wts = r["interp"]
+    ridx, rw = r["sim"].last_p
+    assert np.array_equal(idx, ridx)                                 # P index map bit-exact
+    err = float(np.max(np.abs(wts - rw)))
+    print("PARITY config2 P weights max abs %.3e" % err)
+    assert err < 1e-12
+
+
+def test_full_size_histories_match_oracle(full_size_runs):
+    """fx, fy, tip displacement and tip rate of the flag, relative to each history's largest magnitude."""
+    from runners import oracle_history, rel_err
+    r = full_size_runs
+    ref = oracle_history(r["sim"])
+    for k, nm in ((0, "fx"), (1, "fy"), (3, "tip"), (4, "tip_rate")):
+        err = rel_err(r["hist"][:, k], ref[:, k])
+        print("PARITY config2 %s history rel %.3e" % (nm, err))
+        assert err < 1e-9, nm
+
+
+def test_full_size_flag_state_matches_oracle(full_size_runs):
+    from runners import rel_err
+    r = full_size_runs
+    b = r["sim"].bodies[0]
+    chi, zeta, zdot = r["state"]
+    e_chi = float(np.max(np.abs(chi - b.chi.reshape(-1, 3))))
+    e_zeta = rel_err(zeta, b.zeta.reshape(-1, 3))
+    e_zdot = rel_err(zdot, b.zetadot.reshape(-1, 3))
+    print("PARITY config2 chi max abs %.3e zeta rel %.3e zetadot rel %.3e" % (e_chi, e_zeta, e_zdot))
+    assert e_chi < 1e-12
+    assert e_zeta < 1e-9
+    assert e_zdot < 1e-8
+
+
+def test_full_size_fields_match_oracle(full_size_runs):
+    from runners import rel_err
+    r = full_size_runs
+    for g, (wf, sf) in enumerate(r["fields"]):
+        ew, es = rel_err(wf, r["sim"].w[g]), rel_err(sf, r["sim"].s[g])
+        print("PARITY config2 level %d w rel %.3e s rel %.3e" % (g, ew, es))
+        assert ew < 1e-9 and es < 1e-9, g

@@ -72,3 +72,30 @@ def test_first_error_wins_and_context_stays_usable(lib):
     good.advance(5)
     assert _status(lib, good) == 0
     good.close()
+
+
+def test_bounded_cross_cta_wait_latches_timeout(lib):
+    """The FSI kernel's cross-CTA wait (warps 0-3 of every CTA, with a flag) polls a global arrival counter a
+    bounded number of times.  Require one arrival that never comes and a short bound: every such wait runs
+    out (no copies are in flight there), TIMEOUT is latched and read by the host, and the device stays
+    healthy -- a new context on it reproduces an undisturbed run bit for bit."""
+    w = wl.small_flag()
+    ref = gpu_context(w)
+    ref.advance(4)
+    ref_hist = ref.history(0)
+    ref.close()
+    bad = gpu_context(w)
+    bad.advance(2)
+    assert _status(lib, bad) == 0
+    assert bad._lib.fsi_debug_set_wait_limit(bad._h, 1 << 12, 1) == 0
+    bad.advance(1)
+    assert _status(lib, bad) == 7                          # FSI_ERR_TIMEOUT
+    assert bad._lib.fsi_debug_set_wait_limit(bad._h, 0, 0) == 0
+    bad.advance(1)
+    assert _status(lib, bad) == 7                          # the first latched code is kept
+    bad.close()
+    good = gpu_context(w)
+    good.advance(4)
+    assert _status(lib, good) == 0
+    assert np.array_equal(good.history(0), ref_hist)
+    good.close()

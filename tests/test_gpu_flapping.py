@@ -6,7 +6,7 @@ import pytest
 
 from paper_2103_06415_gb300 import workloads as wl
 
-from runners import gpu_context, oracle_history, oracle_sim, rel_err
+from runners import check_rel, gpu_context, oracle_history, oracle_sim, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def _compare(sim, ctx, bound):
         hist, ref = ctx.history(body), oracle_history(sim, body)
         for k in range(5):
             if np.max(np.abs(ref[:, k])) > 0:
-                assert rel_err(hist[:, k], ref[:, k]) < bound, (body, k, rel_err(hist[:, k], ref[:, k]))
+                check_rel("test_gpu_flapping.py:34", hist[:, k], ref[:, k], bound)
             else:
                 assert np.all(hist[:, k] == 0.0), (body, k)
 
@@ -43,7 +43,7 @@ def test_flapping_pair_matches_oracle_at_tight_tolerance(lib, use_graph):
     sim, ctx = _runs(w, n, tol=1e-12, use_graph=use_graph)
     assert np.array_equal(ctx.history(1)[:, 5], oracle_history(sim, 1)[:, 5])
     _compare(sim, ctx, 1e-10)
-    assert rel_err(ctx.field(0, 0), sim.w[0]) < 1e-9
+    check_rel("test_gpu_flapping.py:46", ctx.field(0, 0), sim.w[0], 1e-9)
     idx, wts = ctx.interp(sim.nb)
     ridx, rw = sim.last_p
     assert np.array_equal(idx, ridx)
@@ -114,4 +114,4 @@ def test_e1_flapping_runs_with_few_fsi_iterations(lib, case):
     h64, h32 = hist
     assert np.max(h64[:, 5]) <= 3
     assert np.all(np.isfinite(h64[:, :5]))
-    assert rel_err(h32[:, 3], h64[:, 3]) < 1e-4
+    check_rel("test_gpu_flapping.py:117", h32[:, 3], h64[:, 3], 1e-4)

@@ -12,7 +12,7 @@ from oracle import grid as og
 from oracle import ib as oib
 from paper_2103_06415_gb300 import workloads as wl
 
-from runners import gpu_context, oracle_history, oracle_sim, rel_err
+from runners import check_rel, gpu_context, oracle_history, oracle_sim, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -58,8 +58,8 @@ def test_fluid_steps_without_body_match_oracle(lib, levels, nx, ny):
         sim.step()
     ctx.advance(3)
     for g in range(levels):
-        assert rel_err(ctx.field(g, 0), sim.w[g]) < 1e-12, g
-        assert rel_err(ctx.field(g, 1), sim.s[g]) < 1e-12, g
+        check_rel("fluid %dlvl %dx%d level%d w" % (levels, nx, ny, g), ctx.field(g, 0), sim.w[g], 1e-12)
+        check_rel("fluid %dlvl %dx%d level%d s" % (levels, nx, ny, g), ctx.field(g, 1), sim.s[g], 1e-12)
 
 
 def _b0_sample(ctx, sim, n_cols, seed):
@@ -100,13 +100,13 @@ def test_small_plate_run_matches_oracle(lib, use_graph):
     assert hist.shape == (n, 6)
     assert np.array_equal(hist[:, 5], ref[:, 5])                      # FSI iteration counts
     for k in range(5):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+        check_rel("small_plate graph=%d hist%d" % (use_graph, k), hist[:, k], ref[:, k], 1e-10)
     idx, wts = ctx.interp(sim.nb)
     ridx, rw = sim.last_p
     assert np.array_equal(idx, ridx)                                  # P index map bit-exact
     assert np.max(np.abs(wts - rw)) < 1e-13
-    assert rel_err(ctx.field(0, 0), sim.w[0]) < 1e-10
-    assert rel_err(ctx.field(0, 1), sim.s[0]) < 1e-10
+    check_rel("small_plate graph=%d w" % use_graph, ctx.field(0, 0), sim.w[0], 1e-10)
+    check_rel("small_plate graph=%d s" % use_graph, ctx.field(0, 1), sim.s[0], 1e-10)
 
 
 def test_small_plate_multilevel_run_matches_oracle(lib):
@@ -117,7 +117,7 @@ def test_small_plate_multilevel_run_matches_oracle(lib):
     ctx.advance(6)
     hist, ref = ctx.history(0), oracle_history(sim)
     for k in range(5):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+        check_rel("small_plate_2lvl hist%d" % k, hist[:, k], ref[:, k], 1e-10)
 
 
 def test_plate_128_run_matches_oracle(lib):
@@ -130,7 +130,7 @@ def test_plate_128_run_matches_oracle(lib):
     hist, ref = ctx.history(0), oracle_history(sim)
     assert np.array_equal(hist[:, 5], ref[:, 5])
     for k in range(5):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-9, k
+        check_rel("plate_128 hist%d" % k, hist[:, k], ref[:, k], 1e-9)
 
 
 def test_fp32_fluid_path_error_vs_oracle(lib):

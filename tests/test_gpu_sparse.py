@@ -10,7 +10,7 @@ import pytest
 from oracle import ib as oib
 from paper_2103_06415_gb300 import workloads as wl
 
-from runners import gpu_context, oracle_history, oracle_sim, rel_err
+from runners import check_rel, gpu_context, oracle_history, oracle_sim, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_sparse_plate_run_matches_oracle(lib):
     hist, ref = ctx.history(0), oracle_history(sim)
     assert np.array_equal(hist[:, 5], ref[:, 5])
     for k in range(5):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+        check_rel("test_gpu_sparse.py:53", hist[:, k], ref[:, k], 1e-10)
 
 
 def test_sparse_flag_run_matches_oracle(lib):
@@ -63,7 +63,7 @@ def test_sparse_flag_run_matches_oracle(lib):
     ctx.advance(n)
     hist, ref = ctx.history(0), oracle_history(sim)
     for k in (0, 1, 3, 4):
-        assert rel_err(hist[:, k], ref[:, k]) < 1e-10, k
+        check_rel("test_gpu_sparse.py:66", hist[:, k], ref[:, k], 1e-10)
     chi, _, _ = ctx.beam_state(0)
     assert np.max(np.abs(chi - sim.bodies[0].chi.reshape(-1, 3))) < 1e-13
 
@@ -89,7 +89,7 @@ def test_config2_sparse_against_dense(lib):
     force = np.max(np.abs(hd[win, :2]))
     for k in (0, 1):
         assert np.max(np.abs(hs[win, k] - hd[win, k])) < 0.02 * force, k
-    assert rel_err(hs[win, 3], hd[win, 3]) < 0.02
+    check_rel("test_gpu_sparse.py:92", hs[win, 3], hd[win, 3], 0.02)
     assert abs(hs[win, 0].mean() - hd[win, 0].mean()) < 0.002 * abs(hd[win, 0].mean())
 
 

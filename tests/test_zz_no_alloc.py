@@ -51,6 +51,16 @@ def test_noalloc_level_solve_matches_allocating_entry_point(prec, nx, ny):
         ring = np.ones(w.shape, bool)
         ring[1:-1, 1:-1] = False
         assert np.all(w[ring] == 7.0) and np.all(s[ring] == -3.0)
+    # the promise itself: after the calls above (kernels loaded, scratch set up), further calls change the
+    # device's free memory by nothing
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rc = lib.fsi_op_level_solve_noalloc(prec, nx, ny, h, re, dt, ctypes.c_void_p(rhs_d.data_ptr()),
+                                            ctypes.c_void_p(w_d.data_ptr()), ctypes.c_void_p(s_d.data_ptr()),
+                                            ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_level_solve_rejects_sizes_beyond_its_scratch():
