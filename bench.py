@@ -34,7 +34,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="mixed: double fields, float transforms, finest level in increment form (the headline); "
+                         "fp32: all-float fields; fp64: the plain FP64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--offline", action="store_true",
                     help="measure the offline stage instead (B0 for 8192 unknowns on a 1024^2 grid by both "
@@ -354,23 +356,25 @@ def run_comparator(args, timed_steps):
     return out
 
 
-def mixed_vs_fp64_horizon(w, n, make, lib):
-    """The mixed path's error over the workload's whole horizon: n steps of the FP32-fluid run and of the FP64
-    run from the same start, relative L2 difference of each force / deflection history (Eq. errortheta
-    without the factor 100), beside the FP64 path's own sensitivity -- the same difference between two FP64
-    runs whose initial deflection differs by 1 part in 1e13."""
+def mixed_vs_fp64_horizon(w, n, make, lib, prec):
+    """The timed path's error over the workload's whole horizon: n steps of its run (precision prec) and of
+    the FP64 run from the same start, relative L2 difference of each force / deflection history (Eq.
+    errortheta without the factor 100), beside the FP64 path's own sensitivity -- the same difference between
+    two FP64 runs whose initial deflection differs by 1 part in 1e13 -- and the all-float FP32 mode's error."""
     import copy
     import numpy as np
     hist = {}
-    for tag, prec, rel in (("fp64", lib.FSI_PREC_FP64, 0.0), ("mixed", lib.FSI_PREC_FP32, 0.0),
-                           ("fp64_perturbed", lib.FSI_PREC_FP64, 1e-13)):
+    runs = [("fp64", lib.FSI_PREC_FP64, 0.0), ("mixed", prec, 0.0), ("fp64_perturbed", lib.FSI_PREC_FP64, 1e-13)]
+    if prec != lib.FSI_PREC_FP32:
+        runs.append(("fp32", lib.FSI_PREC_FP32, 0.0))
+    for tag, prec_k, rel in runs:
         wk = copy.deepcopy(w)
         for b in wk["bodies"]:
             if "tip_angle" in b:
                 b["tip_angle"] *= 1.0 + rel
             elif "theta" in b:
                 b["theta"] *= 1.0 + rel
-        c, _, _ = make(prec, wk_override=wk)
+        c, _, _ = make(prec_k, wk_override=wk)
         t0 = time.perf_counter()
         c.advance(n)
         c.sync()
@@ -390,13 +394,17 @@ def mixed_vs_fp64_horizon(w, n, make, lib):
     ref = hist["fp64"][0]
     mixed = rel_l2(hist["mixed"][0], ref)
     env = rel_l2(hist["fp64_perturbed"][0], ref)
-    return {"mixed_vs_fp64_rel_l2": mixed, "mixed_within_1e-5": bool(max(mixed.values()) <= 1e-5),
-            "fp64_perturbation_envelope_rel_l2": env,
+    out = {"mixed_vs_fp64_rel_l2": mixed, "mixed_within_1e-5": bool(max(mixed.values()) <= 1e-5),
+           "fp64_perturbation_envelope_rel_l2": env}
+    if "fp32" in hist:
+        out["fp32_mode_vs_fp64_rel_l2"] = rel_l2(hist["fp32"][0], ref)
+    out.update({
             "horizon": {"steps": n, "histories": "all bodies; deflection = theta (torsional) or tip "
                                                  "displacement (flag)",
                         "envelope": "FP64 vs FP64 with the initial deflection scaled by 1 + 1e-13",
                         "fsi_iterations_max": int(ref[:, :, 5].max()),
-                        "wall_s": {k: v[1] for k, v in hist.items()}}}
+                        "wall_s": {k: v[1] for k, v in hist.items()}}})
+    return out
 
 
 def run_reference(args, w):
@@ -437,7 +445,8 @@ def main():
         import paper_2103_06415_gb300 as lib
         from runners import gpu_context
         wr = wl.flag_512x256_3lvl_reduced_omega0()
-        c = gpu_context(wr, precision=lib.FSI_PREC_FP32 if args.precision == "fp32" else lib.FSI_PREC_FP64,
+        c = gpu_context(wr, precision={"mixed": lib.FSI_PREC_MIXED, "fp32": lib.FSI_PREC_FP32,
+                                       "fp64": lib.FSI_PREC_FP64}[args.precision],
                         use_graph=False)
         c.advance(args.profile_steps)
         c.sync()
@@ -483,7 +492,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    prec = lib.FSI_PREC_FP32 if args.precision == "fp32" else lib.FSI_PREC_FP64
+    prec = {"mixed": lib.FSI_PREC_MIXED, "fp32": lib.FSI_PREC_FP32, "fp64": lib.FSI_PREC_FP64}[args.precision]
 
     def make(p, drop_tol=0.0, wk_override=None):
         st = torch.cuda.Stream()
@@ -525,7 +534,7 @@ def main():
 
     # FP64 path on the same workload (same steps) and the force error of the mixed path against it
     extra = {}
-    if prec == lib.FSI_PREC_FP32 and rank == 0:
+    if prec != lib.FSI_PREC_FP64 and rank == 0:
         ctx64, stream64, b0_64 = make(lib.FSI_PREC_FP64)
         ctx64.advance(args.warmup)
         t64 = timed_steps(ctx64, stream64, args.steps)
@@ -542,7 +551,7 @@ def main():
         ctx64.close()
         horizon = w["steps"] if args.horizon_steps < 0 else args.horizon_steps
         if horizon > 0:
-            extra.update(mixed_vs_fp64_horizon(w, horizon, make, lib))
+            extra.update(mixed_vs_fp64_horizon(w, horizon, make, lib, prec))
         # the same run with the sparse B0' of Eq. filtereq at the paper's drop tolerance (0.007)
         ctxs, streams, b0_sp = make(prec, 0.007)
         ctxs.advance(args.warmup)
@@ -574,7 +583,7 @@ def main():
         for name in ("ysolve", "xf", "xi", "fsi", "rhs", "src"):
             ms, nl = ctx.profile_kernel(name, 8)
             shares[name] = (ms, nl / 8.0)
-        esz = 4 if prec == lib.FSI_PREC_FP32 else 8
+        esz = 8 if prec == lib.FSI_PREC_FP64 else 4
         nxi, nyi = w["nx"] - 1, w["ny"] - 1
         per_step = {k: v[0] * v[1] for k, v in shares.items()}
         ys_ms = shares["ysolve"][0]
@@ -641,7 +650,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "p50_ms": statistics.median(times), "p99_ms": float(np.percentile(times, 99)),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if prec == lib.FSI_PREC_FP32 else "f64", "data": "synthetic",
+                "dtype": {lib.FSI_PREC_FP32: "f32", lib.FSI_PREC_FP64: "f64"}.get(prec, "f32 transforms / f64 fields"),
+                "data": "synthetic",
                 "config": {"workload": w["name"] + " (clamped flag, corotational beam elements)",
                            "levels": w["n_levels"], "nx": w["nx"], "ny": w["ny"], "cells_per_step": cells,
                            "body_points": sum(b["n_pts"] for b in w["bodies"]), "n_sd": stats["n_sd"],

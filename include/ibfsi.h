@@ -48,8 +48,13 @@ typedef enum {
 
 typedef enum {
   FSI_PREC_FP64 = 0, /* every fluid transform and stencil in double */
-  FSI_PREC_FP32 = 1  /* fluid transforms and stencils in float; B0, the small system, Newton update and
+  FSI_PREC_FP32 = 1, /* fluid transforms and stencils in float; B0, the small system, Newton update and
                         force reductions stay in double */
+  FSI_PREC_MIXED = 2 /* as FSI_PREC_FP32, but the vorticity and streamfunction fields are kept in double and,
+                        after the first step, the finest level is advanced in increment form: its float
+                        transforms compute w^{n+1} - w^n and s^{n+1} - s^n, which are added to the double
+                        fields (coarser levels: full float solves).  No tensor-core transforms
+                        (dst_method 1: FSI_ERR_UNSUPPORTED; 2 keeps the FFT) and no coupling 1. */
 } fsi_precision;
 
 typedef enum { FSI_BODY_RIGID = 0, FSI_BODY_TORSIONAL = 1, FSI_BODY_DEFORMABLE = 2, FSI_BODY_DRIVEN = 3 } fsi_body_type;

@@ -11,9 +11,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import COUPLING_SUBDOMAIN, COUPLING_TRUE_E, FSI_PREC_FP32, FSI_PREC_FP64, FsiError, check  # noqa: F401
+from ._lib import (COUPLING_SUBDOMAIN, COUPLING_TRUE_E, FSI_PREC_FP32, FSI_PREC_FP64, FSI_PREC_MIXED,  # noqa: F401
+                   FsiError, check)
 
-__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "flapping_kinematics", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FsiError",
+__all__ = ["Context", "B0Set", "level_solve", "beam_solve", "flapping_kinematics", "fma_rate", "FSI_PREC_FP64", "FSI_PREC_FP32", "FSI_PREC_MIXED", "FsiError",
            "COUPLING_SUBDOMAIN", "COUPLING_TRUE_E"]
 
 
@@ -25,7 +26,8 @@ class Context:
     """One FSI run on the current CUDA device.
 
     grid: nx, ny (powers of two), n_levels, x0, y0, h, re, dt, uinf=(U, V)
-    precision: FSI_PREC_FP64 or FSI_PREC_FP32; stream: a cudaStream_t handle (int) or None.
+    precision: FSI_PREC_FP64, FSI_PREC_FP32 or FSI_PREC_MIXED (double fields, float transforms, the finest level
+    in increment form); stream: a cudaStream_t handle (int) or None.
     dst_method: 0 FFT sine transforms, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotune per pass.
     coupling: COUPLING_SUBDOMAIN (the method) or COUPLING_TRUE_E (the true-E comparator; krylov_tol and
     krylov_max_iters control its conjugate-gradient solve, 0 = library defaults).

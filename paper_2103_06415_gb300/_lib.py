@@ -14,6 +14,7 @@ FSI_PREC_FP64 = 0
 COUPLING_SUBDOMAIN = 0  # E0, P and the precomputed B0 (Sec. 3)
 COUPLING_TRUE_E = 1     # E, E^T at the body points, Krylov solve per FSI iteration (Sec. 2.2)
 FSI_PREC_FP32 = 1
+FSI_PREC_MIXED = 2      # double level fields, float transforms, finest level in increment form
 FSI_BODY_RIGID = 0
 FSI_BODY_TORSIONAL = 1
 FSI_BODY_DEFORMABLE = 2

@@ -124,7 +124,8 @@ static fsi_status create_impl(fsi_ctx* c) {
   c->ring_ld = padded_stride(c->Nx > c->Ny ? c->Nx : c->Ny);
   const size_t E = c->esz;
   const size_t lvl = (size_t)c->G * c->lvl_elems * E;
-  if (!(c->w_all = ctx_alloc(c, lvl)) || !(c->s_all = ctx_alloc(c, lvl)) || !(c->nprev_all = ctx_alloc(c, lvl)) ||
+  const size_t flvl = (size_t)c->G * c->lvl_elems * c->fesz;
+  if (!(c->w_all = ctx_alloc(c, flvl)) || !(c->s_all = ctx_alloc(c, flvl)) || !(c->nprev_all = ctx_alloc(c, flvl)) ||
       !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)c->G * c->Nx * c->ldT * E)) ||
       !(c->T2w = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) || !(c->T2s = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) ||
       !(c->src = ctx_alloc(c, (size_t)c->lvl_elems * E)) || !(c->ring = ctx_alloc(c, (size_t)8 * c->ring_ld * E)))
@@ -174,8 +175,8 @@ static fsi_status create_impl(fsi_ctx* c) {
   std::vector<void*> srcs(8 * (size_t)c->G), dsts(8 * (size_t)c->G);
   std::vector<long> es(8 * (size_t)c->G);
   for (int l = 0; l < c->G; ++l) {
-    char* w = (char*)c->w_all + (size_t)l * c->lvl_elems * E;
-    char* s = (char*)c->s_all + (size_t)l * c->lvl_elems * E;
+    char* w = (char*)c->w_all + (size_t)l * c->lvl_elems * c->fesz;
+    char* s = (char*)c->s_all + (size_t)l * c->lvl_elems * c->fesz;
     char* r = (char*)c->ring;
     const long ps = c->ps;
     void* side0[4] = {w + ps * E, w + (ps + c->nx) * E, s + ps * E, s + (ps + c->nx) * E};
@@ -286,7 +287,8 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
   c->g = *grid;
   memset(&c->x, 0, sizeof(c->x));
   if (exec) c->x = *exec;
-  if ((c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32) || c->x.dst_method < 0 ||
+  if ((c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32 && c->x.precision != FSI_PREC_MIXED) ||
+      c->x.dst_method < 0 ||
       c->x.dst_method > 2) {
     delete c;
     return FSI_ERR_INVALID_ARG;
@@ -305,6 +307,7 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
   if (c->x.history_cap <= 0) c->x.history_cap = 1 << 16;
   c->prec = c->x.precision;
   c->esz = c->prec == FSI_PREC_FP64 ? 8 : 4;
+  c->fesz = c->prec == FSI_PREC_FP32 ? 4 : 8;
   c->own_stream = 0;
   if (c->x.stream) {
     c->stream = (cudaStream_t)c->x.stream;
@@ -498,7 +501,7 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
   c->n_sd = c->n_box + c->n_app;
   if (c->n_app > 0 && (drop_tol > 0.0 || load)) return FSI_ERR_UNSUPPORTED;
   if (true_e) {  // true E at the body points: no B0; torsional and rigid bodies
-    if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024) return FSI_ERR_UNSUPPORTED;
+    if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024 || c->prec == FSI_PREC_MIXED) return FSI_ERR_UNSUPPORTED;
     if (c->x.krylov_max_iters <= 0) c->x.krylov_max_iters = 2 * c->nf + 20;
   } else if (c->nb > 0 && !fsi_smem_fits(c)) {
     return FSI_ERR_UNSUPPORTED;
@@ -867,10 +870,10 @@ static void to_double(const void* src, double* dst, long rows, long cols, long l
 extern "C" fsi_status fsi_get_field(fsi_ctx* c, int level, int which, double* out) {
   if (!c || !out || level < 0 || level >= c->G || which < 0 || which > 1) return FSI_ERR_INVALID_ARG;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  std::vector<char> buf((size_t)c->lvl_elems * c->esz);
-  const char* base = (const char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->esz;
+  std::vector<char> buf((size_t)c->lvl_elems * c->fesz);
+  const char* base = (const char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->fesz;
   FSI_CUDA_TRY(cudaMemcpy(buf.data(), base, buf.size(), cudaMemcpyDeviceToHost));
-  if (c->prec == FSI_PREC_FP64)
+  if (c->fesz == 8)
     to_double<double>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
   else
     to_double<float>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
@@ -880,16 +883,16 @@ extern "C" fsi_status fsi_get_field(fsi_ctx* c, int level, int which, double* ou
 extern "C" fsi_status fsi_set_field(fsi_ctx* c, int level, int which, const double* in) {
   if (!c || !in || level < 0 || level >= c->G || which < 0 || which > 1) return FSI_ERR_INVALID_ARG;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  std::vector<char> buf((size_t)c->lvl_elems * c->esz, 0);
+  std::vector<char> buf((size_t)c->lvl_elems * c->fesz, 0);
   for (long j = 0; j <= c->ny; ++j)
     for (long i = 0; i <= c->nx; ++i) {
       const double v = in[j * (c->nx + 1) + i];
-      if (c->prec == FSI_PREC_FP64)
+      if (c->fesz == 8)
         ((double*)buf.data())[j * c->ps + i] = v;
       else
         ((float*)buf.data())[j * c->ps + i] = (float)v;
     }
-  char* base = (char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->esz;
+  char* base = (char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->fesz;
   FSI_CUDA_TRY(cudaMemcpy(base, buf.data(), buf.size(), cudaMemcpyHostToDevice));
   c->first_pending = 1;
   return FSI_OK;

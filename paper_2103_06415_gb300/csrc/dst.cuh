@@ -465,12 +465,13 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
 }
 
 // Pass XI: rows j of inw and ins (length N = Nx) -> DST along x -> w, s rows written to the level fields
-// (row j+1, columns 1..N of a vertex array with row stride f_ld).  mode 0: store, 1: subtract.
+// (row j+1, columns 1..N of a vertex array of type TF with row stride f_ld).  mode 0: store, 1: subtract,
+// 2: add (fields of type TF = double with float transforms: the increments of the mixed mode).
 // blockIdx.x = 2 * (row block) + field: a CTA takes 2*nf rows of one field (0: w, 1: s), so w and s run on
 // different CTAs (twice the CTAs, one transform buffer per row pair); rows j, j+1 share one FFT.
-template <typename T, int PER>
+template <typename T, int PER, typename TF = T>
 __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* __restrict__ ins, long in_ld,
-                                            long in_bs, int nrows, int N, T* __restrict__ fw, T* __restrict__ fs,
+                                            long in_bs, int nrows, int N, TF* __restrict__ fw, TF* __restrict__ fs,
                                             long f_ld, long f_bs, int mode,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
   using c2 = typename C2<T>::t;
@@ -485,9 +486,9 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
   const int field = blockIdx.x & 1;
   const int row0 = (blockIdx.x >> 1) * 2 * nf;
   const T* in = (field ? ins : inw) + (long)blockIdx.y * in_bs;
-  T* fo = (field ? fs : fw) + (long)blockIdx.y * f_bs;
-  // mode 1 subtracts from the field: the old values under the first pair of rows load with the inputs
-  T old[NC][2];
+  TF* fo = (field ? fs : fw) + (long)blockIdx.y * f_bs;
+  // modes 1 and 2 update the field: the old values under the first pair of rows load with the inputs
+  TF old[NC][2];
   if (mode != 0) {
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const bool ok = i < N && row0 + e < nrows;
-        old[m][e] = ok ? fo[(long)(row0 + e + 1) * f_ld + 1 + i] : T(0);
+        old[m][e] = ok ? fo[(long)(row0 + e + 1) * f_ld + 1 + i] : TF(0);
       }
     }
   }
@@ -530,12 +531,12 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
         if (r >= nrows) continue;
         const long o = (long)(r + 1) * f_ld + 1 + i;
         const T v = e ? T(0.5) * z.x : T(-0.5) * z.y;
-        if (mode == 0)
-          fo[o] = v;
-        else if (f == 0)
-          fo[o] = old[m][e] - v;
-        else
-          fo[o] -= v;
+        if (mode == 0) {
+          fo[o] = TF(v);
+        } else {
+          const TF prev = f == 0 ? old[m][e] : fo[o];
+          fo[o] = mode == 1 ? prev - TF(v) : prev + TF(v);
+        }
       }
     }
   }

@@ -24,7 +24,7 @@ FftCfg fft_cfg(int logL) {
   return c;
 }
 
-template <typename T>
+template <typename T, typename TF = T>
 void set_smem_limits() {
   static bool done = false;
   if (done) return;
@@ -36,46 +36,50 @@ void set_smem_limits() {
   cudaFuncSetAttribute(dst::k_ysolve<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_ysolve<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_ysolve<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_xi<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_xi<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(dst::k_xi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 1, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // ---------------------------------------------------------------------------------------------
 // O2: advection N = div(u w) with vertex-averaged velocities (reading R7) and
 // rhs = w/dt + lap_h w/(2 Re) - 3/2 N^n + 1/2 N^{n-1}.  Block (32, 8) = one tile of interior vertices; the
 // tile of w and s with a one-vertex halo is staged in shared memory (each value read once from L2).
-// Per-level constants in the field precision (computed on the host).
+// Per-level constants in the transform precision T (computed on the host).  The fields are of type TF
+// (TF = T, or double fields with float transforms in the mixed mode: the differences of field values are
+// taken in TF, the rest in T).  delta0: level 0 takes the right-hand side of the increment
+// w* - w^n instead, A_w (w* - w^n) = lap_h w^n / Re - 3/2 N^n + 1/2 N^{n-1} (the same equation with
+// A_w w^n = w^n/dt - lap_h w^n/(2 Re) moved to the right; its boundary values are the ring increments).
 template <typename T>
 struct RhsConst {
   T i2h[12], inv_h2[12];  // 1/(2 h_g), 1/h_g^2 for level g (at most 12 levels)
-  T inv_dt, half_inv_re, U, V;
+  T inv_dt, half_inv_re, inv_re, U, V;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const T* __restrict__ s_all,
-                                             T* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps, int nx,
-                                             int ny, RhsConst<T> k, int first) {
+template <typename T, typename TF = T>
+__global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const TF* __restrict__ s_all,
+                                             TF* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps,
+                                             int nx, int ny, RhsConst<T> k, int first, int delta0) {
   pdl_enter();
-  __shared__ T tw[10][35], ts[10][35];
+  __shared__ TF tw[10][35], ts[10][35];
   const int g = blockIdx.z;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;  // tile vertex (i0 + 1, j0 + 1) at smem (1, 1)
-  const T* s = s_all + (long)g * lvl;
+  const TF* s = s_all + (long)g * lvl;
   const int t = threadIdx.y * 32 + threadIdx.x;
   const int i = i0 + threadIdx.x + 1, j = j0 + threadIdx.y + 1;
   const bool inner = i < nx && j < ny;
   const long o = (long)j * ps + i;
-  T* np = np_all + (long)g * lvl;
+  TF* np = np_all + (long)g * lvl;
   // every global load of the thread is issued before any is consumed: N^{n-1} of its vertex and its (at
   // most two) elements of the 10 x 34 tile of w and s
-  const T nprev = (inner && !first) ? np[o] : T(0);
-  T wv[2], sv[2];
+  const T nprev = (inner && !first) ? T(np[o]) : T(0);
+  TF wv[2], sv[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int e = t + 256 * q;
     const int r = e / 34, c = e - r * 34;
     const int I = i0 + c, J = j0 + r;  // vertex indices 0..nx, 0..ny
-    wv[q] = sv[q] = T(0);
+    wv[q] = sv[q] = TF(0);
     if (e < 10 * 34 && I <= nx && J <= ny) {
       // O1 on the fly: a vertex strictly inside a finer level takes the vorticity of the finest level that
       // contains it (the coarse array itself is overwritten by this level's solve before any other use)
@@ -102,18 +106,19 @@ __global__ void __launch_bounds__(256) k_rhs(const T* __restrict__ w_all, const 
   if (!inner) return;
   const int x = threadIdx.x + 1, y = threadIdx.y + 1;
   const T i2h = k.i2h[g];
-  const T wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
+  const TF wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
   // ubar at (i+-1, j) = (s[j+1] - s[j-1])/(2h) + U ; vbar at (i, j+-1) = -(s[i+1] - s[i-1])/(2h) + V
-  const T ue = (ts[y + 1][x + 1] - ts[y - 1][x + 1]) * i2h + k.U;
-  const T uw = (ts[y + 1][x - 1] - ts[y - 1][x - 1]) * i2h + k.U;
-  const T vn = -(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + k.V;
-  const T vs = -(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
-  const T n = (ue * we - uw * ww) * i2h + (vn * wn - vs * wsx) * i2h;
-  const T lap = (we + ww + wn + wsx - T(4) * wc) * k.inv_h2[g];
+  const T ue = T(ts[y + 1][x + 1] - ts[y - 1][x + 1]) * i2h + k.U;
+  const T uw = T(ts[y + 1][x - 1] - ts[y - 1][x - 1]) * i2h + k.U;
+  const T vn = -T(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + k.V;
+  const T vs = -T(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
+  const T n = (ue * T(we) - uw * T(ww)) * i2h + (vn * T(wn) - vs * T(wsx)) * i2h;
+  const T lap = T(we + ww + wn + wsx - TF(4) * wc) * k.inv_h2[g];
   const long oi = (long)(j - 1) * ps + (i - 1);
   const T nold = first ? n : nprev;
-  np[o] = n;
-  rhs_all[(long)g * lvl + oi] = wc * k.inv_dt + lap * k.half_inv_re - T(1.5) * n + T(0.5) * nold;
+  np[o] = TF(n);
+  const T base = (delta0 && g == 0) ? lap * k.inv_re : T(wc) * k.inv_dt + lap * k.half_inv_re;
+  rhs_all[(long)g * lvl + oi] = base - T(1.5) * n + T(0.5) * nold;
 }
 
 // O3 and the boundary-side transforms of a nested level in one launch.  Ring vectors: side 0 = left/right
@@ -130,13 +135,15 @@ __device__ __forceinline__ T ring_value(const T* __restrict__ c, long ps, int nx
   return T(0.5) * (c[(long)J0 * ps + I0] + c[(long)J1 * ps + I1]);
 }
 
-template <typename T, int PER>
-__global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restrict__ sf, const T* __restrict__ wc,
-                                                  const T* __restrict__ sc, long ps, int nx, int ny,
+// delta: the spectra are those of the ring increments (new value minus the fine level's current one; the
+// increment form of the finest level in the mixed mode).  TF: type of the level fields.
+template <typename T, int PER, typename TF = T>
+__global__ void __launch_bounds__(256) k_ring_dst(TF* __restrict__ wf, TF* __restrict__ sf, const TF* __restrict__ wc,
+                                                  const TF* __restrict__ sc, long ps, int nx, int ny,
                                                   T* __restrict__ ring, long ring_ld,
                                                   const typename C2<T>::t* __restrict__ twx,
                                                   const typename C2<T>::t* __restrict__ twy, int logLx, int logLy,
-                                                  int nblk_y) {
+                                                  int nblk_y, int delta) {
   pdl_enter();
   using c2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -165,9 +172,10 @@ __global__ void __launch_bounds__(256) k_ring_dst(T* __restrict__ wf, T* __restr
         const int i = side ? n + 1 : ((v & 1) ? nx : 0);
         const int j = side ? ((v & 1) ? ny : 0) : n + 1;
         const bool is_w = v < 2;
-        const T val = ring_value(is_w ? wc : sc, ps, nx, ny, i, j);
-        (is_w ? wf : sf)[(long)j * ps + i] = val;
-        ab[e] = val;
+        const TF val = ring_value(is_w ? wc : sc, ps, nx, ny, i, j);
+        TF* fld = (is_w ? wf : sf) + (long)j * ps + i;
+        ab[e] = delta ? T(val - *fld) : T(val);
+        *fld = val;
       }
     }
     dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
@@ -367,26 +375,31 @@ fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
   return FSI_OK;
 }
 
-// Pass XI into the level fields w, s (mode 0 store, 1 subtract): 2*nf rows of one field per CTA, rows
-// j, j+1 sharing one FFT.
-template <typename T>
-fsi_status xi_pass(fsi_ctx* c, T* w, T* s, int mode) {
+// Pass XI into the level fields w, s of type TF (mode 0 store, 1 subtract, 2 add): 2*nf rows of one field
+// per CTA, rows j, j+1 sharing one FFT.
+template <typename T, typename TF = T>
+fsi_status xi_pass(fsi_ctx* c, TF* w, TF* s, int mode) {
   using c2 = typename C2<T>::t;
-  set_smem_limits<T>();
+  set_smem_limits<T, TF>();
   const FftCfg cx = fft_cfg(c->logLx);
   const int Lx = 1 << c->logLx;
   const c2* twx = (const c2*)c->twx;
   prof_mark(c, KC_XI);
   if (use_gemm<T>(c, 2)) {
-    const fsi_status st = gemm_xi(c, (float*)w, (float*)s, mode);
-    if (st != FSI_OK) return st;
+    if constexpr (std::is_same<T, TF>::value) {
+      if (mode == 2) return FSI_ERR_UNSUPPORTED;
+      const fsi_status st = gemm_xi(c, (float*)w, (float*)s, mode);
+      if (st != FSI_OK) return st;
+    } else {
+      return FSI_ERR_UNSUPPORTED;
+    }
   } else {
     dim3 grid(dst::xi_blocks(c->Ny, cx.nf), 1);
     const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     switch (cx.per) {
-      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 1>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
-      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 2>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
-      default: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 4>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
+      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 1, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
+      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 2, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
+      default: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 4, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
     }
   }
   prof_mark(c, KC_XI);
@@ -395,21 +408,21 @@ fsi_status xi_pass(fsi_ctx* c, T* w, T* s, int mode) {
   return FSI_OK;
 }
 
-template <typename T>
-fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, T* w, T* s, int use_ring, int mode) {
+template <typename T, typename TF = T>
+fsi_status level_solve_t(fsi_ctx* c, int g, const T* rhs, TF* w, TF* s, int use_ring, int mode) {
   fsi_status st = xf_pass<T>(c, rhs, 1);
   if (st == FSI_OK) st = y_pass<T>(c, g, (const T*)c->T1, use_ring);
-  if (st == FSI_OK) st = xi_pass<T>(c, w, s, mode);
+  if (st == FSI_OK) st = xi_pass<T, TF>(c, w, s, mode);
   return st;
 }
 
-template <typename T>
-fsi_status ring_spectra_t(fsi_ctx* c, int g) {
+template <typename T, typename TF = T>
+fsi_status ring_spectra_t(fsi_ctx* c, int g, int delta) {
   using c2 = typename C2<T>::t;
-  T* wf = (T*)c->w_all + (long)g * c->lvl_elems;
-  T* sf = (T*)c->s_all + (long)g * c->lvl_elems;
-  const T* wc = (const T*)c->w_all + (long)(g + 1) * c->lvl_elems;
-  const T* sc = (const T*)c->s_all + (long)(g + 1) * c->lvl_elems;
+  TF* wf = (TF*)c->w_all + (long)g * c->lvl_elems;
+  TF* sf = (TF*)c->s_all + (long)g * c->lvl_elems;
+  const TF* wc = (const TF*)c->w_all + (long)(g + 1) * c->lvl_elems;
+  const TF* sc = (const TF*)c->s_all + (long)(g + 1) * c->lvl_elems;
   const int Lmax = c->logLx > c->logLy ? (1 << c->logLx) : (1 << c->logLy);
   const int per = Lmax <= 1024 ? 1 : Lmax / 1024;
   const int nf_y = 4 * per * 256 / (1 << c->logLy), nf_x = 4 * per * 256 / (1 << c->logLx);
@@ -420,16 +433,16 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g) {
   static bool attrs = false;  // per instantiation
   if (!attrs) {
     attrs = true;
-    cudaFuncSetAttribute(k_ring_dst<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_ring_dst<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_ring_dst<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 1, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   prof_mark(c, KC_RING);
   const dim3 grid(nblk_y + nblk_x);
   switch (per) {
-    case 1: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 1>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
-    case 2: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 2>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
-    default: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 4>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y)); break;
+    case 1: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 1, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
+    case 2: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 2, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
+    default: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 4, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
   }
   prof_mark(c, KC_RING);
   c->launches_per_step += 1;
@@ -437,10 +450,18 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g) {
   return FSI_OK;
 }
 
-template <typename T>
+// Predictor of every level, coarse to fine.  In the mixed mode (double fields, float transforms) the finest
+// level is advanced in increment form after the first step: its right-hand side, ring spectra and inverse
+// transforms are those of w* - w^n and s* - s^n, added to the double fields, so the float transforms carry
+// errors relative to the increments (O(dt) smaller than the fields) and the fields keep double precision.
+// The increment of s solves -lap_h (s* - s^n) = w* - w^n, which holds because -lap_h s^n = w^n at the end of
+// every step (the first step, and any step after fields were set, takes the full form).  Coarser levels
+// take the full form: their solutions reach the finest level only through its ring values, smoothly.
+template <typename T, typename TF = T>
 fsi_status predictor_t(fsi_ctx* c, int first) {
-  T* w_all = (T*)c->w_all;
-  T* s_all = (T*)c->s_all;
+  TF* w_all = (TF*)c->w_all;
+  TF* s_all = (TF*)c->s_all;
+  const int delta0 = (!std::is_same<T, TF>::value && !first) ? 1 : 0;
   {
     dim3 b(32, 8), gr((c->Nx + 31) / 32, (c->Ny + 7) / 8, c->G);
     c->launches_per_step += 1;
@@ -453,10 +474,11 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
     }
     k.inv_dt = T(1.0 / c->g.dt);
     k.half_inv_re = T(0.5 / c->g.re);
+    k.inv_re = T(1.0 / c->g.re);
     k.U = T(c->g.uinf[0]);
     k.V = T(c->g.uinf[1]);
-    FSI_CUDA_TRY(pdl_launch(k_rhs<T>, gr, dim3(b), 0, c->stream, w_all, s_all, (T*)c->nprev_all, (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx,
-                                      c->ny, k, first));
+    FSI_CUDA_TRY(pdl_launch(k_rhs<T, TF>, gr, dim3(b), 0, c->stream, (const TF*)w_all, (const TF*)s_all, (TF*)c->nprev_all,
+                            (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx, c->ny, k, first, delta0));
     prof_mark(c, KC_RHS);
   }
   FSI_CUDA_TRY(cudaGetLastError());
@@ -470,25 +492,26 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
   }
   for (int g = c->G - 1; g >= 0; --g) {
     const int ring = g < c->G - 1;
+    const int inc = delta0 && g == 0;
     if (ring) {
-      fsi_status st = ring_spectra_t<T>(c, g);
+      fsi_status st = ring_spectra_t<T, TF>(c, g, inc);
       if (st != FSI_OK) return st;
     }
-    T* wg = w_all + (long)g * c->lvl_elems;
-    T* sg = s_all + (long)g * c->lvl_elems;
+    TF* wg = w_all + (long)g * c->lvl_elems;
+    TF* sg = s_all + (long)g * c->lvl_elems;
     fsi_status st;
     if (batch) {
       st = y_pass<T>(c, g, (const T*)c->T1 + (long)g * c->Nx * c->ldT, ring);
-      if (st == FSI_OK) st = xi_pass<T>(c, wg, sg, 0);
+      if (st == FSI_OK) st = xi_pass<T, TF>(c, wg, sg, inc ? 2 : 0);
     } else {
-      st = level_solve_t<T>(c, g, (const T*)c->rhs_all + (long)g * c->lvl_elems, wg, sg, ring, 0);
+      st = level_solve_t<T, TF>(c, g, (const T*)c->rhs_all + (long)g * c->lvl_elems, wg, sg, ring, inc ? 2 : 0);
     }
     if (st != FSI_OK) return st;
   }
   return FSI_OK;
 }
 
-template <typename T>
+template <typename T, typename TF = T>
 fsi_status corrector_t(fsi_ctx* c) {
   const int wi = c->ni + 6, wj = c->nj + 6;
   dim3 gr((wi + 31) / 32, (wj + 3) / 4);
@@ -507,11 +530,13 @@ fsi_status corrector_t(fsi_ctx* c) {
   FSI_CUDA_TRY(cudaGetLastError());
   const fsi_status st = launch_appended_source(c);  // E^T f of the appended points (appended.cu)
   if (st != FSI_OK) return st;
-  return level_solve_t<T>(c, 0, (const T*)c->src, (T*)c->w_all, (T*)c->s_all, 0, 1);
+  return level_solve_t<T, TF>(c, 0, (const T*)c->src, (TF*)c->w_all, (TF*)c->s_all, 0, 1);
 }
 
 }  // namespace
 
+// One level solve whose right-hand side and fields are all in the transform precision of the context (scratch
+// fields of the offline stage and the operator tests; not the double level fields of the mixed mode).
 fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void* s, int use_ring, int mode) {
   if (c->prec == FSI_PREC_FP64) return level_solve_t<double>(c, g, (const double*)rhs, (double*)w, (double*)s, use_ring, mode);
   return level_solve_t<float>(c, g, (const float*)rhs, (float*)w, (float*)s, use_ring, mode);
@@ -519,10 +544,12 @@ fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void*
 
 fsi_status launch_predictor(fsi_ctx* c, int first) {
   if (c->prec == FSI_PREC_FP64) return predictor_t<double>(c, first);
+  if (c->prec == FSI_PREC_MIXED) return predictor_t<float, double>(c, first);
   return predictor_t<float>(c, first);
 }
 
 fsi_status launch_corrector(fsi_ctx* c) {
   if (c->prec == FSI_PREC_FP64) return corrector_t<double>(c);
+  if (c->prec == FSI_PREC_MIXED) return corrector_t<float, double>(c);
   return corrector_t<float>(c);
 }

@@ -1387,7 +1387,7 @@ int fsi_min_grid(int nf) { return (nf + kMaxR - 1) / kMaxR; }
 fsi_status launch_fsi(fsi_ctx* c) {
   FsiArgs a;
   a.s0 = c->s_all;
-  a.fp64 = c->prec == FSI_PREC_FP64;
+  a.fp64 = c->fesz == 8;  // the level fields (double in the FP64 and mixed modes)
   a.ps = c->ps;
   a.x0 = c->g.x0;
   a.y0 = c->g.y0;

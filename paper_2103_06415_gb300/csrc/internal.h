@@ -103,7 +103,8 @@ struct fsi_ctx {
   fsi_grid_desc g;
   fsi_exec_desc x;
   int prec;  // FSI_PREC_*
-  size_t esz;
+  size_t esz;   // bytes per element of the transform buffers, right-hand sides and spectral tables
+  size_t fesz;  // bytes per element of the level fields w, s and the previous advection term
   cudaStream_t stream;
   int G, nx, ny, Nx, Ny, Mx, My, logLx, logLy;
   long ps;        // vertex row stride (elements)

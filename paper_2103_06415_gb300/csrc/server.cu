@@ -53,10 +53,11 @@ struct fsi_server {
 // Device bytes a request will hold: per-level fields and transform scratch, B0 and the FSI workspace.
 static size_t predict_bytes(const fsi_request* r) {
   const fsi_grid_desc& g = r->grid;
-  const size_t esz = r->precision == FSI_PREC_FP64 ? 8 : 4;
+  const size_t esz = r->precision == FSI_PREC_FP64 ? 8 : 4;      // transforms and right-hand sides
+  const size_t fesz = r->precision == FSI_PREC_FP32 ? 4 : 8;     // level fields
   const size_t ps = ((size_t)g.nx + 1 + 7) / 8 * 8;
   const size_t lvl = ((size_t)g.ny + 1) * ps;
-  size_t b = (size_t)g.n_levels * lvl * esz * 4 + lvl * esz + (2 + (size_t)g.n_levels) * g.nx * g.ny * esz;
+  size_t b = (size_t)g.n_levels * lvl * (fesz * 3 + esz) + lvl * esz + (2 + (size_t)g.n_levels) * g.nx * g.ny * esz;
   const double h = g.h;
   long i_lo = (long)std::ceil((r->box.x_lo - g.x0) / h - 1e-9), i_hi = (long)std::floor((r->box.x_hi - g.x0) / h + 1e-9);
   long j_lo = (long)std::ceil((r->box.y_lo - g.y0) / h - 1e-9), j_hi = (long)std::floor((r->box.y_hi - g.y0) / h + 1e-9);

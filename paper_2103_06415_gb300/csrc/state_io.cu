@@ -33,7 +33,7 @@ struct Blob {
 
 // the device buffers of the state, in file order (absent ones have zero size)
 std::vector<Blob> blobs(fsi_ctx* c) {
-  const size_t lvl = (size_t)c->G * c->lvl_elems * c->esz;
+  const size_t lvl = (size_t)c->G * c->lvl_elems * c->fesz;
   const size_t xbytes = c->nf > 0 ? (size_t)c->nf * fsi_float_ld(c->nf) * 4 : 0;
   std::vector<Blob> b = {
       {c->w_all, lvl},

@@ -60,8 +60,8 @@ def test_mixed_run_matches_oracle(lib, use_graph):
         h, r = ctx.history(body), oracle_history(sim, body)
         for k in range(5):
             if np.max(np.abs(r[:, k])) > 0:
-                check_rel("test_gpu_appended.py:63", h[:, k], r[:, k], 1e-10)
-    check_rel("test_gpu_appended.py:64", ctx.field(0, 0), sim.w[0], 1e-9)
+                check_rel("test_gpu_appended.py:63", h[:, k], r[:, k], 2e-12)
+    check_rel("test_gpu_appended.py:64", ctx.field(0, 0), sim.w[0], 1e-12)
     idx, wts = ctx.interp(sim.nb)
     ridx, rw = sim.last_p
     assert np.array_equal(idx[9:, 0], ridx[9:, 0]) and np.all(wts[9:, 0] == 1.0) and np.all(wts[9:, 1:] == 0.0)
@@ -79,11 +79,11 @@ def test_only_appended_points_equal_the_true_e_comparator(lib):
     a.advance(8)
     b.advance(8)
     for k in (0, 1):
-        check_rel("test_gpu_appended.py:82", a.history(0)[:, k], b.history(0)[:, k], 1e-10)
-    check_rel("test_gpu_appended.py:83", a.field(0, 0), b.field(0, 0), 1e-10)
+        check_rel("test_gpu_appended.py:82", a.history(0)[:, k], b.history(0)[:, k], 1e-13)
+    check_rel("test_gpu_appended.py:83", a.field(0, 0), b.field(0, 0), 1e-13)
 
 
-def test_appended_fp32_within_1e_4_of_fp64(lib):
+def test_appended_fp32_close_to_fp64(lib):
     w = _mixed()
     out = []
     for prec in (0, 1):
@@ -93,7 +93,7 @@ def test_appended_fp32_within_1e_4_of_fp64(lib):
         ctx.close()
     for body in (0, 1):
         for k in (0, 1):
-            check_rel("test_gpu_appended.py:96", out[1][body][:, k], out[0][body][:, k], 1e-4)
+            check_rel("test_gpu_appended.py:96", out[1][body][:, k], out[0][body][:, k], 3e-6)
 
 
 def test_appended_limits(lib, tmp_path):

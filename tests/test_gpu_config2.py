@@ -107,7 +107,7 @@ def test_full_size_histories_match_oracle(full_size_runs):
     for k, nm in ((0, "fx"), (1, "fy"), (3, "tip"), (4, "tip_rate")):
         err = rel_err(r["hist"][:, k], ref[:, k])
         print("PARITY config2 %s history rel %.3e" % (nm, err))
-        assert err < 1e-9, nm
+        assert err < 2e-11, nm
 
 
 def test_full_size_flag_state_matches_oracle(full_size_runs):
@@ -119,9 +119,9 @@ def test_full_size_flag_state_matches_oracle(full_size_runs):
     e_zeta = rel_err(zeta, b.zeta.reshape(-1, 3))
     e_zdot = rel_err(zdot, b.zetadot.reshape(-1, 3))
     print("PARITY config2 chi max abs %.3e zeta rel %.3e zetadot rel %.3e" % (e_chi, e_zeta, e_zdot))
-    assert e_chi < 1e-12
-    assert e_zeta < 1e-9
-    assert e_zdot < 1e-8
+    assert e_chi < 3e-13
+    assert e_zeta < 1e-10
+    assert e_zdot < 1e-9
 
 
 def test_full_size_fields_match_oracle(full_size_runs):
@@ -130,4 +130,4 @@ def test_full_size_fields_match_oracle(full_size_runs):
     for g, (wf, sf) in enumerate(r["fields"]):
         ew, es = rel_err(wf, r["sim"].w[g]), rel_err(sf, r["sim"].s[g])
         print("PARITY config2 level %d w rel %.3e s rel %.3e" % (g, ew, es))
-        assert ew < 1e-9 and es < 1e-9, g
+        assert ew < 1e-10 and es < 1e-10, g

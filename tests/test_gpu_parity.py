@@ -1,7 +1,8 @@
 """Parity of the CUDA library against the FP64 oracle (needs a GB300 and the built library).
 
-Tolerances: the FP64 path is held to 1e-12 relative on single solves and B0 entries, and to 1e-10 on
-multi-step histories (rounding-order differences grow slowly through the time loop).  The FP32 fluid
+Tolerances: the FP64 path is held to 1e-12 relative on single solves and B0 entries, and multi-step
+histories to about ten times the measured difference (1e-12 on the small plate, 4e-11 over config 1's 100
+steps; rounding-order differences grow slowly through the time loop).  The FP32 fluid
 path reports its error against the oracle and is held to the bounds stated in each test.
 """
 
@@ -100,13 +101,13 @@ def test_small_plate_run_matches_oracle(lib, use_graph):
     assert hist.shape == (n, 6)
     assert np.array_equal(hist[:, 5], ref[:, 5])                      # FSI iteration counts
     for k in range(5):
-        check_rel("small_plate graph=%d hist%d" % (use_graph, k), hist[:, k], ref[:, k], 1e-10)
+        check_rel("small_plate graph=%d hist%d" % (use_graph, k), hist[:, k], ref[:, k], 1e-12)
     idx, wts = ctx.interp(sim.nb)
     ridx, rw = sim.last_p
     assert np.array_equal(idx, ridx)                                  # P index map bit-exact
     assert np.max(np.abs(wts - rw)) < 1e-13
-    check_rel("small_plate graph=%d w" % use_graph, ctx.field(0, 0), sim.w[0], 1e-10)
-    check_rel("small_plate graph=%d s" % use_graph, ctx.field(0, 1), sim.s[0], 1e-10)
+    check_rel("small_plate graph=%d w" % use_graph, ctx.field(0, 0), sim.w[0], 1e-12)
+    check_rel("small_plate graph=%d s" % use_graph, ctx.field(0, 1), sim.s[0], 1e-12)
 
 
 def test_small_plate_multilevel_run_matches_oracle(lib):
@@ -117,7 +118,7 @@ def test_small_plate_multilevel_run_matches_oracle(lib):
     ctx.advance(6)
     hist, ref = ctx.history(0), oracle_history(sim)
     for k in range(5):
-        check_rel("small_plate_2lvl hist%d" % k, hist[:, k], ref[:, k], 1e-10)
+        check_rel("small_plate_2lvl hist%d" % k, hist[:, k], ref[:, k], 2e-12)
 
 
 def test_plate_128_run_matches_oracle(lib):
@@ -130,7 +131,7 @@ def test_plate_128_run_matches_oracle(lib):
     hist, ref = ctx.history(0), oracle_history(sim)
     assert np.array_equal(hist[:, 5], ref[:, 5])
     for k in range(5):
-        check_rel("plate_128 hist%d" % k, hist[:, k], ref[:, k], 1e-9)
+        check_rel("plate_128 hist%d" % k, hist[:, k], ref[:, k], 4e-11)
 
 
 def test_fp32_fluid_path_error_vs_oracle(lib):
