@@ -61,7 +61,10 @@ typedef enum { FSI_BODY_RIGID = 0, FSI_BODY_TORSIONAL = 1, FSI_BODY_DEFORMABLE =
 
 /* Fluid grid (Sec. 2.2; multidomain of Sec. 5).  Level 0 is the finest: nx x ny cells of spacing h with
  * lower-left corner (x0, y0).  Level g has the same cell counts, spacing 2^g h and the same centre.
- * nx and ny must be powers of two in [16, 2048] (the DST length N+1 = nx, ny); n_levels >= 1.
+ * nx and ny must be 2^k or 3 * 2^k in [16, 2048] (the DST lengths N+1 = nx, ny; the sine transforms use
+ * radix-4/2 stages and, for 3 * 2^k, one radix-3 stage); when one axis has 3 * 2^k cells, an axis of 2^k
+ * cells may have at most 512 (e.g. 1536 x 768, 1536 x 512, 768 x 512); otherwise FSI_ERR_INVALID_ARG.
+ * n_levels >= 1.
  * re = Reynolds number, dt = time step, uinf = free-stream velocity. */
 typedef struct {
   int nx, ny, n_levels;

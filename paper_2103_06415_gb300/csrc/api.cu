@@ -64,16 +64,31 @@ static void ctx_free_all(fsi_ctx* c) {
   c->dev_bytes = 0;
 }
 
-static bool pow2_ok(int n) { return n >= 16 && (n & (n - 1)) == 0 && n <= 2048; }
+// Cells per axis: 2^k or 3 * 2^k in [16, 2048] (the sine-transform length 2n is then 2^(k+1) or 3 * 2^(k+1)).
+static bool cells_ok(int n) {
+  int logP = 0, r3 = 1;
+  return n >= 16 && n <= 2048 && dst::split_length(2 * n, &logP, &r3);
+}
 
-// Complex twiddles of length L in the stage order of dst::block_fft (entry p: m = twiddle_exponent(p, log2 L)).
+// The ring transforms of a grid with a 3 * 2^k axis run with one butterfly set per thread: both axes' lengths
+// must then have power-of-two parts of at most 1024 (e.g. 1536 x 768, 1536 x 512, 768 x 512).
+static bool grid_ok(int nx, int ny) {
+  int lx = 0, ly = 0, rx = 1, ry = 1;
+  if (!cells_ok(nx) || !cells_ok(ny)) return false;
+  dst::split_length(2 * nx, &lx, &rx);
+  dst::split_length(2 * ny, &ly, &ry);
+  return (rx == 1 && ry == 1) || (lx <= 10 && ly <= 10);
+}
+
+// Complex twiddles of length L = r3 2^logP in the stage order of dst::block_fft (entry p: m =
+// twiddle_exponent(p, logP, r3)).
 template <typename T>
 static fsi_status upload_twiddles(fsi_ctx* c, int L, void** out) {
   std::vector<T> tw(2 * (size_t)L);
-  int logL = 0;
-  while ((1 << logL) < L) ++logL;
+  int logP = 0, r3 = 1;
+  dst::split_length(L, &logP, &r3);
   for (int p = 0; p < L; ++p) {
-    const int m = dst::twiddle_exponent(p, logL);
+    const int m = dst::twiddle_exponent(p, logP, r3);
     const double a = -2.0 * M_PI * (double)m / (double)L;
     tw[2 * p] = (T)std::cos(a);
     tw[2 * p + 1] = (T)std::sin(a);
@@ -115,8 +130,8 @@ static fsi_status create_impl(fsi_ctx* c) {
   c->Ny = g.ny - 1;
   c->Mx = g.nx;
   c->My = g.ny;
-  c->logLx = ilog2_exact(2 * g.nx);
-  c->logLy = ilog2_exact(2 * g.ny);
+  dst::split_length(2 * g.nx, &c->logPx, &c->r3x);
+  dst::split_length(2 * g.ny, &c->logPy, &c->r3y);
   c->ps = padded_stride(g.nx + 1);
   c->lvl_elems = (long)(g.ny + 1) * c->ps;
   c->ldT = padded_stride(c->Ny);
@@ -279,7 +294,7 @@ static fsi_status dst_select(fsi_ctx* c) {
 extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc* exec, fsi_ctx** out) {
   if (!grid || !out) return FSI_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!pow2_ok(grid->nx) || !pow2_ok(grid->ny) || grid->n_levels < 1 || grid->n_levels > 12 || !(grid->h > 0) ||
+  if (!grid_ok(grid->nx, grid->ny) || grid->n_levels < 1 || grid->n_levels > 12 || !(grid->h > 0) ||
       !(grid->re > 0) || !(grid->dt > 0) || !std::isfinite(grid->x0) || !std::isfinite(grid->y0))
     return FSI_ERR_INVALID_ARG;
   fsi_ctx* c = new (std::nothrow) fsi_ctx();

@@ -26,7 +26,7 @@ namespace {
 // so two rows packed as y_a + i y_b give Y_a = Re Z, Y_b = Im Z of one complex FFT of length L = 2M.
 // Rows come from `in` (element (r, l) at in[r*in_rs + (l-1)*in_es]) or, when in == NULL, from the spectral
 // Green's-function weights d_kl = 1/(lambda_kl a_kl) with k = r+1 (the first cosine sum of g).
-template <int PER>
+template <int PER, int R3 = 1>
 __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, long in_rs, long in_es, int nrows,
                                               int M, double* __restrict__ out, long out_rs, long out_es,
                                               const double2* __restrict__ tw, int logL, double scale,
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, lon
                                               double inv_h2, double inv_dt, double inv_2re) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* buf = reinterpret_cast<double2*>(smem_raw);
-  const int L = 1 << logL;
+  const int L = R3 << logL;  // logL: log2 of the power-of-two part
   const double2* tws = dst::stage_twiddles<double>(buf + L, tw, L, (size_t)2 * L * sizeof(double2));
   const int r0 = 2 * blockIdx.x;
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, lon
     buf[l] = make_double2(a, b);
   }
   __syncthreads();
-  dst::block_fft<double, PER>(buf, L, logL, tws);
+  dst::block_fft<double, PER, R3>(buf, L, logL, tws);
   for (int q = threadIdx.x; q <= M; q += blockDim.x) {
     const double2 z = buf[q];
     if (r0 < nrows) out[(long)r0 * out_rs + (long)q * out_es] = 0.5 * scale * z.x;
@@ -67,13 +67,15 @@ __global__ void __launch_bounds__(256) k_dct1(const double* __restrict__ in, lon
   }
 }
 
-// launch: one CTA per row pair, L/(4 PER) threads (one complex row of length L per CTA)
+// launch: one CTA per row pair, 2^logP / (4 PER) threads (one complex row of length L = r3 2^logP per CTA)
 fsi_status launch_dct1(const double* in, long in_rs, long in_es, int nrows, int M, double* out, long out_rs,
-                       long out_es, const double2* tw, int logL, double scale, const double* lx, const double* ly,
+                       long out_es, const double2* tw, int L, double scale, const double* lx, const double* ly,
                        double inv_h2, double inv_dt, double inv_2re, cudaStream_t st) {
-  const int L = 1 << logL;
-  const int nthr = L / 4 < 256 ? L / 4 : 256;
-  const int per = L / (4 * nthr);
+  int logL = 0, r3 = 1;
+  if (!dst::split_length(L, &logL, &r3)) return FSI_ERR_UNSUPPORTED;
+  const int P = 1 << logL;
+  const int nthr = P / 4 < 256 ? P / 4 : 256;
+  const int per = P / (4 * nthr);
   const size_t sm = dst::pass_smem<double>((size_t)L, L);
   const dim3 grid((nrows + 1) / 2);
   static bool attrs = false;
@@ -82,6 +84,14 @@ fsi_status launch_dct1(const double* in, long in_rs, long in_es, int nrows, int 
     cudaFuncSetAttribute(k_dct1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dct1<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dct1<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+  if (r3 == 3) {
+    if (per == 1) k_dct1<1, 3><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re);
+    else if (per == 2) k_dct1<2, 3><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re);
+    else return FSI_ERR_UNSUPPORTED;
+    return cudaGetLastError() == cudaSuccess ? FSI_OK : FSI_ERR_CUDA;
   }
   switch (per) {
     case 1: k_dct1<1><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re); break;
@@ -214,14 +224,16 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
     if (t > max_tab) max_tab = t;
   }
   std::vector<double> twx(4 * (size_t)Mx), twy(4 * (size_t)My);  // stage order of dst::block_fft
-  const int logLx = ilog2_exact(2 * Mx), logLy = ilog2_exact(2 * My);
+  int logLx = 0, logLy = 0, r3x = 1, r3y = 1;
+  dst::split_length(2 * Mx, &logLx, &r3x);
+  dst::split_length(2 * My, &logLy, &r3y);
   for (int p = 0; p < 2 * Mx; ++p) {
-    const int m = dst::twiddle_exponent(p, logLx);
+    const int m = dst::twiddle_exponent(p, logLx, r3x);
     twx[2 * p] = std::cos(-M_PI * (double)m / (double)Mx);
     twx[2 * p + 1] = std::sin(-M_PI * (double)m / (double)Mx);
   }
   for (int p = 0; p < 2 * My; ++p) {
-    const int m = dst::twiddle_exponent(p, logLy);
+    const int m = dst::twiddle_exponent(p, logLy, r3y);
     twy[2 * p] = std::cos(-M_PI * (double)m / (double)My);
     twy[2 * p + 1] = std::sin(-M_PI * (double)m / (double)My);
   }
@@ -245,10 +257,10 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
       st = FSI_ERR_CUDA;
       break;
     }
-    st = launch_dct1(nullptr, 0, 0, Nx, My, d_T1, My + 1, 1, (const double2*)d_twy, ilog2_exact(2 * My), 1.0, c->lx,
+    st = launch_dct1(nullptr, 0, 0, Nx, My, d_T1, My + 1, 1, (const double2*)d_twy, 2 * My, 1.0, c->lx,
                      c->ly, 1.0 / (h * h), 1.0 / c->g.dt, 0.5 / c->g.re, c->stream);
     if (st != FSI_OK) break;
-    st = launch_dct1(d_T1, 1, My + 1, My + 1, Mx, d_g, 1, My + 1, (const double2*)d_twx, ilog2_exact(2 * Mx),
+    st = launch_dct1(d_T1, 1, My + 1, My + 1, Mx, d_g, 1, My + 1, (const double2*)d_twx, 2 * Mx,
                      1.0 / ((double)Mx * (double)My), nullptr, nullptr, 0.0, 0.0, 0.0, c->stream);
     if (st != FSI_OK) break;
     k_tables<<<dim3((unsigned)((max_tab + 127) / 128), nb), 128, 0, c->stream>>>(d_tab, d_bx, d_g, Mx, My, h);

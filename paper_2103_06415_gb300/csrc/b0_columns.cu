@@ -66,22 +66,41 @@ void set_attrs() {
   cudaFuncSetAttribute(dst::k_xi<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xf<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_ysolve<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 1, T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
+// Launch shape of the passes for a length r3 2^logP (as the fluid step's): 4 PER threads = nf 2^logP.
 struct Shape {
-  int nthr, per, nf;
+  int nthr, per, nf, r3, logP, L;
 };
-Shape shape_for(int logL) {
-  const int L = 1 << logL;
+Shape shape_for(int logP, int r3) {
+  const int P = 1 << logP;
   Shape c;
-  c.nthr = L / 4;
+  c.nthr = P / 4;
   if (c.nthr < 32) c.nthr = 32;
   if (c.nthr > 256) c.nthr = 256;
   c.per = 1;
-  while (4 * c.per * c.nthr < L) c.per *= 2;
-  c.nf = 4 * c.per * c.nthr / L;
+  while (4 * c.per * c.nthr < P) c.per *= 2;
+  c.nf = 4 * c.per * c.nthr / P;
+  c.r3 = r3;
+  c.logP = logP;
+  c.L = r3 << logP;
   return c;
 }
+
+#define COL_DISPATCH(cfg, LAUNCH)   \
+  do {                              \
+    if ((cfg).r3 == 3)              \
+      LAUNCH(1, 3);                 \
+    else if ((cfg).per == 1)        \
+      LAUNCH(1, 1);                 \
+    else if ((cfg).per == 2)        \
+      LAUNCH(2, 1);                 \
+    else                            \
+      LAUNCH(4, 1);                 \
+  } while (0)
 
 template <typename T>
 fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
@@ -117,8 +136,8 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
                              c->stream) != cudaSuccess) {
     st = FSI_ERR_CUDA;
   }
-  const Shape cx = shape_for(c->logLx), cy = shape_for(c->logLy);
-  const int Lx = 1 << c->logLx, Ly = 1 << c->logLy;
+  const Shape cx = shape_for(c->logPx, c->r3x), cy = shape_for(c->logPy, c->r3y);
+  const int Lx = cx.L, Ly = cy.L;
   const c2* twx = (const c2*)c->twx;
   const c2* twy = (const c2*)c->twy;
   const double h = c->g.h, inv2h = 0.5 / h;
@@ -133,23 +152,23 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     {
       dim3 grid((Ny + 2 * cx.nf - 1) / (2 * cx.nf), nc);
       const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
-      if (cx.per == 1) dst::k_xf<T, 1><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
-      else if (cx.per == 2) dst::k_xf<T, 2><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
-      else dst::k_xf<T, 4><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, c->logLx, cx.nf);
+#define XF(P, R) dst::k_xf<T, P, R><<<grid, cx.nthr, sm, c->stream>>>(src, ps, lvl, Ny, Nx, T1, c->ldT, t1, twx, cx.logP, cx.nf)
+      COL_DISPATCH(cx, XF);
+#undef XF
     }
     {
       dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf), nc);
       const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-      if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
-      else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
-      else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, c->logLy, cy.nf, sp);
+#define YS(P, R) dst::k_ysolve<T, P, R><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, cy.logP, cy.nf, sp)
+      COL_DISPATCH(cy, YS);
+#undef YS
     }
     {
       dim3 grid(dst::xi_blocks(Ny, cx.nf), nc);
       const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
-      if (cx.per == 1) dst::k_xi<T, 1><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
-      else if (cx.per == 2) dst::k_xi<T, 2><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
-      else dst::k_xi<T, 4><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, c->logLx, cx.nf);
+#define XI(P, R) dst::k_xi<T, P, T, R><<<grid, cx.nthr, sm, c->stream>>>(T2w, T2s, c->ldX, t2, Ny, Nx, fw, fs, ps, lvl, 0, twx, cx.logP, cx.nf)
+      COL_DISPATCH(cx, XI);
+#undef XI
     }
     k_col_gather<T><<<dim3((unsigned)((max_n2 + 255) / 256), nc), 256, 0, c->stream>>>(out, fs, lvl, ps, col0, nc,
                                                                                        d_bx, n_boxes, inv2h);

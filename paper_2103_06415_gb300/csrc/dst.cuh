@@ -1,5 +1,5 @@
-// Batched DST-I passes built on a shared-memory Stockham FFT (radix 4, one radix-2 stage when log2 L is
-// odd).  The DST-I of two real rows x1, x2 of length N = M-1 is read off one complex FFT of length
+// Batched DST-I passes built on a shared-memory Stockham FFT (radix 4, one radix-2 stage when the log2 of the
+// power-of-two part is odd, one radix-3 stage for lengths 3 * 2^k).  The DST-I of two real rows x1, x2 of length N = M-1 is read off one complex FFT of length
 // L = 2M of the packed odd extension z = (x1 + i x2) extended oddly about 0 and M:
 //   X1_k = -Im(Z_k)/2,  X2_k = Re(Z_k)/2,  k = 1..N,
 // with X_k = sum_j x_j sin(pi j k / M) (unnormalised; the inverse is (2/M) times the same transform).
@@ -11,124 +11,227 @@
 
 namespace dst {
 
+// Transform lengths L = R3 * 2^logP with R3 = 1 or 3 (DST-I lengths N = L/2 - 1 for grids of 2^k or 3 * 2^k
+// cells).  The power-of-two part is done by radix-4 stages (one radix-2 stage when logP is odd); with R3 = 3 a
+// final radix-3 stage follows (ns = 2^logP, inputs and outputs at the same three positions j, j + P, j + 2P).
+//
 // Twiddle table of length L in stage order: entry p holds exp(-2 pi i m / L) with m = twiddle_exponent(p,
-// logL).  A radix-4 stage with ns = 4^s > 1 (s >= 1) reads its three twiddles w_r(k) = exp(-2 pi i r k /
-// (4 ns)), r = 1..3, k < ns, from the block at ns - 4, laid out [r - 1][k]; a final radix-2 stage (odd
-// logL) reads exp(-2 pi i k / L), k < L/2, from the block at L/2 - 4.  The threads of a warp read
-// consecutive k (or the same k), so these shared-memory loads are free of bank conflicts, which the
-// natural-order table (index r k L/(4 ns), a power-of-two stride) is not.  The blocks fill L - 4 entries.
-__host__ __device__ inline int twiddle_exponent(int p, int logL) {
-  for (int logNs = 2; logL - logNs >= 2; logNs += 2) {
+// logP, R3).  A radix-4 stage with ns = 4^s > 1 (s >= 1) reads its three twiddles w_r(k) = exp(-2 pi i r k /
+// (4 ns)), r = 1..3, k < ns, from the block at ns - 4, laid out [r - 1][k]; a radix-2 stage (odd logP) reads
+// exp(-2 pi i k / P), k < P/2, from the block at P/2 - 4; the radix-3 stage reads exp(-2 pi i r k / L),
+// r = 1, 2, k < P, from the block at P - 4, laid out [r - 1][k].  The threads of a warp read consecutive k (or
+// the same k), so these shared-memory loads are free of bank conflicts, which the natural-order table (index
+// r k L/(4 ns), a power-of-two stride) is not.  The blocks fill L - 4 entries.
+__host__ __device__ inline int twiddle_exponent(int p, int logP, int R3 = 1) {
+  for (int logNs = 2; logP - logNs >= 2; logNs += 2) {
     const int ns = 1 << logNs;
     const int q = p - (ns - 4);
-    if (q < 3 * ns) return (q / ns + 1) * ((q % ns) << (logL - logNs - 2));
+    if (q < 3 * ns) return (q / ns + 1) * (((q % ns) * R3) << (logP - logNs - 2));
   }
-  if (logL & 1) {
-    const int q = p - ((1 << (logL - 1)) - 4);
-    if (q >= 0 && q < (1 << (logL - 1))) return q;
+  const int P = 1 << logP;
+  if (logP & 1) {
+    const int q = p - ((P >> 1) - 4);
+    if (q >= 0 && q < (P >> 1)) return q * R3;
+  }
+  if (R3 == 3) {
+    const int q = p - (P - 4);
+    if (q >= 0 && q < 2 * P) return (q / P + 1) * (q % P);
   }
   return 0;
 }
 
+// Split a transform length L into R3 * 2^logP (R3 = 1 or 3, logP >= 4); false for other lengths.
+__host__ __device__ inline bool split_length(int L, int* logP, int* R3) {
+  int r = 1;
+  if (L % 3 == 0) {
+    r = 3;
+    L /= 3;
+  }
+  if (L < 16 || (L & (L - 1)) != 0) return false;
+  int k = 0;
+  while ((1 << k) < L) ++k;
+  *logP = k;
+  *R3 = r;
+  return true;
+}
+
+// Butterfly b of a stage splits into the transform f it belongs to and its index j inside the transform,
+// with Lr = R3 * 2^logLr butterflies per transform.
+template <int R3>
+__host__ __device__ __forceinline__ void stage_index(int b, int logLr, int* f, int* j) {
+  const int q = b >> logLr;
+  const int fv = R3 == 1 ? q : q / 3;
+  *f = fv;
+  *j = b - ((fv * R3) << logLr);
+}
+
+// The butterflies of one stage, split into a load (from the stage's input, which a barrier separates from
+// the stores) and a compute-and-store, so that a host program can run the same code over all butterflies to
+// check indices and results.  buf holds the transforms back to back (transform f at f * L).
+template <typename T, int R3>
+__host__ __device__ __forceinline__ void r4_load(const typename C2<T>::t* buf, int L, int logP, int b,
+                                                 typename C2<T>::t* a) {
+  const int logLr = logP - 2, Lr = R3 << logLr;
+  int f, j;
+  stage_index<R3>(b, logLr, &f, &j);
+  const typename C2<T>::t* x = buf + (long)f * L;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) a[r] = x[j + r * Lr];
+}
+
+template <typename T, int R3>
+__host__ __device__ __forceinline__ void r4_store(typename C2<T>::t* buf, int L, int logP, int logNs, int b,
+                                                  const typename C2<T>::t* tw, typename C2<T>::t* a) {
+  using c2 = typename C2<T>::t;
+  const int logLr = logP - 2;
+  int f, j;
+  stage_index<R3>(b, logLr, &f, &j);
+  const int k = j & ((1 << logNs) - 1);
+  if (logNs > 0) {
+    const c2* tws = tw + ((1 << logNs) - 4) + k;  // stage block [r - 1][k]
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+      const c2 w = tws[(r - 1) << logNs];
+      const T re = a[r].x * w.x - a[r].y * w.y;
+      const T im = a[r].x * w.y + a[r].y * w.x;
+      a[r].x = re;
+      a[r].y = im;
+    }
+  }
+  const T a0x = a[0].x + a[2].x, a0y = a[0].y + a[2].y;
+  const T a1x = a[0].x - a[2].x, a1y = a[0].y - a[2].y;
+  const T a2x = a[1].x + a[3].x, a2y = a[1].y + a[3].y;
+  const T dx = a[1].x - a[3].x, dy = a[1].y - a[3].y;  // (d)(-i) = (dy, -dx)
+  c2* x = buf + (long)f * L;
+  const int o = ((j >> logNs) << (logNs + 2)) + k;
+  const int ns = 1 << logNs;
+  if (sizeof(T) == 4 && logNs == 0) {  // the four outputs are adjacent: two 16-byte stores
+    float4* x4 = reinterpret_cast<float4*>(x + o);
+    x4[0] = make_float4(a0x + a2x, a0y + a2y, a1x + dy, a1y - dx);
+    x4[1] = make_float4(a0x - a2x, a0y - a2y, a1x - dy, a1y + dx);
+    return;
+  }
+  x[o].x = a0x + a2x;
+  x[o].y = a0y + a2y;
+  x[o + ns].x = a1x + dy;
+  x[o + ns].y = a1y - dx;
+  x[o + 2 * ns].x = a0x - a2x;
+  x[o + 2 * ns].y = a0y - a2y;
+  x[o + 3 * ns].x = a1x - dy;
+  x[o + 3 * ns].y = a1y + dx;
+}
+
+template <typename T, int R3>
+__host__ __device__ __forceinline__ void r2_load(const typename C2<T>::t* buf, int L, int logP, int b,
+                                                 typename C2<T>::t* a) {
+  const int logLr = logP - 1, Lr = R3 << logLr;
+  int f, j;
+  stage_index<R3>(b, logLr, &f, &j);
+  const typename C2<T>::t* x = buf + (long)f * L;
+  a[0] = x[j];
+  a[1] = x[j + Lr];
+}
+
+template <typename T, int R3>
+__host__ __device__ __forceinline__ void r2_store(typename C2<T>::t* buf, int L, int logP, int logNs, int b,
+                                                  const typename C2<T>::t* tw, typename C2<T>::t* a) {
+  using c2 = typename C2<T>::t;
+  const int logLr = logP - 1;
+  int f, j;
+  stage_index<R3>(b, logLr, &f, &j);
+  const int k = j & ((1 << logNs) - 1);
+  c2 a0 = a[0], a1 = a[1];
+  if (logNs > 0) {
+    const c2 w = tw[(1 << (logP - 1)) - 4 + k];  // logNs = logP - 1: the radix-2 stage of an odd logP
+    const T re = a1.x * w.x - a1.y * w.y;
+    const T im = a1.x * w.y + a1.y * w.x;
+    a1.x = re;
+    a1.y = im;
+  }
+  c2* x = buf + (long)f * L;
+  const int o = ((j >> logNs) << (logNs + 1)) + k;
+  x[o].x = a0.x + a1.x;
+  x[o].y = a0.y + a1.y;
+  x[o + (1 << logNs)].x = a0.x - a1.x;
+  x[o + (1 << logNs)].y = a0.y - a1.y;
+}
+
+// Radix-3 stage (the last one, ns = P = 2^logP): butterfly j of transform f takes x[j], x[j + P], x[j + 2P],
+// twists the second and third by w^k, w^2k (w = exp(-2 pi i / L), k = j) and writes back to the same places:
+// with s = a1 + a2, d = a1 - a2, t = a0 - s/2 and c = sqrt(3)/2 the outputs are a0 + s, t - i c d, t + i c d.
+template <typename T>
+__host__ __device__ __forceinline__ void r3_load(const typename C2<T>::t* buf, int L, int logP, int b,
+                                                 typename C2<T>::t* a) {
+  const int P = 1 << logP;
+  const int f = b >> logP, j = b & (P - 1);
+  const typename C2<T>::t* x = buf + (long)f * L;
+  a[0] = x[j];
+  a[1] = x[j + P];
+  a[2] = x[j + 2 * P];
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void r3_store(typename C2<T>::t* buf, int L, int logP, int b,
+                                                  const typename C2<T>::t* tw, typename C2<T>::t* a) {
+  using c2 = typename C2<T>::t;
+  const int P = 1 << logP;
+  const int f = b >> logP, k = b & (P - 1);
+  const c2 w1 = tw[P - 4 + k], w2 = tw[2 * P - 4 + k];
+  const T b1x = a[1].x * w1.x - a[1].y * w1.y, b1y = a[1].x * w1.y + a[1].y * w1.x;
+  const T b2x = a[2].x * w2.x - a[2].y * w2.y, b2y = a[2].x * w2.y + a[2].y * w2.x;
+  const T sx = b1x + b2x, sy = b1y + b2y, dx = b1x - b2x, dy = b1y - b2y;
+  const T tx = a[0].x - T(0.5) * sx, ty = a[0].y - T(0.5) * sy;
+  const T c = T(0.86602540378443864676);  // sqrt(3) / 2
+  c2* x = buf + (long)f * L;
+  x[k].x = a[0].x + sx;
+  x[k].y = a[0].y + sy;
+  x[k + P].x = tx + c * dy;   // t - i c d
+  x[k + P].y = ty - c * dx;
+  x[k + 2 * P].x = tx - c * dy;  // t + i c d
+  x[k + 2 * P].y = ty + c * dx;
+}
+
 // The passes below copy the table into shared memory before their first barrier, so the stages read it
-// there.
-template <typename T, int PER>
-__device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int logL,
+// there.  A CTA transforms nf = 4 PER blockDim / 2^logP transforms of length L = R3 2^logP: PER R3 radix-4
+// butterflies (2 PER R3 radix-2, 4 PER radix-3) per thread and stage.
+template <typename T, int PER, int R3 = 1>
+__device__ __forceinline__ void block_fft(typename C2<T>::t* buf, int L, int logP,
                                           const typename C2<T>::t* __restrict__ tw) {
   using c2 = typename C2<T>::t;
   const int nthr = blockDim.x, tid = threadIdx.x;
   int logNs = 0;
-  int rem = logL;
+  int rem = logP;
   while (rem > 0) {
-    c2 v[4 * PER];
     if (rem >= 2) {
-      const int logLr = logL - 2, Lr = 1 << logLr;
+      c2 v[4 * PER * R3];
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int b = tid + q * nthr;
-        const int f = b >> logLr, j = b & (Lr - 1);
-        const c2* x = buf + ((long)f << logL);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[4 * q + r] = x[j + r * Lr];
-      }
+      for (int q = 0; q < PER * R3; ++q) r4_load<T, R3>(buf, L, logP, tid + q * nthr, &v[4 * q]);
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int b = tid + q * nthr;
-        const int f = b >> logLr, j = b & (Lr - 1);
-        const int k = j & ((1 << logNs) - 1);
-        c2* a = &v[4 * q];
-        if (logNs > 0) {
-          const c2* tws = tw + ((1 << logNs) - 4) + k;  // stage block [r - 1][k]
-#pragma unroll
-          for (int r = 1; r < 4; ++r) {
-            const c2 w = tws[(r - 1) << logNs];
-            const T re = a[r].x * w.x - a[r].y * w.y;
-            const T im = a[r].x * w.y + a[r].y * w.x;
-            a[r].x = re;
-            a[r].y = im;
-          }
-        }
-        const T a0x = a[0].x + a[2].x, a0y = a[0].y + a[2].y;
-        const T a1x = a[0].x - a[2].x, a1y = a[0].y - a[2].y;
-        const T a2x = a[1].x + a[3].x, a2y = a[1].y + a[3].y;
-        const T dx = a[1].x - a[3].x, dy = a[1].y - a[3].y;  // (d)(-i) = (dy, -dx)
-        c2* x = buf + ((long)f << logL);
-        const int o = ((j >> logNs) << (logNs + 2)) + k;
-        const int ns = 1 << logNs;
-        if (sizeof(T) == 4 && logNs == 0) {  // the four outputs are adjacent: two 16-byte stores
-          float4* x4 = reinterpret_cast<float4*>(x + o);
-          x4[0] = make_float4(a0x + a2x, a0y + a2y, a1x + dy, a1y - dx);
-          x4[1] = make_float4(a0x - a2x, a0y - a2y, a1x - dy, a1y + dx);
-          continue;
-        }
-        x[o].x = a0x + a2x;
-        x[o].y = a0y + a2y;
-        x[o + ns].x = a1x + dy;
-        x[o + ns].y = a1y - dx;
-        x[o + 2 * ns].x = a0x - a2x;
-        x[o + 2 * ns].y = a0y - a2y;
-        x[o + 3 * ns].x = a1x - dy;
-        x[o + 3 * ns].y = a1y + dx;
-      }
+      for (int q = 0; q < PER * R3; ++q) r4_store<T, R3>(buf, L, logP, logNs, tid + q * nthr, tw, &v[4 * q]);
       __syncthreads();
       logNs += 2;
       rem -= 2;
     } else {
-      const int logLr = logL - 1, Lr = 1 << logLr;
+      c2 v[4 * PER * R3];
 #pragma unroll
-      for (int q = 0; q < 2 * PER; ++q) {
-        const int b = tid + q * nthr;
-        const int f = b >> logLr, j = b & (Lr - 1);
-        const c2* x = buf + ((long)f << logL);
-        v[2 * q] = x[j];
-        v[2 * q + 1] = x[j + Lr];
-      }
+      for (int q = 0; q < 2 * PER * R3; ++q) r2_load<T, R3>(buf, L, logP, tid + q * nthr, &v[2 * q]);
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 2 * PER; ++q) {
-        const int b = tid + q * nthr;
-        const int f = b >> logLr, j = b & (Lr - 1);
-        const int k = j & ((1 << logNs) - 1);
-        c2 a0 = v[2 * q], a1 = v[2 * q + 1];
-        if (logNs > 0) {
-          const c2 w = tw[(1 << (logL - 1)) - 4 + k];  // logNs = logL - 1: the final radix-2 stage
-          const T re = a1.x * w.x - a1.y * w.y;
-          const T im = a1.x * w.y + a1.y * w.x;
-          a1.x = re;
-          a1.y = im;
-        }
-        c2* x = buf + ((long)f << logL);
-        const int o = ((j >> logNs) << (logNs + 1)) + k;
-        x[o].x = a0.x + a1.x;
-        x[o].y = a0.y + a1.y;
-        x[o + (1 << logNs)].x = a0.x - a1.x;
-        x[o + (1 << logNs)].y = a0.y - a1.y;
-      }
+      for (int q = 0; q < 2 * PER * R3; ++q) r2_store<T, R3>(buf, L, logP, logNs, tid + q * nthr, tw, &v[2 * q]);
       __syncthreads();
       logNs += 1;
       rem -= 1;
     }
+  }
+  if (R3 == 3) {
+    c2 v[12 * PER];
+#pragma unroll
+    for (int q = 0; q < 4 * PER; ++q) r3_load<T>(buf, L, logP, tid + q * nthr, &v[3 * q]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4 * PER; ++q) r3_store<T>(buf, L, logP, tid + q * nthr, tw, &v[3 * q]);
+    __syncthreads();
   }
 }
 
@@ -265,17 +368,17 @@ __device__ __forceinline__ void store_pair(T* __restrict__ out, long off, int ro
 
 // Pass XF: rows j of `in` (row stride in_ld, nrows rows of length N) -> unnormalised DST along the row ->
 // transposed store out[k*out_ld + j] (k = 0..N-1).  blockIdx.y indexes a batch with element strides.
-template <typename T, int PER>
+template <typename T, int PER, int R3 = 1>
 __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                             T* __restrict__ out, long out_ld, long out_bs,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
   using c2 = typename C2<T>::t;
-  constexpr int NC = 2 * PER;
+  constexpr int NC = 2 * PER * R3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
-  const int L = 1 << logL;
+  const int L = R3 << logL;  // logL: log2 of the power-of-two part of the length
   const int tid = threadIdx.x, nthr = blockDim.x;
-  TwiddleStage<T, 4 * PER> ts;
+  TwiddleStage<T, 4 * PER * R3> ts;
   ts.load(tw, L, ((size_t)nf + 1) * L * sizeof(c2));
   pdl_enter();
   const int row0 = blockIdx.x * 2 * nf;
@@ -299,11 +402,11 @@ __global__ void __launch_bounds__(256) k_xf(const T* __restrict__ in, long in_ld
   }
   const c2* tws = ts.store(buf + (long)nf * L, tw, L);
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tws);
+  block_fft<T, PER, R3>(buf, L, logL, tws);
   const int lognf = __ffs(nf) - 1;
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    const int idx = tid + q * nthr;  // nf * N < 2 PER blockDim.x
+    const int idx = tid + q * nthr;  // nf * N < 2 PER R3 blockDim.x
     if (idx < nf * N) {
       const int f = idx & (nf - 1), k = idx >> lognf;
       const int row = row0 + 2 * f;
@@ -342,21 +445,21 @@ __device__ __forceinline__ YRow<T> y_row(const SpecParams<T>& sp, int k, int nro
 // Pass Y: rows k of `in` (x-frequency k+1; nrows = Nx rows of length N = Ny) -> DST along y -> diagonal
 // solve for w~ = (r^ + bc_w)/A_w and s~ = (w~ + bc_s)/lambda, both times norm -> DST along y (inverse) ->
 // transposed stores outw[j*out_ld + k], outs[j*out_ld + k].
-template <typename T, int PER>
+template <typename T, int PER, int R3 = 1>
 __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                                 T* __restrict__ outw, T* __restrict__ outs, long out_ld,
                                                 long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
                                                 int nf, SpecParams<T> sp) {
   using c2 = typename C2<T>::t;
-  constexpr int NC = 2 * PER;
+  constexpr int NC = 2 * PER * R3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
-  const int L = 1 << logL;
+  const int L = R3 << logL;
   c2* buf2 = buf + (long)nf * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int row0 = blockIdx.x * 2 * nf;
   // constant tables (set up with the context): loaded before the wait for the predecessor
-  TwiddleStage<T, 4 * PER> ts;
+  TwiddleStage<T, 4 * PER * R3> ts;
   ts.load(tw, L, (3 * (size_t)nf + 1) * L * sizeof(c2));
   T lyv[NC], sy1v[NC], syNv[NC];
 #pragma unroll
@@ -404,7 +507,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
   }
   const c2* tws = ts.store(buf + 3L * nf * L, tw, L);
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tws);
+  block_fft<T, PER, R3>(buf, L, logL, tws);
   for (int f = 0; f < nf; ++f) {
     YRow<T> rw[2];
     if (f == 0) {
@@ -449,11 +552,11 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     }
   }
   __syncthreads();
-  block_fft<T, 2 * PER>(buf2, L, logL, tws);
+  block_fft<T, 2 * PER, R3>(buf2, L, logL, tws);
   const int lognf = __ffs(nf) - 1;
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    const int idx = tid + q * nthr;  // nf * N < 2 PER blockDim.x
+    const int idx = tid + q * nthr;  // nf * N < 2 PER R3 blockDim.x
     if (idx < nf * N) {
       const int f = idx & (nf - 1), j = idx >> lognf;
       const int row = row0 + 2 * f;
@@ -469,18 +572,18 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
 // 2: add (fields of type TF = double with float transforms: the increments of the mixed mode).
 // blockIdx.x = 2 * (row block) + field: a CTA takes 2*nf rows of one field (0: w, 1: s), so w and s run on
 // different CTAs (twice the CTAs, one transform buffer per row pair); rows j, j+1 share one FFT.
-template <typename T, int PER, typename TF = T>
+template <typename T, int PER, typename TF = T, int R3 = 1>
 __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* __restrict__ ins, long in_ld,
                                             long in_bs, int nrows, int N, TF* __restrict__ fw, TF* __restrict__ fs,
                                             long f_ld, long f_bs, int mode,
                                             const typename C2<T>::t* __restrict__ tw, int logL, int nf) {
   using c2 = typename C2<T>::t;
-  constexpr int NC = 2 * PER;
+  constexpr int NC = 2 * PER * R3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
-  const int L = 1 << logL;
+  const int L = R3 << logL;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  TwiddleStage<T, 4 * PER> ts;
+  TwiddleStage<T, 4 * PER * R3> ts;
   ts.load(tw, L, ((size_t)nf + 1) * L * sizeof(c2));
   pdl_enter();
   const int field = blockIdx.x & 1;
@@ -518,7 +621,7 @@ __global__ void __launch_bounds__(256) k_xi(const T* __restrict__ inw, const T* 
   }
   const c2* tws = ts.store(buf + (long)nf * L, tw, L);
   __syncthreads();
-  block_fft<T, PER>(buf, L, logL, tws);
+  block_fft<T, PER, R3>(buf, L, logL, tws);
   for (int f = 0; f < nf; ++f) {
 #pragma unroll
     for (int m = 0; m < NC; ++m) {

@@ -566,7 +566,9 @@ struct GemmDst {
   CUtensorMap sy128_hi, sy128_lo;  // S_y, boxes of 128 rows (G2 A operand)
 };
 
-bool gemm_dst_supported(int nx, int ny) { return nx >= 128 && ny >= 128 && nx <= 1024 && ny <= 512; }
+bool gemm_dst_supported(int nx, int ny) {
+  return nx >= 128 && ny >= 128 && nx <= 1024 && ny <= 512 && (nx & (nx - 1)) == 0 && (ny & (ny - 1)) == 0;
+}
 
 fsi_status gemm_dst_setup(fsi_ctx* c) {
   if (c->prec != FSI_PREC_FP32 || !gemm_dst_supported(c->nx, c->ny)) return FSI_ERR_UNSUPPORTED;

@@ -8,21 +8,39 @@
 namespace {
 
 // ---------------------------------------------------------------------------------------------
-// Launch shapes of the FFT passes: elements per CTA = 4 * PER * threads = nf * L.
+// Launch shapes of the FFT passes for a length L = r3 * 2^logP: 4 * PER * threads = nf * 2^logP (nf
+// transforms per CTA).  Lengths 3 * 2^k stop at 3072 (grids of 1536 cells), so they always take PER = 1.
 struct FftCfg {
-  int nthr, per, nf;
+  int nthr, per, nf, r3, logP, L;
 };
-FftCfg fft_cfg(int logL) {
-  const int L = 1 << logL;
+FftCfg fft_cfg(int logP, int r3) {
+  const int P = 1 << logP;
   FftCfg c;
-  c.nthr = L / 4;
+  c.nthr = P / 4;
   if (c.nthr < 32) c.nthr = 32;
   if (c.nthr > 256) c.nthr = 256;
   c.per = 1;
-  while (4 * c.per * c.nthr < L) c.per *= 2;
-  c.nf = 4 * c.per * c.nthr / L;
+  while (4 * c.per * c.nthr < P) c.per *= 2;
+  c.nf = 4 * c.per * c.nthr / P;
+  c.r3 = r3;
+  c.logP = logP;
+  c.L = r3 << logP;
   return c;
 }
+
+// Calls LAUNCH(PER, R3) with the template arguments of a launch shape.
+#define FFT_DISPATCH(cfg, LAUNCH)                     \
+  do {                                                \
+    if ((cfg).r3 == 3) {                              \
+      LAUNCH(1, 3);                                   \
+    } else if ((cfg).per == 1) {                      \
+      LAUNCH(1, 1);                                   \
+    } else if ((cfg).per == 2) {                      \
+      LAUNCH(2, 1);                                   \
+    } else {                                          \
+      LAUNCH(4, 1);                                   \
+    }                                                 \
+  } while (0)
 
 template <typename T, typename TF = T>
 void set_smem_limits() {
@@ -39,6 +57,9 @@ void set_smem_limits() {
   cudaFuncSetAttribute(dst::k_xi<T, 1, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xi<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xf<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_ysolve<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(dst::k_xi<T, 1, TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -137,7 +158,9 @@ __device__ __forceinline__ T ring_value(const T* __restrict__ c, long ps, int nx
 
 // delta: the spectra are those of the ring increments (new value minus the fine level's current one; the
 // increment form of the finest level in the mixed mode).  TF: type of the level fields.
-template <typename T, int PER, typename TF = T>
+// Side transform lengths: x (side 1) R3X * 2^logPx, y (side 0) R3Y * 2^logPy; per side a CTA transforms
+// nf = 4 PER blockDim / 2^logP vectors.
+template <typename T, int PER, typename TF = T, int R3X = 1, int R3Y = 1>
 __global__ void __launch_bounds__(256) k_ring_dst(TF* __restrict__ wf, TF* __restrict__ sf, const TF* __restrict__ wc,
                                                   const TF* __restrict__ sc, long ps, int nx, int ny,
                                                   T* __restrict__ ring, long ring_ld,
@@ -149,9 +172,9 @@ __global__ void __launch_bounds__(256) k_ring_dst(TF* __restrict__ wf, TF* __res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int side = (int)blockIdx.x < nblk_y ? 0 : 1;
-  const int logL = side ? logLx : logLy, L = 1 << logL;
+  const int logL = side ? logLx : logLy, L = (side ? R3X : R3Y) << logL;
   const int N = side ? nx - 1 : ny - 1;
-  const int nf = 4 * PER * (int)blockDim.x / L;
+  const int nf = 4 * PER * (int)blockDim.x / (1 << logL);
   const int v0 = 2 * nf * (side ? (int)blockIdx.x - nblk_y : (int)blockIdx.x);
   if (blockIdx.x == 0 && threadIdx.x < 8) {  // corners (i, j) in {0, nx} x {0, ny} of w and s
     const int q = threadIdx.x & 3;
@@ -181,7 +204,8 @@ __global__ void __launch_bounds__(256) k_ring_dst(TF* __restrict__ wf, TF* __res
     dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
   }
   __syncthreads();
-  dst::block_fft<T, PER>(buf, L, logL, tws);
+  if (side) dst::block_fft<T, PER, R3X>(buf, L, logL, tws);
+  else dst::block_fft<T, PER, R3Y>(buf, L, logL, tws);
   const int dmap[2][4] = {{0, 1, 4, 5}, {2, 3, 6, 7}};
   for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
     const int f = idx / N, n = idx - f * N;
@@ -321,8 +345,8 @@ template <typename T>
 fsi_status xf_pass(fsi_ctx* c, const T* rhs, int nlev) {
   using c2 = typename C2<T>::t;
   set_smem_limits<T>();
-  const FftCfg cx = fft_cfg(c->logLx);
-  const int Lx = 1 << c->logLx;
+  const FftCfg cx = fft_cfg(c->logPx, c->r3x);
+  const int Lx = cx.L;
   const c2* twx = (const c2*)c->twx;
   prof_mark(c, KC_XF);
   if (use_gemm<T>(c, 0)) {
@@ -333,11 +357,9 @@ fsi_status xf_pass(fsi_ctx* c, const T* rhs, int nlev) {
     dim3 grid((c->Ny + 2 * cx.nf - 1) / (2 * cx.nf), nlev);
     const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
     const long ib = c->lvl_elems, ob = (long)c->Nx * c->ldT;
-    switch (cx.per) {
-      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 1>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
-      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 2>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
-      default: FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, 4>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, c->logLx, cx.nf)); break;
-    }
+#define XF_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_xf<T, P, R>, grid, dim3(cx.nthr), sm, c->stream, rhs, c->ps, ib, c->Ny, c->Nx, (T*)c->T1, c->ldT, ob, twx, cx.logP, cx.nf))
+    FFT_DISPATCH(cx, XF_LAUNCH);
+#undef XF_LAUNCH
   }
   prof_mark(c, KC_XF);
   c->launches_per_step += 1;
@@ -349,8 +371,8 @@ template <typename T>
 fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
   using c2 = typename C2<T>::t;
   set_smem_limits<T>();
-  const FftCfg cy = fft_cfg(c->logLy);
-  const int Ly = 1 << c->logLy;
+  const FftCfg cy = fft_cfg(c->logPy, c->r3y);
+  const int Ly = cy.L;
   const c2* twy = (const c2*)c->twy;
   prof_mark(c, KC_YSOLVE);
   const double h = c->g.h * (double)(1 << g);
@@ -364,11 +386,9 @@ fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
   } else {
     dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
     const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-    switch (cy.per) {
-      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 1>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 2>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-      default: FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, 4>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, c->logLy, cy.nf, sp)); break;
-    }
+#define Y_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, P, R>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, cy.logP, cy.nf, sp))
+    FFT_DISPATCH(cy, Y_LAUNCH);
+#undef Y_LAUNCH
   }
   prof_mark(c, KC_YSOLVE);
   c->launches_per_step += 1;
@@ -381,8 +401,8 @@ template <typename T, typename TF = T>
 fsi_status xi_pass(fsi_ctx* c, TF* w, TF* s, int mode) {
   using c2 = typename C2<T>::t;
   set_smem_limits<T, TF>();
-  const FftCfg cx = fft_cfg(c->logLx);
-  const int Lx = 1 << c->logLx;
+  const FftCfg cx = fft_cfg(c->logPx, c->r3x);
+  const int Lx = cx.L;
   const c2* twx = (const c2*)c->twx;
   prof_mark(c, KC_XI);
   if (use_gemm<T>(c, 2)) {
@@ -396,11 +416,9 @@ fsi_status xi_pass(fsi_ctx* c, TF* w, TF* s, int mode) {
   } else {
     dim3 grid(dst::xi_blocks(c->Ny, cx.nf), 1);
     const size_t sm = dst::pass_smem<T>((size_t)cx.nf * Lx, Lx);
-    switch (cx.per) {
-      case 1: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 1, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
-      case 2: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 2, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
-      default: FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, 4, TF>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, c->logLx, cx.nf)); break;
-    }
+#define XI_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_xi<T, P, TF, R>, grid, dim3(cx.nthr), sm, c->stream, (const T*)c->T2w, (const T*)c->T2s, c->ldX, 0, c->Ny, c->Nx, w, s, c->ps, 0, mode, twx, cx.logP, cx.nf))
+    FFT_DISPATCH(cx, XI_LAUNCH);
+#undef XI_LAUNCH
   }
   prof_mark(c, KC_XI);
   FSI_CUDA_TRY(cudaGetLastError());
@@ -423,11 +441,15 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g, int delta) {
   TF* sf = (TF*)c->s_all + (long)g * c->lvl_elems;
   const TF* wc = (const TF*)c->w_all + (long)(g + 1) * c->lvl_elems;
   const TF* sc = (const TF*)c->s_all + (long)(g + 1) * c->lvl_elems;
-  const int Lmax = c->logLx > c->logLy ? (1 << c->logLx) : (1 << c->logLy);
-  const int per = Lmax <= 1024 ? 1 : Lmax / 1024;
-  const int nf_y = 4 * per * 256 / (1 << c->logLy), nf_x = 4 * per * 256 / (1 << c->logLx);
+  // per side nf = 4 PER 256 / 2^logP vectors per CTA; grids with a 3 * 2^k axis keep both power-of-two parts
+  // at most 1024 (checked at fsi_create), so they take PER = 1
+  const int Pmax = 1 << (c->logPx > c->logPy ? c->logPx : c->logPy);
+  const int per = Pmax <= 1024 ? 1 : Pmax / 1024;
+  const int nf_y = 4 * per * 256 / (1 << c->logPy), nf_x = 4 * per * 256 / (1 << c->logPx);
   const int nblk_y = (4 + 2 * nf_y - 1) / (2 * nf_y), nblk_x = (4 + 2 * nf_x - 1) / (2 * nf_x);
-  const size_t sm = dst::pass_smem<T>((size_t)4 * per * 256, Lmax);
+  const int Lx = c->r3x << c->logPx, Ly = c->r3y << c->logPy;
+  const int r3max = c->r3x > c->r3y ? c->r3x : c->r3y;
+  const size_t sm = dst::pass_smem<T>((size_t)4 * per * 256 * r3max, Lx > Ly ? Lx : Ly);
   const c2* twx = (const c2*)c->twx;
   const c2* twy = (const c2*)c->twy;
   static bool attrs = false;  // per instantiation
@@ -436,14 +458,20 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g, int delta) {
     cudaFuncSetAttribute(k_ring_dst<T, 1, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   prof_mark(c, KC_RING);
   const dim3 grid(nblk_y + nblk_x);
-  switch (per) {
-    case 1: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 1, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
-    case 2: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 2, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
-    default: FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, 4, TF>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logLx, c->logLy, nblk_y, delta)); break;
-  }
+#define RING_LAUNCH(P, RX, RY) FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, P, TF, RX, RY>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logPx, c->logPy, nblk_y, delta))
+  if (c->r3x == 3 && c->r3y == 3) RING_LAUNCH(1, 3, 3);
+  else if (c->r3x == 3) RING_LAUNCH(1, 3, 1);
+  else if (c->r3y == 3) RING_LAUNCH(1, 1, 3);
+  else if (per == 1) RING_LAUNCH(1, 1, 1);
+  else if (per == 2) RING_LAUNCH(2, 1, 1);
+  else RING_LAUNCH(4, 1, 1);
+#undef RING_LAUNCH
   prof_mark(c, KC_RING);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());

@@ -106,7 +106,8 @@ struct fsi_ctx {
   size_t esz;   // bytes per element of the transform buffers, right-hand sides and spectral tables
   size_t fesz;  // bytes per element of the level fields w, s and the previous advection term
   cudaStream_t stream;
-  int G, nx, ny, Nx, Ny, Mx, My, logLx, logLy;
+  int G, nx, ny, Nx, Ny, Mx, My;
+  int logPx, logPy, r3x, r3y;  // transform lengths 2 nx = r3x 2^logPx, 2 ny = r3y 2^logPy (r3 = 1 or 3)
   long ps;        // vertex row stride (elements)
   long lvl_elems; // (ny+1)*ps
   long ldT;       // row stride of the x->y transposed buffer (>= Ny)
