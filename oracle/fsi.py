@@ -128,7 +128,12 @@ class Sim:
         # exact points of stationary bodies appended to Omega_0 (Sec. 3.1.1), in body order
         app = [b.pts for b in self.bodies if getattr(b, "appended", False)]
         extra = np.concatenate(app) if app else None
-        self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box, extra=extra) if sd_box is not None else None
+        if sd_box is None:
+            self.sd = None
+        elif np.ndim(sd_box) == 2:           # a union of boxes (reading R16)
+            self.sd = ib.Subdomain.from_boxes(self.levels[0], sd_box, extra=extra)
+        else:
+            self.sd = ib.Subdomain.from_box(self.levels[0], *sd_box, extra=extra)
         self.appended = np.full(sum(b.n_pts for b in self.bodies), -1, dtype=np.int64)
         o = e = 0
         for b in self.bodies:

@@ -43,33 +43,57 @@ def hat(r, dr):
 
 
 class Subdomain:
-    """Omega_0: the vertices ``i_lo..i_hi`` x ``j_lo..j_hi`` of the finest level (Sec. 3.1.1), followed by
-    ``extra`` appended points -- the exact points of stationary bodies, interpolated with E itself
-    (Sec. 3.1.1: such points may be added to the sub-domain with weight one).  Unknowns: the x components
-    of the ``n_box`` vertices (row by row) and of the extra points, then the y components likewise."""
+    """Omega_0: the vertices ``i_lo..i_hi`` x ``j_lo..j_hi`` of the finest level (Sec. 3.1.1) -- or a union of
+    such vertex boxes (reading R16: one box per body, the cross-box blocks of B0 included) -- followed by
+    ``extra`` appended points, the exact points of stationary bodies, interpolated with E itself (Sec. 3.1.1:
+    such points may be added to the sub-domain with weight one).  Unknowns: the x components of the ``n_box``
+    box vertices (box by box, row by row inside a box) and of the extra points, then the y components
+    likewise."""
 
-    def __init__(self, lev, i_lo, i_hi, j_lo, j_hi, extra=None):
-        if i_lo < 2 or j_lo < 2 or i_hi > lev.nx - 2 or j_hi > lev.ny - 2 or i_hi <= i_lo or j_hi <= j_lo:
-            raise ValueError("sub-domain must lie at least 2 cells inside the grid")
+    def __init__(self, lev, i_lo, i_hi, j_lo, j_hi, extra=None, boxes=None):
+        boxes = [(i_lo, i_hi, j_lo, j_hi)] if boxes is None else [tuple(int(v) for v in b) for b in boxes]
+        for (a, b, c, d) in boxes:
+            if a < 2 or c < 2 or b > lev.nx - 2 or d > lev.ny - 2 or b <= a or d <= c:
+                raise ValueError("sub-domain must lie at least 2 cells inside the grid")
+        for k, (a, b, c, d) in enumerate(boxes):
+            for (a2, b2, c2, d2) in boxes[:k]:
+                if a <= b2 and a2 <= b and c <= d2 and c2 <= d:
+                    raise ValueError("sub-domain boxes must not share vertices")
         self.lev = lev
-        self.i_lo, self.i_hi, self.j_lo, self.j_hi = int(i_lo), int(i_hi), int(j_lo), int(j_hi)
+        self.boxes = boxes
+        self.i_lo, self.i_hi, self.j_lo, self.j_hi = boxes[0]
         self.ni = self.i_hi - self.i_lo + 1
         self.nj = self.j_hi - self.j_lo + 1
-        self.n_box = self.ni * self.nj
+        pis, pjs, self.box_off = [], [], []
+        for (a, b, c, d) in boxes:
+            self.box_off.append(sum(len(x) for x in pis))
+            jj, ii = np.meshgrid(np.arange(c, d + 1), np.arange(a, b + 1), indexing="ij")
+            pis.append(ii.ravel())
+            pjs.append(jj.ravel())
+        self.pi = np.concatenate(pis)
+        self.pj = np.concatenate(pjs)
+        self.n_box = len(self.pi)
         self.extra = np.zeros((0, 2)) if extra is None else np.asarray(extra, dtype=np.float64).reshape(-1, 2)
         self.n_sd = self.n_box + len(self.extra)
-        jj, ii = np.meshgrid(np.arange(self.j_lo, self.j_hi + 1), np.arange(self.i_lo, self.i_hi + 1), indexing="ij")
-        self.pi = ii.ravel()
-        self.pj = jj.ravel()
 
-    @classmethod
-    def from_box(cls, lev, x_lo, x_hi, y_lo, y_hi, extra=None):
+    @staticmethod
+    def _snap(lev, x_lo, x_hi, y_lo, y_hi):
         """Snap a physical box to vertices, clipped to >= 2 cells from the boundary (reading R10)."""
         i_lo = max(int(np.ceil((x_lo - lev.x0) / lev.h - 1e-9)), 2)
         i_hi = min(int(np.floor((x_hi - lev.x0) / lev.h + 1e-9)), lev.nx - 2)
         j_lo = max(int(np.ceil((y_lo - lev.y0) / lev.h - 1e-9)), 2)
         j_hi = min(int(np.floor((y_hi - lev.y0) / lev.h + 1e-9)), lev.ny - 2)
-        return cls(lev, i_lo, i_hi, j_lo, j_hi, extra)
+        return i_lo, i_hi, j_lo, j_hi
+
+    @classmethod
+    def from_box(cls, lev, x_lo, x_hi, y_lo, y_hi, extra=None):
+        return cls(lev, *cls._snap(lev, x_lo, x_hi, y_lo, y_hi), extra)
+
+    @classmethod
+    def from_boxes(cls, lev, boxes, extra=None):
+        """The union of several physical boxes, each snapped as ``from_box`` (reading R16)."""
+        snapped = [cls._snap(lev, *b) for b in boxes]
+        return cls(lev, *snapped[0], extra, boxes=snapped)
 
     # -- E0 (Eq. ibsdinterp): weights d(x_face - x_k) d(y_face - y_k) --------------------
 
@@ -135,23 +159,25 @@ class Subdomain:
                 idx[p, :] = self.n_box + app[p]
                 wts[p, 0] = 1.0
             return idx, wts
-        x_lo = lev.x0 + self.i_lo * lev.h
-        y_lo = lev.y0 + self.j_lo * lev.h
-        x_hi = lev.x0 + self.i_hi * lev.h
-        y_hi = lev.y0 + self.j_hi * lev.h
         idx = np.zeros((len(pts), 4), dtype=np.int64)
         wts = np.zeros((len(pts), 4))
         for p, (x, y) in enumerate(pts):
-            if not (x_lo <= x <= x_hi and y_lo <= y <= y_hi):
+            for (i_lo, i_hi, j_lo, j_hi), off in zip(self.boxes, self.box_off):   # the first box holding it
+                x_lo, y_lo = lev.x0 + i_lo * lev.h, lev.y0 + j_lo * lev.h
+                x_hi, y_hi = lev.x0 + i_hi * lev.h, lev.y0 + j_hi * lev.h
+                if x_lo <= x <= x_hi and y_lo <= y <= y_hi:
+                    break
+            else:
                 raise ValueError("body point outside the sub-domain")
-            ci = min(max(int(np.floor((x - x_lo) / lev.h)), 0), self.ni - 2)
-            cj = min(max(int(np.floor((y - y_lo) / lev.h)), 0), self.nj - 2)
+            ni, nj = i_hi - i_lo + 1, j_hi - j_lo + 1
+            ci = min(max(int(np.floor((x - x_lo) / lev.h)), 0), ni - 2)
+            cj = min(max(int(np.floor((y - y_lo) / lev.h)), 0), nj - 2)
             k = 0
             for b in (0, 1):
                 for a in (0, 1):
                     xs = x_lo + (ci + a) * lev.h
                     ys = y_lo + (cj + b) * lev.h
-                    idx[p, k] = (cj + b) * self.ni + (ci + a)
+                    idx[p, k] = off + (cj + b) * ni + (ci + a)
                     wts[p, k] = hat(x - xs, lev.h) * hat(y - ys, lev.h)
                     k += 1
         return idx, wts
