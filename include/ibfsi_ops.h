@@ -16,7 +16,7 @@ extern "C" {
  * w = A_w^{-1} rhs with A_w = 1/dt - lap_h/(2 re), then s = (-lap_h)^{-1} w.
  * rhs: interior values, row-major [(ny-1) x (nx-1)] (rows = y).  w_out, s_out: same layout.
  * precision: FSI_PREC_FP64 or FSI_PREC_FP32 (inputs/outputs are double either way).
- * nx, ny: as fsi_grid_desc (2^k or 3 * 2^k in [16, 2048]); h, re, dt > 0.  Runs on the current device,
+ * nx, ny: cell counts as in a grid descriptor, 2^k or 3 * 2^k in [16, 2048]; h, re, dt > 0.  Runs on the current device,
  * synchronously. */
 fsi_status fsi_op_level_solve(int precision, int nx, int ny, double h, double re, double dt, const double* rhs,
                               double* w_out, double* s_out);

@@ -118,8 +118,12 @@ class Context:
         return bid.value
 
     def set_subdomain(self, x_lo, x_hi, y_lo, y_hi):
-        box = _lib.Box(x_lo, x_hi, y_lo, y_hi)
-        check(self._lib.fsi_set_subdomain(self._h, ctypes.byref(box), 1, None, 0), "fsi_set_subdomain")
+        self.set_subdomain_boxes([(x_lo, x_hi, y_lo, y_hi)])
+
+    def set_subdomain_boxes(self, boxes):
+        """Omega_0 as the union of disjoint boxes (x_lo, x_hi, y_lo, y_hi), e.g. one per body (reading R16)."""
+        arr = (_lib.Box * len(boxes))(*[_lib.Box(*b) for b in boxes])
+        check(self._lib.fsi_set_subdomain(self._h, arr, len(boxes), None, 0), "fsi_set_subdomain")
 
     def precompute(self, drop_tol=0.0):
         check(self._lib.fsi_precompute(self._h, drop_tol), "fsi_precompute")

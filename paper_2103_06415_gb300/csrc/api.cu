@@ -1,4 +1,5 @@
 // C ABI: context life cycle, offline/online stages and read-back (see include/ibfsi.h).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -475,20 +476,57 @@ fsi_status snap_box(const fsi_grid_desc& g, const fsi_box& b, int* i_lo_, int* i
 extern "C" fsi_status fsi_set_subdomain(fsi_ctx* c, const fsi_box* boxes, int n_boxes, const double* extra,
                                         int n_extra) {
   (void)extra;
-  if (!c || !boxes) return FSI_ERR_INVALID_ARG;
+  if (!c || !boxes || n_boxes < 1) return FSI_ERR_INVALID_ARG;
   if (c->stage >= 1) return FSI_ERR_STATE;
-  if (n_boxes != 1 || n_extra != 0) return FSI_ERR_UNSUPPORTED;
-  int i_lo, i_hi, j_lo, j_hi;
-  const fsi_status st = snap_box(c->g, boxes[0], &i_lo, &i_hi, &j_lo, &j_hi);
-  if (st != FSI_OK) return st;
+  if (n_boxes > 16 || n_extra != 0) return FSI_ERR_UNSUPPORTED;
+  int sdb[16][4];
+  int n_pts = 0;
+  for (int k = 0; k < n_boxes; ++k) {
+    const fsi_status st = snap_box(c->g, boxes[k], &sdb[k][0], &sdb[k][1], &sdb[k][2], &sdb[k][3]);
+    if (st != FSI_OK) return st;
+    for (int q = 0; q < k; ++q)  // boxes of a union share no vertex
+      if (sdb[k][0] <= sdb[q][1] && sdb[q][0] <= sdb[k][1] && sdb[k][2] <= sdb[q][3] && sdb[q][2] <= sdb[k][3])
+        return FSI_ERR_INVALID_ARG;
+    n_pts += (sdb[k][1] - sdb[k][0] + 1) * (sdb[k][3] - sdb[k][2] + 1);
+  }
+  c->n_sdb = n_boxes;
+  memcpy(c->sdb, sdb, sizeof(int) * 4 * (size_t)n_boxes);
+  int i_lo = sdb[0][0], i_hi = sdb[0][1], j_lo = sdb[0][2], j_hi = sdb[0][3];
+  for (int k = 1; k < n_boxes; ++k) {  // bounding box of the union
+    i_lo = std::min(i_lo, sdb[k][0]);
+    i_hi = std::max(i_hi, sdb[k][1]);
+    j_lo = std::min(j_lo, sdb[k][2]);
+    j_hi = std::max(j_hi, sdb[k][3]);
+  }
   c->i_lo = i_lo;
   c->i_hi = i_hi;
   c->j_lo = j_lo;
   c->j_hi = j_hi;
   c->ni = i_hi - i_lo + 1;
   c->nj = j_hi - j_lo + 1;
-  c->n_box = c->n_sd = c->ni * c->nj;
+  c->n_box = c->n_sd = n_pts;
   c->have_sd = 1;
+  return FSI_OK;
+}
+
+// Bounding-box map and point list of a union of boxes (fsi_ctx::d_sd_map, d_sd_vert).
+static fsi_status setup_union(fsi_ctx* c) {
+  if (c->n_sdb <= 1) return FSI_OK;
+  std::vector<int> map((size_t)c->ni * c->nj, -1), vert(2 * (size_t)c->n_box);
+  int p = 0;
+  for (int k = 0; k < c->n_sdb; ++k)
+    for (int j = c->sdb[k][2]; j <= c->sdb[k][3]; ++j)
+      for (int i = c->sdb[k][0]; i <= c->sdb[k][1]; ++i, ++p) {
+        const int ii = i - c->i_lo, jj = j - c->j_lo;
+        map[(size_t)jj * c->ni + ii] = p;
+        vert[2 * (size_t)p] = ii;
+        vert[2 * (size_t)p + 1] = jj;
+      }
+  if (!(c->d_sd_map = (int*)ctx_alloc(c, map.size() * sizeof(int))) ||
+      !(c->d_sd_vert = (int*)ctx_alloc(c, vert.size() * sizeof(int))))
+    return FSI_ERR_OOM;
+  FSI_CUDA_TRY(cudaMemcpyAsync(c->d_sd_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  FSI_CUDA_TRY(cudaMemcpyAsync(c->d_sd_vert, vert.data(), vert.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   return FSI_OK;
 }
 
@@ -515,6 +553,9 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
       }
   c->n_sd = c->n_box + c->n_app;
   if (c->n_app > 0 && (drop_tol > 0.0 || load)) return FSI_ERR_UNSUPPORTED;
+  // a union of boxes: the Green's-function operator (dense or filtered) and the sub-domain coupling only
+  if (c->n_sdb > 1 && (c->n_app > 0 || load || true_e || c->x.b0_method != 0)) return FSI_ERR_UNSUPPORTED;
+  TRY(setup_union(c));
   if (true_e) {  // true E at the body points: no B0; torsional and rigid bodies
     if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024 || c->prec == FSI_PREC_MIXED) return FSI_ERR_UNSUPPORTED;
     if (c->x.krylov_max_iters <= 0) c->x.krylov_max_iters = 2 * c->nf + 20;

@@ -207,6 +207,21 @@ __global__ void __launch_bounds__(256) k_fill(double* __restrict__ out, const do
   }
 }
 
+// Dense B0 of a union of boxes (reading R16) from the stencil tables of its bounding box bx: one CTA per row
+// (ca, pa) over all 2 n_sd columns, entries in the rounding order of k_fill, cross-box blocks included.
+__global__ void __launch_bounds__(256) k_fill_union(double* __restrict__ out, const double* __restrict__ tab, B0Box bx,
+                                                    int n_sd, const int* __restrict__ vert) {
+  const int ni = bx.ni, nj = bx.nj, nx2 = 2 * ni - 1;
+  const long per = (long)nx2 * (2 * nj - 1), n2 = 2L * n_sd;
+  const long row = blockIdx.x;
+  const int ca = row >= n_sd, pa = (int)(row - (long)ca * n_sd);
+  const int ia = vert[2 * pa], ja = vert[2 * pa + 1];
+  for (long col = threadIdx.x; col < n2; col += blockDim.x) {
+    const int cb = col >= n_sd, pb = (int)(col - (long)cb * n_sd);
+    out[row * n2 + col] = b0_entry(tab, per, nx2, ni, nj, ca, ja, ia, cb, vert[2 * pb + 1], vert[2 * pb]);
+  }
+}
+
 }  // namespace
 
 // The 16 stencil tables of every box (layout of k_tables) into a new device array *tab_out (caller frees
@@ -321,6 +336,18 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
 fsi_status build_b0(fsi_ctx* c) {
   auto t0 = std::chrono::steady_clock::now();
   std::vector<B0Box> one(1, ctx_box(c));
+  if (c->n_sdb > 1) {  // a union: tables of the bounding box, then every entry from its two points' vertices
+    b0_layout(one);
+    double* d_tab = nullptr;
+    fsi_status st = b0_green_tables(c, one, &d_tab);
+    if (st == FSI_OK) {
+      k_fill_union<<<(unsigned)(2L * c->n_sd), 256, 0, c->stream>>>(c->B0, d_tab, one[0], c->n_sd, c->d_sd_vert);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
+    }
+    cudaFree(d_tab);
+    c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  }
   const fsi_status st = b0_green(c, one, c->B0);
   c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;

@@ -5,7 +5,8 @@
 // nearly the same for every column (near-translation invariance).  Each column j therefore stores one
 // window of (2w+1) x (2w+1) Omega_0 points around its point, for both velocity components of the row:
 //   W[j][ca][dj + w][di + w] = b'((ca, jb + dj, ib + di), j),  |dj|, |di| <= w,
-// zero where the filter drops the entry or the point lies outside the box, and a lookup of any entry is
+// zero where the filter drops the entry or the point lies outside Omega_0 (for a union of boxes the window
+// is taken in the bounding box, so columns near another box hold the cross-box entries), and a lookup of any entry is
 // O(1).  w is the largest extent of a kept entry over all columns, found by a scan whose radius doubles
 // until no kept entry touches its edge; B0' built this way equals the filter of the dense B0 entry by
 // entry (the entries come from the same lattice Green's-function tables, in the same rounding order, as
@@ -16,18 +17,6 @@
 #include "internal.h"
 
 namespace {
-
-// B0[(ca, ja, ia)][(cb, jb, ib)] from the 16 stencil tables of one box (formula and rounding order of the
-// dense fill: (T-- - T-+) - (T+- - T++)).
-__device__ __forceinline__ double b0_entry(const double* __restrict__ tab, long per, int nx2, int ni, int nj,
-                                           int ca, int ja, int ia, int cb, int jb, int ib) {
-  const double* t = tab + (long)((ca * 2 + cb) * 4) * per;
-  const long r1 = (long)(ja - jb + nj - 1) * nx2, r2 = (long)(ja + jb) * nx2;
-  const int D = ia - ib + ni - 1, S = ia + ib;
-  const double U = t[r1 + D] - t[2 * per + r2 + D];
-  const double V = t[per + r1 + S] - t[3 * per + r2 + S];
-  return U - V;
-}
 
 __device__ __forceinline__ int block_max_int(int v, int* red) {
   v = __reduce_max_sync(0xffffffffu, v);
@@ -40,20 +29,31 @@ __device__ __forceinline__ int block_max_int(int v, int* red) {
   return r;
 }
 
-// One CTA per column: the largest |dj|, |di| of a kept entry within radius W (into ext[0], ext[1]).
-__global__ void __launch_bounds__(256) k_window_extent(const double* __restrict__ tab, B0Box bx, double eps, int W,
-                                                       int* ext) {
+// Omega_0 membership of box vertex (ia, ja): inside the box (or the union's bounding box) and, for a union,
+// marked in its map.
+__device__ __forceinline__ bool sd_member(const int* map, int ni, int nj, int ia, int ja) {
+  if (ja < 0 || ja >= nj || ia < 0 || ia >= ni) return false;
+  return !map || map[(long)ja * ni + ia] >= 0;
+}
+
+// One CTA per column: the largest |dj|, |di| of a kept entry within radius W (into ext[0], ext[1]).  bx is the
+// box (or the bounding box of a union, with its map and point list) of the n_sd Omega_0 points.
+__global__ void __launch_bounds__(256) k_window_extent(const double* __restrict__ tab, B0Box bx, int n_sd,
+                                                       const int* __restrict__ map, const int* __restrict__ vert,
+                                                       double eps, int W, int* ext) {
   __shared__ int red[32];
-  const int n_sd = bx.n_sd, ni = bx.ni, nj = bx.nj, nx2 = 2 * ni - 1;
+  const int ni = bx.ni, nj = bx.nj, nx2 = 2 * ni - 1;
   const long per = (long)nx2 * (2 * nj - 1);
-  const int col = blockIdx.x, cb = col / n_sd, p = col - cb * n_sd, jb = p / ni, ib = p - jb * ni;
+  const int col = blockIdx.x, cb = col / n_sd, p = col - cb * n_sd;
+  int ib, jb;
+  sd_vertex(vert, ni, p, &ib, &jb);
   const double thr = eps * fabs(b0_entry(tab, per, nx2, ni, nj, cb, jb, ib, cb, jb, ib));
   const int side = 2 * W + 1, area = side * side;
   int mj = 0, mi = 0;
   for (int e = threadIdx.x; e < 2 * area; e += blockDim.x) {
     const int ca = e / area, r = e - ca * area, dj = r / side - W, di = r - (r / side) * side - W;
     const int ja = jb + dj, ia = ib + di;
-    if (ja < 0 || ja >= nj || ia < 0 || ia >= ni) continue;
+    if (!sd_member(map, ni, nj, ia, ja)) continue;
     if (fabs(b0_entry(tab, per, nx2, ni, nj, ca, ja, ia, cb, jb, ib)) > thr) {
       mj = max(mj, abs(dj));
       mi = max(mi, abs(di));
@@ -67,13 +67,17 @@ __global__ void __launch_bounds__(256) k_window_extent(const double* __restrict_
   }
 }
 
-// One CTA per column: its window (zero where dropped or outside the box); kept entries counted in nnz.
+// One CTA per column: its window (zero where dropped or outside Omega_0); kept entries counted in nnz.
 __global__ void __launch_bounds__(256) k_fill_window(double* __restrict__ Wv, const double* __restrict__ tab,
-                                                     B0Box bx, double eps, int w, unsigned long long* nnz) {
+                                                     B0Box bx, int n_sd, const int* __restrict__ map,
+                                                     const int* __restrict__ vert, double eps, int w,
+                                                     unsigned long long* nnz) {
   __shared__ int red[32];
-  const int n_sd = bx.n_sd, ni = bx.ni, nj = bx.nj, nx2 = 2 * ni - 1;
+  const int ni = bx.ni, nj = bx.nj, nx2 = 2 * ni - 1;
   const long per = (long)nx2 * (2 * nj - 1);
-  const int col = blockIdx.x, cb = col / n_sd, p = col - cb * n_sd, jb = p / ni, ib = p - jb * ni;
+  const int col = blockIdx.x, cb = col / n_sd, p = col - cb * n_sd;
+  int ib, jb;
+  sd_vertex(vert, ni, p, &ib, &jb);
   const double thr = eps * fabs(b0_entry(tab, per, nx2, ni, nj, cb, jb, ib, cb, jb, ib));
   const int side = 2 * w + 1, area = side * side;
   double* out = Wv + (long)col * 2 * area;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(256) k_fill_window(double* __restrict__ Wv, co
     const int ca = e / area, r = e - ca * area, dj = r / side - w, di = r - (r / side) * side - w;
     const int ja = jb + dj, ia = ib + di;
     double v = 0.0;
-    if (ja >= 0 && ja < nj && ia >= 0 && ia < ni) {
+    if (sd_member(map, ni, nj, ia, ja)) {
       v = b0_entry(tab, per, nx2, ni, nj, ca, ja, ia, cb, jb, ib);
       if (!(fabs(v) > thr)) v = 0.0;
       else ++kept;
@@ -101,10 +105,10 @@ __global__ void __launch_bounds__(256) k_fill_window(double* __restrict__ Wv, co
 }
 
 __global__ void k_window_entries(const double* __restrict__ Wv, int w, int ni, int n_sd, const int64_t* rows,
-                                 const int64_t* cols, int n, double* out) {
+                                 const int64_t* cols, int n, const int* __restrict__ vert, double* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  out[k] = b0w_lookup(Wv, w, ni, n_sd, rows[k], cols[k]);
+  out[k] = b0w_lookup(Wv, w, ni, n_sd, rows[k], cols[k], vert);
 }
 
 }  // namespace
@@ -135,7 +139,7 @@ fsi_status build_b0_window(fsi_ctx* c, double drop_tol) {
         st = FSI_ERR_CUDA;
         break;
       }
-      k_window_extent<<<n2, 256, 0, c->stream>>>(d_tab, bx, drop_tol, W, d_ext);
+      k_window_extent<<<n2, 256, 0, c->stream>>>(d_tab, bx, c->n_sd, c->d_sd_map, c->d_sd_vert, drop_tol, W, d_ext);
       if (cudaGetLastError() != cudaSuccess ||
           cudaMemcpyAsync(ext, d_ext, sizeof(ext), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
           cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -157,7 +161,7 @@ fsi_status build_b0_window(fsi_ctx* c, double drop_tol) {
       st = FSI_ERR_CUDA;
       break;
     }
-    k_fill_window<<<n2, 256, 0, c->stream>>>(c->Bw, d_tab, bx, drop_tol, w, d_nnz);
+    k_fill_window<<<n2, 256, 0, c->stream>>>(c->Bw, d_tab, bx, c->n_sd, c->d_sd_map, c->d_sd_vert, drop_tol, w, d_nnz);
     unsigned long long nnz = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&nnz, d_nnz, sizeof(nnz), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -176,6 +180,7 @@ fsi_status build_b0_window(fsi_ctx* c, double drop_tol) {
 }
 
 fsi_status b0_window_entries(fsi_ctx* c, const int64_t* d_rows, const int64_t* d_cols, int n, double* d_out) {
-  k_window_entries<<<(n + 255) / 256, 256, 0, c->stream>>>(c->Bw, c->bw, c->ni, c->n_sd, d_rows, d_cols, n, d_out);
+  k_window_entries<<<(n + 255) / 256, 256, 0, c->stream>>>(c->Bw, c->bw, c->ni, c->n_sd, d_rows, d_cols, n,
+                                                           c->d_sd_vert, d_out);
   return cudaGetLastError() == cudaSuccess ? FSI_OK : FSI_ERR_CUDA;
 }

@@ -262,6 +262,7 @@ __device__ __forceinline__ T v_face(const T* vt, int ci, int cj, int fi, int fj)
 // keeps, in point order, the points whose face support can reach it, with their face tables.
 template <typename T>
 __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
+                                             const int* __restrict__ pcij,
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
                                              int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
                                              T coef, int n_box) {
@@ -289,8 +290,8 @@ __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int n
     bool take = false;
     if (p < nb) {
       const int n0 = pidx[4 * p];
-      ci = n0 % ni + i_lo;
-      cj = n0 / ni + j_lo;
+      ci = pcij[2 * p] + i_lo;  // hat cell in the (bounding) box, as grid vertex indices
+      cj = pcij[2 * p + 1] + j_lo;
       take = n0 < n_box && ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;  // appended: elsewhere
     }
     const unsigned m = __ballot_sync(0xffffffffu, take);
@@ -551,7 +552,7 @@ fsi_status corrector_t(fsi_ctx* c) {
     cudaFuncSetAttribute(k_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   prof_mark(c, KC_SRC);
-  FSI_CUDA_TRY(pdl_launch(k_src<T>, gr, dim3(128), sm, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pw, c->d_f, c->nb, c->ni,
+  FSI_CUDA_TRY(pdl_launch(k_src<T>, gr, dim3(128), sm, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pcij, c->d_pw, c->d_f, c->nb, c->ni,
                                       c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h), c->n_box));
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;

@@ -31,6 +31,7 @@
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
+#include <cstring>
 #include "beam.cuh"
 #include "internal.h"
 #include "tc.cuh"
@@ -104,6 +105,11 @@ struct FsiArgs {
   // sets these to make the wait run out; 0 in normal runs)
   unsigned lb_spins;
   int lb_missing;
+  // Omega_0 as a union of boxes (reading R16): n_sdb boxes (grid vertex i_lo, i_hi, j_lo, j_hi) and the
+  // Omega_0 index of every vertex of the bounding box (i_lo, j_lo, ni, nj above); n_sdb = 1: one box
+  int n_sdb;
+  int sdb[16][4];
+  const int* sd_map;
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -764,29 +770,46 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
               uby += (W.w[8 + d] * W.w[12 + q]) * v;
             }
           }
-          const double xl = a.x0 + a.i_lo * a.h, yl = a.y0 + a.j_lo * a.h;
+          // the box holding the point: the only box, or the first box of a union that holds it; (ox, oy) its
+          // corner in the bounding box, (bni, bnj) its vertex counts
+          int ox = 0, oy = 0, bni = a.ni, bnj = a.nj;
+          if (a.n_sdb > 1 && ap < 0) {
+            int k = 0;
+            for (int b = a.n_sdb - 1; b >= 0; --b) {
+              const double gx = (x - (a.x0 + a.sdb[b][0] * a.h)) / a.h, gy = (y - (a.y0 + a.sdb[b][2] * a.h)) / a.h;
+              if (gx >= 0.0 && gy >= 0.0 && gx <= (double)(a.sdb[b][1] - a.sdb[b][0]) &&
+                  gy <= (double)(a.sdb[b][3] - a.sdb[b][2]))
+                k = b;
+            }
+            ox = a.sdb[k][0] - a.i_lo;
+            oy = a.sdb[k][2] - a.j_lo;
+            bni = a.sdb[k][1] - a.sdb[k][0] + 1;
+            bnj = a.sdb[k][3] - a.sdb[k][2] + 1;
+          }
+          const double xl = a.x0 + (a.i_lo + ox) * a.h, yl = a.y0 + (a.j_lo + oy) * a.h;
           const double fx = (x - xl) / a.h, fy = (y - yl) / a.h;
           int ci = (int)floor(fx), cj = (int)floor(fy);
           if (ap >= 0) {
-          } else if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(a.ni - 1) && fy <= (double)(a.nj - 1))) {
+          } else if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(bni - 1) && fy <= (double)(bnj - 1))) {
             if (q == 0) dev_set_status(a.status, FSI_ERR_BODY_OUTSIDE_SUBDOMAIN);
             ci = 0;
             cj = 0;
           }
-          ci = min(max(ci, 0), a.ni - 2);
-          cj = min(max(cj, 0), a.nj - 2);
+          ci = min(max(ci, 0), bni - 2);
+          cj = min(max(cj, 0), bnj - 2);
           if (ap < 0) {
             const double rx = fx - ci, ry = fy - cj;
             const int aa = q & 1, bb = q >> 1;
             const double wq = (aa ? rx : 1.0 - rx) * (bb ? ry : 1.0 - ry);
-            a.pidx[4 * p + q] = (cj + bb) * a.ni + (ci + aa);
+            const int vi = ox + ci + aa, vj = oy + cj + bb;  // hat vertex in the bounding box
+            a.pidx[4 * p + q] = a.sd_map ? a.sd_map[vj * a.ni + vi] : vj * a.ni + vi;
             a.pw[4 * p + q] = wq;
             if (q == 0) {
-              a.pcij[2 * p] = ci;
-              a.pcij[2 * p + 1] = cj;
+              a.pcij[2 * p] = ox + ci;
+              a.pcij[2 * p + 1] = oy + cj;
             }
             double u, v;
-            e0cs(a, a.i_lo + ci + aa, a.j_lo + cj + bb, &u, &v);
+            e0cs(a, a.i_lo + vi, a.j_lo + vj, &u, &v);
             ubx = wq * u;
             uby = wq * v;
           }
@@ -1309,7 +1332,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     for (int p = tid; p < nb; p += nthr) {
       const int n0 = pidx_s[4 * p];
       if (n0 >= a.n_box) continue;  // appended point: its source is written by its own kernel
-      const int ci = n0 % a.ni, cj = n0 / a.ni;
+      const int ci = pcij_s[2 * p], cj = pcij_s[2 * p + 1];  // hat cell in the (bounding) box
       imin = min(imin, ci);
       imax = max(imax, ci);
       jmin = min(jmin, cj);
@@ -1448,6 +1471,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.app_idx = c->n_app > 0 ? c->d_app_idx : nullptr;
   a.app_win = c->d_app_win;
   a.lb_spins = c->wait_spins ? c->wait_spins : (1u << 22);
+  a.n_sdb = c->n_sdb > 1 ? c->n_sdb : 1;
+  memcpy(a.sdb, c->sdb, sizeof(a.sdb));
+  a.sd_map = c->n_sdb > 1 ? c->d_sd_map : nullptr;
   a.lb_missing = c->wait_missing;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);

@@ -123,9 +123,16 @@ struct fsi_ctx {
   // ring DST pointer tables, per level: [G][8] src pointers, strides, dst pointers
   void **ring_src, **ring_dst;
   long* ring_es;
-  // sub-domain
+  // sub-domain: one vertex box, or a union of n_sdb disjoint boxes (reading R16), whose points are numbered
+  // box by box; i_lo .. j_hi, ni, nj then describe the bounding box of the union, d_sd_map holds the Omega_0
+  // index of every bounding-box vertex (-1: not in Omega_0) and d_sd_vert the bounding-box vertex (i, j) of
+  // every Omega_0 point (both NULL for one box, whose numbering is row by row over the box)
   int have_sd;
   int i_lo, i_hi, j_lo, j_hi, ni, nj, n_sd;
+  int n_sdb;
+  int sdb[16][4];  // i_lo, i_hi, j_lo, j_hi of every box (grid vertex indices)
+  int* d_sd_map;
+  int* d_sd_vert;
   // appended points (exact points of RIGID bodies flagged append, Sec. 3.1.1): unknowns n_box .. n_sd - 1 of
   // each component follow the box's n_box = ni * nj points; their face windows, the Omega_0 index of every
   // body point (-1: interpolated by P), and the vertex box their corrector source covers
@@ -224,13 +231,42 @@ struct B0Box {
   long tab_off;  // first entry of this box's stencil tables (Green's-function method)
 };
 
+// B0[(ca, ja, ia)][(cb, jb, ib)] of points at box vertices (ia, ja), (ib, jb) from the 16 stencil tables of
+// that box (b0.cu k_tables; nx2 = 2 ni - 1, per = nx2 (2 nj - 1) entries per table), in the rounding order of
+// the dense fill: (T-- - T-+) - (T+- - T++).
+__device__ __forceinline__ double b0_entry(const double* __restrict__ tab, long per, int nx2, int ni, int nj,
+                                           int ca, int ja, int ia, int cb, int jb, int ib) {
+  const double* t = tab + (long)((ca * 2 + cb) * 4) * per;
+  const long r1 = (long)(ja - jb + nj - 1) * nx2, r2 = (long)(ja + jb) * nx2;
+  const int D = ia - ib + ni - 1, S = ia + ib;
+  const double U = t[r1 + D] - t[2 * per + r2 + D];
+  const double V = t[per + r1 + S] - t[3 * per + r2 + S];
+  return U - V;
+}
+
+// Box vertex (i, j) of Omega_0 point p: row by row over one box of ni columns, or from the point list of a
+// union (vert: (i, j) of every point in its bounding box; NULL for one box).
+__host__ __device__ __forceinline__ void sd_vertex(const int* vert, int ni, int p, int* i, int* j) {
+  if (vert) {
+    *i = vert[2 * p];
+    *j = vert[2 * p + 1];
+  } else {
+    *j = p / ni;
+    *i = p - *j * ni;
+  }
+}
+
 // Entry (row, col) of the sparse B0' in the windowed column format of b0_sparse.cu (unknown ordering of
-// B0: the n_sd x-components, then the n_sd y-components, points row by row): column col keeps, for each
-// component of the row, the (2w+1)^2 Omega_0 points within w of its own point.
-__host__ __device__ __forceinline__ double b0w_lookup(const double* Wv, int w, int ni, int n_sd, long row, long col) {
+// B0: the n_sd x-components, then the n_sd y-components; points as sd_vertex numbers them): column col
+// keeps, for each component of the row, the (2w+1)^2 box vertices within w of its own point (zero where a
+// vertex is not in Omega_0).
+__host__ __device__ __forceinline__ double b0w_lookup(const double* Wv, int w, int ni, int n_sd, long row, long col,
+                                                      const int* vert = nullptr) {
   const int ca = row >= n_sd, cb = col >= n_sd;
   const int pa = (int)(row - (long)ca * n_sd), pb = (int)(col - (long)cb * n_sd);
-  const int ja = pa / ni, ia = pa - ja * ni, jb = pb / ni, ib = pb - jb * ni;
+  int ia, ja, ib, jb;
+  sd_vertex(vert, ni, pa, &ia, &ja);
+  sd_vertex(vert, ni, pb, &ib, &jb);
   const int dj = ja - jb, di = ia - ib;
   if (dj > w || dj < -w || di > w || di < -w) return 0.0;
   const long side = 2 * w + 1;

@@ -53,6 +53,7 @@ extern "C" fsi_status fsi_save_operator(fsi_ctx* c, const char* path) {
   if (!c->have_b0) return FSI_ERR_STATE;
   if (!c->B0 && !c->Bw) return FSI_ERR_UNSUPPORTED;  // true-E coupling: no operator
   if (c->n_app > 0) return FSI_ERR_UNSUPPORTED;        // appended points are not recorded in the header
+  if (c->n_sdb > 1) return FSI_ERR_UNSUPPORTED;        // nor are the boxes of a union
   const OpHeader hd = header_of(c);
   const double* src = c->Bw ? c->Bw : c->B0;
   FILE* f = fopen(path, "wb");

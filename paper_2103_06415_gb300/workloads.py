@@ -220,3 +220,23 @@ def random_field(shape, seed, smooth=True):
 
 def random_rhs(ny_int, nx_int, seed):
     return np.random.default_rng(seed).standard_normal((ny_int, nx_int))
+
+
+def tandem_small(nx=96, ny=48, n_levels=2):
+    """A small case shaped like the large coupled workload (5 levels of 1536 x 768): a grid of 3 * 2^k cells,
+    two torsional plates in tandem and a clamped flag behind them, each inside its own Omega_0 box (the
+    union of the three boxes, reading R16); h = 1/16 on [-1, 5] x [-1.5, 1.5], Re 100, dt 0.004, chords
+    0.5 (9 points at ds = h), plate springs 0.5 and 2, flag mass ratio 0.5, bending stiffness 1e-2."""
+    h = 1.0 / 16
+    hinges = [(0.0, 0.0), (1.25, 0.0), (2.5, 0.0)]
+    return dict(
+        name="tandem_small_%dx%d_%dlvl" % (nx, ny, n_levels), nx=nx, ny=ny, n_levels=n_levels, x0=-1.0,
+        y0=-ny * h / 2, h=h, re=100.0, dt=0.004, uinf=(1.0, 0.0), steps=20,
+        sd_box=[(hx - 0.2, hx + 0.7, -0.6, 0.6) for hx, _ in hinges],
+        bodies=[dict(kind="torsional", hinge=hinges[0], theta0=0.0, n_pts=9, inertia=0.05, damping=0.0,
+                     stiffness=0.5, theta=np.deg2rad(20.0)),
+                dict(kind="torsional", hinge=hinges[1], theta0=0.0, n_pts=9, inertia=0.05, damping=0.0,
+                     stiffness=2.0, theta=np.deg2rad(20.0)),
+                dict(kind="deformable", clamp=hinges[2], theta0=0.0, n_pts=9, mass=0.5, ei=1e-2, ea=1e3,
+                     tip_angle=0.1)],
+        ds=h)

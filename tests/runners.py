@@ -47,7 +47,10 @@ def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0
         else:
             c.add_rigid(b["pts"], w["ds"], b.get("ur"), b.get("appended", False))
     if w.get("sd_box") is not None:
-        c.set_subdomain(*w["sd_box"])
+        if np.ndim(w["sd_box"]) == 2:      # a union of boxes
+            c.set_subdomain_boxes(w["sd_box"])
+        else:
+            c.set_subdomain(*w["sd_box"])
         if precompute:
             c.precompute(drop_tol)
     return c
