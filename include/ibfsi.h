@@ -102,6 +102,14 @@ typedef struct {
   double krylov_tol; /* coupling 1: stop when |r| <= krylov_tol |rhs| (<= 0 -> 1e-10 FP64, 1e-5 FP32) */
   int krylov_max_iters; /* coupling 1: Krylov iterations per FSI iteration (<= 0 -> 2 nf + 20); reaching it
                            without convergence latches FSI_ERR_NOT_CONVERGED */
+  int fsi_solver; /* solver of the small system of Eq. stress2 (coupling 0): 0 automatic; 1 a float inverse of
+                     K held in the shared memory of every CTA of the FSI kernel, refined in double (nf up to
+                     about 230); 2 distributed: a block-Jacobi float inverse (one block per body, the body's
+                     x and y rows) and K in global memory, up to 12 rows per CTA, refined in double against
+                     the full K (nf up to 12 x the SM count; it converges when the bodies' cross coupling in
+                     K is weak, exactly block-diagonal K for bodies farther apart than the window of B0').
+                     0 takes 1 when it fits, else 2.  A size the choice cannot hold: FSI_ERR_UNSUPPORTED at
+                     fsi_precompute; other values: FSI_ERR_INVALID_ARG. */
 } fsi_exec_desc;
 
 /* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at

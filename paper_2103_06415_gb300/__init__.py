@@ -31,15 +31,17 @@ class Context:
     dst_method: 0 FFT sine transforms, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotune per pass.
     coupling: COUPLING_SUBDOMAIN (the method) or COUPLING_TRUE_E (the true-E comparator; krylov_tol and
     krylov_max_iters control its conjugate-gradient solve, 0 = library defaults).
+    fsi_solver: 0 automatic, 1 float inverse in shared memory, 2 distributed block-Jacobi inverse (large nf).
     """
 
     def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
                  stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0,
-                 dst_method=0, coupling=COUPLING_SUBDOMAIN, krylov_tol=0.0, krylov_max_iters=0):
+                 dst_method=0, coupling=COUPLING_SUBDOMAIN, krylov_tol=0.0, krylov_max_iters=0, fsi_solver=0):
         self._lib = _lib.load()
         g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
         x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
-                          1 if use_graph else 0, b0_method, dst_method, coupling, krylov_tol, krylov_max_iters)
+                          1 if use_graph else 0, b0_method, dst_method, coupling, krylov_tol, krylov_max_iters,
+                          fsi_solver)
         h_ = ctypes.c_void_p()
         check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
         self._h = h_

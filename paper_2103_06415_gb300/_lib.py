@@ -36,7 +36,7 @@ class ExecDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("b0_method", ctypes.c_int), ("dst_method", ctypes.c_int), ("coupling", ctypes.c_int),
-                ("krylov_tol", ctypes.c_double), ("krylov_max_iters", ctypes.c_int)]
+                ("krylov_tol", ctypes.c_double), ("krylov_max_iters", ctypes.c_int), ("fsi_solver", ctypes.c_int)]
 
 
 class BodyDesc(ctypes.Structure):

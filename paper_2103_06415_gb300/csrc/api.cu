@@ -14,10 +14,10 @@
 
 int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c);
 size_t fsi_smem_bytes(const fsi_ctx* c);
-bool fsi_smem_fits(const fsi_ctx* c);
+bool fsi_smem_fits(const fsi_ctx* c, bool big);
 double beam_initial_state(const BodyHost& h, double ds, double tip, double* chi, double* zeta, double* zdot,
                           double* ref);
-int fsi_min_grid(int nf);
+int fsi_min_grid(int nf, bool big);
 int fsi_float_ld(int nf);
 
 static thread_local char g_errmsg[512] = "";
@@ -559,8 +559,15 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
   if (true_e) {  // true E at the body points: no B0; torsional and rigid bodies
     if (drop_tol > 0.0 || c->n_def > 0 || c->nb > 1024 || c->prec == FSI_PREC_MIXED) return FSI_ERR_UNSUPPORTED;
     if (c->x.krylov_max_iters <= 0) c->x.krylov_max_iters = 2 * c->nf + 20;
-  } else if (c->nb > 0 && !fsi_smem_fits(c)) {
-    return FSI_ERR_UNSUPPORTED;
+  } else if (c->nb > 0) {
+    // the FSI kernel keeps the float inverse in every CTA's shared memory when it fits (nf up to ~230), and
+    // otherwise distributes a block-Jacobi inverse and K over the CTAs through global memory
+    const int want = c->x.fsi_solver;
+    if (want < 0 || want > 2) return FSI_ERR_INVALID_ARG;
+    const bool small_ok = fsi_smem_fits(c, false);
+    c->fsi_big = want == 2 || (want == 0 && !small_ok);
+    if (!c->fsi_big && !small_ok) return FSI_ERR_UNSUPPORTED;
+    if (c->fsi_big && !fsi_smem_fits(c, true)) return FSI_ERR_UNSUPPORTED;
   }
   const size_t n2 = 2 * (size_t)c->n_sd;
   fsi_status st = FSI_OK;
@@ -699,10 +706,13 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
     if (per_sm < 1) return FSI_ERR_UNSUPPORTED;
     // two rows of the small system per CTA (at most one CTA per SM): small systems leave SMs free for
     // the kernels of other runs on the same GPU
-    c->fsi_grid = (c->nf + 1) / 2;
+    c->fsi_grid = c->fsi_big ? nsm : (c->nf + 1) / 2;
     if (c->fsi_grid < 8) c->fsi_grid = 8;
     if (c->fsi_grid > nsm) c->fsi_grid = nsm;
-    if (c->fsi_grid < fsi_min_grid(c->nf)) return FSI_ERR_UNSUPPORTED;
+    if (c->fsi_grid < fsi_min_grid(c->nf, c->fsi_big != 0)) return FSI_ERR_UNSUPPORTED;
+    if (c->fsi_big && (!(c->d_dvec = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+                       !(c->d_rsum = (double*)ctx_alloc(c, (size_t)c->nf * 8))))
+      return FSI_ERR_OOM;
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->stage = 1;

@@ -49,6 +49,11 @@ constexpr int BS = 32;       // Cholesky / inverse / GEMM tile (one warp wide)
 constexpr int kMaxBodies = 64;
 constexpr int kMaxR = 4;     // rows (and columns) of the small system owned by one CTA
 constexpr int kMaxRhs = 1 + kMaxR;  // structural solves per flag in phase A: y and the owned columns
+// The distributed variant (nf too large for the float inverse in shared memory): rows per CTA and Newton-Schulz
+// steps of a rebuild from a scaled identity.
+constexpr int kMaxRB = 12;
+constexpr int kNsRebuild = 30;
+
 constexpr unsigned FULL = 0xffffffffu;
 
 struct FsiArgs {
@@ -110,6 +115,9 @@ struct FsiArgs {
   int n_sdb;
   int sdb[16][4];
   const int* sd_map;
+  // distributed variant: the correction d = X r of every row, and per-row absolute sums of K (rebuild)
+  double* dvec;
+  double* rsum;
 };
 
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
@@ -386,16 +394,18 @@ __host__ __device__ inline int fsi_ldx(int nf) {
   if (((l / 4) & 1) == 0) l += 4;
   return l;
 }
-__host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
+// big: the distributed variant, which keeps X and K in global memory (no X or owned K rows in shared memory;
+// the work area holds the tiles of its block products).
+__host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd, bool big = false) {
   FsiLayout L;
   const size_t lx = (size_t)fsi_ldx(nf);
   const size_t xa = (size_t)nf * lx, xb = (size_t)nf * (size_t)(nf | 1);  // X, or the Cholesky factor
   L.xs = 0;
-  L.krow = L.xs + al16((xa > xb ? xa : xb) * 4);
-  L.vec = L.krow + al16((size_t)kMaxR * nf * 8);
+  L.krow = L.xs + (big ? 0 : al16((xa > xb ? xa : xb) * 4));
+  L.vec = L.krow + (big ? 0 : al16((size_t)kMaxR * nf * 8));
   L.pw = L.vec + al16((size_t)3 * nf * 8);
   L.work = L.pw + al16((size_t)4 * nb * 8);
-  L.rf = L.work + al16(lx * 16);
+  L.rf = L.work + (big ? al16((size_t)(64 * 33 + 32 * 64) * 4) : al16(lx * 16));
   L.pidx = L.rf + al16(lx * 4);
   L.pcij = L.pidx + al16((size_t)4 * nb * 4);
   L.chi = L.pcij + al16((size_t)2 * nb * 4);
@@ -408,7 +418,7 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd) {
   L.bm = L.mi + al16((size_t)6 * bd.ne * 4);
   L.ey = L.bm + al16((size_t)9 * bd.ne * 4);
   L.ys = L.ey + al16((size_t)12 * bd.ne * 4);
-  L.kb = L.ys + al16((size_t)kMaxRhs * bd.nd_max * 4);
+  L.kb = L.ys + al16((size_t)(big ? 1 + kMaxRB : kMaxRhs) * bd.nd_max * 4);
   L.total = L.kb + al16((size_t)bd.nkb * KB_N * 8);
   return L;
 }
@@ -468,7 +478,111 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// ---- Distributed small-system solver (the kernel's BIG variant) -------------------------------------------
+// X is a block-Jacobi float inverse of K: one block per body (its 2n rows and columns, x then y components),
+// kept in global memory with K's float copy S.  Row r of the block of body b has its columns at
+// off + t (t < n) and nb + off + t - n (n <= t < 2n).  A CTA owns rows r0 .. r0 + nr - 1 of every matrix;
+// consecutive owned rows with the same block form a group, whose rows are multiplied together so that each
+// CTA reads the block operand once per product.
+struct RowBlock {
+  int off, n;
+};
+__device__ __forceinline__ RowBlock row_block(const FsiArgs& a, int r) {
+  const BodyDev& b = a.bodies[a.point_body[r % a.nb]];
+  return RowBlock{b.off, b.n};
+}
+__device__ __forceinline__ int blk_col(RowBlock b, int nb, int t) { return t < b.n ? b.off + t : nb + b.off + (t - b.n); }
+
+// Tiled block products of the Newton-Schulz steps: out = alpha X0 + beta A B on every block (A, B, X0, out
+// restricted to the block's rows and columns), each block's output cut into 64 x 64 tiles and all tiles of
+// all blocks dealt round-robin to the CTAs.  A CTA streams a tile's 64 rows of A and 64 columns of B through
+// shared memory in steps of 32 (the next step's loads issued before the current step is multiplied); a
+// thread accumulates a 4 x 4 part of the tile.  smem: 64 x 33 + 32 x 64 floats.
+constexpr int kGT = 64, kGK = 32;
+__device__ void blk_gemm(const FsiArgs& a, const float* A, const float* B, const float* X0, float alpha, float beta,
+                         float* out, int lx, float* smem) {
+  const int tid = threadIdx.x, nb = a.nb;
+  const int ty = tid >> 4, tx = tid & 15;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 of the tile
+  float* As = smem;                        // [kGT][kGK + 1]
+  float* Bs = smem + kGT * (kGK + 1);      // [kGK][kGT]
+  int tiles_before = 0;
+  for (int bi = 0; bi < a.n_bodies; ++bi) {
+    const BodyDev bd = a.bodies[bi];
+    const RowBlock b{bd.off, bd.n};
+    const int n2 = 2 * b.n, nt = (n2 + kGT - 1) / kGT;
+    for (int tile = (int)blockIdx.x - tiles_before % (int)gridDim.x; tile < nt * nt; tile += gridDim.x) {
+      if (tile < 0) continue;
+      const int i0 = (tile / nt) * kGT, j0 = (tile % nt) * kGT;
+      float acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+      float ra[8], rb[8];  // this thread's share of the next step's A (64 x 32) and B (32 x 64) tiles
+      auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = tid + q * 256;
+          const int ar = e >> 5, ak = e & 31;  // A tile: row ar, step column ak
+          const int gi = i0 + ar, gk = k0 + ak;
+          ra[q] = (gi < n2 && gk < n2) ? __ldcg(&A[(long)blk_col(b, nb, gi) * lx + blk_col(b, nb, gk)]) : 0.0f;
+          const int bk = e >> 6, bc = e & 63;  // B tile: step row bk, column bc
+          const int gk2 = k0 + bk, gj = j0 + bc;
+          rb[q] = (gk2 < n2 && gj < n2) ? __ldcg(&B[(long)blk_col(b, nb, gk2) * lx + blk_col(b, nb, gj)]) : 0.0f;
+        }
+      };
+      load(0);
+      for (int k0 = 0; k0 < n2; k0 += kGK) {
+        __syncthreads();  // the previous step's tiles are no longer read
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = tid + q * 256;
+          As[(e >> 5) * (kGK + 1) + (e & 31)] = ra[q];
+          Bs[e] = rb[q];
+        }
+        __syncthreads();
+        if (k0 + kGK < n2) load(k0 + kGK);  // in flight while this step is multiplied
+#pragma unroll 8
+        for (int kk = 0; kk < kGK; ++kk) {
+          float av[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) av[u] = As[(4 * ty + u) * (kGK + 1) + kk];
+          const float4 b4 = reinterpret_cast<const float4*>(Bs)[kk * (kGT / 4) + tx];  // 16-byte aligned rows
+          const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int gi = i0 + 4 * ty + u;
+        if (gi >= n2) continue;
+        const long ro = (long)blk_col(b, nb, gi) * lx;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int gj = j0 + 4 * tx + v;
+          if (gj >= n2) continue;
+          const long o = ro + blk_col(b, nb, gj);
+          out[o] = alpha != 0.0f ? alpha * __ldcg(&X0[o]) + beta * acc[u][v] : beta * acc[u][v];
+        }
+      }
+    }
+    tiles_before += nt * nt;
+  }
+  __syncthreads();
+}
+
+template <bool BIG>
 __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
+  constexpr int MR = BIG ? kMaxRB : kMaxR;  // owned rows per CTA
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ double red[256];
@@ -495,7 +609,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   const int R = (nf + (int)gridDim.x - 1) / (int)gridDim.x;
   const int r0 = min(nf, (int)blockIdx.x * R);
   const int nr = min(nf, r0 + R) - r0;
-  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max, a.nkb});
+  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max, a.nkb}, BIG);
   float* Xs = reinterpret_cast<float*>(dyn_smem + L.xs);
   double* Krow = reinterpret_cast<double*>(dyn_smem + L.krow);
   double* rhs_s = reinterpret_cast<double*>(dyn_smem + L.vec);
@@ -518,9 +632,21 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   float* ys_s = reinterpret_cast<float*>(dyn_smem + L.ys);
   // per-body kinematics block of this step (KB_* in internal.h), NULL without driven bodies
   double* kb_s = a.nkb > 0 ? reinterpret_cast<double*>(dyn_smem + L.kb) : nullptr;
+  float* tile = reinterpret_cast<float*>(dyn_smem + L.work);  // BIG: tile of the block products
+  // BIG: the owned rows in groups of consecutive rows with the same block (same in every thread of the CTA)
+  auto for_groups = [&](auto fn) {
+    int g0 = r0;
+    while (g0 < r0 + nr) {
+      const RowBlock b = row_block(a, g0);
+      int g1 = g0 + 1;
+      while (g1 < r0 + nr && row_block(a, g1).off == b.off) ++g1;
+      fn(g0, g1 - g0, b);
+      g0 = g1;
+    }
+  };
   // rows owned by this CTA that are x / y rows of a free flag node: their structural column is solved here
-  __shared__ int g_body[kMaxR], g_dof[kMaxR];
-  if (tid < kMaxR) {
+  __shared__ int g_body[MR], g_dof[MR];
+  if (tid < MR) {
     g_body[tid] = -1;
     g_dof[tid] = 0;
     if (tid < nr && a.n_def > 0) {
@@ -615,7 +741,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   }
   for (int k = nf + tid; k < lx; k += nthr) rf[k] = 0.0f;
   __syncthreads();
-  if (kinv_valid) load_x(Xs, cur ? a.Xb : a.Xa, nf, lx, &xbar, &xphase, a.status);
+  if (!BIG && kinv_valid) load_x(Xs, cur ? a.Xb : a.Xa, nf, lx, &xbar, &xphase, a.status);
   PhaseClock clk(sh_phase, blockIdx.x == 0 && tid == 0 && a.phase_ns);
   __syncthreads();
 
@@ -648,7 +774,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
     } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
       const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
-      for (int al = 0; al < 4; ++al) {
+      // every vertex pair lies outside the window when the hat cells are more than bw + 1 apart
+      const bool near = dj0 <= bw + 1 && dj0 >= -bw - 1 && di0 <= bw + 1 && di0 >= -bw - 1;
+      for (int al = 0; near && al < 4; ++al) {
         const double wa = pw_s[4 * pa + al];
         double t = 0.0;
 #pragma unroll
@@ -833,7 +961,11 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
         for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
         named_sync_lower();
-        for (int e = tid; e < nr * nf; e += 128) Krow[e] = k_entry(r0 + e / nf, e % nf, false);
+        for (int e = tid; e < nr * nf; e += 128) {
+          const double kv = k_entry(r0 + e / nf, e % nf, false);
+          if constexpr (BIG) a.K[(long)r0 * nf + e] = kv;  // owned rows stay in global memory
+          else Krow[e] = kv;
+        }
       }
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
@@ -866,9 +998,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
                              nb};
           beam::flag_elements(F, st, 128);
           named_sync_upper();
-          int nrhs = 1, rdof[kMaxR], rrow[kMaxR];  // owned structural columns of this flag
+          int nrhs = 1, rdof[MR], rrow[MR];  // owned structural columns of this flag
 #pragma unroll
-          for (int c = 0; c < kMaxR; ++c)
+          for (int c = 0; c < MR; ++c)
             if (g_body[c] == bi) {
               rdof[nrhs - 1] = g_dof[c];
               rrow[nrhs - 1] = r0 + c;
@@ -901,11 +1033,11 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       __syncthreads();
       for (int e = tid; e < nr * nf; e += nthr) {
         const int r = r0 + e / nf, cidx = e % nf;
-        double kv = Krow[e];
+        double kv = BIG ? a.K[(long)r0 * nf + e] : Krow[e];
         const int ba = a.point_body[r % nb];
         if (ba == a.point_body[cidx % nb] && a.bodies[ba].type == FSI_BODY_DEFORMABLE)
           kv += a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
-        Krow[e] = kv;
+        if constexpr (!BIG) Krow[e] = kv;
         a.K[(long)r * nf + cidx] = kv;
         a.S[(long)r * lx + cidx] = (float)kv;
       }
@@ -948,15 +1080,16 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
       }
       grid.sync();
-      for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
+      if constexpr (!BIG)
+        for (int e = tid; e < nr * nf; e += nthr) Krow[e] = __ldcg(&a.K[(long)r0 * nf + e]);  // owned rows of K
     }
     // Flags.  The structural right-hand side was formed from J_d^-1 (r^zeta(k) + ds T^T f_prev) instead of
     // J_d^-1 r^zeta(k); the two differ by (2 ds/dt) T J_d^-1 T^T f_prev, which the owned residual rows add
     // back here with the same entries of T J_d^-1 T^T that K holds.  Both FP32 structural solves then act
     // on quantities that vanish at the fixed point, whose float errors therefore vanish with them.
-    __shared__ double gfp_s[kMaxR];
+    __shared__ double gfp_s[MR];
     if (a.n_def > 0) {
-      for (int c = wid; c < kMaxR; c += nw) {
+      for (int c = wid; c < MR; c += nw) {
         double acc = 0.0;
         if (c < nr) {
           const int r = r0 + c;
@@ -972,14 +1105,31 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         acc = warp_sum(acc);
         if (lane == 0) gfp_s[c] = a.ds * a.two_dt * acc;
       }
-    } else if (tid < kMaxR) {
+    } else if (tid < MR) {
       gfp_s[tid] = 0.0;
     }
     __syncthreads();
     clk.mark(1);
     // ---- C: refresh the float inverse (Newton-Schulz from the previous one, or a rebuild), then refine
     // Newton-Schulz refresh of the float inverse for the current K: X <- 2X - (X K) X, kNsSteps times
+    // BIG: one Newton-Schulz step on every block, T = X K then X <- 2X - T X, by owned rows
+    auto big_ns_step = [&]() {
+      float* Xc = cur ? a.Xb : a.Xa;
+      float* Xn = cur ? a.Xa : a.Xb;
+      blk_gemm(a, Xc, a.S, Xc, 0.0f, 1.0f, a.T, lx, tile);
+      grid.sync();
+      clk.sub(8);
+      blk_gemm(a, a.T, Xc, Xc, 2.0f, -1.0f, Xn, lx, tile);
+      grid.sync();
+      clk.sub(9);
+      cur ^= 1;
+    };
     auto ns_refresh = [&]() {
+      if constexpr (BIG) {  // one step: the error I - K X is squared, and a step costs four block GEMMs
+        big_ns_step();
+        clk.mark(2);
+        return;
+      }
       for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - (X K) X: the error I - K X is squared
         float* Xn = cur ? a.Xa : a.Xb;
         // (a) owned columns of T = X K: T[i][r0 + c] = sum_m X[i][m] K[m][r0 + c]
@@ -1053,7 +1203,38 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     };
     for (int attempt = 0; attempt < 2; ++attempt) {
       bool fresh = false;  // X was refreshed or rebuilt for this K
-      if (!kinv_valid) {
+      if (BIG && !kinv_valid) {
+        // X0 = alpha I on every block with alpha = 1 / (largest absolute row sum of the block of K), so that the
+        // eigenvalues of alpha K lie in the unit disc about 1, then Newton-Schulz steps to convergence
+        for (int c = wid; c < nr; c += nw) {
+          const int i = r0 + c;
+          const RowBlock b = row_block(a, i);
+          double acc = 0.0;
+          for (int t = lane; t < 2 * b.n; t += 32) acc += fabs(__ldcg(&a.K[(long)i * nf + blk_col(b, nb, t)]));
+          acc = warp_sum(acc);
+          if (lane == 0) a.rsum[i] = acc;
+        }
+        grid.sync();
+        float* Xc = cur ? a.Xb : a.Xa;
+        for_groups([&](int g0, int ng, RowBlock b) {
+          double mx = 0.0;
+          for (int t = tid; t < 2 * b.n; t += nthr) mx = fmax(mx, __ldcg(&a.rsum[blk_col(b, nb, t)]));
+          mx = block_max(mx, red);
+          const float alpha = (float)(1.0 / mx);
+          for (int e = tid; e < ng * 2 * b.n; e += nthr) {
+            const int g = e / (2 * b.n), t = e - g * 2 * b.n, col = blk_col(b, nb, t);
+            Xc[(long)(g0 + g) * lx + col] = col == g0 + g ? alpha : 0.0f;
+          }
+          __syncthreads();
+        });
+        grid.sync();
+        for (int k = 0; k < kNsRebuild; ++k) big_ns_step();
+        kinv_valid = 1;
+        fresh = true;
+        if (blockIdx.x == 0 && tid == 0) a.ctrl[6] += 1;  // rebuild count
+        clk.mark(3);
+      }
+      if (!BIG && !kinv_valid) {
         float* Lf = Xs;  // CTA 0 factors in the space of X, which is being rebuilt
         if (blockIdx.x == 0) {
           for (int i = tid >> 5; i < nf; i += nthr >> 5)
@@ -1098,9 +1279,14 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           __syncthreads();
         }
         for (int c = wid; c < nr; c += nw) {
-          const double* kr = Krow + (long)c * nf;
           double acc = 0.0;
-          for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          if constexpr (BIG) {
+            const double* kr = a.K + (long)(r0 + c) * nf;
+            for (int k = lane; k < nf; k += 32) acc += __ldcg(&kr[k]) * f_s[k];
+          } else {
+            const double* kr = Krow + (long)c * nf;
+            for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          }
           acc = warp_sum(acc);
           if (lane == 0) res1[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
         }
@@ -1113,7 +1299,30 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
         __syncthreads();
         unsigned dbits = 0u, xbits = 0u;  // max |d|, max |f| as float bit patterns
-        for (int i = tid; i < nf; i += nthr) {  // d = X r, f += d (every CTA, all rows; thread per row)
+        if constexpr (BIG) {  // owned rows of d = X r (block columns), shared through global memory
+          const float* Xc = cur ? a.Xb : a.Xa;
+          for (int c = wid; c < nr; c += nw) {
+            const int i = r0 + c;
+            const RowBlock b = row_block(a, i);
+            float acc = 0.0f;
+            for (int t = lane; t < 2 * b.n; t += 32) {
+              const int col = blk_col(b, nb, t);
+              acc += __ldcg(&Xc[(long)i * lx + col]) * rf[col];
+            }
+            acc = warp_sum_f(acc);
+            if (lane == 0) a.dvec[i] = (double)acc;
+          }
+          grid.sync();
+          for (int i = tid; i < nf; i += nthr) {
+            const double di = __ldcg(&a.dvec[i]);
+            const double xi = (s == 0 && !warm ? 0.0 : f_s[i]) + di;
+            f_s[i] = xi;
+            const float xf = (float)xi;
+            dbits = max(dbits, isfinite(xf) ? __float_as_uint(fabsf((float)di)) : 0x7f800000u);
+            xbits = max(xbits, __float_as_uint(fabsf(xf)));
+          }
+        }
+        for (int i = BIG ? nf : tid; i < nf; i += nthr) {  // d = X r, f += d (every CTA, all rows; thread per row)
           const float4* xr = reinterpret_cast<const float4*>(Xs + (long)i * lx);
           const float4* r4 = reinterpret_cast<const float4*>(rf);
           float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // four chains, summed in a fixed order
@@ -1148,7 +1357,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           break;
         }
         if (s == kMaxSolves - 1) break;
-        if (!fresh && s > 0 && ratio > kNsTrigger) {  // X is stale for this K: refresh it, keep f and r
+        // X is stale for this K: refresh it, keep f and r (the distributed variant tolerates a slower
+        // contraction before paying for its block GEMMs)
+        if (!fresh && s > 0 && ratio > (BIG ? 0.05 : kNsTrigger)) {
           ns_refresh();
           ++refreshes;
           fresh = true;
@@ -1157,9 +1368,14 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           worst_ratio = fmax(worst_ratio, ratio);
         }
         for (int c = wid; c < nr; c += nw) {  // owned residual rows r = rhs - K f in double
-          const double* kr = Krow + (long)c * nf;
           double acc = 0.0;
-          for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          if constexpr (BIG) {
+            const double* kr = a.K + (long)(r0 + c) * nf;
+            for (int k = lane; k < nf; k += 32) acc += __ldcg(&kr[k]) * f_s[k];
+          } else {
+            const double* kr = Krow + (long)c * nf;
+            for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
+          }
           acc = warp_sum(acc);
           if (lane == 0) ((s & 1) ? res1 : res0)[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
         }
@@ -1173,7 +1389,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
       solves_total += s + 1;
       if (done) {
-        if (worst_ratio > kStaleRatio) kinv_valid = 0;
+        // a slow contraction marks X for a rebuild at the next iteration; the distributed variant refreshes it
+        // there instead (its rebuild starts from a scaled identity)
+        if (!BIG && worst_ratio > kStaleRatio) kinv_valid = 0;
         break;
       }
       kinv_valid = 0;  // not converged with this inverse: rebuild it and solve again
@@ -1375,18 +1593,21 @@ static BeamDims beam_dims(const fsi_ctx* c) {
   return BeamDims{c->nd_tot, c->ne_tot, c->nd_max, c->d_kin ? c->n_bodies : 0};
 }
 
-size_t fsi_smem_bytes(const fsi_ctx* c) { return fsi_layout(c->nf, c->nb, beam_dims(c)).total; }
+// Dynamic shared memory of the FSI kernel: the variant with the float inverse in shared memory, or (big) the
+// distributed one.
+size_t fsi_smem_bytes(const fsi_ctx* c, bool big) { return fsi_layout(c->nf, c->nb, beam_dims(c), big).total; }
+size_t fsi_smem_bytes(const fsi_ctx* c) { return fsi_smem_bytes(c, c->fsi_big != 0); }
 
-// dynamic plus static shared memory of the FSI kernel within the per-block opt-in limit of the device
-bool fsi_smem_fits(const fsi_ctx* c) {
+// dynamic plus static shared memory of a variant of the FSI kernel within the per-block opt-in limit
+bool fsi_smem_fits(const fsi_ctx* c, bool big) {
   cudaFuncAttributes fa;
   int dev = 0, optin = 0;
-  if (cudaFuncGetAttributes(&fa, k_fsi) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+  if (cudaFuncGetAttributes(&fa, big ? k_fsi<true> : k_fsi<false>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return fsi_smem_bytes(c) + fa.sharedSizeBytes <= (size_t)optin;
+  return fsi_smem_bytes(c, big) + fa.sharedSizeBytes <= (size_t)optin;
 }
 
 // row stride (floats) of the float nf x nf matrices of the FSI kernel
@@ -1395,17 +1616,18 @@ int fsi_float_ld(int nf) { return fsi_ldx(nf); }
 // CTAs of the FSI kernel per SM at this size (0: does not fit)
 int fsi_kernel_max_ctas_per_sm(const fsi_ctx* c) {
   const size_t bytes = fsi_smem_bytes(c);
-  if (raise_smem_limit(k_fsi, bytes) != cudaSuccess) {
+  const bool big = c->fsi_big != 0;
+  if (raise_smem_limit(big ? k_fsi<true> : k_fsi<false>, bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fsi, 256, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big ? k_fsi<true> : k_fsi<false>, 256, bytes);
   return n;
 }
 
-// every CTA owns at most kMaxR rows of the small system
-int fsi_min_grid(int nf) { return (nf + kMaxR - 1) / kMaxR; }
+// every CTA owns at most kMaxR rows of the small system (kMaxRB in the distributed variant)
+int fsi_min_grid(int nf, bool big) { return big ? (nf + kMaxRB - 1) / kMaxRB : (nf + kMaxR - 1) / kMaxR; }
 
 fsi_status launch_fsi(fsi_ctx* c) {
   FsiArgs a;
@@ -1474,6 +1696,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.n_sdb = c->n_sdb > 1 ? c->n_sdb : 1;
   memcpy(a.sdb, c->sdb, sizeof(a.sdb));
   a.sd_map = c->n_sdb > 1 ? c->d_sd_map : nullptr;
+  a.dvec = c->d_dvec;
+  a.rsum = c->d_rsum;
+  const bool big = c->fsi_big != 0;
   a.lb_missing = c->wait_missing;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->fsi_grid);
@@ -1485,9 +1710,9 @@ fsi_status launch_fsi(fsi_ctx* c) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FSI_CUDA_TRY(raise_smem_limit(k_fsi, cfg.dynamicSmemBytes));
+  FSI_CUDA_TRY(raise_smem_limit(big ? k_fsi<true> : k_fsi<false>, cfg.dynamicSmemBytes));
   prof_mark(c, KC_FSI);
-  FSI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fsi, a));
+  FSI_CUDA_TRY(cudaLaunchKernelEx(&cfg, big ? k_fsi<true> : k_fsi<false>, a));
   prof_mark(c, KC_FSI);
   c->launches_per_step += 1;
   return FSI_OK;

@@ -197,6 +197,9 @@ struct fsi_ctx {
   long long steps_done;
   int max_iters_seen;
   int fsi_grid;  // CTAs of the cooperative FSI kernel
+  int fsi_big;   // 1: the distributed variant of the FSI kernel (block-Jacobi inverse and K in global memory)
+  double* d_dvec;  // distributed variant: [nf] corrections d = X r shared between the CTAs
+  double* d_rsum;  // distributed variant: [nf] absolute row sums of K (rebuild of the inverse)
   // bounded cross-CTA wait of the FSI kernel (fsi_debug_set_wait_limit): poll limit (0: default) and
   // arrivals it waits for that never come (0 in normal runs)
   unsigned wait_spins;

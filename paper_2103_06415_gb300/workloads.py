@@ -240,3 +240,41 @@ def tandem_small(nx=96, ny=48, n_levels=2):
                 dict(kind="deformable", clamp=hinges[2], theta0=0.0, n_pts=9, mass=0.5, ei=1e-2, ea=1e3,
                      tip_angle=0.1)],
         ds=h)
+
+
+def tandem_nf246():
+    """Three bodies of 41 points (two torsional plates and a flag, chord 1.25 at ds = h = 1/32) in three
+    Omega_0 boxes on 192 x 96 cells, 2 levels: nf = 246, beyond the small system the FSI kernel can hold in
+    shared memory, so the distributed block-inverse solver runs; small enough for the oracle."""
+    h = 1.0 / 32
+    hinges = [(-0.6, 0.0), (1.2, 0.0), (3.0, 0.0)]
+    return dict(
+        name="tandem_nf246_192x96_2lvl", nx=192, ny=96, n_levels=2, x0=-1.0, y0=-1.5, h=h, re=100.0, dt=0.004,
+        uinf=(1.0, 0.0), steps=20, sd_box=[(hx - 0.2, hx + 1.45, -0.7, 0.7) for hx, _ in hinges],
+        bodies=[dict(kind="torsional", hinge=hinges[0], theta0=0.0, n_pts=41, inertia=0.5, damping=0.0,
+                     stiffness=0.5, theta=np.deg2rad(15.0)),
+                dict(kind="torsional", hinge=hinges[1], theta0=0.0, n_pts=41, inertia=0.5, damping=0.0,
+                     stiffness=2.0, theta=np.deg2rad(15.0)),
+                dict(kind="deformable", clamp=hinges[2], theta0=0.0, n_pts=41, mass=0.5, ei=1e-2, ea=1e3,
+                     tip_angle=0.1)],
+        ds=h)
+
+
+def tandem_1536x768_5lvl():
+    """The large coupled workload: 5 nested levels of 1536 x 768 cells, finest h = 1/200 on
+    [-1, 6.68] x [-1.92, 1.92], Re 1000, dt 2e-4, 5000 steps; three torsionally hinged plates of chord 1
+    (201 points at ds = h) in tandem, hinged at (0, 0), (1.5, 0), (3, 0), initial angle 20 degrees, springs
+    0.2, 1 and 5 (inertia 1, no damping; the workload gives the springs only), and a clamped flag of length 1
+    (201 points) at (4.5, 0) with mass ratio 1, bending stiffness 1e-4, stretching stiffness 1e3 and initial tip
+    slope 0.1 rad; each body inside its own Omega_0 box [x_h - 0.1, x_h + 1.1] x [-1.1, 1.1] (241 x 441
+    vertices, 425 k points in the union, 850 k unknowns), so B0 is the filtered B0' (Eq. filtereq, eps = 0.007;
+    dense it would hold 5.8 TB).  nf = 1608."""
+    h = 1.0 / 200
+    hinges = [(0.0, 0.0), (1.5, 0.0), (3.0, 0.0), (4.5, 0.0)]
+    plates = [dict(kind="torsional", hinge=hinges[k], theta0=0.0, n_pts=201, inertia=1.0, damping=0.0,
+                   stiffness=kk, theta=np.deg2rad(20.0)) for k, kk in enumerate((0.2, 1.0, 5.0))]
+    flag = dict(kind="deformable", clamp=hinges[3], theta0=0.0, n_pts=201, mass=1.0, ei=1e-4, ea=1e3, tip_angle=0.1)
+    return dict(
+        name="tandem_1536x768_5lvl", nx=1536, ny=768, n_levels=5, x0=-1.0, y0=-1.92, h=h, re=1000.0, dt=2e-4,
+        uinf=(1.0, 0.0), steps=5000, sd_box=[(hx - 0.1, hx + 1.1, -1.1, 1.1) for hx, _ in hinges],
+        bodies=plates + [flag], ds=h, drop_tol=0.007)

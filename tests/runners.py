@@ -24,11 +24,14 @@ def oracle_sim(w, **kw):
                                      tip_angle=b["tip_angle"]))
         else:
             bodies.append(ofsi.RigidBody(b["pts"], b.get("ur"), b.get("appended", False)))
+    kw.setdefault("drop_tol", w.get("drop_tol", 0.0))
     return ofsi.Sim(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["n_levels"], w["re"], w["dt"], w["uinf"],
                     w["sd_box"], bodies, w["ds"], **kw)
 
 
-def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0, drop_tol=0.0, **kw):
+def gpu_context(w, precision=0, use_graph=True, precompute=True, stream=None, b0_method=0, drop_tol=None, **kw):
+    if drop_tol is None:
+        drop_tol = w.get("drop_tol", 0.0)     # the workload's filter of B0 (Eq. filtereq), if it names one
     import paper_2103_06415_gb300 as lib
     c = lib.Context(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"], w["uinf"],
                     precision=precision, use_graph=use_graph, stream=stream, b0_method=b0_method, **kw)

@@ -64,20 +64,29 @@ def test_no_slip_after_corrector_at_full_size(lib, setup, precision, bound):
 
 
 N_FULL = 12
+_ORACLE = {}
 
 
-@pytest.fixture(scope="module")
-def full_size_runs(lib, setup):
+def _oracle_run(w):
+    """The oracle's N_FULL steps of the workload at FSI tolerance 1e-12 (computed once per module)."""
+    if "sim" not in _ORACLE:
+        from runners import oracle_sim
+        sim = oracle_sim(w, tol=1e-12)
+        for _ in range(N_FULL):
+            sim.step()
+        _ORACLE["sim"] = sim
+    return _ORACLE["sim"]
+
+
+@pytest.fixture(scope="module", params=[1, 2], ids=["shared_memory_solver", "distributed_solver"])
+def full_size_runs(lib, setup, request):
     """The headline workload at full size, FP64 on the GPU (the bench's CUDA graph, the 101-CTA FSI kernel
     with owned-row assembly and the warps 0-3 barrier) and in the oracle, N_FULL steps from the same
     start, at an FSI tolerance of 1e-12 on both sides (so the iteration counts are decided far from the
     threshold and must agree)."""
-    from runners import oracle_sim
     w, lev, sd = setup
-    sim = oracle_sim(w, tol=1e-12)
-    for _ in range(N_FULL):
-        sim.step()
-    ctx = gpu_context(w, precision=0, tol=1e-12)
+    sim = _oracle_run(w)
+    ctx = gpu_context(w, precision=0, tol=1e-12, fsi_solver=request.param)
     ctx.advance(N_FULL)
     nb = w["bodies"][0]["n_pts"]
     out = dict(sim=sim, hist=ctx.history(0), state=ctx.beam_state(0), interp=ctx.interp(nb),
