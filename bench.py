@@ -54,8 +54,11 @@ def parse():
                     help="comma-separated comparator runs (default: all), e.g. fp64_true_e")
     ap.add_argument("--oracle-worker", default="", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=10.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-level", default="", help=argparse.SUPPRESS)
     ap.add_argument("--horizon-steps", type=int, default=-1,
                     help="steps of the mixed-vs-FP64 history check (default: the workload's own horizon)")
+    ap.add_argument("--profile-case", default="tandem", choices=["tandem", "flag"],
+                    help="profiling mode workload: the reduced tandem case (nf = 1608) or the reduced flag case")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: build the reduced-Omega_0 variant of the workload, run this many "
                          "eager (non-graph) steps and exit without timing (for ncu captures)")
@@ -63,6 +66,13 @@ def parse():
 
 
 def workload():
+    """The largest single-GPU configuration: 5 levels of 1536 x 768, three plates and a flag (nf = 1608)."""
+    from paper_2103_06415_gb300 import workloads as wl
+    return wl.tandem_1536x768_5lvl()
+
+
+def secondary_workload():
+    """The 3-level 512 x 256 flag, measured beside the headline with its 2000-step precision check."""
     from paper_2103_06415_gb300 import workloads as wl
     return wl.flag_512x256_3lvl()
 
@@ -98,6 +108,59 @@ def _oracle_worker(path, budget_s):
         if el > budget_s or n >= 50:
             break
     print(json.dumps({"steps": n, "seconds": el}), flush=True)
+
+
+def _level_pair_seconds(w, nx, ny):
+    """Wall time of the oracle's two level solves of a step (A_w^-1 then Lap^-1 by dense DSTs) on one level of
+    nx x ny cells with the workload's spacing, Re and dt."""
+    import numpy as np
+    from oracle import grid as og
+    lev = og.Level(nx, ny, w["h"], w["x0"], w["y0"])
+    rhs = np.random.default_rng(1).standard_normal((ny - 1, nx - 1))
+    zero = np.zeros(lev.shape)
+    t0 = time.perf_counter()
+    wv = og.solve_aw(rhs, zero, lev, w["re"], w["dt"])
+    og.solve_lap(wv, zero, lev)
+    return time.perf_counter() - t0
+
+
+def oracle_level_sample(w):
+    """The FP64 oracle as it stands cannot take one step of the 1536 x 768 x 5 workload in a bounded time (its
+    first FSI iteration alone needs ~6400 B0 columns of full dense-DST solves), so its rate is sampled: the
+    oracle's pair of level solves on one level of the workload's grid, timed once with every host core available
+    to numpy's BLAS, and extrapolated to a step as (levels + 1) such pairs (every predictor level and the
+    corrector).  Advection, the FSI iteration and the B0 columns are left out, so the figure is an upper bound
+    on the oracle's rate.  At one BLAS thread the same pair is timed on a half-size level (nx/2 x ny/2) and
+    scaled by the dense-DST operation count Nx Ny (Nx + Ny)."""
+    cores = os.cpu_count()
+    pairs = w["n_levels"] + 1
+    t = _level_pair_seconds(w, w["nx"], w["ny"])
+    out = dict(value=cells_per_step(w) / (pairs * t), unit="cell-steps/s", cores=cores, kind="oracle",
+               sample="one pair of level solves (A_w^-1, Lap^-1; naive dense DST, numpy FP64) on one %d x %d level "
+                      "of %s in %.1f s with all %d cores, extrapolated to a step as %d pairs; advection, FSI and "
+                      "B0 columns not counted (an upper bound on the oracle's rate)"
+                      % (w["nx"], w["ny"], w["name"], t, cores, pairs),
+               ms_per_step=1e3 * pairs * t)
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    hx, hy = w["nx"] // 2, w["ny"] // 2
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-level", "%d,%d" % (hx, hy)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    try:
+        th = float(r.stdout.strip().splitlines()[-1])
+
+        def ops(nx, ny):
+            return (nx - 1) * (ny - 1) * ((nx - 1) + (ny - 1))
+        t1 = th * ops(w["nx"], w["ny"]) / ops(hx, hy)
+        out["one_thread"] = dict(value=cells_per_step(w) / (pairs * t1), unit="cell-steps/s", cores=1,
+                                 sample="the same pair on a %d x %d level at one BLAS thread (%.1f s), scaled by "
+                                        "the dense-DST operation count to %d x %d (%.0f s), %d pairs per step"
+                                        % (hx, hy, th, w["nx"], w["ny"], t1, pairs),
+                                 ms_per_step=1e3 * pairs * t1)
+    except (ValueError, IndexError):
+        pass
+    return out
 
 
 def oracle_sample(w, budget_s, one_thread_budget_s=None):
@@ -408,21 +471,32 @@ def mixed_vs_fp64_horizon(w, n, make, lib, prec):
 
 
 def run_reference(args, w):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on the same workload and metric.  Each
+    step is the bounded sample of oracle_level_sample (a pair of dense-DST level solves, extrapolated to the
+    step); as many of the K steps as fit in about a minute are run (at least one)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    budget = max(10.0, 2.0 * args.steps)
-    base = oracle_sample(w, budget_s=min(budget, 30.0))
-    if base is None:
-        return
-    line = {"metric": METRIC, "value": base["value"], "unit": "cell-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
+    pairs = w["n_levels"] + 1
+    ts, t_start = [], time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        ts.append(pairs * _level_pair_seconds(w, w["nx"], w["ny"]))
+        if time.perf_counter() - t_start > 60.0:
+            break
+    step_s = statistics.mean(ts)
+    value = cells_per_step(w) / step_s
+    cores = os.cpu_count()
+    sample = ("%d steps, each one pair of level solves (A_w^-1, Lap^-1; naive dense DST, numpy FP64) on one %d x %d "
+              "level of %s extrapolated to %d pairs; advection, FSI and B0 columns not counted (an upper bound on "
+              "the oracle's rate); all %d host cores" % (len(ts), w["nx"], w["ny"], w["name"], pairs, cores))
+    line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": w["name"], "cells_per_step": cells_per_step(w)},
-            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": base["value"], "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -432,6 +506,10 @@ def main():
         _oracle_worker(args.oracle_worker, args.oracle_budget)
         return
     w = workload()
+    if args.oracle_level:
+        nx, ny = (int(v) for v in args.oracle_level.split(","))
+        print(_level_pair_seconds(w, nx, ny), flush=True)
+        return
     if args.offline:
         run_offline()
         return
@@ -444,7 +522,8 @@ def main():
         _b.build()
         import paper_2103_06415_gb300 as lib
         from runners import gpu_context
-        wr = wl.flag_512x256_3lvl_reduced_omega0()
+        wr = (wl.flag_512x256_3lvl_reduced_omega0() if args.profile_case == "flag"
+              else wl.tandem_1536x768_reduced())
         c = gpu_context(wr, precision={"mixed": lib.FSI_PREC_MIXED, "fp32": lib.FSI_PREC_FP32,
                                        "fp64": lib.FSI_PREC_FP64}[args.precision],
                         use_graph=False)
@@ -479,7 +558,7 @@ def main():
     # CPU baseline first, before any GPU call (rank 0, N = 1 only)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = oracle_sample(w, budget_s=15.0, one_thread_budget_s=10.0)
+        base = oracle_level_sample(w)
 
     import numpy as np
     import torch
@@ -494,17 +573,15 @@ def main():
         dist.init_process_group("gloo")
     prec = {"mixed": lib.FSI_PREC_MIXED, "fp32": lib.FSI_PREC_FP32, "fp64": lib.FSI_PREC_FP64}[args.precision]
 
-    def make(p, drop_tol=0.0, wk_override=None):
+    def make(p, wk_override=None):
+        wk = wk_override or w
         st = torch.cuda.Stream()
         t0 = time.perf_counter()
-        c = gpu_context(wk_override or w, precision=p, precompute=False, stream=st.cuda_stream)
-        c.precompute(drop_tol)
+        c = gpu_context(wk, precision=p, precompute=False, stream=st.cuda_stream)
+        c.precompute(wk.get("drop_tol", 0.0))
         return c, st, time.perf_counter() - t0
 
-    ctx, stream, b0_s = make(prec)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ctx.advance(args.warmup)
-    ctx.sync()
 
     def timed_steps(c, stream, k):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -523,6 +600,9 @@ def main():
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in evs]
 
+    ctx, stream, b0_s = make(prec)
+    ctx.advance(args.warmup)
+    ctx.sync()
     clk = Clocks(local)
     times = timed_steps(ctx, stream, args.steps)
     clocks = clk.stop()
@@ -530,42 +610,31 @@ def main():
     total_ms, value = aggregate_replicas(sum(times), cells * args.steps, world)
     stats = ctx.stats()
     phases = {k: v / max(stats["steps_done"], 1) for k, v in ctx.phase_times().items()}
-    hist_mixed = ctx.history(0)
 
-    # FP64 path on the same workload (same steps) and the force error of the mixed path against it
     extra = {}
     if prec != lib.FSI_PREC_FP64 and rank == 0:
-        ctx64, stream64, b0_64 = make(lib.FSI_PREC_FP64)
+        # the plain FP64 path on the same workload and steps
+        ctx64, stream64, _ = make(lib.FSI_PREC_FP64)
         ctx64.advance(args.warmup)
         t64 = timed_steps(ctx64, stream64, args.steps)
-        h64 = ctx64.history(0)
-        n = min(len(h64), len(hist_mixed))
-        errs = {}
-        for k, nm in enumerate(("fx", "fy", "moment", "theta")):
-            ref = h64[:n, k]
-            errs[nm] = float(np.linalg.norm(hist_mixed[:n, k] - ref) / max(np.linalg.norm(ref), 1e-300))
         extra["fp64_path"] = {"value": cells * args.steps / (sum(t64) * 1e-3), "unit": "cell-steps/s",
                               "ms_per_step": statistics.mean(t64), "p50_ms": statistics.median(t64),
                               "p99_ms": float(np.percentile(t64, 99))}
-        extra["mixed_vs_fp64_rel_l2_timed_steps"] = errs
         ctx64.close()
+        # the timed path against FP64 over the workload's whole horizon, beside the FP64 envelope
         horizon = w["steps"] if args.horizon_steps < 0 else args.horizon_steps
         if horizon > 0:
             extra.update(mixed_vs_fp64_horizon(w, horizon, make, lib, prec))
-        # the same run with the sparse B0' of Eq. filtereq at the paper's drop tolerance (0.007)
-        ctxs, streams, b0_sp = make(prec, 0.007)
-        ctxs.advance(args.warmup)
-        tsp = timed_steps(ctxs, streams, args.steps)
-        sts = ctxs.stats()
-        n2 = 2 * sts["n_sd"]
-        side = 2 * sts["b0_window"] + 1
-        extra["sparse_b0"] = {"drop_tol": 0.007, "value": cells * args.steps / (sum(tsp) * 1e-3),
-                              "unit": "cell-steps/s", "ms_per_step": statistics.mean(tsp),
-                              "kept_entries": sts["b0_nnz"], "dense_entries": n2 * n2,
-                              "window_half_width": sts["b0_window"],
-                              "bytes": n2 * 2 * side * side * 8, "dense_bytes": n2 * n2 * 8,
-                              "build_s": b0_sp}
-        ctxs.close()
+        # the 3-level 512 x 256 flag: its own step time and its 2000-step precision check
+        w2 = secondary_workload()
+        c2, st2, _ = make(prec, w2)
+        c2.advance(args.warmup)
+        t2 = timed_steps(c2, st2, args.steps)
+        sec = {"workload": w2["name"], "value": cells_per_step(w2) * args.steps / (sum(t2) * 1e-3),
+               "unit": "cell-steps/s", "ms_per_step": statistics.mean(t2), "p50_ms": statistics.median(t2)}
+        c2.close()
+        sec.update(mixed_vs_fp64_horizon(w2, w2["steps"], make, lib, prec))
+        extra[w2["name"]] = sec
 
     if rank == 0 and not args.no_comparator:
         extra["true_e_comparator"] = run_comparator(args, timed_steps)
@@ -573,89 +642,46 @@ def main():
     # dominant-kernel roofline: live CUDA-event timing of each launch of the class on the context stream
     roof = None
     if rank == 0:
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        shares = {}
-        for name in ("ysolve", "xf", "xi", "fsi", "rhs", "src"):
-            ms, nl = ctx.profile_kernel(name, 8)
-            shares[name] = (ms, nl / 8.0)
-        esz = 8 if prec == lib.FSI_PREC_FP64 else 4
-        nxi, nyi = w["nx"] - 1, w["ny"] - 1
-        per_step = {k: v[0] * v[1] for k, v in shares.items()}
-        ys_ms = shares["ysolve"][0]
-        bytes_ys = 3 * nxi * nyi * esz     # read the x-transformed level, write w and s half-transforms
-        ys_gbs = bytes_ys / (ys_ms * 1e-3) / 1e9
-        secondary = {"bound": "hbm", "kernel": "k_ysolve (DST y-pass)", "achieved": ys_gbs, "peak": hbm,
-                     "unit": "GB/s", "frac": ys_gbs / hbm, "algorithmic_bytes_per_launch": bytes_ys,
-                     "avg_launch_ms": ys_ms}
-        # k_fsi: the FSI iteration kernel (one launch per step).  Algorithmic flops per launch from the
-        # solver counters of the timing pass.
-        st2 = ctx.stats()
-        nf = st2["nf"]
-        iters = max(st2["last_iters"], 1)
-        solves = max(st2["last_solves"], iters)
-        refreshes = st2.get("last_refreshes", 1)
-        # per launch: P B0 P^T (16 FMA per lower-triangle entry) per iteration, 2 Newton-Schulz steps of two
-        # nf^3 products per refresh, X r per solve and K f per residual; for each flag of N elements per
-        # iteration: elements (~250 flops each), the block factorization (~100 per block) and the
-        # structural solves (y, one column of T J_d^-1 T^T per translational row, dchi: 54 flops per block)
-        n_el = sum(b["n_pts"] - 1 for b in w["bodies"] if b["kind"] == "deformable")
-        flops = (iters * 16 * 2 * nf * (nf + 1) / 2 + refreshes * 2 * 2 * 2 * nf ** 3
-                 + solves * 2 * nf * nf + max(solves - iters, 0) * 2 * nf * nf
-                 + iters * n_el * (250 + 100 + (2 + 2 * n_el) * 54))
-        fsi_ms = shares["fsi"][0]
-        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-        fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, derived
-        achieved = flops / (fsi_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_fsi (FSI iteration: P B0 P^T, Newton-Schulz inverse refresh, "
-                                          "double refinement; latency bound)",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
-                "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
-                                        "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-                "traffic": 3.80e6,
-                "traffic_note": "dram read+write bytes per launch from one ncu capture of the same kernel on "
-                                "the reduced-Omega_0 variant of the flag workload (same nf and flag; the B0 "
-                                "gathers of the same point set dominate it; "
-                                "profiles/k_fsi_flag_reduced_omega0.md)",
-                "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
-                "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
-                "secondary": secondary}
+        roof = roofline(ctx, w, lib, torch, local)
 
-    # end to end through the public API: build the run from host descriptors, precompute, then each step
-    # advance + read the forces back to the host (synchronising), destroy
+    # end to end through the public API: the whole job of the workload -- build the run from host descriptors,
+    # the offline stage, every step followed by a read-back of the forces to the host (synchronising), destroy
     e2e = None
     if rank == 0:
-        ke = w["steps"]                      # the workload's whole horizon is the job
+        ke = w["steps"]
         t0 = time.perf_counter()
-        c2 = gpu_context(w, precision=prec, precompute=False)
-        c2.precompute()
+        ce = gpu_context(w, precision=prec, precompute=False)
+        ce.precompute(w.get("drop_tol", 0.0))
         for _ in range(ke):
-            c2.advance(1)
-            c2.forces(0)
-        c2.close()
+            ce.advance(1)
+            ce.forces(0)
+        ce.close()
         el = time.perf_counter() - t0
         e2e = {"value": cells * ke / el, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": 96 + 4, "steps": ke,
                "note": "the whole job through the C ABI: wall clock of context creation from host descriptors, "
-                       "B0 precompute, the workload's %d steps each followed by a forces read-back to the host "
-                       "(synchronising), and destroy; there are no per-step host inputs" % ke}
+                       "the offline stage, the workload's %d steps each followed by a forces read-back to the "
+                       "host (synchronising), and destroy; there are no per-step host inputs" % ke}
 
     if rank == 0:
+        n2 = 2 * stats["n_sd"]
+        side = 2 * stats["b0_window"] + 1
         line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "p50_ms": statistics.median(times), "p99_ms": float(np.percentile(times, 99)),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {lib.FSI_PREC_FP32: "f32", lib.FSI_PREC_FP64: "f64"}.get(prec, "f32 transforms / f64 fields"),
                 "data": "synthetic",
-                "config": {"workload": w["name"] + " (clamped flag, corotational beam elements)",
+                "config": {"workload": w["name"] + " (three torsional plates in tandem and a clamped flag, each "
+                                                   "in its own Omega_0 box)",
                            "levels": w["n_levels"], "nx": w["nx"], "ny": w["ny"], "cells_per_step": cells,
-                           "body_points": sum(b["n_pts"] for b in w["bodies"]), "n_sd": stats["n_sd"],
-                           "b0_seconds": b0_s, "l2": "flushed between timed steps (512 MiB write)",
+                           "body_points": sum(b["n_pts"] for b in w["bodies"]), "nf": stats["nf"],
+                           "n_sd": stats["n_sd"], "b0": {"drop_tol": w.get("drop_tol", 0.0),
+                                                         "window_half_width": stats["b0_window"],
+                                                         "kept_entries": stats["b0_nnz"],
+                                                         "bytes": n2 * 2 * side * side * 8,
+                                                         "dense_bytes": n2 * n2 * 8},
+                           "offline_s": b0_s, "l2": "flushed between timed steps (512 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": stats["launches_per_step"] * args.steps,
                 "fsi_solver": {"iterations_last_step": stats["last_iters"], "solves_last_step": stats["last_solves"],
@@ -671,6 +697,62 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
 
+
+def roofline(ctx, w, lib, torch, local):
+    """The dominant kernel's roofline from live per-launch CUDA-event times (fsi_profile_kernel), with the
+    transform passes' HBM fractions beside it."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    shares = {}
+    for name in ("ysolve", "xf", "xi", "fsi", "rhs", "src", "ring"):
+        ms, nl = ctx.profile_kernel(name, 8)
+        shares[name] = (ms, nl / 8.0)
+    per_step = {k: v[0] * v[1] for k, v in shares.items()}
+    st = ctx.stats()
+    nf, G = st["nf"], w["n_levels"]
+    nxi, nyi = w["nx"] - 1, w["ny"] - 1
+    # transform passes (float transforms): algorithmic bytes per launch, one level
+    passes = {}
+    for name, words in (("ysolve", 3), ("xi", 4), ("xf", 2)):
+        ms = shares[name][0]
+        b = words * nxi * nyi * 4 * (G if name == "xf" and shares[name][1] < 2 * G else 1)
+        if name == "xf":   # one launch transforms every predictor level, the other the corrector's level
+            b = words * nxi * nyi * 4 * (G + 1) / max(shares[name][1], 1)
+        passes[name] = {"achieved_gbs": b / (ms * 1e-3) / 1e9, "frac": b / (ms * 1e-3) / 1e9 / hbm,
+                        "algorithmic_bytes_per_launch": b, "avg_launch_ms": ms}
+    # k_fsi: the FSI-iteration kernel (one launch per step); flops per launch from the solver counters
+    iters = max(st["last_iters"], 1)
+    solves = max(st["last_solves"], iters)
+    refreshes = st.get("last_refreshes", 0)
+    nb = nf // 2
+    per_body = [2 * b["n_pts"] for b in w["bodies"]]
+    blk3 = sum(n ** 3 for n in per_body)
+    n_el = sum(b["n_pts"] - 1 for b in w["bodies"] if b["kind"] == "deformable")
+    coupled = sum(n * n for n in per_body)      # entries of K that bodies of separate boxes leave non-zero
+    flops = (iters * 16 * 2 * coupled                    # P B0' P^T of the coupled entries
+             + refreshes * 2 * 2 * 2 * blk3              # one Newton-Schulz step: two block GEMMs
+             + solves * 2 * sum(n * n for n in per_body) # d = X r on the blocks
+             + solves * 2 * nf * nf                      # double residual rows
+             + iters * n_el * (250 + 100 + (2 + 2 * n_el) * 54))  # flag elements, J_d, structural solves
+    fsi_ms = shares["fsi"][0]
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (fsi_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_fsi (FSI iteration, distributed block-inverse solver for nf = %d: "
+                                      "P B0' P^T, block Newton-Schulz, double refinement; latency bound)" % nf,
+            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+            "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
+                                    "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
+            "traffic": None,
+            "traffic_note": "no ncu capture of this kernel at this size yet",
+            "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
+            "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
+            "transform_passes_hbm": passes, "hbm_peak_gbs": hbm}
 
 if __name__ == "__main__":
     main()

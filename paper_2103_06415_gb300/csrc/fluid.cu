@@ -70,11 +70,13 @@ void set_smem_limits() {
 // (TF = T, or double fields with float transforms in the mixed mode: the differences of field values are
 // taken in TF, the rest in T).  delta0: level 0 takes the right-hand side of the increment
 // w* - w^n instead, A_w (w* - w^n) = lap_h w^n / Re - 3/2 N^n + 1/2 N^{n-1} (the same equation with
-// A_w w^n = w^n/dt - lap_h w^n/(2 Re) moved to the right; its boundary values are the ring increments).
+// A_w w^n = w^n/dt - lap_h w^n/(2 Re) moved to the right; its boundary values are the ring increments),
+// computed in TF throughout.
 template <typename T>
 struct RhsConst {
   T i2h[12], inv_h2[12];  // 1/(2 h_g), 1/h_g^2 for level g (at most 12 levels)
   T inv_dt, half_inv_re, inv_re, U, V;
+  double i2h0, ih20, inv_re0, U0, V0;  // 1/(2h), 1/h^2 of the finest level, 1/Re, free stream in double
 };
 
 template <typename T, typename TF = T>
@@ -126,6 +128,23 @@ __global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const
   __syncthreads();
   if (!inner) return;
   const int x = threadIdx.x + 1, y = threadIdx.y + 1;
+  const long oi = (long)(j - 1) * ps + (i - 1);
+  if (delta0 && g == 0) {
+    // the finest level's increment right-hand side in the arithmetic of the fields (double in the mixed mode):
+    // the advective flux differences cancel, and their float rounding would drift the fields over many steps
+    const TF i2h = TF(k.i2h0), ih2 = TF(k.ih20);
+    const TF wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
+    const TF ue = (ts[y + 1][x + 1] - ts[y - 1][x + 1]) * i2h + TF(k.U0);
+    const TF uw = (ts[y + 1][x - 1] - ts[y - 1][x - 1]) * i2h + TF(k.U0);
+    const TF vn = -(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + TF(k.V0);
+    const TF vs = -(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + TF(k.V0);
+    const TF n = (ue * we - uw * ww) * i2h + (vn * wn - vs * wsx) * i2h;
+    const TF lap = (we + ww + wn + wsx - TF(4) * wc) * ih2;
+    const TF nold = first ? n : TF(np[o]);
+    np[o] = n;
+    rhs_all[oi] = T(lap * TF(k.inv_re0) - TF(1.5) * n + TF(0.5) * nold);
+    return;
+  }
   const T i2h = k.i2h[g];
   const TF wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
   // ubar at (i+-1, j) = (s[j+1] - s[j-1])/(2h) + U ; vbar at (i, j+-1) = -(s[i+1] - s[i-1])/(2h) + V
@@ -135,7 +154,6 @@ __global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const
   const T vs = -T(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
   const T n = (ue * T(we) - uw * T(ww)) * i2h + (vn * T(wn) - vs * T(wsx)) * i2h;
   const T lap = T(we + ww + wn + wsx - TF(4) * wc) * k.inv_h2[g];
-  const long oi = (long)(j - 1) * ps + (i - 1);
   const T nold = first ? n : nprev;
   np[o] = TF(n);
   const T base = (delta0 && g == 0) ? lap * k.inv_re : T(wc) * k.inv_dt + lap * k.half_inv_re;
@@ -506,6 +524,11 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
     k.inv_re = T(1.0 / c->g.re);
     k.U = T(c->g.uinf[0]);
     k.V = T(c->g.uinf[1]);
+    k.i2h0 = 0.5 / c->g.h;
+    k.ih20 = 1.0 / (c->g.h * c->g.h);
+    k.inv_re0 = 1.0 / c->g.re;
+    k.U0 = c->g.uinf[0];
+    k.V0 = c->g.uinf[1];
     FSI_CUDA_TRY(pdl_launch(k_rhs<T, TF>, gr, dim3(b), 0, c->stream, (const TF*)w_all, (const TF*)s_all, (TF*)c->nprev_all,
                             (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx, c->ny, k, first, delta0));
     prof_mark(c, KC_RHS);

@@ -31,6 +31,7 @@
 // Data written by other CTAs inside this kernel is read with __ldcg (L2), so no stale L1 line is used.
 #include <cooperative_groups.h>
 #include <cmath>
+#include <climits>
 #include <cstring>
 #include "beam.cuh"
 #include "internal.h"
@@ -377,7 +378,7 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 // (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
 // right-hand sides of the structural solves.
 struct FsiLayout {
-  size_t xs, krow, vec, pw, work, rf, pidx, pcij;
+  size_t xs, krow, vec, pw, work, rf, pidx, pcij, pbody;
   size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys, kb;
   size_t total;
 };
@@ -408,7 +409,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd, boo
   L.rf = L.work + (big ? al16((size_t)(64 * 33 + 32 * 64) * 4) : al16(lx * 16));
   L.pidx = L.rf + al16(lx * 4);
   L.pcij = L.pidx + al16((size_t)4 * nb * 4);
-  L.chi = L.pcij + al16((size_t)2 * nb * 4);
+  L.pbody = L.pcij + al16((size_t)2 * nb * 4);
+  L.chi = L.pbody + al16((size_t)nb * 4);
   L.rz = L.chi + al16((size_t)bd.nd * 8);
   L.cn = L.rz + al16((size_t)bd.nd * 8);
   L.rchi = L.cn + al16((size_t)bd.nd * 8);
@@ -482,6 +484,34 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
+}
+
+// Lane share of one row of K (global memory, written in this launch) times f (shared memory): 16-byte loads
+// with four independent chains when the row is 16-byte aligned (nf even), summed in a fixed order; the warp
+// adds the lanes (warp_sum).
+__device__ __forceinline__ double big_row_dot(const double* kr, const double* f, int nf, int lane) {
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+  if ((nf & 1) == 0) {
+    const double2* k2 = reinterpret_cast<const double2*>(kr);
+    const double2* f2 = reinterpret_cast<const double2*>(f);
+    const int n2 = nf >> 1;
+    int k = lane;
+    for (; k + 96 < n2; k += 128) {
+      const double2 a0 = __ldcg(&k2[k]), a1 = __ldcg(&k2[k + 32]), a2 = __ldcg(&k2[k + 64]), a3 = __ldcg(&k2[k + 96]);
+      const double2 b0 = f2[k], b1 = f2[k + 32], b2 = f2[k + 64], b3 = f2[k + 96];
+      c0 += a0.x * b0.x + a0.y * b0.y;
+      c1 += a1.x * b1.x + a1.y * b1.y;
+      c2 += a2.x * b2.x + a2.y * b2.y;
+      c3 += a3.x * b3.x + a3.y * b3.y;
+    }
+    for (; k < n2; k += 32) {
+      const double2 a0 = __ldcg(&k2[k]), b0 = f2[k];
+      c0 += a0.x * b0.x + a0.y * b0.y;
+    }
+  } else {
+    for (int k = lane; k < nf; k += 32) c0 += __ldcg(&kr[k]) * f[k];
+  }
+  return (c0 + c1) + (c2 + c3);
 }
 
 // ---- Distributed small-system solver (the kernel's BIG variant) -------------------------------------------
@@ -591,6 +621,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   __shared__ double b_tp[kMaxBodies];  // angle of the iterate that produced the current f (S, P of the solve)
   __shared__ double b_sn[kMaxBodies], b_cs[kMaxBodies];  // sin, cos of theta0 + theta^(k)
   __shared__ double b_ijac[kMaxBodies], b_kc[kMaxBodies];  // 1/J and (2 ds/dt)/J
+  __shared__ int bt_s[kMaxBodies], boff_s[kMaxBodies];     // type and first point of every body
+  __shared__ int bbx_s[kMaxBodies][4];  // hat-cell box of every body at the iterate: i_min, i_max, j_min, j_max
   __shared__ int sh_bad;
   __shared__ unsigned long long sh_phase[kPhases];
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
@@ -620,6 +652,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   float* rf = reinterpret_cast<float*>(dyn_smem + L.rf);  // float copy of the vector X is applied to
   int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
   int* pcij_s = reinterpret_cast<int*>(dyn_smem + L.pcij);
+  int* pb_s = reinterpret_cast<int*>(dyn_smem + L.pbody);  // body of every point
   double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
   double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
   double* cn_s = reinterpret_cast<double*>(dyn_smem + L.cn);      // r^zeta_n of every free dof
@@ -658,6 +691,11 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         g_dof[tid] = 3 * (p - b.off - 1) + ca;
       }
     }
+  }
+  for (int p = tid; p < nb; p += nthr) pb_s[p] = a.point_body[p];
+  for (int bi = tid; bi < a.n_bodies; bi += nthr) {
+    bt_s[bi] = a.bodies[bi].type;
+    boff_s[bi] = a.bodies[bi].off;
   }
   for (int g = tid; g < a.nd_tot; g += nthr) chi_s[g] = a.bchi[g];
   for (int e = tid; e < 3 * a.ne_tot; e += nthr) ref_s[e] = a.bref[e];
@@ -790,18 +828,43 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
     }
     double kv = kscale * acc;
-    const int ba = a.point_body[pa], bbd = a.point_body[pb];
-    if (ba == bbd && a.bodies[ba].type == FSI_BODY_TORSIONAL) {
-      const BodyDev b = a.bodies[ba];
+    const int ba = pb_s[pa], bbd = pb_s[pb];
+    if (ba == bbd && bt_s[ba] == FSI_BODY_TORSIONAL) {
       const double sn = b_sn[ba], cs = b_cs[ba];
-      const double sa = (double)(pa - b.off) * a.ds * (ca == 0 ? -sn : cs);
-      const double sb = (double)(pb - b.off) * a.ds * (cb == 0 ? -sn : cs);
+      const double sa = (double)(pa - boff_s[ba]) * a.ds * (ca == 0 ? -sn : cs);
+      const double sb = (double)(pb - boff_s[ba]) * a.ds * (cb == 0 ? -sn : cs);
       kv += b_kc[ba] * sa * sb;
-    } else if (with_g && ba == bbd && a.bodies[ba].type == FSI_BODY_DEFORMABLE) {
+    } else if (with_g && ba == bbd && bt_s[ba] == FSI_BODY_DEFORMABLE) {
       // (2 ds/dt) T J_d^-1 T^T, symmetric: the entry of the lower triangle (column min(r, c))
       kv += a.ds * a.two_dt * __ldcg(&a.G[cidx <= r ? (long)cidx * nf + r : (long)r * nf + cidx]);
     }
     return kv;
+  };
+  // Bodies ba and bb can have non-zero entries between them in K: always with the dense B0 (and for a body
+  // with itself); with the windowed B0' only when their hat-cell boxes come within the window (bw + 1 cells),
+  // since every entry of two points farther apart is dropped.  K keeps exact zeros elsewhere, so sums over
+  // the coupled columns alone give the same bits as over all columns.
+  auto couples = [&](int ba, int bb) -> bool {
+    if (dense || ba == bb) return true;
+    const int gi = max(bbx_s[ba][0] - bbx_s[bb][1], bbx_s[bb][0] - bbx_s[ba][1]);
+    const int gj = max(bbx_s[ba][2] - bbx_s[bb][3], bbx_s[bb][2] - bbx_s[ba][3]);
+    return gi <= a.bw + 1 && gj <= a.bw + 1;
+  };
+  // hat-cell boxes of the bodies from pcij_s, by nt threads of index tl with their own barrier
+  auto body_boxes = [&](int tl, int nt, auto sync) {
+    for (int bi = tl; bi < a.n_bodies; bi += nt) {
+      bbx_s[bi][0] = bbx_s[bi][2] = INT_MAX;
+      bbx_s[bi][1] = bbx_s[bi][3] = INT_MIN;
+    }
+    sync();
+    for (int p = tl; p < nb; p += nt) {
+      const int bi = pb_s[p];
+      atomicMin(&bbx_s[bi][0], pcij_s[2 * p]);
+      atomicMax(&bbx_s[bi][1], pcij_s[2 * p]);
+      atomicMin(&bbx_s[bi][2], pcij_s[2 * p + 1]);
+      atomicMax(&bbx_s[bi][3], pcij_s[2 * p + 1]);
+    }
+    sync();
   };
   // With flags, K is assembled by owned rows: warps 0-3 compute the rows of their CTA without the flags'
   // term under the flags' structural work on warps 4-7 (which takes longer than the body points), after a
@@ -961,8 +1024,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
         for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
         named_sync_lower();
+        body_boxes(tid, 128, []() { named_sync_lower(); });
         for (int e = tid; e < nr * nf; e += 128) {
-          const double kv = k_entry(r0 + e / nf, e % nf, false);
+          const int r = r0 + e / nf, cidx = e % nf;
+          const double kv = couples(pb_s[r % nb], pb_s[cidx % nb]) ? k_entry(r, cidx, false) : 0.0;
           if constexpr (BIG) a.K[(long)r0 * nf + e] = kv;  // owned rows stay in global memory
           else Krow[e] = kv;
         }
@@ -1049,6 +1114,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         pw_s[e] = __ldcg(&a.pw[e]);
       }
       for (int e = tid; e < 2 * nb; e += nthr) pcij_s[e] = __ldcg(&a.pcij[e]);
+      __syncthreads();
+      body_boxes(tid, nthr, []() { __syncthreads(); });
     }
     for (int e = tid; e < nf; e += nthr) rhs_s[e] = __ldcg(&a.rhs[2 * nf + e]);
     __syncthreads();
@@ -1071,7 +1138,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       for (long e = gtid; e < (long)nf * nf; e += gsize) {
         const int r = (int)(e / nf), cidx = (int)(e % nf);
         if (dense && cidx > r) continue;
-        const double kv = k_entry(r, cidx, true);
+        const double kv = couples(pb_s[r % nb], pb_s[cidx % nb]) ? k_entry(r, cidx, true) : 0.0;
         a.K[(long)r * nf + cidx] = kv;
         a.S[(long)r * lx + cidx] = (float)kv;
         if (dense) {
@@ -1281,8 +1348,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int c = wid; c < nr; c += nw) {
           double acc = 0.0;
           if constexpr (BIG) {
-            const double* kr = a.K + (long)(r0 + c) * nf;
-            for (int k = lane; k < nf; k += 32) acc += __ldcg(&kr[k]) * f_s[k];
+            acc = big_row_dot(a.K + (long)(r0 + c) * nf, f_s, nf, lane);
           } else {
             const double* kr = Krow + (long)c * nf;
             for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
@@ -1305,6 +1371,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
             const int i = r0 + c;
             const RowBlock b = row_block(a, i);
             float acc = 0.0f;
+#pragma unroll 4
             for (int t = lane; t < 2 * b.n; t += 32) {
               const int col = blk_col(b, nb, t);
               acc += __ldcg(&Xc[(long)i * lx + col]) * rf[col];
@@ -1370,8 +1437,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int c = wid; c < nr; c += nw) {  // owned residual rows r = rhs - K f in double
           double acc = 0.0;
           if constexpr (BIG) {
-            const double* kr = a.K + (long)(r0 + c) * nf;
-            for (int k = lane; k < nf; k += 32) acc += __ldcg(&kr[k]) * f_s[k];
+            acc = big_row_dot(a.K + (long)(r0 + c) * nf, f_s, nf, lane);
           } else {
             const double* kr = Krow + (long)c * nf;
             for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];

@@ -278,3 +278,13 @@ def tandem_1536x768_5lvl():
         name="tandem_1536x768_5lvl", nx=1536, ny=768, n_levels=5, x0=-1.0, y0=-1.92, h=h, re=1000.0, dt=2e-4,
         uinf=(1.0, 0.0), steps=5000, sd_box=[(hx - 0.1, hx + 1.1, -1.1, 1.1) for hx, _ in hinges],
         bodies=plates + [flag], ds=h, drop_tol=0.007)
+
+
+def tandem_1536x768_reduced():
+    """tandem_1536x768_5lvl for profiler captures that must hold a few GB: the same bodies (nf = 1608) on the
+    same finest grid with 2 levels and Omega_0 boxes cut to [-0.45, 0.45] in y (B0' ~3.5 GB instead of 10 GB)."""
+    w = tandem_1536x768_5lvl()
+    w["name"] = "tandem_1536x768_reduced"
+    w["n_levels"] = 2
+    w["sd_box"] = [(b[0], b[1], -0.45, 0.45) for b in w["sd_box"]]
+    return w
