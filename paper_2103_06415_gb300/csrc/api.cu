@@ -139,10 +139,13 @@ static fsi_status create_impl(fsi_ctx* c) {
   c->ldX = padded_stride(c->Nx);
   c->ring_ld = padded_stride(c->Nx > c->Ny ? c->Nx : c->Ny);
   const size_t E = c->esz;
-  const size_t lvl = (size_t)c->G * c->lvl_elems * E;
+  // the mixed mode keeps a second right-hand-side slot (and x-transform slot) per level: the defect of the
+  // level's streamfunction, transformed with the right-hand sides (fluid.cu)
+  const int slots = c->prec == FSI_PREC_MIXED ? 2 * c->G : c->G;
+  const size_t lvl = (size_t)slots * c->lvl_elems * E;
   const size_t flvl = (size_t)c->G * c->lvl_elems * c->fesz;
   if (!(c->w_all = ctx_alloc(c, flvl)) || !(c->s_all = ctx_alloc(c, flvl)) || !(c->nprev_all = ctx_alloc(c, flvl)) ||
-      !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)c->G * c->Nx * c->ldT * E)) ||
+      !(c->rhs_all = ctx_alloc(c, lvl)) || !(c->T1 = ctx_alloc(c, (size_t)slots * c->Nx * c->ldT * E)) ||
       !(c->T2w = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) || !(c->T2s = ctx_alloc(c, (size_t)c->Ny * c->ldX * E)) ||
       !(c->src = ctx_alloc(c, (size_t)c->lvl_elems * E)) || !(c->ring = ctx_alloc(c, (size_t)8 * c->ring_ld * E)))
     return FSI_ERR_OOM;
@@ -187,33 +190,6 @@ static fsi_status create_impl(fsi_ctx* c) {
     TRY(upload_twiddles<float>(c, 2 * c->Mx, &c->twx));
     TRY(upload_twiddles<float>(c, 2 * c->My, &c->twy));
   }
-  // ring-side pointer tables: per level [side0: wL wR sL sR | side1: wB wT sB sT]
-  std::vector<void*> srcs(8 * (size_t)c->G), dsts(8 * (size_t)c->G);
-  std::vector<long> es(8 * (size_t)c->G);
-  for (int l = 0; l < c->G; ++l) {
-    char* w = (char*)c->w_all + (size_t)l * c->lvl_elems * c->fesz;
-    char* s = (char*)c->s_all + (size_t)l * c->lvl_elems * c->fesz;
-    char* r = (char*)c->ring;
-    const long ps = c->ps;
-    void* side0[4] = {w + ps * E, w + (ps + c->nx) * E, s + ps * E, s + (ps + c->nx) * E};
-    void* side1[4] = {w + E, w + ((long)c->ny * ps + 1) * E, s + E, s + ((long)c->ny * ps + 1) * E};
-    const int d0[4] = {0, 1, 4, 5}, d1[4] = {2, 3, 6, 7};
-    for (int v = 0; v < 4; ++v) {
-      srcs[8 * l + v] = side0[v];
-      es[8 * l + v] = ps;
-      dsts[8 * l + v] = r + (size_t)d0[v] * c->ring_ld * E;
-      srcs[8 * l + 4 + v] = side1[v];
-      es[8 * l + 4 + v] = 1;
-      dsts[8 * l + 4 + v] = r + (size_t)d1[v] * c->ring_ld * E;
-    }
-  }
-  if (!(c->ring_src = (void**)ctx_alloc(c, srcs.size() * sizeof(void*))) ||
-      !(c->ring_dst = (void**)ctx_alloc(c, dsts.size() * sizeof(void*))) ||
-      !(c->ring_es = (long*)ctx_alloc(c, es.size() * sizeof(long))))
-    return FSI_ERR_OOM;
-  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_src, srcs.data(), srcs.size() * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
-  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_dst, dsts.data(), dsts.size() * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
-  FSI_CUDA_TRY(cudaMemcpyAsync(c->ring_es, es.data(), es.size() * sizeof(long), cudaMemcpyHostToDevice, c->stream));
   if (!(c->d_status = (int*)ctx_alloc(c, 64)) || !(c->d_ctrl = (int*)ctx_alloc(c, 64))) return FSI_ERR_OOM;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return FSI_OK;
@@ -939,7 +915,9 @@ extern "C" fsi_status fsi_get_field(fsi_ctx* c, int level, int which, double* ou
   std::vector<char> buf((size_t)c->lvl_elems * c->fesz);
   const char* base = (const char*)(which == 0 ? c->w_all : c->s_all) + (size_t)level * c->lvl_elems * c->fesz;
   FSI_CUDA_TRY(cudaMemcpy(buf.data(), base, buf.size(), cudaMemcpyDeviceToHost));
-  if (c->fesz == 8)
+  if (c->prec == FSI_PREC_MIXED)
+    to_double<f2s>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
+  else if (c->fesz == 8)
     to_double<double>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
   else
     to_double<float>(buf.data(), out, c->ny + 1, c->nx + 1, c->ps);
@@ -953,7 +931,9 @@ extern "C" fsi_status fsi_set_field(fsi_ctx* c, int level, int which, const doub
   for (long j = 0; j <= c->ny; ++j)
     for (long i = 0; i <= c->nx; ++i) {
       const double v = in[j * (c->nx + 1) + i];
-      if (c->fesz == 8)
+      if (c->prec == FSI_PREC_MIXED)
+        ((f2s*)buf.data())[j * c->ps + i] = f2s_from_double(v);
+      else if (c->fesz == 8)
         ((double*)buf.data())[j * c->ps + i] = v;
       else
         ((float*)buf.data())[j * c->ps + i] = (float)v;

@@ -158,8 +158,8 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     }
     {
       dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf), nc);
-      const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-#define YS(P, R) dst::k_ysolve<T, P, R><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, cy.logP, cy.nf, sp)
+      const size_t sm = dst::pass_smem<T>((size_t)2 * cy.nf * Ly, Ly);
+#define YS(P, R) dst::k_ysolve<T, P, R><<<grid, cy.nthr, sm, c->stream>>>(T1, c->ldT, t1, Nx, Ny, T2w, T2s, c->ldX, t2, twy, cy.logP, cy.nf, sp, (const T*)nullptr)
       COL_DISPATCH(cy, YS);
 #undef YS
     }

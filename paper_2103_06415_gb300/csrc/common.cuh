@@ -4,6 +4,64 @@
 #include <stdint.h>
 #include "../../include/ibfsi.h"
 
+
+// ---------------------------------------------------------------------------------------------
+// Float pair: a value held as the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2, 8 bytes like
+// a double (the level fields of the mixed mode).  Sums and differences use Knuth's error-free two-sum and
+// Dekker's fast two-sum (renormalisation) in float arithmetic only, so the difference of two nearby field
+// values is exact up to the final rounding of the difference itself, without FP64 instructions or
+// double-to-float conversions, both of which run at a small fraction of the FP32 rate on this GPU.
+struct __align__(8) f2s {
+  float hi, lo;
+  f2s() = default;
+  __host__ __device__ __forceinline__ f2s(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ explicit f2s(float v) : hi(v), lo(0.0f) {}
+  __host__ __device__ __forceinline__ explicit f2s(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// s + e = a + b exactly (Knuth's two-sum)
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// renormalise s + e with |e| small against |s| (Dekker's fast two-sum)
+__host__ __device__ __forceinline__ f2s f2s_norm(float s, float e) {
+  const float h = s + e;
+  return f2s(h, e - (h - s));
+}
+__host__ __device__ __forceinline__ f2s operator+(f2s a, f2s b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return f2s_norm(s, e + (a.lo + b.lo));
+}
+__host__ __device__ __forceinline__ f2s operator-(f2s a, f2s b) {
+  float s, e;
+  two_sum(a.hi, -b.hi, s, e);
+  return f2s_norm(s, e + (a.lo - b.lo));
+}
+// a * m for a float m: the product of hi exactly (fused multiply-add residual), the low part rounded
+__host__ __device__ __forceinline__ f2s f2s_scale(f2s a, float m) {
+  const float p = a.hi * m;
+  const float e = fmaf(a.hi, m, -p);
+  return f2s_norm(p, e + a.lo * m);
+}
+__host__ __device__ __forceinline__ f2s f2s_from_double(double v) {
+  const float h = (float)v;
+  return f2s(h, (float)(v - (double)h));
+}
+
+// Midpoint of two field values (ring values of a nested level)
+template <typename T>
+__host__ __device__ __forceinline__ T field_mid(T a, T b) { return T(0.5) * (a + b); }
+template <>
+__host__ __device__ __forceinline__ f2s field_mid<f2s>(f2s a, f2s b) {
+  const f2s s = a + b;
+  return f2s(0.5f * s.hi, 0.5f * s.lo);
+}
+
 template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };

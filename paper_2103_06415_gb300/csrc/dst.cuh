@@ -444,23 +444,27 @@ __device__ __forceinline__ YRow<T> y_row(const SpecParams<T>& sp, int k, int nro
 
 // Pass Y: rows k of `in` (x-frequency k+1; nrows = Nx rows of length N = Ny) -> DST along y -> diagonal
 // solve for w~ = (r^ + bc_w)/A_w and s~ = (w~ + bc_s)/lambda, both times norm -> DST along y (inverse) ->
-// transposed stores outw[j*out_ld + k], outs[j*out_ld + k].
-template <typename T, int PER, int R3 = 1>
+// transposed stores outw[j*out_ld + k], outs[j*out_ld + k].  DEF: rows of `inr` (x-transforms of a defect d,
+// same layout) are transformed beside `in` and enter the streamfunction only: s~ = (w~ + bc_s + d^)/lambda.
+template <typename T, int PER, int R3 = 1, bool DEF = false>
 __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                                 T* __restrict__ outw, T* __restrict__ outs, long out_ld,
                                                 long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
-                                                int nf, SpecParams<T> sp) {
+                                                int nf, SpecParams<T> sp, const T* __restrict__ inr) {
   using c2 = typename C2<T>::t;
   constexpr int NC = 2 * PER * R3;
+  constexpr int NB = DEF ? 2 : 1;  // forward transforms per row pair
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // [2 nf][L]: the forward transforms of the row pairs of `in` (buffers 0..nf-1) and `inr` (nf..2nf-1), replaced
+  // in place by the w~ (0..nf-1) and s~ (nf..2nf-1) spectra: a thread reads and writes the same frequencies
+  // l + 1 <= N and writes the mirrored ones L - 1 - l >= L - N, which no thread reads
   c2* buf = reinterpret_cast<c2*>(smem_raw);
   const int L = R3 << logL;
-  c2* buf2 = buf + (long)nf * L;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int row0 = blockIdx.x * 2 * nf;
   // constant tables (set up with the context): loaded before the wait for the predecessor
   TwiddleStage<T, 4 * PER * R3> ts;
-  ts.load(tw, L, (3 * (size_t)nf + 1) * L * sizeof(c2));
+  ts.load(tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
   T lyv[NC], sy1v[NC], syNv[NC];
 #pragma unroll
   for (int m = 0; m < NC; ++m) {
@@ -472,6 +476,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
   }
   pdl_enter();
   in += (long)blockIdx.y * in_bs;
+  if (DEF) inr += (long)blockIdx.y * in_bs;
   outw += (long)blockIdx.y * out_bs;
   outs += (long)blockIdx.y * out_bs;
   const T* ring = sp.ring;
@@ -488,26 +493,27 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
     }
   }
   YRow<T> rows0[2] = {y_row<T>(sp, row0 + 1, nrows), y_row<T>(sp, row0 + 2, nrows)};
-  zero_ends<T>(buf, nf, L);
-  zero_ends<T>(buf2, 2 * nf, L);
-  for (int f = 0; f < nf; ++f) {
+  zero_ends<T>(buf, NB * nf, L);
+  for (int q = 0; q < NB * nf; ++q) {  // rows of `in` into buffers 0..nf-1, rows of `inr` into nf..2nf-1
+    const int f = q < nf ? q : q - nf;
+    const T* src = q < nf ? in : inr;
     const int r0 = row0 + 2 * f;
     T a[NC], b[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int n = tid + m * nthr;
-      a[m] = (n < N && r0 < nrows) ? in[(long)r0 * in_ld + n] : T(0);
-      b[m] = (n < N && r0 + 1 < nrows) ? in[(long)(r0 + 1) * in_ld + n] : T(0);
+      a[m] = (n < N && r0 < nrows) ? src[(long)r0 * in_ld + n] : T(0);
+      b[m] = (n < N && r0 + 1 < nrows) ? src[(long)(r0 + 1) * in_ld + n] : T(0);
     }
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int n = tid + m * nthr;
-      if (n < N) put_pair<T>(buf + (long)f * L, L, n, a[m], b[m]);
+      if (n < N) put_pair<T>(buf + (long)q * L, L, n, a[m], b[m]);
     }
   }
-  const c2* tws = ts.store(buf + 3L * nf * L, tw, L);
+  const c2* tws = ts.store(buf + 2L * nf * L, tw, L);
   __syncthreads();
-  block_fft<T, PER, R3>(buf, L, logL, tws);
+  block_fft<T, NB * PER, R3>(buf, L, logL, tws);
   for (int f = 0; f < nf; ++f) {
     YRow<T> rw[2];
     if (f == 0) {
@@ -522,6 +528,8 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
       const int l0 = tid + m * nthr;
       if (l0 >= N) continue;
       const c2 z = buf[(long)f * L + l0 + 1];
+      c2 zd;
+      if (DEF) zd = buf[(long)(nf + f) * L + l0 + 1];
       T wv[2], sv[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -537,6 +545,7 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
             bcs *= sp.inv_h2;
           }
           const T wt = rh / aw;
+          if (DEF) bcs += e ? T(0.5) * zd.x : T(-0.5) * zd.y;
           const T st = (wt + bcs) / lam;
           wv[e] = wt * sp.norm;
           sv[e] = st * sp.norm;
@@ -547,12 +556,14 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
       }
       // the w~ rows of a pair share one complex transform (buffers 0..nf-1), the s~ rows another
       // (nf..2nf-1): s~ is smaller than w~ by ~1/lambda, so packing w~ with s~ would bury s~ in rounding.
-      put_pair<T>(buf2 + (long)f * L, L, l0, wv[0], wv[1]);
-      put_pair<T>(buf2 + (long)(nf + f) * L, L, l0, sv[0], sv[1]);
+      put_pair<T>(buf + (long)f * L, L, l0, wv[0], wv[1]);
+      put_pair<T>(buf + (long)(nf + f) * L, L, l0, sv[0], sv[1]);
     }
   }
   __syncthreads();
-  block_fft<T, 2 * PER, R3>(buf2, L, logL, tws);
+  zero_ends<T>(buf, 2 * nf, L);  // the forward transforms left rounding at frequencies 0 and L/2
+  __syncthreads();
+  block_fft<T, 2 * PER, R3>(buf, L, logL, tws);
   const int lognf = __ffs(nf) - 1;
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
@@ -561,8 +572,8 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
       const int f = idx & (nf - 1), j = idx >> lognf;
       const int row = row0 + 2 * f;
       const long o = (long)j * out_ld + row;
-      store_pair<T>(outw, o, row, nrows, buf2[(long)f * L + j + 1]);
-      store_pair<T>(outs, o, row, nrows, buf2[(long)(nf + f) * L + j + 1]);
+      store_pair<T>(outw, o, row, nrows, buf[(long)f * L + j + 1]);
+      store_pair<T>(outs, o, row, nrows, buf[(long)(nf + f) * L + j + 1]);
     }
   }
 }

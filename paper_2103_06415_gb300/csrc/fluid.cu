@@ -59,6 +59,12 @@ void set_smem_limits() {
   cudaFuncSetAttribute(dst::k_xi<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xf<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_ysolve<T, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if constexpr (std::is_same<T, float>::value) {
+    cudaFuncSetAttribute(dst::k_ysolve<T, 1, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(dst::k_ysolve<T, 2, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(dst::k_ysolve<T, 4, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(dst::k_ysolve<T, 1, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  }
   cudaFuncSetAttribute(dst::k_xi<T, 1, TF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
@@ -68,31 +74,36 @@ void set_smem_limits() {
 // tile of w and s with a one-vertex halo is staged in shared memory (each value read once from L2).
 // Per-level constants in the transform precision T (computed on the host).  The fields are of type TF
 // (TF = T, or double fields with float transforms in the mixed mode: the differences of field values are
-// taken in TF, the rest in T).  delta0: level 0 takes the right-hand side of the increment
-// w* - w^n instead, A_w (w* - w^n) = lap_h w^n / Re - 3/2 N^n + 1/2 N^{n-1} (the same equation with
-// A_w w^n = w^n/dt - lap_h w^n/(2 Re) moved to the right; its boundary values are the ring increments),
-// computed in TF throughout.
+// taken in TF, the rest in T).  delta: every level takes the right-hand side of the increment w* - w~^n
+// instead, A_w (w* - w~^n) = lap_h w~^n / Re - 3/2 N^n + 1/2 N^{n-1} (the same equation with
+// A_w w~^n = w~^n/dt - lap_h w~^n/(2 Re) moved to the right; its boundary values are the ring increments),
+// computed in TF throughout, where w~^n is the level's vorticity with the finer levels' values injected at
+// the vertices they cover.  The injected values are written into the level's own array, so that the
+// increment is added to w~^n, and the defect w~^n + lap_h s^n of the level's streamfunction goes to its
+// slot of `defect` (levels lvl apart).
 template <typename T>
 struct RhsConst {
   T i2h[12], inv_h2[12];  // 1/(2 h_g), 1/h_g^2 for level g (at most 12 levels)
   T inv_dt, half_inv_re, inv_re, U, V;
-  double i2h0, ih20, inv_re0, U0, V0;  // 1/(2h), 1/h^2 of the finest level, 1/Re, free stream in double
+  float ih2_hi[12], ih2_lo[12];  // 1/h_g^2 as a float pair, for the defect of the increment form
 };
 
 template <typename T, typename TF = T>
-__global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const TF* __restrict__ s_all,
-                                             TF* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps,
-                                             int nx, int ny, RhsConst<T> k, int first, int delta0) {
+__global__ void __launch_bounds__(256) k_rhs(TF* __restrict__ w_all, const TF* __restrict__ s_all,
+                                             T* __restrict__ np_all, T* __restrict__ rhs_all, long lvl, long ps,
+                                             int nx, int ny, RhsConst<T> k, int first, int delta,
+                                             T* __restrict__ defect) {
   pdl_enter();
   __shared__ TF tw[10][35], ts[10][35];
   const int g = blockIdx.z;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;  // tile vertex (i0 + 1, j0 + 1) at smem (1, 1)
   const TF* s = s_all + (long)g * lvl;
+  TF* w_own = w_all + (long)g * lvl;
   const int t = threadIdx.y * 32 + threadIdx.x;
   const int i = i0 + threadIdx.x + 1, j = j0 + threadIdx.y + 1;
   const bool inner = i < nx && j < ny;
   const long o = (long)j * ps + i;
-  TF* np = np_all + (long)g * lvl;
+  T* np = np_all + (long)g * lvl;
   // every global load of the thread is issued before any is consumed: N^{n-1} of its vertex and its (at
   // most two) elements of the 10 x 34 tile of w and s
   const T nprev = (inner && !first) ? T(np[o]) : T(0);
@@ -129,21 +140,42 @@ __global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const
   if (!inner) return;
   const int x = threadIdx.x + 1, y = threadIdx.y + 1;
   const long oi = (long)(j - 1) * ps + (i - 1);
-  if (delta0 && g == 0) {
-    // the finest level's increment right-hand side in the arithmetic of the fields (double in the mixed mode):
-    // the advective flux differences cancel, and their float rounding would drift the fields over many steps
-    const TF i2h = TF(k.i2h0), ih2 = TF(k.ih20);
-    const TF wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
-    const TF ue = (ts[y + 1][x + 1] - ts[y - 1][x + 1]) * i2h + TF(k.U0);
-    const TF uw = (ts[y + 1][x - 1] - ts[y - 1][x - 1]) * i2h + TF(k.U0);
-    const TF vn = -(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + TF(k.V0);
-    const TF vs = -(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + TF(k.V0);
-    const TF n = (ue * we - uw * ww) * i2h + (vn * wn - vs * wsx) * i2h;
-    const TF lap = (we + ww + wn + wsx - TF(4) * wc) * ih2;
-    const TF nold = first ? n : TF(np[o]);
-    np[o] = n;
-    rhs_all[oi] = T(lap * TF(k.inv_re0) - TF(1.5) * n + TF(0.5) * nold);
-    return;
+  if constexpr (std::is_same<TF, f2s>::value) {
+    if (delta) {
+      // The increment right-hand side: the differences of field values, which cancel, as exact float pairs,
+      // then rounded to float; the products and sums of those differences in float.  The flux differences are
+      // rewritten so that no product of two field values is differenced: ue we - uw ww = ue (we - wc) -
+      // uw (ww - wc) + (ue - uw) wc, with ue - uw a second difference of s summed in pairs.
+      const T i2h = k.i2h[g], ih2 = k.inv_h2[g];
+      const TF wc = tw[y][x];
+      const TF dwe = tw[y][x + 1] - wc, dww = tw[y][x - 1] - wc, dwn = tw[y + 1][x] - wc, dws = tw[y - 1][x] - wc;
+      const TF lapd = (dwe + dww) + (dwn + dws);
+      const TF sne = ts[y + 1][x + 1], sse = ts[y - 1][x + 1], snw = ts[y + 1][x - 1], ssw = ts[y - 1][x - 1];
+      const TF dse = sne - sse, dsw = snw - ssw, dsn = sne - snw, dss = sse - ssw;
+      const T ue = T(dse) * i2h + k.U, uw = T(dsw) * i2h + k.U;
+      const T vn = -T(dsn) * i2h + k.V, vs = -T(dss) * i2h + k.V;
+      const T du = T(dse - dsw) * i2h, dv = -T(dsn - dss) * i2h;  // ue - uw, vn - vs
+      const T wcf = T(wc);
+      const T fx = ue * T(dwe) - uw * T(dww) + du * wcf;
+      const T fy = vn * T(dwn) - vs * T(dws) + dv * wcf;
+      const T n = (fx + fy) * i2h;
+      const T nold = first ? n : np[o];
+      np[o] = n;
+      const long og = (long)g * lvl;
+      rhs_all[og + oi] = T(lapd) * ih2 * k.inv_re - T(1.5) * n + T(0.5) * nold;
+      // defect of the streamfunction (a small difference, in pairs, with 1/h^2 as a pair): the increment of s
+      // solves -lap_h ds = dw + defect, so s* satisfies -lap_h s* = w* to the rounding of the increment (the
+      // rounding of earlier float transforms left in s is removed at every step instead of accumulating)
+      const TF sc = ts[y][x];
+      const TF laps = ((ts[y][x + 1] - sc) + (ts[y][x - 1] - sc)) + ((ts[y + 1][x] - sc) + (ts[y - 1][x] - sc));
+      const float p = laps.hi * k.ih2_hi[g];
+      const TF lap_s = f2s_norm(p, fmaf(laps.hi, k.ih2_hi[g], -p) + (laps.hi * k.ih2_lo[g] + laps.lo * k.ih2_hi[g]));
+      defect[og + oi] = T(wc + lap_s);
+      // w~^n into the level's array at a covered vertex (no launch reads a level's covered vertices: they
+      // are always taken from the finest level that contains them)
+      if (g > 0 && abs(2 * i - nx) < nx / 2 && abs(2 * j - ny) < ny / 2) w_own[o] = wc;
+      return;
+    }
   }
   const T i2h = k.i2h[g];
   const TF wc = tw[y][x], we = tw[y][x + 1], ww = tw[y][x - 1], wn = tw[y + 1][x], wsx = tw[y - 1][x];
@@ -153,10 +185,14 @@ __global__ void __launch_bounds__(256) k_rhs(const TF* __restrict__ w_all, const
   const T vn = -T(ts[y + 1][x + 1] - ts[y + 1][x - 1]) * i2h + k.V;
   const T vs = -T(ts[y - 1][x + 1] - ts[y - 1][x - 1]) * i2h + k.V;
   const T n = (ue * T(we) - uw * T(ww)) * i2h + (vn * T(wn) - vs * T(wsx)) * i2h;
-  const T lap = T(we + ww + wn + wsx - TF(4) * wc) * k.inv_h2[g];
+  T lap;
+  if constexpr (std::is_same<TF, f2s>::value)
+    lap = T(((we - wc) + (ww - wc)) + ((wn - wc) + (wsx - wc))) * k.inv_h2[g];
+  else
+    lap = T(we + ww + wn + wsx - TF(4) * wc) * k.inv_h2[g];
   const T nold = first ? n : nprev;
-  np[o] = TF(n);
-  const T base = (delta0 && g == 0) ? lap * k.inv_re : T(wc) * k.inv_dt + lap * k.half_inv_re;
+  np[o] = n;
+  const T base = T(wc) * k.inv_dt + lap * k.half_inv_re;
   rhs_all[(long)g * lvl + oi] = base - T(1.5) * n + T(0.5) * nold;
 }
 
@@ -171,7 +207,7 @@ __device__ __forceinline__ T ring_value(const T* __restrict__ c, long ps, int nx
   const int a = i + nx / 2, b = j + ny / 2;
   const int I0 = a >> 1, J0 = b >> 1;
   const int I1 = I0 + (a & 1), J1 = J0 + (b & 1);
-  return T(0.5) * (c[(long)J0 * ps + I0] + c[(long)J1 * ps + I1]);
+  return field_mid(c[(long)J0 * ps + I0], c[(long)J1 * ps + I1]);
 }
 
 // delta: the spectra are those of the ring increments (new value minus the fine level's current one; the
@@ -277,17 +313,21 @@ __device__ __forceinline__ T v_face(const T* vt, int ci, int cj, int fi, int fj)
 
 // Thread per vertex over tiles of 32 x 4 vertices covering the Omega_0 box grown by 3 cells.  Vertices
 // outside the box written by the FSI kernel (ctrl[8..11]) are set to zero.  A tile that meets the box
-// keeps, in point order, the points whose face support can reach it, with their face tables.
-template <typename T>
+// walks the points in chunks of kSrcChunk and keeps, in point order, those whose face support can reach
+// it, with their face tables.  The face values and the curl are taken in TS and stored in T: along a plate
+// the normal stress is smooth, so the curl is a small difference of large face values (about h / chord of
+// them), and the mixed mode takes it in double so that only the transform of the source is in float.
+constexpr int kSrcChunk = 256;
+
+template <typename T, typename TS = T>
 __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int nx, int ny, const int* __restrict__ pidx,
                                              const int* __restrict__ pcij,
                                              const double* __restrict__ pw, const double* __restrict__ f, int nb, int ni,
                                              int i_lo, int i_hi, int j_lo, int j_hi, const int* __restrict__ box,
-                                             T coef, int n_box) {
+                                             TS coef, int n_box) {
   pdl_enter();
-  extern __shared__ __align__(16) unsigned char src_smem[];
-  T* tab = reinterpret_cast<T*>(src_smem);                  // [nb][16]: ut (8) then vt (8)
-  SrcPoint* pt = reinterpret_cast<SrcPoint*>(tab + 16 * nb);  // [nb]
+  __shared__ TS tab[kSrcChunk * 16];  // [chunk point][16]: ut (8) then vt (8)
+  __shared__ SrcPoint pt[kSrcChunk];
   __shared__ int wcount[4], n_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ti0 = i_lo - 3 + blockIdx.x * 32, tj0 = j_lo - 3 + blockIdx.y * 4;
@@ -298,57 +338,63 @@ __global__ void __launch_bounds__(128) k_src(T* __restrict__ src, long ps, int n
   const bool inside = i >= bi0 && i <= bi1 && j >= bj0 && j <= bj1;
   if (valid && !inside) src[(long)(j - 1) * ps + (i - 1)] = T(0);
   if (!tile_hits) return;
-  // select (in point order) the points whose faces enter the curl at some vertex of this tile: vertex
-  // offsets i - ci and j - cj in -1..2
-  if (tid == 0) n_sel = 0;
-  __syncthreads();
-  for (int base = 0; base < nb; base += 128) {
-    const int p = base + tid;
-    int ci = 0, cj = 0;
-    bool take = false;
-    if (p < nb) {
-      const int n0 = pidx[4 * p];
-      ci = pcij[2 * p] + i_lo;  // hat cell in the (bounding) box, as grid vertex indices
-      cj = pcij[2 * p + 1] + j_lo;
-      take = n0 < n_box && ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;  // appended: elsewhere
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (lane == 0) wcount[wid] = __popc(m);
+  TS fve = 0, fvw = 0, fun = 0, fus = 0;
+  for (int c0 = 0; c0 < nb; c0 += kSrcChunk) {
+    const int c1 = c0 + kSrcChunk < nb ? c0 + kSrcChunk : nb;
+    // select the chunk's points whose faces enter the curl at some vertex of this tile: vertex offsets
+    // i - ci and j - cj in -1..2
+    if (tid == 0) n_sel = 0;
     __syncthreads();
-    int off = n_sel;
-    for (int w = 0; w < wid; ++w) off += wcount[w];
-    if (take) {
-      const int q = off + __popc(m & ((1u << lane) - 1u));
-      pt[q].ci = ci;
-      pt[q].cj = cj;
-      const T w00 = T(pw[4 * p]), w10 = T(pw[4 * p + 1]), w01 = T(pw[4 * p + 2]), w11 = T(pw[4 * p + 3]);
-      const T fx = T(0.5) * T(f[p]), fy = T(0.5) * T(f[nb + p]);
-      T* t = tab + 16 * q;
-      for (int d = -1; d <= 2; ++d) {
-        t[0 * 4 + d + 1] = (w00 * wx3t<T>(d) + w10 * wx3t<T>(d - 1)) * fx;  // U_0(d)
-        t[1 * 4 + d + 1] = (w01 * wx3t<T>(d) + w11 * wx3t<T>(d - 1)) * fx;  // U_1(d)
-        t[8 + 0 * 4 + d + 1] = (w00 * wx3t<T>(d) + w01 * wx3t<T>(d - 1)) * fy;  // V_0(e = d)
-        t[8 + 1 * 4 + d + 1] = (w10 * wx3t<T>(d) + w11 * wx3t<T>(d - 1)) * fy;  // V_1(e = d)
+    for (int base = c0; base < c1; base += 128) {
+      const int p = base + tid;
+      int ci = 0, cj = 0;
+      bool take = false;
+      if (p < c1) {
+        const int n0 = pidx[4 * p];
+        ci = pcij[2 * p] + i_lo;  // hat cell in the (bounding) box, as grid vertex indices
+        cj = pcij[2 * p + 1] + j_lo;
+        take = n0 < n_box && ci - 1 <= ti0 + 31 && ci + 2 >= ti0 && cj - 1 <= tj0 + 3 && cj + 2 >= tj0;  // appended: elsewhere
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      if (lane == 0) wcount[wid] = __popc(m);
+      __syncthreads();
+      int off = n_sel;
+      for (int w = 0; w < wid; ++w) off += wcount[w];
+      if (take) {
+        const int q = off + __popc(m & ((1u << lane) - 1u));
+        pt[q].ci = ci;
+        pt[q].cj = cj;
+        const TS w00 = TS(pw[4 * p]), w10 = TS(pw[4 * p + 1]), w01 = TS(pw[4 * p + 2]), w11 = TS(pw[4 * p + 3]);
+        const TS fx = TS(0.5) * TS(f[p]), fy = TS(0.5) * TS(f[nb + p]);
+        TS* t = tab + 16 * q;
+        for (int d = -1; d <= 2; ++d) {
+          t[0 * 4 + d + 1] = (w00 * wx3t<TS>(d) + w10 * wx3t<TS>(d - 1)) * fx;  // U_0(d)
+          t[1 * 4 + d + 1] = (w01 * wx3t<TS>(d) + w11 * wx3t<TS>(d - 1)) * fx;  // U_1(d)
+          t[8 + 0 * 4 + d + 1] = (w00 * wx3t<TS>(d) + w01 * wx3t<TS>(d - 1)) * fy;  // V_0(e = d)
+          t[8 + 1 * 4 + d + 1] = (w10 * wx3t<TS>(d) + w11 * wx3t<TS>(d - 1)) * fy;  // V_1(e = d)
+        }
+      }
+      __syncthreads();
+      if (tid == 0) n_sel += wcount[0] + wcount[1] + wcount[2] + wcount[3];
+      __syncthreads();
+    }
+    const int ns = n_sel;
+    if (valid && inside) {
+      for (int q = 0; q < ns; ++q) {
+        const int ci = pt[q].ci, cj = pt[q].cj;
+        if (i < ci - 1 || i > ci + 2 || j < cj - 1 || j > cj + 2) continue;
+        const TS* t = tab + 16 * q;
+        fun += u_face<TS>(t, ci, cj, i, j);
+        fus += u_face<TS>(t, ci, cj, i, j - 1);
+        fve += v_face<TS>(t + 8, ci, cj, i, j);
+        fvw += v_face<TS>(t + 8, ci, cj, i - 1, j);
       }
     }
-    __syncthreads();
-    if (tid == 0) n_sel += wcount[0] + wcount[1] + wcount[2] + wcount[3];
-    __syncthreads();
+    __syncthreads();  // the next chunk overwrites the tables
   }
   if (!valid || !inside) return;
-  T fve = 0, fvw = 0, fun = 0, fus = 0;
-  const int ns = n_sel;
-  for (int q = 0; q < ns; ++q) {
-    const int ci = pt[q].ci, cj = pt[q].cj;
-    if (i < ci - 1 || i > ci + 2 || j < cj - 1 || j > cj + 2) continue;
-    const T* t = tab + 16 * q;
-    fun += u_face<T>(t, ci, cj, i, j);
-    fus += u_face<T>(t, ci, cj, i, j - 1);
-    fve += v_face<T>(t + 8, ci, cj, i, j);
-    fvw += v_face<T>(t + 8, ci, cj, i - 1, j);
-  }
   // curl at (i,j): (Fv(i+1/2,j) - Fv(i-1/2,j))/h - (Fu(i,j+1/2) - Fu(i,j-1/2))/h
-  src[(long)(j - 1) * ps + (i - 1)] = coef * ((fve - fvw) - (fun - fus));
+  src[(long)(j - 1) * ps + (i - 1)] = T(coef * ((fve - fvw) - (fun - fus)));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -385,9 +431,10 @@ fsi_status xf_pass(fsi_ctx* c, const T* rhs, int nlev) {
   return FSI_OK;
 }
 
-// Pass Y of level g (spacing h 2^g) from the x-transforms at t1, with the ring spectra when use_ring.
+// Pass Y of level g (spacing h 2^g) from the x-transforms at t1, with the ring spectra when use_ring, and
+// the x-transforms t1r of the streamfunction defect when not null (float transforms only).
 template <typename T>
-fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
+fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring, const T* t1r = nullptr) {
   using c2 = typename C2<T>::t;
   set_smem_limits<T>();
   const FftCfg cy = fft_cfg(c->logPy, c->r3y);
@@ -404,10 +451,21 @@ fsi_status y_pass(fsi_ctx* c, int g, const T* t1, int use_ring) {
     }
   } else {
     dim3 grid((c->Nx + 2 * cy.nf - 1) / (2 * cy.nf), 1);
-    const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-#define Y_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, P, R>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, cy.logP, cy.nf, sp))
-    FFT_DISPATCH(cy, Y_LAUNCH);
+    if (t1r) {
+      if constexpr (std::is_same<T, float>::value) {
+        const size_t sm = dst::pass_smem<T>((size_t)2 * cy.nf * Ly, Ly);
+#define Y_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, P, R, true>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, cy.logP, cy.nf, sp, t1r))
+        FFT_DISPATCH(cy, Y_LAUNCH);
 #undef Y_LAUNCH
+      } else {
+        return FSI_ERR_UNSUPPORTED;
+      }
+    } else {
+      const size_t sm = dst::pass_smem<T>((size_t)2 * cy.nf * Ly, Ly);
+#define Y_LAUNCH(P, R) FSI_CUDA_TRY(pdl_launch(dst::k_ysolve<T, P, R>, grid, dim3(cy.nthr), sm, c->stream, t1, c->ldT, 0, c->Nx, c->Ny, (T*)c->T2w, (T*)c->T2s, c->ldX, 0, twy, cy.logP, cy.nf, sp, (const T*)nullptr))
+      FFT_DISPATCH(cy, Y_LAUNCH);
+#undef Y_LAUNCH
+    }
   }
   prof_mark(c, KC_YSOLVE);
   c->launches_per_step += 1;
@@ -497,18 +555,24 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g, int delta) {
   return FSI_OK;
 }
 
-// Predictor of every level, coarse to fine.  In the mixed mode (double fields, float transforms) the finest
-// level is advanced in increment form after the first step: its right-hand side, ring spectra and inverse
-// transforms are those of w* - w^n and s* - s^n, added to the double fields, so the float transforms carry
-// errors relative to the increments (O(dt) smaller than the fields) and the fields keep double precision.
-// The increment of s solves -lap_h (s* - s^n) = w* - w^n, which holds because -lap_h s^n = w^n at the end of
-// every step (the first step, and any step after fields were set, takes the full form).  Coarser levels
-// take the full form: their solutions reach the finest level only through its ring values, smoothly.
+// Predictor of every level, coarse to fine.  In the mixed mode (double fields, float transforms) every level
+// is advanced in increment form after the first step: its right-hand side, ring spectra and inverse
+// transforms are those of w* - w~^n and s* - s^n, added to the double fields, so the float transforms carry
+// errors relative to the increments (O(dt) smaller than the fields) and the fields keep double precision
+// (in the full form the float rounding of w^n/dt, which dominates the right-hand side, would accumulate in
+// the coarse levels' vorticity step after step).  The increment of s solves
+// -lap_h (s* - s^n) = w* - w~^n + (w~^n + lap_h s^n): the defect term is zero for the finest level in exact
+// arithmetic and equals the injection's change of w on a coarser one; carrying it makes s* satisfy
+// -lap_h s* = w* to float rounding of the increment, so the white rounding noise of earlier float
+// transforms does not stay in s (differentiated for the body-point velocities it would be amplified by the
+// inverse of the small system).  The first step, and any step after fields were set, takes the full form.
 template <typename T, typename TF = T>
 fsi_status predictor_t(fsi_ctx* c, int first) {
   TF* w_all = (TF*)c->w_all;
   TF* s_all = (TF*)c->s_all;
-  const int delta0 = (!std::is_same<T, TF>::value && !first) ? 1 : 0;
+  const int delta = (!std::is_same<T, TF>::value && !first) ? 1 : 0;
+  // the streamfunction defects of the levels sit in the right-hand-side slots after the last level
+  T* defect = delta ? (T*)c->rhs_all + (long)c->G * c->lvl_elems : nullptr;
   {
     dim3 b(32, 8), gr((c->Nx + 31) / 32, (c->Ny + 7) / 8, c->G);
     c->launches_per_step += 1;
@@ -518,33 +582,32 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
       const double hg = c->g.h * (double)(1 << g);
       k.i2h[g] = T(0.5 / hg);
       k.inv_h2[g] = T(1.0 / (hg * hg));
+      const f2s ih2 = f2s_from_double(1.0 / (hg * hg));
+      k.ih2_hi[g] = ih2.hi;
+      k.ih2_lo[g] = ih2.lo;
     }
     k.inv_dt = T(1.0 / c->g.dt);
     k.half_inv_re = T(0.5 / c->g.re);
     k.inv_re = T(1.0 / c->g.re);
     k.U = T(c->g.uinf[0]);
     k.V = T(c->g.uinf[1]);
-    k.i2h0 = 0.5 / c->g.h;
-    k.ih20 = 1.0 / (c->g.h * c->g.h);
-    k.inv_re0 = 1.0 / c->g.re;
-    k.U0 = c->g.uinf[0];
-    k.V0 = c->g.uinf[1];
-    FSI_CUDA_TRY(pdl_launch(k_rhs<T, TF>, gr, dim3(b), 0, c->stream, (const TF*)w_all, (const TF*)s_all, (TF*)c->nprev_all,
-                            (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx, c->ny, k, first, delta0));
+    FSI_CUDA_TRY(pdl_launch(k_rhs<T, TF>, gr, dim3(b), 0, c->stream, w_all, (const TF*)s_all, (T*)c->nprev_all,
+                            (T*)c->rhs_all, c->lvl_elems, c->ps, c->nx, c->ny, k, first, delta, defect));
     prof_mark(c, KC_RHS);
   }
   FSI_CUDA_TRY(cudaGetLastError());
   // The x-transforms need only each level's own right-hand side (the coarser level's solution enters
   // through the ring terms of pass Y), so the FFT path takes all levels in one launch, each into its own
   // scratch slot; the chain of dependent launches per step is two shorter for three levels.
-  const bool batch = c->G > 1 && !use_gemm<T>(c, 0) && !use_gemm<T>(c, 1);
+  const bool batch = (c->G > 1 || delta) && !use_gemm<T>(c, 0) && !use_gemm<T>(c, 1);
+  if (delta && !batch) return FSI_ERR_UNSUPPORTED;  // the increment form runs on the FFT passes
   if (batch) {
-    const fsi_status st = xf_pass<T>(c, (const T*)c->rhs_all, c->G);
+    const fsi_status st = xf_pass<T>(c, (const T*)c->rhs_all, delta ? 2 * c->G : c->G);
     if (st != FSI_OK) return st;
   }
   for (int g = c->G - 1; g >= 0; --g) {
     const int ring = g < c->G - 1;
-    const int inc = delta0 && g == 0;
+    const int inc = delta;
     if (ring) {
       fsi_status st = ring_spectra_t<T, TF>(c, g, inc);
       if (st != FSI_OK) return st;
@@ -553,7 +616,8 @@ fsi_status predictor_t(fsi_ctx* c, int first) {
     TF* sg = s_all + (long)g * c->lvl_elems;
     fsi_status st;
     if (batch) {
-      st = y_pass<T>(c, g, (const T*)c->T1 + (long)g * c->Nx * c->ldT, ring);
+      st = y_pass<T>(c, g, (const T*)c->T1 + (long)g * c->Nx * c->ldT, ring,
+                     inc ? (const T*)c->T1 + (long)(c->G + g) * c->Nx * c->ldT : nullptr);
       if (st == FSI_OK) st = xi_pass<T, TF>(c, wg, sg, inc ? 2 : 0);
     } else {
       st = level_solve_t<T, TF>(c, g, (const T*)c->rhs_all + (long)g * c->lvl_elems, wg, sg, ring, inc ? 2 : 0);
@@ -568,15 +632,11 @@ fsi_status corrector_t(fsi_ctx* c) {
   const int wi = c->ni + 6, wj = c->nj + 6;
   dim3 gr((wi + 31) / 32, (wj + 3) / 4);
   const double scale = c->ds / (c->g.h * c->g.h);
-  const size_t sm = (size_t)c->nb * (16 * sizeof(T) + sizeof(SrcPoint));
-  static bool attr = false;  // per instantiation
-  if (!attr) {
-    attr = true;
-    cudaFuncSetAttribute(k_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  }
   prof_mark(c, KC_SRC);
-  FSI_CUDA_TRY(pdl_launch(k_src<T>, gr, dim3(128), sm, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pcij, c->d_pw, c->d_f, c->nb, c->ni,
-                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, T(scale / c->g.h), c->n_box));
+  // the curl of the spread stress in double whenever the fields carry more than float precision
+  using TS = typename std::conditional<std::is_same<TF, f2s>::value, double, TF>::type;
+  FSI_CUDA_TRY(pdl_launch(k_src<T, TS>, gr, dim3(128), 0, c->stream, (T*)c->src, c->ps, c->nx, c->ny, c->d_pidx, c->d_pcij, c->d_pw, c->d_f, c->nb, c->ni,
+                                      c->i_lo, c->i_hi, c->j_lo, c->j_hi, c->d_ctrl + 8, TS(scale / c->g.h), c->n_box));
   prof_mark(c, KC_SRC);
   c->launches_per_step += 1;
   FSI_CUDA_TRY(cudaGetLastError());
@@ -596,12 +656,12 @@ fsi_status launch_level_solve(fsi_ctx* c, int g, const void* rhs, void* w, void*
 
 fsi_status launch_predictor(fsi_ctx* c, int first) {
   if (c->prec == FSI_PREC_FP64) return predictor_t<double>(c, first);
-  if (c->prec == FSI_PREC_MIXED) return predictor_t<float, double>(c, first);
+  if (c->prec == FSI_PREC_MIXED) return predictor_t<float, f2s>(c, first);
   return predictor_t<float>(c, first);
 }
 
 fsi_status launch_corrector(fsi_ctx* c) {
   if (c->prec == FSI_PREC_FP64) return corrector_t<double>(c);
-  if (c->prec == FSI_PREC_MIXED) return corrector_t<float, double>(c);
+  if (c->prec == FSI_PREC_MIXED) return corrector_t<float, f2s>(c);
   return corrector_t<float>(c);
 }

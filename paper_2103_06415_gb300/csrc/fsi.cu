@@ -121,7 +121,9 @@ struct FsiArgs {
   double* rsum;
 };
 
+// level-0 streamfunction at vertex offset o: fp64 = 0 float, 1 double, 2 float pair (the mixed mode)
 __device__ __forceinline__ double load_s(const FsiArgs& a, long o) {
+  if (a.fp64 == 2) return (double)((const f2s*)a.s0)[o];
   return a.fp64 ? ((const double*)a.s0)[o] : (double)((const float*)a.s0)[o];
 }
 
@@ -1698,7 +1700,7 @@ int fsi_min_grid(int nf, bool big) { return big ? (nf + kMaxRB - 1) / kMaxRB : (
 fsi_status launch_fsi(fsi_ctx* c) {
   FsiArgs a;
   a.s0 = c->s_all;
-  a.fp64 = c->fesz == 8;  // the level fields (double in the FP64 and mixed modes)
+  a.fp64 = c->prec == FSI_PREC_MIXED ? 2 : (c->fesz == 8 ? 1 : 0);  // type of the level fields
   a.ps = c->ps;
   a.x0 = c->g.x0;
   a.y0 = c->g.y0;

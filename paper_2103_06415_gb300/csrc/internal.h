@@ -104,7 +104,7 @@ struct fsi_ctx {
   fsi_exec_desc x;
   int prec;  // FSI_PREC_*
   size_t esz;   // bytes per element of the transform buffers, right-hand sides and spectral tables
-  size_t fesz;  // bytes per element of the level fields w, s and the previous advection term
+  size_t fesz;  // bytes per element of the level fields w, s (float, double, or a float pair in the mixed mode)
   cudaStream_t stream;
   int G, nx, ny, Nx, Ny, Mx, My;
   int logPx, logPy, r3x, r3y;  // transform lengths 2 nx = r3x 2^logPx, 2 ny = r3y 2^logPy (r3 = 1 or 3)
@@ -120,9 +120,6 @@ struct fsi_ctx {
   double *lx, *ly, *sx1, *sxN, *sy1, *syN;
   void *lxT, *lyT, *sx1T, *sxNT, *sy1T, *syNT;  // the same tables in the context precision
   void *twx, *twy;  // complex twiddles in precision prec (length Lx, Ly)
-  // ring DST pointer tables, per level: [G][8] src pointers, strides, dst pointers
-  void **ring_src, **ring_dst;
-  long* ring_es;
   // sub-domain: one vertex box, or a union of n_sdb disjoint boxes (reading R16), whose points are numbered
   // box by box; i_lo .. j_hi, ni, nj then describe the bounding box of the union, d_sd_map holds the Omega_0
   // index of every bounding-box vertex (-1: not in Omega_0) and d_sd_vert the bounding-box vertex (i, j) of

@@ -159,10 +159,10 @@ fsi_status solve_t(int nx, int ny, double h, double re, double dt, const T* rhs,
     sp.Mx = Mx;
     sp.My = My;
     dim3 grid((Nx + 2 * cy.nf - 1) / (2 * cy.nf));
-    const size_t sm = dst::pass_smem<T>((size_t)3 * cy.nf * Ly, Ly);
-    if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
-    else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
-    else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp);
+    const size_t sm = dst::pass_smem<T>((size_t)2 * cy.nf * Ly, Ly);
+    if (cy.per == 1) dst::k_ysolve<T, 1><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp, (const T*)nullptr);
+    else if (cy.per == 2) dst::k_ysolve<T, 2><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp, (const T*)nullptr);
+    else dst::k_ysolve<T, 4><<<grid, cy.nthr, sm, st>>>(T1, ldT, 0, Nx, Ny, T2w, T2s, ldX, 0, twy, logLy, cy.nf, sp, (const T*)nullptr);
   }
   {  // inverse x into the interior of the caller's vertex arrays (row stride nx + 1)
     dim3 grid(dst::xi_blocks(Ny, cx.nf));

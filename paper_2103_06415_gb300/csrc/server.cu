@@ -57,7 +57,8 @@ static size_t predict_bytes(const fsi_request* r) {
   const size_t fesz = r->precision == FSI_PREC_FP32 ? 4 : 8;     // level fields
   const size_t ps = ((size_t)g.nx + 1 + 7) / 8 * 8;
   const size_t lvl = ((size_t)g.ny + 1) * ps;
-  size_t b = (size_t)g.n_levels * lvl * (fesz * 3 + esz) + lvl * esz + (2 + (size_t)g.n_levels) * g.nx * g.ny * esz;
+  const size_t slots = (size_t)g.n_levels * (r->precision == FSI_PREC_MIXED ? 2 : 1);  // right-hand sides
+  size_t b = (size_t)g.n_levels * lvl * fesz * 3 + slots * lvl * esz + lvl * esz + (2 + slots) * g.nx * g.ny * esz;
   const double h = g.h;
   long i_lo = (long)std::ceil((r->box.x_lo - g.x0) / h - 1e-9), i_hi = (long)std::floor((r->box.x_hi - g.x0) / h + 1e-9);
   long j_lo = (long)std::ceil((r->box.y_lo - g.y0) / h - 1e-9), j_hi = (long)std::floor((r->box.y_hi - g.y0) / h + 1e-9);
