@@ -57,10 +57,14 @@ def parse():
     ap.add_argument("--oracle-level", default="", help=argparse.SUPPRESS)
     ap.add_argument("--horizon-steps", type=int, default=-1,
                     help="steps of the mixed-vs-FP64 history check (default: the workload's own horizon)")
-    ap.add_argument("--profile-case", default="tandem", choices=["tandem", "flag"],
-                    help="profiling mode workload: the reduced tandem case (nf = 1608) or the reduced flag case")
+    ap.add_argument("--profile-case", default="tandem", choices=["tandem", "tandem_full", "flag"],
+                    help="profiling mode workload: the reduced tandem case (nf = 1608), the full five-level "
+                         "tandem workload (one-pass launch lists only), or the reduced flag case")
+    ap.add_argument("--profile-dst", default="fft", choices=["fft", "gemm"],
+                    help="profiling mode: sine transforms by FFT passes or by tensor-core sine-matrix GEMMs "
+                         "(the GEMM passes need --precision fp32)")
     ap.add_argument("--profile-steps", type=int, default=0,
-                    help="profiling mode: build the reduced-Omega_0 variant of the workload, run this many "
+                    help="profiling mode: build the --profile-case workload, run this many "
                          "eager (non-graph) steps and exit without timing (for ncu captures)")
     return ap.parse_args()
 
@@ -522,11 +526,11 @@ def main():
         _b.build()
         import paper_2103_06415_gb300 as lib
         from runners import gpu_context
-        wr = (wl.flag_512x256_3lvl_reduced_omega0() if args.profile_case == "flag"
-              else wl.tandem_1536x768_reduced())
+        wr = {"flag": wl.flag_512x256_3lvl_reduced_omega0, "tandem_full": wl.tandem_1536x768_5lvl,
+              "tandem": wl.tandem_1536x768_reduced}[args.profile_case]()
         c = gpu_context(wr, precision={"mixed": lib.FSI_PREC_MIXED, "fp32": lib.FSI_PREC_FP32,
                                        "fp64": lib.FSI_PREC_FP64}[args.precision],
-                        use_graph=False)
+                        use_graph=False, dst_method=1 if args.profile_dst == "gemm" else 0)
         c.advance(args.profile_steps)
         c.sync()
         print(json.dumps({"profile_case": wr["name"], "steps": args.profile_steps, "stats": c.stats()}))

@@ -314,8 +314,11 @@ fsi_status fsi_debug_set_wait_limit(fsi_ctx* ctx, unsigned spin_limit, int missi
  * of the float inverse, 3 rebuild of the float inverse, 4 refinement solves, 5 double residuals,
  * 6 dtheta and convergence, 7 outputs; a finer split of 2, 4 and 5: 8 columns of X K, 9 rows of the new
  * X, 10 reload of X, 11 d = X r, 12 residual rows and barrier, 13 residual gather; inside 0, measured on
- * their own threads: 14 the body points (warps 0-3), 15 the linearisation and solves of the flags (warps 4-7).
- * out[0..n-1] (n <= 16 meaningful; synchronising). */
+ * their own threads: 14 the body points (warps 0-3), 15 the linearisation and solves of the flags (warps 4-7),
+ * and with flags the steps of 0 on thread 0: 16 wait for every CTA's points, 17 point tables into shared
+ * memory, 18 owned rows of P B0 P^T, 19 wait for the flags' warps, 20 flags' term and publication of the rows,
+ * 21 grid barrier, 22 right-hand side; 23 the owned rows of d = X r and their barrier (distributed variant;
+ * 11 is then the update of f).  out[0..n-1] (n <= 24 meaningful; synchronising). */
 fsi_status fsi_get_phase_times(fsi_ctx* ctx, double* out, int n);
 
 /* Live timing of one kernel class: runs n_steps (1..1024) ordinary time steps without a graph, records a

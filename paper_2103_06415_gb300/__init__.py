@@ -239,12 +239,14 @@ class Context:
 
     PHASES = ("points_rhs", "assemble_PB0PT", "inverse_refresh", "inverse_rebuild", "refine_solves",
               "residuals", "dtheta", "outputs", "ns_xk_columns", "ns_new_x_rows", "ns_reload_x", "solve_d",
-              "residual_rows_barrier", "residual_gather", "a_points_warps0_3", "a_flags_warps4_7")
+              "residual_rows_barrier", "residual_gather", "a_points_warps0_3", "a_flags_warps4_7",
+              "a_wait_points", "a_point_tables", "a_owned_rows", "a_wait_flags", "a_flag_term", "a_grid_barrier",
+              "a_rhs", "solve_d_rows_barrier")
 
     def phase_times(self):
         """Accumulated device wall time (ms) per phase of the FSI-iteration kernel."""
-        out = np.zeros(16)
-        check(self._lib.fsi_get_phase_times(self._h, _dp(out), 16), "fsi_get_phase_times")
+        out = np.zeros(len(self.PHASES))
+        check(self._lib.fsi_get_phase_times(self._h, _dp(out), len(self.PHASES)), "fsi_get_phase_times")
         return dict(zip(self.PHASES, out.tolist()))
 
     def stats(self):

@@ -620,7 +620,7 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
         !(c->d_W = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
         !(c->d_S = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
         !(c->d_T = (float*)ctx_alloc(c, (size_t)c->nf * fsi_float_ld(c->nf) * 4)) ||
-        !(c->d_phase = (unsigned long long*)ctx_alloc(c, 16 * sizeof(unsigned long long))) ||
+        !(c->d_phase = (unsigned long long*)ctx_alloc(c, 24 * sizeof(unsigned long long))) ||
         !(c->d_part = (double*)ctx_alloc(c, (size_t)2 * 1024 * 8)) ||
         !(c->d_hist = (double*)ctx_alloc(c, (size_t)c->hist_cap * c->n_bodies * 6 * 8)))
       return FSI_ERR_OOM;
@@ -687,7 +687,8 @@ static fsi_status precompute_impl(fsi_ctx* c, double drop_tol, const char* load)
     if (c->fsi_grid > nsm) c->fsi_grid = nsm;
     if (c->fsi_grid < fsi_min_grid(c->nf, c->fsi_big != 0)) return FSI_ERR_UNSUPPORTED;
     if (c->fsi_big && (!(c->d_dvec = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
-                       !(c->d_rsum = (double*)ctx_alloc(c, (size_t)c->nf * 8))))
+                       !(c->d_rsum = (double*)ctx_alloc(c, (size_t)c->nf * 8)) ||
+                       !(c->d_resf = (float*)ctx_alloc(c, (size_t)2 * c->nf * 4))))
       return FSI_ERR_OOM;
   }
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -817,9 +818,9 @@ extern "C" fsi_status fsi_get_phase_times(fsi_ctx* c, double* ms, int n) {
   for (int k = 0; k < n; ++k) ms[k] = 0.0;
   if (!c->d_phase) return FSI_OK;
   FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  unsigned long long ns[16];
+  unsigned long long ns[24];
   FSI_CUDA_TRY(cudaMemcpy(ns, c->d_phase, sizeof(ns), cudaMemcpyDeviceToHost));
-  for (int k = 0; k < n && k < 16; ++k) ms[k] = (double)ns[k] * 1e-6;
+  for (int k = 0; k < n && k < 24; ++k) ms[k] = (double)ns[k] * 1e-6;
   return FSI_OK;
 }
 

@@ -447,7 +447,7 @@ __device__ __forceinline__ YRow<T> y_row(const SpecParams<T>& sp, int k, int nro
 // transposed stores outw[j*out_ld + k], outs[j*out_ld + k].  DEF: rows of `inr` (x-transforms of a defect d,
 // same layout) are transformed beside `in` and enter the streamfunction only: s~ = (w~ + bc_s + d^)/lambda.
 template <typename T, int PER, int R3 = 1, bool DEF = false>
-__global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_ysolve(const T* __restrict__ in, long in_ld, long in_bs, int nrows, int N,
                                                 T* __restrict__ outw, T* __restrict__ outs, long out_ld,
                                                 long out_bs, const typename C2<T>::t* __restrict__ tw, int logL,
                                                 int nf, SpecParams<T> sp, const T* __restrict__ inr) {
@@ -465,34 +465,12 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
   // constant tables (set up with the context): loaded before the wait for the predecessor
   TwiddleStage<T, 4 * PER * R3> ts;
   ts.load(tw, L, (2 * (size_t)nf + 1) * L * sizeof(c2));
-  T lyv[NC], sy1v[NC], syNv[NC];
-#pragma unroll
-  for (int m = 0; m < NC; ++m) {
-    const int l = tid + m * nthr + 1;
-    const int ll = l <= N ? l : 1;
-    lyv[m] = sp.ly[ll];
-    sy1v[m] = sp.ring ? sp.sy1[ll] : T(0);
-    syNv[m] = sp.ring ? sp.syN[ll] : T(0);
-  }
   pdl_enter();
   in += (long)blockIdx.y * in_bs;
   if (DEF) inr += (long)blockIdx.y * in_bs;
   outw += (long)blockIdx.y * out_bs;
   outs += (long)blockIdx.y * out_bs;
   const T* ring = sp.ring;
-  T rc[NC][4];  // left/right ring spectra of w and s at this thread's columns
-  if (ring) {
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-      const int l0 = tid + m * nthr;
-      const int ll = l0 < N ? l0 : 0;
-      rc[m][0] = ring[0 * sp.ring_ld + ll];
-      rc[m][1] = ring[1 * sp.ring_ld + ll];
-      rc[m][2] = ring[4 * sp.ring_ld + ll];
-      rc[m][3] = ring[5 * sp.ring_ld + ll];
-    }
-  }
-  YRow<T> rows0[2] = {y_row<T>(sp, row0 + 1, nrows), y_row<T>(sp, row0 + 2, nrows)};
   zero_ends<T>(buf, NB * nf, L);
   for (int q = 0; q < NB * nf; ++q) {  // rows of `in` into buffers 0..nf-1, rows of `inr` into nf..2nf-1
     const int f = q < nf ? q : q - nf;
@@ -514,19 +492,24 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
   const c2* tws = ts.store(buf + 2L * nf * L, tw, L);
   __syncthreads();
   block_fft<T, NB * PER, R3>(buf, L, logL, tws);
+  // the per-column tables (eigenvalues, boundary sines, ring spectra) are read here, after the transforms,
+  // rather than held in registers across them (more resident CTAs)
   for (int f = 0; f < nf; ++f) {
-    YRow<T> rw[2];
-    if (f == 0) {
-      rw[0] = rows0[0];
-      rw[1] = rows0[1];
-    } else {
-      rw[0] = y_row<T>(sp, row0 + 2 * f + 1, nrows);
-      rw[1] = y_row<T>(sp, row0 + 2 * f + 2, nrows);
-    }
+    const YRow<T> rw[2] = {y_row<T>(sp, row0 + 2 * f + 1, nrows), y_row<T>(sp, row0 + 2 * f + 2, nrows)};
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
       const int l0 = tid + m * nthr;
       if (l0 >= N) continue;
+      const T lyv = sp.ly[l0 + 1];
+      T sy1v = T(0), syNv = T(0), rc[4] = {T(0), T(0), T(0), T(0)};  // left/right ring spectra of w and s
+      if (ring) {
+        sy1v = sp.sy1[l0 + 1];
+        syNv = sp.syN[l0 + 1];
+        rc[0] = ring[0 * sp.ring_ld + l0];
+        rc[1] = ring[1 * sp.ring_ld + l0];
+        rc[2] = ring[4 * sp.ring_ld + l0];
+        rc[3] = ring[5 * sp.ring_ld + l0];
+      }
       const c2 z = buf[(long)f * L + l0 + 1];
       c2 zd;
       if (DEF) zd = buf[(long)(nf + f) * L + l0 + 1];
@@ -535,12 +518,12 @@ __global__ void __launch_bounds__(256) k_ysolve(const T* __restrict__ in, long i
       for (int e = 0; e < 2; ++e) {
         T rh = e ? T(0.5) * z.x : T(-0.5) * z.y;
         if (rw[e].on) {
-          const T lam = (rw[e].lx + lyv[m]) * sp.inv_h2;
+          const T lam = (rw[e].lx + lyv) * sp.inv_h2;
           const T aw = sp.inv_dt + lam * sp.inv_2re;
           T bcs = T(0);
           if (ring) {
-            const T bw = rw[e].sx1 * rc[m][0] + rw[e].sxN * rc[m][1] + rw[e].wb * sy1v[m] + rw[e].wt * syNv[m];
-            bcs = rw[e].sx1 * rc[m][2] + rw[e].sxN * rc[m][3] + rw[e].sb * sy1v[m] + rw[e].st * syNv[m];
+            const T bw = rw[e].sx1 * rc[0] + rw[e].sxN * rc[1] + rw[e].wb * sy1v + rw[e].wt * syNv;
+            bcs = rw[e].sx1 * rc[2] + rw[e].sxN * rc[3] + rw[e].sb * sy1v + rw[e].st * syNv;
             rh += bw * sp.ring_w;
             bcs *= sp.inv_h2;
           }

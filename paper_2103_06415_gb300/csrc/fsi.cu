@@ -119,6 +119,7 @@ struct FsiArgs {
   // distributed variant: the correction d = X r of every row, and per-row absolute sums of K (rebuild)
   double* dvec;
   double* rsum;
+  float* resf;  // float copies of the residual rows, [2][nf] by solve parity
 };
 
 // level-0 streamfunction at vertex offset o: fp64 = 0 float, 1 double, 2 float pair (the mixed mode)
@@ -145,7 +146,7 @@ __device__ void e0cs(const FsiArgs& a, int I, int J, double* u, double* v) {
 // refresh, 3 inverse rebuild, 4 refinement solves, 5 double residuals, 6 dtheta/convergence, 7 outputs;
 // sub-phases (split of 2, 4 and 5): 8 X K columns, 9 new X rows, 10 reload of X, 11 d = X r,
 // 12 residual rows and barrier, 13 residual gather.
-constexpr int kPhases = 16;
+constexpr int kPhases = 24;
 struct PhaseClock {
   unsigned long long* acc;  // shared [kPhases]
   bool on;
@@ -214,6 +215,42 @@ __device__ double block_max(double x, double* red) {
 
 // Block-wide maxima of two non-negative floats given as bit patterns (integer order = float order; +inf
 // and NaN patterns sort above every finite value).  One barrier pair.
+// dst[k] = src[k], k < n (global, written in this launch), by the CTA: a thread's loads issued together
+__device__ __forceinline__ void gather_f(float* dst, const float* src, int n) {
+  for (int k0 = threadIdx.x; k0 < n; k0 += blockDim.x * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = k0 + u * (int)blockDim.x < n ? __ldcg(&src[k0 + u * blockDim.x]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u * (int)blockDim.x < n) dst[k0 + u * blockDim.x] = v[u];
+  }
+}
+
+// block maxima of two 64-bit patterns (non-negative doubles order as their bit patterns); red: >= 64 doubles
+__device__ void block_max2_bits64(unsigned long long& a, unsigned long long& b, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(FULL, a, o));
+    b = max(b, __shfl_xor_sync(FULL, b, o));
+  }
+  unsigned long long* r = reinterpret_cast<unsigned long long*>(red);
+  if (lane == 0) {
+    r[wid] = a;
+    r[32 + wid] = b;
+  }
+  __syncthreads();
+  unsigned long long ra = r[0], rb = r[32];
+  for (int w = 1; w < nw; ++w) {
+    ra = max(ra, r[w]);
+    rb = max(rb, r[32 + w]);
+  }
+  __syncthreads();
+  a = ra;
+  b = rb;
+}
+
 __device__ void block_max2_bits(unsigned& a, unsigned& b, unsigned* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   a = __reduce_max_sync(FULL, a);
@@ -380,7 +417,7 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 // (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
 // right-hand sides of the structural solves.
 struct FsiLayout {
-  size_t xs, krow, vec, pw, work, rf, pidx, pcij, pbody;
+  size_t xs, krow, vec, pw, work, rf, pidx, pcij, pbody, tors;
   size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys, kb;
   size_t total;
 };
@@ -412,7 +449,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd, boo
   L.pidx = L.rf + al16(lx * 4);
   L.pcij = L.pidx + al16((size_t)4 * nb * 4);
   L.pbody = L.pcij + al16((size_t)2 * nb * 4);
-  L.chi = L.pbody + al16((size_t)nb * 4);
+  L.tors = L.pbody + al16((size_t)nb * 4);
+  L.chi = L.tors + (big ? al16((size_t)nf * 8) : 0);
   L.rz = L.chi + al16((size_t)bd.nd * 8);
   L.cn = L.rz + al16((size_t)bd.nd * 8);
   L.rchi = L.cn + al16((size_t)bd.nd * 8);
@@ -486,34 +524,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
-}
-
-// Lane share of one row of K (global memory, written in this launch) times f (shared memory): 16-byte loads
-// with four independent chains when the row is 16-byte aligned (nf even), summed in a fixed order; the warp
-// adds the lanes (warp_sum).
-__device__ __forceinline__ double big_row_dot(const double* kr, const double* f, int nf, int lane) {
-  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-  if ((nf & 1) == 0) {
-    const double2* k2 = reinterpret_cast<const double2*>(kr);
-    const double2* f2 = reinterpret_cast<const double2*>(f);
-    const int n2 = nf >> 1;
-    int k = lane;
-    for (; k + 96 < n2; k += 128) {
-      const double2 a0 = __ldcg(&k2[k]), a1 = __ldcg(&k2[k + 32]), a2 = __ldcg(&k2[k + 64]), a3 = __ldcg(&k2[k + 96]);
-      const double2 b0 = f2[k], b1 = f2[k + 32], b2 = f2[k + 64], b3 = f2[k + 96];
-      c0 += a0.x * b0.x + a0.y * b0.y;
-      c1 += a1.x * b1.x + a1.y * b1.y;
-      c2 += a2.x * b2.x + a2.y * b2.y;
-      c3 += a3.x * b3.x + a3.y * b3.y;
-    }
-    for (; k < n2; k += 32) {
-      const double2 a0 = __ldcg(&k2[k]), b0 = f2[k];
-      c0 += a0.x * b0.x + a0.y * b0.y;
-    }
-  } else {
-    for (int k = lane; k < nf; k += 32) c0 += __ldcg(&kr[k]) * f[k];
-  }
-  return (c0 + c1) + (c2 + c3);
 }
 
 // ---- Distributed small-system solver (the kernel's BIG variant) -------------------------------------------
@@ -624,6 +634,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   __shared__ double b_sn[kMaxBodies], b_cs[kMaxBodies];  // sin, cos of theta0 + theta^(k)
   __shared__ double b_ijac[kMaxBodies], b_kc[kMaxBodies];  // 1/J and (2 ds/dt)/J
   __shared__ int bt_s[kMaxBodies], boff_s[kMaxBodies];     // type and first point of every body
+  __shared__ int bn_s[kMaxBodies];                          // points of every body
   __shared__ int bbx_s[kMaxBodies][4];  // hat-cell box of every body at the iterate: i_min, i_max, j_min, j_max
   __shared__ int sh_bad;
   __shared__ unsigned long long sh_phase[kPhases];
@@ -655,6 +666,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   int* pidx_s = reinterpret_cast<int*>(dyn_smem + L.pidx);
   int* pcij_s = reinterpret_cast<int*>(dyn_smem + L.pcij);
   int* pb_s = reinterpret_cast<int*>(dyn_smem + L.pbody);  // body of every point
+  // BIG: the torsional moment arm of every unknown at the iterate, (p - off) ds (-sin, cos)[component]
+  double* tors_s = reinterpret_cast<double*>(dyn_smem + L.tors);
   double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
   double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
   double* cn_s = reinterpret_cast<double*>(dyn_smem + L.cn);      // r^zeta_n of every free dof
@@ -698,6 +711,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   for (int bi = tid; bi < a.n_bodies; bi += nthr) {
     bt_s[bi] = a.bodies[bi].type;
     boff_s[bi] = a.bodies[bi].off;
+    bn_s[bi] = a.bodies[bi].n;
   }
   for (int g = tid; g < a.nd_tot; g += nthr) chi_s[g] = a.bchi[g];
   for (int e = tid; e < 3 * a.ne_tot; e += nthr) ref_s[e] = a.bref[e];
@@ -788,11 +802,42 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   // Entry (r, c) of K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S; with_g = false leaves out the flags'
   // (2 ds/dt) T J_d^-1 T^T.
   const bool dense = a.Bw == nullptr;
-  auto k_entry = [&](int r, int cidx, bool with_g) -> double {
-    const double kscale = a.ds / (a.h * a.h);
-    const long n2 = 2L * a.n_sd;
+  // The windowed B0': hat cells of points pa and pb more than bw + 1 cells apart share no entry of the window,
+  // and for nearer ones sum_{al, be} w_al(pa) w_be(pb) B0'[(ca, vertex al)][(cb, vertex be)] comes from the
+  // windows of pb's hat vertices (its sixteen loads independent: all issued before the sums).
+  auto window_near = [&](int dj0, int di0) -> bool {
+    return dj0 <= a.bw + 1 && dj0 >= -a.bw - 1 && di0 <= a.bw + 1 && di0 >= -a.bw - 1;
+  };
+  auto window_acc = [&](int pa, int ca, int pb, int cb, int dj0, int di0) -> double {
     const int bw = a.bw, side = 2 * bw + 1;
     const long carea = (long)side * side;
+    int ib[4];
+    double wb[4], t[4];
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {
+      ib[be] = pidx_s[4 * pb + be];
+      wb[be] = pw_s[4 * pb + be];
+    }
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      t[al] = 0.0;
+#pragma unroll
+      for (int be = 0; be < 4; ++be) {
+        const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+        if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
+          t[al] += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea + (long)(dj + bw) * side +
+                                 (di + bw)];
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int al = 0; al < 4; ++al) acc += pw_s[4 * pa + al] * t[al];
+    return acc;
+  };
+  // fluid_only: the sum over the hat vertices alone, without the factor ds/h^2 and the structural terms
+  auto k_entry = [&](int r, int cidx, bool with_g, bool fluid_only = false) -> double {
+    const double kscale = a.ds / (a.h * a.h);
+    const long n2 = 2L * a.n_sd;
     const int ca = r / nb, pa = r % nb, cb = cidx / nb, pb = cidx % nb;
     double acc = 0.0;
     int ib[4];
@@ -815,20 +860,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     } else {  // B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] from the column's window
       const int dj0 = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1], di0 = pcij_s[2 * pa] - pcij_s[2 * pb];
       // every vertex pair lies outside the window when the hat cells are more than bw + 1 apart
-      const bool near = dj0 <= bw + 1 && dj0 >= -bw - 1 && di0 <= bw + 1 && di0 >= -bw - 1;
-      for (int al = 0; near && al < 4; ++al) {
-        const double wa = pw_s[4 * pa + al];
-        double t = 0.0;
-#pragma unroll
-        for (int be = 0; be < 4; ++be) {
-          const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
-          if (dj >= -bw && dj <= bw && di >= -bw && di <= bw)
-            t += wb[be] * a.Bw[((long)cb * a.n_sd + ib[be]) * 2 * carea + (long)ca * carea +
-                               (long)(dj + bw) * side + (di + bw)];
-        }
-        acc += wa * t;
-      }
+      if (window_near(dj0, di0)) acc = window_acc(pa, ca, pb, cb, dj0, di0);
     }
+    if (fluid_only) return acc;
     double kv = kscale * acc;
     const int ba = pb_s[pa], bbd = pb_s[pb];
     if (ba == bbd && bt_s[ba] == FSI_BODY_TORSIONAL) {
@@ -851,6 +885,35 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     const int gi = max(bbx_s[ba][0] - bbx_s[bb][1], bbx_s[bb][0] - bbx_s[ba][1]);
     const int gj = max(bbx_s[ba][2] - bbx_s[bb][3], bbx_s[bb][2] - bbx_s[ba][3]);
     return gi <= a.bw + 1 && gj <= a.bw + 1;
+  };
+  // (K f)_r by a warp over the columns of the bodies that couple with row r's body (the other blocks of K are
+  // zero): two chains per lane, summed in a fixed order
+  auto coupled_dot = [&](int r) -> double {
+    const int ba = pb_s[r % nb];
+    const double* kr = a.K + (long)r * nf;
+    double c0 = 0.0, c1 = 0.0;
+    for (int bb = 0; bb < a.n_bodies; ++bb) {
+      if (!couples(ba, bb)) continue;
+      const int n = bn_s[bb];
+      for (int comp = 0; comp < 2; ++comp) {
+        const int off = comp * nb + boff_s[bb];
+        for (int t0 = lane; t0 < n; t0 += 32 * 8) {  // the lane's loads of a segment issued together
+          double kv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int t = t0 + 32 * u;
+            kv[u] = t < n ? __ldcg(&kr[off + t]) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const int t = t0 + 32 * u;
+            if (t < n) c0 += kv[u] * f_s[off + t];
+            if (t + 32 < n) c1 += kv[u + 1] * f_s[off + t + 32];
+          }
+        }
+      }
+    }
+    return c0 + c1;
   };
   // hat-cell boxes of the bodies from pcij_s, by nt threads of index tl with their own barrier
   auto body_boxes = [&](int tl, int nt, auto sync) {
@@ -894,6 +957,14 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
       }
     __syncthreads();
+    if constexpr (BIG) {
+      for (int k = tid; k < nf; k += nthr) {
+        const int p = k % nb, bb = pb_s[p];
+        tors_s[k] = bt_s[bb] == FSI_BODY_TORSIONAL ? (double)(p - boff_s[bb]) * a.ds * (k < nb ? -b_sn[bb] : b_cs[bb])
+                                                   : 0.0;
+      }
+      __syncthreads();
+    }
     {
       const int per = (nb + (int)gridDim.x - 1) / (int)gridDim.x;
       const int p0 = (int)blockIdx.x * per;
@@ -1017,9 +1088,18 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           a.rhs[2 * nf + nb + p] = uby - ucy + svy * coef;
         }
       }
-      if (side_clock && tid == 0) sh_phase[14] += PhaseClock::now() - ta0;
+      unsigned long long tb = side_clock ? PhaseClock::now() : 0ull;
+      if (side_clock && tid == 0) sh_phase[14] += tb - ta0;
+      auto side_sub = [&](int slot) {  // consecutive sub-steps of phase A on thread 0 of CTA 0
+        if (side_clock && tid == 0) {
+          const unsigned long long t = PhaseClock::now();
+          sh_phase[slot] += t - tb;
+          tb = t;
+        }
+      };
       if (overlap_b && wid < 4) {
         lower_grid_barrier(&a.ctrl[15], (it + 1) * (int)gridDim.x + a.lb_missing, a.status, a.lb_spins);
+        side_sub(16);
         for (int e = tid; e < 4 * nb; e += 128) {
           pidx_s[e] = __ldcg(&a.pidx[e]);
           pw_s[e] = __ldcg(&a.pw[e]);
@@ -1027,12 +1107,50 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
         named_sync_lower();
         body_boxes(tid, 128, []() { named_sync_lower(); });
-        for (int e = tid; e < nr * nf; e += 128) {
-          const int r = r0 + e / nf, cidx = e % nf;
-          const double kv = couples(pb_s[r % nb], pb_s[cidx % nb]) ? k_entry(r, cidx, false) : 0.0;
-          if constexpr (BIG) a.K[(long)r0 * nf + e] = kv;  // owned rows stay in global memory
-          else Krow[e] = kv;
+        side_sub(17);
+        if constexpr (BIG) {
+          // owned rows stay in global memory, body block by body block: the blocks of bodies that do not
+          // couple (Omega_0 hat cells farther apart than the B0' window) are zero and cost one store per entry.
+          // S, the float copy, is written here except where a flag's structural term is still to come.
+          // (FP64 and double-to-float conversions run at a small fraction of the FP32 rate on this GPU: a far
+          // entry of a coupled block costs one multiply-add with the row's factor hoisted, a zero no conversion)
+          const double kscale = a.ds / (a.h * a.h);
+          for (int c = 0; c < nr; ++c) {
+            const int r = r0 + c, ca = r >= nb ? 1 : 0, pa = r - ca * nb, ba = pb_s[pa];
+            const int cia = pcij_s[2 * pa], cja = pcij_s[2 * pa + 1];
+            const double ka = bt_s[ba] == FSI_BODY_TORSIONAL ? b_kc[ba] * tors_s[r] : 0.0;
+            double* kr = a.K + (long)r * nf;
+            float* sr = a.S + (long)r * lx;
+            for (int bb = 0; bb < a.n_bodies; ++bb) {
+              const int n = bn_s[bb], off = boff_s[bb];
+              const bool cp = couples(ba, bb), later = cp && ba == bb && bt_s[bb] == FSI_BODY_DEFORMABLE;
+              const bool rank1 = cp && ba == bb && bt_s[bb] == FSI_BODY_TORSIONAL;
+              for (int t = tid; t < 2 * n; t += 128) {
+                const int cb = t >= n ? 1 : 0, pb = off + t - cb * n, cidx = cb * nb + pb;
+                double kv = 0.0;
+                if (cp) {
+                  double acc = 0.0;
+                  if (dense) {
+                    acc = k_entry(r, cidx, false, true);
+                  } else {
+                    const int dj0 = cja - pcij_s[2 * pb + 1], di0 = cia - pcij_s[2 * pb];
+                    if (window_near(dj0, di0)) acc = window_acc(pa, ca, pb, cb, dj0, di0);
+                  }
+                  kv = acc != 0.0 ? kscale * acc : 0.0;
+                  if (rank1) kv += ka * tors_s[cidx];
+                }
+                kr[cidx] = kv;
+                if (!later) sr[cidx] = cp ? (float)kv : 0.0f;
+              }
+            }
+          }
+        } else {
+          for (int e = tid; e < nr * nf; e += 128) {
+            const int r = r0 + e / nf, cidx = e % nf;
+            Krow[e] = couples(pb_s[r % nb], pb_s[cidx % nb]) ? k_entry(r, cidx, false) : 0.0;
+          }
         }
+        side_sub(18);
       }
       if (wid >= 4 && a.n_def > 0) {
         // ---- A': every flag linearised at chi^(k) (warps 4-7): element forces (FP64) and tangents (FP32),
@@ -1096,20 +1214,46 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         if (side_clock) sh_phase[15] += PhaseClock::now() - ta0;
       }
     }
+    const bool pclk = blockIdx.x == 0 && tid == 0 && a.phase_ns;
+    unsigned long long tc = pclk ? PhaseClock::now() : 0ull;
+    auto a_sub = [&](int slot) {
+      if (pclk) {
+        const unsigned long long t = PhaseClock::now();
+        sh_phase[slot] += t - tc;
+        tc = t;
+      }
+    };
     if (overlap_b) {  // owned rows: the flags' term from this CTA's columns of T J_d^-1 T^T, then publish
       __syncthreads();
-      for (int e = tid; e < nr * nf; e += nthr) {
-        const int r = r0 + e / nf, cidx = e % nf;
-        double kv = BIG ? a.K[(long)r0 * nf + e] : Krow[e];
-        const int ba = a.point_body[r % nb];
-        if (ba == a.point_body[cidx % nb] && a.bodies[ba].type == FSI_BODY_DEFORMABLE)
-          kv += a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
-        if constexpr (!BIG) Krow[e] = kv;
-        a.K[(long)r * nf + cidx] = kv;
-        a.S[(long)r * lx + cidx] = (float)kv;
+      a_sub(19);
+      if constexpr (BIG) {  // only a flag's own block receives the term
+        for (int c = 0; c < nr; ++c) {
+          const int r = r0 + c, ba = pb_s[r % nb];
+          if (bt_s[ba] != FSI_BODY_DEFORMABLE) continue;
+          const int n = bn_s[ba], off = boff_s[ba];
+          for (int t = tid; t < 2 * n; t += nthr) {
+            const int cidx = t < n ? off + t : nb + off + t - n;
+            const double kv = a.K[(long)r * nf + cidx] + a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
+            a.K[(long)r * nf + cidx] = kv;
+            a.S[(long)r * lx + cidx] = (float)kv;
+          }
+        }
+      } else {
+        for (int e = tid; e < nr * nf; e += nthr) {
+          const int r = r0 + e / nf, cidx = e % nf;
+          double kv = Krow[e];
+          const int ba = a.point_body[r % nb];
+          if (ba == a.point_body[cidx % nb] && a.bodies[ba].type == FSI_BODY_DEFORMABLE)
+            kv += a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
+          Krow[e] = kv;
+          a.K[(long)r * nf + cidx] = kv;
+          a.S[(long)r * lx + cidx] = (float)kv;
+        }
       }
+      a_sub(20);
     }
     grid.sync();
+    a_sub(21);
     if (!overlap_b) {
       for (int e = tid; e < 4 * nb; e += nthr) {
         pidx_s[e] = __ldcg(&a.pidx[e]);
@@ -1134,9 +1278,25 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       }
       __syncthreads();
     }
+    a_sub(22);
     clk.mark(0);
     // ---- B: K = (ds/h^2) P B0 P^T + (2 ds/dt) S^T J^{-1} S (with flags already assembled by owned rows)
-    if (!overlap_b) {
+    if (!overlap_b && BIG) {  // owned rows, body block by body block (see the flags' variant above)
+      for (int c = 0; c < nr; ++c) {
+        const int r = r0 + c, ba = pb_s[r % nb];
+        for (int bb = 0; bb < a.n_bodies; ++bb) {
+          const int n = bn_s[bb], off = boff_s[bb];
+          const bool cp = couples(ba, bb);
+          for (int t = tid; t < 2 * n; t += nthr) {
+            const int cidx = t < n ? off + t : nb + off + t - n;
+            const double kv = cp ? k_entry(r, cidx, true) : 0.0;
+            a.K[(long)r * nf + cidx] = kv;
+            a.S[(long)r * lx + cidx] = (float)kv;
+          }
+        }
+      }
+      grid.sync();
+    } else if (!overlap_b) {
       for (long e = gtid; e < (long)nf * nf; e += gsize) {
         const int r = (int)(e / nf), cidx = (int)(e % nf);
         if (dense && cidx > r) continue;
@@ -1196,77 +1356,76 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     auto ns_refresh = [&]() {
       if constexpr (BIG) {  // one step: the error I - K X is squared, and a step costs four block GEMMs
         big_ns_step();
-        clk.mark(2);
-        return;
-      }
-      for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - (X K) X: the error I - K X is squared
-        float* Xn = cur ? a.Xa : a.Xb;
-        // (a) owned columns of T = X K: T[i][r0 + c] = sum_m X[i][m] K[m][r0 + c]
-        for (int m = tid; m < lx; m += nthr) {  // entries m >= nf stay zero
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float* kr = a.S + (long)m * lx + r0;
-          if (m < nf && nr > 0) v.x = __ldcg(kr);
-          if (m < nf && nr > 1) v.y = __ldcg(kr + 1);
-          if (m < nf && nr > 2) v.z = __ldcg(kr + 2);
-          if (m < nf && nr > 3) v.w = __ldcg(kr + 3);
-          work4[m] = v;
-        }
-        __syncthreads();
-        if (nr > 0) {
-          for (int i = tid; i < nf; i += nthr) {  // thread per row i, 128-bit loads (conflict-free stride)
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4* xr = reinterpret_cast<const float4*>(Xs + (long)i * lx);
-            for (int m4 = 0; m4 < lx / 4; ++m4) {
-              const float4 xv = xr[m4];
-              const float4 k0 = work4[4 * m4], k1 = work4[4 * m4 + 1], k2 = work4[4 * m4 + 2], k3 = work4[4 * m4 + 3];
-              acc.x += xv.x * k0.x + xv.y * k1.x + xv.z * k2.x + xv.w * k3.x;
-              acc.y += xv.x * k0.y + xv.y * k1.y + xv.z * k2.y + xv.w * k3.y;
-              acc.z += xv.x * k0.z + xv.y * k1.z + xv.z * k2.z + xv.w * k3.z;
-              acc.w += xv.x * k0.w + xv.y * k1.w + xv.z * k2.w + xv.w * k3.w;
-            }
-            float* tr = a.T + (long)i * lx + r0;
-            tr[0] = acc.x;
-            if (nr > 1) tr[1] = acc.y;
-            if (nr > 2) tr[2] = acc.z;
-            if (nr > 3) tr[3] = acc.w;
+      } else {
+        for (int ns = 0; ns < kNsSteps; ++ns) {  // X <- 2X - (X K) X: the error I - K X is squared
+          float* Xn = cur ? a.Xa : a.Xb;
+          // (a) owned columns of T = X K: T[i][r0 + c] = sum_m X[i][m] K[m][r0 + c]
+          for (int m = tid; m < lx; m += nthr) {  // entries m >= nf stay zero
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float* kr = a.S + (long)m * lx + r0;
+            if (m < nf && nr > 0) v.x = __ldcg(kr);
+            if (m < nf && nr > 1) v.y = __ldcg(kr + 1);
+            if (m < nf && nr > 2) v.z = __ldcg(kr + 2);
+            if (m < nf && nr > 3) v.w = __ldcg(kr + 3);
+            work4[m] = v;
           }
-        }
-        grid.sync();
-        clk.sub(8);
-        // (b) owned rows of the new X: Xn[r0 + c][j] = 2 X[r0 + c][j] - sum_m T[r0 + c][m] X[m][j]
-        for (int m = tid; m < nf; m += nthr) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (nr > 0) v.x = __ldcg(&a.T[(long)r0 * lx + m]);
-          if (nr > 1) v.y = __ldcg(&a.T[(long)(r0 + 1) * lx + m]);
-          if (nr > 2) v.z = __ldcg(&a.T[(long)(r0 + 2) * lx + m]);
-          if (nr > 3) v.w = __ldcg(&a.T[(long)(r0 + 3) * lx + m]);
-          work4[m] = v;
-        }
-        __syncthreads();
-        if (nr > 0) {
-          for (int j = tid; j < nf; j += nthr) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-            for (int m = 0; m < nf; ++m) {
-              const float xv = Xs[(long)m * lx + j];
-              const float4 tv = work4[m];
-              acc.x += tv.x * xv;
-              acc.y += tv.y * xv;
-              acc.z += tv.z * xv;
-              acc.w += tv.w * xv;
+          __syncthreads();
+          if (nr > 0) {
+            for (int i = tid; i < nf; i += nthr) {  // thread per row i, 128-bit loads (conflict-free stride)
+              float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+              const float4* xr = reinterpret_cast<const float4*>(Xs + (long)i * lx);
+              for (int m4 = 0; m4 < lx / 4; ++m4) {
+                const float4 xv = xr[m4];
+                const float4 k0 = work4[4 * m4], k1 = work4[4 * m4 + 1], k2 = work4[4 * m4 + 2], k3 = work4[4 * m4 + 3];
+                acc.x += xv.x * k0.x + xv.y * k1.x + xv.z * k2.x + xv.w * k3.x;
+                acc.y += xv.x * k0.y + xv.y * k1.y + xv.z * k2.y + xv.w * k3.y;
+                acc.z += xv.x * k0.z + xv.y * k1.z + xv.z * k2.z + xv.w * k3.z;
+                acc.w += xv.x * k0.w + xv.y * k1.w + xv.z * k2.w + xv.w * k3.w;
+              }
+              float* tr = a.T + (long)i * lx + r0;
+              tr[0] = acc.x;
+              if (nr > 1) tr[1] = acc.y;
+              if (nr > 2) tr[2] = acc.z;
+              if (nr > 3) tr[3] = acc.w;
             }
-            Xn[(long)r0 * lx + j] = 2.0f * Xs[(long)r0 * lx + j] - acc.x;
-            if (nr > 1) Xn[(long)(r0 + 1) * lx + j] = 2.0f * Xs[(long)(r0 + 1) * lx + j] - acc.y;
-            if (nr > 2) Xn[(long)(r0 + 2) * lx + j] = 2.0f * Xs[(long)(r0 + 2) * lx + j] - acc.z;
-            if (nr > 3) Xn[(long)(r0 + 3) * lx + j] = 2.0f * Xs[(long)(r0 + 3) * lx + j] - acc.w;
           }
+          grid.sync();
+          clk.sub(8);
+          // (b) owned rows of the new X: Xn[r0 + c][j] = 2 X[r0 + c][j] - sum_m T[r0 + c][m] X[m][j]
+          for (int m = tid; m < nf; m += nthr) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nr > 0) v.x = __ldcg(&a.T[(long)r0 * lx + m]);
+            if (nr > 1) v.y = __ldcg(&a.T[(long)(r0 + 1) * lx + m]);
+            if (nr > 2) v.z = __ldcg(&a.T[(long)(r0 + 2) * lx + m]);
+            if (nr > 3) v.w = __ldcg(&a.T[(long)(r0 + 3) * lx + m]);
+            work4[m] = v;
+          }
+          __syncthreads();
+          if (nr > 0) {
+            for (int j = tid; j < nf; j += nthr) {
+              float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  #pragma unroll 4
+              for (int m = 0; m < nf; ++m) {
+                const float xv = Xs[(long)m * lx + j];
+                const float4 tv = work4[m];
+                acc.x += tv.x * xv;
+                acc.y += tv.y * xv;
+                acc.z += tv.z * xv;
+                acc.w += tv.w * xv;
+              }
+              Xn[(long)r0 * lx + j] = 2.0f * Xs[(long)r0 * lx + j] - acc.x;
+              if (nr > 1) Xn[(long)(r0 + 1) * lx + j] = 2.0f * Xs[(long)(r0 + 1) * lx + j] - acc.y;
+              if (nr > 2) Xn[(long)(r0 + 2) * lx + j] = 2.0f * Xs[(long)(r0 + 2) * lx + j] - acc.z;
+              if (nr > 3) Xn[(long)(r0 + 3) * lx + j] = 2.0f * Xs[(long)(r0 + 3) * lx + j] - acc.w;
+            }
+          }
+          grid.sync();
+          clk.sub(9);
+          load_x(Xs, Xn, nf, lx, &xbar, &xphase, a.status);  // (c) every CTA takes the whole new X
+          __syncthreads();
+          clk.sub(10);
+          cur ^= 1;
         }
-        grid.sync();
-        clk.sub(9);
-        load_x(Xs, Xn, nf, lx, &xbar, &xphase, a.status);  // (c) every CTA takes the whole new X
-        __syncthreads();
-        clk.sub(10);
-        cur ^= 1;
       }
       clk.mark(2);
     };
@@ -1350,45 +1509,77 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int c = wid; c < nr; c += nw) {
           double acc = 0.0;
           if constexpr (BIG) {
-            acc = big_row_dot(a.K + (long)(r0 + c) * nf, f_s, nf, lane);
+            acc = coupled_dot(r0 + c);
           } else {
             const double* kr = Krow + (long)c * nf;
             for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
           }
           acc = warp_sum(acc);
-          if (lane == 0) res1[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
+          if (lane == 0) {
+            const double rv = rhs_s[r0 + c] + gfp_s[c] - acc;
+            res1[r0 + c] = rv;
+            if constexpr (BIG) a.resf[nf + r0 + c] = (float)rv;
+          }
         }
         grid.sync();
-        for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&res1[k]);
+        if constexpr (BIG)
+          gather_f(rf, a.resf + nf, nf);
+        else
+          for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&res1[k]);
         __syncthreads();
       }
       for (; s < kMaxSolves; ++s) {
-        const double* r = (s == 0 && !warm) ? rhs_s : r_s;
-        for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
+        if (!BIG || (s == 0 && !warm)) {  // the distributed variant gathered the float residual already
+          const double* r = (s == 0 && !warm) ? rhs_s : r_s;
+          for (int k = tid; k < nf; k += nthr) rf[k] = (float)r[k];
+        }
         __syncthreads();
         unsigned dbits = 0u, xbits = 0u;  // max |d|, max |f| as float bit patterns
+        unsigned long long dbits64 = 0ull, xbits64 = 0ull;  // the same as double bit patterns (BIG)
         if constexpr (BIG) {  // owned rows of d = X r (block columns), shared through global memory
           const float* Xc = cur ? a.Xb : a.Xa;
           for (int c = wid; c < nr; c += nw) {
-            const int i = r0 + c;
-            const RowBlock b = row_block(a, i);
+            const int i = r0 + c, bi = pb_s[i % nb];
+            const RowBlock b{boff_s[bi], bn_s[bi]};
+            const float* xr = Xc + (long)i * lx;
             float acc = 0.0f;
-#pragma unroll 4
-            for (int t = lane; t < 2 * b.n; t += 32) {
-              const int col = blk_col(b, nb, t);
-              acc += __ldcg(&Xc[(long)i * lx + col]) * rf[col];
+            for (int t0 = lane; t0 < 2 * b.n; t0 += 32 * 16) {  // the lane's loads of the row issued together
+              float xv[16];
+#pragma unroll
+              for (int u = 0; u < 16; ++u) {
+                const int t = t0 + 32 * u;
+                xv[u] = t < 2 * b.n ? __ldcg(&xr[blk_col(b, nb, t)]) : 0.0f;
+              }
+#pragma unroll
+              for (int u = 0; u < 16; ++u) {
+                const int t = t0 + 32 * u;
+                if (t < 2 * b.n) acc += xv[u] * rf[blk_col(b, nb, t)];
+              }
             }
             acc = warp_sum_f(acc);
             if (lane == 0) a.dvec[i] = (double)acc;
           }
           grid.sync();
-          for (int i = tid; i < nf; i += nthr) {
-            const double di = __ldcg(&a.dvec[i]);
-            const double xi = (s == 0 && !warm ? 0.0 : f_s[i]) + di;
-            f_s[i] = xi;
-            const float xf = (float)xi;
-            dbits = max(dbits, isfinite(xf) ? __float_as_uint(fabsf((float)di)) : 0x7f800000u);
-            xbits = max(xbits, __float_as_uint(fabsf(xf)));
+          clk.sub(23);
+          // the maxima on the bit patterns of |d| and |f| (integer operations: no conversions), a non-finite
+          // f recorded as infinity
+          constexpr unsigned long long kAbs = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+          for (int i0 = tid; i0 < nf; i0 += nthr * 8) {  // the thread's loads issued together
+            double dv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dv[u] = i0 + u * nthr < nf ? __ldcg(&a.dvec[i0 + u * nthr]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int i = i0 + u * nthr;
+              if (i >= nf) break;
+              const double di = dv[u];
+              const double xi = (s == 0 && !warm ? 0.0 : f_s[i]) + di;
+              f_s[i] = xi;
+              const unsigned long long xb = (unsigned long long)__double_as_longlong(xi) & kAbs;
+              const unsigned long long db = (unsigned long long)__double_as_longlong(di) & kAbs;
+              dbits64 = max(dbits64, xb >= kInf ? kInf : db);
+              xbits64 = max(xbits64, xb);
+            }
           }
         }
         for (int i = BIG ? nf : tid; i < nf; i += nthr) {  // d = X r, f += d (every CTA, all rows; thread per row)
@@ -1409,9 +1600,16 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
           dbits = max(dbits, isfinite(xf) ? __float_as_uint(fabsf(acc)) : 0x7f800000u);
           xbits = max(xbits, __float_as_uint(fabsf(xf)));
         }
-        block_max2_bits(dbits, xbits, redu);
-        const double gd = (double)__uint_as_float(dbits);
-        const double gx = (double)__uint_as_float(xbits);
+        double gd, gx;
+        if constexpr (BIG) {
+          block_max2_bits64(dbits64, xbits64, red);
+          gd = __longlong_as_double((long long)dbits64);
+          gx = __longlong_as_double((long long)xbits64);
+        } else {
+          block_max2_bits(dbits, xbits, redu);
+          gd = (double)__uint_as_float(dbits);
+          gx = (double)__uint_as_float(xbits);
+        }
         clk.sub(11);
         clk.mark(4);
         if (!isfinite(gd)) {  // a diverged inverse: rebuild and retry
@@ -1439,18 +1637,26 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int c = wid; c < nr; c += nw) {  // owned residual rows r = rhs - K f in double
           double acc = 0.0;
           if constexpr (BIG) {
-            acc = big_row_dot(a.K + (long)(r0 + c) * nf, f_s, nf, lane);
+            acc = coupled_dot(r0 + c);
           } else {
             const double* kr = Krow + (long)c * nf;
             for (int k = lane; k < nf; k += 32) acc += kr[k] * f_s[k];
           }
           acc = warp_sum(acc);
-          if (lane == 0) ((s & 1) ? res1 : res0)[r0 + c] = rhs_s[r0 + c] + gfp_s[c] - acc;
+          if (lane == 0) {
+            const double rv = rhs_s[r0 + c] + gfp_s[c] - acc;
+            ((s & 1) ? res1 : res0)[r0 + c] = rv;
+            if constexpr (BIG) a.resf[(s & 1) * nf + r0 + c] = (float)rv;
+          }
         }
         grid.sync();
         clk.sub(12);
-        const double* rg = (s & 1) ? res1 : res0;
-        for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&rg[k]);
+        if constexpr (BIG) {  // the float residual is all the next solve needs
+          gather_f(rf, a.resf + (s & 1) * nf, nf);
+        } else {
+          const double* rg = (s & 1) ? res1 : res0;
+          for (int k = tid; k < nf; k += nthr) r_s[k] = __ldcg(&rg[k]);
+        }
         __syncthreads();
         clk.sub(13);
         clk.mark(5);
@@ -1766,6 +1972,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.sd_map = c->n_sdb > 1 ? c->d_sd_map : nullptr;
   a.dvec = c->d_dvec;
   a.rsum = c->d_rsum;
+  a.resf = c->d_resf;
   const bool big = c->fsi_big != 0;
   a.lb_missing = c->wait_missing;
   cudaLaunchConfig_t cfg = {};

@@ -197,6 +197,7 @@ struct fsi_ctx {
   int fsi_big;   // 1: the distributed variant of the FSI kernel (block-Jacobi inverse and K in global memory)
   double* d_dvec;  // distributed variant: [nf] corrections d = X r shared between the CTAs
   double* d_rsum;  // distributed variant: [nf] absolute row sums of K (rebuild of the inverse)
+  float* d_resf;   // distributed variant: [2][nf] float copies of the residual rows (by solve parity)
   // bounded cross-CTA wait of the FSI kernel (fsi_debug_set_wait_limit): poll limit (0: default) and
   // arrivals it waits for that never come (0 in normal runs)
   unsigned wait_spins;
