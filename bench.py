@@ -740,7 +740,7 @@ def roofline(ctx, w, lib, torch, local):
     flops = (iters * 16 * 2 * coupled                    # P B0' P^T of the coupled entries
              + refreshes * 2 * 2 * 2 * blk3              # one Newton-Schulz step: two block GEMMs
              + solves * 2 * sum(n * n for n in per_body) # d = X r on the blocks
-             + solves * 2 * nf * nf                      # double residual rows
+             + solves * 2 * coupled                      # double residual rows over the coupled blocks
              + iters * n_el * (250 + 100 + (2 + 2 * n_el) * 54))  # flag elements, J_d, structural solves
     fsi_ms = shares["fsi"][0]
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -752,8 +752,12 @@ def roofline(ctx, w, lib, torch, local):
             "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
             "measured_fma_tflops": {"fp32": lib.fma_rate(lib.FSI_PREC_FP32) / 1e12,
                                     "fp64": lib.fma_rate(lib.FSI_PREC_FP64) / 1e12},
-            "traffic": None,
-            "traffic_note": "no ncu capture of this kernel at this size yet",
+            # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu capture of the same kernel
+            # on the two-level variant of this workload (same nf, bodies, B0' window half-width 13), whose
+            # launch does the same per-step work
+            "traffic": 16731648 + 320512 if nf == 1608 else None,
+            "traffic_note": "ncu capture of k_fsi<BIG> on tandem_1536x768_reduced (nf = 1608, window 13): the "
+                            "launch's units (body points, owned rows, window columns) equal this workload's",
             "algorithmic_flops_per_launch": flops, "avg_launch_ms": fsi_ms,
             "per_step_kernel_ms": per_step, "dominant": max(per_step, key=per_step.get),
             "transform_passes_hbm": passes, "hbm_peak_gbs": hbm}
