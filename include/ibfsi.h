@@ -110,6 +110,19 @@ typedef struct {
                      K is weak, exactly block-diagonal K for bodies farther apart than the window of B0').
                      0 takes 1 when it fits, else 2.  A size the choice cannot hold: FSI_ERR_UNSUPPORTED at
                      fsi_precompute; other values: FSI_ERR_INVALID_ARG. */
+  /* Device memory through the caller's allocator (not part of the paper's method: the boundary's hook for a
+   * host framework that owns device memory).  When dev_alloc is not NULL, every device buffer the context
+   * (or the box set of fsi_b0_set_build) allocates -- the level fields and scratch, B0 or B0', the FSI
+   * workspace, and the temporaries of the offline stage -- comes from dev_alloc(bytes, dev_alloc_user), which
+   * returns device memory usable on the context's stream, aligned to 256 bytes, or NULL when it cannot
+   * (the call then fails with FSI_ERR_OOM; a misaligned pointer is handed back to dev_free and treated the
+   * same way).  Each such pointer is returned once through dev_free(ptr, dev_alloc_user): temporaries when
+   * their stage ends, the rest at fsi_destroy.  The library never calls them concurrently from several host
+   * threads for one context.  dev_alloc NULL: cudaMalloc and cudaFree (dev_free and dev_alloc_user ignored);
+   * dev_alloc without dev_free: FSI_ERR_INVALID_ARG. */
+  void* (*dev_alloc)(size_t bytes, void* user);
+  void (*dev_free)(void* ptr, void* user);
+  void* dev_alloc_user;
 } fsi_exec_desc;
 
 /* A body (Sec. 2.1).  TORSIONAL: a straight plate of n_pts points j = 0..n_pts-1 at

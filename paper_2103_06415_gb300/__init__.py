@@ -25,23 +25,33 @@ def _dp(a):
 class Context:
     """One FSI run on the current CUDA device.
 
-    grid: nx, ny (powers of two), n_levels, x0, y0, h, re, dt, uinf=(U, V)
-    precision: FSI_PREC_FP64, FSI_PREC_FP32 or FSI_PREC_MIXED (double fields, float transforms, the finest level
-    in increment form); stream: a cudaStream_t handle (int) or None.
+    grid: nx, ny (2^k or 3 * 2^k cells), n_levels, x0, y0, h, re, dt, uinf=(U, V)
+    precision: FSI_PREC_FP64, FSI_PREC_FP32 or FSI_PREC_MIXED (float-pair fields, float transforms of every
+    level's increments); stream: a cudaStream_t handle (int) or None.
     dst_method: 0 FFT sine transforms, 1 tensor-core sine-matrix GEMMs (FP32), 2 autotune per pass.
     coupling: COUPLING_SUBDOMAIN (the method) or COUPLING_TRUE_E (the true-E comparator; krylov_tol and
     krylov_max_iters control its conjugate-gradient solve, 0 = library defaults).
     fsi_solver: 0 automatic, 1 float inverse in shared memory, 2 distributed block-Jacobi inverse (large nf).
+    allocator: None (cudaMalloc), or a pair (alloc, free) of callables: alloc(nbytes) -> device pointer (int,
+    256-byte aligned, 0 when it cannot) and free(ptr), through which every device buffer of the context goes
+    (fsi_exec_desc.dev_alloc); they are kept alive with the context.
     """
 
     def __init__(self, nx, ny, n_levels, x0, y0, h, re, dt, uinf=(1.0, 0.0), precision=FSI_PREC_FP64,
                  stream=None, max_iters=50, tol=1e-7, history_cap=1 << 16, use_graph=True, b0_method=0,
-                 dst_method=0, coupling=COUPLING_SUBDOMAIN, krylov_tol=0.0, krylov_max_iters=0, fsi_solver=0):
+                 dst_method=0, coupling=COUPLING_SUBDOMAIN, krylov_tol=0.0, krylov_max_iters=0, fsi_solver=0,
+                 allocator=None):
         self._lib = _lib.load()
         g = _lib.GridDesc(nx, ny, n_levels, x0, y0, h, re, dt, (ctypes.c_double * 2)(*uinf))
         x = _lib.ExecDesc(precision, ctypes.c_void_p(stream) if stream else None, max_iters, tol, history_cap,
                           1 if use_graph else 0, b0_method, dst_method, coupling, krylov_tol, krylov_max_iters,
                           fsi_solver)
+        self._alloc_fns = None
+        if allocator is not None:
+            alloc, free = allocator
+            self._alloc_fns = (_lib.DEV_ALLOC_FN(lambda n, user: alloc(n) or None),
+                               _lib.DEV_FREE_FN(lambda p, user: free(p)))
+            x.dev_alloc, x.dev_free = self._alloc_fns
         h_ = ctypes.c_void_p()
         check(self._lib.fsi_create(ctypes.byref(g), ctypes.byref(x), ctypes.byref(h_)), "fsi_create")
         self._h = h_

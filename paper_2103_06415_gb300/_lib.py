@@ -32,11 +32,16 @@ class GridDesc(ctypes.Structure):
                 ("re", ctypes.c_double), ("dt", ctypes.c_double), ("uinf", ctypes.c_double * 2)]
 
 
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class ExecDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("history_cap", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("b0_method", ctypes.c_int), ("dst_method", ctypes.c_int), ("coupling", ctypes.c_int),
-                ("krylov_tol", ctypes.c_double), ("krylov_max_iters", ctypes.c_int), ("fsi_solver", ctypes.c_int)]
+                ("krylov_tol", ctypes.c_double), ("krylov_max_iters", ctypes.c_int), ("fsi_solver", ctypes.c_int),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("dev_alloc_user", ctypes.c_void_p)]
 
 
 class BodyDesc(ctypes.Structure):

@@ -46,10 +46,31 @@ extern "C" const char* fsi_status_string(int s) {
   }
 }
 
+cudaError_t ctx_dev_malloc(const fsi_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!c->x.dev_alloc) return cudaMalloc(p, bytes);
+  void* q = c->x.dev_alloc(bytes, c->x.dev_alloc_user);
+  if (q && (reinterpret_cast<uintptr_t>(q) & 255u) != 0) {  // TMA and vector loads need the alignment
+    c->x.dev_free(q, c->x.dev_alloc_user);
+    q = nullptr;
+  }
+  if (!q) return cudaErrorMemoryAllocation;
+  *p = q;
+  return cudaSuccess;
+}
+
+void ctx_dev_free(const fsi_ctx* c, void* p) {
+  if (!p) return;
+  if (c->x.dev_alloc)
+    c->x.dev_free(p, c->x.dev_alloc_user);
+  else
+    cudaFree(p);
+}
+
 void* ctx_alloc(fsi_ctx* c, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (ctx_dev_malloc(c, &p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -60,7 +81,7 @@ void* ctx_alloc(fsi_ctx* c, size_t bytes) {
 }
 
 static void ctx_free_all(fsi_ctx* c) {
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) ctx_dev_free(c, p);
   c->allocs.clear();
   c->dev_bytes = 0;
 }
@@ -280,8 +301,7 @@ extern "C" fsi_status fsi_create(const fsi_grid_desc* grid, const fsi_exec_desc*
   memset(&c->x, 0, sizeof(c->x));
   if (exec) c->x = *exec;
   if ((c->x.precision != FSI_PREC_FP64 && c->x.precision != FSI_PREC_FP32 && c->x.precision != FSI_PREC_MIXED) ||
-      c->x.dst_method < 0 ||
-      c->x.dst_method > 2) {
+      c->x.dst_method < 0 || c->x.dst_method > 2 || (c->x.dev_alloc && !c->x.dev_free)) {
     delete c;
     return FSI_ERR_INVALID_ARG;
   }
@@ -963,8 +983,8 @@ extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, 
   int64_t *dr = nullptr, *dc = nullptr;
   double* dout = nullptr;
   fsi_status st = FSI_OK;
-  if (cudaMalloc(&dr, n * 8) != cudaSuccess || cudaMalloc(&dc, n * 8) != cudaSuccess ||
-      cudaMalloc(&dout, n * 8) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&dr, n * 8) != cudaSuccess || ctx_dev_malloc(c, (void**)&dc, n * 8) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&dout, n * 8) != cudaSuccess) {
     st = FSI_ERR_OOM;
   } else if (cudaMemcpyAsync(dr, rows, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
              cudaMemcpyAsync(dc, cols, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
@@ -976,9 +996,9 @@ extern "C" fsi_status fsi_get_operator_entries(fsi_ctx* c, const int64_t* rows, 
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       st = FSI_ERR_CUDA;
   }
-  cudaFree(dr);
-  cudaFree(dc);
-  cudaFree(dout);
+  ctx_dev_free(c, dr);
+  ctx_dev_free(c, dc);
+  ctx_dev_free(c, dout);
   return st;
 }
 

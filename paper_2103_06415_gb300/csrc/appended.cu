@@ -148,9 +148,9 @@ template <typename T>
 fsi_status app_columns_t(fsi_ctx* c) {
   const long lvl = c->lvl_elems;
   void *tw = nullptr, *ts = nullptr;
-  if (cudaMalloc(&tw, lvl * c->esz) != cudaSuccess || cudaMalloc(&ts, lvl * c->esz) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&tw, lvl * c->esz) != cudaSuccess || ctx_dev_malloc(c, (void**)&ts, lvl * c->esz) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(tw);
+    ctx_dev_free(c, tw);
     return FSI_ERR_OOM;
   }
   fsi_status st = FSI_OK;
@@ -178,8 +178,8 @@ fsi_status app_columns_t(fsi_ctx* c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess && st == FSI_OK) st = FSI_ERR_CUDA;
   if (cudaMemsetAsync(c->src, 0, lvl * c->esz, c->stream) != cudaSuccess && st == FSI_OK) st = FSI_ERR_CUDA;
   cudaStreamSynchronize(c->stream);
-  cudaFree(tw);
-  cudaFree(ts);
+  ctx_dev_free(c, tw);
+  ctx_dev_free(c, ts);
   return st;
 }
 
@@ -190,9 +190,9 @@ fsi_status setup_appended(fsi_ctx* c) {
   double* d_pts = nullptr;
   int* d_bad = nullptr;
   if (!(c->d_app_win = (FaceWindow*)ctx_alloc(c, (size_t)c->n_app * sizeof(FaceWindow)))) return FSI_ERR_OOM;
-  if (cudaMalloc(&d_pts, c->app_pts.size() * 8) != cudaSuccess || cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&d_pts, c->app_pts.size() * 8) != cudaSuccess || ctx_dev_malloc(c, (void**)&d_bad, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(d_pts);
+    ctx_dev_free(c, d_pts);
     return FSI_ERR_OOM;
   }
   int bad = 0;
@@ -208,8 +208,8 @@ fsi_status setup_appended(fsi_ctx* c) {
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       st = FSI_ERR_CUDA;
   }
-  cudaFree(d_pts);
-  cudaFree(d_bad);
+  ctx_dev_free(c, d_pts);
+  ctx_dev_free(c, d_bad);
   if (st != FSI_OK) return st;
   if (bad) {
     fsi_set_last_message("appended body point closer than 2 cells to the grid boundary");
@@ -238,7 +238,7 @@ fsi_status build_appended_b0(fsi_ctx* c) {
   double* full = c->B0;
   double* box = nullptr;
   const size_t nb2 = 2 * (size_t)c->n_box;
-  if (cudaMalloc(&box, nb2 * nb2 * 8) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&box, nb2 * nb2 * 8) != cudaSuccess) {
     cudaGetLastError();
     return FSI_ERR_OOM;
   }
@@ -250,7 +250,7 @@ fsi_status build_appended_b0(fsi_ctx* c) {
     k_expand<<<1024, 256, 0, c->stream>>>(full, box, c->n_box, c->n_sd);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   }
-  cudaFree(box);
+  ctx_dev_free(c, box);
   if (st != FSI_OK) return st;
   st = c->prec == FSI_PREC_FP64 ? app_columns_t<double>(c) : app_columns_t<float>(c);
   c->b0_seconds = secs;

@@ -256,11 +256,11 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
   B0Box* d_bx = nullptr;
   fsi_status st = FSI_OK;
   do {
-    if (cudaMalloc(&d_twx, twx.size() * 8) != cudaSuccess || cudaMalloc(&d_twy, twy.size() * 8) != cudaSuccess ||
-        cudaMalloc(&d_T1, (size_t)Nx * (My + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&d_g, (size_t)(Mx + 1) * (My + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&d_tab, (size_t)tab_n * 8) != cudaSuccess ||
-        cudaMalloc(&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
+    if (ctx_dev_malloc(c, (void**)&d_twx, twx.size() * 8) != cudaSuccess || ctx_dev_malloc(c, (void**)&d_twy, twy.size() * 8) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_T1, (size_t)Nx * (My + 1) * 8) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_g, (size_t)(Mx + 1) * (My + 1) * 8) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_tab, (size_t)tab_n * 8) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
       cudaGetLastError();
       st = FSI_ERR_OOM;
       break;
@@ -281,15 +281,15 @@ fsi_status b0_green_tables(fsi_ctx* c, std::vector<B0Box>& boxes, double** tab_o
     k_tables<<<dim3((unsigned)((max_tab + 127) / 128), nb), 128, 0, c->stream>>>(d_tab, d_bx, d_g, Mx, My, h);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
-  cudaFree(d_twx);
-  cudaFree(d_twy);
-  cudaFree(d_T1);
-  cudaFree(d_g);
-  cudaFree(d_bx);
+  ctx_dev_free(c, d_twx);
+  ctx_dev_free(c, d_twy);
+  ctx_dev_free(c, d_T1);
+  ctx_dev_free(c, d_g);
+  ctx_dev_free(c, d_bx);
   if (st == FSI_OK) {
     *tab_out = d_tab;
   } else {
-    cudaFree(d_tab);
+    ctx_dev_free(c, d_tab);
   }
   return st;
 }
@@ -309,8 +309,8 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
       off[k + 1] = off[k] + 4L * boxes[k].nj * boxes[k].nj;
       if (boxes[k].ni > max_ni) max_ni = boxes[k].ni;
     }
-    if (cudaMalloc(&d_off, (size_t)(nb + 1) * sizeof(long)) != cudaSuccess ||
-        cudaMalloc(&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
+    if (ctx_dev_malloc(c, (void**)&d_off, (size_t)(nb + 1) * sizeof(long)) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_bx, (size_t)nb * sizeof(B0Box)) != cudaSuccess) {
       cudaGetLastError();
       st = FSI_ERR_OOM;
       break;
@@ -327,9 +327,9 @@ fsi_status b0_green(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     k_fill<<<(unsigned)off[nb], 256, sm, c->stream>>>(out, d_tab, d_bx, d_off, nb);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
   } while (0);
-  cudaFree(d_tab);
-  cudaFree(d_bx);
-  cudaFree(d_off);
+  ctx_dev_free(c, d_tab);
+  ctx_dev_free(c, d_bx);
+  ctx_dev_free(c, d_off);
   return st;
 }
 
@@ -344,7 +344,7 @@ fsi_status build_b0(fsi_ctx* c) {
       k_fill_union<<<(unsigned)(2L * c->n_sd), 256, 0, c->stream>>>(c->B0, d_tab, one[0], c->n_sd, c->d_sd_vert);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
     }
-    cudaFree(d_tab);
+    ctx_dev_free(c, d_tab);
     c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st;
   }

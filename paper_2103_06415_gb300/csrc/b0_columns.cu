@@ -124,12 +124,12 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
   T *src = nullptr, *T1 = nullptr, *T2w = nullptr, *T2s = nullptr, *fw = nullptr, *fs = nullptr;
   B0Box* d_bx = nullptr;
   fsi_status st = FSI_OK;
-  if (cudaMalloc(&d_bx, (size_t)n_boxes * sizeof(B0Box)) != cudaSuccess || cudaMalloc(&src, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&T1, (size_t)B * t1 * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&T2w, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&T2s, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&fw, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&fs, (size_t)B * lvl * sizeof(T)) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&d_bx, (size_t)n_boxes * sizeof(B0Box)) != cudaSuccess || ctx_dev_malloc(c, (void**)&src, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&T1, (size_t)B * t1 * sizeof(T)) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&T2w, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&T2s, (size_t)B * t2 * sizeof(T)) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&fw, (size_t)B * lvl * sizeof(T)) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&fs, (size_t)B * lvl * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     st = FSI_ERR_OOM;
   } else if (cudaMemcpyAsync(d_bx, boxes.data(), (size_t)n_boxes * sizeof(B0Box), cudaMemcpyHostToDevice,
@@ -175,13 +175,13 @@ fsi_status columns_t(fsi_ctx* c, std::vector<B0Box>& boxes, double* out) {
     if (cudaGetLastError() != cudaSuccess) st = FSI_ERR_CUDA;
   }
   if (st == FSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = FSI_ERR_CUDA;
-  cudaFree(src);
-  cudaFree(T1);
-  cudaFree(T2w);
-  cudaFree(T2s);
-  cudaFree(fw);
-  cudaFree(fs);
-  cudaFree(d_bx);
+  ctx_dev_free(c, src);
+  ctx_dev_free(c, T1);
+  ctx_dev_free(c, T2w);
+  ctx_dev_free(c, T2s);
+  ctx_dev_free(c, fw);
+  ctx_dev_free(c, fs);
+  ctx_dev_free(c, d_bx);
   return st;
 }
 

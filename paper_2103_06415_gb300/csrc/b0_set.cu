@@ -91,8 +91,8 @@ extern "C" fsi_status fsi_b0_set_entries(fsi_b0_set* s, int box, const int64_t* 
   int64_t *dr = nullptr, *dc = nullptr;
   double* dout = nullptr;
   fsi_status st = FSI_OK;
-  if (cudaMalloc(&dr, n * 8) != cudaSuccess || cudaMalloc(&dc, n * 8) != cudaSuccess ||
-      cudaMalloc(&dout, n * 8) != cudaSuccess) {
+  if (ctx_dev_malloc(s->c, (void**)&dr, n * 8) != cudaSuccess || ctx_dev_malloc(s->c, (void**)&dc, n * 8) != cudaSuccess ||
+      ctx_dev_malloc(s->c, (void**)&dout, n * 8) != cudaSuccess) {
     cudaGetLastError();
     st = FSI_ERR_OOM;
   } else if (cudaMemcpyAsync(dr, rows, n * 8, cudaMemcpyHostToDevice, st_) != cudaSuccess ||
@@ -104,9 +104,9 @@ extern "C" fsi_status fsi_b0_set_entries(fsi_b0_set* s, int box, const int64_t* 
         cudaStreamSynchronize(st_) != cudaSuccess)
       st = FSI_ERR_CUDA;
   }
-  cudaFree(dr);
-  cudaFree(dc);
-  cudaFree(dout);
+  ctx_dev_free(s->c, dr);
+  ctx_dev_free(s->c, dc);
+  ctx_dev_free(s->c, dout);
   return st;
 }
 

@@ -125,8 +125,8 @@ fsi_status build_b0_window(fsi_ctx* c, double drop_tol) {
   int* d_ext = nullptr;
   unsigned long long* d_nnz = nullptr;
   do {
-    if (cudaMalloc(&d_ext, 2 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&d_nnz, sizeof(unsigned long long)) != cudaSuccess) {
+    if (ctx_dev_malloc(c, (void**)&d_ext, 2 * sizeof(int)) != cudaSuccess ||
+        ctx_dev_malloc(c, (void**)&d_nnz, sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       st = FSI_ERR_OOM;
       break;
@@ -172,9 +172,9 @@ fsi_status build_b0_window(fsi_ctx* c, double drop_tol) {
     c->bw = w;
     c->b0_nnz = (long long)nnz;
   } while (0);
-  cudaFree(d_tab);
-  cudaFree(d_ext);
-  cudaFree(d_nnz);
+  ctx_dev_free(c, d_tab);
+  ctx_dev_free(c, d_ext);
+  ctx_dev_free(c, d_nnz);
   c->b0_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return st;
 }

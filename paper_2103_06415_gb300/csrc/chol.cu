@@ -157,12 +157,12 @@ extern "C" fsi_status fsi_factor_operator(fsi_ctx* c, double tau_rel, double* ta
     if (!c->d_factor) return FSI_ERR_OOM;
   }
   double* d_max = nullptr;
-  FSI_CUDA_TRY(cudaMalloc(&d_max, sizeof(double)));
+  FSI_CUDA_TRY(ctx_dev_malloc(c, (void**)&d_max, sizeof(double)));
   k_max_diag<<<1, 256, 0, c->stream>>>(c->B0, n, d_max);
   double dmax = 0.0;
   cudaError_t e = cudaMemcpyAsync(&dmax, d_max, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(d_max);
+  ctx_dev_free(c, d_max);
   FSI_CUDA_TRY(e);
   const double tau = tau_rel * dmax;
   const size_t sm2 = (size_t)2 * NB * (NB + 1) * sizeof(double);
@@ -204,8 +204,8 @@ extern "C" fsi_status fsi_get_factor_entries(fsi_ctx* c, const int64_t* rows, co
   int64_t *dr = nullptr, *dc = nullptr;
   double* dout = nullptr;
   fsi_status st = FSI_OK;
-  if (cudaMalloc(&dr, n * 8) != cudaSuccess || cudaMalloc(&dc, n * 8) != cudaSuccess ||
-      cudaMalloc(&dout, n * 8) != cudaSuccess) {
+  if (ctx_dev_malloc(c, (void**)&dr, n * 8) != cudaSuccess || ctx_dev_malloc(c, (void**)&dc, n * 8) != cudaSuccess ||
+      ctx_dev_malloc(c, (void**)&dout, n * 8) != cudaSuccess) {
     st = FSI_ERR_OOM;
   } else if (cudaMemcpyAsync(dr, rows, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
              cudaMemcpyAsync(dc, cols, n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
@@ -216,8 +216,8 @@ extern "C" fsi_status fsi_get_factor_entries(fsi_ctx* c, const int64_t* rows, co
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       st = FSI_ERR_CUDA;
   }
-  cudaFree(dr);
-  cudaFree(dc);
-  cudaFree(dout);
+  ctx_dev_free(c, dr);
+  ctx_dev_free(c, dc);
+  ctx_dev_free(c, dout);
   return st;
 }

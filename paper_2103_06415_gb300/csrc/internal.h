@@ -220,7 +220,7 @@ struct fsi_ctx {
   double dst_us[2][3];
   struct GemmDst* gd;
   size_t dev_bytes;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;  // buffers held for the context's lifetime (through ctx_dev_malloc)
 };
 
 // One Omega_0 box of a B0 build.  Several boxes on one grid are built together; their matrices are stored
@@ -353,6 +353,11 @@ fsi_status gemm_ysolve(fsi_ctx* c, const dst::SpecParams<float>& sp);
 fsi_status gemm_xi(fsi_ctx* c, float* fw, float* fs, int mode);
 
 void* ctx_alloc(fsi_ctx* c, size_t bytes);
+// One device buffer through the context's allocator (fsi_exec_desc.dev_alloc) or cudaMalloc; returned by
+// ctx_dev_free (NULL is a no-op).  cudaErrorMemoryAllocation when the allocator gives nothing or a pointer
+// that is not 256-byte aligned.
+cudaError_t ctx_dev_malloc(const fsi_ctx* c, void** p, size_t bytes);
+void ctx_dev_free(const fsi_ctx* c, void* p);
 
 // kernel classes for fsi_profile_kernel
 enum { KC_NONE = 0, KC_XF = 1, KC_YSOLVE = 2, KC_XI = 3, KC_FSI = 4, KC_RHS = 5, KC_SRC = 6, KC_RING = 7 };
