@@ -319,35 +319,75 @@ def run_serving(n_req):
     from paper_2103_06415_gb300 import workloads as wl
     _b.build()
     import paper_2103_06415_gb300 as lib
+    from paper_2103_06415_gb300 import serving
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     reqs = wl.serving_requests(n_req, steps=(200, 400))
+    if world > 1:  # disjoint shares of the one stream, no collective on the data path
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+        dist.barrier()
+    mine = serving.partition_requests(reqs, world, rank)
     srv = lib.Server(200 << 30)
     t0 = time.perf_counter()
     k, res, max_active = 0, [], 0
     while True:
         now = time.perf_counter() - t0
-        while k < len(reqs) and reqs[k][0] <= now:
-            _, w, b, n = reqs[k]
-            srv.submit(w, b, n, precision=lib.FSI_PREC_FP32, tag=k)
+        while k < len(mine) and reqs[mine[k]][0] <= now:
+            _, w, b, n = reqs[mine[k]]
+            srv.submit(w, b, n, precision=lib.FSI_PREC_FP32, tag=mine[k])
             k += 1
         n_active = srv.step()
         max_active = max(max_active, n_active)
         res += srv.poll()
-        if k == len(reqs) and n_active == 0 and srv.stats()["queued"] == 0:
+        if k == len(mine) and n_active == 0 and srv.stats()["queued"] == 0:
             break
-        if n_active == 0 and k < len(reqs):
-            time.sleep(max(0.0, reqs[k][0] - (time.perf_counter() - t0)))
+        if n_active == 0 and k < len(mine):
+            time.sleep(max(0.0, reqs[mine[k]][0] - (time.perf_counter() - t0)))
     wall = time.perf_counter() - t0
     st = srv.stats()
-    p50 = [r["p50_step_ms"] for r in res]
-    p99 = [r["p99_step_ms"] for r in res]
-    out = {"metric": "serving: aggregate FSI cell-steps/s and per-step latency (Poisson stream of plate runs)",
-           "requests": n_req, "finished": len(res), "errors": sum(r["status"] != 0 for r in res),
-           "wall_s": wall, "cell_steps": st["cell_steps"], "value": st["cell_steps"] / wall,
-           "unit": "cell-steps/s", "max_active": max_active, "ticks": st["ticks"],
-           "p50_step_ms": float(np.median(p50)), "p99_step_ms": float(np.percentile(p99, 99)),
-           "mean_wait_ms": float(np.mean([r["wait_ms"] for r in res])), "dtype": "f32 fluid / f64 FSI"}
-    print(json.dumps(out), flush=True)
+    local = {"cell_steps": st["cell_steps"], "wall": wall, "finished": len(res),
+             "errors": sum(r["status"] != 0 for r in res), "max_active": max_active, "ticks": st["ticks"],
+             "p50": [r["p50_step_ms"] for r in res], "p99": [r["p99_step_ms"] for r in res],
+             "wait": [r["wait_ms"] for r in res]}
     srv.close()
+    parts = gather_serving(local, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    agg = aggregate_serving(parts)
+    out = {"metric": "serving: aggregate FSI cell-steps/s and per-step latency (Poisson stream of plate runs)",
+           "requests": n_req, "n_gpus": world, "finished": agg["finished"], "errors": agg["errors"],
+           "wall_s": agg["wall"], "cell_steps": agg["cell_steps"], "value": agg["value"],
+           "unit": "cell-steps/s", "max_active": agg["max_active"], "ticks": agg["ticks"],
+           "p50_step_ms": float(np.median(agg["p50"])), "p99_step_ms": float(np.percentile(agg["p99"], 99)),
+           "mean_wait_ms": float(np.mean(agg["wait"])), "dtype": "f32 fluid / f64 FSI",
+           "partition": "requests by decreasing cell-steps to the least-loaded rank (no data-path collective)"}
+    print(json.dumps(out), flush=True)
+
+
+def gather_serving(local, world):
+    """Every rank's serving record on every rank (torch.distributed object gather; the records only)."""
+    if world == 1:
+        return [local]
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, local)
+    return parts
+
+
+def aggregate_serving(parts):
+    """Whole-job figures from the ranks' records: work summed, time the slowest rank's, latencies pooled."""
+    wall = max(p["wall"] for p in parts)
+    cs = sum(p["cell_steps"] for p in parts)
+    return {"wall": wall, "cell_steps": cs, "value": cs / wall, "finished": sum(p["finished"] for p in parts),
+            "errors": sum(p["errors"] for p in parts), "max_active": max(p["max_active"] for p in parts),
+            "ticks": sum(p["ticks"] for p in parts), "p50": [x for p in parts for x in p["p50"]],
+            "p99": [x for p in parts for x in p["p99"]], "wait": [x for p in parts for x in p["wait"]]}
 
 
 def run_comparator(args, timed_steps):

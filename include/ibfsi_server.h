@@ -15,8 +15,12 @@
 extern "C" {
 #endif
 
-/* One run: grid (Sec. 2.2, Sec. 5), one torsional body (Sec. 2.1; other body types return UNSUPPORTED),
- * one sub-domain box (Sec. 3.1.1), the compute precision, the number of steps and a caller tag. */
+/* One run: grid (Sec. 2.2, Sec. 5), one torsional or deformable body (Sec. 2.1, App. A; other types return
+ * UNSUPPORTED), one sub-domain box (Sec. 3.1.1), the compute precision, the number of steps and a caller tag.
+ * history_out: NULL, or a host array of n_steps x 6 doubles that the server fills when the run retires with
+ * its per-step history (fx, fy, moment, deflection and its rate as fsi_get_history's fields 0-4, FSI
+ * iterations; oldest first; rows past the steps done are left as they were).  The caller keeps it valid
+ * until the run's result has been polled. */
 typedef struct {
   fsi_grid_desc grid;
   fsi_body_desc body;
@@ -24,6 +28,7 @@ typedef struct {
   int precision;
   int n_steps;
   uint64_t tag;
+  double* history_out;
 } fsi_request;
 
 /* Result of a finished run.  status: FSI_OK or the first error of the run.  Forces and deflection of the
@@ -39,6 +44,7 @@ typedef struct {
 
 typedef struct {
   int queued, active, finished;
+  int admitting;     /* admitted runs whose context and B0 are being built (counted in bytes_in_use) */
   size_t bytes_in_use;
   long long ticks, run_steps;
   double cell_steps; /* sum over run steps of levels x nx x ny */
@@ -52,8 +58,12 @@ typedef struct fsi_server fsi_server;
 fsi_status fsi_server_create(size_t hbm_budget_bytes, int max_active, fsi_server** out);
 /* Queue a request (copied); *id receives its id.  FSI_ERR_OOM if it can never fit the budget. */
 fsi_status fsi_server_submit(fsi_server* s, const fsi_request* req, uint64_t* id);
-/* One tick: admit what fits (context + B0 precompute), advance every active run by one step, retire runs
- * that are done.  *n_active receives the number of runs still resident (may be NULL). */
+/* One tick: admit what fits, advance every active run by one step, retire runs that are done.  Admission
+ * (context creation and the B0 precompute of Algorithm 1 on the run's own stream) runs on a host worker
+ * thread of the server, so resident runs keep stepping while a newcomer's operator is built; a run joins
+ * the active set at the first tick after its admission completed (when no run is active, the tick waits for
+ * the next admission instead of returning at once).  *n_active receives the number of resident runs,
+ * active or being admitted (may be NULL). */
 fsi_status fsi_server_step(fsi_server* s, int* n_active);
 /* Move up to cap finished results to out; *n receives the count. */
 fsi_status fsi_server_poll(fsi_server* s, fsi_result* out, int cap, int* n);

@@ -377,18 +377,29 @@ class Server:
         h = ctypes.c_void_p()
         check(self._lib.fsi_server_create(int(hbm_budget_bytes), max_active, ctypes.byref(h)), "fsi_server_create")
         self._h = h
+        self._hist = {}   # run id -> history array the server fills at retirement (kept alive until polled)
 
-    def submit(self, w, body, n_steps, precision=FSI_PREC_FP32, tag=0):
-        """w: grid/sub-domain description (workloads dict keys); body: torsional body dict."""
+    def submit(self, w, body, n_steps, precision=FSI_PREC_FP32, tag=0, history=False):
+        """w: grid/sub-domain description (workloads dict keys); body: a torsional body dict (kind "torsional",
+        the default) or a deformable one (kind "deformable": clamp, theta0, mass, ei, ea, tip_angle).  history:
+        the poll result then carries the run's per-step history [n_steps, 6]."""
         g = _lib.GridDesc(w["nx"], w["ny"], w["n_levels"], w["x0"], w["y0"], w["h"], w["re"], w["dt"],
                           (ctypes.c_double * 2)(*w["uinf"]))
-        b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, body["n_pts"], w["ds"], (ctypes.c_double * 2)(*body["hinge"]),
-                          body["theta0"], body["theta"], 0.0, body["inertia"], body["damping"], body["stiffness"],
-                          None, None)
+        if body.get("kind", "torsional") == "deformable":
+            b = _lib.BodyDesc(_lib.FSI_BODY_DEFORMABLE, body["n_pts"], w["ds"], (ctypes.c_double * 2)(*body["clamp"]),
+                              body["theta0"], body["tip_angle"], 0.0, 0.0, 0.0, 0.0, None, None, body["mass"],
+                              body["ei"], body["ea"])
+        else:
+            b = _lib.BodyDesc(_lib.FSI_BODY_TORSIONAL, body["n_pts"], w["ds"], (ctypes.c_double * 2)(*body["hinge"]),
+                              body["theta0"], body["theta"], 0.0, body["inertia"], body["damping"], body["stiffness"],
+                              None, None)
         box = _lib.Box(*w["sd_box"])
-        req = _lib.Request(g, b, box, precision, n_steps, tag)
+        out = np.full((n_steps, 6), np.nan) if history else None
+        req = _lib.Request(g, b, box, precision, n_steps, tag, _dp(out) if history else None)
         rid = ctypes.c_uint64()
         check(self._lib.fsi_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)), "fsi_server_submit")
+        if history:
+            self._hist[rid.value] = out
         return rid.value
 
     def step(self):
@@ -400,7 +411,12 @@ class Server:
         buf = (_lib.Result * cap)()
         n = ctypes.c_int()
         check(self._lib.fsi_server_poll(self._h, buf, cap, ctypes.byref(n)), "fsi_server_poll")
-        return [{k: getattr(buf[i], k) for k, _ in _lib.Result._fields_} for i in range(n.value)]
+        out = [{k: getattr(buf[i], k) for k, _ in _lib.Result._fields_} for i in range(n.value)]
+        for r in out:
+            hist = self._hist.pop(r["id"], None)
+            if hist is not None:
+                r["history"] = hist[: r["steps"]]
+        return out
 
     def stats(self):
         s = _lib.ServerStats()

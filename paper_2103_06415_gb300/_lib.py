@@ -152,7 +152,7 @@ def check(code, where):
 
 class Request(ctypes.Structure):
     _fields_ = [("grid", GridDesc), ("body", BodyDesc), ("box", Box), ("precision", ctypes.c_int),
-                ("n_steps", ctypes.c_int), ("tag", ctypes.c_uint64)]
+                ("n_steps", ctypes.c_int), ("tag", ctypes.c_uint64), ("history_out", ctypes.POINTER(ctypes.c_double))]
 
 
 class Result(ctypes.Structure):
@@ -165,7 +165,7 @@ class Result(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("finished", ctypes.c_int),
-                ("bytes_in_use", ctypes.c_size_t), ("ticks", ctypes.c_longlong), ("run_steps", ctypes.c_longlong),
+                ("admitting", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t), ("ticks", ctypes.c_longlong), ("run_steps", ctypes.c_longlong),
                 ("cell_steps", ctypes.c_double), ("busy_ms", ctypes.c_double)]
 
 

@@ -15,6 +15,7 @@
 // kernel.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <vector>
 #include "dst.cuh"
 #include "internal.h"
@@ -78,15 +79,14 @@ fsi_status launch_dct1(const double* in, long in_rs, long in_es, int nrows, int 
   const int per = P / (4 * nthr);
   const size_t sm = dst::pass_smem<double>((size_t)L, L);
   const dim3 grid((nrows + 1) / 2);
-  static bool attrs = false;
-  if (!attrs) {
-    attrs = true;
+  static std::once_flag attrs;  // contexts may be built on several host threads (the server's worker)
+  std::call_once(attrs, [] {
     cudaFuncSetAttribute(k_dct1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dct1<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  }
+  });
   if (r3 == 3) {
     if (per == 1) k_dct1<1, 3><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re);
     else if (per == 2) k_dct1<2, 3><<<grid, nthr, sm, st>>>(in, in_rs, in_es, nrows, M, out, out_rs, out_es, tw, logL, scale, lx, ly, inv_h2, inv_dt, inv_2re);

@@ -2,6 +2,7 @@
 // multidomain coupling (Sec. 5, far-field multidomain), the DST-diagonalised predictor solves
 // (Eq. predictor2) and the corrector (Eq. corrector2) with its surface-stress source.
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 #include "spec.cuh"
 
@@ -42,11 +43,17 @@ FftCfg fft_cfg(int logP, int r3) {
     }                                                 \
   } while (0)
 
+template <typename T, typename TF>
+void set_smem_limits_once();
+
 template <typename T, typename TF = T>
 void set_smem_limits() {
-  static bool done = false;
-  if (done) return;
-  done = true;
+  static std::once_flag once;  // contexts may run on several host threads (the server's worker)
+  std::call_once(once, set_smem_limits_once<T, TF>);
+}
+
+template <typename T, typename TF>
+void set_smem_limits_once() {
   const int big = 200 * 1024;
   cudaFuncSetAttribute(dst::k_xf<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(dst::k_xf<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -529,16 +536,15 @@ fsi_status ring_spectra_t(fsi_ctx* c, int g, int delta) {
   const size_t sm = dst::pass_smem<T>((size_t)4 * per * 256 * r3max, Lx > Ly ? Lx : Ly);
   const c2* twx = (const c2*)c->twx;
   const c2* twy = (const c2*)c->twy;
-  static bool attrs = false;  // per instantiation
-  if (!attrs) {
-    attrs = true;
+  static std::once_flag attrs;  // per instantiation; contexts may run on several host threads
+  std::call_once(attrs, [] {
     cudaFuncSetAttribute(k_ring_dst<T, 1, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_ring_dst<T, 1, TF, 1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  }
+  });
   prof_mark(c, KC_RING);
   const dim3 grid(nblk_y + nblk_x);
 #define RING_LAUNCH(P, RX, RY) FSI_CUDA_TRY(pdl_launch(k_ring_dst<T, P, TF, RX, RY>, grid, dim3(256), sm, c->stream, wf, sf, wc, sc, c->ps, c->nx, c->ny, (T*)c->ring, c->ring_ld, twx, twy, c->logPx, c->logPy, nblk_y, delta))

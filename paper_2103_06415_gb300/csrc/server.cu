@@ -3,18 +3,25 @@
 // The paper notes that a precomputed B' is reusable across parametric studies (Sec. 3.4); a serving loop
 // turns that into throughput: many runs (different grids, Re, structural parameters) are resident at once.
 // Each tick of fsi_server_step
-//   1. admits queued requests in arrival order while their predicted device footprint fits the HBM budget
-//      (a context, its B0 precompute and a CUDA stream of its own),
+//   1. takes the runs whose admission completed into the active set, and hands queued requests, in arrival
+//      order, to the admission worker while their predicted device footprint fits the HBM budget; the worker
+//      (a host thread of the server) creates each context on a CUDA stream of its own and runs its B0
+//      precompute there, so the resident runs keep stepping meanwhile,
 //   2. enqueues one time step of every active run on its own stream (captured CUDA graph), bracketed by a
 //      pair of events, so the runs' kernels overlap on the device,
 //   3. waits for the tick, records each run's step time, and retires runs that reached their step count,
-//      keeping their results (forces, deflection, per-step latency percentiles) for fsi_server_poll.
-// Runs never share device buffers, so a run gives the same bits alone and in the mix.
+//      keeping their results (forces, deflection, per-step latency percentiles, optionally the whole
+//      history) for fsi_server_poll.
+// Runs never share device buffers, so a run gives the same bits alone and in the mix.  Graph capture is
+// thread-local, so the worker's CUDA calls do not interfere with a capture on the tick's thread.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <deque>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 #include "internal.h"
 #include "../../include/ibfsi_server.h"
@@ -48,6 +55,14 @@ struct fsi_server {
   long long ticks = 0, steps = 0;
   double cell_steps = 0.0;
   double busy_ms = 0.0;
+  // admission worker: runs handed over (to_admit), runs whose context and B0 are built (admitted_runs);
+  // admitting = handed over and not yet taken back by a tick
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Run*> to_admit, admitted_runs;
+  int admitting = 0;
+  bool stop = false;
+  std::thread worker;
 };
 
 // Device bytes a request will hold: per-level fields and transform scratch, B0 and the FSI workspace.
@@ -70,6 +85,7 @@ static size_t predict_bytes(const fsi_request* r) {
   b += 4 * nsd * nsd * 8;                               // B0 (2 n_sd)^2 doubles
   const size_t nf = 2 * (size_t)r->body.n_pts;
   b += nf * nf * (8 + 12) + 64 * 1024;                  // K, float inverses, small buffers
+  if (r->body.type == FSI_BODY_DEFORMABLE) b += nf * nf * 8 + 64 * (size_t)r->body.n_pts;  // T J_d^-1 T^T, state
   return b;
 }
 
@@ -82,6 +98,14 @@ static void retire(fsi_server* s, Run* r) {
   if (r->ctx && r->status == FSI_OK) {
     fsi_status st = fsi_get_forces(r->ctx, 0, &out.fx, &out.fy, &out.moment);
     if (st == FSI_OK) st = fsi_get_deflection(r->ctx, 0, &out.theta, &out.phi);
+    if (st == FSI_OK && r->req.history_out && r->done > 0) {  // rows [step][field] from the history ring
+      std::vector<double> col(r->done);
+      for (int f = 0; f < 6 && st == FSI_OK; ++f) {
+        int n = 0;
+        st = fsi_get_history(r->ctx, 0, f, col.data(), r->done, &n);
+        for (int k = 0; k < n && st == FSI_OK; ++k) r->req.history_out[(long)k * 6 + f] = col[k];
+      }
+    }
     out.status = st;
   }
   std::vector<float> v = r->step_ms;
@@ -115,7 +139,7 @@ static fsi_status admit(fsi_server* s, Run* r) {
   x.precision = r->req.precision;
   x.stream = r->stream;
   x.use_graph = 1;
-  x.history_cap = 16;
+  x.history_cap = r->req.history_out ? std::max(16, r->req.n_steps) : 16;
   fsi_status st = fsi_create(&r->req.grid, &x, &r->ctx);
   int bid = 0;
   if (st == FSI_OK) st = fsi_add_body(r->ctx, &r->req.body, &bid);
@@ -124,12 +148,40 @@ static fsi_status admit(fsi_server* s, Run* r) {
   return st;
 }
 
+// The admission worker: builds every handed-over run (context, body, sub-domain, B0) on the run's stream and
+// hands it back with its status.
+static void admission_worker(fsi_server* s) {
+  for (;;) {
+    Run* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [s] { return s->stop || !s->to_admit.empty(); });
+      if (s->stop && s->to_admit.empty()) return;
+      r = s->to_admit.front();
+      s->to_admit.pop_front();
+    }
+    const fsi_status st = admit(s, r);
+    if (st != FSI_OK) r->status = st;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->admitted_runs.push_back(r);
+    }
+    s->cv_done.notify_all();
+  }
+}
+
 extern "C" fsi_status fsi_server_create(size_t hbm_budget_bytes, int max_active, fsi_server** out) {
   if (!out || hbm_budget_bytes == 0) return FSI_ERR_INVALID_ARG;
   fsi_server* s = new (std::nothrow) fsi_server();
   if (!s) return FSI_ERR_OOM;
   s->budget = hbm_budget_bytes;
   s->max_active = max_active > 0 ? max_active : 1 << 20;
+  try {
+    s->worker = std::thread(admission_worker, s);
+  } catch (...) {
+    delete s;
+    return FSI_ERR_OOM;
+  }
   *out = s;
   return FSI_OK;
 }
@@ -141,9 +193,9 @@ extern "C" fsi_status fsi_server_submit(fsi_server* s, const fsi_request* req, u
   if (!r) return FSI_ERR_OOM;
   r->id = s->next_id++;
   r->req = *req;
-  r->req.body.pts = nullptr;  // only torsional bodies are served (no host arrays to keep)
+  r->req.body.pts = nullptr;  // torsional and deformable bodies are served (no host arrays to keep)
   r->req.body.ur = nullptr;
-  if (req->body.type != FSI_BODY_TORSIONAL) {
+  if (req->body.type != FSI_BODY_TORSIONAL && req->body.type != FSI_BODY_DEFORMABLE) {
     delete r;
     return FSI_ERR_UNSUPPORTED;
   }
@@ -161,19 +213,33 @@ extern "C" fsi_status fsi_server_submit(fsi_server* s, const fsi_request* req, u
 extern "C" fsi_status fsi_server_step(fsi_server* s, int* n_active) {
   if (!s) return FSI_ERR_INVALID_ARG;
   NvtxRange range("fsi_server_step");
-  // 1. admission in arrival order while the budget allows
-  while (!s->queue.empty() && (int)s->active.size() < s->max_active &&
-         s->in_use + s->queue.front()->bytes <= s->budget) {
-    Run* r = s->queue.front();
-    s->queue.pop_front();
-    s->in_use += r->bytes;
-    const fsi_status st = admit(s, r);
-    if (st != FSI_OK) {
-      r->status = st;
-      retire(s, r);
-      continue;
+  // 1. hand queued requests to the admission worker in arrival order while the budget allows
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    while (!s->queue.empty() && (int)s->active.size() + s->admitting < s->max_active &&
+           s->in_use + s->queue.front()->bytes <= s->budget) {
+      Run* r = s->queue.front();
+      s->queue.pop_front();
+      s->in_use += r->bytes;
+      s->to_admit.push_back(r);
+      s->admitting += 1;
     }
-    s->active.push_back(r);
+  }
+  s->cv_work.notify_one();
+  //    and take the admitted runs into the active set (with no active run, wait for the next one)
+  std::deque<Run*> ready;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->active.empty() && s->admitting > 0)
+      s->cv_done.wait(lk, [s] { return !s->admitted_runs.empty(); });
+    ready.swap(s->admitted_runs);
+    s->admitting -= (int)ready.size();
+  }
+  for (Run* r : ready) {
+    if (r->status != FSI_OK)
+      retire(s, r);
+    else
+      s->active.push_back(r);
   }
   // 2. one step of every active run, each on its own stream
   auto t0 = clk::now();
@@ -210,7 +276,10 @@ extern "C" fsi_status fsi_server_step(fsi_server* s, int* n_active) {
   s->active.swap(keep);
   s->busy_ms += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
   s->ticks += 1;
-  if (n_active) *n_active = (int)s->active.size();
+  if (n_active) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    *n_active = (int)s->active.size() + s->admitting;
+  }
   return FSI_OK;
 }
 
@@ -229,6 +298,10 @@ extern "C" fsi_status fsi_server_get_stats(fsi_server* s, fsi_server_stats* out)
   if (!s || !out) return FSI_ERR_INVALID_ARG;
   out->queued = (int)s->queue.size();
   out->active = (int)s->active.size();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->admitting = s->admitting;
+  }
   out->finished = (int)s->results.size();
   out->bytes_in_use = s->in_use;
   out->ticks = s->ticks;
@@ -240,6 +313,14 @@ extern "C" fsi_status fsi_server_get_stats(fsi_server* s, fsi_server_stats* out)
 
 extern "C" void fsi_server_destroy(fsi_server* s) {
   if (!s) return;
+  {  // the worker finishes what it was handed, then stops
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (Run* r : s->admitted_runs) s->active.push_back(r);
+  s->admitted_runs.clear();
   for (Run* r : s->active) retire(s, r);
   s->active.clear();
   while (!s->queue.empty()) {

@@ -73,3 +73,78 @@ def test_admission_respects_the_hbm_budget():
     assert len(res) == 4 and all(r["status"] == 0 for r in res)
     waits = sorted(r["wait_ms"] for r in res)
     assert waits[-1] > waits[0]
+
+
+def _solo_history(w, body, n, precision):
+    import paper_2103_06415_gb300 as p
+    ctx = gpu_context(dict(w, bodies=[body]), precision=precision)
+    ctx.advance(n)
+    h = ctx.history(0)
+    ctx.close()
+    return h
+
+
+def test_run_admitted_while_others_step_keeps_every_history_bitwise():
+    """Two runs start; a third is submitted after they have stepped five times and admitted while they keep
+    stepping.  Every run's whole history equals the same run's on a context of its own, bit for bit."""
+    import paper_2103_06415_gb300 as p
+    reqs = wl.serving_requests(3, seed=7, sizes=(128, 256), steps=(24, 30))
+    srv = p.Server(64 << 30)
+    ids = {}
+    for k, (_, w, b, n) in enumerate(reqs[:2]):
+        ids[srv.submit(w, b, n, tag=k, history=True)] = k
+    res = []
+    for _ in range(5):
+        srv.step()
+        res += srv.poll()
+    st = srv.stats()
+    assert st["active"] == 2 and not res
+    _, w3, b3, n3 = reqs[2]
+    ids[srv.submit(w3, b3, n3, tag=2, history=True)] = 2
+    res += _drain(srv)
+    assert len(res) == 3 and all(r["status"] == 0 for r in res)
+    for r in res:
+        _, w, b, n = reqs[r["tag"]]
+        want = _solo_history(w, b, n, p.FSI_PREC_FP32)
+        assert r["history"].shape == want.shape
+        assert np.array_equal(r["history"], want), r["tag"]
+    srv.close()
+
+
+def test_served_flag_equals_a_context_run():
+    """A deformable body (the clamped flag of App. A) served, against a context run: the whole history."""
+    import paper_2103_06415_gb300 as p
+    w = wl.small_flag()
+    body = w["bodies"][0]
+    n = 12
+    srv = p.Server(16 << 30)
+    srv.submit(w, body, n, precision=p.FSI_PREC_FP64, history=True)
+    res = _drain(srv)[0]
+    assert res["status"] == 0 and res["steps"] == n
+    want = _solo_history(w, body, n, p.FSI_PREC_FP64)
+    assert np.array_equal(res["history"], want)
+    srv.close()
+
+
+def test_resident_runs_step_while_a_newcomer_is_admitted():
+    """The operator of a newcomer (a 1024^2 grid) is built on the server's worker thread: meanwhile every tick
+    still advances the resident run by one step."""
+    import paper_2103_06415_gb300 as p
+    small = wl.serving_requests(1, seed=8, sizes=(128,), steps=(4000, 4000))[0]
+    big = wl.serving_requests(1, seed=9, sizes=(1024,), steps=(3, 3))[0]
+    srv = p.Server(64 << 30)
+    srv.submit(small[1], small[2], small[3], tag=0)
+    while srv.stats()["active"] < 1:
+        srv.step()
+    srv.submit(big[1], big[2], big[3], tag=1)
+    ticks_while_admitting = 0
+    steps0 = srv.stats()["run_steps"]
+    for _ in range(20000):
+        srv.step()
+        st = srv.stats()
+        if st["admitting"] == 0:
+            break
+        ticks_while_admitting += 1
+    assert ticks_while_admitting >= 2
+    assert srv.stats()["run_steps"] - steps0 >= ticks_while_admitting   # the resident run kept stepping
+    srv.close()
