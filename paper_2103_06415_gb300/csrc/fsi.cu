@@ -1125,6 +1125,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
               const int n = bn_s[bb], off = boff_s[bb];
               const bool cp = couples(ba, bb), later = cp && ba == bb && bt_s[bb] == FSI_BODY_DEFORMABLE;
               const bool rank1 = cp && ba == bb && bt_s[bb] == FSI_BODY_TORSIONAL;
+              // a block of bodies that do not couple is read by nothing in the solve (residual rows, block
+              // products and rebuild take the coupled and diagonal blocks): its zeros are written in the first
+              // iteration of a launch only, for fsi_get_small_system
+              if (!cp && it > 0) continue;
               for (int t = tid; t < 2 * n; t += 128) {
                 const int cb = t >= n ? 1 : 0, pb = off + t - cb * n, cidx = cb * nb + pb;
                 double kv = 0.0;
@@ -1287,6 +1291,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         for (int bb = 0; bb < a.n_bodies; ++bb) {
           const int n = bn_s[bb], off = boff_s[bb];
           const bool cp = couples(ba, bb);
+          if (!cp && it > 0) continue;  // zeros written once per launch (see the flags' variant)
           for (int t = tid; t < 2 * n; t += nthr) {
             const int cidx = t < n ? off + t : nb + off + t - n;
             const double kv = cp ? k_entry(r, cidx, true) : 0.0;
