@@ -91,6 +91,7 @@ struct FsiArgs {
   int hist_cap;
   // deformable bodies: free dofs (x, y, theta of nodes 1..n-1) and elements, context-wide numbering
   int n_def, nd_tot, ne_tot, nd_max;
+  int nbody_max;  // points of the largest body
   double* bchi;   // [nd_tot] chi_n (updated at the end of the step)
   double* bzeta;  // [nd_tot] zeta_n
   double* bzdot;  // [nd_tot] zetadot_n
@@ -424,8 +425,15 @@ struct FsiLayout {
 struct BeamDims {
   int nd, ne, nd_max;  // free dofs and elements of all flags, dofs of the largest flag
   int nkb;             // bodies with a per-step kinematics block (all bodies when a driven plate exists)
+  int nbody_max;       // points of the largest body (the distributed variant's copy of X's owned blocks)
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+// Work area of the distributed variant (floats): a 64 x 33 + 32 x 64 tile of the block products, or the
+// owned rows' blocks of X (kMaxRB rows of 2 nbody_max floats)
+__host__ __device__ inline size_t fsi_big_work_floats(int nbody_max) {
+  const size_t t = 64 * 33 + 32 * 64, x = (size_t)kMaxRB * 2 * (size_t)nbody_max;
+  return t > x ? t : x;
+}
 // Row stride (floats) of the float matrices X, X K and K in global and shared memory: a multiple of 4 (rows
 // start on 16 bytes) with an odd number of 16-byte units, so that threads reading consecutive rows with
 // 128-bit loads hit distinct banks.  Columns nf .. ldx-1 stay zero.
@@ -445,7 +453,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd, boo
   L.vec = L.krow + (big ? 0 : al16((size_t)kMaxR * nf * 8));
   L.pw = L.vec + al16((size_t)3 * nf * 8);
   L.work = L.pw + al16((size_t)4 * nb * 8);
-  L.rf = L.work + (big ? al16((size_t)(64 * 33 + 32 * 64) * 4) : al16(lx * 16));
+  // big: the tiles of the block products, or between two changes of X the CTA's owned rows of X's blocks
+  L.rf = L.work + (big ? al16(fsi_big_work_floats(bd.nbody_max) * 4) : al16(lx * 16));
   L.pidx = L.rf + al16(lx * 4);
   L.pcij = L.pidx + al16((size_t)4 * nb * 4);
   L.pbody = L.pcij + al16((size_t)2 * nb * 4);
@@ -654,7 +663,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   const int R = (nf + (int)gridDim.x - 1) / (int)gridDim.x;
   const int r0 = min(nf, (int)blockIdx.x * R);
   const int nr = min(nf, r0 + R) - r0;
-  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max, a.nkb}, BIG);
+  const FsiLayout L = fsi_layout(nf, nb, BeamDims{a.nd_tot, a.ne_tot, a.nd_max, a.nkb, a.nbody_max}, BIG);
   float* Xs = reinterpret_cast<float*>(dyn_smem + L.xs);
   double* Krow = reinterpret_cast<double*>(dyn_smem + L.krow);
   double* rhs_s = reinterpret_cast<double*>(dyn_smem + L.vec);
@@ -787,6 +796,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   }
   int kinv_valid = *(volatile int*)&a.ctrl[4];
   int cur = *(volatile int*)&a.ctrl[7];
+  // BIG: changes of X in this launch, and the change whose owned-row blocks the tile area holds (-1: none)
+  int x_version = 0, xs_version = -1;
   __shared__ uint64_t xbar;  // bulk copies of X into shared memory
   uint32_t xphase = 0;
   if (tid == 0) {
@@ -1357,6 +1368,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       grid.sync();
       clk.sub(9);
       cur ^= 1;
+      ++x_version;
     };
     auto ns_refresh = [&]() {
       if constexpr (BIG) {  // one step: the error I - K X is squared, and a step costs four block GEMMs
@@ -1543,24 +1555,27 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         unsigned long long dbits64 = 0ull, xbits64 = 0ull;  // the same as double bit patterns (BIG)
         if constexpr (BIG) {  // owned rows of d = X r (block columns), shared through global memory
           const float* Xc = cur ? a.Xb : a.Xa;
+          // X changes only at a Newton-Schulz step or a rebuild, once or twice a time step, while a dozen
+          // solves apply it: each CTA keeps its owned rows' blocks of X in shared memory (the block products'
+          // tile area) from one change to the next.  (Read from global memory in every solve, the loads of
+          // this register-heavy kernel stay nearly serialised: 6.3 us per solve against 0.8 us for the same
+          // loop in a light kernel.)
+          const int w2 = 2 * a.nbody_max;
+          if (xs_version != x_version) {
+            for (int e = tid; e < nr * w2; e += nthr) {
+              const int c = e / w2, t = e - c * w2, i = r0 + c, bi = pb_s[i % nb];
+              const RowBlock b{boff_s[bi], bn_s[bi]};
+              if (t < 2 * b.n) tile[e] = __ldcg(&Xc[(long)i * lx + blk_col(b, nb, t)]);
+            }
+            __syncthreads();
+            xs_version = x_version;
+          }
           for (int c = wid; c < nr; c += nw) {
             const int i = r0 + c, bi = pb_s[i % nb];
             const RowBlock b{boff_s[bi], bn_s[bi]};
-            const float* xr = Xc + (long)i * lx;
+            const float* xs = tile + c * w2;
             float acc = 0.0f;
-            for (int t0 = lane; t0 < 2 * b.n; t0 += 32 * 16) {  // the lane's loads of the row issued together
-              float xv[16];
-#pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                const int t = t0 + 32 * u;
-                xv[u] = t < 2 * b.n ? __ldcg(&xr[blk_col(b, nb, t)]) : 0.0f;
-              }
-#pragma unroll
-              for (int u = 0; u < 16; ++u) {
-                const int t = t0 + 32 * u;
-                if (t < 2 * b.n) acc += xv[u] * rf[blk_col(b, nb, t)];
-              }
-            }
+            for (int t = lane; t < 2 * b.n; t += 32) acc += xs[t] * rf[blk_col(b, nb, t)];
             acc = warp_sum_f(acc);
             if (lane == 0) a.dvec[i] = (double)acc;
           }
@@ -1869,7 +1884,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
 }  // namespace
 
 static BeamDims beam_dims(const fsi_ctx* c) {
-  return BeamDims{c->nd_tot, c->ne_tot, c->nd_max, c->d_kin ? c->n_bodies : 0};
+  int nbmax = 0;
+  for (const auto& b : c->bodies) nbmax = b.n > nbmax ? b.n : nbmax;
+  return BeamDims{c->nd_tot, c->ne_tot, c->nd_max, c->d_kin ? c->n_bodies : 0, nbmax};
 }
 
 // Dynamic shared memory of the FSI kernel: the variant with the float inverse in shared memory, or (big) the
@@ -1957,6 +1974,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.nd_tot = c->nd_tot;
   a.ne_tot = c->ne_tot;
   a.nd_max = c->nd_max;
+  a.nbody_max = beam_dims(c).nbody_max;
   a.bchi = c->d_bchi;
   a.bzeta = c->d_bzeta;
   a.bzdot = c->d_bzdot;
