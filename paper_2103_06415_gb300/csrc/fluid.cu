@@ -246,23 +246,51 @@ __global__ void __launch_bounds__(256) k_ring_dst(TF* __restrict__ wf, TF* __res
   const c2* tws =
       dst::stage_twiddles<T>(buf + (long)nf * L, side ? twx : twy, L, ((size_t)nf * L + L) * sizeof(c2));
   dst::zero_ends<T>(buf, nf, L);
-  for (int idx = threadIdx.x; idx < nf * N; idx += blockDim.x) {
-    const int f = idx / N, n = idx - f * N;
-    T ab[2];
-    for (int e = 0; e < 2; ++e) {
-      const int v = v0 + 2 * f + e;
-      ab[e] = T(0);
-      if (v < 4) {
-        const int i = side ? n + 1 : ((v & 1) ? nx : 0);
-        const int j = side ? ((v & 1) ? ny : 0) : n + 1;
-        const bool is_w = v < 2;
-        const TF val = ring_value(is_w ? wc : sc, ps, nx, ny, i, j);
-        TF* fld = (is_w ? wf : sf) + (long)j * ps + i;
-        ab[e] = delta ? T(val - *fld) : T(val);
-        *fld = val;
+  // The gather of the coarse values (two per ring vertex, and the fine level's current value for an increment):
+  // a thread's loads for four of its vertices are issued before any is used (with only a few CTAs in the
+  // launch, one vertex at a time left the kernel waiting on one load after another).
+  constexpr int U = 4;
+  for (int idx0 = threadIdx.x; idx0 < nf * N; idx0 += blockDim.x * U) {
+    TF c0[U][2], c1[U][2], fo[U][2];
+    int fo_off[U][2];  // offset of the fine vertex; -1 where the vector does not exist
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = idx0 + u * (int)blockDim.x;
+      const int f = idx / N, n = idx - f * N;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int v = v0 + 2 * f + e;
+        fo_off[u][e] = -1;
+        if (idx < nf * N && v < 4) {
+          const int i = side ? n + 1 : ((v & 1) ? nx : 0);
+          const int j = side ? ((v & 1) ? ny : 0) : n + 1;
+          const TF* c = v < 2 ? wc : sc;
+          const int ia = i + nx / 2, jb = j + ny / 2;
+          const int I0 = ia >> 1, J0 = jb >> 1, I1 = I0 + (ia & 1), J1 = J0 + (jb & 1);
+          c0[u][e] = c[(long)J0 * ps + I0];
+          c1[u][e] = c[(long)J1 * ps + I1];
+          fo_off[u][e] = j * (int)ps + i;
+          fo[u][e] = delta ? (v < 2 ? wf : sf)[fo_off[u][e]] : TF(0);
+        }
       }
     }
-    dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = idx0 + u * (int)blockDim.x;
+      if (idx >= nf * N) break;
+      const int f = idx / N, n = idx - f * N;
+      T ab[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        ab[e] = T(0);
+        if (fo_off[u][e] >= 0) {
+          const TF val = field_mid(c0[u][e], c1[u][e]);  // injection at coincident vertices: c0 == c1
+          ab[e] = delta ? T(val - fo[u][e]) : T(val);
+          (v0 + 2 * f + e < 2 ? wf : sf)[fo_off[u][e]] = val;
+        }
+      }
+      dst::put_pair<T>(buf + (long)f * L, L, n, ab[0], ab[1]);
+    }
   }
   __syncthreads();
   if (side) dst::block_fft<T, PER, R3X>(buf, L, logL, tws);
