@@ -333,6 +333,10 @@ fsi_status fsi_debug_set_wait_limit(fsi_ctx* ctx, unsigned spin_limit, int missi
  * 21 grid barrier, 22 right-hand side; 23 the owned rows of d = X r and their barrier (distributed variant;
  * 11 is then the update of f).  out[0..n-1] (n <= 24 meaningful; synchronising). */
 fsi_status fsi_get_phase_times(fsi_ctx* ctx, double* out, int n);
+/* Phase timers of the FSI kernel on (nonzero: the counters read by fsi_get_phase_times are cleared and the
+ * steps that follow are timed) or off (the default: the timers' reads of the global timer sit in every
+ * step, about 1 % of the kernel's time).  Synchronising; a captured step is captured again. */
+fsi_status fsi_set_phase_timing(fsi_ctx* ctx, int on);
 
 /* Live timing of one kernel class: runs n_steps (1..1024) ordinary time steps without a graph, records a
  * CUDA event pair on the context stream around every launch of that class and returns the mean launch

@@ -253,6 +253,10 @@ class Context:
               "a_wait_points", "a_point_tables", "a_owned_rows", "a_wait_flags", "a_flag_term", "a_grid_barrier",
               "a_rhs", "solve_d_rows_barrier")
 
+    def set_phase_timing(self, on):
+        """Phase timers of the FSI kernel on (counters cleared) or off (the default)."""
+        check(self._lib.fsi_set_phase_timing(self._h, 1 if on else 0), "fsi_set_phase_timing")
+
     def phase_times(self):
         """Accumulated device wall time (ms) per phase of the FSI-iteration kernel."""
         out = np.zeros(len(self.PHASES))

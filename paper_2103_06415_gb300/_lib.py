@@ -100,6 +100,7 @@ SIGNATURES = {
     "fsi_debug_set_wait_limit": (_INT, [_P, ctypes.c_uint, _INT]),
     "fsi_profile_kernel": (_INT, [_P, _INT, _INT, _D, ctypes.POINTER(_INT)]),
     "fsi_get_phase_times": (_INT, [_P, _D, _INT]),
+    "fsi_set_phase_timing": (_INT, [_P, _INT]),
     "fsi_destroy": (None, [_P]),
     "fsi_op_level_solve": (_INT, [_INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D]),
     "fsi_op_level_solve_ex": (_INT, [_INT, _INT, _INT, _INT, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,

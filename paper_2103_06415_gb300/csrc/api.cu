@@ -1051,17 +1051,31 @@ extern "C" fsi_status fsi_get_stats(fsi_ctx* c, fsi_stats* out) {
   return FSI_OK;
 }
 
-extern "C" fsi_status fsi_debug_set_wait_limit(fsi_ctx* c, unsigned spin_limit, int missing_arrivals) {
-  if (!c || missing_arrivals < 0 || missing_arrivals > 1024) return FSI_ERR_INVALID_ARG;
-  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  c->wait_spins = spin_limit;
-  c->wait_missing = missing_arrivals;
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);  // the captured step holds the old kernel arguments
+// The captured step holds the kernels' arguments: drop it so that the next step captures anew.
+static void drop_graph(fsi_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->gexec = nullptr;
   c->graph = nullptr;
   c->graph_ok = 0;
   c->graph_failed = 0;
+}
+
+extern "C" fsi_status fsi_set_phase_timing(fsi_ctx* c, int on) {
+  if (!c) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (on && c->d_phase) FSI_CUDA_TRY(cudaMemset(c->d_phase, 0, 24 * sizeof(unsigned long long)));
+  if ((on != 0) != (c->phase_on != 0)) drop_graph(c);
+  c->phase_on = on != 0;
+  return FSI_OK;
+}
+
+extern "C" fsi_status fsi_debug_set_wait_limit(fsi_ctx* c, unsigned spin_limit, int missing_arrivals) {
+  if (!c || missing_arrivals < 0 || missing_arrivals > 1024) return FSI_ERR_INVALID_ARG;
+  FSI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->wait_spins = spin_limit;
+  c->wait_missing = missing_arrivals;
+  drop_graph(c);
   return FSI_OK;
 }
 

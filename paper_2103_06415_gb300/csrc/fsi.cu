@@ -1966,7 +1966,7 @@ fsi_status launch_fsi(fsi_ctx* c) {
   a.T = c->d_T;
   a.part = c->d_part;
   a.ctrl = c->d_ctrl;
-  a.phase_ns = c->d_phase;
+  a.phase_ns = c->phase_on ? c->d_phase : nullptr;  // timers only when asked for: they sit in every step
   a.status = c->d_status;
   a.hist = c->d_hist;
   a.hist_cap = c->hist_cap;

@@ -207,6 +207,7 @@ struct fsi_ctx {
   cudaGraphExec_t gexec;
   int graph_ok, graph_failed;
   int own_stream;     // stream created by the library (caller passed NULL)
+  int phase_on;  // in-kernel phase timers of the FSI kernel (fsi_set_phase_timing), off by default
   int first_pending;  // next step uses N^{n-1} := N^n (first step, or fields were overwritten)
   int stage;          // 0 = setup, 1 = precomputed
   // live kernel timing: events around every launch of one kernel class (eager steps only)

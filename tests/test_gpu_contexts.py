@@ -26,3 +26,27 @@ def test_larger_context_runs_after_a_smaller_one_is_set_up(coupling):
     assert np.array_equal(c_big.history(len(big["bodies"]) - 1), h_ref)
     c_small.close()
     c_big.close()
+
+
+def test_phase_timers_are_opt_in_and_leave_results_unchanged():
+    """The FSI kernel's phase timers are off by default (no counts); turned on they count the steps that
+    follow; the run's histories are the same bits with them on, off, and toggled mid-run (the captured step
+    is captured anew)."""
+    from paper_2103_06415_gb300 import workloads as wl
+    from runners import gpu_context
+    w = wl.small_flag()
+    ref = gpu_context(w)
+    ref.advance(9)
+    want = ref.history(0)
+    assert sum(ref.phase_times().values()) == 0.0
+    ref.close()
+    c = gpu_context(w)
+    c.advance(3)
+    c.set_phase_timing(True)
+    c.advance(3)
+    t = c.phase_times()
+    assert t["points_rhs"] > 0 and t["outputs"] > 0
+    c.set_phase_timing(False)
+    c.advance(3)
+    assert (c.history(0) == want).all()
+    c.close()
