@@ -199,6 +199,30 @@ __device__ double block_sum(double x, double* red) {
   return red[32];
 }
 
+// Sums over the CTA of K values per thread (nw K + K <= 256): each by warp butterflies, then warp 0 adds the
+// warps' partial sums in order; one set of barriers for all K.
+template <int K>
+__device__ void block_sum_k(double (&x)[K], double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) x[k] += __shfl_xor_sync(FULL, x[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[wid * K + k] = x[k];
+  __syncthreads();
+  if (wid == 0 && lane < K) {
+    double r = red[lane];
+    for (int w = 1; w < nw; ++w) r += red[w * K + lane];
+    red[nw * K + lane] = r;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) x[k] = red[nw * K + k];
+  __syncthreads();  // red is free again
+}
+
 __device__ double block_max(double x, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -418,7 +442,7 @@ __device__ void tri_inverse(const float* L, int n, int ld, float* W) {
 // (Mi, Bm, and per flag [Em | y] where the element tangents are staged before the factorization) and the
 // right-hand sides of the structural solves.
 struct FsiLayout {
-  size_t xs, krow, vec, pw, work, rf, pidx, pcij, pbody, tors;
+  size_t xs, krow, vec, pw, work, rf, pidx, pcij, pbody, tors, torsf;
   size_t chi, rz, cn, rchi, ref, fab, mi, bm, ey, ys, kb;
   size_t total;
 };
@@ -459,7 +483,8 @@ __host__ __device__ inline FsiLayout fsi_layout(int nf, int nb, BeamDims bd, boo
   L.pcij = L.pidx + al16((size_t)4 * nb * 4);
   L.pbody = L.pcij + al16((size_t)2 * nb * 4);
   L.tors = L.pbody + al16((size_t)nb * 4);
-  L.chi = L.tors + (big ? al16((size_t)nf * 8) : 0);
+  L.torsf = L.tors + (big ? al16((size_t)nf * 8) : 0);
+  L.chi = L.torsf + (big ? al16((size_t)nf * 4) : 0);
   L.rz = L.chi + al16((size_t)bd.nd * 8);
   L.cn = L.rz + al16((size_t)bd.nd * 8);
   L.rchi = L.cn + al16((size_t)bd.nd * 8);
@@ -677,6 +702,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   int* pb_s = reinterpret_cast<int*>(dyn_smem + L.pbody);  // body of every point
   // BIG: the torsional moment arm of every unknown at the iterate, (p - off) ds (-sin, cos)[component]
   double* tors_s = reinterpret_cast<double*>(dyn_smem + L.tors);
+  float* torsf_s = reinterpret_cast<float*>(dyn_smem + L.torsf);  // BIG: its float copy
   double* chi_s = reinterpret_cast<double*>(dyn_smem + L.chi);  // chi^(k) of every flag
   double* rz_s = reinterpret_cast<double*>(dyn_smem + L.rz);    // r^zeta(k)
   double* cn_s = reinterpret_cast<double*>(dyn_smem + L.cn);      // r^zeta_n of every free dof
@@ -845,6 +871,41 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     for (int al = 0; al < 4; ++al) acc += pw_s[4 * pa + al] * t[al];
     return acc;
   };
+  // window_acc in two halves, so that a thread can issue the loads of several entries before it sums any:
+  // v[4 al + be] = B0'[(ca, vertex al of pa)][(cb, vertex be of pb)] where the pair lies in the window (zero
+  // elsewhere, or everywhere when on is false); window_sum then adds exactly the terms window_acc adds, in its
+  // order, so the two give the same bits
+  auto window_load = [&](int ca, int pb, int cb, int dj0, int di0, bool on, double* v) {
+    const int bw = a.bw, side = 2 * bw + 1;
+    const long carea = (long)side * side;
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {
+      const long col = ((long)cb * a.n_sd + (on ? pidx_s[4 * pb + be] : 0)) * 2 * carea + (long)ca * carea;
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+        const bool in = on && dj >= -bw && dj <= bw && di >= -bw && di <= bw;
+        v[4 * al + be] = in ? a.Bw[col + (long)(dj + bw) * side + (di + bw)] : 0.0;
+      }
+    }
+  };
+  auto window_sum = [&](int pa, int pb, int dj0, int di0, const double* v) -> double {
+    const int bw = a.bw;
+    double wb[4], acc = 0.0;
+#pragma unroll
+    for (int be = 0; be < 4; ++be) wb[be] = pw_s[4 * pb + be];
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      double t = 0.0;
+#pragma unroll
+      for (int be = 0; be < 4; ++be) {
+        const int dj = dj0 + (al >> 1) - (be >> 1), di = di0 + (al & 1) - (be & 1);
+        if (dj >= -bw && dj <= bw && di >= -bw && di <= bw) t += wb[be] * v[4 * al + be];
+      }
+      acc += pw_s[4 * pa + al] * t;
+    }
+    return acc;
+  };
   // fluid_only: the sum over the hat vertices alone, without the factor ds/h^2 and the structural terms
   auto k_entry = [&](int r, int cidx, bool with_g, bool fluid_only = false) -> double {
     const double kscale = a.ds / (a.h * a.h);
@@ -953,6 +1014,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
   bool converged = false;
   int it = 0, solves_total = 0, refreshes = 0;
   for (; it < a.max_iters; ++it) {
+    // BIG with flags: the owned-row assembly below lists its near entries in the work area, over the cached owned
+    // rows of X (every thread drops the copy, so all take the same reload branch at the next solve)
+    if constexpr (BIG)
+      if (overlap_b) xs_version = -1;
     // ---- A: body points, P, right-hand side.  Points are split over the CTAs (four threads per point, one
     // per hat vertex; FP64 throughput per SM is low on sm_103), published, then every CTA takes all of them.
     for (int bi = tid; bi < a.n_bodies; bi += nthr)
@@ -973,6 +1038,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         const int p = k % nb, bb = pb_s[p];
         tors_s[k] = bt_s[bb] == FSI_BODY_TORSIONAL ? (double)(p - boff_s[bb]) * a.ds * (k < nb ? -b_sn[bb] : b_cs[bb])
                                                    : 0.0;
+        torsf_s[k] = (float)tors_s[k];
       }
       __syncthreads();
     }
@@ -1120,16 +1186,30 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         body_boxes(tid, 128, []() { named_sync_lower(); });
         side_sub(17);
         if constexpr (BIG) {
-          // owned rows stay in global memory, body block by body block: the blocks of bodies that do not
-          // couple (Omega_0 hat cells farther apart than the B0' window) are zero and cost one store per entry.
-          // S, the float copy, is written here except where a flag's structural term is still to come.
-          // (FP64 and double-to-float conversions run at a small fraction of the FP32 rate on this GPU: a far
-          // entry of a coupled block costs one multiply-add with the row's factor hoisted, a zero no conversion)
+          // Owned rows stay in global memory, body block by body block: the blocks of bodies that do not couple
+          // (Omega_0 hat cells farther apart than the B0' window) are zero and cost one store per entry.  S, the
+          // float copy, is written here except where a flag's structural term is still to come.  Two passes:
+          // (1) every entry without its window term -- zero, or the torsional rank-one term (one FP64 multiply-add
+          // with the row's factor hoisted; its float copy a float product, since FP64 instructions and
+          // double-to-float conversions run at a small fraction of the FP32 rate on this GPU) -- while the near
+          // entries (hat cells within the window: a band of ~2 x 29 columns around a row's own point) are listed
+          // in shared memory; (2) the listed entries dealt evenly over the threads, two per thread at a time with
+          // the loads of both windows issued before either is summed.  (Computed where they fall in the rows, a
+          // warp meets near entries in one or two of its column steps of every row, and each such step waits a
+          // full memory latency for its few lanes.)  The list lives in the work area that caches the owned rows
+          // of X between its changes, so that copy is reloaded at the next solve; entries beyond its capacity
+          // are computed in pass 1.
           const double kscale = a.ds / (a.h * a.h);
+          __shared__ int n_near;
+          int* nlist = reinterpret_cast<int*>(tile);
+          const int ncap = nf < 65536 ? (int)fsi_big_work_floats(a.nbody_max) : 0;  // (row, column) in one int
+          if (tid == 0) n_near = 0;
+          named_sync_lower();
           for (int c = 0; c < nr; ++c) {
             const int r = r0 + c, ca = r >= nb ? 1 : 0, pa = r - ca * nb, ba = pb_s[pa];
             const int cia = pcij_s[2 * pa], cja = pcij_s[2 * pa + 1];
             const double ka = bt_s[ba] == FSI_BODY_TORSIONAL ? b_kc[ba] * tors_s[r] : 0.0;
+            const float kaf = (float)ka;
             double* kr = a.K + (long)r * nf;
             float* sr = a.S + (long)r * lx;
             for (int bb = 0; bb < a.n_bodies; ++bb) {
@@ -1142,21 +1222,62 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
               if (!cp && it > 0) continue;
               for (int t = tid; t < 2 * n; t += 128) {
                 const int cb = t >= n ? 1 : 0, pb = off + t - cb * n, cidx = cb * nb + pb;
-                double kv = 0.0;
+                bool nz = false;
                 if (cp) {
-                  double acc = 0.0;
-                  if (dense) {
-                    acc = k_entry(r, cidx, false, true);
-                  } else {
-                    const int dj0 = cja - pcij_s[2 * pb + 1], di0 = cia - pcij_s[2 * pb];
-                    if (window_near(dj0, di0)) acc = window_acc(pa, ca, pb, cb, dj0, di0);
+                  const int dj0 = cja - pcij_s[2 * pb + 1], di0 = cia - pcij_s[2 * pb];
+                  nz = dense || window_near(dj0, di0);
+                  if (nz) {
+                    const int q = atomicAdd(&n_near, 1);
+                    if (q < ncap) {
+                      nlist[q] = (c << 16) | cidx;
+                      continue;
+                    }
                   }
-                  kv = acc != 0.0 ? kscale * acc : 0.0;
-                  if (rank1) kv += ka * tors_s[cidx];
                 }
+                double kv = 0.0;
+                float sv = 0.0f;
+                if (nz) {  // beyond the list's capacity
+                  const double acc = dense ? k_entry(r, cidx, false, true)
+                                           : window_acc(pa, ca, pb, cb, cja - pcij_s[2 * pb + 1], cia - pcij_s[2 * pb]);
+                  kv = acc != 0.0 ? kscale * acc : 0.0;
+                }
+                if (rank1) kv += ka * tors_s[cidx];
+                if (nz) sv = (float)kv;
+                else if (rank1) sv = kaf * torsf_s[cidx];
                 kr[cidx] = kv;
-                if (!later) sr[cidx] = cp ? (float)kv : 0.0f;
+                if (!later) sr[cidx] = sv;
               }
+            }
+          }
+          named_sync_lower();
+          const int nn = min(n_near, ncap);
+          for (int q0 = tid; q0 < nn; q0 += 256) {
+            int cq[2], idq[2], dj[2], di[2];
+            bool on[2];
+            double v[2][16];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int q = q0 + 128 * u;
+              on[u] = q < nn;
+              const int e = on[u] ? nlist[q] : 0;
+              cq[u] = e >> 16;
+              idq[u] = e & 0xffff;
+              const int r = r0 + cq[u], ca = r >= nb ? 1 : 0, pa = r - ca * nb;
+              const int cb = idq[u] >= nb ? 1 : 0, pb = idq[u] - cb * nb;
+              dj[u] = pcij_s[2 * pa + 1] - pcij_s[2 * pb + 1];
+              di[u] = pcij_s[2 * pa] - pcij_s[2 * pb];
+              window_load(ca, pb, cb, dj[u], di[u], on[u] && !dense, v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (!on[u]) continue;
+              const int c = cq[u], r = r0 + c, ca = r >= nb ? 1 : 0, pa = r - ca * nb, ba = pb_s[pa];
+              const int cidx = idq[u], cb = cidx >= nb ? 1 : 0, pb = cidx - cb * nb, bb = pb_s[pb];
+              const double acc = dense ? k_entry(r, cidx, false, true) : window_sum(pa, pb, dj[u], di[u], v[u]);
+              double kv = acc != 0.0 ? kscale * acc : 0.0;
+              if (ba == bb && bt_s[bb] == FSI_BODY_TORSIONAL) kv += (b_kc[ba] * tors_s[r]) * tors_s[cidx];
+              a.K[(long)r * nf + cidx] = kv;
+              if (!(ba == bb && bt_s[bb] == FSI_BODY_DEFORMABLE)) a.S[(long)r * lx + cidx] = (float)kv;
             }
           }
         } else {
@@ -1756,20 +1877,43 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     if (tid == 0 && !converged) dev_set_status(a.status, FSI_ERR_NOT_CONVERGED);
     for (int k = tid; k < nf; k += nthr) a.f[k] = f_s[k];  // surface stress for the corrector
     const int slot = a.ctrl[2] % a.hist_cap;
+    // force and moment sums of all bodies, kOs bodies at a time reduced together; a torsional body's S is that of
+    // the final solve, whose angle b_tp gave b_sn, b_cs at the start of the last iteration
+    constexpr int kOs = 5;
+    __shared__ double fsum_s[kMaxBodies][3];
+    for (int g0 = 0; g0 < a.n_bodies; g0 += kOs) {
+      double part[3 * kOs];
+#pragma unroll
+      for (int k = 0; k < kOs; ++k) {
+        double px = 0.0, py = 0.0, pm = 0.0;
+        const int bi = g0 + k;
+        if (bi < a.n_bodies) {
+          const bool tb = bt_s[bi] == FSI_BODY_TORSIONAL;
+          const double sn = tb ? b_sn[bi] : 0.0, cs = tb ? b_cs[bi] : 0.0;
+          const int off = boff_s[bi], n = bn_s[bi];
+          for (int p = off + tid; p < off + n; p += nthr) {
+            const double fxp = f_s[p], fyp = f_s[nb + p];
+            const double q = (double)(p - off) * a.ds;
+            px += fxp;
+            py += fyp;
+            pm += q * (-sn) * fxp + q * cs * fyp;
+          }
+        }
+        part[3 * k] = px;
+        part[3 * k + 1] = py;
+        part[3 * k + 2] = pm;
+      }
+      block_sum_k<3 * kOs>(part, red);
+      if (tid == 0)
+#pragma unroll
+        for (int k = 0; k < kOs; ++k)
+          if (g0 + k < a.n_bodies)
+            for (int m = 0; m < 3; ++m) fsum_s[g0 + k][m] = part[3 * k + m];
+    }
+    __syncthreads();
     for (int bi = 0; bi < a.n_bodies; ++bi) {
       const BodyDev b = a.bodies[bi];
-      double sn = 0.0, cs = 0.0;
-      if (b.type == FSI_BODY_TORSIONAL)  // S of the final solve
-        sincos((kb_s ? kb_s[bi * KB_N + KB_T0] : b.theta0) + b_tp[bi], &sn, &cs);
-      double px = 0.0, py = 0.0, pm = 0.0;
-      for (int p = b.off + tid; p < b.off + b.n; p += nthr) {
-        const double fxp = f_s[p], fyp = f_s[nb + p];
-        const double q = (double)(p - b.off) * a.ds;
-        px += fxp;
-        py += fyp;
-        pm += q * (-sn) * fxp + q * cs * fyp;
-      }
-      const double sx = block_sum(px, red), sy = block_sum(py, red), sm = block_sum(pm, red);
+      const double sx = fsum_s[bi][0], sy = fsum_s[bi][1], sm = fsum_s[bi][2];
       double tipd = 0.0, tipr = 0.0;
       if (b.type == FSI_BODY_DEFORMABLE) {
         const int N = b.n - 1, e0 = b.el_off, d0 = 3 * e0;

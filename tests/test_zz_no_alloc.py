@@ -4,8 +4,10 @@ The entry point serves callers that cannot call cudaMalloc themselves -- code th
 whose allocator owns all device memory, or a callback that must not allocate -- by keeping its transform
 scratch in a fixed array inside the library.  Here it is called through the C ABI with device buffers the
 test owns, twice in a row with different inputs, and its results are compared with the allocating entry
-point fsi_op_level_solve within the tolerances of the other parity tests (1e-12 FP64, 2e-5 FP32 relative).
-The file name makes pytest collect it last.
+point fsi_op_level_solve within the tolerances of the other parity tests (1e-12 FP64, 2e-5 FP32 relative);
+on the two smaller grids they are also compared with the FP64 oracle's dense sine-transform solves of the same
+right-hand sides, so that the check does not rest on a second CUDA path alone.  The file name makes pytest
+collect it last.
 """
 
 import ctypes
@@ -48,6 +50,14 @@ def test_noalloc_level_solve_matches_allocating_entry_point(prec, nx, ny):
         s = s_d.cpu().double().numpy()
         assert _rel(w[1:-1, 1:-1], w_ref) < tol
         assert _rel(s[1:-1, 1:-1], s_ref) < tol
+        if nx * ny <= 256 * 128:   # the oracle: A_w w = rhs, -lap_h s = w with zero boundary values (Eq. predictor2)
+            from oracle import grid as og
+            lev = og.Level(nx, ny, h, 0.0, 0.0)
+            zero = np.zeros(lev.shape)
+            w_or = og.solve_aw(rhs, zero, lev, re, dt)
+            s_or = og.solve_lap(w_or, zero, lev)
+            assert _rel(w[1:-1, 1:-1], w_or) < tol
+            assert _rel(s[1:-1, 1:-1], s_or) < tol
         ring = np.ones(w.shape, bool)
         ring[1:-1, 1:-1] = False
         assert np.all(w[ring] == 7.0) and np.all(s[ring] == -3.0)
