@@ -266,6 +266,18 @@ fsi_status fsi_sync(fsi_ctx* ctx);
 fsi_status fsi_get_forces(fsi_ctx* ctx, int body, double* fx, double* fy, double* moment);
 fsi_status fsi_get_deflection(fsi_ctx* ctx, int body, double* theta, double* phi);
 
+/* The same outputs of every body, read without waiting (the per-step read of a running job: the outputs of
+ * Algorithm 2's step, as above).  Enqueues on the context stream, behind the steps enqueued so far, copies
+ * into out[5 b + 0 .. 4] = fx, fy, moment, theta, phi of body b (theta, phi as fsi_get_deflection) for every
+ * body b; cap = capacity of out in values, at least 5 * (number of bodies).  The values are in place once the
+ * stream has passed the copies (after fsi_sync, or an event the caller records on the stream after this
+ * call); the caller owns out and keeps it alive until then.  For the call to return before the steps have
+ * run, out must be page-locked host memory (cudaHostAlloc or cudaHostRegister); with pageable memory the
+ * CUDA runtime finishes the copy before it returns.  The device status of the steps is not read here
+ * (fsi_sync returns it).  Errors: FSI_ERR_INVALID_ARG (NULL context or out, no bodies, cap too small);
+ * FSI_ERR_CUDA if the copy cannot be enqueued. */
+fsi_status fsi_read_outputs_async(fsi_ctx* ctx, double* out, int cap);
+
 /* State of a DEFORMABLE body after the last completed step (synchronising): chi = node positions and
  * rotations (x, y, theta) of nodes 1..n_pts-1 (3*(n_pts-1) values, node-major), zeta = their rates,
  * zetadot = their second derivatives.  cap = capacity of each non-NULL output array in values;

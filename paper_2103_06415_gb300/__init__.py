@@ -172,6 +172,13 @@ class Context:
               "fsi_get_forces")
         return fx.value, fy.value, m.value
 
+    def read_outputs_async(self, host_ptr, cap):
+        """Enqueue a copy of every body's (fx, fy, moment, theta, phi) after the steps enqueued so far into the
+        host memory at the integer address host_ptr (cap doubles, at least 5 per body; page-locked for the call
+        not to wait); the values are there after the next sync."""
+        check(self._lib.fsi_read_outputs_async(self._h, ctypes.c_void_p(host_ptr), int(cap)),
+              "fsi_read_outputs_async")
+
     def deflection(self, body=0):
         th, ph = ctypes.c_double(), ctypes.c_double()
         check(self._lib.fsi_get_deflection(self._h, body, ctypes.byref(th), ctypes.byref(ph)), "fsi_get_deflection")

@@ -87,6 +87,7 @@ SIGNATURES = {
     "fsi_sync": (_INT, [_P]),
     "fsi_get_forces": (_INT, [_P, _INT, _D, _D, _D]),
     "fsi_get_deflection": (_INT, [_P, _INT, _D, _D]),
+    "fsi_read_outputs_async": (_INT, [_P, _P, _INT]),
     "fsi_get_history": (_INT, [_P, _INT, _INT, _D, _INT, ctypes.POINTER(_INT)]),
     "fsi_get_beam_state": (_INT, [_P, _INT, _D, _D, _D, _INT, ctypes.POINTER(_INT)]),
     "fsi_get_field": (_INT, [_P, _INT, _INT, _D]),

@@ -870,6 +870,19 @@ extern "C" fsi_status fsi_get_forces(fsi_ctx* c, int body, double* fx, double* f
   return st;
 }
 
+extern "C" fsi_status fsi_read_outputs_async(fsi_ctx* c, double* out, int cap) {
+  if (!c || !out || !c->d_state) return FSI_ERR_INVALID_ARG;
+  const int nbody = (int)c->bodies.size();
+  if (nbody == 0 || cap < 5 * nbody) return FSI_ERR_INVALID_ARG;
+  // fx, fy, moment and theta, phi are two runs of consecutive doubles in every body's state record
+  const size_t pitch = sizeof(BodyState), row = 5 * sizeof(double);
+  FSI_CUDA_TRY(cudaMemcpy2DAsync(out, row, &c->d_state[0].fx, pitch, 3 * sizeof(double), nbody,
+                                 cudaMemcpyDeviceToHost, c->stream));
+  FSI_CUDA_TRY(cudaMemcpy2DAsync(out + 3, row, &c->d_state[0].theta, pitch, 2 * sizeof(double), nbody,
+                                 cudaMemcpyDeviceToHost, c->stream));
+  return FSI_OK;
+}
+
 extern "C" fsi_status fsi_get_deflection(fsi_ctx* c, int body, double* theta, double* phi) {
   BodyState s;
   fsi_status st = read_state(c, body, &s);

@@ -50,3 +50,31 @@ def test_phase_timers_are_opt_in_and_leave_results_unchanged():
     c.advance(3)
     assert (c.history(0) == want).all()
     c.close()
+
+
+def test_asynchronous_output_reads_match_the_synchronising_ones():
+    """fsi_read_outputs_async enqueued after every step into page-locked memory gives, once the stream is
+    synchronised, each step's forces and deflections of every body: equal to the step's history row (the
+    synchronising reads) and to fsi_get_forces / fsi_get_deflection after the last step; too small a buffer
+    is rejected."""
+    import torch
+
+    from paper_2103_06415_gb300 import _lib
+    w = wl.small_mixed_bodies()       # two flags and a torsional plate
+    nbody, n = len(w["bodies"]), 7
+    c = gpu_context(w)
+    out = torch.zeros((n, 5 * nbody), dtype=torch.float64, pin_memory=True)
+    row = 5 * nbody * 8
+    for k in range(n):
+        c.advance(1)
+        c.read_outputs_async(out.data_ptr() + k * row, 5 * nbody)
+    c.sync()
+    got = out.numpy()
+    for b in range(nbody):
+        h = c.history(b)[-n:]
+        assert np.array_equal(got[:, 5 * b:5 * b + 5], h[:, :5]), b
+        assert np.array_equal(got[-1, 5 * b:5 * b + 3], np.array(c.forces(b)))
+        assert np.array_equal(got[-1, 5 * b + 3:5 * b + 5], np.array(c.deflection(b)))
+    lib = _lib.load()
+    assert lib.fsi_read_outputs_async(c._h, out.data_ptr(), 5 * nbody - 1) == 1   # FSI_ERR_INVALID_ARG
+    c.close()
