@@ -488,7 +488,7 @@ def mixed_vs_fp64_horizon(w, n, make, lib, prec):
         c.advance(n)
         c.sync()
         el = time.perf_counter() - t0
-        hist[tag] = (np.stack([c.history(b) for b in range(len(w["bodies"]))]), el)
+        hist[tag] = (np.stack([c.history(b) for b in range(len(w["bodies"]))]), el, c.stats()["inverse_rebuilds"])
         c.close()
     names = ("fx", "fy", "moment", "deflection")
 
@@ -512,7 +512,8 @@ def mixed_vs_fp64_horizon(w, n, make, lib, prec):
                                                  "displacement (flag)",
                         "envelope": "FP64 vs FP64 with the initial deflection scaled by 1 + 1e-13",
                         "fsi_iterations_max": int(ref[:, :, 5].max()),
-                        "wall_s": {k: v[1] for k, v in hist.items()}}})
+                        "wall_s": {k: v[1] for k, v in hist.items()},
+                        "inverse_rebuilds": {k: v[2] for k, v in hist.items()}}})
     return out
 
 

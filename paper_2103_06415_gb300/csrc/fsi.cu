@@ -54,6 +54,11 @@ constexpr int kMaxRhs = 1 + kMaxR;  // structural solves per flag in phase A: y 
 // steps of a rebuild from a scaled identity.
 constexpr int kMaxRB = 12;
 constexpr int kNsRebuild = 30;
+// Refreshes (one Newton-Schulz step each) per solve attempt of the distributed variant: when one step leaves the
+// contraction above the trigger (a body moved far since X was last refreshed), a second or third squares the
+// error again; a rebuild from a scaled identity (kNsRebuild steps) is left for an inverse that diverged or an
+// attempt that did not converge.
+constexpr int kMaxRefreshB = 3;
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -1363,17 +1368,37 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       __syncthreads();
       a_sub(19);
       if constexpr (BIG) {  // only a flag's own block receives the term
-        for (int c = 0; c < nr; ++c) {
-          const int r = r0 + c, ba = pb_s[r % nb];
-          if (bt_s[ba] != FSI_BODY_DEFORMABLE) continue;
-          const int n = bn_s[ba], off = boff_s[ba];
-          for (int t = tid; t < 2 * n; t += nthr) {
-            const int cidx = t < n ? off + t : nb + off + t - n;
-            const double kv = a.K[(long)r * nf + cidx] + a.ds * a.two_dt * __ldcg(&a.G[(long)r * nf + cidx]);
-            a.K[(long)r * nf + cidx] = kv;
-            a.S[(long)r * lx + cidx] = (float)kv;
+        // four owned rows at a time, every K and G entry of the four loaded before any is updated (one memory
+        // latency per four rows instead of one per row)
+        const double gsc = a.ds * a.two_dt;
+        for (int c0 = 0; c0 < nr; c0 += 4)
+          for (int tb = 0; tb < 2 * a.nbody_max; tb += 2 * nthr) {
+            double kv[4][2], gv[4][2];
+            long ik[4][2], is[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + u, r = r0 + c, ba = c < nr ? pb_s[r % nb] : 0;
+              const int n = c < nr && bt_s[ba] == FSI_BODY_DEFORMABLE ? bn_s[ba] : 0, off = boff_s[ba];
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                const int t = tb + tid + v * nthr;
+                const int cidx = t < n ? off + t : nb + off + t - n;
+                ik[u][v] = t < 2 * n ? (long)r * nf + cidx : -1;
+                is[u][v] = t < 2 * n ? (long)r * lx + cidx : -1;
+                kv[u][v] = t < 2 * n ? a.K[ik[u][v]] : 0.0;
+                gv[u][v] = t < 2 * n ? __ldcg(&a.G[ik[u][v]]) : 0.0;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                if (ik[u][v] < 0) continue;
+                const double k = kv[u][v] + gsc * gv[u][v];
+                a.K[ik[u][v]] = k;
+                a.S[is[u][v]] = (float)k;
+              }
           }
-        }
       } else {
         for (int e = tid; e < nr * nf; e += nthr) {
           const int r = r0 + e / nf, cidx = e % nf;
@@ -1569,6 +1594,7 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
     };
     for (int attempt = 0; attempt < 2; ++attempt) {
       bool fresh = false;  // X was refreshed or rebuilt for this K
+      int n_refresh = 0;   // Newton-Schulz refreshes in this attempt (the distributed variant allows several)
       if (BIG && !kinv_valid) {
         // X0 = alpha I on every block with alpha = 1 / (largest absolute row sum of the block of K), so that the
         // eigenvalues of alpha K lie in the unit disc about 1, then Newton-Schulz steps to convergence
@@ -1767,9 +1793,10 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         if (s == kMaxSolves - 1) break;
         // X is stale for this K: refresh it, keep f and r (the distributed variant tolerates a slower
         // contraction before paying for its block GEMMs)
-        if (!fresh && s > 0 && ratio > (BIG ? 0.05 : kNsTrigger)) {
+        if ((BIG ? n_refresh < kMaxRefreshB : !fresh) && s > 0 && ratio > (BIG ? 0.05 : kNsTrigger)) {
           ns_refresh();
           ++refreshes;
+          ++n_refresh;
           fresh = true;
           gd_prev = 0.0;  // the next correction is the first one made with the new X: no ratio for it
         } else if (s > 0) {
