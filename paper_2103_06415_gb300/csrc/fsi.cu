@@ -1371,7 +1371,9 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         // four owned rows at a time, every K and G entry of the four loaded before any is updated (one memory
         // latency per four rows instead of one per row)
         const double gsc = a.ds * a.two_dt;
-        for (int c0 = 0; c0 < nr; c0 += 4)
+        bool any_flag = false;  // an owned row of a flag (the same in every thread)
+        for (int c = 0; c < nr; ++c) any_flag = any_flag || bt_s[pb_s[(r0 + c) % nb]] == FSI_BODY_DEFORMABLE;
+        for (int c0 = 0; any_flag && c0 < nr; c0 += 4)
           for (int tb = 0; tb < 2 * a.nbody_max; tb += 2 * nthr) {
             double kv[4][2], gv[4][2];
             long ik[4][2], is[4][2];
