@@ -1182,11 +1182,32 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
       if (overlap_b && wid < 4) {
         lower_grid_barrier(&a.ctrl[15], (it + 1) * (int)gridDim.x + a.lb_missing, a.status, a.lb_spins);
         side_sub(16);
-        for (int e = tid; e < 4 * nb; e += 128) {
-          pidx_s[e] = __ldcg(&a.pidx[e]);
-          pw_s[e] = __ldcg(&a.pw[e]);
+        for (int e0 = tid; e0 < 4 * nb; e0 += 128 * 8) {  // eight entries' loads in flight per thread
+          int iv[8];
+          double wv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 128 * u;
+            iv[u] = e < 4 * nb ? __ldcg(&a.pidx[e]) : 0;
+            wv[u] = e < 4 * nb ? __ldcg(&a.pw[e]) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 128 * u;
+            if (e < 4 * nb) {
+              pidx_s[e] = iv[u];
+              pw_s[e] = wv[u];
+            }
+          }
         }
-        for (int e = tid; e < 2 * nb; e += 128) pcij_s[e] = __ldcg(&a.pcij[e]);
+        for (int e0 = tid; e0 < 2 * nb; e0 += 128 * 8) {
+          int cv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) cv[u] = e0 + 128 * u < 2 * nb ? __ldcg(&a.pcij[e0 + 128 * u]) : 0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (e0 + 128 * u < 2 * nb) pcij_s[e0 + 128 * u] = cv[u];
+        }
         named_sync_lower();
         body_boxes(tid, 128, []() { named_sync_lower(); });
         side_sub(17);
@@ -1228,12 +1249,19 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
               for (int t = tid; t < 2 * n; t += 128) {
                 const int cb = t >= n ? 1 : 0, pb = off + t - cb * n, cidx = cb * nb + pb;
                 bool nz = false;
-                if (cp) {
+                if (cp) {  // cp is the same in every thread
                   const int dj0 = cja - pcij_s[2 * pb + 1], di0 = cia - pcij_s[2 * pb];
                   nz = dense || window_near(dj0, di0);
-                  if (nz) {
-                    const int q = atomicAdd(&n_near, 1);
-                    if (q < ncap) {
+                  // list slots taken warp by warp: one shared-memory atomic per warp step (per-lane atomics on
+                  // the one counter serialise)
+                  const unsigned act = __activemask(), m = __ballot_sync(act, nz);
+                  if (m) {
+                    const int lead = __ffs(act) - 1;
+                    int base = 0;
+                    if (lane == lead) base = atomicAdd(&n_near, __popc(m));
+                    base = __shfl_sync(act, base, lead);
+                    const int q = base + __popc(m & ((1u << lane) - 1u));
+                    if (nz && q < ncap) {
                       nlist[q] = (c << 16) | cidx;
                       continue;
                     }
