@@ -838,7 +838,7 @@ def roofline(ctx, w, lib, torch, local):
             # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu capture of the same kernel
             # on the two-level variant of this workload (same nf, bodies, B0' window half-width 13), whose
             # launch does the same per-step work
-            "traffic": 16710912 + 253952 if nf == 1608 else None,
+            "traffic": 16719616 + 232192 if nf == 1608 else None,
             "traffic_note": "ncu capture of k_fsi<BIG> on tandem_1536x768_reduced (nf = 1608, window 13): the "
                             "launch's units (body points, owned rows, window columns) equal this workload's",
             "algorithmic_flops_per_launch": {"fp64": fp64_flops, "fp32": fp32_flops}, "avg_launch_ms": fsi_ms,
