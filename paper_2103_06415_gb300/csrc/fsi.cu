@@ -570,7 +570,9 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // kept in global memory with K's float copy S.  Row r of the block of body b has its columns at
 // off + t (t < n) and nb + off + t - n (n <= t < 2n).  A CTA owns rows r0 .. r0 + nr - 1 of every matrix;
 // consecutive owned rows with the same block form a group, whose rows are multiplied together so that each
-// CTA reads the block operand once per product.
+// CTA reads the block operand once per product.  X is refreshed by one Newton-Schulz step when the refinement
+// contracts by more than 0.05 per solve, up to kMaxRefreshB times per solve attempt, and rebuilt from a scaled
+// identity only when it diverged or an attempt did not converge.
 struct RowBlock {
   int off, n;
 };
