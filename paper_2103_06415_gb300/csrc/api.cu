@@ -1,4 +1,5 @@
 // C ABI: context life cycle, offline/online stages and read-back (see include/ibfsi.h).
+#include <cstddef>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -876,9 +877,10 @@ extern "C" fsi_status fsi_read_outputs_async(fsi_ctx* c, double* out, int cap) {
   if (nbody == 0 || cap < 5 * nbody) return FSI_ERR_INVALID_ARG;
   // fx, fy, moment and theta, phi are two runs of consecutive doubles in every body's state record
   const size_t pitch = sizeof(BodyState), row = 5 * sizeof(double);
-  FSI_CUDA_TRY(cudaMemcpy2DAsync(out, row, &c->d_state[0].fx, pitch, 3 * sizeof(double), nbody,
+  const char* st = reinterpret_cast<const char*>(c->d_state);  // device address: offsets only, no access
+  FSI_CUDA_TRY(cudaMemcpy2DAsync(out, row, st + offsetof(BodyState, fx), pitch, 3 * sizeof(double), nbody,
                                  cudaMemcpyDeviceToHost, c->stream));
-  FSI_CUDA_TRY(cudaMemcpy2DAsync(out + 3, row, &c->d_state[0].theta, pitch, 2 * sizeof(double), nbody,
+  FSI_CUDA_TRY(cudaMemcpy2DAsync(out + 3, row, st + offsetof(BodyState, theta), pitch, 2 * sizeof(double), nbody,
                                  cudaMemcpyDeviceToHost, c->stream));
   return FSI_OK;
 }
