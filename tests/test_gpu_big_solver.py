@@ -80,9 +80,9 @@ def test_distributed_solver_agrees_with_shared_memory_solver(lib, precision, bou
 
 
 def _plate_201():
-    """A 201-point torsional plate at ds = h = 1/200 (chord 1, 20 degrees, config 5's first plate) on one level
-    of 384 x 256 cells, Omega_0 [-0.1, 1.1] x [-0.1, 0.5], B0' filtered at eps = 0.007: nf = 402, beyond the
-    shared-memory solver."""
+    """A 201-point torsional plate at ds = h = 1/200 (chord 1, 20 degrees: the first plate of the 5-level
+    1536 x 768 tandem workload) on one level of 384 x 256 cells, Omega_0 [-0.1, 1.1] x [-0.1, 0.5], B0'
+    filtered at eps = 0.007: nf = 402, beyond the shared-memory solver."""
     h = 1.0 / 200
     return dict(name="plate_201_sparse", nx=384, ny=256, n_levels=1, x0=-0.3, y0=-0.64, h=h, re=1000.0, dt=2e-4,
                 uinf=(1.0, 0.0), steps=2, sd_box=(-0.1, 1.1, -0.1, 0.5), ds=h, drop_tol=0.007,

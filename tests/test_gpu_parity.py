@@ -1,8 +1,8 @@
 """Parity of the CUDA library against the FP64 oracle (needs a GB300 and the built library).
 
 Tolerances: the FP64 path is held to 1e-12 relative on single solves and B0 entries, and multi-step
-histories to about ten times the measured difference (1e-12 on the small plate, 4e-11 over config 1's 100
-steps; rounding-order differences grow slowly through the time loop).  The FP32 fluid
+histories to about ten times the measured difference (1e-12 on the small plate, 4e-11 over the 128 x 128
+plate's 100 steps; rounding-order differences grow slowly through the time loop).  The FP32 fluid
 path reports its error against the oracle and is held to the bounds stated in each test.
 """
 
