@@ -1824,7 +1824,8 @@ __global__ void __launch_bounds__(256, 1) k_fsi(FsiArgs a) {
         }
         if (s == kMaxSolves - 1) break;
         // X is stale for this K: refresh it, keep f and r (the distributed variant tolerates a slower
-        // contraction before paying for its block GEMMs)
+        // contraction before paying for its block GEMMs, and refreshes again, up to kMaxRefreshB times, while
+        // the contraction measured after a refresh stays above its trigger)
         if ((BIG ? n_refresh < kMaxRefreshB : !fresh) && s > 0 && ratio > (BIG ? 0.05 : kNsTrigger)) {
           ns_refresh();
           ++refreshes;
